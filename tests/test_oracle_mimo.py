@@ -1,0 +1,143 @@
+"""Pins for the oracle's A2 (CMA), A3 (FO estimate) and A4 (segmented DD-LMS)."""
+
+import numpy as np
+import pytest
+
+from oracle import cdc, mimo, qam, theory
+from oracle.receiver import RxConfig, receive
+from synth import LinkParams, generate, workload
+
+
+def test_butterfly_and_gradient_by_explicit_loops():
+    rng = np.random.default_rng(0)
+    T, S, off = 5, 40, 1
+    x = rng.normal(size=(2, S)) + 1j * rng.normal(size=(2, S))
+    h = rng.normal(size=(2, 2, T)) + 1j * rng.normal(size=(2, 2, T))
+    n = np.arange(-1, 22)
+    X = mimo.gather(x, n, T, off)
+    y = mimo.butterfly(h, X)
+    e = rng.normal(size=(2, n.size)) + 1j * rng.normal(size=(2, n.size))
+    g = mimo.gradient(e, X)
+    c = (T - 1) // 2
+    xs = lambda p, i: x[p, i] if 0 <= i < S else 0.0
+    for q in range(2):
+        for i, nn in enumerate(n):
+            ref = sum(h[q, p, k] * xs(p, off + 2 * nn + c - k) for p in range(2) for k in range(T))
+            assert abs(y[q, i] - ref) < 1e-12
+        for p in range(2):
+            for k in range(T):
+                ref = sum(e[q, i] * np.conj(xs(p, off + 2 * nn + c - k)) for i, nn in enumerate(n))
+                assert abs(g[q, p, k] - ref) < 1e-12
+
+
+def test_dd_block_update_by_explicit_loops():
+    """One DD-LMS block (phase, decision, error, update) written out symbol by symbol."""
+    rng = np.random.default_rng(1)
+    m, T, L = 4, 3, 6
+    x = 0.5 * (rng.normal(size=(2, 40)) + 1j * rng.normal(size=(2, 40)))
+    h = mimo.identity_taps(T) + 0.05 * (rng.normal(size=(2, 2, T)) + 1j * rng.normal(size=(2, 2, T)))
+    mu = 0.01
+    y, h2 = mimo._dd_blocks(x, h[None], np.arange(5, 5 + L)[None], m, mu, 0)
+    c = 1
+    ref_h = h.copy()
+    for q in range(2):
+        yq = [sum(h[q, p, k] * x[p, 2 * n + c - k] for p in range(2) for k in range(T)) for n in range(5, 5 + L)]
+        assert np.allclose(y[0, q], yq, atol=1e-13)
+        s4 = sum(v ** 4 for v in yq)
+        psi = np.arctan2((-s4).imag, (-s4).real) / 4
+        for i, n in enumerate(range(5, 5 + L)):
+            d = qam.decide(np.array([yq[i] * np.exp(-1j * psi)]), m)[0]
+            err = d * np.exp(1j * psi) - yq[i]
+            for p in range(2):
+                for k in range(T):
+                    ref_h[q, p, k] += mu * err * np.conj(x[p, 2 * n + c - k])
+    assert np.allclose(h2[0], ref_h, atol=1e-13)
+
+
+def _noiseless_link(m=2, **kw):
+    base = dict(bits_per_sym=m, symbol_rate=32e9, n_sym=1 << 14, length=80e3, linewidth=0.0,
+                freq_offset=0.0, snr_db=None, jones=True)
+    base.update(kw)
+    return LinkParams(**base)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_cma_recovers_a_unitary_on_noiseless_input(seed):
+    p = _noiseless_link()
+    fr = generate(p, seed)
+    cfg = RxConfig(bits_per_sym=2, symbol_rate=p.symbol_rate, length=p.length, fft_size=1024,
+                   n_taps=15, lms_block=64, bps_phases=32, bps_window=64)
+    r = receive(fr.samples, cfg, fr.ref_words)
+    # combined DC response of the acquired CMA taps times the channel's Jones matrix
+    W = r.taps_cma.sum(axis=-1) * r.scale[None, :]
+    G = W @ fr.jones
+    P = np.abs(G)
+    if P[0, 1] > P[0, 0]:
+        G = G[::-1]
+    D = G / np.abs(np.diag(G)).mean()
+    assert np.max(np.abs(D @ D.conj().T - np.eye(2))) < 1e-2        # unitary x diag, up to a permutation
+    assert np.max(np.abs(D - np.diag(np.diag(D)))) < 1e-2        # crosstalk below -40 dB
+    evm2 = r.counts["evm_num"] / r.counts["evm_den"]
+    assert 10 * np.log10(evm2) < -30
+    assert r.counts["bit_errors"] == 0
+
+
+def test_large_offset_is_removed_on_noiseless_input():
+    p = _noiseless_link(freq_offset=1.3e9)
+    fr = generate(p, 4)
+    cfg = RxConfig(bits_per_sym=2, symbol_rate=p.symbol_rate, length=p.length, fft_size=1024,
+                   n_taps=15, lms_block=64, bps_phases=32, bps_window=64)
+    r = receive(fr.samples, cfg, fr.ref_words)
+    assert r.fo_code == 13000
+    # the matched filter sits ahead of the derotation, so a 4 % offset clips the band edge: about -26 dB
+    assert 10 * np.log10(r.counts["evm_num"] / r.counts["evm_den"]) < -24
+    assert r.counts["bit_errors"] == 0
+    # the corrected taps on the derotated samples give the CMA outputs, derotated:
+    # y'[n] = y[n] exp(-j 2 w n) with w the offset per sample
+    n = np.arange(2048, 4096)
+    xd = mimo.derotate(r.cdc, r.fo_code, cfg.fo_grid_hz, cfg.fs, 0)
+    y1 = mimo.butterfly(r.taps_foe, mimo.gather(xd, n, cfg.n_taps, 0))
+    y0 = mimo.butterfly(r.taps_cma, mimo.gather(r.cdc, n, cfg.n_taps, 0))
+    w = 2 * np.pi * r.fo_code * cfg.fo_grid_hz / cfg.fs
+    assert np.max(np.abs(y1 - y0 * np.exp(-1j * w * 2 * n))) < 1e-9
+
+
+def test_foe_exact_code_on_noiseless_grid_offset():
+    rng = np.random.default_rng(3)
+    Rs, grid, L_b = 32e9, 100e3, 128
+    for true_code in (0, 7, -4321, 5000, 30000):
+        s = qam.alphabet(2)[rng.integers(0, 4, size=(2, 4096))]
+        w = 2 * np.pi * true_code * grid / Rs
+        y = s * np.exp(1j * (w * np.arange(4096) + rng.uniform(0, 6, (2, 1))))
+        code, what, _ = mimo.foe_code(y, Rs, grid, L_b)
+        assert code == true_code
+        assert what == pytest.approx(w, abs=1e-9)
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_foe_within_one_grid_step_at_12db(m):
+    rng = np.random.default_rng(4)
+    Rs, grid, L_b = 32e9, 100e3, 128
+    for trial in range(4):
+        f0 = rng.uniform(-1e9, 1e9)
+        s = qam.alphabet(m)[rng.integers(0, 2**m, size=(2, 8192))]
+        sig = np.sqrt(1 / (2 * 10 ** 1.2))
+        y = s * np.exp(1j * 2 * np.pi * f0 / Rs * np.arange(8192)) + sig * (
+            rng.normal(size=s.shape) + 1j * rng.normal(size=s.shape))
+        code, _, _ = mimo.foe_code(y, Rs, grid, L_b)
+        assert abs(code * grid - f0) < grid
+
+
+def test_segment_schedule_costs_nothing():
+    """Segmented DD-LMS BER lies within binomial 3 sigma of the fully serial schedule."""
+    w = workload("dp-16qam-32gbd", n_sym=1 << 16)
+    p = w["link"].with_(snr_db=15.0)
+    fr = generate(p, 5)
+    cfg = RxConfig.from_dict(w["rx"])
+    seg = receive(fr.samples, cfg, fr.ref_words).counts
+    cfg_serial = RxConfig.from_dict(dict(w["rx"], seg_blocks=1 << 20))
+    ser = receive(fr.samples, cfg_serial, fr.ref_words).counts
+    b1, b2 = seg["bit_errors"] / seg["bits"], ser["bit_errors"] / ser["bits"]
+    pth = theory.gray_qam_ber(4, 15.0)
+    sigma = np.sqrt(pth * (1 - pth) / seg["bits"])
+    assert abs(b1 - b2) < 3 * sigma * 1.5

@@ -1,0 +1,69 @@
+"""Plausible mistakes planted in the oracle (on the CPU) must make a pin fail.
+
+Each case patches one oracle function with a typical slip (a sign, a missing
+conjugate, an argmax for an argmin, a non-Gray map) and re-runs a pin from the
+other test files; the pin has to raise.
+"""
+
+import numpy as np
+import pytest
+
+import oracle.bps as obps
+import oracle.cdc as ocdc
+import oracle.mimo as omimo
+import oracle.qam as oqam
+from tests import test_oracle_bps, test_oracle_cdc, test_oracle_mimo, test_oracle_qam
+
+
+def test_flipped_dispersion_sign_is_caught(monkeypatch):
+    real = ocdc.cdc_response
+    monkeypatch.setattr(ocdc, "cdc_response", lambda n, fs, D, L, lam, *a, **k: real(n, fs, -D, L, lam, *a, **k))
+    with pytest.raises(AssertionError):
+        test_oracle_cdc.test_cd_all_pass_round_trip(50)
+
+
+def test_missing_conjugate_in_gradient_is_caught(monkeypatch):
+    monkeypatch.setattr(omimo, "gradient", lambda e, X: np.einsum("...qn,...pnk->...qpk", e, X))
+    with pytest.raises(AssertionError):
+        test_oracle_mimo.test_butterfly_and_gradient_by_explicit_loops()
+
+
+def test_reversed_tap_index_is_caught(monkeypatch):
+    real = omimo.gather
+    monkeypatch.setattr(omimo, "gather", lambda x, n, T, off: real(x, n, T, off)[..., ::-1])
+    with pytest.raises(AssertionError):
+        test_oracle_mimo.test_butterfly_and_gradient_by_explicit_loops()
+
+
+def test_argmax_instead_of_argmin_is_caught(monkeypatch):
+    real = obps.window_sums
+    monkeypatch.setattr(obps, "window_sums", lambda d, W, **k: -real(d, W))
+    with pytest.raises(AssertionError):
+        test_oracle_bps.test_bps_matches_brute_force_on_tiny_inputs(2, 4, 4)
+
+
+def test_off_by_one_window_is_caught(monkeypatch):
+    real = obps.window_sums
+    monkeypatch.setattr(obps, "window_sums", lambda d, W, **k: real(d, W + 1))
+    with pytest.raises(AssertionError):
+        test_oracle_bps.test_bps_matches_brute_force_on_tiny_inputs(4, 4, 4)
+
+
+def test_natural_binary_map_is_caught(monkeypatch):
+    monkeypatch.setattr(oqam, "_level_to_gray", lambda l: l)
+    with pytest.raises(AssertionError):
+        test_oracle_qam.test_gray_map_is_a_bijection_with_single_bit_neighbours(4)
+
+
+def test_fo_correction_with_wrong_sign_is_caught(monkeypatch):
+    real = omimo.fo_correct_taps
+    monkeypatch.setattr(omimo, "fo_correct_taps", lambda h, code, grid, fs: real(h, -code, grid, fs))
+    with pytest.raises(AssertionError):
+        test_oracle_mimo.test_large_offset_is_removed_on_noiseless_input()
+
+
+def test_derotation_with_wrong_sign_is_caught(monkeypatch):
+    real = omimo.derotate
+    monkeypatch.setattr(omimo, "derotate", lambda x, code, grid, fs, g0: real(x, -code, grid, fs, g0))
+    with pytest.raises(AssertionError):
+        test_oracle_mimo.test_large_offset_is_removed_on_noiseless_input()
