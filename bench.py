@@ -1,0 +1,340 @@
+"""Throughput benchmark of the dual-polarisation coherent receiver on GB300.
+
+Workload: DP-16QAM at 32 GBd, one frame of 2^20 symbols per polarisation at
+2 samples/symbol (complex64), 80 km SSMF dispersion, Jones rotation, 100 kHz
+linewidth, 500 MHz offset, SNR 20 dB; FFT 4096 (50 % overlap), 21-tap 2x2
+MIMO with 128-symbol blocks, 64 BPS phases over 64 symbols. Synthetic, seeded.
+
+A step is one rx_process call over the whole frame (every stage A0-A6,
+including the per-frame acquisition, alignment and BER counting). `value` is
+decided line rate (2 * m * N bits per frame, edges included) over the CUDA
+event time of the step with the input already in HBM; `e2e` is the same
+metric through rx_process_host from pinned host memory, copies included. L2
+is flushed (a 512 MiB write) between timed steps, outside the timed region.
+
+`--impl reference` times the FP64 CPU oracle (the reference arm here) on a
+bounded sample of the same workload on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "dp-16qam-32gbd"
+SEED = 1
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+# --------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on a bounded sample
+# --------------------------------------------------------------------------------------
+
+CPU_SAMPLE_SYMBOLS = 1 << 18
+
+
+def oracle_worker(n_sym: int, reps: int) -> dict:
+    from oracle.receiver import Receiver, RxConfig
+    from synth import generate, workload
+    w = workload(WORKLOAD, n_sym=n_sym)
+    fr = generate(w["link"], SEED)
+    cfg = RxConfig.from_dict(w["rx"])
+    rx = Receiver(cfg)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        rx.process(fr.samples, fr.ref_words)
+        times.append(time.perf_counter() - t0)
+    bits = 2 * w["link"].bits_per_sym * n_sym
+    return dict(times=times, bits=bits)
+
+
+def run_oracle_subprocess(n_sym: int, reps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_worker(%d, %d)))" % (ROOT, n_sym, reps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(reps: int = 3) -> dict:
+    res = run_oracle_subprocess(CPU_SAMPLE_SYMBOLS, reps)
+    t = statistics.median(res["times"])
+    return {"value": res["bits"] / t / 1e9, "unit": "Gb/s", "cores": 1, "kind": "oracle",
+            "sample": f"{WORKLOAD} frame of {CPU_SAMPLE_SYMBOLS} symbols/pol (of 2^20), full chain A0-A6 in FP64 "
+                      f"NumPy, single thread, median of {reps}"}
+
+
+def reference_arm(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle_subprocess(CPU_SAMPLE_SYMBOLS, args.warmup + args.steps)
+    times = res["times"][args.warmup:]
+    t = sum(times) / len(times)
+    v = res["bits"] / t / 1e9
+    line = {"metric": "processed line rate", "value": v, "unit": "Gb/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "symbols_per_pol": CPU_SAMPLE_SYMBOLS, "sample_of": 1 << 20},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "Gb/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{CPU_SAMPLE_SYMBOLS} symbols/pol per step, FP64 NumPy, single thread"},
+            "e2e": {"value": v, "unit": "Gb/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------
+# roofline of a stage
+# --------------------------------------------------------------------------------------
+
+def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz: float | None) -> dict:
+    rxs = w["rx"]
+    m = rxs["bits_per_sym"]
+    clock_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12      # Tops/s, 1 op per lane per clock
+    t = ms * 1e-3
+    if stage == "bps":
+        ops = 2 * n_sym * rxs["bps_phases"] * 16          # FP32 ops per (symbol, test phase)
+        a = ops / t / 1e12
+        return {"kernel": "k_bps", "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
+                "frac": a / alu_peak, "traffic": None, "algorithmic_ops": ops}
+    if stage == "lms":
+        ops = n_sym * 32 * rxs["n_taps"]                  # FMA per output symbol pair: outputs + gradient
+        a = ops / t / 1e12
+        return {"kernel": "k_lms", "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
+                "frac": a / alu_peak, "traffic": None, "algorithmic_ops": ops}
+    # HBM-bound stages: compulsory bytes
+    byts = {"cdc": 2 * (2 * n_sym) * 8 * 2, "unwrap": 2 * n_sym * (8 + 1 + 8 + 4),
+            "count": 2 * n_sym * 8 + 2 * 2 * n_sym * m / 8}.get(stage, 0)
+    a = byts / t / 1e9 if t > 0 else 0.0
+    peak = pk.get("hbm_gbs", 6800.0)
+    return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+            "traffic": None, "algorithmic_bytes": byts}
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+
+def our_arm(args) -> None:
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import Receiver
+    from synth import generate, workload
+
+    w = workload(WORKLOAD)
+    link = w["link"]
+    N = link.n_sym
+    m = link.bits_per_sym
+    fr = generate(link, SEED + rank)
+    x_host = np.ascontiguousarray(fr.samples.astype(np.complex64))
+    ref_host = np.ascontiguousarray(fr.ref_words.astype(np.uint32))
+    x = torch.from_numpy(x_host.view(np.float32)).cuda()
+    ref = torch.from_numpy(ref_host.view(np.int32)).cuda()
+    rcv = Receiver(w["rx"], N)
+    out = torch.zeros(2 * rcv.words(N), dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    bits_per_step = 2 * m * N
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-resident steps
+    for _ in range(args.warmup):
+        rcv.process(x, N, ref, out)
+    barrier()
+    rx.rx_set_timing(rcv.h, True)
+    launches0 = rx.rx_launch_count(rcv.h)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            rcv.process(x, N, ref, out)
+            evs[i][1].record(stream)
+        barrier()
+    launches = rx.rx_launch_count(rcv.h) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    stages = rx.rx_stage_times(rcv.h)
+    rx.rx_set_timing(rcv.h, False)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = rcv.stats()
+
+    # end to end from pinned host memory
+    xh = torch.from_numpy(x_host.view(np.float32)).pin_memory()
+    rh = torch.from_numpy(ref_host.view(np.int32)).pin_memory()
+    oh = torch.zeros(2 * rcv.words(N), dtype=torch.int32).pin_memory()
+    for _ in range(args.warmup):
+        rcv.process_host(xh, N, rh, oh)
+    barrier()
+    e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e_evs[i][0].record(stream)
+        rcv.process_host(xh, N, rh, oh)
+        e_evs[i][1].record(stream)
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e_evs)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    csum = clk.summary()
+    per_stage = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
+    dom = max(per_stage, key=per_stage.get)
+    roof = stage_roofline(dom, per_stage[dom], w, N, pk, csum.get("sm_mhz"))
+    roof["peak_source"] = "fallback" if pk.get("fallback") else "measured (MEASURED_PEAKS.json) / nominal unit count"
+    value = world * bits_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    e2e = world * bits_per_step * args.steps / (e2e_ms * 1e-3) / 1e9
+    line = {
+        "metric": "processed line rate", "value": value, "unit": "Gb/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "symbols_per_pol": N, "bits_per_sym": m, "symbol_rate_gbd": 32,
+                   "fft": 4096, "taps": 21, "bps_phases": 64, "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "e2e": {"value": e2e, "unit": "Gb/s", "h2d_bytes_per_step": int(x_host.nbytes + ref_host.nbytes),
+                "d2h_bytes_per_step": int(oh.numel() * 4)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        "ber": st["ber"], "evm": st["evm"], "fo_code": st["fo_code"],
+        "clocks": csum,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as e:  # report, do not hide
+            line["cpu_baseline"] = {"error": str(e)[:300]}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

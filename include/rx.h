@@ -1,0 +1,215 @@
+/*
+ * rx.h - C ABI of librx, a dual-polarisation coherent receiver for sm_103a.
+ *
+ * One handle processes frames of 2 samples/symbol complex ADC samples of two
+ * polarisations into decided bits, with BER/EVM counters:
+ *
+ *   A0  power normalisation of the ADC samples
+ *   A1  overlap-save frequency-domain chromatic-dispersion compensation with
+ *       the RRC matched filter (paper Sec. III-A: 1024-point FFT, "100 %"
+ *       overlap-save, 512 valid samples per block, FD multiply with 128-bit
+ *       accesses; Sec. IV-C: matched filtering in the FD static filter)
+ *   A2  2x2 butterfly FIR MIMO: CMA acquisition, then block DD-LMS
+ *   A3  frequency-offset estimate (4th-power periodogram peak + 4th-power
+ *       phase slope) and derotation by a 64-bit fixed-point phase accumulator
+ *   A4  segmented block DD-LMS with in-loop 4th-power block phase (the paper's
+ *       serial TD DD-LMS with warp shuffles, Sec. IV-D, made parallel by a
+ *       fixed segment schedule)
+ *   A5  blind phase search with an exact integer unwrap (the paper's serial
+ *       warp-level phase unwrap, Sec. III-B, becomes a parallel scan)
+ *   A6  polarisation/rotation/delay alignment, Gray demapping, bit and symbol
+ *       error counting (Sec. II-D Step 6; Q from BER, Sec. V-D)
+ *
+ * Conventions (all entry points):
+ *  - Every pointer named d_* is DEVICE memory on the handle's device, owned by
+ *    the caller; every pointer named h_* is HOST memory owned by the caller.
+ *  - Sample layout: [2 polarisations][S] contiguous, S = 2 * n_sym samples per
+ *    polarisation; complex samples are interleaved (I, Q) pairs of the input
+ *    format (float32, float16 or int8).
+ *  - Bit layout: [2][ceil(n_sym * m / 32)] uint32 words, bit i of a
+ *    polarisation is bit (i % 32) of word i / 32; symbol n carries bits
+ *    n*m .. n*m+m-1, the first m/2 are the Gray word of the in-phase level
+ *    (MSB first), the last m/2 that of the quadrature level.
+ *  - Work is enqueued on the caller's stream and is asynchronous; rx_process
+ *    neither allocates nor synchronises. Handles are not thread-safe.
+ *  - Errors are returned as rx_status and never thrown across the ABI.
+ *    Faults seen on the device (non-finite input, a failed alignment) set
+ *    bits of the error word reported by rx_stats.
+ */
+#ifndef RX_H
+#define RX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* rx_stream_t; /* same object as cudaStream_t */
+typedef struct rx_handle rx_handle;
+
+typedef enum {
+    RX_OK = 0,
+    RX_EINVAL = -1,   /* bad argument or configuration */
+    RX_ENOMEM = -2,   /* device allocation failed in rx_create */
+    RX_ECUDA = -3,    /* a CUDA call failed; rx_stats reports the CUDA error text */
+    RX_ETIMEOUT = -4, /* a bounded device wait gave up */
+    RX_ESTATE = -5    /* call out of order (e.g. a state blob of another config) */
+} rx_status;
+
+typedef enum { RX_IN_C64 = 0, RX_IN_F16 = 1, RX_IN_I8 = 2 } rx_input;
+
+/* Device error word bits (rx_stats.error_word). */
+#define RX_ERR_NONFINITE 0x1u   /* a non-finite sample reached the equaliser */
+#define RX_ERR_SYNC_LOST 0x2u   /* best alignment matched < 90 % of the sync window */
+#define RX_ERR_SINGULAR 0x4u    /* CMA outputs still correlated after the rerun */
+
+typedef struct rx_config {
+    int32_t bits_per_sym;       /* m per polarisation: 2 (QPSK), 4 (16QAM), 6 (64QAM) */
+    int32_t sps;                /* samples per symbol; must be 2 */
+    double symbol_rate_hz;      /* Rs */
+    double wavelength_m;        /* lambda, for the dispersion filter */
+    double dispersion_s_per_m2; /* D (17e-6 = 17 ps/nm/km) */
+    double length_m;            /* L; H_cdc = exp(+j pi D L lambda^2 f^2 / c) */
+    double rrc_rolloff;         /* matched filter in the FD stage; 0 = none */
+    int32_t fft_size;           /* FD block N = 2^K, 512..8192; keeps N/2 per block */
+    int32_t n_taps;             /* T, odd, 3..63 */
+    int32_t lms_block;          /* L_b symbols per block update, 16..256 */
+    int32_t cma_blocks;         /* CMA acquisition blocks (first frame) */
+    int32_t dd_acq_blocks;      /* DD-LMS acquisition blocks (first frame) */
+    int32_t seg_blocks;         /* blocks per DD-LMS segment */
+    int32_t warmup_blocks;      /* warm-up blocks ahead of every segment but the first */
+    int32_t bps_phases;         /* B test phases, 2..64 */
+    int32_t bps_window;         /* W symbols, even, 2..64 */
+    int32_t edge_skip;          /* E: symbols left out of the counts at each frame edge */
+    int32_t sync_len;           /* symbols of the alignment window, 1..32768 */
+    int32_t max_delay;          /* alignment searches delays in [-max_delay, max_delay] */
+    float mu_cma;               /* CMA step */
+    float mu_dd;                /* DD-LMS step */
+    double fo_grid_hz;          /* frequency-offset quantum (code * grid = offset) */
+    int32_t input_format;       /* rx_input */
+    float input_scale;          /* multiplies every input value (e.g. the int8 step) */
+    int32_t streaming;          /* 0: each call is one frame; 1: calls are frames of one stream */
+    int64_t max_symbols;        /* largest n_sym per call (sizes the workspace) */
+} rx_config;
+
+typedef struct rx_stats_t {
+    uint64_t frames;            /* rx_process calls since create/reset */
+    uint64_t symbols_processed; /* 2 * sum of n_sym */
+    uint64_t bits_processed;    /* m * symbols_processed */
+    uint64_t bits_counted;      /* bits inside the counted windows */
+    uint64_t bit_errors;
+    uint64_t symbols_counted;
+    uint64_t symbol_errors;
+    double evm_num, evm_den;    /* sum |z - s|^2 and sum |s|^2 over the counted symbols */
+    double ber;                 /* bit_errors / bits_counted */
+    double evm;                 /* sqrt(evm_num / evm_den) */
+    double q_db;                /* 20 log10(sqrt(2) erfcinv(2 BER)); +inf when BER = 0 */
+    int32_t fo_code;            /* frequency offset = fo_code * fo_grid_hz */
+    double fo_hz;
+    int32_t pol_map[2];         /* tx polarisation of each output */
+    int32_t rotation[2];        /* quarter turns applied to each output */
+    int32_t delay[2];           /* symbol delay of each output */
+    int32_t sync_matches[2];    /* decisions matching in the sync window */
+    int32_t sync_len;           /* length of the sync window used */
+    int32_t cma_reran;          /* 1 if the singularity check restarted CMA */
+    float cma_rho;              /* output correlation after the first CMA pass */
+    int32_t latency_symbols;    /* output delay of a stream (0 for single frames) */
+    uint32_t error_word;        /* RX_ERR_* bits */
+} rx_stats_t;
+
+/* Internal buffers that rx_get_buffer can export (for inspection and tests). */
+typedef enum {
+    RX_BUF_CDC = 0,      /* float2 [2][S]   A1 output of the last frame */
+    RX_BUF_Y = 1,        /* float2 [2][N]   A4 equaliser output (P1) */
+    RX_BUF_Z = 2,        /* float2 [2][N]   A5 carrier-recovered symbols (P2) */
+    RX_BUF_BSTAR = 3,    /* uint8  [2][N]   A5 chosen test phase */
+    RX_BUF_M = 4,        /* int32  [2][N]   A5 unwrap quarter-turn count */
+    RX_BUF_TAPS_CMA = 5, /* float2 [2][2][T] taps after CMA (first frame) */
+    RX_BUF_TAPS_INIT = 6,/* float2 [2][2][T] taps the segments start from */
+    RX_BUF_TAPS_LAST = 7,/* float2 [2][2][T] final taps of the last segment */
+    RX_BUF_Y_ACQ = 8,    /* float2 [2][N_acq] CMA outputs while adapting */
+    RX_BUF_Y_FOE = 9,    /* float2 [2][N_acq/2] fixed-tap outputs the FO estimate uses */
+    RX_BUF_SCALE = 10    /* float  [2]      A0 scale */
+} rx_buffer;
+
+/*
+ * rx_create: validate *cfg, allocate every device buffer the handle will use
+ * (sized by cfg->max_symbols) on the current device and precompute the FD
+ * filter. No allocation happens after this call. Returns RX_EINVAL for an
+ * invalid configuration, RX_ENOMEM when the device is out of memory.
+ * The caller owns *out and frees it with rx_destroy.
+ */
+rx_status rx_create(const rx_config* cfg, rx_handle** out);
+
+/*
+ * rx_process: run the chain A0-A6 on one frame of n_sym symbols per
+ * polarisation (d_in: [2][2*n_sym] samples of cfg->input_format).
+ * d_ref_bits (nullable): the transmitted bits in the bit layout above; when
+ * given, the frame is aligned (first frame of a stream, or every call in
+ * single-frame mode) and errors are counted on [E, n_sym - E).
+ * d_out_bits (nullable): receives the decided bits of each output
+ * polarisation, quarter turn applied, in output order.
+ * Asynchronous on `stream`; RX_EINVAL for n_sym < 1, n_sym > max_symbols or
+ * (streaming) n_sym not a multiple of fft_size / 4.
+ */
+rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32_t* d_ref_bits,
+                     uint32_t* d_out_bits, rx_stream_t stream);
+
+/*
+ * rx_process_host: the same frame from HOST buffers. Copies h_in (and
+ * h_ref_bits, nullable) to handle-owned device staging buffers on `stream`,
+ * runs rx_process and copies the decided bits back to h_out_bits (nullable).
+ * Asynchronous: the host buffers must stay valid until the stream reaches
+ * this point (pinned memory makes the copies asynchronous).
+ */
+rx_status rx_process_host(rx_handle* h, const void* h_in, int64_t n_sym, const uint32_t* h_ref_bits,
+                          uint32_t* h_out_bits, rx_stream_t stream);
+
+/* rx_stats: wait for the last stream used by the handle, then fill *out. */
+rx_status rx_stats(rx_handle* h, rx_stats_t* out);
+
+/*
+ * rx_get_buffer: enqueue a device-to-device copy of an internal buffer
+ * (rx_buffer) of the last frame into d_dst (bytes must equal the buffer
+ * size, which rx_buffer_bytes returns). Not part of the timed path.
+ */
+rx_status rx_buffer_bytes(rx_handle* h, int32_t which, int64_t* bytes);
+rx_status rx_get_buffer(rx_handle* h, int32_t which, void* d_dst, int64_t bytes, rx_stream_t stream);
+
+/* rx_reset: forget the stream state and zero the counters (synchronous). */
+rx_status rx_reset(rx_handle* h);
+
+/*
+ * Checkpoint/resume of a stream: rx_state_size gives the blob size; get
+ * copies the carried state (dispersion tail, equaliser history, taps, FO
+ * code, unwrap state, alignment, counters) to host memory; set restores it
+ * into a handle created with the same configuration (RX_ESTATE otherwise).
+ * Both synchronise the handle's last stream.
+ */
+rx_status rx_state_size(rx_handle* h, size_t* bytes);
+rx_status rx_state_get(rx_handle* h, void* h_blob, size_t bytes);
+rx_status rx_state_set(rx_handle* h, const void* h_blob, size_t bytes);
+
+/*
+ * Per-stage timing: with timing on, rx_process records CUDA events around
+ * each stage on the caller's stream; rx_stage_times returns, per stage, the
+ * total milliseconds and launch count since timing was switched on
+ * (synchronises). Stage names come from rx_stage_name.
+ */
+rx_status rx_set_timing(rx_handle* h, int32_t enable);
+int32_t rx_stage_count(void);
+const char* rx_stage_name(int32_t stage);
+rx_status rx_stage_times(rx_handle* h, double* ms, int64_t* launches, int32_t n);
+
+/* Kernels launched by this handle since creation (all stages). */
+uint64_t rx_launch_count(rx_handle* h);
+
+void rx_destroy(rx_handle* h);
+const char* rx_strerror(rx_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RX_H */

@@ -1,0 +1,327 @@
+// A5 blind phase search (Pfau, Hoffmann, Noe 2009), integer unwrap, derotation.
+//
+// Test phases theta_b = (b/B - 1/2) pi/2. For symbol k and phase b,
+// dist = |y_k e^{-j theta_b} - dec(.)|^2 and D[k, b] is its sum over the window
+// [k - W/2, k + W/2) clipped to the frame; b*_k = argmin_b D (first minimum).
+//
+// Layout: one thread per test phase and strip of LEN consecutive symbols
+// (32 or 64 threads per strip), strips of one polarisation side by side in a
+// CTA. The strip's symbols (with a W/2 halo on each side) are staged in
+// shared memory and read as broadcasts. Each thread keeps the last W
+// distances of its phase in registers (a ring indexed at compile time), slides
+// the window sum by one add and one subtract per symbol and re-forms it as a
+// direct sum of the ring every W symbols, which bounds the rounding drift to
+// that of a W-term sum. The minimum over phases is one warp-wide min reduction
+// of the (non-negative) sums' bit patterns plus a ballot for the first lane
+// holding it, so ties go to the smallest b exactly. The decision per real
+// dimension is evaluated in level units: v = r / (2a) + (L-1)/2, the nearest
+// level is rint(clamp(v, 0, L-1)), computed with a saturating multiply and
+// the 1.5 * 2^23 rounding constant, so the distance costs only FMA-pipe
+// instructions.
+//
+// The paper's phase unwrap (Sec. III-B) is a single warp walking the blocks
+// in order; here the unwrap is exact integer arithmetic on b*, so it becomes
+// a three-step scan: per-tile jump sums, a scan of the tile sums with the
+// carried count, then per-tile prefixes that also write z.
+#include "rx_kernels.h"
+
+namespace {
+
+constexpr int BPS_THREADS = 256;
+
+template <int W, int GS>
+__global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ y, int64_t ystride, int64_t N, int B,
+                                                   float cI0, float hL, float invLm1, float Lm1, int LEN,
+                                                   uint8_t* __restrict__ bstar, int64_t bstride) {
+    constexpr int NSTRIP = BPS_THREADS / GS;
+    constexpr int NW = GS / 32;
+    extern __shared__ float2 ys[];                    // [NSTRIP][LEN + W]
+    __shared__ unsigned int wmin[NSTRIP][NW][W];
+    __shared__ unsigned char wb[NSTRIP][NW][W];
+    const int tid = threadIdx.x;
+    const int sl = tid / GS;                          // strip within the CTA
+    const int b = tid % GS;
+    const int lane = tid & 31, wip = b >> 5;          // warp within the strip
+    const int q = blockIdx.y;
+    const int64_t strip = (int64_t)blockIdx.x * NSTRIP + sl;
+    const int64_t s0 = strip * LEN;
+    const int span = LEN + W;
+    const float2* yq = y + (int64_t)q * ystride;
+    float2* yl = ys + sl * span;
+
+    // stage y[s0 - W/2, s0 + LEN + W/2), zero outside [0, N)
+    for (int t = tid; t < NSTRIP * span; t += BPS_THREADS) {
+        const int st = t / span, u = t - st * span;
+        const int64_t i = ((int64_t)blockIdx.x * NSTRIP + st) * LEN - W / 2 + u;
+        ys[st * span + u] = (i >= 0 && i < N) ? yq[i] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+
+    // rotation by e^{-j theta_b} folded with 1/(2a): r_I = y_I c + y_Q s, r_Q = y_Q c - y_I s
+    float sn, cs;
+    sincospif((float)((double)b / (double)B - 0.5) * 0.5f, &sn, &cs);
+    const float c = cs * cI0, s = sn * cI0;
+    const bool active = b < B;
+    const float MAGIC = 12582912.0f;                  // 1.5 * 2^23
+
+    float ring[W];
+    float D = 0.0f;
+    const int nchunks = 1 + (LEN + W - 1) / W;
+    unsigned int keep = 0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int li = ch * W + u;                // local index into yl (symbol s0 - W/2 + li)
+            float d = 0.0f;
+            if (li < span) {
+                const float2 v = yl[li];
+                const float vI = fmaf(v.x, c, fmaf(v.y, s, hL));
+                const float vQ = fmaf(v.y, c, fmaf(-v.x, s, hL));
+                const float wI = __saturatef(vI * invLm1);
+                const float wQ = __saturatef(vQ * invLm1);
+                const float tI = fmaf(wI, Lm1, MAGIC) - MAGIC;
+                const float tQ = fmaf(wQ, Lm1, MAGIC) - MAGIC;
+                const float eI = vI - tI, eQ = vQ - tQ;
+                d = fmaf(eI, eI, eQ * eQ);
+                const int64_t gi = s0 - W / 2 + li;
+                if (gi < 0 || gi >= N) d = 0.0f;
+            }
+            if (ch == 0) {
+                ring[u] = d;
+            } else {
+                D = (D + d) - ring[u];
+                ring[u] = d;
+            }
+            // the window of symbol k = s0 - W/2 + li - W/2 + 1 is complete
+            const int kl = li - W + 1;                // local output index (symbol s0 + kl)
+            if (ch == 0 && u == W - 1) {
+                float t = 0.0f;
+#pragma unroll
+                for (int r = 0; r < W; ++r) t += ring[r];
+                D = t;
+            }
+            if (kl >= 0 && kl < LEN) {
+                const unsigned int bits = active ? __float_as_uint(fmaxf(D, 0.0f)) : 0xffffffffu;
+                const unsigned int mn = __reduce_min_sync(0xffffffffu, bits);
+                const unsigned int bal = __ballot_sync(0xffffffffu, bits == mn);
+                const int first = __ffs(bal) - 1;
+                if (NW == 1) {
+                    if (lane == (kl & 31)) keep = (unsigned)first;
+                    if ((kl & 31) == 31 || kl == LEN - 1) {
+                        const int64_t k = s0 + (kl & ~31) + lane;
+                        if (lane <= (kl & 31) && k < N) bstar[(int64_t)q * bstride + k] = (uint8_t)keep;
+                    }
+                } else {
+                    if (lane == 0) {
+                        wmin[sl][wip][kl % W] = mn;
+                        wb[sl][wip][kl % W] = (unsigned char)(first + 32 * wip);
+                    }
+                }
+            }
+        }
+        if (ch > 0) {                                 // re-form the sum directly from the ring
+            float t = 0.0f;
+#pragma unroll
+            for (int r = 0; r < W; ++r) t += ring[r];
+            D = t;
+        }
+        if (NW > 1) {
+            __syncthreads();
+            // combine the two warps of each strip for the outputs of this chunk
+            const int kl0 = ch * W - W + 1;           // first local output of this chunk
+            for (int u = b; u < W; u += GS) {
+                const int kl = kl0 + u;
+                if (kl >= 0 && kl < LEN && s0 + kl < N) {
+                    const unsigned int m0 = wmin[sl][0][kl % W], m1 = wmin[sl][1][kl % W];
+                    const unsigned char r = (m1 < m0) ? wb[sl][1][kl % W] : wb[sl][0][kl % W];
+                    bstar[(int64_t)q * bstride + s0 + kl] = r;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int W, int GS>
+cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
+                  cudaStream_t s) {
+    const Qam qm = make_qam(m);
+    const int LEN = 512;
+    constexpr int NSTRIP = BPS_THREADS / GS;
+    const int64_t nstrip = (N + LEN - 1) / LEN;
+    dim3 grid((unsigned)((nstrip + NSTRIP - 1) / NSTRIP), 2);
+    const size_t smem = sizeof(float2) * NSTRIP * (LEN + W);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bps<W, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const float Lm1 = (float)(qm.L - 1);
+    k_bps<W, GS><<<grid, BPS_THREADS, smem, s>>>(y, ystride, N, B, qm.half_inv_a, qm.hL, 1.0f / Lm1, Lm1, LEN, bstar,
+                                                bstride);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t bps_w(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
+                  cudaStream_t s) {
+    if (B <= 32) return bps_t<W, 32>(y, ystride, N, B, m, bstar, bstride, s);
+    return bps_t<W, 64>(y, ystride, N, B, m, bstar, bstride, s);
+}
+
+// ---------------------------------------------------------------------------
+// unwrap: m_k = m_{k-1} + J(b*_{k-1} - b*_k), J(d) = +1 (d > B/2), -1 (d < -B/2), 0
+// ---------------------------------------------------------------------------
+constexpr int UT = 1024;          // symbols per tile
+constexpr int UTHR = 256;         // 4 symbols per thread
+
+__device__ __forceinline__ int jump(int prev, int cur, int B) {
+    const int d = prev - cur;
+    return (2 * d > B) ? 1 : ((2 * d < -B) ? -1 : 0);
+}
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* red, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += n;
+    }
+    if (lane == 31) red[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += n;
+        }
+        red[lane] = t;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? red[w - 1] : 0) + x - v;
+    if (total) *total = red[(blockDim.x >> 5) - 1];
+    return before;
+}
+
+__global__ void k_unwrap_sums(const uint8_t* __restrict__ bstar, int64_t bstride, int64_t N, int B,
+                              const RxDevState* st, int* tile_sums, int ntiles) {
+    __shared__ int red[32];
+    const int q = blockIdx.y;
+    const uint8_t* bq = bstar + (int64_t)q * bstride;
+    const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;
+    int sum = 0;
+    for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + u;
+        if (k < N) {
+            int prev;
+            if (k > 0) prev = bq[k - 1];
+            else prev = st->b_prev[q] >= 0 ? st->b_prev[q] : bq[0];
+            sum += jump(prev, bq[k], B);
+        }
+    }
+    int total;
+    block_exclusive_scan(sum, red, &total);
+    if (threadIdx.x == 0) tile_sums[q * ntiles + blockIdx.x] = total;
+}
+
+__global__ void k_unwrap_scan(int* tile_sums, int ntiles, const RxDevState* st) {
+    __shared__ int red[32];
+    const int q = blockIdx.x;
+    int carry = st->m_prev[q];
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < ntiles ? tile_sums[q * ntiles + i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, red, &total);
+        __syncthreads();
+        if (i < ntiles) tile_sums[q * ntiles + i] = carry + ex;     // becomes the tile's base
+        carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, const uint8_t* __restrict__ bstar,
+                               int64_t bstride, int64_t N, int B, const int* tile_base, int ntiles,
+                               const RxDevState* st, int* m_out, int64_t mstride, float2* z, int64_t zstride) {
+    __shared__ int red[32];
+    __shared__ float2 rot[RX_BPS_MAXB];
+    const int q = blockIdx.y;
+    if (threadIdx.x < B) {
+        double s, c;
+        sincospi(-((double)threadIdx.x / (double)B - 0.5) * 0.5, &s, &c);   // e^{-j theta_b}
+        rot[threadIdx.x] = make_float2((float)c, (float)s);
+    }
+    const uint8_t* bq = bstar + (int64_t)q * bstride;
+    const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;
+    int J[4], bs[4];
+    int sum = 0;
+    for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + u;
+        J[u] = 0;
+        bs[u] = 0;
+        if (k < N) {
+            bs[u] = bq[k];
+            int prev;
+            if (k > 0) prev = bq[k - 1];
+            else prev = st->b_prev[q] >= 0 ? st->b_prev[q] : bs[u];
+            J[u] = jump(prev, bs[u], B);
+        }
+        sum += J[u];
+    }
+    int m = tile_base[q * ntiles + blockIdx.x] + block_exclusive_scan(sum, red, nullptr);
+    __syncthreads();
+    for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + u;
+        m += J[u];
+        if (k < N) {
+            m_out[(int64_t)q * mstride + k] = m;
+            float2 v = cmul(y[(int64_t)q * ystride + k], rot[bs[u]]);
+            switch (m & 3) {                          // (-j)^(m mod 4)
+                case 1: v = make_float2(v.y, -v.x); break;
+                case 2: v = make_float2(-v.x, -v.y); break;
+                case 3: v = make_float2(-v.y, v.x); break;
+                default: break;
+            }
+            z[(int64_t)q * zstride + k] = v;
+        }
+    }
+}
+
+__global__ void k_unwrap_commit(const uint8_t* bstar, int64_t bstride, const int* m_out, int64_t mstride, int64_t N,
+                                RxDevState* st) {
+    const int q = threadIdx.x;
+    if (q < 2 && N > 0) {
+        st->b_prev[q] = bstar[(int64_t)q * bstride + N - 1];
+        st->m_prev[q] = m_out[(int64_t)q * mstride + N - 1];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bps(const float2* y, int64_t ystride, int64_t N, int B, int W, int m, uint8_t* bstar,
+                       int64_t bstride, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    switch (W) {
+        case 2: return bps_w<2>(y, ystride, N, B, m, bstar, bstride, s);
+        case 4: return bps_w<4>(y, ystride, N, B, m, bstar, bstride, s);
+        case 8: return bps_w<8>(y, ystride, N, B, m, bstar, bstride, s);
+        case 16: return bps_w<16>(y, ystride, N, B, m, bstar, bstride, s);
+        case 32: return bps_w<32>(y, ystride, N, B, m, bstar, bstride, s);
+        case 64: return bps_w<64>(y, ystride, N, B, m, bstar, bstride, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_unwrap(const float2* y, int64_t ystride, const uint8_t* bstar, int64_t bstride, int64_t N, int B,
+                          int* tile_sums, int* m_out, int64_t mstride, float2* z, int64_t zstride, RxDevState* st,
+                          cudaStream_t s, int* nlaunch) {
+    if (N <= 0) return cudaSuccess;
+    const int ntiles = (int)((N + UT - 1) / UT);
+    k_unwrap_sums<<<dim3(ntiles, 2), UTHR, 0, s>>>(bstar, bstride, N, B, st, tile_sums, ntiles);
+    k_unwrap_scan<<<2, 1024, 0, s>>>(tile_sums, ntiles, st);
+    k_unwrap_apply<<<dim3(ntiles, 2), UTHR, 0, s>>>(y, ystride, bstar, bstride, N, B, tile_sums, ntiles, st, m_out,
+                                                    mstride, z, zstride);
+    k_unwrap_commit<<<1, 32, 0, s>>>(bstar, bstride, m_out, mstride, N, st);
+    if (nlaunch) *nlaunch += 4;
+    return cudaGetLastError();
+}

@@ -1,0 +1,204 @@
+// A6 alignment, Gray hard demapping, bit/symbol error and EVM counting.
+//
+// Paper anchor: decisions are demapped on the GPU and the bits go to host
+// memory (Sec. II-D Step 6); quality is a Q-factor derived from the BER of
+// each 21 ms section (Sec. V-D). A blind receiver must first find which
+// transmitted polarisation, quarter turn and symbol delay each output
+// carries: 16 CTAs (output q, tx pol p, turn r) count decision matches for
+// every delay in [-D, D] over the sync window (a warp ballot + popcount per
+// delay), and one thread picks the best (p, r, d) with ties to the smallest
+// tuple. Counting then runs one thread per output symbol: the decided levels
+// become Gray bits, 32 symbols of a warp assemble m output words with
+// warp-wide ORs, errors are the popcount of the XOR with the reference bits,
+// integer counters accumulate with 64-bit atomics, EVM sums in FP64.
+#include "rx_kernels.h"
+
+namespace {
+
+// rotate by j^r (exact)
+__device__ __forceinline__ float2 quarter(float2 v, int r) {
+    switch (r & 3) {
+        case 1: return make_float2(-v.y, v.x);
+        case 2: return make_float2(-v.x, -v.y);
+        case 3: return make_float2(v.y, -v.x);
+        default: return v;
+    }
+}
+
+__device__ __forceinline__ int gray_to_level(uint32_t g) {
+    return (int)(g ^ (g >> 1) ^ (g >> 2) ^ (g >> 3));
+}
+
+// m stream bits of symbol t (bit 0 = first transmitted bit)
+__device__ __forceinline__ uint32_t ref_symbol_bits(const uint32_t* ref, int64_t t, int m) {
+    const int64_t b0 = t * m;
+    const int64_t w = b0 >> 5;
+    const int off = (int)(b0 & 31);
+    uint64_t v = ref[w];
+    if (off + m > 32) v |= (uint64_t)ref[w + 1] << 32;
+    return (uint32_t)(v >> off) & ((1u << m) - 1u);
+}
+
+// stream bits -> (l_I, l_Q)
+__device__ __forceinline__ void bits_to_levels(uint32_t sbits, int m, int& li, int& lq) {
+    const uint32_t msb = __brev(sbits) >> (32 - m);
+    const int h = m / 2;
+    li = gray_to_level(msb >> h);
+    lq = gray_to_level(msb & ((1u << h) - 1u));
+}
+
+__global__ void k_sync(const float2* __restrict__ z, int64_t zstride, const uint32_t* __restrict__ ref,
+                       int64_t refstride, int64_t n_ref, int m, int64_t lo, int64_t hi, int D, int64_t lat,
+                       int* counts) {
+    const int q = blockIdx.x >> 3, p = (blockIdx.x >> 2) & 1, r = blockIdx.x & 3;
+    extern __shared__ int16_t txl[];                  // tx levels for t in [lo - lat - D, hi - lat + D)
+    __shared__ int cnt[2 * RX_MAX_DELAY + 1];
+    const int64_t t0 = lo - lat - D;
+    const int64_t nt = (hi - lo) + 2 * D;
+    const uint32_t* rp = ref + (int64_t)p * refstride;
+    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) {
+        const int64_t t = t0 + i;
+        int16_t v = -1;
+        if (t >= 0 && t < n_ref) {
+            int li, lq;
+            bits_to_levels(ref_symbol_bits(rp, t, m), m, li, lq);
+            v = (int16_t)(li | (lq << 8));
+        }
+        txl[i] = v;
+    }
+    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const Qam qm = make_qam(m);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+        const int64_t n = base + lane;
+        int16_t mine = -2;
+        if (n < hi) {
+            const float2 v = quarter(z[(int64_t)q * zstride + n], r);
+            mine = (int16_t)(qam_level(v.x, qm) | (qam_level(v.y, qm) << 8));
+        }
+        for (int d = -D; d <= D; ++d) {
+            const bool hit = (n < hi) && (txl[n - lo + D + d] == mine);
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0 && bal) atomicAdd(&cnt[d + D], __popc(bal));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) counts[blockIdx.x * (2 * D + 1) + i] = cnt[i];
+}
+
+__global__ void k_sync_pick(const int* counts, int D, int64_t len, RxDevState* st) {
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 2; ++q) {
+        int bp = 0, br = 0, bd = -D, bm = -1;
+        for (int p = 0; p < 2; ++p)
+            for (int r = 0; r < 4; ++r)
+                for (int d = -D; d <= D; ++d) {
+                    const int v = counts[((q * 2 + p) * 4 + r) * (2 * D + 1) + d + D];
+                    if (v > bm) { bm = v; bp = p; br = r; bd = d; }
+                }
+        st->sync_p[q] = bp;
+        st->sync_r[q] = br;
+        st->sync_d[q] = bd;
+        st->sync_match[q] = bm;
+        if ((double)bm < 0.9 * (double)len) atomicOr(&st->err_word, 2u);
+    }
+    st->sync_len = (int)len;
+    st->sync_valid = 1;
+}
+
+__global__ void k_count(const float2* __restrict__ z, int64_t zstride, int64_t N, const uint32_t* __restrict__ ref,
+                        int64_t refstride, int64_t n_ref, int m, int64_t lo, int64_t hi, int64_t lat,
+                        uint32_t* __restrict__ out, int64_t outstride, RxDevState* st) {
+    const int q = blockIdx.y;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool have_sync = ref != nullptr && st->sync_valid;
+    const int r = have_sync ? st->sync_r[q] : 0;
+    const Qam qm = make_qam(m);
+    uint32_t sbits = 0;
+    int li = 0, lq = 0;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (n < N) {
+        v = quarter(z[(int64_t)q * zstride + n], r);
+        li = qam_level(v.x, qm);
+        lq = qam_level(v.y, qm);
+        sbits = msb_first_to_stream(qam_bits(li, lq, qm), m);
+    }
+    if (out) {
+        // warp symbols n0..n0+31 fill words [n0*m/32, n0*m/32 + m)
+        const int64_t n0 = n - lane;
+        const int64_t nwords = (N * m + 31) / 32;
+        for (int w = 0; w < m; ++w) {
+            const int sh = lane * m - 32 * w;          // position of this symbol's bit 0 in word w
+            uint32_t contrib = 0;
+            if (n < N) {
+                if (sh >= 0 && sh < 32) contrib = sbits << sh;
+                else if (sh < 0 && sh > -m) contrib = sbits >> (-sh);
+            }
+            const uint32_t word = __reduce_or_sync(0xffffffffu, contrib);
+            const int64_t wi = n0 * m / 32 + w;
+            if (lane == w && wi < nwords) out[(int64_t)q * outstride + wi] = word;
+        }
+    }
+    if (!have_sync) return;
+    const int p = st->sync_p[q], d = st->sync_d[q];
+    const bool counted = (n >= lo && n < hi);
+    uint32_t errs = 0, serr = 0, cnt = 0;
+    float en = 0.0f, ed = 0.0f;
+    if (counted) {
+        const int64_t t = n + d - lat;
+        if (t >= 0 && t < n_ref) {
+            const uint32_t rb = ref_symbol_bits(ref + (int64_t)p * refstride, t, m);
+            errs = __popc(rb ^ sbits);
+            serr = errs ? 1u : 0u;
+            cnt = 1;
+            int ti, tq;
+            bits_to_levels(rb, m, ti, tq);
+            const float2 s = make_float2(qam_value(ti, qm), qam_value(tq, qm));
+            const float2 e = csub(v, s);
+            en = cabs2(e);
+            ed = cabs2(s);
+        }
+    }
+    errs = __reduce_add_sync(0xffffffffu, errs);
+    serr = __reduce_add_sync(0xffffffffu, serr);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    en = warp_sum(en);
+    ed = warp_sum(ed);
+    if (lane == 0 && cnt) {
+        atomicAdd(&st->bit_errors, (unsigned long long)errs);
+        atomicAdd(&st->symbol_errors, (unsigned long long)serr);
+        atomicAdd(&st->symbols, (unsigned long long)cnt);
+        atomicAdd(&st->bits, (unsigned long long)cnt * (unsigned long long)m);
+        atomicAdd(&st->evm_num, (double)en);
+        atomicAdd(&st->evm_den, (double)ed);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sync(const float2* z, int64_t zstride, const uint32_t* ref, int64_t refstride, int64_t n_ref,
+                        int m, int64_t lo, int64_t hi, int max_delay, int64_t lat, int* counts, RxDevState* st,
+                        cudaStream_t s, int* nlaunch) {
+    const int64_t nt = (hi - lo) + 2 * max_delay;
+    const size_t smem = sizeof(int16_t) * (size_t)nt;
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        cudaFuncSetAttribute(k_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_sync<<<16, 256, smem, s>>>(z, zstride, ref, refstride, n_ref, m, lo, hi, max_delay, lat, counts);
+    k_sync_pick<<<1, 32, 0, s>>>(counts, max_delay, hi - lo, st);
+    if (nlaunch) *nlaunch += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const float2* z, int64_t zstride, int64_t N, const uint32_t* ref, int64_t refstride,
+                         int64_t n_ref, int m, int64_t lo, int64_t hi, int64_t lat, uint32_t* out,
+                         int64_t outstride, RxDevState* st, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((N + 255) / 256), 2);
+    k_count<<<grid, 256, 0, s>>>(z, zstride, N, ref, refstride, n_ref, m, lo, hi, lat, out, outstride, st);
+    return cudaGetLastError();
+}

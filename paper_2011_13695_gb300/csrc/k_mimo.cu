@@ -1,0 +1,445 @@
+// A2 CMA / DD acquisition, A3 frequency-offset estimate, A4 segmented DD-LMS.
+//
+// The paper's adaptive equaliser (Sec. IV-D) is a serial 4-tap TD DD-LMS in
+// one kernel that exchanges data with warp shuffles and decides/demaps as it
+// goes. Here the equaliser is the 2x2 butterfly FIR at 2 samples/symbol with
+// block updates:
+//   y_q[n] = sum_p sum_k h_qp[k] x_p[2n + c - k],   c = (T-1)/2
+//   h_qp[k] += mu * sum_{n in block} e_q[n] conj(x_p[2n + c - k])
+// with e = y (R2 - |y|^2) (CMA, Godard) or e = dec(y e^{-j psi}) e^{j psi} - y
+// (DD, psi = arg(-sum y^4)/4 per block). The serial recursion is broken by a
+// fixed segment schedule: one CTA per segment of seg_blocks blocks, started
+// from common taps and warmed up on the warmup_blocks blocks before it.
+// Per block a CTA stages the block's input window (both polarisations, FO
+// derotation by the 64-bit phase accumulator fused into the load) in shared
+// memory, computes the outputs, the block phase (a fixed-order reduction, so
+// results do not depend on scheduling), the errors and the tap gradients
+// (fixed-order partial sums), then updates the taps it keeps in shared memory.
+#include "rx_fft.cuh"
+#include "rx_kernels.h"
+
+namespace {
+
+struct LmsSmem {
+    float2* taps;    // [4][T]
+    float2* xs;      // [2][XW]
+    float2* ys;      // [2][Lb]
+    float2* es;      // [2][Lb]
+    float2* part;    // [G][4T]
+    float2* rot;     // [2] e^{-j psi}
+    int XW, G;
+};
+
+__device__ void lms_block(const LmsArgs& a, LmsSmem& s, int64_t n0, int L, bool store, int nthreads,
+                          long long inc) {
+    const int tid = threadIdx.x;
+    const int T = a.T, c = (a.T - 1) / 2;
+    const int XW = 2 * L + T - 2 + 1;
+    // 1. stage x[i], i = off + 2 n0 - c + j, j < XW (derotated, zero outside the buffer)
+    const int64_t i0 = a.off + 2 * n0 - c;
+    for (int t = tid; t < 2 * XW; t += nthreads) {
+        const int p = t / XW, jj = t - p * XW;
+        const int64_t i = i0 + jj;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (i >= 0 && i < a.xlen) {
+            v = a.x[(int64_t)p * a.xstride + i];
+            if (inc) v = cmul(v, nco_conj(inc, a.g0 + i));
+        }
+        s.xs[p * s.XW + jj] = v;
+    }
+    __syncthreads();
+    // 2. outputs with the taps the block starts with
+    for (int o = tid; o < 2 * L; o += nthreads) {
+        const int q = o / L, n = o - q * L;
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+        for (int p = 0; p < 2; ++p) {
+            const float2* hq = s.taps + (q * 2 + p) * T;
+            const float2* xp = s.xs + p * s.XW + 2 * n + T - 1;
+            for (int k = 0; k < T; ++k) acc = cmac(acc, hq[k], xp[-k]);
+        }
+        s.ys[q * L + n] = acc;
+        if (a.cma) {
+            const float r = a.R2 - cabs2(acc);
+            s.es[q * L + n] = cscale(acc, r);
+        }
+        if (store) a.y[(int64_t)q * a.ystride + n0 + n] = acc;
+    }
+    __syncthreads();
+    // 3. DD: block phase and errors
+    if (!a.cma) {
+        const int w = tid >> 5, lane = tid & 31;
+        if (w < 2) {
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int n = lane; n < L; n += 32) {
+                const float2 y = s.ys[w * L + n];
+                const float2 y2 = cmul(y, y);
+                acc = cadd(acc, cmul(y2, y2));
+            }
+            acc.x = warp_sum(acc.x);
+            acc.y = warp_sum(acc.y);
+            if (lane == 0) {
+                const float psi = 0.25f * atan2f(-acc.y, -acc.x);
+                float sn, cs;
+                sincosf(psi, &sn, &cs);
+                s.rot[w] = make_float2(cs, -sn);
+            }
+        }
+        __syncthreads();
+        const Qam qm = make_qam(a.m);
+        for (int o = tid; o < 2 * L; o += nthreads) {
+            const int q = o / L;
+            const float2 y = s.ys[o];
+            const float2 r = s.rot[q];
+            const float2 d = qam_decide(cmul(y, r), qm);
+            s.es[o] = csub(cmulc(d, r), y);
+        }
+        __syncthreads();
+    }
+    // 4. gradient: partial sums of G groups in a fixed order
+    const int NTAP = 4 * T;
+    {
+        const int g = tid / NTAP, t = tid - g * NTAP;
+        if (g < s.G) {
+            const int q = t / (2 * T), p = (t / T) & 1, k = t - (t / T) * T;
+            const int per = (L + s.G - 1) / s.G;
+            const int nb = g * per, ne = min(L, nb + per);
+            float2 acc = make_float2(0.0f, 0.0f);
+            const float2* xp = s.xs + p * s.XW + T - 1 - k;
+            const float2* eq = s.es + q * L;
+            for (int n = nb; n < ne; ++n) acc = cmacc(acc, eq[n], xp[2 * n]);
+            s.part[g * NTAP + t] = acc;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < NTAP; t += nthreads) {
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int g = 0; g < s.G; ++g) acc = cadd(acc, s.part[g * NTAP + t]);
+        // taps index [q][p][k] = t (same ordering as the partial sums)
+        s.taps[t] = make_float2(fmaf(a.mu, acc.x, s.taps[t].x), fmaf(a.mu, acc.y, s.taps[t].y));
+    }
+    __syncthreads();
+}
+
+__global__ void k_lms(LmsArgs a) {
+    extern __shared__ float2 smem[];
+    if (a.run_if && *a.run_if == 0) return;
+    const int nthreads = blockDim.x;
+    const int T = a.T, Lb = a.Lb;
+    LmsSmem s;
+    s.XW = 2 * Lb + T;
+    s.G = max(1, nthreads / (4 * T));
+    s.taps = smem;
+    s.xs = s.taps + 4 * T;
+    s.ys = s.xs + 2 * s.XW;
+    s.es = s.ys + 2 * Lb;
+    s.part = s.es + 2 * Lb;
+    s.rot = s.part + s.G * 4 * T;
+
+    const int64_t seg = blockIdx.x;
+    const int64_t nseg = gridDim.x;
+    const long long inc = a.derotate ? a.st->nco_inc : 0;
+    for (int t = threadIdx.x; t < 4 * T; t += nthreads) s.taps[t] = a.taps_in[t];
+    __syncthreads();
+    const int64_t start = seg * a.L_seg;
+    const int64_t end = min(a.n_sym, start + a.L_seg);
+    if (seg > 0) {
+        for (int w = a.n_wu; w > 0; --w) lms_block(a, s, start - (int64_t)w * Lb, Lb, false, nthreads, inc);
+    }
+    for (int64_t n0 = start; n0 < end; n0 += Lb) {
+        const int L = (int)min((int64_t)Lb, end - n0);
+        lms_block(a, s, n0, L, a.y != nullptr, nthreads, inc);
+    }
+    if (seg == nseg - 1 && a.taps_out) {
+        for (int t = threadIdx.x; t < 4 * T; t += nthreads) a.taps_out[t] = s.taps[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A3 on the fixed CMA taps
+// ---------------------------------------------------------------------------
+
+__global__ void k_foe_window(const float2* __restrict__ x, int64_t xstride, int64_t xlen, int64_t off, int T,
+                             int64_t n0, int64_t nw, const float2* __restrict__ taps, float2* yw) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= 2 * nw) return;
+    const int q = (int)(o / nw);
+    const int64_t n = n0 + (o - q * nw);
+    const int c = (T - 1) / 2;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int p = 0; p < 2; ++p) {
+        for (int k = 0; k < T; ++k) {
+            const int64_t i = off + 2 * n + c - k;
+            if (i >= 0 && i < xlen) acc = cmac(acc, taps[(q * 2 + p) * T + k], x[(int64_t)p * xstride + i]);
+        }
+    }
+    yw[o] = acc;
+}
+
+// |FFT_Nf(y_q^4)|^2 per polarisation, zero padded beyond nw
+template <int K>
+__global__ void __launch_bounds__((1 << K) / 16) k_foe_pgram(const float2* yw, int64_t nw, const float2* tw,
+                                                            float* P) {
+    constexpr int N = 1 << K;
+    extern __shared__ float2 sm[];
+    const int q = blockIdx.x;
+    const float2* y = yw + (int64_t)q * nw;
+    auto load = [&](int i) -> float2 {
+        if (i >= nw) return make_float2(0.0f, 0.0f);
+        const float2 v = y[i];
+        const float2 v2 = cmul(v, v);
+        return cmul(v2, v2);
+    };
+    float* Pq = P + (int64_t)q * N;
+    auto store = [&](int i, float2 v) { Pq[i] = cabs2(v); };
+    fft_run<K, -1, true, true>(sm, tw, load, store);
+}
+
+// coarse peak, fine slope, code, phase increment and corrected taps
+__global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __restrict__ yw, int64_t nw, int Lb,
+                           double rs, double fs, double grid, int T, RxDevState* st) {
+    const int nf = 1 << kf;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    __shared__ float bv[32];
+    __shared__ int bi[32];
+    __shared__ int s_kappa;
+    __shared__ double2 s_a[1024];
+    // first maximum of P0 + P1
+    float best = -1.0f;
+    int besti = 0;
+    for (int k = tid; k < nf; k += nthr) {
+        const float v = P[k] + P[nf + k];
+        if (v > best) { best = v; besti = k; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+        if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
+    }
+    if ((tid & 31) == 0) { bv[tid >> 5] = best; bi[tid >> 5] = besti; }
+    __syncthreads();
+    if (tid == 0) {
+        float b = -1.0f;
+        int idx = 0;
+        for (int w = 0; w < (nthr >> 5); ++w) {
+            if (bv[w] > b || (bv[w] == b && bi[w] < idx)) { b = bv[w]; idx = bi[w]; }
+        }
+        s_kappa = idx < nf / 2 ? idx : idx - nf;
+    }
+    __syncthreads();
+    const int kappa = s_kappa;
+    // a_j = sum_q sum_{n in block j} (y_q[n] e^{-j w_c n})^4, w_c = 2 pi kappa / (4 nf); one warp per block
+    const int nb = (int)(nw / Lb);
+    const int w = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
+    const long long period = 4LL * nf;
+    for (int j = w; j < nb; j += nwarp) {
+        double ax = 0.0, ay = 0.0;
+        for (int q = 0; q < 2; ++q) {
+            for (int n = j * Lb + lane; n < (j + 1) * Lb; n += 32) {
+                long long r = ((long long)kappa * n) % period;
+                if (r < 0) r += period;
+                float sn, cs;
+                sincospif(-2.0f * (float)r / (float)period, &sn, &cs);
+                const float2 v = cmul(yw[(int64_t)q * nw + n], make_float2(cs, sn));
+                const float2 v2 = cmul(v, v);
+                const float2 v4 = cmul(v2, v2);
+                ax += v4.x;
+                ay += v4.y;
+            }
+        }
+        ax = warp_sum_d(ax);
+        ay = warp_sum_d(ay);
+        if (lane == 0) s_a[j] = make_double2(ax, ay);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double PI = 3.14159265358979323846;
+        const double wc = 2.0 * PI * (double)kappa / (4.0 * nf);
+        double wf = 0.0;
+        if (nb >= 2) {
+            double prev = atan2(s_a[0].y, s_a[0].x), shift = 0.0;
+            double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+            for (int j = 0; j < nb; ++j) {
+                double ph = atan2(s_a[j].y, s_a[j].x);
+                if (j > 0) {
+                    const double d = (ph + shift) - prev;
+                    if (d > PI) shift -= 2.0 * PI;
+                    else if (d < -PI) shift += 2.0 * PI;
+                }
+                ph += shift;
+                prev = ph;
+                const double cx = (double)j * Lb + 0.5 * (Lb - 1);
+                sx += cx; sy += ph; sxx += cx * cx; sxy += cx * ph;
+            }
+            const double mx = sx / nb, my = sy / nb;
+            const double slope = (sxy - nb * mx * my) / (sxx - nb * mx * mx);
+            wf = slope / 4.0;
+        }
+        const double wh = wc + wf;
+        const double u = wh * rs / (2.0 * PI) / grid;
+        const double code = rint(u);
+        st->fo_code = (int)code;
+        st->fo_w = wh;
+        st->coarse_bin = kappa;
+        st->fo_margin = fabs(fabs(u - floor(u)) - 0.5);
+        st->fo_valid = 1;
+        const double F = code * grid / fs;                // turns per sample, |F| < 0.5
+        st->nco_inc = llrint(ldexp(F, 64));
+    }
+    __syncthreads();
+    // taps_init = taps_cma * exp(-j 2 pi code grid (k - c) / fs)
+    const int c = (T - 1) / 2;
+    const double code = (double)st->fo_code;
+    for (int t = tid; t < 4 * T; t += nthr) {
+        const int k = t % T;
+        double s, cs;
+        sincospi(-2.0 * code * grid * (double)(k - c) / fs, &s, &cs);
+        const float2 h = st->taps_cma[t];
+        st->taps_init[t] = cmul(h, make_float2((float)cs, (float)s));
+    }
+}
+
+// max over |d| <= c of |rho_d| between the two CMA outputs (second half of y_acq)
+__global__ void k_cma_check(const float2* __restrict__ yacq, int64_t nacq, int T, RxDevState* st, int* flag,
+                            int pass) {
+    if (pass == 1 && *flag == 0) return;
+    const int64_t h0 = nacq / 2;
+    const int64_t L = nacq - h0;
+    const float2* y0 = yacq + h0;
+    const float2* y1 = yacq + nacq + h0;
+    const int maxlag = (T - 1) / 2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    __shared__ double red[32][2];
+    __shared__ double s_den;
+    // energies
+    double e0 = 0.0, e1 = 0.0;
+    for (int64_t n = tid; n < L; n += nthr) {
+        e0 += cabs2(y0[n]);
+        e1 += cabs2(y1[n]);
+    }
+    e0 = warp_sum_d(e0);
+    e1 = warp_sum_d(e1);
+    if ((tid & 31) == 0) { red[tid >> 5][0] = e0; red[tid >> 5][1] = e1; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (nthr >> 5); ++w) { a += red[w][0]; b += red[w][1]; }
+        s_den = sqrt(a * b);
+    }
+    __syncthreads();
+    double best = 0.0;
+    for (int d = -maxlag; d <= maxlag; ++d) {
+        const int64_t a0 = d < 0 ? -d : 0, a1 = L - (d > 0 ? d : 0);
+        double sx = 0.0, sy = 0.0;
+        for (int64_t n = a0 + tid; n < a1; n += nthr) {
+            const float2 v = cmulc(y0[n], y1[n + d]);
+            sx += v.x;
+            sy += v.y;
+        }
+        sx = warp_sum_d(sx);
+        sy = warp_sum_d(sy);
+        __syncthreads();
+        if ((tid & 31) == 0) { red[tid >> 5][0] = sx; red[tid >> 5][1] = sy; }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < (nthr >> 5); ++w) { a += red[w][0]; b += red[w][1]; }
+            const double r = s_den > 0.0 ? sqrt(a * a + b * b) / s_den : 0.0;
+            if (r > best) best = r;
+        }
+    }
+    if (tid == 0) {
+        if (pass == 0) {
+            *flag = best > 0.5 ? 1 : 0;
+            st->cma_rho = (float)best;
+            st->cma_reran = 0;
+        } else if (best > 0.5) {
+            atomicOr(&st->err_word, 4u);
+        }
+    }
+}
+
+// second row from the first: h_yy[k] = conj h_xx[T-1-k], h_yx[k] = -conj h_xy[T-1-k]
+__global__ void k_cma_rebuild(RxDevState* st, int T, const int* flag) {
+    if (*flag == 0) return;
+    const int k = threadIdx.x;
+    if (k < T) {
+        const float2 hxx = st->taps_cma[0 * T + (T - 1 - k)];
+        const float2 hxy = st->taps_cma[1 * T + (T - 1 - k)];
+        st->taps_init[0 * T + k] = st->taps_cma[0 * T + k];
+        st->taps_init[1 * T + k] = st->taps_cma[1 * T + k];
+        st->taps_init[3 * T + k] = make_float2(hxx.x, -hxx.y);
+        st->taps_init[2 * T + k] = make_float2(-hxy.x, hxy.y);
+    }
+    if (k == 0) st->cma_reran = 1;
+}
+
+}  // namespace
+
+int64_t lms_smem_bytes(int T, int Lb, int threads) {
+    const int XW = 2 * Lb + T;
+    const int G = threads / (4 * T) > 1 ? threads / (4 * T) : 1;
+    return (int64_t)sizeof(float2) * (4 * T + 2 * XW + 4 * Lb + G * 4 * T + 2);
+}
+
+cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
+    const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
+    if (nseg <= 0) return cudaSuccess;
+    const size_t smem = (size_t)lms_smem_bytes(a.T, a.Lb, threads);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        cudaFuncSetAttribute(k_lms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_lms<<<(unsigned)nseg, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
+                              int64_t nw, const float2* taps, float2* yw, cudaStream_t s) {
+    const int64_t tot = 2 * nw;
+    k_foe_window<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, xstride, xlen, off, T, n0, nw, taps, yw);
+    return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t pgram_t(const float2* yw, int64_t nw, const float2* tw, float* P, cudaStream_t s) {
+    constexpr int N = 1 << K;
+    const size_t smem = sizeof(float2) * fft_smem_elems(N);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_foe_pgram<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_foe_pgram<K><<<2, N / 16, smem, s>>>(yw, nw, tw, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_foe_pgram(const float2* yw, int64_t nw, int kf, const float2* tw, float* P, cudaStream_t s) {
+    switch (kf) {
+        case 9: return pgram_t<9>(yw, nw, tw, P, s);
+        case 10: return pgram_t<10>(yw, nw, tw, P, s);
+        case 11: return pgram_t<11>(yw, nw, tw, P, s);
+        case 12: return pgram_t<12>(yw, nw, tw, P, s);
+        case 13: return pgram_t<13>(yw, nw, tw, P, s);
+        case 14: return pgram_t<14>(yw, nw, tw, P, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw, int Lb, double rs, double fs,
+                            double grid, int T, RxDevState* st, cudaStream_t s) {
+    k_foe_fine<<<1, 1024, 0, s>>>(P, kf, yw, nw, Lb, rs, fs, grid, T, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cma_check(const float2* yacq, int64_t nacq, int T, RxDevState* st, int* flag, int pass,
+                             cudaStream_t s) {
+    k_cma_check<<<1, 1024, 0, s>>>(yacq, nacq, T, st, flag, pass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cma_rebuild(RxDevState* st, int T, const int* flag, cudaStream_t s) {
+    k_cma_rebuild<<<1, 64, 0, s>>>(st, T, flag);
+    return cudaGetLastError();
+}

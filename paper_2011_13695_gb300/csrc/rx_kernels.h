@@ -1,0 +1,77 @@
+// Host-side launchers of the librx kernels (one translation unit per stage group).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rx_dev.cuh"
+
+struct CdcArgs {
+    const void* in;        // [2][S] input samples
+    int fmt;               // rx_input
+    float in_scale;
+    int64_t S;             // samples per polarisation in this frame
+    int nfft;
+    const float2* H;       // [nfft] FD filter, 1/nfft folded in
+    const float2* tw;      // twiddle table
+    const float2* tail;    // [2][nfft/2] carried scaled input (stream) or null (single frame)
+    float2* out;           // buffer base; polarisation p writes out + p*ostride + obase
+    int64_t ostride, obase;
+    RxDevState* st;
+};
+
+struct LmsArgs {
+    const float2* x;       // equaliser buffer base (polarisation stride xstride)
+    int64_t xstride, xlen; // valid buffer indices [0, xlen)
+    int64_t off;           // buffer index of symbol 0: off + 2n + c - k
+    int T, Lb;
+    int64_t n_sym;         // symbols the segments cover
+    int64_t L_seg;         // symbols per segment
+    int n_wu;              // warm-up blocks ahead of segments s >= 1
+    int cma;               // 1 = CMA error, 0 = DD error
+    float mu, R2;
+    int m;
+    int derotate;          // 1: multiply the input by the state's phase accumulator conjugate
+    long long g0;          // input-sample index of buffer index 0
+    const float2* taps_in; // [2][2][T]
+    float2* taps_out;      // final taps of the last segment (may alias taps_in)
+    float2* y;             // outputs [2][ystride] (nullable)
+    int64_t ystride;
+    const int* run_if;     // nullable: the kernel does nothing unless *run_if != 0
+    RxDevState* st;
+};
+
+cudaError_t launch_power(const void* in, int fmt, float in_scale, int64_t S, int64_t n_win, RxDevState* st,
+                         cudaStream_t s);
+cudaError_t launch_cdc(const CdcArgs& a, cudaStream_t s);
+cudaError_t launch_tail(const void* in, int fmt, float in_scale, int64_t S, int hop, float2* tail,
+                        const RxDevState* st, cudaStream_t s);
+cudaError_t launch_copy_hist(float2* buf, int64_t stride, int64_t S, int hist, cudaStream_t s);
+cudaError_t launch_fill_twiddles(float2* tw, cudaStream_t s);
+cudaError_t launch_fill_filter(float2* H, int nfft, double fs, double dl_lambda2_over_c, double rs, double rolloff,
+                               cudaStream_t s);
+
+cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s);
+int64_t lms_smem_bytes(int T, int Lb, int threads);
+
+cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
+                              int64_t nw, const float2* taps, float2* yw, cudaStream_t s);
+cudaError_t launch_foe_pgram(const float2* yw, int64_t nw, int kf, const float2* tw, float* P, cudaStream_t s);
+cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw, int Lb, double rs, double fs,
+                            double grid, int T, RxDevState* st, cudaStream_t s);
+cudaError_t launch_cma_check(const float2* yacq, int64_t nacq, int T, RxDevState* st, int* flag_dev, int pass,
+                             cudaStream_t s);
+cudaError_t launch_cma_rebuild(RxDevState* st, int T, const int* flag_dev, cudaStream_t s);
+
+cudaError_t launch_bps(const float2* y, int64_t ystride, int64_t N, int B, int W, int m, uint8_t* bstar,
+                       int64_t bstride, cudaStream_t s);
+cudaError_t launch_unwrap(const float2* y, int64_t ystride, const uint8_t* bstar, int64_t bstride, int64_t N,
+                          int B, int* tile_sums, int* m_out, int64_t mstride, float2* z, int64_t zstride,
+                          RxDevState* st, cudaStream_t s, int* nlaunch);
+
+cudaError_t launch_sync(const float2* z, int64_t zstride, const uint32_t* ref, int64_t refstride, int64_t n_ref,
+                        int m, int64_t lo, int64_t hi, int max_delay, int64_t lat, int* counts, RxDevState* st,
+                        cudaStream_t s, int* nlaunch);
+cudaError_t launch_count(const float2* z, int64_t zstride, int64_t N, const uint32_t* ref, int64_t refstride,
+                         int64_t n_ref, int m, int64_t lo, int64_t hi, int64_t lat, uint32_t* out,
+                         int64_t outstride, RxDevState* st, cudaStream_t s);

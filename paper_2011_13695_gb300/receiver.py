@@ -1,0 +1,77 @@
+"""Handle wrapper over the librx C ABI for torch device buffers (marshalling only)."""
+
+from __future__ import annotations
+
+import torch
+
+from . import rx
+
+# workload keys -> rx_config fields
+_RENAME = {"symbol_rate": "symbol_rate_hz", "wavelength": "wavelength_m", "dispersion": "dispersion_s_per_m2",
+           "length": "length_m"}
+
+_BUF_LAYOUT = {
+    rx.RX_BUF_Y: torch.complex64, rx.RX_BUF_Z: torch.complex64, rx.RX_BUF_CDC: torch.complex64,
+    rx.RX_BUF_TAPS_CMA: torch.complex64, rx.RX_BUF_TAPS_INIT: torch.complex64, rx.RX_BUF_TAPS_LAST: torch.complex64,
+    rx.RX_BUF_Y_ACQ: torch.complex64, rx.RX_BUF_Y_FOE: torch.complex64, rx.RX_BUF_BSTAR: torch.uint8,
+    rx.RX_BUF_M: torch.int32, rx.RX_BUF_SCALE: torch.float32,
+}
+
+
+def config_from(rx_settings: dict, max_symbols: int, input_format: int = rx.RX_IN_C64, input_scale: float = 1.0,
+                streaming: bool = False) -> rx.rx_config:
+    kw = {_RENAME.get(k, k): v for k, v in rx_settings.items()}
+    kw.update(input_format=input_format, input_scale=input_scale, streaming=1 if streaming else 0,
+              max_symbols=max_symbols)
+    kw.setdefault("sps", 2)
+    return rx.make_config(**kw)
+
+
+class Receiver:
+    """One librx handle on the current CUDA device."""
+
+    def __init__(self, rx_settings: dict, max_symbols: int, input_format: int = rx.RX_IN_C64,
+                 input_scale: float = 1.0, streaming: bool = False):
+        self.cfg = config_from(rx_settings, max_symbols, input_format, input_scale, streaming)
+        self.m = self.cfg.bits_per_sym
+        self.h = rx.rx_create(self.cfg)
+
+    def close(self):
+        if self.h:
+            rx.rx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def words(self, n_sym: int) -> int:
+        return (n_sym * self.m + 31) // 32
+
+    def process(self, x: torch.Tensor, n_sym: int, ref: torch.Tensor | None = None,
+                out: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None) -> None:
+        s = stream or torch.cuda.current_stream()
+        rx.rx_process(self.h, x.data_ptr(), n_sym, ref.data_ptr() if ref is not None else None,
+                      out.data_ptr() if out is not None else None, s.cuda_stream)
+
+    def process_host(self, x_host, n_sym: int, ref_host=None, out_host=None, stream=None) -> None:
+        s = stream or torch.cuda.current_stream()
+        rx.rx_process_host(self.h, x_host.data_ptr(), n_sym, ref_host.data_ptr() if ref_host is not None else None,
+                           out_host.data_ptr() if out_host is not None else None, s.cuda_stream)
+
+    def stats(self) -> dict:
+        return rx.rx_stats(self.h)
+
+    def reset(self) -> None:
+        rx.rx_reset(self.h)
+
+    def buffer(self, which: int) -> torch.Tensor:
+        nbytes = rx.rx_buffer_bytes(self.h, which)
+        dt = _BUF_LAYOUT[which]
+        esz = torch.tensor([], dtype=dt).element_size()
+        t = torch.empty(nbytes // esz, dtype=dt, device="cuda")
+        rx.rx_get_buffer(self.h, which, t.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.current_stream().synchronize()
+        return t

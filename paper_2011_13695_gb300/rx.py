@@ -1,0 +1,205 @@
+"""ctypes binding of librx (include/rx.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the receiver: all of it runs in the CUDA library. Device
+buffers are passed as integer device addresses (e.g. ``tensor.data_ptr()``)
+and streams as ``torch.cuda.Stream.cuda_stream``. The library is loaded from
+the package directory; if it is missing, :func:`lib` raises instead of
+falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librx.so")
+
+RX_OK, RX_EINVAL, RX_ENOMEM, RX_ECUDA, RX_ETIMEOUT, RX_ESTATE = 0, -1, -2, -3, -4, -5
+RX_IN_C64, RX_IN_F16, RX_IN_I8 = 0, 1, 2
+RX_ERR_NONFINITE, RX_ERR_SYNC_LOST, RX_ERR_SINGULAR = 0x1, 0x2, 0x4
+(RX_BUF_CDC, RX_BUF_Y, RX_BUF_Z, RX_BUF_BSTAR, RX_BUF_M, RX_BUF_TAPS_CMA, RX_BUF_TAPS_INIT, RX_BUF_TAPS_LAST,
+ RX_BUF_Y_ACQ, RX_BUF_Y_FOE, RX_BUF_SCALE) = range(11)
+
+EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_bytes", "rx_get_buffer",
+           "rx_reset", "rx_state_size", "rx_state_get", "rx_state_set", "rx_set_timing", "rx_stage_count",
+           "rx_stage_name", "rx_stage_times", "rx_launch_count", "rx_destroy", "rx_strerror")
+
+
+class rx_config(C.Structure):
+    _fields_ = [
+        ("bits_per_sym", C.c_int32), ("sps", C.c_int32),
+        ("symbol_rate_hz", C.c_double), ("wavelength_m", C.c_double),
+        ("dispersion_s_per_m2", C.c_double), ("length_m", C.c_double), ("rrc_rolloff", C.c_double),
+        ("fft_size", C.c_int32), ("n_taps", C.c_int32), ("lms_block", C.c_int32), ("cma_blocks", C.c_int32),
+        ("dd_acq_blocks", C.c_int32), ("seg_blocks", C.c_int32), ("warmup_blocks", C.c_int32),
+        ("bps_phases", C.c_int32), ("bps_window", C.c_int32), ("edge_skip", C.c_int32), ("sync_len", C.c_int32),
+        ("max_delay", C.c_int32), ("mu_cma", C.c_float), ("mu_dd", C.c_float), ("fo_grid_hz", C.c_double),
+        ("input_format", C.c_int32), ("input_scale", C.c_float), ("streaming", C.c_int32),
+        ("max_symbols", C.c_int64),
+    ]
+
+
+class rx_stats_t(C.Structure):
+    _fields_ = [
+        ("frames", C.c_uint64), ("symbols_processed", C.c_uint64), ("bits_processed", C.c_uint64),
+        ("bits_counted", C.c_uint64), ("bit_errors", C.c_uint64), ("symbols_counted", C.c_uint64),
+        ("symbol_errors", C.c_uint64), ("evm_num", C.c_double), ("evm_den", C.c_double), ("ber", C.c_double),
+        ("evm", C.c_double), ("q_db", C.c_double), ("fo_code", C.c_int32), ("fo_hz", C.c_double),
+        ("pol_map", C.c_int32 * 2), ("rotation", C.c_int32 * 2), ("delay", C.c_int32 * 2),
+        ("sync_matches", C.c_int32 * 2), ("sync_len", C.c_int32), ("cma_reran", C.c_int32),
+        ("cma_rho", C.c_float), ("latency_symbols", C.c_int32), ("error_word", C.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load librx.so (built by ``paper_2011_13695_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librx.so is not built ({LIB_PATH}); run paper_2011_13695_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        sig = {
+            "rx_create": (i32, [C.POINTER(rx_config), C.POINTER(vp)]),
+            "rx_process": (i32, [vp, vp, i64, vp, vp, vp]),
+            "rx_process_host": (i32, [vp, vp, i64, vp, vp, vp]),
+            "rx_stats": (i32, [vp, C.POINTER(rx_stats_t)]),
+            "rx_buffer_bytes": (i32, [vp, i32, C.POINTER(i64)]),
+            "rx_get_buffer": (i32, [vp, i32, vp, i64, vp]),
+            "rx_reset": (i32, [vp]),
+            "rx_state_size": (i32, [vp, C.POINTER(C.c_size_t)]),
+            "rx_state_get": (i32, [vp, vp, C.c_size_t]),
+            "rx_state_set": (i32, [vp, vp, C.c_size_t]),
+            "rx_set_timing": (i32, [vp, i32]),
+            "rx_stage_count": (i32, []),
+            "rx_stage_name": (C.c_char_p, [i32]),
+            "rx_stage_times": (i32, [vp, C.POINTER(C.c_double), C.POINTER(i64), i32]),
+            "rx_launch_count": (u64, [vp]),
+            "rx_destroy": (None, [vp]),
+            "rx_strerror": (C.c_char_p, [i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {lib().rx_strerror(status).decode()} ({status})")
+        self.status = status
+
+
+def _check(status: int, where: str) -> None:
+    if status != RX_OK:
+        raise RxError(status, where)
+
+
+def make_config(**kw) -> rx_config:
+    """rx_config from keyword fields (missing fields are 0)."""
+    cfg = rx_config()
+    names = {n for n, _ in rx_config._fields_}
+    for k, v in kw.items():
+        if k in names:
+            setattr(cfg, k, v)
+    return cfg
+
+
+# --- entry points, same names as the C ABI ---------------------------------
+
+def rx_create(cfg: rx_config) -> int:
+    h = C.c_void_p()
+    _check(lib().rx_create(C.byref(cfg), C.byref(h)), "rx_create")
+    return h.value
+
+
+def rx_process(h: int, d_in: int, n_sym: int, d_ref: int | None, d_out: int | None, stream: int | None) -> None:
+    _check(lib().rx_process(h, d_in, n_sym, d_ref or None, d_out or None, stream or None), "rx_process")
+
+
+def rx_process_host(h: int, h_in: int, n_sym: int, h_ref: int | None, h_out: int | None, stream: int | None) -> None:
+    _check(lib().rx_process_host(h, h_in, n_sym, h_ref or None, h_out or None, stream or None), "rx_process_host")
+
+
+def rx_stats(h: int) -> dict:
+    st = rx_stats_t()
+    _check(lib().rx_stats(h, C.byref(st)), "rx_stats")
+    return st.as_dict()
+
+
+def rx_buffer_bytes(h: int, which: int) -> int:
+    n = C.c_int64()
+    _check(lib().rx_buffer_bytes(h, which, C.byref(n)), "rx_buffer_bytes")
+    return n.value
+
+
+def rx_get_buffer(h: int, which: int, d_dst: int, nbytes: int, stream: int | None) -> None:
+    _check(lib().rx_get_buffer(h, which, d_dst, nbytes, stream or None), "rx_get_buffer")
+
+
+def rx_reset(h: int) -> None:
+    _check(lib().rx_reset(h), "rx_reset")
+
+
+def rx_state_size(h: int) -> int:
+    n = C.c_size_t()
+    _check(lib().rx_state_size(h, C.byref(n)), "rx_state_size")
+    return n.value
+
+
+def rx_state_get(h: int) -> bytes:
+    n = rx_state_size(h)
+    buf = C.create_string_buffer(n)
+    _check(lib().rx_state_get(h, buf, n), "rx_state_get")
+    return buf.raw
+
+
+def rx_state_set(h: int, blob: bytes) -> None:
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().rx_state_set(h, buf, len(blob)), "rx_state_set")
+
+
+def rx_set_timing(h: int, enable: bool) -> None:
+    _check(lib().rx_set_timing(h, 1 if enable else 0), "rx_set_timing")
+
+
+def rx_stage_count() -> int:
+    return lib().rx_stage_count()
+
+
+def rx_stage_name(i: int) -> str:
+    return lib().rx_stage_name(i).decode()
+
+
+def rx_stage_times(h: int) -> dict:
+    n = rx_stage_count()
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _check(lib().rx_stage_times(h, ms, cnt, n), "rx_stage_times")
+    return {rx_stage_name(i): (ms[i], cnt[i]) for i in range(n)}
+
+
+def rx_launch_count(h: int) -> int:
+    return int(lib().rx_launch_count(h))
+
+
+def rx_destroy(h: int) -> None:
+    lib().rx_destroy(h)
+
+
+def rx_strerror(status: int) -> str:
+    return lib().rx_strerror(status).decode()

@@ -1,0 +1,78 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and the
+FP64 oracle on the same seeded frame, and compare them."""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def rel_rms(a, b) -> float:
+    a = np.asarray(a)
+    b = np.asarray(b)
+    den = np.sum(np.abs(b) ** 2)
+    return float(np.sqrt(np.sum(np.abs(a - b) ** 2) / den)) if den > 0 else float(np.sqrt(np.sum(np.abs(a) ** 2)))
+
+
+def device_input(samples: np.ndarray, fmt: int = 0):
+    """Host samples -> (torch device tensor, the values the oracle should see, input_scale)."""
+    import torch
+    from synth.channel import quantise_int8, to_fp16
+    if fmt == 0:
+        c = np.ascontiguousarray(samples.astype(np.complex64))
+        return torch.from_numpy(c.view(np.float32)).cuda(), c.astype(np.complex128), 1.0
+    if fmt == 1:
+        h = to_fp16(samples)
+        vals = h[..., 0].astype(np.float64) + 1j * h[..., 1].astype(np.float64)
+        return torch.from_numpy(np.ascontiguousarray(h).view(np.int16)).cuda(), vals, 1.0
+    codes, delta = quantise_int8(samples)
+    # one step for both polarisations: the power normalisation removes any common scale
+    step = float(delta[0])
+    vals = (codes[..., 0].astype(np.float64) + 1j * codes[..., 1].astype(np.float64)) * np.float64(np.float32(step))
+    return torch.from_numpy(np.ascontiguousarray(codes)).cuda(), vals, step
+
+
+def run_gpu_frames(rx_settings: dict, frames: list, refs: list | None = None, fmt: int = 0, streaming=False,
+                   buffers=("y", "z", "bstar", "m", "cdc", "taps_cma", "taps_init", "taps_last", "y_foe", "scale")):
+    """Process frames (host complex128 [2, S] each) through librx; returns per-frame dicts."""
+    import torch
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import Receiver
+    n_max = max(f.shape[1] // 2 for f in frames)
+    inputs = [device_input(f, fmt) for f in frames]
+    scale = inputs[0][2]
+    rcv = Receiver(rx_settings, n_max, input_format=fmt, input_scale=scale, streaming=streaming)
+    names = {"y": rx.RX_BUF_Y, "z": rx.RX_BUF_Z, "bstar": rx.RX_BUF_BSTAR, "m": rx.RX_BUF_M, "cdc": rx.RX_BUF_CDC,
+             "taps_cma": rx.RX_BUF_TAPS_CMA, "taps_init": rx.RX_BUF_TAPS_INIT, "taps_last": rx.RX_BUF_TAPS_LAST,
+             "y_foe": rx.RX_BUF_Y_FOE, "scale": rx.RX_BUF_SCALE, "y_acq": rx.RX_BUF_Y_ACQ}
+    out = []
+    T = rx_settings["n_taps"]
+    hist = (T - 1) // 2 + 2 * (((T - 1) // 2 + 1) // 2)
+    for i, (x, vals, _) in enumerate(inputs):
+        N = frames[i].shape[1] // 2
+        ref = torch.from_numpy(refs[i].astype(np.int32).view(np.int32)).cuda() if refs is not None else None
+        words = rcv.words(N)
+        bits = torch.zeros(2 * words, dtype=torch.int32, device="cuda")
+        before = rcv.stats()
+        rcv.process(x, N, ref, bits)
+        st = rcv.stats()
+        res = dict(stats=st, oracle_input=vals, n=N)
+        res["delta"] = {k: st[k] - before[k] for k in ("bits_counted", "bit_errors", "symbols_counted",
+                                                      "symbol_errors", "evm_num", "evm_den")}
+        res["bits"] = bits.cpu().numpy().view(np.uint32).reshape(2, words)
+        for b in buffers:
+            t = rcv.buffer(names[b]).cpu().numpy()
+            if b in ("y", "z"):
+                t = t.reshape(2, -1)[:, :N]
+            elif b in ("bstar", "m"):
+                t = t.reshape(2, -1)[:, :N]
+            elif b == "cdc":
+                t = t.reshape(2, -1)
+                t = t[:, hist:hist + 2 * N] if streaming else t[:, :2 * N]
+            elif b.startswith("taps"):
+                t = t.reshape(2, 2, T)
+            elif b == "y_foe":
+                t = t.reshape(2, -1)
+            res[b] = t
+        out.append(res)
+    rcv.close()
+    return out

@@ -1,0 +1,87 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every declared symbol,
+and the ctypes mirrors of the structs have the C layout (no GPU needed)."""
+
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rx.h")
+
+
+@pytest.fixture(scope="module")
+def librx():
+    from paper_2011_13695_gb300 import build, rx
+    build.build()
+    return rx.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rx_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("rx_create", "rx_process", "rx_stats", "rx_destroy", "rx_process_host", "rx_get_buffer",
+                 "rx_state_get", "rx_state_set", "rx_reset", "rx_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(librx):
+    from paper_2011_13695_gb300 import rx
+    for name in declared_functions():
+        assert hasattr(librx, name), name
+    assert set(rx.EXPORTS) == set(declared_functions())
+
+
+def test_status_strings_without_a_gpu(librx):
+    from paper_2011_13695_gb300 import rx
+    assert rx.rx_strerror(rx.RX_OK) == "ok"
+    assert "invalid" in rx.rx_strerror(rx.RX_EINVAL)
+    assert rx.rx_stage_count() == len([rx.rx_stage_name(i) for i in range(rx.rx_stage_count())])
+    assert rx.rx_stage_name(1) == "cdc"
+
+
+def test_invalid_configs_are_rejected_before_any_device_call(librx):
+    from paper_2011_13695_gb300 import rx
+    base = dict(bits_per_sym=4, sps=2, symbol_rate_hz=32e9, wavelength_m=1550e-9, dispersion_s_per_m2=17e-6,
+                length_m=80e3, rrc_rolloff=0.1, fft_size=4096, n_taps=21, lms_block=128, cma_blocks=64,
+                dd_acq_blocks=128, seg_blocks=16, warmup_blocks=4, bps_phases=64, bps_window=64, edge_skip=512,
+                sync_len=4096, max_delay=16, mu_cma=1e-3, mu_dd=1e-3, fo_grid_hz=100e3, input_format=0,
+                input_scale=1.0, streaming=0, max_symbols=1 << 16)
+    bad = [dict(sps=4), dict(bits_per_sym=3), dict(fft_size=3000), dict(fft_size=16384), dict(n_taps=20),
+           dict(n_taps=65), dict(lms_block=8), dict(bps_phases=65), dict(bps_window=48), dict(max_delay=65),
+           dict(warmup_blocks=17), dict(max_symbols=0), dict(input_format=3), dict(symbol_rate_hz=0.0),
+           dict(cma_blocks=200), dict(streaming=1, max_symbols=1000), dict(fo_grid_hz=0.0), dict(mu_dd=-1.0)]
+    for b in bad:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_create(rx.make_config(**dict(base, **b)))
+        assert e.value.status == rx.RX_EINVAL, b
+
+
+def test_struct_layout_matches_the_c_compiler(librx):
+    from paper_2011_13695_gb300 import rx
+    fields = [n for n, _ in rx.rx_config._fields_]
+    sfields = [n for n, _ in rx.rx_stats_t._fields_]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){",
+            'printf("%zu %zu\\n", sizeof(rx_config), sizeof(rx_stats_t));']
+    prog += [f'printf("%zu\\n", offsetof(rx_config, {f}));' for f in fields]
+    prog += [f'printf("%zu\\n", offsetof(rx_stats_t, {f}));' for f in sfields]
+    prog += ["return 0;}"]
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write("\n".join(prog))
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-std=c99", "-o", exe, c], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    vals = list(map(int, out))
+    assert vals[0] == ctypes.sizeof(rx.rx_config) and vals[1] == ctypes.sizeof(rx.rx_stats_t)
+    offs = vals[2:]
+    assert offs[:len(fields)] == [getattr(rx.rx_config, f).offset for f in fields]
+    assert offs[len(fields):] == [getattr(rx.rx_stats_t, f).offset for f in sfields]

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA chain (through the C ABI) against the FP64 oracle on the same seeded frames.
+
+Tolerances (FP32 on the GPU, FP64 in the oracle):
+  * equaliser output y (P1) and carrier-recovered z (P2): relative RMS <= 1e-4;
+  * FD-compensated samples: relative RMS <= 1e-5 (one FP32 FFT pair);
+  * FO code: equal (unless the oracle's estimate lies within 1 % of a grid step
+    of a rounding boundary, where both codes are correct);
+  * BPS phase index b* and hard decisions: differ on <= 1e-5 of the symbols
+    (rounded up to whole symbols);
+  * bit-error counts: exact; the GPU count equals the count recomputed on the
+    host from the GPU's own output bits, and equals the oracle's count when
+    the decisions agree.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import decide as odec
+from oracle import qam as oqam
+from oracle.receiver import Receiver as OracleRx
+from oracle.receiver import RxConfig
+from synth import generate, workload
+from synth.channel import LinkParams, pack_bits
+from tests.gpu_util import rel_rms, run_gpu_frames
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2011_13695_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    build.build()
+
+
+def allowed(n_sym_total: int) -> int:
+    return math.ceil(1e-5 * n_sym_total)
+
+
+def host_recount(g, o_sync, ref_words, m, n, lo, hi, lat=0):
+    """Bit errors from the GPU's own output bits, aligned with the GPU's sync result."""
+    st = g["stats"]
+    bits = oqam.unpack_words(g["bits"], n * m).reshape(2, n, m)
+    ref = oqam.unpack_words(ref_words, n * m).reshape(2, n, m)
+    errs = 0
+    for q in range(2):
+        p, d = st["pol_map"][q], st["delay"][q]
+        k = np.arange(lo, hi)
+        errs += int(np.sum(bits[q, k] != ref[p, k + d - lat]))
+    return errs
+
+
+def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True):
+    N = g["n"]
+    m = cfg.bits_per_sym
+    if check_cdc:
+        assert rel_rms(g["cdc"], r.cdc) < 1e-5
+    assert rel_rms(g["scale"], r.scale) < 1e-6
+    if r.fo_margin < 0.01:
+        pytest.skip("oracle FO estimate within 1 % of a rounding boundary: two correct codes")
+    assert g["stats"]["fo_code"] == r.fo_code
+    assert rel_rms(g["y"], r.y) < tol_y
+    nb = int(np.sum(g["bstar"] != r.bstar))
+    assert nb <= allowed(2 * N), f"b* differs on {nb} symbols"
+    assert rel_rms(g["z"], r.z) < tol_y
+    gl = oqam.decide_levels(g["z"], m)
+    ol = oqam.decide_levels(r.z, m)
+    ndiff = int(np.sum((gl[0] != ol[0]) | (gl[1] != ol[1])))
+    assert ndiff <= allowed(2 * N), f"decisions differ on {ndiff} symbols"
+    # output bits: the GPU's bits are the demap of its own z (with its quarter turns)
+    if ref_words is not None and r.sync is not None:
+        st = g["stats"]
+        assert [tuple(s[:3]) for s in r.sync] == list(zip(st["pol_map"], st["rotation"], st["delay"]))
+        d = g["delta"]
+        assert d["bits_counted"] == r.counts["bits"]
+        E = max(cfg.edge_skip, lat + cfg.max_delay) if lat else cfg.edge_skip
+        assert host_recount(g, r.sync, ref_words, m, N, E, max(N - E, E), lat) == d["bit_errors"]
+        if ndiff == 0:
+            assert d["bit_errors"] == r.counts["bit_errors"]
+            assert d["symbol_errors"] == r.counts["symbol_errors"]
+        assert d["evm_num"] / d["evm_den"] == pytest.approx(r.counts["evm_num"] / r.counts["evm_den"], rel=1e-3)
+    want_bits = oqam.pack_words(odec.demap_output(g["z"], r.sync, m))
+    assert np.array_equal(g["bits"], want_bits)
+
+
+def run_pair(w, seed, n_sym=None, fmt=0, link_kw=None, rx_kw=None):
+    link = w["link"]
+    if n_sym is not None:
+        link = link.with_(n_sym=n_sym)
+    if link_kw:
+        link = link.with_(**link_kw)
+    fr = generate(link, seed)
+    rxs = dict(w["rx"], **(rx_kw or {}))
+    g = run_gpu_frames(rxs, [fr.samples], [fr.ref_words], fmt=fmt)[0]
+    cfg = RxConfig.from_dict(rxs)
+    r = OracleRx(cfg).process(g["oracle_input"], fr.ref_words)
+    return g, r, cfg, fr
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_qpsk_25gbd_frame(seed):
+    w = workload("dp-qpsk-25gbd")
+    g, r, cfg, fr = run_pair(w, seed)
+    assert rel_rms(g["taps_cma"], r.taps_cma) < 1e-4
+    check_frame(g, r, cfg, fr.ref_words)
+
+
+def test_16qam_32gbd_reduced_frame():
+    w = workload("dp-16qam-32gbd", n_sym=1 << 16)
+    g, r, cfg, fr = run_pair(w, 3)
+    check_frame(g, r, cfg, fr.ref_words)
+
+
+def test_16qam_32gbd_full_frame():
+    """The bench workload at its full size (2^20 symbols per polarisation, one frame)."""
+    w = workload("dp-16qam-32gbd")
+    g, r, cfg, fr = run_pair(w, 1)
+    check_frame(g, r, cfg, fr.ref_words)
+
+
+@pytest.mark.parametrize("n_sym", [5003, 777, 100, 40])
+def test_ragged_and_tiny_frames(n_sym):
+    """Frames that are not a whole number of blocks/segments/tiles, shorter than the
+    counted window, shorter than the acquisition, shorter than one LMS block."""
+    w = workload("dp-qpsk-25gbd")
+    g, r, cfg, fr = run_pair(w, 4, n_sym=n_sym)
+    assert rel_rms(g["cdc"], r.cdc) < 1e-5
+    assert rel_rms(g["y"], r.y) < 1e-4
+    assert int(np.sum(g["bstar"] != r.bstar)) <= allowed(2 * n_sym)
+    want_bits = oqam.pack_words(odec.demap_output(g["z"], r.sync, cfg.bits_per_sym))
+    assert np.array_equal(g["bits"], want_bits)
+    if r.sync is None:
+        assert g["delta"]["bits_counted"] == 0
+
+
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_precision_inputs_64qam(fmt):
+    """FP16 and int8 (4 sigma clip) ADC samples: the oracle sees the same dequantised values."""
+    w = workload("dp-64qam-48gbd-stream", n_frames=1, frame_sym=1 << 15)
+    g, r, cfg, fr = run_pair(w, 5, fmt=fmt)
+    check_frame(g, r, cfg, fr.ref_words)
+
+
+def test_stream_of_frames_matches_the_oracle_stream():
+    w = workload("dp-64qam-48gbd-stream", n_frames=3, frame_sym=1 << 14)
+    link = w["link"].with_(n_sym=3 << 14)
+    fr = generate(link, 6)
+    S = 2 << 14
+    frames = [fr.samples[:, f * S:(f + 1) * S] for f in range(3)]
+    refs = [pack_bits(fr.bits[:, f * (S // 2) * 6:(f + 1) * (S // 2) * 6]) for f in range(3)]
+    gs = run_gpu_frames(w["rx"], frames, refs, streaming=True)
+    cfg = RxConfig.from_dict(w["rx"])
+    orx = OracleRx(cfg, stream=True)
+    for f in range(3):
+        r = orx.process(gs[f]["oracle_input"], refs[f])
+        check_frame(gs[f], r, cfg, refs[f], lat=cfg.stream_latency)
+
+
+def test_nonfinite_input_sets_the_error_word():
+    import torch
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import Receiver
+    w = workload("dp-qpsk-25gbd", n_sym=4096)
+    fr = generate(w["link"], 1)
+    x = np.ascontiguousarray(fr.samples.astype(np.complex64))
+    x[1, 1234] = np.nan
+    t = torch.from_numpy(x.view(np.float32)).cuda()
+    rcv = Receiver(w["rx"], 4096)
+    rcv.process(t, 4096)
+    assert rcv.stats()["error_word"] & rx.RX_ERR_NONFINITE
+
+
+def test_invalid_process_arguments():
+    import torch
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import Receiver
+    w = workload("dp-qpsk-25gbd")
+    rcv = Receiver(w["rx"], 2048)
+    t = torch.zeros(2 * 2 * 4096 * 2, device="cuda")
+    for n in (0, -5, 4096):
+        with pytest.raises(rx.RxError) as e:
+            rcv.process(t, n)
+        assert e.value.status == rx.RX_EINVAL
+    srx = Receiver(w["rx"], 2048, streaming=True)
+    with pytest.raises(rx.RxError):
+        srx.process(t, 1000)                         # not a whole number of N_fft/4 symbols
+
+
+def test_host_entry_point_matches_device_entry_point():
+    import torch
+    from paper_2011_13695_gb300.receiver import Receiver
+    w = workload("dp-qpsk-25gbd")
+    fr = generate(w["link"], 2)
+    N = w["link"].n_sym
+    x = np.ascontiguousarray(fr.samples.astype(np.complex64))
+    ref = fr.ref_words.astype(np.uint32)
+    a = Receiver(w["rx"], N)
+    out_d = torch.zeros(2 * a.words(N), dtype=torch.int32, device="cuda")
+    a.process(torch.from_numpy(x.view(np.float32)).cuda(), N, torch.from_numpy(ref.view(np.int32)).cuda(), out_d)
+    b = Receiver(w["rx"], N)
+    xh = torch.from_numpy(x.view(np.float32)).pin_memory()
+    rh = torch.from_numpy(ref.view(np.int32)).pin_memory()
+    out_h = torch.zeros(2 * b.words(N), dtype=torch.int32).pin_memory()
+    b.process_host(xh, N, rh, out_h)
+    sb = b.stats()
+    assert np.array_equal(out_h.numpy(), out_d.cpu().numpy())
+    sa = a.stats()
+    assert sa["bit_errors"] == sb["bit_errors"] and sa["bits_counted"] == sb["bits_counted"]
+
+
+def test_stream_state_checkpoint_resume():
+    import torch
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import Receiver
+    w = workload("dp-64qam-48gbd-stream", n_frames=3, frame_sym=1 << 13)
+    fr = generate(w["link"].with_(n_sym=3 << 13), 7)
+    S = 2 << 13
+    xs = [torch.from_numpy(np.ascontiguousarray(fr.samples[:, f * S:(f + 1) * S].astype(np.complex64))
+                           .view(np.float32)).cuda() for f in range(3)]
+    a = Receiver(w["rx"], 1 << 13, streaming=True)
+    a.process(xs[0], 1 << 13)
+    a.process(xs[1], 1 << 13)
+    blob = rx.rx_state_get(a.h)
+    b = Receiver(w["rx"], 1 << 13, streaming=True)
+    rx.rx_state_set(b.h, blob)
+    a.process(xs[2], 1 << 13)
+    b.process(xs[2], 1 << 13)
+    za = a.buffer(rx.RX_BUF_Z).cpu().numpy()
+    zb = b.buffer(rx.RX_BUF_Z).cpu().numpy()
+    assert np.array_equal(za, zb)
+    other = Receiver(dict(w["rx"], n_taps=15), 1 << 13, streaming=True)
+    with pytest.raises(rx.RxError) as e:
+        rx.rx_state_set(other.h, blob)
+    assert e.value.status == rx.RX_ESTATE
