@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
     return ap.parse_args()
 
 
@@ -225,7 +227,7 @@ def our_arm(args) -> None:
     from paper_2011_13695_gb300.receiver import Receiver
     from synth import generate, workload
 
-    w = workload(WORKLOAD)
+    w = workload(WORKLOAD, **({"n_sym": args.n_sym} if args.n_sym else {}))
     link = w["link"]
     N = link.n_sym
     m = link.bits_per_sym
@@ -275,17 +277,20 @@ def our_arm(args) -> None:
     xh = torch.from_numpy(x_host.view(np.float32)).pin_memory()
     rh = torch.from_numpy(ref_host.view(np.int32)).pin_memory()
     oh = torch.zeros(2 * rcv.words(N), dtype=torch.int32).pin_memory()
-    for _ in range(args.warmup):
-        rcv.process_host(xh, N, rh, oh)
-    barrier()
-    e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        e_evs[i][0].record(stream)
-        rcv.process_host(xh, N, rh, oh)
-        e_evs[i][1].record(stream)
-    barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e_evs)
+    e2e_ms = float("nan")
+    if not args.no_e2e:
+        for _ in range(args.warmup):
+            rcv.process_host(xh, N, rh, oh)
+        barrier()
+        e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e_evs[i][0].record(stream)
+            rcv.process_host(xh, N, rh, oh)
+            e_evs[i][1].record(stream)
+        barrier()
+        e2e_ms = sum(a.elapsed_time(b) for a, b in e_evs)
     if dist:
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -302,7 +307,7 @@ def our_arm(args) -> None:
     roof = stage_roofline(dom, per_stage[dom], w, N, pk, csum.get("sm_mhz"))
     roof["peak_source"] = "fallback" if pk.get("fallback") else "measured (MEASURED_PEAKS.json) / nominal unit count"
     value = world * bits_per_step * args.steps / (total_ms * 1e-3) / 1e9
-    e2e = world * bits_per_step * args.steps / (e2e_ms * 1e-3) / 1e9
+    e2e = world * bits_per_step * args.steps / (e2e_ms * 1e-3) / 1e9 if e2e_ms == e2e_ms else None
     line = {
         "metric": "processed line rate", "value": value, "unit": "Gb/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -11,6 +11,8 @@
 // become Gray bits, 32 symbols of a warp assemble m output words with
 // warp-wide ORs, errors are the popcount of the XOR with the reference bits,
 // integer counters accumulate with 64-bit atomics, EVM sums in FP64.
+#include <algorithm>
+
 #include "rx_kernels.h"
 
 namespace {
@@ -107,72 +109,89 @@ __global__ void k_sync_pick(const int* counts, int D, int64_t len, RxDevState* s
     st->sync_valid = 1;
 }
 
-__global__ void k_count(const float2* __restrict__ z, int64_t zstride, int64_t N, const uint32_t* __restrict__ ref,
-                        int64_t refstride, int64_t n_ref, int m, int64_t lo, int64_t hi, int64_t lat,
-                        uint32_t* __restrict__ out, int64_t outstride, RxDevState* st) {
+// Grid-stride over the symbols of one output polarisation; counters stay in
+// registers until one block-wide reduction and one set of atomics per CTA.
+__global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int64_t zstride, int64_t N,
+                                               const uint32_t* __restrict__ ref, int64_t refstride, int64_t n_ref,
+                                               int m, int64_t lo, int64_t hi, int64_t lat,
+                                               uint32_t* __restrict__ out, int64_t outstride, RxDevState* st) {
     const int q = blockIdx.y;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool have_sync = ref != nullptr && st->sync_valid;
     const int r = have_sync ? st->sync_r[q] : 0;
+    const int p = have_sync ? st->sync_p[q] : 0, d = have_sync ? st->sync_d[q] : 0;
     const Qam qm = make_qam(m);
-    uint32_t sbits = 0;
-    int li = 0, lq = 0;
-    float2 v = make_float2(0.0f, 0.0f);
-    if (n < N) {
-        v = quarter(z[(int64_t)q * zstride + n], r);
-        li = qam_level(v.x, qm);
-        lq = qam_level(v.y, qm);
-        sbits = msb_first_to_stream(qam_bits(li, lq, qm), m);
-    }
-    if (out) {
-        // warp symbols n0..n0+31 fill words [n0*m/32, n0*m/32 + m)
-        const int64_t n0 = n - lane;
-        const int64_t nwords = (N * m + 31) / 32;
-        for (int w = 0; w < m; ++w) {
-            const int sh = lane * m - 32 * w;          // position of this symbol's bit 0 in word w
-            uint32_t contrib = 0;
-            if (n < N) {
-                if (sh >= 0 && sh < 32) contrib = sbits << sh;
-                else if (sh < 0 && sh > -m) contrib = sbits >> (-sh);
+    const int64_t nwords = (N * m + 31) / 32;
+    const uint32_t* refp = have_sync ? ref + (int64_t)p * refstride : nullptr;
+    uint32_t errs = 0, serr = 0, cnt = 0;
+    double en = 0.0, ed = 0.0;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n - lane < N; n += step) {
+        uint32_t sbits = 0;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (n < N) {
+            v = quarter(z[(int64_t)q * zstride + n], r);
+            sbits = msb_first_to_stream(qam_bits(qam_level(v.x, qm), qam_level(v.y, qm), qm), m);
+        }
+        if (out) {
+            // warp symbols n0..n0+31 fill words [n0*m/32, n0*m/32 + m)
+            const int64_t n0 = n - lane;
+            for (int w = 0; w < m; ++w) {
+                const int sh = lane * m - 32 * w;      // position of this symbol's bit 0 in word w
+                uint32_t contrib = 0;
+                if (n < N) {
+                    if (sh >= 0 && sh < 32) contrib = sbits << sh;
+                    else if (sh < 0 && sh > -m) contrib = sbits >> (-sh);
+                }
+                const uint32_t word = __reduce_or_sync(0xffffffffu, contrib);
+                const int64_t wi = n0 * m / 32 + w;
+                if (lane == w && wi < nwords) out[(int64_t)q * outstride + wi] = word;
             }
-            const uint32_t word = __reduce_or_sync(0xffffffffu, contrib);
-            const int64_t wi = n0 * m / 32 + w;
-            if (lane == w && wi < nwords) out[(int64_t)q * outstride + wi] = word;
+        }
+        if (have_sync && n >= lo && n < hi) {
+            const int64_t t = n + d - lat;
+            if (t >= 0 && t < n_ref) {
+                const uint32_t rb = ref_symbol_bits(refp, t, m);
+                const uint32_t e = __popc(rb ^ sbits);
+                errs += e;
+                serr += e ? 1u : 0u;
+                cnt += 1;
+                int ti, tq;
+                bits_to_levels(rb, m, ti, tq);
+                const float2 s = make_float2(qam_value(ti, qm), qam_value(tq, qm));
+                en += (double)cabs2(csub(v, s));
+                ed += (double)cabs2(s);
+            }
         }
     }
     if (!have_sync) return;
-    const int p = st->sync_p[q], d = st->sync_d[q];
-    const bool counted = (n >= lo && n < hi);
-    uint32_t errs = 0, serr = 0, cnt = 0;
-    float en = 0.0f, ed = 0.0f;
-    if (counted) {
-        const int64_t t = n + d - lat;
-        if (t >= 0 && t < n_ref) {
-            const uint32_t rb = ref_symbol_bits(ref + (int64_t)p * refstride, t, m);
-            errs = __popc(rb ^ sbits);
-            serr = errs ? 1u : 0u;
-            cnt = 1;
-            int ti, tq;
-            bits_to_levels(rb, m, ti, tq);
-            const float2 s = make_float2(qam_value(ti, qm), qam_value(tq, qm));
-            const float2 e = csub(v, s);
-            en = cabs2(e);
-            ed = cabs2(s);
-        }
-    }
+    __shared__ unsigned int ri[3][8];
+    __shared__ double rd[2][8];
     errs = __reduce_add_sync(0xffffffffu, errs);
     serr = __reduce_add_sync(0xffffffffu, serr);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
-    en = warp_sum(en);
-    ed = warp_sum(ed);
-    if (lane == 0 && cnt) {
-        atomicAdd(&st->bit_errors, (unsigned long long)errs);
-        atomicAdd(&st->symbol_errors, (unsigned long long)serr);
-        atomicAdd(&st->symbols, (unsigned long long)cnt);
-        atomicAdd(&st->bits, (unsigned long long)cnt * (unsigned long long)m);
-        atomicAdd(&st->evm_num, (double)en);
-        atomicAdd(&st->evm_den, (double)ed);
+    en = warp_sum_d(en);
+    ed = warp_sum_d(ed);
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        ri[0][w] = errs; ri[1][w] = serr; ri[2][w] = cnt;
+        rd[0][w] = en; rd[1][w] = ed;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0, c = 0;
+        double x = 0.0, y = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += ri[0][i]; b += ri[1][i]; c += ri[2][i]; x += rd[0][i]; y += rd[1][i];
+        }
+        if (c) {
+            atomicAdd(&st->bit_errors, a);
+            atomicAdd(&st->symbol_errors, b);
+            atomicAdd(&st->symbols, c);
+            atomicAdd(&st->bits, c * (unsigned long long)m);
+            atomicAdd(&st->evm_num, x);
+            atomicAdd(&st->evm_den, y);
+        }
     }
 }
 
@@ -198,7 +217,11 @@ cudaError_t launch_count(const float2* z, int64_t zstride, int64_t N, const uint
                          int64_t n_ref, int m, int64_t lo, int64_t hi, int64_t lat, uint32_t* out,
                          int64_t outstride, RxDevState* st, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((N + 255) / 256), 2);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (N + 255) / 256;
+    dim3 grid((unsigned)std::min<int64_t>(want, (int64_t)nsm * 4), 2);
     k_count<<<grid, 256, 0, s>>>(z, zstride, N, ref, refstride, n_ref, m, lo, hi, lat, out, outstride, st);
     return cudaGetLastError();
 }

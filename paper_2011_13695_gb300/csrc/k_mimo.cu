@@ -20,53 +20,101 @@
 
 namespace {
 
-struct LmsSmem {
+template <int NT>
+struct LmsCtx {
+    static constexpr int PF = (2 * (2 * 256 + RX_TMAX) + NT - 1) / NT;   // prefetch registers per thread
     float2* taps;    // [4][T]
-    float2* xs;      // [2][XW]
+    float2* xs[2];   // staging double buffer, each [2][XS]
     float2* ys;      // [2][Lb]
     float2* es;      // [2][Lb]
     float2* part;    // [G][4T]
     float2* rot;     // [2] e^{-j psi}
-    int XW, G;
+    int XS, G, P;
+    float2 pf[PF];   // next window, raw
 };
 
-__device__ void lms_block(const LmsArgs& a, LmsSmem& s, int64_t n0, int L, bool store, int nthreads,
-                          long long inc) {
-    const int tid = threadIdx.x;
-    const int T = a.T, c = (a.T - 1) / 2;
-    const int XW = 2 * L + T - 2 + 1;
-    // 1. stage x[i], i = off + 2 n0 - c + j, j < XW (derotated, zero outside the buffer)
+// Window of the block starting at symbol n0 with L symbols: buffer indices
+// i = off + 2 n0 - c + j, j < 2L + T - 1 (zero outside [0, xlen)).
+template <int NT>
+__device__ __forceinline__ void lms_prefetch(const LmsArgs& a, LmsCtx<NT>& s, int64_t n0, int L) {
+    const int c = (a.T - 1) / 2;
+    const int XW = 2 * L + a.T - 1;
     const int64_t i0 = a.off + 2 * n0 - c;
-    for (int t = tid; t < 2 * XW; t += nthreads) {
-        const int p = t / XW, jj = t - p * XW;
-        const int64_t i = i0 + jj;
+#pragma unroll
+    for (int r = 0; r < LmsCtx<NT>::PF; ++r) {
+        const int t = threadIdx.x + r * NT;
         float2 v = make_float2(0.0f, 0.0f);
-        if (i >= 0 && i < a.xlen) {
-            v = a.x[(int64_t)p * a.xstride + i];
-            if (inc) v = cmul(v, nco_conj(inc, a.g0 + i));
+        if (t < 2 * XW) {
+            const int p = t >= XW ? 1 : 0, jj = t - p * XW;
+            const int64_t i = i0 + jj;
+            if (i >= 0 && i < a.xlen) v = a.x[(int64_t)p * a.xstride + i];
         }
-        s.xs[p * s.XW + jj] = v;
+        s.pf[r] = v;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void lms_commit(const LmsArgs& a, LmsCtx<NT>& s, int buf, int64_t n0, int L,
+                                           long long inc) {
+    const int c = (a.T - 1) / 2;
+    const int XW = 2 * L + a.T - 1;
+    const int64_t i0 = a.off + 2 * n0 - c;
+    float2* xs = s.xs[buf];
+#pragma unroll
+    for (int r = 0; r < LmsCtx<NT>::PF; ++r) {
+        const int t = threadIdx.x + r * NT;
+        if (t < 2 * XW) {
+            const int p = t >= XW ? 1 : 0, jj = t - p * XW;
+            float2 v = s.pf[r];
+            if (inc) v = cmul(v, nco_conj(inc, a.g0 + i0 + jj));
+            xs[p * s.XS + jj] = v;
+        }
+    }
+}
+
+// One block update. Outputs: P lanes per output split the 2T terms and combine
+// with xor-shuffles. Gradient: G thread groups take every G-th symbol of the
+// block and their partial sums are added in a fixed order.
+template <int NT>
+__device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const float2* xs, int64_t n0, int L,
+                                          bool store, const Qam& qm) {
+    const int tid = threadIdx.x;
+    const int T = a.T, T2 = 2 * a.T;
+    const int P = s.P;
+    // outputs with the taps the block starts with
+    {
+        const int j = tid & (P - 1);
+        // ob is uniform across a warp so that every lane reaches the shuffles
+        for (int ob = (tid >> 5) * (32 / P); ob < 2 * L; ob += NT / P) {
+            const int o = ob + (tid & 31) / P;
+            const bool valid = o < 2 * L;
+            const int q = valid ? (o >= L ? 1 : 0) : 0, n = valid ? o - q * L : 0;
+            float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+            int u = valid ? j : T2;
+            for (; u + P < T2; u += 2 * P) {
+                const int p0 = u >= T ? 1 : 0, k0 = u - p0 * T;
+                const int u1 = u + P;
+                const int p1 = u1 >= T ? 1 : 0, k1 = u1 - p1 * T;
+                acc0 = cmac(acc0, s.taps[(q * 2 + p0) * T + k0], xs[p0 * s.XS + 2 * n + T - 1 - k0]);
+                acc1 = cmac(acc1, s.taps[(q * 2 + p1) * T + k1], xs[p1 * s.XS + 2 * n + T - 1 - k1]);
+            }
+            if (u < T2) {
+                const int p0 = u >= T ? 1 : 0, k0 = u - p0 * T;
+                acc0 = cmac(acc0, s.taps[(q * 2 + p0) * T + k0], xs[p0 * s.XS + 2 * n + T - 1 - k0]);
+            }
+            float2 acc = cadd(acc0, acc1);
+            for (int w = 1; w < P; w <<= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, w);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, w);
+            }
+            if (valid && j == 0) {
+                s.ys[q * L + n] = acc;
+                if (a.cma) s.es[q * L + n] = cscale(acc, a.R2 - cabs2(acc));
+                if (store) a.y[(int64_t)q * a.ystride + n0 + n] = acc;
+            }
+        }
     }
     __syncthreads();
-    // 2. outputs with the taps the block starts with
-    for (int o = tid; o < 2 * L; o += nthreads) {
-        const int q = o / L, n = o - q * L;
-        float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-        for (int p = 0; p < 2; ++p) {
-            const float2* hq = s.taps + (q * 2 + p) * T;
-            const float2* xp = s.xs + p * s.XW + 2 * n + T - 1;
-            for (int k = 0; k < T; ++k) acc = cmac(acc, hq[k], xp[-k]);
-        }
-        s.ys[q * L + n] = acc;
-        if (a.cma) {
-            const float r = a.R2 - cabs2(acc);
-            s.es[q * L + n] = cscale(acc, r);
-        }
-        if (store) a.y[(int64_t)q * a.ystride + n0 + n] = acc;
-    }
-    __syncthreads();
-    // 3. DD: block phase and errors
     if (!a.cma) {
         const int w = tid >> 5, lane = tid & 31;
         if (w < 2) {
@@ -86,9 +134,8 @@ __device__ void lms_block(const LmsArgs& a, LmsSmem& s, int64_t n0, int L, bool 
             }
         }
         __syncthreads();
-        const Qam qm = make_qam(a.m);
-        for (int o = tid; o < 2 * L; o += nthreads) {
-            const int q = o / L;
+        for (int o = tid; o < 2 * L; o += NT) {
+            const int q = o >= L ? 1 : 0;
             const float2 y = s.ys[o];
             const float2 r = s.rot[q];
             const float2 d = qam_decide(cmul(y, r), qm);
@@ -96,62 +143,87 @@ __device__ void lms_block(const LmsArgs& a, LmsSmem& s, int64_t n0, int L, bool 
         }
         __syncthreads();
     }
-    // 4. gradient: partial sums of G groups in a fixed order
-    const int NTAP = 4 * T;
+    // gradient partial sums
+    const int NTAP = 2 * T2;
     {
         const int g = tid / NTAP, t = tid - g * NTAP;
         if (g < s.G) {
-            const int q = t / (2 * T), p = (t / T) & 1, k = t - (t / T) * T;
-            const int per = (L + s.G - 1) / s.G;
-            const int nb = g * per, ne = min(L, nb + per);
-            float2 acc = make_float2(0.0f, 0.0f);
-            const float2* xp = s.xs + p * s.XW + T - 1 - k;
+            const int q = t / T2, p = (t / T) & 1, k = t - (t / T) * T;
+            const float2* xp = xs + p * s.XS + T - 1 - k;
             const float2* eq = s.es + q * L;
-            for (int n = nb; n < ne; ++n) acc = cmacc(acc, eq[n], xp[2 * n]);
-            s.part[g * NTAP + t] = acc;
+            float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+            int n = g;
+            for (; n + s.G < L; n += 2 * s.G) {
+                acc0 = cmacc(acc0, eq[n], xp[2 * n]);
+                acc1 = cmacc(acc1, eq[n + s.G], xp[2 * (n + s.G)]);
+            }
+            if (n < L) acc0 = cmacc(acc0, eq[n], xp[2 * n]);
+            s.part[g * NTAP + t] = cadd(acc0, acc1);
         }
     }
     __syncthreads();
-    for (int t = tid; t < NTAP; t += nthreads) {
+    for (int t = tid; t < NTAP; t += NT) {
         float2 acc = make_float2(0.0f, 0.0f);
         for (int g = 0; g < s.G; ++g) acc = cadd(acc, s.part[g * NTAP + t]);
-        // taps index [q][p][k] = t (same ordering as the partial sums)
         s.taps[t] = make_float2(fmaf(a.mu, acc.x, s.taps[t].x), fmaf(a.mu, acc.y, s.taps[t].y));
     }
-    __syncthreads();
 }
 
-__global__ void k_lms(LmsArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
     extern __shared__ float2 smem[];
     if (a.run_if && *a.run_if == 0) return;
-    const int nthreads = blockDim.x;
     const int T = a.T, Lb = a.Lb;
-    LmsSmem s;
-    s.XW = 2 * Lb + T;
-    s.G = max(1, nthreads / (4 * T));
+    LmsCtx<NT> s;
+    s.XS = 2 * Lb + T;
+    s.G = max(1, NT / (4 * T));
+    int P = 1;
+    while (P < 8 && 2 * P * 2 * Lb <= NT) P *= 2;
+    s.P = P;
     s.taps = smem;
-    s.xs = s.taps + 4 * T;
-    s.ys = s.xs + 2 * s.XW;
+    s.xs[0] = s.taps + 4 * T;
+    s.xs[1] = s.xs[0] + 2 * s.XS;
+    s.ys = s.xs[1] + 2 * s.XS;
     s.es = s.ys + 2 * Lb;
     s.part = s.es + 2 * Lb;
     s.rot = s.part + s.G * 4 * T;
+    const Qam qm = make_qam(a.m);
 
     const int64_t seg = blockIdx.x;
     const int64_t nseg = gridDim.x;
     const long long inc = a.derotate ? a.st->nco_inc : 0;
-    for (int t = threadIdx.x; t < 4 * T; t += nthreads) s.taps[t] = a.taps_in[t];
-    __syncthreads();
+    for (int t = threadIdx.x; t < 4 * T; t += NT) s.taps[t] = a.taps_in[t];
     const int64_t start = seg * a.L_seg;
     const int64_t end = min(a.n_sym, start + a.L_seg);
-    if (seg > 0) {
-        for (int w = a.n_wu; w > 0; --w) lms_block(a, s, start - (int64_t)w * Lb, Lb, false, nthreads, inc);
+    const int nwarm = seg > 0 ? a.n_wu : 0;
+    const int nmain = (int)((end - start + Lb - 1) / Lb);
+    const int nblk = nwarm + nmain;
+    auto blk = [&](int b, int64_t& n0, int& L) {
+        if (b < nwarm) { n0 = start - (int64_t)(nwarm - b) * Lb; L = Lb; }
+        else { n0 = start + (int64_t)(b - nwarm) * Lb; L = (int)min((int64_t)Lb, end - n0); }
+    };
+    int64_t n0;
+    int L;
+    if (nblk > 0) {
+        blk(0, n0, L);
+        lms_prefetch(a, s, n0, L);
+        lms_commit(a, s, 0, n0, L, inc);
     }
-    for (int64_t n0 = start; n0 < end; n0 += Lb) {
-        const int L = (int)min((int64_t)Lb, end - n0);
-        lms_block(a, s, n0, L, a.y != nullptr, nthreads, inc);
+    __syncthreads();
+    for (int b = 0; b < nblk; ++b) {
+        blk(b, n0, L);
+        int64_t nn0 = 0;
+        int nL = 0;
+        if (b + 1 < nblk) {
+            blk(b + 1, nn0, nL);
+            lms_prefetch(a, s, nn0, nL);
+        }
+        lms_block<NT>(a, s, s.xs[b & 1], n0, L, b >= nwarm && a.y != nullptr, qm);
+        if (b + 1 < nblk) lms_commit(a, s, (b + 1) & 1, nn0, nL, inc);
+        __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out) {
-        for (int t = threadIdx.x; t < 4 * T; t += nthreads) a.taps_out[t] = s.taps[t];
+        for (int t = threadIdx.x; t < 4 * T; t += NT) a.taps_out[t] = s.taps[t];
     }
 }
 
@@ -377,22 +449,28 @@ __global__ void k_cma_rebuild(RxDevState* st, int T, const int* flag) {
 }  // namespace
 
 int64_t lms_smem_bytes(int T, int Lb, int threads) {
-    const int XW = 2 * Lb + T;
+    const int XS = 2 * Lb + T;
     const int G = threads / (4 * T) > 1 ? threads / (4 * T) : 1;
-    return (int64_t)sizeof(float2) * (4 * T + 2 * XW + 4 * Lb + G * 4 * T + 2);
+    return (int64_t)sizeof(float2) * (4 * T + 4 * XS + 4 * Lb + G * 4 * T + 2);
+}
+
+template <int NT>
+static cudaError_t launch_lms_t(const LmsArgs& a, cudaStream_t s) {
+    const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
+    if (nseg <= 0) return cudaSuccess;
+    const size_t smem = (size_t)lms_smem_bytes(a.T, a.Lb, NT);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        cudaFuncSetAttribute(k_lms<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_lms<NT><<<(unsigned)nseg, NT, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
-    const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
-    if (nseg <= 0) return cudaSuccess;
-    const size_t smem = (size_t)lms_smem_bytes(a.T, a.Lb, threads);
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        cudaFuncSetAttribute(k_lms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
-    }
-    k_lms<<<(unsigned)nseg, threads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (threads >= 1024) return launch_lms_t<1024>(a, s);
+    return launch_lms_t<256>(a, s);
 }
 
 cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
