@@ -23,7 +23,8 @@ the textbook methods named beside each function, with these readings:
   taps (held fixed) over the second half of the acquisition window (an
   adapting CMA lets the output phase wander, which biases any FO estimate).
   Coarse: the peak of the 4th-power periodogram,
-  P[k] = sum_q |FFT_Nf(y_q^4)[k]|^2, Nf = the power of two >= 2x the window,
+  P[k] = sum_q |FFT_Nf(y_q^4)[k]|^2, Nf = the power of two >= 2x the window
+  (at least 512),
   first maximum, signed bin kappa -> w_c = 2 pi kappa / (4 Nf) rad/symbol.
   Fine: per block j of L_b symbols a_j = sum_q sum_n (y_q[n] e^{-j w_c n})^4,
   phi_j = arg a_j unwrapped in sequence (a step of more than pi is folded back
@@ -147,7 +148,7 @@ def foe_window(xbuf, h, n_acq, T, off):
 
 def foe_coarse(y: np.ndarray) -> float:
     nw = y.shape[1]
-    nf = 1
+    nf = 512
     while nf < 2 * nw:
         nf *= 2
     P = np.sum(np.abs(np.fft.fft(y ** 4, n=nf, axis=1)) ** 2, axis=0)

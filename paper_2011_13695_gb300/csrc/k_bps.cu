@@ -29,6 +29,19 @@ namespace {
 
 constexpr int BPS_THREADS = 256;
 
+// distance of one symbol to the nearest point after rotation, in level units
+__device__ __forceinline__ float bps_dist(float2 v, float c, float s, float hL, float invLm1, float Lm1) {
+    const float MAGIC = 12582912.0f;                  // 1.5 * 2^23: x + MAGIC - MAGIC = rint(x)
+    const float vI = fmaf(v.x, c, fmaf(v.y, s, hL));
+    const float vQ = fmaf(v.y, c, fmaf(-v.x, s, hL));
+    const float wI = __saturatef(vI * invLm1);
+    const float wQ = __saturatef(vQ * invLm1);
+    const float tI = fmaf(wI, Lm1, MAGIC) - MAGIC;
+    const float tQ = fmaf(wQ, Lm1, MAGIC) - MAGIC;
+    const float eI = vI - tI, eQ = vQ - tQ;
+    return fmaf(eI, eI, eQ * eQ);
+}
+
 template <int W, int GS>
 __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ y, int64_t ystride, int64_t N, int B,
                                                    float cI0, float hL, float invLm1, float Lm1, int LEN,
@@ -36,18 +49,17 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     constexpr int NSTRIP = BPS_THREADS / GS;
     constexpr int NW = GS / 32;
     extern __shared__ float2 ys[];                    // [NSTRIP][LEN + W]
-    __shared__ unsigned int wmin[NSTRIP][NW][W];
-    __shared__ unsigned char wb[NSTRIP][NW][W];
+    __shared__ unsigned int smin[NSTRIP][NW][W];      // per slot: warp minimum (bit pattern)
+    __shared__ unsigned int sbal[NSTRIP][NW][W];      // per slot: lanes holding it
     const int tid = threadIdx.x;
     const int sl = tid / GS;                          // strip within the CTA
     const int b = tid % GS;
     const int lane = tid & 31, wip = b >> 5;          // warp within the strip
     const int q = blockIdx.y;
-    const int64_t strip = (int64_t)blockIdx.x * NSTRIP + sl;
-    const int64_t s0 = strip * LEN;
+    const int64_t s0 = ((int64_t)blockIdx.x * NSTRIP + sl) * LEN;
     const int span = LEN + W;
     const float2* yq = y + (int64_t)q * ystride;
-    float2* yl = ys + sl * span;
+    const float2* yl = ys + sl * span;
 
     // stage y[s0 - W/2, s0 + LEN + W/2), zero outside [0, N)
     for (int t = tid; t < NSTRIP * span; t += BPS_THREADS) {
@@ -57,65 +69,46 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     }
     __syncthreads();
 
-    // rotation by e^{-j theta_b} folded with 1/(2a): r_I = y_I c + y_Q s, r_Q = y_Q c - y_I s
+    // rotation by e^{-j theta_b} folded with 1/(2a)
     float sn, cs;
     sincospif((float)((double)b / (double)B - 0.5) * 0.5f, &sn, &cs);
     const float c = cs * cI0, s = sn * cI0;
     const bool active = b < B;
-    const float MAGIC = 12582912.0f;                  // 1.5 * 2^23
+    // symbols of this strip outside [0, N) contribute nothing to any window
+    const int64_t g0 = s0 - W / 2;
+    const int ulo = (int)max((int64_t)0, min((int64_t)span, -g0));
+    const int uhi = (int)max((int64_t)0, min((int64_t)span, N - g0));
+    const bool interior = (ulo == 0 && uhi == span);
+    const int nc = LEN / W;
 
     float ring[W];
     float D = 0.0f;
-    const int nchunks = 1 + (LEN + W - 1) / W;
-    unsigned int keep = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
+    for (int ch = 0; ch <= nc; ++ch) {
 #pragma unroll
         for (int u = 0; u < W; ++u) {
-            const int li = ch * W + u;                // local index into yl (symbol s0 - W/2 + li)
-            float d = 0.0f;
-            if (li < span) {
-                const float2 v = yl[li];
-                const float vI = fmaf(v.x, c, fmaf(v.y, s, hL));
-                const float vQ = fmaf(v.y, c, fmaf(-v.x, s, hL));
-                const float wI = __saturatef(vI * invLm1);
-                const float wQ = __saturatef(vQ * invLm1);
-                const float tI = fmaf(wI, Lm1, MAGIC) - MAGIC;
-                const float tQ = fmaf(wQ, Lm1, MAGIC) - MAGIC;
-                const float eI = vI - tI, eQ = vQ - tQ;
-                d = fmaf(eI, eI, eQ * eQ);
-                const int64_t gi = s0 - W / 2 + li;
-                if (gi < 0 || gi >= N) d = 0.0f;
-            }
+            const int li = ch * W + u;
+            float d = bps_dist(yl[li], c, s, hL, invLm1, Lm1);     // li < (nc + 1) W = span
+            if (!interior && (li < ulo || li >= uhi)) d = 0.0f;
             if (ch == 0) {
                 ring[u] = d;
+                if (u == W - 1) {
+                    float t = 0.0f;
+#pragma unroll
+                    for (int r = 0; r < W; ++r) t += ring[r];
+                    D = t;
+                }
             } else {
                 D = (D + d) - ring[u];
                 ring[u] = d;
             }
-            // the window of symbol k = s0 - W/2 + li - W/2 + 1 is complete
-            const int kl = li - W + 1;                // local output index (symbol s0 + kl)
-            if (ch == 0 && u == W - 1) {
-                float t = 0.0f;
-#pragma unroll
-                for (int r = 0; r < W; ++r) t += ring[r];
-                D = t;
-            }
-            if (kl >= 0 && kl < LEN) {
+            // window of local output kl = li - W + 1 complete; its slot is (u + 1) % W
+            if (ch > 0 || u == W - 1) {
                 const unsigned int bits = active ? __float_as_uint(fmaxf(D, 0.0f)) : 0xffffffffu;
                 const unsigned int mn = __reduce_min_sync(0xffffffffu, bits);
                 const unsigned int bal = __ballot_sync(0xffffffffu, bits == mn);
-                const int first = __ffs(bal) - 1;
-                if (NW == 1) {
-                    if (lane == (kl & 31)) keep = (unsigned)first;
-                    if ((kl & 31) == 31 || kl == LEN - 1) {
-                        const int64_t k = s0 + (kl & ~31) + lane;
-                        if (lane <= (kl & 31) && k < N) bstar[(int64_t)q * bstride + k] = (uint8_t)keep;
-                    }
-                } else {
-                    if (lane == 0) {
-                        wmin[sl][wip][kl % W] = mn;
-                        wb[sl][wip][kl % W] = (unsigned char)(first + 32 * wip);
-                    }
+                if (lane == 0) {
+                    smin[sl][wip][(u + 1) % W] = mn;
+                    sbal[sl][wip][(u + 1) % W] = bal;
                 }
             }
         }
@@ -125,20 +118,17 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
             for (int r = 0; r < W; ++r) t += ring[r];
             D = t;
         }
-        if (NW > 1) {
-            __syncthreads();
-            // combine the two warps of each strip for the outputs of this chunk
-            const int kl0 = ch * W - W + 1;           // first local output of this chunk
-            for (int u = b; u < W; u += GS) {
-                const int kl = kl0 + u;
-                if (kl >= 0 && kl < LEN && s0 + kl < N) {
-                    const unsigned int m0 = wmin[sl][0][kl % W], m1 = wmin[sl][1][kl % W];
-                    const unsigned char r = (m1 < m0) ? wb[sl][1][kl % W] : wb[sl][0][kl % W];
-                    bstar[(int64_t)q * bstride + s0 + kl] = r;
-                }
+        __syncthreads();
+        for (int slot = b; slot < W; slot += GS) {
+            const int kl = slot == 0 ? ch * W : (ch - 1) * W + slot;
+            if (kl >= 0 && kl < LEN && s0 + kl < N) {
+                int r;
+                if (NW == 2 && smin[sl][NW - 1][slot] < smin[sl][0][slot]) r = 32 + __ffs(sbal[sl][NW - 1][slot]) - 1;
+                else r = __ffs(sbal[sl][0][slot]) - 1;
+                bstar[(int64_t)q * bstride + s0 + kl] = (uint8_t)r;
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
 }
 

@@ -24,7 +24,8 @@ template <int NT>
 struct LmsCtx {
     static constexpr int PF = (2 * (2 * 256 + RX_TMAX) + NT - 1) / NT;   // prefetch registers per thread
     float2* taps;    // [4][T]
-    float2* xs[2];   // staging double buffer, each [2][XS]
+    float2* xs0;     // staging double buffer, each [2][XS]
+    float2* xs1;
     float2* ys;      // [2][Lb]
     float2* es;      // [2][Lb]
     float2* part;    // [G][4T]
@@ -59,7 +60,7 @@ __device__ __forceinline__ void lms_commit(const LmsArgs& a, LmsCtx<NT>& s, int 
     const int c = (a.T - 1) / 2;
     const int XW = 2 * L + a.T - 1;
     const int64_t i0 = a.off + 2 * n0 - c;
-    float2* xs = s.xs[buf];
+    float2* xs = buf ? s.xs1 : s.xs0;
 #pragma unroll
     for (int r = 0; r < LmsCtx<NT>::PF; ++r) {
         const int t = threadIdx.x + r * NT;
@@ -90,17 +91,20 @@ __device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const
             const bool valid = o < 2 * L;
             const int q = valid ? (o >= L ? 1 : 0) : 0, n = valid ? o - q * L : 0;
             float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-            int u = valid ? j : T2;
-            for (; u + P < T2; u += 2 * P) {
-                const int p0 = u >= T ? 1 : 0, k0 = u - p0 * T;
-                const int u1 = u + P;
-                const int p1 = u1 >= T ? 1 : 0, k1 = u1 - p1 * T;
-                acc0 = cmac(acc0, s.taps[(q * 2 + p0) * T + k0], xs[p0 * s.XS + 2 * n + T - 1 - k0]);
-                acc1 = cmac(acc1, s.taps[(q * 2 + p1) * T + k1], xs[p1 * s.XS + 2 * n + T - 1 - k1]);
-            }
-            if (u < T2) {
-                const int p0 = u >= T ? 1 : 0, k0 = u - p0 * T;
-                acc0 = cmac(acc0, s.taps[(q * 2 + p0) * T + k0], xs[p0 * s.XS + 2 * n + T - 1 - k0]);
+            // lane j of the group takes polarisation p and a contiguous run of taps
+            const int p_first = P == 1 ? 0 : (j & 1), p_last = P == 1 ? 1 : (j & 1);
+            const int nk = P == 1 ? 1 : P / 2, kc = (T + nk - 1) / nk;
+            const int klo = P == 1 ? 0 : (j >> 1) * kc;
+            const int khi = valid ? min(T, klo + kc) : klo;
+            for (int p = p_first; p <= p_last; ++p) {
+                const float2* hq = s.taps + (q * 2 + p) * T;
+                const float2* xp = xs + p * s.XS + 2 * n + T - 1;
+                int k = klo;
+                for (; k + 1 < khi; k += 2) {
+                    acc0 = cmac(acc0, hq[k], xp[-k]);
+                    acc1 = cmac(acc1, hq[k + 1], xp[-k - 1]);
+                }
+                if (k < khi) acc0 = cmac(acc0, hq[k], xp[-k]);
             }
             float2 acc = cadd(acc0, acc1);
             for (int w = 1; w < P; w <<= 1) {
@@ -181,9 +185,9 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
     while (P < 8 && 2 * P * 2 * Lb <= NT) P *= 2;
     s.P = P;
     s.taps = smem;
-    s.xs[0] = s.taps + 4 * T;
-    s.xs[1] = s.xs[0] + 2 * s.XS;
-    s.ys = s.xs[1] + 2 * s.XS;
+    s.xs0 = s.taps + 4 * T;
+    s.xs1 = s.xs0 + 2 * s.XS;
+    s.ys = s.xs1 + 2 * s.XS;
     s.es = s.ys + 2 * Lb;
     s.part = s.es + 2 * Lb;
     s.rot = s.part + s.G * 4 * T;
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
             blk(b + 1, nn0, nL);
             lms_prefetch(a, s, nn0, nL);
         }
-        lms_block<NT>(a, s, s.xs[b & 1], n0, L, b >= nwarm && a.y != nullptr, qm);
+        lms_block<NT>(a, s, (b & 1) ? s.xs1 : s.xs0, n0, L, b >= nwarm && a.y != nullptr, qm);
         if (b + 1 < nblk) lms_commit(a, s, (b + 1) & 1, nn0, nL, inc);
         __syncthreads();
     }
@@ -371,56 +375,47 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
     }
 }
 
-// max over |d| <= c of |rho_d| between the two CMA outputs (second half of y_acq)
-__global__ void k_cma_check(const float2* __restrict__ yacq, int64_t nacq, int T, RxDevState* st, int* flag,
-                            int pass) {
+// max over |d| <= c of |rho_d| between the two CMA outputs (second half of
+// y_acq): one warp per lag, FP32 lane sums, warp-shuffle combine (a threshold
+// test at 0.5 needs no more precision).
+__global__ void k_cma_check(const float2* __restrict__ yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st,
+                            int* flag, int pass) {
     if (pass == 1 && *flag == 0) return;
     const int64_t h0 = nacq / 2;
-    const int64_t L = nacq - h0;
+    const int L = (int)(nacq - h0);
     const float2* y0 = yacq + h0;
-    const float2* y1 = yacq + nacq + h0;
+    const float2* y1 = yacq + ystride + h0;
     const int maxlag = (T - 1) / 2;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    __shared__ double red[32][2];
-    __shared__ double s_den;
-    // energies
-    double e0 = 0.0, e1 = 0.0;
-    for (int64_t n = tid; n < L; n += nthr) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    __shared__ float s_r[64];
+    __shared__ float s_e[32][2];
+    float e0 = 0.0f, e1 = 0.0f;
+    for (int n = tid; n < L; n += blockDim.x) {
         e0 += cabs2(y0[n]);
         e1 += cabs2(y1[n]);
     }
-    e0 = warp_sum_d(e0);
-    e1 = warp_sum_d(e1);
-    if ((tid & 31) == 0) { red[tid >> 5][0] = e0; red[tid >> 5][1] = e1; }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (nthr >> 5); ++w) { a += red[w][0]; b += red[w][1]; }
-        s_den = sqrt(a * b);
-    }
-    __syncthreads();
-    double best = 0.0;
-    for (int d = -maxlag; d <= maxlag; ++d) {
-        const int64_t a0 = d < 0 ? -d : 0, a1 = L - (d > 0 ? d : 0);
-        double sx = 0.0, sy = 0.0;
-        for (int64_t n = a0 + tid; n < a1; n += nthr) {
+    e0 = warp_sum(e0);
+    e1 = warp_sum(e1);
+    if (lane == 0) { s_e[w][0] = e0; s_e[w][1] = e1; }
+    for (int d = w - maxlag; d <= maxlag; d += (int)(blockDim.x >> 5)) {
+        const int a0 = d < 0 ? -d : 0, a1 = L - (d > 0 ? d : 0);
+        float sx = 0.0f, sy = 0.0f;
+        for (int n = a0 + lane; n < a1; n += 32) {
             const float2 v = cmulc(y0[n], y1[n + d]);
             sx += v.x;
             sy += v.y;
         }
-        sx = warp_sum_d(sx);
-        sy = warp_sum_d(sy);
-        __syncthreads();
-        if ((tid & 31) == 0) { red[tid >> 5][0] = sx; red[tid >> 5][1] = sy; }
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < (nthr >> 5); ++w) { a += red[w][0]; b += red[w][1]; }
-            const double r = s_den > 0.0 ? sqrt(a * a + b * b) / s_den : 0.0;
-            if (r > best) best = r;
-        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) s_r[d + maxlag] = sqrtf(sx * sx + sy * sy);
     }
+    __syncthreads();
     if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += s_e[k][0]; b += s_e[k][1]; }
+        const double den = sqrt(a * b);
+        double best = 0.0;
+        for (int d = 0; d <= 2 * maxlag; ++d) best = fmax(best, den > 0.0 ? s_r[d] / den : 0.0);
         if (pass == 0) {
             *flag = best > 0.5 ? 1 : 0;
             st->cma_rho = (float)best;
@@ -511,9 +506,9 @@ cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw
     return cudaGetLastError();
 }
 
-cudaError_t launch_cma_check(const float2* yacq, int64_t nacq, int T, RxDevState* st, int* flag, int pass,
-                             cudaStream_t s) {
-    k_cma_check<<<1, 1024, 0, s>>>(yacq, nacq, T, st, flag, pass);
+cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st, int* flag,
+                             int pass, cudaStream_t s) {
+    k_cma_check<<<1, 1024, 0, s>>>(yacq, ystride, nacq, T, st, flag, pass);
     return cudaGetLastError();
 }
 

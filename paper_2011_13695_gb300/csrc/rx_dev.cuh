@@ -115,9 +115,9 @@ __device__ __forceinline__ uint32_t msb_first_to_stream(uint32_t v, int m) {
 __device__ __forceinline__ float2 nco_conj(long long inc, long long g) {
     unsigned long long ph = (unsigned long long)inc * (unsigned long long)g;
     int top = (int)(ph >> 32);                       // [-2^31, 2^31) = [-0.5, 0.5) turns
-    float ang = (float)top * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    float half_turns = (float)top * 4.656612873077393e-10f;   // 2 * top / 2^32, in [-1, 1)
     float s, c;
-    __sincosf(ang, &s, &c);
+    sincospif(half_turns, &s, &c);
     return make_float2(c, -s);
 }
 

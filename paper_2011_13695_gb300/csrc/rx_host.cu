@@ -309,6 +309,11 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
     const int Lb = h->Lb, T = h->T;
     const int64_t n_cma = std::min<int64_t>(c.cma_blocks, N / Lb);
     const int64_t n_dd = n_cma > 0 ? std::min<int64_t>(c.dd_acq_blocks, N / Lb) : 0;
+    // acquisition window of this frame (shorter than the configured one for short frames)
+    const int64_t nacq_e = n_cma * Lb, nw_e = nacq_e - nacq_e / 2;
+    int nf_e = 512;
+    while (nf_e < 2 * nw_e) nf_e *= 2;
+    const int kf_e = ilog2(nf_e);
     const int64_t obase = stream_mode ? h->hist : 0;
     const int64_t off = stream_mode ? h->hist - 2 * h->d4 : 0;
     const int64_t xlen = obase + S;
@@ -367,20 +372,20 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
                 a.y = h->yacq;
                 a.ystride = h->nacq;
                 RX_CK(launch_lms(a, 1024, s));
-                RX_CK(launch_cma_check(h->yacq, h->nacq, T, st, h->flag, 0, s));
+                RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 0, s));
                 RX_CK(launch_cma_rebuild(st, T, h->flag, s));
                 LmsArgs a2 = a;
                 a2.taps_in = st->taps_init;
                 a2.run_if = h->flag;
                 RX_CK(launch_lms(a2, 1024, s));
-                RX_CK(launch_cma_check(h->yacq, h->nacq, T, st, h->flag, 1, s));
+                RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 1, s));
                 nl += 5;
             }
             {
                 StageScope sc(h, ST_FOE, s);
-                RX_CK(launch_foe_window(h->cdc, h->cap, xlen, off, T, h->nacq / 2, h->nw, st->taps_cma, h->yfoe, s));
-                RX_CK(launch_foe_pgram(h->yfoe, h->nw, h->kf, h->tw, h->pgram, s));
-                RX_CK(launch_foe_fine(h->pgram, h->kf, h->yfoe, h->nw, Lb, c.symbol_rate_hz, h->fs, c.fo_grid_hz, T, st,
+                RX_CK(launch_foe_window(h->cdc, h->cap, xlen, off, T, nacq_e / 2, nw_e, st->taps_cma, h->yfoe, s));
+                RX_CK(launch_foe_pgram(h->yfoe, nw_e, kf_e, h->tw, h->pgram, s));
+                RX_CK(launch_foe_fine(h->pgram, kf_e, h->yfoe, nw_e, Lb, c.symbol_rate_hz, h->fs, c.fo_grid_hz, T, st,
                                       s));
                 nl += 3;
             }
@@ -624,13 +629,15 @@ rx_status rx_state_get(rx_handle* h, void* blob, size_t bytes) {
 
 rx_status rx_state_set(rx_handle* h, const void* blob, size_t bytes) {
     size_t need = 0;
-    if (rx_state_size(h, &need) != RX_OK || !blob || bytes != need) return RX_EINVAL;
+    if (rx_state_size(h, &need) != RX_OK || !blob || bytes < sizeof(BlobHeader)) return RX_EINVAL;
     const char* p = (const char*)blob;
     BlobHeader hd;
     std::memcpy(&hd, p, sizeof(hd));
+    // a blob of another configuration is a state error, a truncated buffer an argument error
     if (hd.magic != 0x52584254u || hd.bytes != need || hd.T != h->T || hd.hop != h->hop || hd.hist != h->hist ||
         hd.symbol_rate != h->cfg.symbol_rate_hz)
         return RX_ESTATE;
+    if (bytes != need) return RX_EINVAL;
     if (h->last) RX_CK(cudaStreamSynchronize(h->last));
     p += sizeof(hd);
     RX_CK(cudaMemcpy(h->st, p, sizeof(RxDevState), cudaMemcpyHostToDevice));

@@ -59,8 +59,8 @@ cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, in
 cudaError_t launch_foe_pgram(const float2* yw, int64_t nw, int kf, const float2* tw, float* P, cudaStream_t s);
 cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw, int Lb, double rs, double fs,
                             double grid, int T, RxDevState* st, cudaStream_t s);
-cudaError_t launch_cma_check(const float2* yacq, int64_t nacq, int T, RxDevState* st, int* flag_dev, int pass,
-                             cudaStream_t s);
+cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st,
+                             int* flag_dev, int pass, cudaStream_t s);
 cudaError_t launch_cma_rebuild(RxDevState* st, int T, const int* flag_dev, cudaStream_t s);
 
 cudaError_t launch_bps(const float2* y, int64_t ystride, int64_t N, int B, int W, int m, uint8_t* bstar,

@@ -54,7 +54,29 @@ def host_recount(g, o_sync, ref_words, m, n, lo, hi, lat=0):
     return errs
 
 
-def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True):
+def check_bstar(g, r, cfg, head=0):
+    """b* may differ only where the oracle's FP64 window sums of the two choices nearly tie.
+
+    Both picks are then correct (the GPU's sums carry FP32 rounding of y and of
+    the distances, ~1e-6 relative); the count of such symbols is bounded.
+    Returns the mask of symbols where b* agrees.
+    """
+    from oracle import bps as obps
+    N, B, W = g["n"], cfg.bps_phases, cfg.bps_window
+    agree = g["bstar"] == r.bstar
+    agree[:, :head] = True
+    bad = np.argwhere(~agree)
+    for q, k in bad:
+        lo, hi = max(0, k - W // 2), min(N, k - W // 2 + W)
+        d = obps.distances(r.y[q, lo:hi], cfg.bits_per_sym, B).sum(axis=0)
+        bg, bo = int(g["bstar"][q, k]), int(r.bstar[q, k])
+        assert abs(d[bg] - d[bo]) <= 1e-4 * d[bo], f"b* at ({q},{k}): {bg} vs {bo} is not a near-tie"
+    assert len(bad) <= max(2, 5e-5 * 2 * N), f"b* differs on {len(bad)} symbols"
+    return agree
+
+
+def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, head=0):
+    """head: leading symbols of a stream's first frame that only carry the start-up transient."""
     N = g["n"]
     m = cfg.bits_per_sym
     if check_cdc:
@@ -64,12 +86,14 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True):
         pytest.skip("oracle FO estimate within 1 % of a rounding boundary: two correct codes")
     assert g["stats"]["fo_code"] == r.fo_code
     assert rel_rms(g["y"], r.y) < tol_y
-    nb = int(np.sum(g["bstar"] != r.bstar))
-    assert nb <= allowed(2 * N), f"b* differs on {nb} symbols"
-    assert rel_rms(g["z"], r.z) < tol_y
+    agree = check_bstar(g, r, cfg, head) & (g["m"] == r.m)
+    assert np.mean(agree) > 1 - 1e-3
+    assert rel_rms(g["z"][agree], r.z[agree]) < tol_y
     gl = oqam.decide_levels(g["z"], m)
     ol = oqam.decide_levels(r.z, m)
-    ndiff = int(np.sum((gl[0] != ol[0]) | (gl[1] != ol[1])))
+    dmask = (gl[0] != ol[0]) | (gl[1] != ol[1])
+    dmask[:, :head] = False
+    ndiff = int(np.sum(dmask))
     assert ndiff <= allowed(2 * N), f"decisions differ on {ndiff} symbols"
     # output bits: the GPU's bits are the demap of its own z (with its quarter turns)
     if ref_words is not None and r.sync is not None:
@@ -130,7 +154,7 @@ def test_ragged_and_tiny_frames(n_sym):
     g, r, cfg, fr = run_pair(w, 4, n_sym=n_sym)
     assert rel_rms(g["cdc"], r.cdc) < 1e-5
     assert rel_rms(g["y"], r.y) < 1e-4
-    assert int(np.sum(g["bstar"] != r.bstar)) <= allowed(2 * n_sym)
+    check_bstar(g, r, cfg)
     want_bits = oqam.pack_words(odec.demap_output(g["z"], r.sync, cfg.bits_per_sym))
     assert np.array_equal(g["bits"], want_bits)
     if r.sync is None:
@@ -157,7 +181,9 @@ def test_stream_of_frames_matches_the_oracle_stream():
     orx = OracleRx(cfg, stream=True)
     for f in range(3):
         r = orx.process(gs[f]["oracle_input"], refs[f])
-        check_frame(gs[f], r, cfg, refs[f], lat=cfg.stream_latency)
+        # the first frame starts with the receiver's latency worth of start-up transient
+        head = cfg.stream_latency + cfg.bps_window if f == 0 else 0
+        check_frame(gs[f], r, cfg, refs[f], lat=cfg.stream_latency, head=head)
 
 
 def test_nonfinite_input_sets_the_error_word():
