@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
+    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch"],
+                    help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
+                         "batch: 16 channels in one graph launch")
+    ap.add_argument("--fmt", default="i8", choices=["i8", "f16"], help="input format of the stream workload")
     return ap.parse_args()
 
 
@@ -333,10 +337,119 @@ def our_arm(args) -> None:
         dist.destroy_process_group()
 
 
+def stream_arm(args) -> None:
+    """64QAM 48 GBd stream: 64 frames of 2^18 symbols/pol, int8 (or FP16) ADC input, carried state."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import Receiver
+    from synth import generate, workload
+    from synth.channel import pack_bits, quantise_int8, to_fp16
+
+    w = workload("dp-64qam-48gbd-stream")
+    F, n = w["n_frames"], w["frame_sym"]
+    fr = generate(w["link"], SEED)
+    S = 2 * n
+    if args.fmt == "i8":
+        codes, delta = quantise_int8(fr.samples)
+        data, fmt, scale, esz = codes, rx.RX_IN_I8, float(delta[0]), 2
+    else:
+        data, fmt, scale, esz = to_fp16(fr.samples).view(np.int16), rx.RX_IN_F16, 1.0, 4
+    xs = [torch.from_numpy(np.ascontiguousarray(data[:, f * S:(f + 1) * S])).cuda() for f in range(F)]
+    m = w["link"].bits_per_sym
+    refs = [torch.from_numpy(pack_bits(fr.bits[:, f * n * m:(f + 1) * n * m]).astype(np.uint32).view(np.int32)).cuda()
+            for f in range(F)]
+    stream = torch.cuda.current_stream()
+    times = []
+    for rep in range(args.warmup + args.steps):
+        rcv = Receiver(w["rx"], n, input_format=fmt, input_scale=scale, streaming=True)
+        out = torch.zeros(2 * rcv.words(n), dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f in range(F):
+            rcv.process(xs[f], n, refs[f], out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+        st = rcv.stats()
+        rcv.close()
+    t = sum(times) / len(times)
+    bits = 2 * m * n * F
+    print(json.dumps({"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+                      "higher_is_better": True, "dtype": f"{args.fmt} in, f32", "data": "synthetic",
+                      "config": {"workload": "dp-64qam-48gbd-stream", "frames": F, "symbols_per_frame": n,
+                                 "input": args.fmt},
+                      "ber": st["ber"], "evm": st["evm"], "q_db": st["q_db"], "error_word": st["error_word"]}))
+
+
+def batch_arm(args) -> None:
+    """16 seeded channels (16..64 GBd, QPSK/16QAM/64QAM, 2^16..2^20 symbols) in one graph launch."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import config_from
+    from synth import generate
+    from synth.workloads import batch_channels
+
+    chans = batch_channels(42)
+    xs, refs, outs, cfgs, n_sym, bits = [], [], [], [], [], 0
+    for ch in chans:
+        fr = generate(ch["link"], ch["seed"])
+        N, m = ch["link"].n_sym, ch["link"].bits_per_sym
+        xs.append(torch.from_numpy(np.ascontiguousarray(fr.samples.astype(np.complex64)).view(np.float32)).cuda())
+        refs.append(torch.from_numpy(fr.ref_words.astype(np.uint32).view(np.int32)).cuda())
+        outs.append(torch.zeros(2 * ((N * m + 31) // 32), dtype=torch.int32, device="cuda"))
+        cfgs.append(config_from(ch["rx"], N))
+        n_sym.append(N)
+        bits += 2 * m * N
+    t0 = time.perf_counter()
+    b = rx.rx_batch_create(cfgs)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    args_ = ([t.data_ptr() for t in xs], n_sym, [t.data_ptr() for t in refs], [t.data_ptr() for t in outs],
+             stream.cuda_stream)
+    for _ in range(args.warmup):
+        rx.rx_batch_process(b, *args_)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rx.rx_batch_process(b, *args_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = sum(ms) / len(ms)
+    tuned = [(rx.rx_batch_config(b, i).fft_size, rx.rx_batch_config(b, i).lms_threads) for i in range(len(chans))]
+    print(json.dumps({"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batch16-seed42", "channels": len(chans), "symbols": sum(n_sym),
+                                 "tuned_fft_and_lms_threads": tuned, "tune_s": round(tune_s, 2),
+                                 "l2": "flushed between timed steps"},
+                      "graph_launches_per_step": 1}))
+    rx.rx_batch_destroy(b)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "stream":
+        stream_arm(args)
+    elif args.workload == "batch":
+        batch_arm(args)
     else:
         our_arm(args)
 

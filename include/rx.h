@@ -92,6 +92,7 @@ typedef struct rx_config {
     float input_scale;          /* multiplies every input value (e.g. the int8 step) */
     int32_t streaming;          /* 0: each call is one frame; 1: calls are frames of one stream */
     int64_t max_symbols;        /* largest n_sym per call (sizes the workspace) */
+    int32_t lms_threads;        /* threads per CTA of the segmented DD-LMS: 128/256/512/1024; 0 = 256 */
 } rx_config;
 
 typedef struct rx_stats_t {
@@ -205,6 +206,38 @@ rx_status rx_stage_times(rx_handle* h, double* ms, int64_t* launches, int32_t n)
 
 /* Kernels launched by this handle since creation (all stages). */
 uint64_t rx_launch_count(rx_handle* h);
+
+/*
+ * Batched channels. The paper keeps its GPU busy with one stream per buffer
+ * and events between dependent kernels (Sec. II-C, Sec. III); a batch runs
+ * many independent channels (single frames, each with its own format,
+ * symbol rate, taps, dispersion and length) as ONE CUDA graph launch.
+ *
+ * rx_batch_create: n configurations (streaming must be 0). A channel with
+ * fft_size == 0 gets the fastest N_fft in 512..8192 whose N/4 covers its
+ * dispersion memory, and lms_threads == 0 the fastest DD-LMS CTA size, both
+ * timed on the device at create time and cached per channel shape for the
+ * process. Allocates every handle's workspace; RX_EINVAL on a bad config.
+ * rx_batch_config returns channel i's configuration as tuned.
+ */
+typedef struct rx_batch rx_batch;
+rx_status rx_batch_create(const rx_config* cfgs, int32_t n, rx_batch** out);
+rx_status rx_batch_config(rx_batch* b, int32_t i, rx_config* out);
+/* the handle of channel i (for rx_get_buffer); owned by the batch */
+rx_handle* rx_batch_handle(rx_batch* b, int32_t i);
+/*
+ * rx_batch_process: d_in[i], n_sym[i], d_ref[i] (array or entries nullable),
+ * d_out[i] (array or entries nullable) as for rx_process, per channel. The
+ * first call with a given set of buffers and stream captures every channel's
+ * chain (each on its own forked stream) into one graph; every call then
+ * launches that graph once on `stream`. Asynchronous.
+ */
+rx_status rx_batch_process(rx_batch* b, const void* const* d_in, const int64_t* n_sym, const uint32_t* const* d_ref,
+                           uint32_t* const* d_out, rx_stream_t stream);
+/* rx_batch_stats: waits for the last batch launch, then rx_stats of channel i */
+rx_status rx_batch_stats(rx_batch* b, int32_t i, rx_stats_t* out);
+uint64_t rx_batch_launch_count(rx_batch* b);
+void rx_batch_destroy(rx_batch* b);
 
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);

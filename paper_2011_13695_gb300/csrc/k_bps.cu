@@ -42,6 +42,14 @@ __device__ __forceinline__ float bps_dist(float2 v, float c, float s, float hL, 
     return fmaf(eI, eI, eQ * eQ);
 }
 
+// publish one window's warp minimum and the lanes holding it
+__device__ __forceinline__ void bps_publish(float D, uint2* slot, int lane) {
+    const unsigned int bits = __float_as_uint(D);
+    const unsigned int mn = __reduce_min_sync(0xffffffffu, bits);
+    const unsigned int bal = __ballot_sync(0xffffffffu, bits == mn);
+    if (lane == 0) *slot = make_uint2(mn, bal);
+}
+
 template <int W, int GS>
 __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ y, int64_t ystride, int64_t N, int B,
                                                    float cI0, float hL, float invLm1, float Lm1, int LEN,
@@ -49,8 +57,7 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     constexpr int NSTRIP = BPS_THREADS / GS;
     constexpr int NW = GS / 32;
     extern __shared__ float2 ys[];                    // [NSTRIP][LEN + W]
-    __shared__ unsigned int smin[NSTRIP][NW][W];      // per slot: warp minimum (bit pattern)
-    __shared__ unsigned int sbal[NSTRIP][NW][W];      // per slot: lanes holding it
+    __shared__ uint2 slots[NSTRIP][NW][W];            // per output slot: (warp minimum bits, ballot of its lanes)
     const int tid = threadIdx.x;
     const int sl = tid / GS;                          // strip within the CTA
     const int b = tid % GS;
@@ -61,59 +68,45 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     const float2* yq = y + (int64_t)q * ystride;
     const float2* yl = ys + sl * span;
 
-    // stage y[s0 - W/2, s0 + LEN + W/2), zero outside [0, N)
+    // stage y[s0 - W/2, s0 + LEN + W/2); symbols outside [0, N) are NaN, whose
+    // distance fmaxf(NaN, 0) turns into 0: they contribute nothing to any window
+    const float qnan = __int_as_float(0x7fc00000);
     for (int t = tid; t < NSTRIP * span; t += BPS_THREADS) {
         const int st = t / span, u = t - st * span;
         const int64_t i = ((int64_t)blockIdx.x * NSTRIP + st) * LEN - W / 2 + u;
-        ys[st * span + u] = (i >= 0 && i < N) ? yq[i] : make_float2(0.0f, 0.0f);
+        ys[st * span + u] = (i >= 0 && i < N) ? yq[i] : make_float2(qnan, qnan);
     }
     __syncthreads();
 
-    // rotation by e^{-j theta_b} folded with 1/(2a)
+    // rotation by e^{-j theta_b} folded with 1/(2a); phases b >= B never win (penalty)
     float sn, cs;
     sincospif((float)((double)b / (double)B - 0.5) * 0.5f, &sn, &cs);
     const float c = cs * cI0, s = sn * cI0;
-    const bool active = b < B;
-    // symbols of this strip outside [0, N) contribute nothing to any window
-    const int64_t g0 = s0 - W / 2;
-    const int ulo = (int)max((int64_t)0, min((int64_t)span, -g0));
-    const int uhi = (int)max((int64_t)0, min((int64_t)span, N - g0));
-    const bool interior = (ulo == 0 && uhi == span);
+    const float pen = b < B ? 0.0f : 3.0e38f;
     const int nc = LEN / W;
+    uint2* myslots = &slots[sl][wip][0];
 
     float ring[W];
-    float D = 0.0f;
+    float D = pen;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        ring[u] = fmaxf(bps_dist(yl[u], c, s, hL, invLm1, Lm1), 0.0f);
+        D += ring[u];
+    }
+    bps_publish(D, &myslots[0], lane);                // window of local output 0
     for (int ch = 0; ch <= nc; ++ch) {
+        if (ch > 0) {
 #pragma unroll
-        for (int u = 0; u < W; ++u) {
-            const int li = ch * W + u;
-            float d = bps_dist(yl[li], c, s, hL, invLm1, Lm1);     // li < (nc + 1) W = span
-            if (!interior && (li < ulo || li >= uhi)) d = 0.0f;
-            if (ch == 0) {
-                ring[u] = d;
-                if (u == W - 1) {
-                    float t = 0.0f;
-#pragma unroll
-                    for (int r = 0; r < W; ++r) t += ring[r];
-                    D = t;
-                }
-            } else {
+            for (int u = 0; u < W; ++u) {
+                const float d = fmaxf(bps_dist(yl[ch * W + u], c, s, hL, invLm1, Lm1), 0.0f);
                 D = (D + d) - ring[u];
                 ring[u] = d;
+                // window of local output (ch - 1) W + u + 1 is complete; its slot is (u + 1) % W
+                bps_publish(fmaxf(D, 0.0f), &myslots[(u + 1) % W], lane);
+                // keep the compiler from hoisting the whole chunk's loads (register pressure)
+                if ((u & 7) == 7) asm volatile("" ::: "memory");
             }
-            // window of local output kl = li - W + 1 complete; its slot is (u + 1) % W
-            if (ch > 0 || u == W - 1) {
-                const unsigned int bits = active ? __float_as_uint(fmaxf(D, 0.0f)) : 0xffffffffu;
-                const unsigned int mn = __reduce_min_sync(0xffffffffu, bits);
-                const unsigned int bal = __ballot_sync(0xffffffffu, bits == mn);
-                if (lane == 0) {
-                    smin[sl][wip][(u + 1) % W] = mn;
-                    sbal[sl][wip][(u + 1) % W] = bal;
-                }
-            }
-        }
-        if (ch > 0) {                                 // re-form the sum directly from the ring
-            float t = 0.0f;
+            float t = pen;                            // re-form the sum directly from the ring
 #pragma unroll
             for (int r = 0; r < W; ++r) t += ring[r];
             D = t;
@@ -122,9 +115,12 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
         for (int slot = b; slot < W; slot += GS) {
             const int kl = slot == 0 ? ch * W : (ch - 1) * W + slot;
             if (kl >= 0 && kl < LEN && s0 + kl < N) {
-                int r;
-                if (NW == 2 && smin[sl][NW - 1][slot] < smin[sl][0][slot]) r = 32 + __ffs(sbal[sl][NW - 1][slot]) - 1;
-                else r = __ffs(sbal[sl][0][slot]) - 1;
+                const uint2 w0 = slots[sl][0][slot];
+                int r = __ffs(w0.y) - 1;
+                if (NW == 2) {
+                    const uint2 w1 = slots[sl][NW - 1][slot];
+                    if (w1.x < w0.x) r = 32 + __ffs(w1.y) - 1;
+                }
                 bstar[(int64_t)q * bstride + s0 + kl] = (uint8_t)r;
             }
         }

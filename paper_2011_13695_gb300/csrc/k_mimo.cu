@@ -7,14 +7,19 @@
 //   y_q[n] = sum_p sum_k h_qp[k] x_p[2n + c - k],   c = (T-1)/2
 //   h_qp[k] += mu * sum_{n in block} e_q[n] conj(x_p[2n + c - k])
 // with e = y (R2 - |y|^2) (CMA, Godard) or e = dec(y e^{-j psi}) e^{j psi} - y
-// (DD, psi = arg(-sum y^4)/4 per block). The serial recursion is broken by a
-// fixed segment schedule: one CTA per segment of seg_blocks blocks, started
-// from common taps and warmed up on the warmup_blocks blocks before it.
+// (DD, psi = arg(-sum y^4)/4 per block). The two output rows q are
+// independent recursions (each has its own taps, error and phase), so one CTA
+// runs one row of one segment: grid (segments, 2). The serial recursion along
+// a row is broken by a fixed segment schedule: segments of seg_blocks blocks,
+// started from common taps and warmed up on the warmup_blocks blocks before.
 // Per block a CTA stages the block's input window (both polarisations, FO
-// derotation by the 64-bit phase accumulator fused into the load) in shared
-// memory, computes the outputs, the block phase (a fixed-order reduction, so
-// results do not depend on scheduling), the errors and the tap gradients
-// (fixed-order partial sums), then updates the taps it keeps in shared memory.
+// derotation by the 64-bit phase accumulator fused into the load, the next
+// window prefetched into registers while the current one is used) in shared
+// memory, computes the outputs (P lanes per output, xor-shuffle combine), the
+// block phase (fixed-order reduction, so results do not depend on
+// scheduling), the errors and the tap gradients (fixed-order partial sums),
+// then updates the row's taps in shared memory. All per-thread index
+// arithmetic is done once per kernel.
 #include "rx_fft.cuh"
 #include "rx_kernels.h"
 
@@ -23,22 +28,26 @@ namespace {
 template <int NT>
 struct LmsCtx {
     static constexpr int PF = (2 * (2 * 256 + RX_TMAX) + NT - 1) / NT;   // prefetch registers per thread
-    float2* taps;    // [4][T]
+    float2* taps;    // row q: [p][k], 2T
     float2* xs0;     // staging double buffer, each [2][XS]
     float2* xs1;
-    float2* ys;      // [2][Lb]
-    float2* es;      // [2][Lb]
-    float2* part;    // [G][4T]
-    float2* rot;     // [2] e^{-j psi}
-    int XS, G, P;
-    float2 pf[PF];   // next window, raw
+    float2* ys;      // [Lb]
+    float2* es;      // [Lb]
+    float2* part;    // [G][2T]
+    float2* rot;     // e^{-j psi}
+    int XS, G, logP, logR;
+    // output lanes: polarisation-0 taps [ka0, ka1), polarisation-1 taps [kb0, kb1)
+    int ka0, ka1, kb0, kb1;
+    // gradient thread: tap index (-1: idle), group, staging offset of its tap
+    int gt, gg, gx;
+    float2 pf[PF];
 };
 
 // Window of the block starting at symbol n0 with L symbols: buffer indices
 // i = off + 2 n0 - c + j, j < 2L + T - 1 (zero outside [0, xlen)).
 template <int NT>
 __device__ __forceinline__ void lms_prefetch(const LmsArgs& a, LmsCtx<NT>& s, int64_t n0, int L) {
-    const int c = (a.T - 1) / 2;
+    const int c = (a.T - 1) >> 1;
     const int XW = 2 * L + a.T - 1;
     const int64_t i0 = a.off + 2 * n0 - c;
 #pragma unroll
@@ -55,121 +64,120 @@ __device__ __forceinline__ void lms_prefetch(const LmsArgs& a, LmsCtx<NT>& s, in
 }
 
 template <int NT>
-__device__ __forceinline__ void lms_commit(const LmsArgs& a, LmsCtx<NT>& s, int buf, int64_t n0, int L,
+__device__ __forceinline__ void lms_commit(const LmsArgs& a, LmsCtx<NT>& s, float2* xs, int64_t n0, int L,
                                            long long inc) {
-    const int c = (a.T - 1) / 2;
+    const int c = (a.T - 1) >> 1;
     const int XW = 2 * L + a.T - 1;
-    const int64_t i0 = a.off + 2 * n0 - c;
-    float2* xs = buf ? s.xs1 : s.xs0;
+    const long long g0 = a.g0 + a.off + 2 * n0 - c;
 #pragma unroll
     for (int r = 0; r < LmsCtx<NT>::PF; ++r) {
         const int t = threadIdx.x + r * NT;
         if (t < 2 * XW) {
             const int p = t >= XW ? 1 : 0, jj = t - p * XW;
             float2 v = s.pf[r];
-            if (inc) v = cmul(v, nco_conj(inc, a.g0 + i0 + jj));
+            if (inc) v = cmul(v, nco_conj(inc, g0 + jj));
             xs[p * s.XS + jj] = v;
         }
     }
 }
 
-// One block update. Outputs: P lanes per output split the 2T terms and combine
-// with xor-shuffles. Gradient: G thread groups take every G-th symbol of the
-// block and their partial sums are added in a fixed order.
+// one block of row q: outputs, (DD) phase and errors, gradient, tap update
 template <int NT>
-__device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const float2* xs, int64_t n0, int L,
-                                          bool store, const Qam& qm) {
+__device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const float2* __restrict__ xs,
+                                          int64_t n0, int L, bool store, const Qam& qm, int q) {
     const int tid = threadIdx.x;
-    const int T = a.T, T2 = 2 * a.T;
-    const int P = s.P;
-    // outputs with the taps the block starts with
+    const int T = a.T;
+    const int P = 1 << s.logP;
     {
-        const int j = tid & (P - 1);
-        // ob is uniform across a warp so that every lane reaches the shuffles
-        for (int ob = (tid >> 5) * (32 / P); ob < 2 * L; ob += NT / P) {
-            const int o = ob + (tid & 31) / P;
-            const bool valid = o < 2 * L;
-            const int q = valid ? (o >= L ? 1 : 0) : 0, n = valid ? o - q * L : 0;
+        const int ostep = NT >> s.logP;
+        const float2* h0 = s.taps;
+        const float2* h1 = s.taps + T;
+        for (int ob = (tid >> 5) << (5 - s.logP); ob < L; ob += ostep) {
+            const int n = ob + ((tid & 31) >> s.logP);
+            const bool valid = n < L;
+            const int nn = valid ? n : 0;
+            const float2* x0 = xs + 2 * nn + T - 1;
+            const float2* x1 = x0 + s.XS;
             float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-            // lane j of the group takes polarisation p and a contiguous run of taps
-            const int p_first = P == 1 ? 0 : (j & 1), p_last = P == 1 ? 1 : (j & 1);
-            const int nk = P == 1 ? 1 : P / 2, kc = (T + nk - 1) / nk;
-            const int klo = P == 1 ? 0 : (j >> 1) * kc;
-            const int khi = valid ? min(T, klo + kc) : klo;
-            for (int p = p_first; p <= p_last; ++p) {
-                const float2* hq = s.taps + (q * 2 + p) * T;
-                const float2* xp = xs + p * s.XS + 2 * n + T - 1;
-                int k = klo;
-                for (; k + 1 < khi; k += 2) {
-                    acc0 = cmac(acc0, hq[k], xp[-k]);
-                    acc1 = cmac(acc1, hq[k + 1], xp[-k - 1]);
-                }
-                if (k < khi) acc0 = cmac(acc0, hq[k], xp[-k]);
+            const int a1 = valid ? s.ka1 : s.ka0, b1 = valid ? s.kb1 : s.kb0;
+            int k = s.ka0;
+            for (; k + 1 < a1; k += 2) {
+                acc0 = cmac(acc0, h0[k], x0[-k]);
+                acc1 = cmac(acc1, h0[k + 1], x0[-k - 1]);
             }
+            if (k < a1) acc0 = cmac(acc0, h0[k], x0[-k]);
+            k = s.kb0;
+            for (; k + 1 < b1; k += 2) {
+                acc0 = cmac(acc0, h1[k], x1[-k]);
+                acc1 = cmac(acc1, h1[k + 1], x1[-k - 1]);
+            }
+            if (k < b1) acc0 = cmac(acc0, h1[k], x1[-k]);
             float2 acc = cadd(acc0, acc1);
             for (int w = 1; w < P; w <<= 1) {
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, w);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, w);
             }
-            if (valid && j == 0) {
-                s.ys[q * L + n] = acc;
-                if (a.cma) s.es[q * L + n] = cscale(acc, a.R2 - cabs2(acc));
+            if (valid && (tid & (P - 1)) == 0) {
+                s.ys[n] = acc;
+                if (a.cma) s.es[n] = cscale(acc, a.R2 - cabs2(acc));
                 if (store) a.y[(int64_t)q * a.ystride + n0 + n] = acc;
             }
         }
     }
     __syncthreads();
     if (!a.cma) {
-        const int w = tid >> 5, lane = tid & 31;
-        if (w < 2) {
+        if (tid < 32) {
             float2 acc = make_float2(0.0f, 0.0f);
-            for (int n = lane; n < L; n += 32) {
-                const float2 y = s.ys[w * L + n];
+            for (int n = tid; n < L; n += 32) {
+                const float2 y = s.ys[n];
                 const float2 y2 = cmul(y, y);
                 acc = cadd(acc, cmul(y2, y2));
             }
             acc.x = warp_sum(acc.x);
             acc.y = warp_sum(acc.y);
-            if (lane == 0) {
+            if (tid == 0) {
                 const float psi = 0.25f * atan2f(-acc.y, -acc.x);
                 float sn, cs;
                 sincosf(psi, &sn, &cs);
-                s.rot[w] = make_float2(cs, -sn);
+                s.rot[0] = make_float2(cs, -sn);
             }
         }
         __syncthreads();
-        for (int o = tid; o < 2 * L; o += NT) {
-            const int q = o >= L ? 1 : 0;
+        const float2 r = s.rot[0];
+        for (int o = tid; o < L; o += NT) {
             const float2 y = s.ys[o];
-            const float2 r = s.rot[q];
             const float2 d = qam_decide(cmul(y, r), qm);
             s.es[o] = csub(cmulc(d, r), y);
         }
         __syncthreads();
     }
-    // gradient partial sums
-    const int NTAP = 2 * T2;
-    {
-        const int g = tid / NTAP, t = tid - g * NTAP;
-        if (g < s.G) {
-            const int q = t / T2, p = (t / T) & 1, k = t - (t / T) * T;
-            const float2* xp = xs + p * s.XS + T - 1 - k;
-            const float2* eq = s.es + q * L;
-            float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-            int n = g;
-            for (; n + s.G < L; n += 2 * s.G) {
-                acc0 = cmacc(acc0, eq[n], xp[2 * n]);
-                acc1 = cmacc(acc1, eq[n + s.G], xp[2 * (n + s.G)]);
-            }
-            if (n < L) acc0 = cmacc(acc0, eq[n], xp[2 * n]);
-            s.part[g * NTAP + t] = cadd(acc0, acc1);
+    if (s.gt >= 0) {
+        const float2* xp = xs + s.gx;
+        float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+        const int G = s.G;
+        int n = s.gg;
+        for (; n + G < L; n += 2 * G) {
+            acc0 = cmacc(acc0, s.es[n], xp[2 * n]);
+            acc1 = cmacc(acc1, s.es[n + G], xp[2 * (n + G)]);
         }
+        if (n < L) acc0 = cmacc(acc0, s.es[n], xp[2 * n]);
+        s.part[s.gg * 2 * T + s.gt] = cadd(acc0, acc1);
     }
     __syncthreads();
-    for (int t = tid; t < NTAP; t += NT) {
+    {
+        // R lanes per tap add every R-th group partial, then combine with xor-shuffles
+        const int logR = s.logR, R = 1 << logR;
+        const int t = tid >> logR, r = tid & (R - 1);
         float2 acc = make_float2(0.0f, 0.0f);
-        for (int g = 0; g < s.G; ++g) acc = cadd(acc, s.part[g * NTAP + t]);
-        s.taps[t] = make_float2(fmaf(a.mu, acc.x, s.taps[t].x), fmaf(a.mu, acc.y, s.taps[t].y));
+        if (t < 2 * T) {
+            for (int g = r; g < s.G; g += R) acc = cadd(acc, s.part[g * 2 * T + t]);
+        }
+        for (int w = 1; w < R; w <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, w);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, w);
+        }
+        if (t < 2 * T && r == 0)
+            s.taps[t] = make_float2(fmaf(a.mu, acc.x, s.taps[t].x), fmaf(a.mu, acc.y, s.taps[t].y));
     }
 }
 
@@ -178,56 +186,71 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
     extern __shared__ float2 smem[];
     if (a.run_if && *a.run_if == 0) return;
     const int T = a.T, Lb = a.Lb;
+    const int q = blockIdx.y;
+    const int tid = threadIdx.x;
     LmsCtx<NT> s;
     s.XS = 2 * Lb + T;
-    s.G = max(1, NT / (4 * T));
-    int P = 1;
-    while (P < 8 && 2 * P * 2 * Lb <= NT) P *= 2;
-    s.P = P;
+    s.G = max(1, NT / (2 * T));
+    int logP = 0;
+    while (logP < 4 && ((Lb << (logP + 1)) <= NT)) ++logP;
+    s.logP = logP;
+    int logR = 0;
+    while (logR < 3 && (1 << (logR + 1)) <= s.G && ((2 * T) << (logR + 1)) <= NT) ++logR;
+    s.logR = logR;
     s.taps = smem;
-    s.xs0 = s.taps + 4 * T;
+    s.xs0 = s.taps + 2 * T;
     s.xs1 = s.xs0 + 2 * s.XS;
     s.ys = s.xs1 + 2 * s.XS;
-    s.es = s.ys + 2 * Lb;
-    s.part = s.es + 2 * Lb;
-    s.rot = s.part + s.G * 4 * T;
+    s.es = s.ys + Lb;
+    s.part = s.es + Lb;
+    s.rot = s.part + s.G * 2 * T;
+    {
+        // output lane j of a group takes the flattened terms u in [j cs, (j + 1) cs), u = p T + k
+        const int P = 1 << logP, j = tid & (P - 1);
+        const int cs = (2 * T + P - 1) >> logP;
+        const int u0 = min(2 * T, j * cs), u1 = min(2 * T, u0 + cs);
+        s.ka0 = min(u0, T);
+        s.ka1 = min(u1, T);
+        s.kb0 = max(u0, T) - T;
+        s.kb1 = max(u1, T) - T;
+        const int g = tid / (2 * T), t = tid - g * 2 * T;
+        s.gt = g < s.G ? t : -1;
+        s.gg = g;
+        const int p = t >= T ? 1 : 0, k = t - p * T;
+        s.gx = p * s.XS + T - 1 - k;
+    }
     const Qam qm = make_qam(a.m);
 
     const int64_t seg = blockIdx.x;
     const int64_t nseg = gridDim.x;
     const long long inc = a.derotate ? a.st->nco_inc : 0;
-    for (int t = threadIdx.x; t < 4 * T; t += NT) s.taps[t] = a.taps_in[t];
+    for (int t = tid; t < 2 * T; t += NT) s.taps[t] = a.taps_in[q * 2 * T + t];
     const int64_t start = seg * a.L_seg;
     const int64_t end = min(a.n_sym, start + a.L_seg);
     const int nwarm = seg > 0 ? a.n_wu : 0;
     const int nmain = (int)((end - start + Lb - 1) / Lb);
     const int nblk = nwarm + nmain;
-    auto blk = [&](int b, int64_t& n0, int& L) {
-        if (b < nwarm) { n0 = start - (int64_t)(nwarm - b) * Lb; L = Lb; }
-        else { n0 = start + (int64_t)(b - nwarm) * Lb; L = (int)min((int64_t)Lb, end - n0); }
+    auto blk_n0 = [&](int b) -> int64_t {
+        return b < nwarm ? start - (int64_t)(nwarm - b) * Lb : start + (int64_t)(b - nwarm) * Lb;
     };
-    int64_t n0;
-    int L;
+    auto blk_L = [&](int b) -> int {
+        return b < nwarm ? Lb : (int)min((int64_t)Lb, end - blk_n0(b));
+    };
     if (nblk > 0) {
-        blk(0, n0, L);
-        lms_prefetch(a, s, n0, L);
-        lms_commit(a, s, 0, n0, L, inc);
+        lms_prefetch(a, s, blk_n0(0), blk_L(0));
+        lms_commit(a, s, s.xs0, blk_n0(0), blk_L(0), inc);
     }
     __syncthreads();
     for (int b = 0; b < nblk; ++b) {
-        blk(b, n0, L);
-        int64_t nn0 = 0;
-        int nL = 0;
-        if (b + 1 < nblk) {
-            blk(b + 1, nn0, nL);
-            lms_prefetch(a, s, nn0, nL);
-        }
-        lms_block<NT>(a, s, (b & 1) ? s.xs1 : s.xs0, n0, L, b >= nwarm && a.y != nullptr, qm);
-        if (b + 1 < nblk) lms_commit(a, s, (b + 1) & 1, nn0, nL, inc);
+        const int64_t n0 = blk_n0(b);
+        const int L = blk_L(b);
+        if (b + 1 < nblk) lms_prefetch(a, s, blk_n0(b + 1), blk_L(b + 1));
+        lms_block<NT>(a, s, (b & 1) ? s.xs1 : s.xs0, n0, L, b >= nwarm && a.y != nullptr, qm, q);
+        if (b + 1 < nblk) lms_commit(a, s, (b & 1) ? s.xs0 : s.xs1, blk_n0(b + 1), blk_L(b + 1), inc);
         __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out) {
-        for (int t = threadIdx.x; t < 4 * T; t += NT) a.taps_out[t] = s.taps[t];
+        for (int t = tid; t < 2 * T; t += NT) a.taps_out[q * 2 * T + t] = s.taps[t];
     }
 }
 
@@ -445,8 +468,8 @@ __global__ void k_cma_rebuild(RxDevState* st, int T, const int* flag) {
 
 int64_t lms_smem_bytes(int T, int Lb, int threads) {
     const int XS = 2 * Lb + T;
-    const int G = threads / (4 * T) > 1 ? threads / (4 * T) : 1;
-    return (int64_t)sizeof(float2) * (4 * T + 4 * XS + 4 * Lb + G * 4 * T + 2);
+    const int G = threads / (2 * T) > 1 ? threads / (2 * T) : 1;
+    return (int64_t)sizeof(float2) * (2 * T + 4 * XS + 2 * Lb + G * 2 * T + 1);
 }
 
 template <int NT>
@@ -459,13 +482,17 @@ static cudaError_t launch_lms_t(const LmsArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_lms<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_lms<NT><<<(unsigned)nseg, NT, smem, s>>>(a);
+    k_lms<NT><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
-    if (threads >= 1024) return launch_lms_t<1024>(a, s);
-    return launch_lms_t<256>(a, s);
+    switch (threads) {
+        case 128: return launch_lms_t<128>(a, s);
+        case 512: return launch_lms_t<512>(a, s);
+        case 1024: return launch_lms_t<1024>(a, s);
+        default: return launch_lms_t<256>(a, s);
+    }
 }
 
 cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,

@@ -174,6 +174,9 @@ rx_status validate(const rx_config* c) {
     if (!std::isfinite(c->input_scale)) return RX_EINVAL;
     if (c->max_symbols < 1 || c->max_symbols > (int64_t)1 << 28) return RX_EINVAL;
     if (c->streaming && (c->max_symbols % (c->fft_size / 4)) != 0) return RX_EINVAL;
+    if (c->lms_threads != 0 && c->lms_threads != 128 && c->lms_threads != 256 && c->lms_threads != 512 &&
+        c->lms_threads != 1024)
+        return RX_EINVAL;
     return RX_OK;
 }
 
@@ -424,7 +427,7 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
         a.taps_out = st->taps_last;
         a.y = h->y;
         a.ystride = h->Nmax;
-        RX_CK(launch_lms(a, 256, s));
+        RX_CK(launch_lms(a, c.lms_threads ? c.lms_threads : 256, s));
         ++nl;
     }
     {

@@ -24,7 +24,9 @@ RX_ERR_NONFINITE, RX_ERR_SYNC_LOST, RX_ERR_SINGULAR = 0x1, 0x2, 0x4
 
 EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_bytes", "rx_get_buffer",
            "rx_reset", "rx_state_size", "rx_state_get", "rx_state_set", "rx_set_timing", "rx_stage_count",
-           "rx_stage_name", "rx_stage_times", "rx_launch_count", "rx_destroy", "rx_strerror")
+           "rx_stage_name", "rx_stage_times", "rx_launch_count", "rx_destroy", "rx_strerror",
+           "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
+           "rx_batch_launch_count", "rx_batch_destroy")
 
 
 class rx_config(C.Structure):
@@ -37,7 +39,7 @@ class rx_config(C.Structure):
         ("bps_phases", C.c_int32), ("bps_window", C.c_int32), ("edge_skip", C.c_int32), ("sync_len", C.c_int32),
         ("max_delay", C.c_int32), ("mu_cma", C.c_float), ("mu_dd", C.c_float), ("fo_grid_hz", C.c_double),
         ("input_format", C.c_int32), ("input_scale", C.c_float), ("streaming", C.c_int32),
-        ("max_symbols", C.c_int64),
+        ("max_symbols", C.c_int64), ("lms_threads", C.c_int32),
     ]
 
 
@@ -89,6 +91,13 @@ def lib() -> C.CDLL:
             "rx_launch_count": (u64, [vp]),
             "rx_destroy": (None, [vp]),
             "rx_strerror": (C.c_char_p, [i32]),
+            "rx_batch_create": (i32, [C.POINTER(rx_config), i32, C.POINTER(vp)]),
+            "rx_batch_config": (i32, [vp, i32, C.POINTER(rx_config)]),
+            "rx_batch_handle": (vp, [vp, i32]),
+            "rx_batch_process": (i32, [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(vp), vp]),
+            "rx_batch_stats": (i32, [vp, i32, C.POINTER(rx_stats_t)]),
+            "rx_batch_launch_count": (u64, [vp]),
+            "rx_batch_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -203,3 +212,44 @@ def rx_destroy(h: int) -> None:
 
 def rx_strerror(status: int) -> str:
     return lib().rx_strerror(status).decode()
+
+
+def rx_batch_create(cfgs: list) -> int:
+    arr = (rx_config * len(cfgs))(*cfgs)
+    b = C.c_void_p()
+    _check(lib().rx_batch_create(arr, len(cfgs), C.byref(b)), "rx_batch_create")
+    return b.value
+
+
+def rx_batch_config(b: int, i: int) -> rx_config:
+    cfg = rx_config()
+    _check(lib().rx_batch_config(b, i, C.byref(cfg)), "rx_batch_config")
+    return cfg
+
+
+def rx_batch_handle(b: int, i: int) -> int:
+    return lib().rx_batch_handle(b, i)
+
+
+def rx_batch_process(b: int, d_in: list, n_sym: list, d_ref: list | None, d_out: list | None,
+                     stream: int | None) -> None:
+    n = len(d_in)
+    ins = (C.c_void_p * n)(*d_in)
+    ns = (C.c_int64 * n)(*n_sym)
+    refs = (C.c_void_p * n)(*d_ref) if d_ref is not None else None
+    outs = (C.c_void_p * n)(*d_out) if d_out is not None else None
+    _check(lib().rx_batch_process(b, ins, ns, refs, outs, stream or None), "rx_batch_process")
+
+
+def rx_batch_stats(b: int, i: int) -> dict:
+    st = rx_stats_t()
+    _check(lib().rx_batch_stats(b, i, C.byref(st)), "rx_batch_stats")
+    return st.as_dict()
+
+
+def rx_batch_launch_count(b: int) -> int:
+    return int(lib().rx_batch_launch_count(b))
+
+
+def rx_batch_destroy(b: int) -> None:
+    lib().rx_batch_destroy(b)
