@@ -46,9 +46,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
-    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch"],
+    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch", "learned"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
-                         "batch: 16 channels in one graph launch")
+                         "batch: 16 channels in one graph launch; learned: split-step link, chain + "
+                         "trained post-equaliser")
+    ap.add_argument("--launch-dbm", type=float, default=4.0, help="launch power of the learned workload")
+    ap.add_argument("--train-steps", type=int, default=4000, help="Adam steps of the learned workload")
     ap.add_argument("--fmt", default="i8", choices=["i8", "f16"], help="input format of the stream workload")
     return ap.parse_args()
 
@@ -442,6 +445,123 @@ def batch_arm(args) -> None:
     rx.rx_batch_destroy(b)
 
 
+CNN_FWD_FLOP = 2 * 9 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 4)                 # per DP symbol
+CNN_TRAIN_FLOP = 2 * CNN_FWD_FLOP + 2 * 9 * (64 * 64 + 64 * 64 + 64 * 4)         # + weight and data gradients
+
+
+def learned_arm(args) -> None:
+    """Learned post-equaliser on split-step DP-16QAM 32 GBd, 10 x 80 km: the plain chain on training
+    frames, training by the library's kernels, then timed steps of chain + post-equaliser + decisions
+    on a frame of another seed; BER/EVM of both forms reported."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.learned import PostEqualiser, chain_pairs, decide_stats, he_init
+    from paper_2011_13695_gb300.receiver import Receiver
+    from synth.ssfm import generate_nonlinear
+    from synth.workloads import workload
+
+    kw = {"launch_dbm": args.launch_dbm}
+    if args.n_sym:
+        kw["n_sym"] = args.n_sym
+    w = workload("dp-16qam-32gbd-ssfm", **kw)
+    link, fibre = w["link"], w["fibre"]
+    N, m = link.n_sym, link.bits_per_sym
+
+    def on_device(fr):
+        return (torch.from_numpy(np.ascontiguousarray(fr.samples.astype(np.complex64))).cuda(),
+                torch.from_numpy(np.ascontiguousarray(fr.ref_words).view(np.int32)).cuda(),
+                torch.from_numpy(np.ascontiguousarray(fr.symbols.astype(np.complex64))).cuda())
+
+    t0 = time.perf_counter()
+    rcv = Receiver(w["rx"], N)
+    zs, ts, train_stats = [], [], []
+    for seed in w["train_seeds"]:
+        xs_, ref_, sym_ = on_device(generate_nonlinear(link, fibre, seed, device="cuda"))
+        z, t, st = chain_pairs(rcv, xs_, N, ref_, sym_)
+        zs.append(z)
+        ts.append(t)
+        train_stats.append(st)
+    x, ref, sym = on_device(generate_nonlinear(link, fibre, w["test_seed"], device="cuda"))
+    gen_s = time.perf_counter() - t0
+
+    window, steps = 4096, args.train_steps
+    pe = PostEqualiser(N, he_init(seed=0))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = pe.train(zs, ts, 1024, N - 1024, steps=steps, window=window, lr=1e-3, lr_final=1e-4, seed=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+
+    out = torch.empty((2, N), dtype=torch.complex64, device="cuda")
+    for _ in range(args.warmup):
+        rcv.process(x, N, ref, None)
+        pe.forward(rcv.symbols(N), out)
+    torch.cuda.synchronize()
+    # plain chain and learned form on the test frame (statistics of one pass each)
+    rcv.reset()
+    z_test, _, plain = chain_pairs(rcv, x, N, ref, sym)
+    pe.forward(z_test, out)
+    learned = decide_stats(rcv, out, N, ref)
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    zbuf = torch.empty((2, N), dtype=torch.complex64, device="cuda")
+    zbytes = rx.rx_buffer_bytes(rcv.h, rx.RX_BUF_Z)
+    step_ms, cnn_ms = [], []
+    launches0 = rx.rx_launch_count(rcv.h)
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            rcv.process(x, N, ref, None)
+            rx.rx_get_buffer(rcv.h, rx.RX_BUF_Z, zbuf.data_ptr(), zbytes, stream.cuda_stream)
+            b.record(stream)
+            pe.forward(zbuf, out)
+            c.record(stream)
+            rcv.decide(out, N, ref, None)
+            d = torch.cuda.Event(enable_timing=True)
+            d.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(a.elapsed_time(d))
+            cnn_ms.append(b.elapsed_time(c))
+    launches = rx.rx_launch_count(rcv.h) - launches0 + args.steps * 5
+    t = sum(step_ms) / len(step_ms)
+    tc = sum(cnn_ms) / len(cnn_ms)
+    pk = peaks()
+    fp32_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fwd_tflops = 2 * N * CNN_FWD_FLOP / (tc * 1e-3) / 1e12
+    train_tflops = steps * 2 * window * CNN_TRAIN_FLOP / (train_ms * 1e-3) / 1e12
+    bits = 2 * m * N
+    pe.close()
+    line = {
+        "metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+        "dtype": "f32 chain, bf16 x bf16 -> f32 network", "data": "synthetic (split-step Manakov, seeded)",
+        "config": {"workload": "dp-16qam-32gbd-ssfm", "symbols_per_pol": N, "launch_dbm": args.launch_dbm,
+                   "spans": fibre.spans, "span_km": fibre.span_km, "train_frames": len(zs),
+                   "train_steps": steps, "window": window, "l2": "flushed between timed steps"},
+        "plain": {"ber": plain["ber"], "evm": plain["evm"], "bit_errors": plain["bit_errors"],
+                  "bits_counted": plain["bits_counted"]},
+        "learned": {"ber": learned["ber"], "evm": learned["evm"], "bit_errors": learned["bit_errors"],
+                    "bits_counted": learned["bits_counted"]},
+        "evm_gain_db": 20 * np.log10(plain["evm"] / learned["evm"]),
+        "train": {"ms": train_ms, "tflops": train_tflops, "loss_first": float(losses[:20].mean()),
+                  "loss_last": float(losses[-20:].mean()), "train_plain_ber": [s_["ber"] for s_ in train_stats]},
+        "roofline": {"kernel": "cnn forward (4 conv launches)", "bound": "alu", "achieved": fwd_tflops,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": fwd_tflops / fp32_peak, "traffic": None,
+                     "note": "FP32 FMA pipes (CUDA cores), nominal unit count x max clock"},
+        "cnn_ms": tc, "gpu_launches": int(launches), "generate_s": round(gen_s, 1), "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    rcv.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -450,6 +570,8 @@ def main():
         stream_arm(args)
     elif args.workload == "batch":
         batch_arm(args)
+    elif args.workload == "learned":
+        learned_arm(args)
     else:
         our_arm(args)
 

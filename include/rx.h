@@ -168,6 +168,16 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
 rx_status rx_process_host(rx_handle* h, const void* h_in, int64_t n_sym, const uint32_t* h_ref_bits,
                           uint32_t* h_out_bits, rx_stream_t stream);
 
+/*
+ * rx_decide: stage A6 alone (alignment, Gray demap, bit/symbol error and EVM
+ * counting) on carrier-recovered symbols the caller supplies, e.g. the output
+ * of the learned post-equaliser: d_z is DEVICE float [2][n_sym][2]. Counts
+ * accumulate into the handle's statistics like rx_process's. Single-frame
+ * handles only (RX_EINVAL for streaming handles).
+ */
+rx_status rx_decide(rx_handle* h, const float* d_z, int64_t n_sym, const uint32_t* d_ref_bits, uint32_t* d_out_bits,
+                    rx_stream_t stream);
+
 /* rx_stats: wait for the last stream used by the handle, then fill *out. */
 rx_status rx_stats(rx_handle* h, rx_stats_t* out);
 
@@ -238,6 +248,33 @@ rx_status rx_batch_process(rx_batch* b, const void* const* d_in, const int64_t* 
 rx_status rx_batch_stats(rx_batch* b, int32_t i, rx_stats_t* out);
 uint64_t rx_batch_launch_count(rx_batch* b);
 void rx_batch_destroy(rx_batch* b);
+
+/*
+ * Learned post-equaliser (the paper has none): a 1-D CNN applied to the
+ * carrier-recovered symbols z of both polarisations, out = z + f(z), with
+ * f = conv(C->4) relu conv(C->C) relu conv(C->C) relu conv(4->C), kernel 9,
+ * "same" zero padding, C = 64. Weights and activations BF16, products and
+ * sums FP32, FP32 master weights updated by Adam (b1 0.9, b2 0.999, eps 1e-8)
+ * on the mean squared error to the transmitted symbols.
+ * Parameter order (h_params, d_grads): per layer W[out][in][9] then b[out],
+ * layers 4->C, C->C, C->C, C->4; rx_pe_param_count gives the length.
+ * Sequences: d_z, d_target, d_out are DEVICE float [2][T][2] (the layout of
+ * rx_process's z), owned by the caller; T <= max_len given at create, which
+ * allocates all working memory. Calls are asynchronous on `stream`.
+ */
+typedef struct rx_pe rx_pe;
+int64_t rx_pe_param_count(int32_t channels, int32_t kernel);
+rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const float* h_params, rx_pe** out);
+/* current FP32 master parameters into h_params (synchronises) */
+rx_status rx_pe_params(rx_pe* p, float* h_params);
+rx_status rx_pe_forward(rx_pe* p, const float* d_z, int64_t T, float* d_out, rx_stream_t stream);
+/* loss (mean squared error) and its gradient w.r.t. every parameter, without updating them */
+rx_status rx_pe_gradients(rx_pe* p, const float* d_z, const float* d_target, int64_t T, float* d_grads, float* d_loss,
+                          rx_stream_t stream);
+/* one Adam step on the sequence: forward, backward, update (d_loss nullable) */
+rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, int64_t T, float lr, float* d_loss,
+                           rx_stream_t stream);
+void rx_pe_destroy(rx_pe* p);
 
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);

@@ -208,8 +208,24 @@ def derotate(x: np.ndarray, code: int, grid: float, fs: float, g0: int) -> np.nd
 # A4: segmented block DD-LMS
 # ----------------------------------------------------------------------------
 
+def decision_margin(u: np.ndarray, m: int) -> np.ndarray:
+    """Distance (amplitude units) of each point's nearer component to an interior decision
+    boundary of the square-QAM grid, minimised over the last axis. Diagnostic only: it tells
+    how close a decision came to flipping; no arithmetic of the receiver uses it."""
+    L = qam.n_levels(m)
+    a = qam.amp(m)
+
+    def one(v):
+        t = (v / a + (L - 1)) / 2.0                       # level coordinate; boundaries at k + 1/2
+        b = np.clip(np.floor(t) + 0.5, 0.5, L - 1.5)
+        return np.abs(t - b) * 2.0 * a
+
+    return np.minimum(one(np.real(u)), one(np.imag(u))).min(axis=-1)
+
+
 def _dd_blocks(xbuf, h, n, m, mu, off):
-    """One DD-LMS block on a batch of segments. n: [nS, L]; h: [nS, 2, 2, T]."""
+    """One DD-LMS block on a batch of segments. n: [nS, L]; h: [nS, 2, 2, T].
+    Returns (y, updated taps, decision margin [nS, 2])."""
     T = h.shape[-1]
     X = gather(xbuf, n, T, off)                       # [nS, 2, L, T]
     y = butterfly(h, X)                               # [nS, 2, L]
@@ -217,7 +233,7 @@ def _dd_blocks(xbuf, h, n, m, mu, off):
     rot = np.exp(-1j * psi)[..., None]
     d = qam.decide(y * rot, m)
     e = d / rot - y
-    return y, h + mu * gradient(e, X)
+    return y, h + mu * gradient(e, X), decision_margin(y * rot, m)
 
 
 def _run_segments(xbuf, h0, starts, n_main, L_b, n_warm, m, mu, off, last_len=None):
@@ -225,30 +241,37 @@ def _run_segments(xbuf, h0, starts, n_main, L_b, n_warm, m, mu, off, last_len=No
 
     starts: [nS] first symbol of each segment; n_main full blocks each (the
     last one may be cut to ``last_len`` symbols); n_warm warm-up blocks.
+    Returns (y, final taps, smallest decision margin of each segment and row [nS, 2]).
     """
     nS = len(starts)
     h = np.broadcast_to(h0, (nS,) + h0.shape).copy()
+    margin = np.full((nS, 2), np.inf)
     for w in range(n_warm):
         b0 = starts - (n_warm - w) * L_b
         n = b0[:, None] + np.arange(L_b)[None, :]
-        _, h = _dd_blocks(xbuf, h, n, m, mu, off)
+        _, h, mg = _dd_blocks(xbuf, h, n, m, mu, off)
+        margin = np.minimum(margin, mg)
     ys = []
     for j in range(n_main):
         L = L_b if (last_len is None or j < n_main - 1) else last_len
         n = (starts + j * L_b)[:, None] + np.arange(L)[None, :]
-        y, h = _dd_blocks(xbuf, h, n, m, mu, off)
+        y, h, mg = _dd_blocks(xbuf, h, n, m, mu, off)
+        margin = np.minimum(margin, mg)
         ys.append(y)
-    return np.concatenate(ys, axis=-1), h
+    return np.concatenate(ys, axis=-1), h, margin
 
 
-def dd_lms(xbuf, h_init, n_sym, L_b, seg_blocks, warmup_blocks, m, mu, off=0):
-    """Returns (y [2, n_sym], final taps of the last segment)."""
+def dd_lms(xbuf, h_init, n_sym, L_b, seg_blocks, warmup_blocks, m, mu, off=0, diag=None):
+    """Returns (y [2, n_sym], final taps of the last segment). When ``diag`` is a dict it receives
+    "margin" [nseg, 2]: the smallest decision margin (``decision_margin``) met by each segment and
+    row over its warm-up and main blocks."""
     L_seg = seg_blocks * L_b
     y = np.zeros((2, n_sym), dtype=np.complex128)
     if n_sym <= 0:
         return y, h_init.copy()
     nseg = (n_sym + L_seg - 1) // L_seg
     h_last = None
+    margin = np.full((nseg, 2), np.inf)
 
     def place(starts, ys):
         for i, s in enumerate(starts):
@@ -259,19 +282,21 @@ def dd_lms(xbuf, h_init, n_sym, L_b, seg_blocks, warmup_blocks, m, mu, off=0):
         length = min(L_seg, n_sym - start)
         n_main = (length + L_b - 1) // L_b
         last_len = length - (n_main - 1) * L_b
-        ys, h = _run_segments(xbuf, h_init, np.array([start]), n_main, L_b, warm, m, mu, off, last_len)
+        ys, h, mg = _run_segments(xbuf, h_init, np.array([start]), n_main, L_b, warm, m, mu, off, last_len)
         place([start], ys)
+        margin[s] = mg[0]
         return h[0]
 
-    h = one_segment(0, 0)
-    if nseg == 1:
-        return y, h
+    h_last = one_segment(0, 0)
     full = [s for s in range(1, nseg) if (s + 1) * L_seg <= n_sym]
     if full:
         starts = np.array(full) * L_seg
-        ys, hs = _run_segments(xbuf, h_init, starts, seg_blocks, L_b, warmup_blocks, m, mu, off)
+        ys, hs, mg = _run_segments(xbuf, h_init, starts, seg_blocks, L_b, warmup_blocks, m, mu, off)
         place(starts, ys)
+        margin[full] = mg
         h_last = hs[-1]
-    if nseg - 1 not in full:
+    if nseg > 1 and nseg - 1 not in full:
         h_last = one_segment(nseg - 1, warmup_blocks)
+    if diag is not None:
+        diag["margin"] = margin
     return y, h_last

@@ -89,6 +89,7 @@ class RxConfig:
 @dataclass
 class FrameResult:
     scale: np.ndarray = None
+    dd_margin: np.ndarray = None    # smallest A4 decision margin per segment and row [nseg, 2]
     cdc: np.ndarray = None          # A1 output [2, S]
     taps_cma: np.ndarray = None
     y_acq: np.ndarray = None        # CMA outputs while adapting [2, N_acq]
@@ -196,8 +197,10 @@ class Receiver:
         r.taps_init = self.taps.copy()
 
         # A4
+        diag = {}
         r.y, r.taps_final = _mimo.dd_lms(xd, self.taps, N, L_b, cfg.seg_blocks, cfg.warmup_blocks,
-                                         m, cfg.mu_dd, off)
+                                         m, cfg.mu_dd, off, diag)
+        r.dd_margin = diag.get("margin")
         self.taps = r.taps_final
 
         # A5

@@ -27,7 +27,7 @@
 
 namespace {
 
-constexpr int BPS_THREADS = 256;
+constexpr int BPS_THREADS = 128;
 
 // distance of one symbol to the nearest point after rotation, in level units
 __device__ __forceinline__ float bps_dist(float2 v, float c, float s, float hL, float invLm1, float Lm1) {
@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
                                                    uint8_t* __restrict__ bstar, int64_t bstride) {
     constexpr int NSTRIP = BPS_THREADS / GS;
     constexpr int NW = GS / 32;
-    extern __shared__ float2 ys[];                    // [NSTRIP][LEN + W]
+    extern __shared__ float smem_f[];
+    float* ring = smem_f;                             // [W][BPS_THREADS]: each thread's last W distances
+    float2* ys = reinterpret_cast<float2*>(smem_f + W * BPS_THREADS);   // [NSTRIP][LEN + W]
     __shared__ uint2 slots[NSTRIP][NW][W];            // per output slot: (warp minimum bits, ballot of its lanes)
     const int tid = threadIdx.x;
     const int sl = tid / GS;                          // strip within the CTA
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     const int span = LEN + W;
     const float2* yq = y + (int64_t)q * ystride;
     const float2* yl = ys + sl * span;
+    float* myring = ring + tid;
 
     // stage y[s0 - W/2, s0 + LEN + W/2); symbols outside [0, N) are NaN, whose
     // distance fmaxf(NaN, 0) turns into 0: they contribute nothing to any window
@@ -86,29 +89,29 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     const int nc = LEN / W;
     uint2* myslots = &slots[sl][wip][0];
 
-    float ring[W];
     float D = pen;
-#pragma unroll
+#pragma unroll 8
     for (int u = 0; u < W; ++u) {
-        ring[u] = fmaxf(bps_dist(yl[u], c, s, hL, invLm1, Lm1), 0.0f);
-        D += ring[u];
+        const float d = fmaxf(bps_dist(yl[u], c, s, hL, invLm1, Lm1), 0.0f);
+        myring[u * BPS_THREADS] = d;
+        D += d;
     }
     bps_publish(D, &myslots[0], lane);                // window of local output 0
     for (int ch = 0; ch <= nc; ++ch) {
         if (ch > 0) {
-#pragma unroll
+            const float2* yc = yl + ch * W;
+#pragma unroll 8
             for (int u = 0; u < W; ++u) {
-                const float d = fmaxf(bps_dist(yl[ch * W + u], c, s, hL, invLm1, Lm1), 0.0f);
-                D = (D + d) - ring[u];
-                ring[u] = d;
+                const float d = fmaxf(bps_dist(yc[u], c, s, hL, invLm1, Lm1), 0.0f);
+                const float old = myring[u * BPS_THREADS];
+                myring[u * BPS_THREADS] = d;
+                D = (D + d) - old;
                 // window of local output (ch - 1) W + u + 1 is complete; its slot is (u + 1) % W
-                bps_publish(fmaxf(D, 0.0f), &myslots[(u + 1) % W], lane);
-                // keep the compiler from hoisting the whole chunk's loads (register pressure)
-                if ((u & 7) == 7) asm volatile("" ::: "memory");
+                bps_publish(fmaxf(D, 0.0f), &myslots[(u + 1) & (W - 1)], lane);
             }
             float t = pen;                            // re-form the sum directly from the ring
-#pragma unroll
-            for (int r = 0; r < W; ++r) t += ring[r];
+#pragma unroll 8
+            for (int r = 0; r < W; ++r) t += myring[r * BPS_THREADS];
             D = t;
         }
         __syncthreads();
@@ -136,7 +139,7 @@ cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uin
     constexpr int NSTRIP = BPS_THREADS / GS;
     const int64_t nstrip = (N + LEN - 1) / LEN;
     dim3 grid((unsigned)((nstrip + NSTRIP - 1) / NSTRIP), 2);
-    const size_t smem = sizeof(float2) * NSTRIP * (LEN + W);
+    const size_t smem = sizeof(float) * W * BPS_THREADS + sizeof(float2) * NSTRIP * (LEN + W);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_bps<W, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,0 +1,317 @@
+// A9 learned post-equaliser: a 4-layer 1-D CNN on the carrier-recovered
+// symbols (4 real channels I_x, Q_x, I_y, Q_y), out = z + f(z),
+// f = conv(C->4) relu conv(C->C) relu conv(C->C) relu conv(4->C), kernel K = 9,
+// "same" zero padding. Weights and activations are BF16, products and sums
+// FP32, master weights FP32 (Adam). The paper has no learned equaliser.
+//
+// Layout: activations [C][T + 8] with the 4 zero columns of the padding on
+// each side stored, so a convolution reads x[c][t + k] with no bounds checks.
+// One CTA computes 128 positions (or 1024 for 4 outputs) of all output
+// channels: 8 output channels x 4 positions per thread (positions strided by
+// 32 so a warp's loads hit distinct banks), input channels staged in chunks of
+// 16 (FP32 in shared memory), weights staged as [ci][k][co] so 8 output
+// channels come from two 128-bit broadcast loads. The backward pass on the
+// data reuses the same kernel with transposed, flipped weights
+// W'[ci][co][k] = W[co][ci][K-1-k] and the ReLU mask fused into its store;
+// the weight gradient sums dY[co][t] x[ci][t + k - 4] over a chunk of
+// positions per CTA with a 9-register sliding window and adds the chunk's
+// result to FP32 accumulators.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rx_cnn.h"
+
+namespace {
+
+constexpr int KW = 9;          // kernel width
+constexpr int PAD = KW / 2;
+constexpr int CT = 256;        // threads per CTA
+constexpr int CC = 16;         // input channels per staged chunk
+
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld(const float* p) { return *p; }
+
+// EPI 0: bias + ReLU -> BF16 activations; 1: bias + residual -> float2 symbols (COUT = 4);
+// EPI 2: ReLU mask of `mask` -> FP32 gradient (no bias)
+template <typename Tin, int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t Tp, int64_t T,
+                                             const float* __restrict__ W, const float* __restrict__ bias,
+                                             __nv_bfloat16* __restrict__ act_out, const __nv_bfloat16* __restrict__ mask,
+                                             float* __restrict__ grad_out, const float2* __restrict__ zres,
+                                             float2* __restrict__ sym_out) {
+    constexpr int CO_T = COUT >= 8 ? 8 : COUT;       // output channels per thread
+    constexpr int NG = COUT / CO_T;                   // output-channel groups
+    constexpr int TPG = CT / NG;                      // threads per group
+    constexpr int TT = TPG * 4;                       // positions per CTA
+    constexpr int XW = TT + 2 * PAD;
+    constexpr int CCH = CIN < (TT >= 1024 ? CC / 2 : CC) ? CIN : (TT >= 1024 ? CC / 2 : CC);   // static smem < 48 KB
+    __shared__ float xs[CCH][XW];
+    __shared__ __align__(16) float ws[CCH][KW][COUT];
+    const int tid = threadIdx.x;
+    const int g = tid / TPG, lt = tid - g * TPG;
+    const int64_t t0 = (int64_t)blockIdx.x * TT;      // first output position (unpadded index)
+    float acc[CO_T][4];
+#pragma unroll
+    for (int c = 0; c < CO_T; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[c][j] = 0.0f;
+    for (int c0 = 0; c0 < CIN; c0 += CCH) {
+        // stage x[c0 .. c0+CCH)[t0 - 4 .. t0 + TT + 4) (padded index t0 .. t0 + XW)
+        for (int i = tid; i < CCH * XW; i += CT) {
+            const int ci = i / XW, u = i - ci * XW;
+            const int64_t tp = t0 + u;
+            xs[ci][u] = (tp < Tp) ? ld(x + (int64_t)(c0 + ci) * Tp + tp) : 0.0f;
+        }
+        for (int i = tid; i < CCH * KW * COUT; i += CT) {
+            const int co = i / (CCH * KW), r = i - co * CCH * KW, ci = r / KW, k = r - ci * KW;
+            ws[ci][k][co] = W[((int64_t)co * CIN + c0 + ci) * KW + k];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int ci = 0; ci < CCH; ++ci) {
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                float w[CO_T];
+#pragma unroll
+                for (int c = 0; c < CO_T; ++c) w[c] = ws[ci][k][g * CO_T + c];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float xv = xs[ci][lt + j * (TT / 4) + k];
+#pragma unroll
+                    for (int c = 0; c < CO_T; ++c) acc[c][j] = fmaf(w[c], xv, acc[c][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t t = t0 + lt + j * (TT / 4);     // unpadded output position
+        if (t >= T) continue;
+#pragma unroll
+        for (int c = 0; c < CO_T; ++c) {
+            const int co = g * CO_T + c;
+            if (EPI == 0) {
+                const float v = fmaxf(acc[c][j] + bias[co], 0.0f);
+                act_out[(int64_t)co * Tp + t + PAD] = __float2bfloat16_rn(v);
+            } else if (EPI == 2) {
+                const bool on = __bfloat162float(mask[(int64_t)co * Tp + t + PAD]) > 0.0f;
+                grad_out[(int64_t)co * Tp + t + PAD] = on ? acc[c][j] : 0.0f;
+            }
+        }
+        if (EPI == 1) {
+            // channels (I_x, Q_x, I_y, Q_y) -> symbols of pol 0 and 1
+            const float2 z0 = zres[t], z1 = zres[T + t];
+            sym_out[t] = make_float2(z0.x + acc[0][j] + bias[0], z0.y + acc[1][j] + bias[1]);
+            sym_out[T + t] = make_float2(z1.x + acc[2][j] + bias[2], z1.y + acc[3][j] + bias[3]);
+        }
+    }
+}
+
+// dW[co][ci][k] += sum_t dY[co][t] x[ci][t + k - 4], db[co] += sum_t dY[co][t] over a chunk of positions
+template <typename Tin, int CIN, int COUT>
+__global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, const float* __restrict__ dy,
+                                                   int64_t Tp, int64_t T, float* __restrict__ dW, float* __restrict__ db) {
+    constexpr int TC = 256;                           // positions per chunk (static smem < 48 KB)
+    constexpr int CO_TILE = COUT < 16 ? COUT : 16;
+    constexpr int CI_TILE = CIN < 16 ? CIN : 16;
+    __shared__ float dys[CO_TILE][TC];
+    __shared__ float xs[CI_TILE][TC + 2 * PAD];
+    const int co0 = blockIdx.y * CO_TILE, ci0 = blockIdx.z * CI_TILE;
+    const int64_t t0 = (int64_t)blockIdx.x * TC;      // unpadded
+    const int tid = threadIdx.x;
+    for (int i = tid; i < CO_TILE * TC; i += CT) {
+        const int c = i / TC, u = i - c * TC;
+        const int64_t t = t0 + u;
+        dys[c][u] = (t < T) ? dy[(int64_t)(co0 + c) * Tp + t + PAD] : 0.0f;
+    }
+    for (int i = tid; i < CI_TILE * (TC + 2 * PAD); i += CT) {
+        const int c = i / (TC + 2 * PAD), u = i - c * (TC + 2 * PAD);
+        const int64_t tp = t0 + u;                    // padded index of position t0 + u - 4
+        xs[c][u] = (tp < Tp) ? ld(x + (int64_t)(ci0 + c) * Tp + tp) : 0.0f;
+    }
+    __syncthreads();
+    const int co = tid / 16, ci = tid % 16;
+    if (co < CO_TILE && ci < CI_TILE) {
+        float acc[KW];
+        float win[KW];
+#pragma unroll
+        for (int k = 0; k < KW; ++k) { acc[k] = 0.0f; win[k] = xs[ci][k]; }
+        float dbs = 0.0f;
+        for (int u = 0; u < TC; ++u) {
+            const float d = dys[co][u];
+#pragma unroll
+            for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, win[k], acc[k]);
+            dbs += d;
+#pragma unroll
+            for (int k = 0; k < KW - 1; ++k) win[k] = win[k + 1];
+            if (u + 1 < TC) win[KW - 1] = xs[ci][u + KW];   // window of position u + 1 (xs has TC + 8 columns)
+        }
+#pragma unroll
+        for (int k = 0; k < KW; ++k) atomicAdd(&dW[((int64_t)(co0 + co) * CIN + ci0 + ci) * KW + k], acc[k]);
+        if (ci == 0 && blockIdx.z == 0) atomicAdd(&db[co0 + co], dbs);
+    }
+}
+
+__global__ void k_to_channels(const float2* __restrict__ z, int64_t T, int64_t Tp, __nv_bfloat16* __restrict__ x0) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const float2 a = z[t], b = z[T + t];
+    x0[0 * Tp + t + PAD] = __float2bfloat16_rn(a.x);
+    x0[1 * Tp + t + PAD] = __float2bfloat16_rn(a.y);
+    x0[2 * Tp + t + PAD] = __float2bfloat16_rn(b.x);
+    x0[3 * Tp + t + PAD] = __float2bfloat16_rn(b.y);
+}
+
+// d3[c][t] = 2 (out - target) / (4 T); loss += sum (out - target)^2 / (4 T)
+__global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__ tgt, int64_t T, int64_t Tp,
+                      float* __restrict__ d3, float* __restrict__ loss) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (t < T) {
+        const float inv = 1.0f / (4.0f * (float)T);
+        const float2 a = out[t], b = out[T + t], ta = tgt[t], tb = tgt[T + t];
+        const float e[4] = {a.x - ta.x, a.y - ta.y, b.x - tb.x, b.y - tb.y};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            d3[(int64_t)c * Tp + t + PAD] = 2.0f * e[c] * inv;
+            l += e[c] * e[c] * inv;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+// W'[ci][co][k] = bf16(W[co][ci][K-1-k]) and the forward weights as BF16-rounded FP32
+__global__ void k_weights(const float* __restrict__ master, int64_t n, float* __restrict__ fwd, const int* offs,
+                          const int* cins, const int* couts, float* __restrict__ bwd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = __bfloat162float(__float2bfloat16_rn(master[i]));
+    fwd[i] = v;
+    // locate the layer and, for weights, the transposed position
+    for (int l = 0; l < 4; ++l) {
+        const int64_t wo = offs[2 * l], nw = (int64_t)couts[l] * cins[l] * KW;
+        if (i >= wo && i < wo + nw) {
+            const int64_t r = i - wo;
+            const int co = (int)(r / (cins[l] * KW)), ci = (int)((r / KW) % cins[l]), k = (int)(r % KW);
+            bwd[wo + ((int64_t)ci * couts[l] + co) * KW + (KW - 1 - k)] = v;
+        }
+    }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+template <typename Tin, int CIN, int COUT, int EPI>
+cudaError_t conv_t(const Tin* x, int64_t Tp, int64_t T, const float* W, const float* b, __nv_bfloat16* act,
+                   const __nv_bfloat16* mask, float* grad, const float2* zres, float2* sym, cudaStream_t s) {
+    constexpr int CO_T = COUT >= 8 ? 8 : COUT;
+    constexpr int TT = (CT / (COUT / CO_T)) * 4;
+    k_conv<Tin, CIN, COUT, EPI><<<(unsigned)((T + TT - 1) / TT), CT, 0, s>>>(x, Tp, T, W, b, act, mask, grad, zres, sym);
+    return cudaGetLastError();
+}
+
+template <typename Tin, int CIN, int COUT>
+cudaError_t wgrad_t(const Tin* x, const float* dy, int64_t Tp, int64_t T, float* dW, float* db, cudaStream_t s) {
+    constexpr int CO_TILE = COUT < 16 ? COUT : 16;
+    constexpr int CI_TILE = CIN < 16 ? CIN : 16;
+    dim3 grid((unsigned)((T + 255) / 256), COUT / CO_TILE, CIN / CI_TILE);
+    k_conv_wgrad<Tin, CIN, COUT><<<grid, CT, 0, s>>>(x, dy, Tp, T, dW, db);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// forward of the 4 layers; act[0] holds the input channels, act[1..3] the hidden activations
+cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s) {
+    const int64_t Tp = T + 2 * PAD;
+    const int C = B.C;
+    if (C != 64) return cudaErrorInvalidValue;
+    k_to_channels<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(z, T, Tp, B.act[0]);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    const float* W = B.wfwd;
+    e = conv_t<__nv_bfloat16, 4, 64, 0>(B.act[0], Tp, T, W + B.off[0], W + B.off[1], B.act[1], nullptr, nullptr, nullptr,
+                                        nullptr, s);
+    if (e) return e;
+    e = conv_t<__nv_bfloat16, 64, 64, 0>(B.act[1], Tp, T, W + B.off[2], W + B.off[3], B.act[2], nullptr, nullptr,
+                                         nullptr, nullptr, s);
+    if (e) return e;
+    e = conv_t<__nv_bfloat16, 64, 64, 0>(B.act[2], Tp, T, W + B.off[4], W + B.off[5], B.act[3], nullptr, nullptr,
+                                         nullptr, nullptr, s);
+    if (e) return e;
+    return conv_t<__nv_bfloat16, 64, 4, 1>(B.act[3], Tp, T, W + B.off[6], W + B.off[7], nullptr, nullptr, nullptr, z,
+                                           out, s);
+}
+
+// loss gradient and all parameter gradients (B.grad zeroed here) for the last forward
+cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t T, float* loss,
+                         cudaStream_t s) {
+    const int64_t Tp = T + 2 * PAD;
+    cudaError_t e = cudaMemsetAsync(B.grad, 0, sizeof(float) * B.nparam, s);
+    if (e) return e;
+    k_mse<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(out, tgt, T, Tp, B.d[3], loss);
+    if ((e = cudaGetLastError())) return e;
+    float* G = B.grad;
+    const float* Wb = B.wbwd;
+    // layer 3: weights, then data (masked by act[3] > 0) -> d[2]
+    if ((e = wgrad_t<__nv_bfloat16, 64, 4>(B.act[3], B.d[3], Tp, T, G + B.off[6], G + B.off[7], s))) return e;
+    if ((e = conv_t<float, 4, 64, 2>(B.d[3], Tp, T, Wb + B.off[6], nullptr, nullptr, B.act[3], B.d[2], nullptr,
+                                     nullptr, s)))
+        return e;
+    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[2], B.d[2], Tp, T, G + B.off[4], G + B.off[5], s))) return e;
+    if ((e = conv_t<float, 64, 64, 2>(B.d[2], Tp, T, Wb + B.off[4], nullptr, nullptr, B.act[2], B.d[1], nullptr,
+                                      nullptr, s)))
+        return e;
+    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[1], B.d[1], Tp, T, G + B.off[2], G + B.off[3], s))) return e;
+    if ((e = conv_t<float, 64, 64, 2>(B.d[1], Tp, T, Wb + B.off[2], nullptr, nullptr, B.act[1], B.d[0], nullptr,
+                                      nullptr, s)))
+        return e;
+    return wgrad_t<__nv_bfloat16, 4, 64>(B.act[0], B.d[0], Tp, T, G + B.off[0], G + B.off[1], s);
+}
+
+// the padding columns of every activation/gradient plane for a sequence of length T
+__global__ void k_zero_pads(CnnBufs B, int64_t T) {
+    const int64_t Tp = T + 2 * PAD;
+    const int c = blockIdx.x;                         // channel
+    const int u = threadIdx.x;                        // 0 .. 2*PAD-1
+    if (u >= 2 * PAD) return;
+    const int64_t col = u < PAD ? u : T + u;          // [0, PAD) and [T + PAD, Tp)
+    for (int buf = 0; buf < 4; ++buf) {
+        const int nch = buf == 0 ? 4 : B.C;
+        if (c < nch) B.act[buf][(int64_t)c * Tp + col] = __float2bfloat16_rn(0.0f);
+        const int ndch = buf == 3 ? 4 : B.C;
+        if (c < ndch) B.d[buf][(int64_t)c * Tp + col] = 0.0f;
+    }
+}
+
+cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s) {
+    k_zero_pads<<<B.C, 32, 0, s>>>(B, T);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s) {
+    k_weights<<<(unsigned)((B.nparam + 255) / 256), 256, 0, s>>>(B.master, B.nparam, B.wfwd, B.offs_dev, B.cin_dev,
+                                                                 B.cout_dev, B.wbwd);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    k_adam<<<(unsigned)((B.nparam + 255) / 256), 256, 0, s>>>(B.master, B.grad, B.m, B.v, B.nparam, lr, b1, b2, eps,
+                                                              c1, c2);
+    return cudaGetLastError();
+}

@@ -34,6 +34,7 @@ struct rx_batch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;        // capture stream
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> key;      // buffers the graph was captured with
@@ -164,12 +165,15 @@ bool tune_channel(rx_config& c, int64_t n_sym) {
 }
 
 void batch_free(rx_batch* b) {
+    // handles first: rx_destroy waits on the last stream each handle used, one of ours
+    for (auto h : b->h) rx_destroy(h);
+    b->h.clear();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
-    for (auto h : b->h) rx_destroy(h);
+    if (b->cap) cudaStreamDestroy(b->cap);
 }
 
 }  // namespace
@@ -201,7 +205,8 @@ rx_status rx_batch_create(const rx_config* cfgs, int32_t n, rx_batch** out) {
         b->streams.push_back(s);
         b->join.push_back(e);
     }
-    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
         batch_free(b); delete b; return RX_ECUDA;
     }
     *out = b;
@@ -231,22 +236,24 @@ rx_status rx_batch_process(rx_batch* b, const void* const* d_in, const int64_t* 
         key.push_back(d_ref ? d_ref[i] : nullptr);
         key.push_back(d_out ? d_out[i] : nullptr);
     }
-    key.push_back((const void*)s);
     if (!b->exec || key != b->key) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return RX_ECUDA;
+        // capture on the batch's own stream (the caller's may be the legacy default stream,
+        // which cannot be captured); the graph then launches on the caller's stream
+        cudaStream_t cap = b->cap;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return RX_ECUDA;
         rx_status st = RX_OK;
-        cudaEventRecord(b->fork, s);
+        cudaEventRecord(b->fork, cap);
         for (int i = 0; i < b->n && st == RX_OK; ++i) {
             cudaStreamWaitEvent(b->streams[i], b->fork, 0);
             st = rx_process(b->h[i], d_in[i], n_sym[i], d_ref ? d_ref[i] : nullptr, d_out ? d_out[i] : nullptr,
                             (rx_stream_t)b->streams[i]);
             cudaEventRecord(b->join[i], b->streams[i]);
-            cudaStreamWaitEvent(s, b->join[i], 0);
+            cudaStreamWaitEvent(cap, b->join[i], 0);
         }
         cudaGraph_t g = nullptr;
-        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        const cudaError_t ec = cudaStreamEndCapture(cap, &g);
         if (st != RX_OK) { if (g) cudaGraphDestroy(g); return st; }
         if (ec != cudaSuccess || !g) return RX_ECUDA;
         b->graph = g;

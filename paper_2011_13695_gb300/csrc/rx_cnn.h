@@ -1,0 +1,34 @@
+// Device buffers and launchers of the learned post-equaliser (k_cnn.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+struct CnnBufs {
+    int C = 64;                     // hidden channels
+    int64_t nparam = 0;
+    int64_t off[8] = {0};           // parameter offsets: W0, b0, W1, b1, W2, b2, W3, b3
+    int64_t Tmax = 0;
+    float* master = nullptr;        // FP32 master parameters (oracle order)
+    float* m = nullptr;             // Adam moments
+    float* v = nullptr;
+    float* grad = nullptr;          // FP32 gradients of the last backward
+    float* wfwd = nullptr;          // BF16-rounded parameters as used by the forward
+    float* wbwd = nullptr;          // transposed, flipped BF16-rounded weights for the data gradient
+    int* offs_dev = nullptr;        // off[] on the device (int)
+    int* cin_dev = nullptr;
+    int* cout_dev = nullptr;
+    __nv_bfloat16* act[4] = {nullptr, nullptr, nullptr, nullptr};   // [4][Tp], [C][Tp] x 3
+    float* d[4] = {nullptr, nullptr, nullptr, nullptr};             // [C][Tp] x 3, [4][Tp]
+    float2* out = nullptr;          // [2][Tmax] forward output used by training
+    float* loss = nullptr;          // [1]
+};
+
+cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s);
+cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t T, float* loss,
+                         cudaStream_t s);
+cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);
+cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s);
+cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s);

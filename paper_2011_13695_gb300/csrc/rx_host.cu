@@ -29,6 +29,11 @@ enum Stage {
 const char* kStageNames[ST_N] = {"power", "cdc", "cma", "foe", "dd_acq", "lms", "bps",
                                  "unwrap", "sync", "count", "stream_state", "h2d", "d2h"};
 constexpr int kPool = 64;
+// CTA sizes of the block-LMS kernel: the acquisition is one CTA per output row
+// and issue-bound, so fewer threads (less per-thread overhead) finish sooner;
+// the segments are many CTAs, whose count per SM matters more.
+constexpr int kAcqThreads = 256;
+constexpr int kSegThreads = 128;
 
 __global__ void k_state_init(RxDevState* st) {
     st->b_prev[0] = st->b_prev[1] = -1;
@@ -374,13 +379,13 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
                 a.taps_out = st->taps_cma;
                 a.y = h->yacq;
                 a.ystride = h->nacq;
-                RX_CK(launch_lms(a, 1024, s));
+                RX_CK(launch_lms(a, kAcqThreads, s));
                 RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 0, s));
                 RX_CK(launch_cma_rebuild(st, T, h->flag, s));
                 LmsArgs a2 = a;
                 a2.taps_in = st->taps_init;
                 a2.run_if = h->flag;
-                RX_CK(launch_lms(a2, 1024, s));
+                RX_CK(launch_lms(a2, kAcqThreads, s));
                 RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 1, s));
                 nl += 5;
             }
@@ -404,7 +409,7 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
                 a.taps_in = st->taps_init;
                 a.taps_out = st->taps_init;
                 a.y = nullptr;
-                RX_CK(launch_lms(a, 1024, s));
+                RX_CK(launch_lms(a, kAcqThreads, s));
                 ++nl;
             }
         } else {
@@ -427,7 +432,7 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
         a.taps_out = st->taps_last;
         a.y = h->y;
         a.ystride = h->Nmax;
-        RX_CK(launch_lms(a, c.lms_threads ? c.lms_threads : 256, s));
+        RX_CK(launch_lms(a, c.lms_threads ? c.lms_threads : kSegThreads, s));
         ++nl;
     }
     {
@@ -469,6 +474,33 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
     h->frames += 1;
     h->sym_processed += 2 * (uint64_t)N;
     h->launches += nl;
+    return RX_OK;
+}
+
+rx_status rx_decide(rx_handle* h, const float* d_z, int64_t n_sym, const uint32_t* d_ref, uint32_t* d_out,
+                    rx_stream_t stream_) {
+    if (!h || !d_z || n_sym < 1 || n_sym > h->Nmax || h->cfg.streaming) return RX_EINVAL;
+    const rx_config& c = h->cfg;
+    cudaStream_t s = (cudaStream_t)stream_;
+    h->last = s;
+    const int64_t N = n_sym;
+    const float2* z = reinterpret_cast<const float2*>(d_z);
+    k_frame_begin<<<1, 1, 0, s>>>(h->st, 1, 0);
+    RX_CK(cudaGetLastError());
+    const int64_t words = (N * h->m + 31) / 32;
+    const int64_t lo = c.edge_skip, hi = std::max<int64_t>(N - c.edge_skip, lo);
+    int k = 0;
+    if (d_ref && hi > lo) {
+        StageScope sc(h, ST_SYNC, s);
+        RX_CK(launch_sync(z, N, d_ref, words, N, h->m, lo, std::min<int64_t>(lo + c.sync_len, hi), c.max_delay, 0,
+                          h->sync_counts, h->st, s, &k));
+    }
+    if (d_ref || d_out) {
+        StageScope sc(h, ST_COUNT, s);
+        RX_CK(launch_count(z, N, N, d_ref, words, N, h->m, lo, hi, 0, d_out, words, h->st, s));
+        ++k;
+    }
+    h->launches += k + 1;
     return RX_OK;
 }
 

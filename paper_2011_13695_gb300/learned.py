@@ -1,0 +1,177 @@
+"""Learned post-equaliser: a handle over the rx_pe_* C ABI and the training
+loop that drives it.
+
+The network (four 1-D convolutions 4->64->64->64->4, kernel 9, ReLU between,
+residual output z + f(z)) maps the carrier-recovered symbols z of both
+polarisations to corrected symbols. Its forward pass, MSE loss, backward pass
+and Adam update all run in librx's kernels (BF16 weights and activations,
+FP32 accumulation and master weights); this module only slices sequences,
+picks learning rates and counts steps. The paper has no learned equaliser.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import rx
+
+
+def he_init(channels: int = 64, kernel: int = 9, seed: int = 0, out_scale: float = 0.1) -> np.ndarray:
+    """Initial parameters in the flat layout of rx_pe (per layer: W [out][in][k], then b [out]):
+    He-normal weights (std sqrt(2 / (in * k))), zero biases, the last layer scaled by ``out_scale``
+    so that the network starts close to the identity z -> z."""
+    rng = np.random.default_rng(seed)
+    dims = [(4, channels), (channels, channels), (channels, channels), (channels, 4)]
+    parts = []
+    for li, (cin, cout) in enumerate(dims):
+        W = rng.normal(0.0, np.sqrt(2.0 / (cin * kernel)), size=(cout, cin, kernel))
+        if li == len(dims) - 1:
+            W *= out_scale
+        parts += [W.ravel(), np.zeros(cout)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+class PostEqualiser:
+    """One rx_pe handle on the current CUDA device."""
+
+    def __init__(self, max_len: int, params: np.ndarray | None = None, channels: int = 64, kernel: int = 9):
+        self.n_params = rx.rx_pe_param_count(channels, kernel)
+        if self.n_params < 0:
+            raise ValueError(f"unsupported post-equaliser shape channels={channels} kernel={kernel}")
+        if params is not None:
+            params = np.ascontiguousarray(params, dtype=np.float32)
+            if params.size != self.n_params:
+                raise ValueError(f"expected {self.n_params} parameters, got {params.size}")
+        self.max_len = max_len
+        self.h = rx.rx_pe_create(max_len, params, channels, kernel)
+
+    def close(self) -> None:
+        if self.h:
+            rx.rx_pe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        rx.rx_pe_params(self.h, out)
+        return out
+
+    @staticmethod
+    def _seq(z: torch.Tensor) -> tuple[int, int]:
+        if z.dtype != torch.complex64 or z.dim() != 2 or z.shape[0] != 2 or not z.is_contiguous() or not z.is_cuda:
+            raise ValueError("sequences are contiguous complex64 CUDA tensors of shape [2, T]")
+        return z.data_ptr(), z.shape[1]
+
+    def forward(self, z: torch.Tensor, out: torch.Tensor | None = None,
+                stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        pz, T = self._seq(z)
+        out = torch.empty_like(z) if out is None else out
+        s = stream or torch.cuda.current_stream()
+        rx.rx_pe_forward(self.h, pz, T, self._seq(out)[0], s.cuda_stream)
+        return out
+
+    def gradients(self, z: torch.Tensor, target: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+        pz, T = self._seq(z)
+        grads = torch.empty(self.n_params, dtype=torch.float32, device=z.device)
+        loss = torch.empty(1, dtype=torch.float32, device=z.device)
+        rx.rx_pe_gradients(self.h, pz, self._seq(target)[0], T, grads.data_ptr(), loss.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+        return grads, loss
+
+    def train_step(self, z: torch.Tensor, target: torch.Tensor, lr: float, loss_ptr: int | None = None,
+                   stream: torch.cuda.Stream | None = None) -> None:
+        pz, T = self._seq(z)
+        s = stream or torch.cuda.current_stream()
+        rx.rx_pe_train_step(self.h, pz, self._seq(target)[0], T, lr, loss_ptr, s.cuda_stream)
+
+    def train(self, z, target, lo: int, hi: int, steps: int, window: int,
+              lr: float = 1e-3, seed: int = 0, lr_final: float | None = None) -> torch.Tensor:
+        """``steps`` Adam steps, each on a contiguous slice [o, o + window) of one (z, target) pair with
+        o drawn uniformly from [lo, hi - window]; ``z`` and ``target`` are tensors or equally long lists of
+        tensors (one pair drawn uniformly per step). The learning rate decays geometrically to
+        ``lr_final`` when given. Returns the per-step losses (device tensor)."""
+        zs_all = z if isinstance(z, (list, tuple)) else [z]
+        ts_all = target if isinstance(target, (list, tuple)) else [target]
+        if len(zs_all) != len(ts_all) or not zs_all:
+            raise ValueError("z and target lists differ in length")
+        if hi - lo < window or window > self.max_len or any(hi > a.shape[1] for a in zs_all):
+            raise ValueError("training range shorter than one window, window above max_len, or range past the end")
+        rng = np.random.default_rng(seed)
+        which = rng.integers(0, len(zs_all), size=steps)
+        offs = rng.integers(lo, hi - window + 1, size=steps)
+        losses = torch.zeros(steps, dtype=torch.float32, device=zs_all[0].device)
+        ratio = 1.0 if lr_final is None else (lr_final / lr) ** (1.0 / max(steps - 1, 1))
+        for i in range(steps):
+            k, o = int(which[i]), int(offs[i])
+            zs = zs_all[k][:, o:o + window].contiguous()
+            ts = ts_all[k][:, o:o + window].contiguous()
+            self.train_step(zs, ts, lr * ratio ** i, losses.data_ptr() + 4 * i)
+        return losses
+
+
+def aligned_targets(stats: dict, symbols: torch.Tensor, n_sym: int) -> torch.Tensor:
+    """Transmitted symbols [2, n_ref] put in the frame of the receiver's outputs z [2, n_sym] using the
+    alignment found by the decision stage: z_q[n] j^r_q carries s_p_q[n + d_q] (single frames), so the
+    target of z_q[n] is s_p_q[n + d_q] (-j)^r_q. Positions without a transmitted symbol get 0."""
+    out = torch.zeros((2, n_sym), dtype=torch.complex64, device=symbols.device)
+    n_ref = symbols.shape[1]
+    for q in range(2):
+        p, r, d = stats["pol_map"][q], stats["rotation"][q], stats["delay"][q]
+        a, b = max(0, -d), min(n_sym, n_ref - d)
+        if b > a:
+            out[q, a:b] = symbols[p, a + d:b + d] * ((-1j) ** r)
+    return out
+
+
+def repair_quarter_turns(z: torch.Tensor, target: torch.Tensor, block: int = 1024) -> torch.Tensor:
+    """Targets with each block of ``block`` symbols turned by the quarter turn that best matches z.
+    A carrier-phase cycle slip of the chain turns all later outputs by a multiple of pi/2 relative to
+    the alignment found at the start of the frame; training labels follow the slip so that the
+    network is not taught to undo it. (Decisions of the chain itself are not changed.)"""
+    n = (z.shape[1] // block) * block
+    if n == 0:
+        return target
+    zb = z[:, :n].reshape(2, -1, block)
+    tb = target[:, :n].reshape(2, -1, block)
+    turns = torch.tensor([1, 1j, -1, -1j], dtype=torch.complex64, device=z.device)
+    err = torch.stack([(zb - tb * u).abs().square().sum(-1) for u in turns])
+    best = turns[err.argmin(0)]
+    out = target.clone()
+    out[:, :n] = (tb * best[..., None]).reshape(2, n)
+    return out
+
+
+def chain_pairs(rcv, x: torch.Tensor, n_sym: int, ref: torch.Tensor, symbols: torch.Tensor):
+    """Run the plain chain on one single frame and return (z, target, stats): the carrier-recovered
+    symbols, the transmitted symbols aligned to them (``aligned_targets``, then
+    ``repair_quarter_turns``) and the chain's statistics for this frame alone. ``rcv`` is a :class:`receiver.Receiver`; ``ref`` the packed transmitted bits
+    on the device; ``symbols`` the transmitted symbols (complex64 [2, n_ref]) on the device."""
+    before = rcv.stats()
+    rcv.process(x, n_sym, ref, None)
+    st = rcv.stats()
+    z = rcv.symbols(n_sym)
+    return z, repair_quarter_turns(z, aligned_targets(st, symbols, n_sym)), stats_delta(before, st)
+
+
+def stats_delta(before: dict, after: dict) -> dict:
+    """Counters accumulated between two rx_stats snapshots, with BER and EVM recomputed."""
+    d = {k: after[k] - before[k] for k in ("bits_counted", "bit_errors", "symbols_counted", "symbol_errors",
+                                           "evm_num", "evm_den")}
+    d["ber"] = d["bit_errors"] / d["bits_counted"] if d["bits_counted"] else float("nan")
+    d["evm"] = float(np.sqrt(d["evm_num"] / d["evm_den"])) if d["evm_den"] else float("nan")
+    for k in ("pol_map", "rotation", "delay", "sync_matches", "sync_len"):
+        d[k] = after[k]
+    return d
+
+
+def decide_stats(rcv, z: torch.Tensor, n_sym: int, ref: torch.Tensor) -> dict:
+    """Stage A6 on symbols z (e.g. the post-equaliser's output) through ``rcv``; its counts alone."""
+    before = rcv.stats()
+    rcv.decide(z, n_sym, ref, None)
+    return stats_delta(before, rcv.stats())

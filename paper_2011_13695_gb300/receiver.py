@@ -75,3 +75,15 @@ class Receiver:
         rx.rx_get_buffer(self.h, which, t.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
         torch.cuda.current_stream().synchronize()
         return t
+
+    def decide(self, z: torch.Tensor, n_sym: int, ref: torch.Tensor | None = None,
+               out: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None) -> None:
+        """Stage A6 alone on caller-supplied symbols z (complex64 [2, n_sym], contiguous)."""
+        s = stream or torch.cuda.current_stream()
+        rx.rx_decide(self.h, z.data_ptr(), n_sym, ref.data_ptr() if ref is not None else None,
+                     out.data_ptr() if out is not None else None, s.cuda_stream)
+
+    def symbols(self, n_sym: int) -> torch.Tensor:
+        """Carrier-recovered symbols z of the last single frame, complex64 [2, n_sym]."""
+        z = self.buffer(rx.RX_BUF_Z).view(2, -1)
+        return z[:, :n_sym].contiguous()

@@ -26,7 +26,9 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_reset", "rx_state_size", "rx_state_get", "rx_state_set", "rx_set_timing", "rx_stage_count",
            "rx_stage_name", "rx_stage_times", "rx_launch_count", "rx_destroy", "rx_strerror",
            "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
-           "rx_batch_launch_count", "rx_batch_destroy")
+           "rx_batch_launch_count", "rx_batch_destroy",
+           "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward", "rx_pe_gradients",
+           "rx_pe_train_step", "rx_pe_destroy")
 
 
 class rx_config(C.Structure):
@@ -98,6 +100,14 @@ def lib() -> C.CDLL:
             "rx_batch_stats": (i32, [vp, i32, C.POINTER(rx_stats_t)]),
             "rx_batch_launch_count": (u64, [vp]),
             "rx_batch_destroy": (None, [vp]),
+            "rx_decide": (i32, [vp, vp, i64, vp, vp, vp]),
+            "rx_pe_param_count": (i64, [i32, i32]),
+            "rx_pe_create": (i32, [i32, i32, i64, vp, C.POINTER(vp)]),
+            "rx_pe_params": (i32, [vp, vp]),
+            "rx_pe_forward": (i32, [vp, vp, i64, vp, vp]),
+            "rx_pe_gradients": (i32, [vp, vp, vp, i64, vp, vp, vp]),
+            "rx_pe_train_step": (i32, [vp, vp, vp, i64, C.c_float, vp, vp]),
+            "rx_pe_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,3 +263,43 @@ def rx_batch_launch_count(b: int) -> int:
 
 def rx_batch_destroy(b: int) -> None:
     lib().rx_batch_destroy(b)
+
+
+def rx_decide(h: int, d_z: int, n_sym: int, d_ref: int | None, d_out: int | None, stream: int | None) -> None:
+    _check(lib().rx_decide(h, d_z, n_sym, d_ref or None, d_out or None, stream or None), "rx_decide")
+
+
+def rx_pe_param_count(channels: int = 64, kernel: int = 9) -> int:
+    return int(lib().rx_pe_param_count(channels, kernel))
+
+
+def rx_pe_create(max_len: int, params=None, channels: int = 64, kernel: int = 9) -> int:
+    """params: host float32 array (contiguous) of rx_pe_param_count values, or None for zeros."""
+    p = C.c_void_p()
+    ptr = params.ctypes.data if params is not None else None
+    _check(lib().rx_pe_create(channels, kernel, max_len, ptr, C.byref(p)), "rx_pe_create")
+    return p.value
+
+
+def rx_pe_params(p: int, out) -> None:
+    _check(lib().rx_pe_params(p, out.ctypes.data), "rx_pe_params")
+
+
+def rx_pe_forward(p: int, d_z: int, T: int, d_out: int, stream: int | None) -> None:
+    _check(lib().rx_pe_forward(p, d_z, T, d_out, stream or None), "rx_pe_forward")
+
+
+def rx_pe_gradients(p: int, d_z: int, d_target: int, T: int, d_grads: int | None, d_loss: int | None,
+                    stream: int | None) -> None:
+    _check(lib().rx_pe_gradients(p, d_z, d_target, T, d_grads or None, d_loss or None, stream or None),
+           "rx_pe_gradients")
+
+
+def rx_pe_train_step(p: int, d_z: int, d_target: int, T: int, lr: float, d_loss: int | None,
+                     stream: int | None) -> None:
+    _check(lib().rx_pe_train_step(p, d_z, d_target, T, lr, d_loss or None, stream or None), "rx_pe_train_step")
+
+
+def rx_pe_destroy(p: int) -> None:
+    lib().rx_pe_destroy(p)
+

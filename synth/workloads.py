@@ -1,4 +1,4 @@
-"""The five synthetic workloads: link parameters plus receiver settings.
+"""The synthetic workloads: link parameters plus receiver settings.
 
 Each entry pairs a :class:`LinkParams` (what the channel does) with the
 receiver settings that process it (plain numbers mirroring the fields of the
@@ -62,6 +62,21 @@ def _qam64_48g_stream(n_frames=64, frame_sym=2**18) -> dict:
                        mu_cma=3e-4))
 
 
+def _qam16_32g_ssfm(n_sym=2**20, launch_dbm=4.0, train_frames=4) -> dict:
+    """Nonlinear link for the learned post-equaliser: 10 x 80 km SSMF simulated by split-step
+    Fourier (synth.ssfm), launch power 2..6 dBm; training frames and a test frame of different
+    seeds. The SNR comes from the amplifiers' noise (snr_db is unused). After 800 km a 64-block CMA
+    acquisition sometimes leaves one output unconverged; this link uses 128 blocks."""
+    from .ssfm import FibreLink
+    fibre = FibreLink(spans=10, span_km=80.0, launch_dbm=launch_dbm)
+    link = LinkParams(bits_per_sym=4, symbol_rate=32e9, n_sym=n_sym, length=fibre.spans * fibre.span_km * 1e3,
+                      linewidth=100e3, freq_offset=500e6, snr_db=None)
+    return dict(name="dp-16qam-32gbd-ssfm", link=link, fibre=fibre, train_frames=train_frames,
+                train_seeds=[1000 + i for i in range(train_frames)], test_seed=2000,
+                rx=_rx(link, fft_size=4096, n_taps=21, lms_block=128, bps_phases=64, bps_window=64,
+                       cma_blocks=128))
+
+
 def batch_channels(seed: int = 42, n_channels: int = 16) -> list[dict]:
     """Seeded per-channel draws of the 16-channel batch."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -85,6 +100,7 @@ WORKLOADS = {
     "dp-qpsk-25gbd": _qpsk_25g,
     "dp-16qam-32gbd": _qam16_32g,
     "dp-64qam-48gbd-stream": _qam64_48g_stream,
+    "dp-16qam-32gbd-ssfm": _qam16_32g_ssfm,
 }
 
 

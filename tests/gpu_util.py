@@ -76,3 +76,27 @@ def run_gpu_frames(rx_settings: dict, frames: list, refs: list | None = None, fm
         out.append(res)
     rcv.close()
     return out
+
+
+def kernel_precision_bits(z: np.ndarray, sync, m: int) -> np.ndarray:
+    """Packed output bits [2, words] of complex64 symbols z decided the way the decision kernel does:
+    each output's exact quarter turn, then the level rint(fma(u, 1/(2a), (L-1)/2)) in FP32 (a NaN
+    input clamps to level 0), then Gray bits. Near a decision boundary the FP32 rule and an FP64 one
+    can differ, so checks of the kernel's own demapping take its precision."""
+    from oracle import qam as oqam
+    L = 1 << (m // 2)
+    M = L * L
+    h = np.float64(np.float32(0.5 * np.sqrt(2.0 * (M - 1) / 3.0)))
+    hl = 0.5 * (L - 1)
+
+    def level(u):
+        v = (u.astype(np.float64) * h + hl).astype(np.float32)     # exact product, one FP32 rounding
+        v = np.where(np.isnan(v), 0.0, np.rint(v))
+        return np.clip(v, 0, L - 1).astype(np.int64)
+
+    rows = []
+    for q in range(2):
+        r = sync[q][1] if sync is not None else 0
+        zr = z[q].astype(np.complex64) * np.complex64(1j ** r)
+        rows.append(oqam.levels_to_bits(level(zr.real), level(zr.imag), m).reshape(-1))
+    return oqam.pack_words(np.stack(rows))

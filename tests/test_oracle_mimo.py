@@ -37,7 +37,7 @@ def test_dd_block_update_by_explicit_loops():
     x = 0.5 * (rng.normal(size=(2, 40)) + 1j * rng.normal(size=(2, 40)))
     h = mimo.identity_taps(T) + 0.05 * (rng.normal(size=(2, 2, T)) + 1j * rng.normal(size=(2, 2, T)))
     mu = 0.01
-    y, h2 = mimo._dd_blocks(x, h[None], np.arange(5, 5 + L)[None], m, mu, 0)
+    y, h2, _ = mimo._dd_blocks(x, h[None], np.arange(5, 5 + L)[None], m, mu, 0)
     c = 1
     ref_h = h.copy()
     for q in range(2):
@@ -141,3 +141,16 @@ def test_segment_schedule_costs_nothing():
     pth = theory.gray_qam_ber(4, 15.0)
     sigma = np.sqrt(pth * (1 - pth) / seg["bits"])
     assert abs(b1 - b2) < 3 * sigma * 1.5
+
+
+def test_decision_margin_by_brute_force():
+    """Distance to the nearest interior decision boundary, against a scan of all boundaries."""
+    rng = np.random.default_rng(5)
+    for m in (2, 4, 6):
+        L, a = qam.n_levels(m), qam.amp(m)
+        bounds = (2 * np.arange(1, L) - L) * a              # midpoints between adjacent levels
+        u = rng.uniform(-1.5, 1.5, size=(3, 50)) + 1j * rng.uniform(-1.5, 1.5, size=(3, 50))
+        got = mimo.decision_margin(u, m)
+        dist = lambda v: np.min(np.abs(v[..., None] - bounds), axis=-1)
+        want = np.minimum(dist(u.real), dist(u.imag)).min(axis=-1)
+        assert np.allclose(got, want, atol=1e-12)
