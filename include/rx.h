@@ -276,6 +276,32 @@ rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, in
                            rx_stream_t stream);
 void rx_pe_destroy(rx_pe* p);
 
+/*
+ * rx_carrier_recovery_static: stage A5 alone (blind phase search, integer
+ * unwrap, derotation) on one single frame of equalised symbols, for callers
+ * that cannot allocate device memory when they process data (a real-time
+ * ingest thread must not block in the CUDA allocator; some host frameworks
+ * give the library a fixed memory budget at load time). The paper has no
+ * counterpart: its kernels run inside a program that owns all its buffers.
+ *
+ * d_y: DEVICE float [2][n_sym][2] (I, Q) equalised symbols of the two
+ * polarisations; d_z: DEVICE float [2][n_sym][2] receives the carrier-
+ * recovered symbols; both owned by the caller. Same arithmetic and results
+ * as the z of rx_process for the same y, with no carried unwrap state.
+ * The working memory is one file-scope device array of RX_STATIC_MAX_SYMBOLS
+ * symbols per polarisation (about 2.6 MB) that every device loading the
+ * library keeps until the process exits; the function allocates nothing.
+ * Its first call on a device looks up that array's device address (make it
+ * before any stream capture). Every call shares the array: calls that
+ * overlap on the GPU (other streams, other threads) race with each other.
+ * RX_EINVAL for n_sym < 1, n_sym > RX_STATIC_MAX_SYMBOLS or invalid BPS
+ * parameters (bps_phases 2..64, bps_window a power of two 2..64).
+ * Asynchronous on `stream`.
+ */
+#define RX_STATIC_MAX_SYMBOLS 262144
+rx_status rx_carrier_recovery_static(const float* d_y, int64_t n_sym, int32_t bits_per_sym, int32_t bps_phases,
+                                     int32_t bps_window, float* d_z, rx_stream_t stream);
+
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);
 

@@ -26,9 +26,10 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_reset", "rx_state_size", "rx_state_get", "rx_state_set", "rx_set_timing", "rx_stage_count",
            "rx_stage_name", "rx_stage_times", "rx_launch_count", "rx_destroy", "rx_strerror",
            "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
-           "rx_batch_launch_count", "rx_batch_destroy",
+           "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward", "rx_pe_gradients",
            "rx_pe_train_step", "rx_pe_destroy")
+RX_STATIC_MAX_SYMBOLS = 262144
 
 
 class rx_config(C.Structure):
@@ -100,6 +101,7 @@ def lib() -> C.CDLL:
             "rx_batch_stats": (i32, [vp, i32, C.POINTER(rx_stats_t)]),
             "rx_batch_launch_count": (u64, [vp]),
             "rx_batch_destroy": (None, [vp]),
+            "rx_carrier_recovery_static": (i32, [vp, i64, i32, i32, i32, vp, vp]),
             "rx_decide": (i32, [vp, vp, i64, vp, vp, vp]),
             "rx_pe_param_count": (i64, [i32, i32]),
             "rx_pe_create": (i32, [i32, i32, i64, vp, C.POINTER(vp)]),
@@ -303,3 +305,9 @@ def rx_pe_train_step(p: int, d_z: int, d_target: int, T: int, lr: float, d_loss:
 def rx_pe_destroy(p: int) -> None:
     lib().rx_pe_destroy(p)
 
+
+def rx_carrier_recovery_static(d_y: int, n_sym: int, bits_per_sym: int, bps_phases: int, bps_window: int, d_z: int,
+                               stream: int | None) -> None:
+    """Carrier recovery with the library's fixed device scratch (no allocation); see include/rx.h."""
+    _check(lib().rx_carrier_recovery_static(d_y, n_sym, bits_per_sym, bps_phases, bps_window, d_z, stream or None),
+           "rx_carrier_recovery_static")
