@@ -186,29 +186,65 @@ class ClockSampler:
 # roofline of a stage
 # --------------------------------------------------------------------------------------
 
+# DRAM traffic per launch from one ncu capture (profiles/), valid while the kernel's source file is
+# unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
+PROFILED_TRAFFIC = {}
+
+
+def _traffic(stage: str):
+    import hashlib
+    rec = PROFILED_TRAFFIC.get(stage)
+    if not rec:
+        return None
+    path = os.path.join(ROOT, "paper_2011_13695_gb300", "csrc", rec[0])
+    try:
+        sha = hashlib.sha1(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec[2] if sha == rec[1] else None
+
+
 def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz: float | None) -> dict:
+    """Roofline of one stage's dominant kernel: algorithmic work of one launch over its duration.
+
+    FP32 arithmetic is counted in flops (an FMA is 2) against the FMA pipes' peak (152 SMs x 128
+    lanes x 2 flops x max SM clock); BPS, whose work is compare/round/select as much as FMA, in
+    lane-operations against 152 x 128 x clock; HBM-bound stages in compulsory bytes against the
+    measured copy bandwidth."""
     rxs = w["rx"]
     m = rxs["bits_per_sym"]
+    T, Lb = rxs["n_taps"], rxs["lms_block"]
     clock_mhz = pk.get("sm_max_mhz", 2070.0)
-    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12      # Tops/s, 1 op per lane per clock
+    lanes = SM_COUNT_GB300 * FP32_LANES_PER_SM * clock_mhz * 1e6
     t = ms * 1e-3
+    lms_flops_per_symbol = 2 * (16 * T + 16 * T)          # 2 rows x (outputs + gradient), 2T complex MACs each
+    alu = {
+        # serial block recursions: one CTA per output row, blocks one after another
+        "cma": ("k_lms (CMA acquisition, serial blocks)", rxs["cma_blocks"] * Lb * lms_flops_per_symbol),
+        "dd_acq": ("k_lms (DD acquisition, serial blocks)", rxs["dd_acq_blocks"] * Lb * lms_flops_per_symbol),
+        "lms": ("k_lms (segmented DD-LMS)",
+                n_sym * (1 + rxs["warmup_blocks"] / rxs["seg_blocks"]) * lms_flops_per_symbol),
+    }
+    if stage in alu:
+        name, flops = alu[stage]
+        peak = 2 * lanes / 1e12
+        a = flops / t / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "traffic": _traffic(stage), "algorithmic_flops": flops,
+                "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"}
     if stage == "bps":
-        ops = 2 * n_sym * rxs["bps_phases"] * 16          # FP32 ops per (symbol, test phase)
+        ops = 2 * n_sym * rxs["bps_phases"] * 16          # lane-ops per (symbol, test phase)
+        peak = lanes / 1e12
         a = ops / t / 1e12
-        return {"kernel": "k_bps", "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": None, "algorithmic_ops": ops}
-    if stage == "lms":
-        ops = n_sym * 32 * rxs["n_taps"]                  # FMA per output symbol pair: outputs + gradient
-        a = ops / t / 1e12
-        return {"kernel": "k_lms", "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": None, "algorithmic_ops": ops}
-    # HBM-bound stages: compulsory bytes
-    byts = {"cdc": 2 * (2 * n_sym) * 8 * 2, "unwrap": 2 * n_sym * (8 + 1 + 8 + 4),
-            "count": 2 * n_sym * 8 + 2 * 2 * n_sym * m / 8}.get(stage, 0)
+        return {"kernel": "k_bps", "bound": "alu", "achieved": a, "peak": peak, "unit": "Tops/s",
+                "frac": a / peak, "traffic": _traffic(stage), "algorithmic_ops": ops,
+                "peak_note": "152 SMs x 128 lanes x max SM clock"}
+    byts = {"cdc": 2 * (2 * n_sym) * 8 * 2, "power": 2 * (2 * n_sym) * 8, "unwrap": 2 * n_sym * (8 + 1 + 8 + 4),
+            "count": 2 * n_sym * 8 + 2 * 2 * n_sym * m / 8, "sync": 0, "foe": 0}.get(stage, 0)
     a = byts / t / 1e9 if t > 0 else 0.0
     peak = pk.get("hbm_gbs", 6800.0)
     return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
-            "traffic": None, "algorithmic_bytes": byts}
+            "traffic": _traffic(stage), "algorithmic_bytes": byts}
 
 
 # --------------------------------------------------------------------------------------

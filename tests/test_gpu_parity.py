@@ -121,11 +121,12 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, he
     yok = check_y(g, r, cfg, tol_y)
     # In a stream's first frame the start-up transient (no signal yet) makes b* arbitrary, so the
     # integer unwrap count may settle on a different whole number of quarter turns; that is the
-    # same quarter-turn ambiguity the alignment resolves. Compare z after removing that constant.
+    # same quarter-turn ambiguity the alignment resolves, and the unwrap carries it into every
+    # later frame of the stream. Compare z after removing that constant.
     dm = np.zeros(2, dtype=np.int64)
-    if head:
-        for q in range(2):
-            vals, cnt = np.unique((g["m"][q, head:] - r.m[q, head:]), return_counts=True)
+    for q in range(2):
+        vals, cnt = np.unique((g["m"][q, head:] - r.m[q, head:]), return_counts=True)
+        if len(vals):
             dm[q] = vals[np.argmax(cnt)]
     m_agree = (g["m"] - r.m) == dm[:, None]
     agree = check_bstar(g, r, cfg, head, skip=~yok) & m_agree & yok
