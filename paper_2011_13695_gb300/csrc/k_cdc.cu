@@ -33,18 +33,19 @@ __device__ __forceinline__ float2 load_sample(const void* in, int64_t idx, float
     }
 }
 
-// A0: mean power of the first n_win samples of each polarisation (FP64 sums).
+// A0: mean power of the first n_win samples of each polarisation: FP32 sums per thread and warp
+// (a few dozen samples each), FP64 across warps.
 template <int FMT>
 __global__ void k_power(const void* in, float in_scale, int64_t S, int64_t n_win, RxDevState* st) {
     const int p = blockIdx.x;
-    double acc = 0.0;
+    float acc = 0.0f;
     for (int64_t i = threadIdx.x; i < n_win; i += blockDim.x) {
         float2 v = load_sample<FMT>(in, (int64_t)p * S + i, in_scale);
-        acc += (double)v.x * v.x + (double)v.y * v.y;
+        acc += cabs2(v);
     }
     __shared__ double red[32];
-    acc = warp_sum_d(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)acc;
     __syncthreads();
     if (threadIdx.x < 32) {
         double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;

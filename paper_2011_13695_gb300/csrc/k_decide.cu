@@ -49,14 +49,20 @@ __device__ __forceinline__ void bits_to_levels(uint32_t sbits, int m, int& li, i
     lq = gray_to_level(msb & ((1u << h) - 1u));
 }
 
+// blockIdx.x: (output q, tx pol p, turn r); blockIdx.y: slice of the sync window. Match counts of
+// the slice for every delay are added into counts (zeroed by k_sync_pick after it reads them).
 __global__ void k_sync(const float2* __restrict__ z, int64_t zstride, const uint32_t* __restrict__ ref,
                        int64_t refstride, int64_t n_ref, int m, int64_t lo, int64_t hi, int D, int64_t lat,
-                       int* counts) {
+                       int64_t slice, int* counts) {
     const int q = blockIdx.x >> 3, p = (blockIdx.x >> 2) & 1, r = blockIdx.x & 3;
-    extern __shared__ int16_t txl[];                  // tx levels for t in [lo - lat - D, hi - lat + D)
+    const int64_t s0 = lo + (int64_t)blockIdx.y * slice;
+    const int64_t s1 = min(hi, s0 + slice);
+    extern __shared__ int16_t txl[];                  // tx levels for t in [s0 - lat - D, s1 - lat + D)
     __shared__ int cnt[2 * RX_MAX_DELAY + 1];
-    const int64_t t0 = lo - lat - D;
-    const int64_t nt = (hi - lo) + 2 * D;
+    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) cnt[i] = 0;
+    if (s0 >= s1) return;
+    const int64_t t0 = s0 - lat - D;
+    const int64_t nt = (s1 - s0) + 2 * D;
     const uint32_t* rp = ref + (int64_t)p * refstride;
     for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) {
         const int64_t t = t0 + i;
@@ -68,45 +74,56 @@ __global__ void k_sync(const float2* __restrict__ z, int64_t zstride, const uint
         }
         txl[i] = v;
     }
-    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     const Qam qm = make_qam(m);
     const int lane = threadIdx.x & 31;
-    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+    for (int64_t base = s0 + (threadIdx.x & ~31); base < s1; base += blockDim.x) {
         const int64_t n = base + lane;
         int16_t mine = -2;
-        if (n < hi) {
+        if (n < s1) {
             const float2 v = quarter(z[(int64_t)q * zstride + n], r);
             mine = (int16_t)(qam_level(v.x, qm) | (qam_level(v.y, qm) << 8));
         }
         for (int d = -D; d <= D; ++d) {
-            const bool hit = (n < hi) && (txl[n - lo + D + d] == mine);
+            const bool hit = (n < s1) && (txl[n - s0 + D + d] == mine);
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
             if (lane == 0 && bal) atomicAdd(&cnt[d + D], __popc(bal));
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) counts[blockIdx.x * (2 * D + 1) + i] = cnt[i];
+    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x)
+        if (cnt[i]) atomicAdd(&counts[blockIdx.x * (2 * D + 1) + i], cnt[i]);
 }
 
-__global__ void k_sync_pick(const int* counts, int D, int64_t len, RxDevState* st) {
-    if (threadIdx.x != 0) return;
-    for (int q = 0; q < 2; ++q) {
-        int bp = 0, br = 0, bd = -D, bm = -1;
-        for (int p = 0; p < 2; ++p)
-            for (int r = 0; r < 4; ++r)
-                for (int d = -D; d <= D; ++d) {
-                    const int v = counts[((q * 2 + p) * 4 + r) * (2 * D + 1) + d + D];
-                    if (v > bm) { bm = v; bp = p; br = r; bd = d; }
-                }
-        st->sync_p[q] = bp;
-        st->sync_r[q] = br;
-        st->sync_d[q] = bd;
-        st->sync_match[q] = bm;
-        if ((double)bm < 0.9 * (double)len) atomicOr(&st->err_word, 2u);
+// One warp per output q: the (p, r, d) with most matches, ties to the smallest tuple (p, then r,
+// then d). The warp then zeroes the counts it read for the next sync.
+__global__ void k_sync_pick(int* counts, int D, int64_t len, RxDevState* st) {
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;     // launched with 64 threads
+    const int nd = 2 * D + 1, ntup = 8 * nd;
+    int* cq = counts + (int64_t)q * ntup;             // tuple index t = (p * 4 + r) * nd + (d + D)
+    int bv = -1, bt = 0;
+    for (int t = lane; t < ntup; t += 32) {
+        const int v = cq[t];
+        if (v > bv) { bv = v; bt = t; }               // t increases along the lane's scan
     }
-    st->sync_len = (int)len;
-    st->sync_valid = 1;
+    for (int o = 16; o > 0; o >>= 1) {
+        const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        if (ov > bv || (ov == bv && ot < bt)) { bv = ov; bt = ot; }
+    }
+    __syncwarp();
+    for (int t = lane; t < ntup; t += 32) cq[t] = 0;
+    if (lane == 0) {
+        const int pr = bt / nd;
+        st->sync_p[q] = pr >> 2;
+        st->sync_r[q] = pr & 3;
+        st->sync_d[q] = bt - pr * nd - D;
+        st->sync_match[q] = bv;
+        if (10LL * bv < 9LL * len) atomicOr(&st->err_word, 2u);
+        if (q == 0) st->sync_len = (int)len;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->sync_valid = 1;
 }
 
 // Grid-stride over the symbols of one output polarisation; counters stay in
@@ -124,7 +141,9 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
     const int64_t nwords = (N * m + 31) / 32;
     const uint32_t* refp = have_sync ? ref + (int64_t)p * refstride : nullptr;
     uint32_t errs = 0, serr = 0, cnt = 0;
-    double en = 0.0, ed = 0.0;
+    // EVM sums: FP32 per thread (a handful of symbols each) and per warp, FP64 from the CTA level
+    // on (FP64 arithmetic runs at a small fraction of the FP32 rate on this part)
+    float en = 0.0f, ed = 0.0f;
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n - lane < N; n += step) {
         uint32_t sbits = 0;
@@ -159,8 +178,8 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
                 int ti, tq;
                 bits_to_levels(rb, m, ti, tq);
                 const float2 s = make_float2(qam_value(ti, qm), qam_value(tq, qm));
-                en += (double)cabs2(csub(v, s));
-                ed += (double)cabs2(s);
+                en += cabs2(csub(v, s));
+                ed += cabs2(s);
             }
         }
     }
@@ -170,12 +189,12 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
     errs = __reduce_add_sync(0xffffffffu, errs);
     serr = __reduce_add_sync(0xffffffffu, serr);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
-    en = warp_sum_d(en);
-    ed = warp_sum_d(ed);
+    en = warp_sum(en);
+    ed = warp_sum(ed);
     const int w = threadIdx.x >> 5;
     if (lane == 0) {
         ri[0][w] = errs; ri[1][w] = serr; ri[2][w] = cnt;
-        rd[0][w] = en; rd[1][w] = ed;
+        rd[0][w] = (double)en; rd[1][w] = (double)ed;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -200,15 +219,19 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
 cudaError_t launch_sync(const float2* z, int64_t zstride, const uint32_t* ref, int64_t refstride, int64_t n_ref,
                         int m, int64_t lo, int64_t hi, int max_delay, int64_t lat, int* counts, RxDevState* st,
                         cudaStream_t s, int* nlaunch) {
-    const int64_t nt = (hi - lo) + 2 * max_delay;
-    const size_t smem = sizeof(int16_t) * (size_t)nt;
+    // 16 (q, p, r) combinations x up to 16 slices of at least 256 symbols
+    const int64_t len = hi - lo;
+    const int nsl = (int)std::max<int64_t>(1, std::min<int64_t>(16, len / 256));
+    const int64_t slice = (len + nsl - 1) / nsl;
+    const size_t smem = sizeof(int16_t) * (size_t)(slice + 2 * max_delay);
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
         cudaFuncSetAttribute(k_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_sync<<<16, 256, smem, s>>>(z, zstride, ref, refstride, n_ref, m, lo, hi, max_delay, lat, counts);
-    k_sync_pick<<<1, 32, 0, s>>>(counts, max_delay, hi - lo, st);
+    k_sync<<<dim3(16, nsl), 256, smem, s>>>(z, zstride, ref, refstride, n_ref, m, lo, hi, max_delay, lat, slice,
+                                           counts);
+    k_sync_pick<<<1, 64, 0, s>>>(counts, max_delay, len, st);
     if (nlaunch) *nlaunch += 2;
     return cudaGetLastError();
 }

@@ -35,6 +35,7 @@ struct LmsCtx {
     float2* es;      // [Lb]
     float2* part;    // [G][2T]
     float2* rot;     // e^{-j psi}
+    float2* tab;     // NCO derotation of window offset jj: exp(-j 2 pi frac(inc jj)), jj < 2 Lb + T - 1
     int XS, G, logP, logR;
     // output lanes: polarisation-0 taps [ka0, ka1), polarisation-1 taps [kb0, kb1)
     int ka0, ka1, kb0, kb1;
@@ -69,13 +70,15 @@ __device__ __forceinline__ void lms_commit(const LmsArgs& a, LmsCtx<NT>& s, floa
     const int c = (a.T - 1) >> 1;
     const int XW = 2 * L + a.T - 1;
     const long long g0 = a.g0 + a.off + 2 * n0 - c;
+    // exp(-j 2 pi frac(inc (g0 + jj))) = exp(-j 2 pi frac(inc g0)) exp(-j 2 pi frac(inc jj)) (mod one turn)
+    const float2 base = inc ? nco_conj(inc, g0) : make_float2(1.0f, 0.0f);
 #pragma unroll
     for (int r = 0; r < LmsCtx<NT>::PF; ++r) {
         const int t = threadIdx.x + r * NT;
         if (t < 2 * XW) {
             const int p = t >= XW ? 1 : 0, jj = t - p * XW;
             float2 v = s.pf[r];
-            if (inc) v = cmul(v, nco_conj(inc, g0 + jj));
+            if (inc) v = cmul(v, cmul(base, s.tab[jj]));
             xs[p * s.XS + jj] = v;
         }
     }
@@ -135,12 +138,7 @@ __device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const
             }
             acc.x = warp_sum(acc.x);
             acc.y = warp_sum(acc.y);
-            if (tid == 0) {
-                const float psi = 0.25f * atan2f(-acc.y, -acc.x);
-                float sn, cs;
-                sincosf(psi, &sn, &cs);
-                s.rot[0] = make_float2(cs, -sn);
-            }
+            if (tid == 0) s.rot[0] = quarter_root_conj(make_float2(-acc.x, -acc.y));
         }
         __syncthreads();
         const float2 r = s.rot[0];
@@ -204,6 +202,7 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
     s.es = s.ys + Lb;
     s.part = s.es + Lb;
     s.rot = s.part + s.G * 2 * T;
+    s.tab = s.rot + 1;
     {
         // output lane j of a group takes the flattened terms u in [j cs, (j + 1) cs), u = p T + k
         const int P = 1 << logP, j = tid & (P - 1);
@@ -225,6 +224,9 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
     const int64_t nseg = gridDim.x;
     const long long inc = a.derotate ? a.st->nco_inc : 0;
     for (int t = tid; t < 2 * T; t += NT) s.taps[t] = a.taps_in[q * 2 * T + t];
+    if (inc)
+        for (int jj = tid; jj < 2 * Lb + T - 1; jj += NT) s.tab[jj] = nco_conj(inc, jj);
+    __syncthreads();
     const int64_t start = seg * a.L_seg;
     const int64_t end = min(a.n_sym, start + a.L_seg);
     const int nwarm = seg > 0 ? a.n_wu : 0;
@@ -327,12 +329,13 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
     }
     __syncthreads();
     const int kappa = s_kappa;
-    // a_j = sum_q sum_{n in block j} (y_q[n] e^{-j w_c n})^4, w_c = 2 pi kappa / (4 nf); one warp per block
-    const int nb = (int)(nw / Lb);
+    // a_j = sum_q sum_{n in block j} (y_q[n] e^{-j w_c n})^4, w_c = 2 pi kappa / (4 nf); one warp per
+    // block, FP32 sums (2 Lb terms of order one), then arg(a_j) in FP64 by one thread per block
+    const int nb = min((int)(nw / Lb), 1024);
     const int w = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
     const long long period = 4LL * nf;
     for (int j = w; j < nb; j += nwarp) {
-        double ax = 0.0, ay = 0.0;
+        float ax = 0.0f, ay = 0.0f;
         for (int q = 0; q < 2; ++q) {
             for (int n = j * Lb + lane; n < (j + 1) * Lb; n += 32) {
                 long long r = ((long long)kappa * n) % period;
@@ -346,20 +349,23 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
                 ay += v4.y;
             }
         }
-        ax = warp_sum_d(ax);
-        ay = warp_sum_d(ay);
-        if (lane == 0) s_a[j] = make_double2(ax, ay);
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        if (lane == 0) s_a[j] = make_double2((double)ax, (double)ay);
     }
+    __syncthreads();
+    for (int j = tid; j < nb; j += nthr) s_a[j].x = atan2(s_a[j].y, s_a[j].x);
     __syncthreads();
     if (tid == 0) {
         const double PI = 3.14159265358979323846;
         const double wc = 2.0 * PI * (double)kappa / (4.0 * nf);
         double wf = 0.0;
         if (nb >= 2) {
-            double prev = atan2(s_a[0].y, s_a[0].x), shift = 0.0;
+            // unwrap the block phases and fit their slope by least squares
+            double prev = s_a[0].x, shift = 0.0;
             double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
             for (int j = 0; j < nb; ++j) {
-                double ph = atan2(s_a[j].y, s_a[j].x);
+                double ph = s_a[j].x;
                 if (j > 0) {
                     const double d = (ph + shift) - prev;
                     if (d > PI) shift -= 2.0 * PI;
@@ -399,8 +405,9 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
 }
 
 // max over |d| <= c of |rho_d| between the two CMA outputs (second half of
-// y_acq): one warp per lag, FP32 lane sums, warp-shuffle combine (a threshold
-// test at 0.5 needs no more precision).
+// y_acq). One CTA per lag d plus one for the two energies, FP32 sums (a
+// threshold test at 0.5 needs no more precision); the CTA that finishes last
+// (a counter in flag[1], reset by it) combines the partials in flag[2 ...].
 __global__ void k_cma_check(const float2* __restrict__ yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st,
                             int* flag, int pass) {
     if (pass == 1 && *flag == 0) return;
@@ -408,44 +415,57 @@ __global__ void k_cma_check(const float2* __restrict__ yacq, int64_t ystride, in
     const int L = (int)(nacq - h0);
     const float2* y0 = yacq + h0;
     const float2* y1 = yacq + ystride + h0;
-    const int maxlag = (T - 1) / 2;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    __shared__ float s_r[64];
-    __shared__ float s_e[32][2];
-    float e0 = 0.0f, e1 = 0.0f;
-    for (int n = tid; n < L; n += blockDim.x) {
-        e0 += cabs2(y0[n]);
-        e1 += cabs2(y1[n]);
-    }
-    e0 = warp_sum(e0);
-    e1 = warp_sum(e1);
-    if (lane == 0) { s_e[w][0] = e0; s_e[w][1] = e1; }
-    for (int d = w - maxlag; d <= maxlag; d += (int)(blockDim.x >> 5)) {
+    const int maxlag = (T - 1) / 2, nlag = 2 * maxlag + 1;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    float* part = reinterpret_cast<float*>(flag + 2);
+    __shared__ float s_x[32], s_y[32];
+    __shared__ bool s_last;
+    float sx = 0.0f, sy = 0.0f;
+    if ((int)blockIdx.x < nlag) {
+        const int d = (int)blockIdx.x - maxlag;
         const int a0 = d < 0 ? -d : 0, a1 = L - (d > 0 ? d : 0);
-        float sx = 0.0f, sy = 0.0f;
-        for (int n = a0 + lane; n < a1; n += 32) {
+        for (int n = a0 + tid; n < a1; n += blockDim.x) {
             const float2 v = cmulc(y0[n], y1[n + d]);
             sx += v.x;
             sy += v.y;
         }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) s_r[d + maxlag] = sqrtf(sx * sx + sy * sy);
+    } else {
+        for (int n = tid; n < L; n += blockDim.x) {
+            sx += cabs2(y0[n]);
+            sy += cabs2(y1[n]);
+        }
     }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) { s_x[w] = sx; s_y[w] = sy; }
     __syncthreads();
     if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += s_e[k][0]; b += s_e[k][1]; }
-        const double den = sqrt(a * b);
-        double best = 0.0;
-        for (int d = 0; d <= 2 * maxlag; ++d) best = fmax(best, den > 0.0 ? s_r[d] / den : 0.0);
-        if (pass == 0) {
-            *flag = best > 0.5 ? 1 : 0;
-            st->cma_rho = (float)best;
-            st->cma_reran = 0;
-        } else if (best > 0.5) {
-            atomicOr(&st->err_word, 4u);
+        float ax = 0.0f, ay = 0.0f;
+        for (int k = 0; k < nw; ++k) { ax += s_x[k]; ay += s_y[k]; }
+        if ((int)blockIdx.x < nlag) {
+            part[blockIdx.x] = sqrtf(ax * ax + ay * ay);
+        } else {
+            part[nlag] = ax;
+            part[nlag + 1] = ay;
         }
+        __threadfence();
+        const unsigned done = atomicAdd(reinterpret_cast<unsigned*>(flag + 1), 1u);
+        s_last = done == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || tid != 0) return;
+    __threadfence();
+    const volatile float* vp = part;
+    const double den = sqrt((double)vp[nlag] * (double)vp[nlag + 1]);
+    double best = 0.0;
+    for (int k = 0; k < nlag; ++k) best = fmax(best, den > 0.0 ? (double)vp[k] / den : 0.0);
+    flag[1] = 0;
+    if (pass == 0) {
+        *flag = best > 0.5 ? 1 : 0;
+        st->cma_rho = (float)best;
+        st->cma_reran = 0;
+    } else if (best > 0.5) {
+        atomicOr(&st->err_word, 4u);
     }
 }
 
@@ -469,7 +489,7 @@ __global__ void k_cma_rebuild(RxDevState* st, int T, const int* flag) {
 int64_t lms_smem_bytes(int T, int Lb, int threads) {
     const int XS = 2 * Lb + T;
     const int G = threads / (2 * T) > 1 ? threads / (2 * T) : 1;
-    return (int64_t)sizeof(float2) * (2 * T + 4 * XS + 2 * Lb + G * 2 * T + 1);
+    return (int64_t)sizeof(float2) * (2 * T + 4 * XS + 2 * Lb + G * 2 * T + 1 + (2 * Lb + T - 1));
 }
 
 template <int NT>
@@ -535,7 +555,8 @@ cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw
 
 cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st, int* flag,
                              int pass, cudaStream_t s) {
-    k_cma_check<<<1, 1024, 0, s>>>(yacq, ystride, nacq, T, st, flag, pass);
+    const int nlag = 2 * ((T - 1) / 2) + 1;
+    k_cma_check<<<nlag + 1, 256, 0, s>>>(yacq, ystride, nacq, T, st, flag, pass);   // lags |d| <= c, energies
     return cudaGetLastError();
 }
 

@@ -121,6 +121,31 @@ __device__ __forceinline__ float2 nco_conj(long long inc, long long g) {
     return make_float2(c, -s);
 }
 
+// Principal square root of a unit complex number (c, s), arg in (-pi, pi] -> arg / 2 in (-pi/2, pi/2],
+// in the cancellation-free form for either sign of c.
+__device__ __forceinline__ float2 unit_sqrt(float2 u) {
+    if (u.x >= 0.0f) {
+        const float t = sqrtf(0.5f * (1.0f + u.x));
+        return make_float2(t, u.y / (2.0f * t));
+    }
+    const float t = sqrtf(0.5f * (1.0f - u.x));
+    return make_float2(fabsf(u.y) / (2.0f * t), copysignf(t, u.y));
+}
+
+// exp(-j psi) with psi = arg(w) / 4, arg in (-pi, pi]: the conjugate of the principal fourth root of
+// w / |w|, as two principal square roots. A zero w takes atan2's signed-zero arguments (0 for
+// x = +0, +-pi for x = -0 by the sign of y).
+__device__ __forceinline__ float2 quarter_root_conj(float2 w) {
+    const float n2 = cabs2(w);
+    if (!(n2 > 0.0f)) {
+        if (!signbit(w.x)) return make_float2(1.0f, 0.0f);
+        return make_float2(0.70710678118654752f, signbit(w.y) ? 0.70710678118654752f : -0.70710678118654752f);
+    }
+    const float inv = rsqrtf(n2);
+    const float2 r = unit_sqrt(unit_sqrt(make_float2(w.x * inv, w.y * inv)));
+    return make_float2(r.x, -r.y);
+}
+
 // block-wide helpers
 __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -7,7 +7,10 @@
 // come first and one radix-2/4/8 pass last when K is not a multiple of 4.
 // N/16 threads take part; each holds 16 points between passes. Shared memory
 // holds one padded copy (index i stored at i + i/16) and every pass reads
-// all points into registers before any thread overwrites them. The first
+// all points into registers before any thread overwrites them. A radix-16
+// pass reads two twiddles of the table (W^k and W^4k) and forms the other
+// thirteen by complex products (at most four roundings deep), instead of
+// fifteen scattered table reads. The first
 // pass can read through a functor (from global memory) and the last can
 // write through one (to global memory), so the transform costs no extra
 // global round trip.
@@ -115,11 +118,28 @@ __device__ __forceinline__ void fft_pass(float2* sm, int Ns, const float2* __res
             const int k = j & (Ns - 1);
             if (Ns > 1) {
                 const int step = (RX_FFT_TW_N / (Ns * R)) * k;
+                if constexpr (R == 16) {
+                    float2 w[16];
+                    w[1] = __ldg(&tw[step]);
+                    w[4] = __ldg(&tw[4 * step]);
+                    if (DIR > 0) { w[1].y = -w[1].y; w[4].y = -w[4].y; }
+                    w[2] = cmul(w[1], w[1]);
+                    w[3] = cmul(w[2], w[1]);
+                    w[5] = cmul(w[4], w[1]);
+                    w[6] = cmul(w[4], w[2]);
+                    w[7] = cmul(w[4], w[3]);
+                    w[8] = cmul(w[4], w[4]);
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[step * r]);
-                    if (DIR > 0) w.y = -w.y;
-                    v[b][r] = cmul(v[b][r], w);
+                    for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+                    for (int r = 1; r < 16; ++r) v[b][r] = cmul(v[b][r], w[r]);
+                } else {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        float2 w = __ldg(&tw[step * r]);
+                        if (DIR > 0) w.y = -w.y;
+                        v[b][r] = cmul(v[b][r], w);
+                    }
                 }
             }
             dftR<R, DIR>(v[b]);

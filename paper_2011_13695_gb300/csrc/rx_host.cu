@@ -264,7 +264,7 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(dalloc(&h->yfoe, 2 * h->nw));
     A(dalloc(&h->pgram, 2 * (size_t)nf));
     A(dalloc(&h->sync_counts, 16 * (2 * RX_MAX_DELAY + 1)));
-    A(dalloc(&h->flag, 1));
+    A(dalloc(&h->flag, 64));            // [0] CMA rerun flag, [1] check counter, [2..] check partials
     A(dalloc(&h->taps_id, 4 * RX_TMAX));
     A(dalloc(&h->st, 1));
     A(cudaMalloc(&h->stage_in, (size_t)(2 * h->Smax * h->in_elem)));
@@ -288,6 +288,9 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaMemset(h->st, 0, sizeof(RxDevState)));
     A(cudaMemset(h->cdc, 0, sizeof(float2) * 2 * h->cap));
     A(cudaMemset(h->tail, 0, sizeof(float2) * 2 * h->hop));
+    // counters that kernels accumulate into and reset after use must start at zero
+    A(cudaMemset(h->sync_counts, 0, sizeof(int) * 16 * (2 * RX_MAX_DELAY + 1)));
+    A(cudaMemset(h->flag, 0, sizeof(int) * 64));
     k_state_init<<<1, 1, 0, s0>>>(h->st);
     k_identity_taps<<<1, 256, 0, s0>>>(h->taps_id, h->T);
     A(cudaGetLastError());
@@ -620,6 +623,8 @@ rx_status rx_reset(rx_handle* h) {
     RX_CK(cudaMemset(h->st, 0, sizeof(RxDevState)));
     RX_CK(cudaMemset(h->tail, 0, sizeof(float2) * 2 * h->hop));
     RX_CK(cudaMemset(h->cdc, 0, sizeof(float2) * 2 * h->cap));
+    RX_CK(cudaMemset(h->sync_counts, 0, sizeof(int) * 16 * (2 * RX_MAX_DELAY + 1)));
+    RX_CK(cudaMemset(h->flag, 0, sizeof(int) * 64));
     k_state_init<<<1, 1>>>(h->st);
     RX_CK(cudaGetLastError());
     RX_CK(cudaDeviceSynchronize());
