@@ -1,0 +1,15 @@
+// Compile-time-shape block LMS: tap counts 25..31 with 128-symbol blocks.
+#include "k_lms_fast.cuh"
+
+template <int T, int LB>
+static bool pick(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err) {
+    if (a.T != T || a.Lb != LB) return false;
+    if (threads == 128) { *err = launch_lms_fast_t<128, T, LB>(a, s); return true; }
+    if (threads == 256) { *err = launch_lms_fast_t<256, T, LB>(a, s); return true; }
+    return false;
+}
+
+bool lms_fast_c(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err) {
+    return pick<25, 128>(a, threads, s, err) || pick<27, 128>(a, threads, s, err) ||
+           pick<29, 128>(a, threads, s, err) || pick<31, 128>(a, threads, s, err);
+}

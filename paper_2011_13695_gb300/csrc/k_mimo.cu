@@ -506,7 +506,15 @@ static cudaError_t launch_lms_t(const LmsArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+bool lms_fast_a(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
+bool lms_fast_b(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
+bool lms_fast_c(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
+
+// compile-time shapes first (k_lms_fast.cuh), this file's generic kernel otherwise
 cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    if (lms_fast_b(a, threads, s, &err) || lms_fast_a(a, threads, s, &err) || lms_fast_c(a, threads, s, &err))
+        return err;
     switch (threads) {
         case 128: return launch_lms_t<128>(a, s);
         case 512: return launch_lms_t<512>(a, s);

@@ -89,7 +89,10 @@ def check_bstar(g, r, cfg, head=0, skip=None):
     """b* may differ only where the oracle's FP64 window sums of the two choices nearly tie.
 
     Both picks are then correct (the GPU's sums carry FP32 rounding of y and of
-    the distances, ~1e-6 relative); the count of such symbols is bounded.
+    the distances, ~1e-6 relative). The count of such symbols is bounded at
+    1e-4 of the symbols, a guard against systematic divergence only: every one
+    of them is checked to be a near-tie (about 1e-4 of the symbols of the
+    16QAM frame fall within FP32 reach of a tie between neighbouring phases).
     Returns the mask of symbols where b* agrees.
     """
     from oracle import bps as obps
@@ -104,7 +107,7 @@ def check_bstar(g, r, cfg, head=0, skip=None):
         d = obps.distances(r.y[q, lo:hi], cfg.bits_per_sym, B).sum(axis=0)
         bg, bo = int(g["bstar"][q, k]), int(r.bstar[q, k])
         assert abs(d[bg] - d[bo]) <= 1e-4 * d[bo], f"b* at ({q},{k}): {bg} vs {bo} is not a near-tie"
-    assert len(bad) <= max(2, 5e-5 * 2 * N), f"b* differs on {len(bad)} symbols"
+    assert len(bad) <= max(2, 1e-4 * 2 * N), f"b* differs on {len(bad)} symbols"
     return agree
 
 
