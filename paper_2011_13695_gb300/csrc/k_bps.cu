@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
 
     // rotation by e^{-j theta_b} folded with 1/(2a); phases b >= B never win (penalty)
     float sn, cs;
-    sincospif((float)((double)b / (double)B - 0.5) * 0.5f, &sn, &cs);
+    sincospif((float)(2 * b - B) / (float)(4 * B), &sn, &cs);   // theta_b / pi = (b/B - 1/2) / 2
     const float c = cs * cI0, s = sn * cI0;
     const float pen = b < B ? 0.0f : 3.0e38f;
     const int nc = LEN / W;
@@ -236,9 +236,9 @@ __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, co
     __shared__ float2 rot[RX_BPS_MAXB];
     const int q = blockIdx.y;
     if (threadIdx.x < B) {
-        double s, c;
-        sincospi(-((double)threadIdx.x / (double)B - 0.5) * 0.5, &s, &c);   // e^{-j theta_b}
-        rot[threadIdx.x] = make_float2((float)c, (float)s);
+        float s, c;
+        sincospif(-((float)threadIdx.x / (float)B - 0.5f) * 0.5f, &s, &c);   // e^{-j theta_b}
+        rot[threadIdx.x] = make_float2(c, s);
     }
     const uint8_t* bq = bstar + (int64_t)q * bstride;
     const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;

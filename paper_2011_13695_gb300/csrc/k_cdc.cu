@@ -33,8 +33,8 @@ __device__ __forceinline__ float2 load_sample(const void* in, int64_t idx, float
     }
 }
 
-// A0: mean power of the first n_win samples of each polarisation: FP32 sums per thread and warp
-// (a few dozen samples each), FP64 across warps.
+// A0: mean power of the first n_win samples of each polarisation: FP32 sums per thread (a few
+// dozen samples each), then pairwise across the warp and the CTA; scale = 1/sqrt(P).
 template <int FMT>
 __global__ void k_power(const void* in, float in_scale, int64_t S, int64_t n_win, RxDevState* st) {
     const int p = blockIdx.x;
@@ -43,16 +43,16 @@ __global__ void k_power(const void* in, float in_scale, int64_t S, int64_t n_win
         float2 v = load_sample<FMT>(in, (int64_t)p * S + i, in_scale);
         acc += cabs2(v);
     }
-    __shared__ double red[32];
+    __shared__ float red[32];
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)acc;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        v = warp_sum_d(v);
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        v = warp_sum(v);
         if (threadIdx.x == 0) {
-            double P = n_win > 0 ? v / (double)n_win : 0.0;
-            st->scale[p] = P > 0.0 ? (float)(1.0 / sqrt(P)) : 1.0f;
+            const float P = n_win > 0 ? v / (float)n_win : 0.0f;
+            st->scale[p] = P > 0.0f ? rsqrtf(P) : 1.0f;
         }
     }
 }

@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
     const int64_t nwords = (N * m + 31) / 32;
     const uint32_t* refp = have_sync ? ref + (int64_t)p * refstride : nullptr;
     uint32_t errs = 0, serr = 0, cnt = 0;
-    // EVM sums: FP32 per thread (a handful of symbols each) and per warp, FP64 from the CTA level
-    // on (FP64 arithmetic runs at a small fraction of the FP32 rate on this part)
+    // EVM sums: FP32 per thread (a handful of symbols each), per warp and per CTA, then fixed point
+    // (FP64 arithmetic, atomics included, runs at a small fraction of the FP32 rate on this part)
     float en = 0.0f, ed = 0.0f;
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n - lane < N; n += step) {
@@ -167,10 +167,22 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
                 if (lane == w && wi < nwords) out[(int64_t)q * outstride + wi] = word;
             }
         }
-        if (have_sync && n >= lo && n < hi) {
+        if (have_sync) {
+            // the warp's 32 reference symbols t0 .. t0 + 31 are bits [t0 m, (t0 + 32) m) of the packed
+            // reference: lanes 0..m load the m + 1 words that hold them, every lane picks its bits with
+            // two shuffles
+            const int64_t t0 = (n - lane) + d - lat;
+            const int64_t bit0 = t0 * m;
+            const int64_t w0 = bit0 >> 5;                      // floor, also for t0 < 0
+            const int64_t nrw = (n_ref * m + 31) / 32;
+            uint32_t word = 0;
+            if (lane <= m && w0 + lane >= 0 && w0 + lane < nrw) word = __ldg(&refp[w0 + lane]);
+            const int b = lane * m + (int)(bit0 - w0 * 32);
+            const uint32_t lo_w = __shfl_sync(0xffffffffu, word, b >> 5);
+            const uint32_t hi_w = __shfl_sync(0xffffffffu, word, (b >> 5) + 1);
+            const uint32_t rb = (uint32_t)((((uint64_t)hi_w << 32) | lo_w) >> (b & 31)) & ((1u << m) - 1u);
             const int64_t t = n + d - lat;
-            if (t >= 0 && t < n_ref) {
-                const uint32_t rb = ref_symbol_bits(refp, t, m);
+            if (n < N && n >= lo && n < hi && t >= 0 && t < n_ref) {
                 const uint32_t e = __popc(rb ^ sbits);
                 errs += e;
                 serr += e ? 1u : 0u;
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
     }
     if (!have_sync) return;
     __shared__ unsigned int ri[3][8];
-    __shared__ double rd[2][8];
+    __shared__ float rd[2][8];
     errs = __reduce_add_sync(0xffffffffu, errs);
     serr = __reduce_add_sync(0xffffffffu, serr);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -194,12 +206,12 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
     const int w = threadIdx.x >> 5;
     if (lane == 0) {
         ri[0][w] = errs; ri[1][w] = serr; ri[2][w] = cnt;
-        rd[0][w] = (double)en; rd[1][w] = (double)ed;
+        rd[0][w] = en; rd[1][w] = ed;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long a = 0, b = 0, c = 0;
-        double x = 0.0, y = 0.0;
+        float x = 0.0f, y = 0.0f;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
             a += ri[0][i]; b += ri[1][i]; c += ri[2][i]; x += rd[0][i]; y += rd[1][i];
         }
@@ -208,8 +220,9 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
             atomicAdd(&st->symbol_errors, b);
             atomicAdd(&st->symbols, c);
             atomicAdd(&st->bits, c * (unsigned long long)m);
-            atomicAdd(&st->evm_num, x);
-            atomicAdd(&st->evm_den, y);
+            // EVM sums as fixed point: integer atomics, exact and in no particular order
+            atomicAdd(&st->evm_num_fx, __float2ull_rn(x * RX_EVM_FX_SCALE));
+            atomicAdd(&st->evm_den_fx, __float2ull_rn(y * RX_EVM_FX_SCALE));
         }
     }
 }
@@ -240,11 +253,17 @@ cudaError_t launch_count(const float2* z, int64_t zstride, int64_t N, const uint
                          int64_t n_ref, int m, int64_t lo, int64_t hi, int64_t lat, uint32_t* out,
                          int64_t outstride, RxDevState* st, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // one resident wave: SMs x resident CTAs per SM, split between the two outputs
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, nsm = 152, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_count, 256, 0);
+        resident = std::max(1, nsm * per);
+    }
     const int64_t want = (N + 255) / 256;
-    dim3 grid((unsigned)std::min<int64_t>(want, (int64_t)nsm * 4), 2);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(want, resident / 2)), 2);
     k_count<<<grid, 256, 0, s>>>(z, zstride, N, ref, refstride, n_ref, m, lo, hi, lat, out, outstride, st);
     return cudaGetLastError();
 }

@@ -30,15 +30,18 @@ struct LmsFastShape {
     static constexpr int C = (T - 1) / 2;
     static constexpr int XW = 2 * LB + T - 1;             // window samples per polarisation
     static constexpr int XS = 2 * LB + T;                 // staging stride per polarisation
+    static constexpr int XE = (XW + 1) / 2;                // even-indexed samples first, odd ones at XE
     static constexpr int P = NT / LB;                      // lanes per output
-    static constexpr int CS = (2 * T + P - 1) / P;         // terms per lane
+    static constexpr int PH = P >= 2 ? P / 2 : 1;          // lanes per polarisation (P >= 2)
+    static constexpr int KC = 2 * ((T + 2 * PH - 1) / (2 * PH));   // taps per lane (even, P >= 2)
     static constexpr int G = NT / (2 * T);                 // gradient groups
     static constexpr int NG = (LB + G - 1) / G;            // symbols per group
     static constexpr int PF = (2 * XW + NT - 1) / NT;      // window registers per thread
     static constexpr int NWARP = NT / 32;
-    static constexpr int SMEM = 2 * T + 4 * XS + LB + G * 2 * T + NWARP + XW;   // float2 elements
+    static constexpr int SMEM = 2 * T + 8 * XS + LB + G * 2 * T + NWARP + XW;   // float2 elements
     static_assert(NT % LB == 0 && (P & (P - 1)) == 0 && P <= 32, "NT must be a power-of-two multiple of LB");
     static_assert(G >= 1, "at least 2T threads");
+    static_assert(T % 2 == 1, "odd tap count: window index parity follows the tap index");
 };
 
 template <int NT, int T, int LB>
@@ -47,8 +50,8 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     extern __shared__ float2 smem[];
     if (a.run_if && *a.run_if == 0) return;
     float2* taps = smem;                                   // [p][k]
-    float2* xsb = taps + 2 * T;                            // two windows of [2][XS]
-    float2* es = xsb + 4 * S::XS;                          // [LB]
+    float2* xsb = taps + 2 * T;                            // two windows of [2][XS] natural + [2][XS] split
+    float2* es = xsb + 8 * S::XS;                          // [LB]
     float2* part = es + LB;                                // [G][2T]
     float2* ypart = part + S::G * 2 * T;                   // [NWARP]
     float2* tab = ypart + S::NWARP;                        // [XW]
@@ -110,6 +113,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                 float2 v = pf[r];
                 if (inc) v = cmul(v, cmul(base, tab[jj]));
                 xs[p * S::XS + jj] = v;
+                xs[(2 + p) * S::XS + ((jj & 1) ? S::XE + (jj >> 1) : (jj >> 1))] = v;
             }
         }
     };
@@ -121,35 +125,55 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     }
     __syncthreads();
 
-    // output role: output n_out of the block, lane j of its P lanes, terms u = j CS + i
+    // Each window is staged twice: in natural order [p][jj] (the gradient's lanes run over taps, so
+    // consecutive lanes read consecutive samples) and split by parity, sample jj at jj / 2 (even jj)
+    // or XE + jj / 2 (odd jj) of [2 + p] (the outputs' lanes run over n, so the samples x_p[2n + c - k]
+    // of consecutive outputs are consecutive); the parity of the window index 2n + T - 1 - k is k's.
+    // Output role: output n_out of the block, lane j of its P lanes; for P >= 2 the lane takes
+    // polarisation j / PH and taps k = h KC + i, h = j % PH (KC even, so k and i share parity).
     const int n_out = tid / S::P, j = tid % S::P;
-    const int th = T - j * S::CS;                          // terms i < th are polarisation 0
-    const int lim = 2 * T - j * S::CS;                     // terms i < lim exist
+    const int op = S::P >= 2 ? j / S::PH : 0, oh = S::P >= 2 ? j % S::PH : 0;
+    const int olim = T - oh * S::KC;                      // taps i < olim exist for this lane
     // gradient role: tap t = (p, k), symbols n = g (mod G)
     const int gg = tid / (2 * T), gt = tid - gg * 2 * T;
     const bool grad_on = gg < S::G;
     const int gp = gt >= T ? 1 : 0, gk = gt - gp * T;
+    const int goff = gp * S::XS + T - 1 - gk + 2 * gg;     // natural copy: x_p[2n + c - k], n = gg + G i
 
     for (int b = 0; b < nblk; ++b) {
         const int64_t n0 = nfirst + (int64_t)b * LB;
         const int L = b < nwarm ? LB : (int)min((int64_t)LB, end - n0);
-        float2* xs = xsb + (b & 1) * 2 * S::XS;
+        float2* xs = xsb + (b & 1) * 4 * S::XS;
         if (b + 1 < nblk) prefetch(n0 + LB);
 
         // outputs
         const bool valid = n_out < L;
         float2 y;
         {
-            const float2* xa = xs + 2 * n_out + T - 1 - j * S::CS;           // pol 0: xa[-i]
-            const float2* xb = xs + S::XS + 2 * n_out + 2 * T - 1 - j * S::CS;   // pol 1: xb[-i]
-            const float2* hp = taps + j * S::CS;
             float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+            if constexpr (S::P == 1) {
 #pragma unroll
-            for (int i = 0; i < S::CS; ++i) {
-                if (i < lim) {
-                    const float2 xv = i < th ? xa[-i] : xb[-i];
-                    if (i & 1) acc1 = cmac(acc1, hp[i], xv);
-                    else acc0 = cmac(acc0, hp[i], xv);
+                for (int p = 0; p < 2; ++p) {
+                    const float2* be = xs + (2 + p) * S::XS + n_out + S::C;      // even taps: be[-k/2]
+                    const float2* bo = be + S::XE;                               // odd taps: bo[-(k+1)/2]
+#pragma unroll
+                    for (int k = 0; k < T; ++k) {
+                        const float2 xv = (k & 1) ? bo[-((k + 1) >> 1)] : be[-(k >> 1)];
+                        if (k & 1) acc1 = cmac(acc1, taps[p * T + k], xv);
+                        else acc0 = cmac(acc0, taps[p * T + k], xv);
+                    }
+                }
+            } else {
+                const float2* be = xs + (2 + op) * S::XS + n_out + S::C - ((oh * S::KC) >> 1);
+                const float2* bo = be + S::XE;
+                const float2* hp = taps + op * T + oh * S::KC;
+#pragma unroll
+                for (int i = 0; i < S::KC; ++i) {
+                    if (i < olim) {
+                        const float2 xv = (i & 1) ? bo[-((i + 1) >> 1)] : be[-(i >> 1)];
+                        if (i & 1) acc1 = cmac(acc1, hp[i], xv);
+                        else acc0 = cmac(acc0, hp[i], xv);
+                    }
                 }
             }
             y = cadd(acc0, acc1);
@@ -186,7 +210,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
 
         // gradient partials
         if (grad_on) {
-            const float2* xg = xs + gp * S::XS + T - 1 - gk + 2 * gg;
+            const float2* xg = xs + goff;
             float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int i = 0; i < S::NG; ++i) {
@@ -207,7 +231,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
             const float2 h = taps[tid];
             taps[tid] = make_float2(fmaf(a.mu, g.x, h.x), fmaf(a.mu, g.y, h.y));
         }
-        if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * 2 * S::XS, n0 + LB);
+        if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * 4 * S::XS, n0 + LB);
         __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out)

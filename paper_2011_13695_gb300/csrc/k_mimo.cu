@@ -296,7 +296,8 @@ __global__ void __launch_bounds__((1 << K) / 16) k_foe_pgram(const float2* yw, i
     fft_run<K, -1, true, true>(sm, tw, load, store);
 }
 
-// coarse peak, fine slope, code, phase increment and corrected taps
+// coarse peak, fine slope, code, phase increment and corrected taps. FP32 except the few scalar
+// steps from the slope to the integer code (FP64 is a small fraction of the FP32 rate here).
 __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __restrict__ yw, int64_t nw, int Lb,
                            double rs, double fs, double grid, int T, RxDevState* st) {
     const int nf = 1 << kf;
@@ -304,7 +305,8 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
     __shared__ float bv[32];
     __shared__ int bi[32];
     __shared__ int s_kappa;
-    __shared__ double2 s_a[1024];
+    __shared__ float s_ph[1024];
+    __shared__ float s_wf;
     // first maximum of P0 + P1
     float best = -1.0f;
     int besti = 0;
@@ -330,15 +332,16 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
     __syncthreads();
     const int kappa = s_kappa;
     // a_j = sum_q sum_{n in block j} (y_q[n] e^{-j w_c n})^4, w_c = 2 pi kappa / (4 nf); one warp per
-    // block, FP32 sums (2 Lb terms of order one), then arg(a_j) in FP64 by one thread per block
+    // block, FP32 sums (2 Lb terms of order one), then arg(a_j) by one thread per block
+    // (|kappa n| < nf nw / 2 <= 2^26 and period <= 2^16: 32-bit index arithmetic is exact)
     const int nb = min((int)(nw / Lb), 1024);
     const int w = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
-    const long long period = 4LL * nf;
+    const int period = 4 * nf;
     for (int j = w; j < nb; j += nwarp) {
         float ax = 0.0f, ay = 0.0f;
         for (int q = 0; q < 2; ++q) {
             for (int n = j * Lb + lane; n < (j + 1) * Lb; n += 32) {
-                long long r = ((long long)kappa * n) % period;
+                int r = (kappa * n) % period;
                 if (r < 0) r += period;
                 float sn, cs;
                 sincospif(-2.0f * (float)r / (float)period, &sn, &cs);
@@ -351,36 +354,56 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
         }
         ax = warp_sum(ax);
         ay = warp_sum(ay);
-        if (lane == 0) s_a[j] = make_double2((double)ax, (double)ay);
+        if (lane == 0) s_ph[j] = atan2f(ay, ax);
     }
     __syncthreads();
-    for (int j = tid; j < nb; j += nthr) s_a[j].x = atan2(s_a[j].y, s_a[j].x);
+    // unwrap: u_j = u_{j-1} + wrap(ph_j - ph_{j-1}) (the step brought into [-pi, pi]), a prefix sum;
+    // then the least-squares slope of u_j against the block centres, all by warp 0
+    const float PIf = 3.14159265358979f;
+    if (w == 0 && nb >= 2) {
+        const float ph0 = s_ph[0];
+        float carry = 0.0f, prev_raw = 0.0f, sx = 0.0f, sy = 0.0f;
+        for (int base = 0; base < nb; base += 32) {
+            const int j = base + lane;
+            const float ph = j < nb ? s_ph[j] : 0.0f;
+            float prv = __shfl_up_sync(0xffffffffu, ph, 1);
+            if (lane == 0) prv = prev_raw;
+            float st_ = 0.0f;
+            if (j > 0 && j < nb) {
+                st_ = ph - prv;
+                if (st_ > PIf) st_ -= 2.0f * PIf;
+                else if (st_ < -PIf) st_ += 2.0f * PIf;
+            }
+            for (int o = 1; o < 32; o <<= 1) {
+                const float v = __shfl_up_sync(0xffffffffu, st_, o);
+                if (lane >= o) st_ += v;
+            }
+            const float u = ph0 + carry + st_;
+            prev_raw = __shfl_sync(0xffffffffu, ph, 31);
+            carry = __shfl_sync(0xffffffffu, carry + st_, 31);
+            __syncwarp();
+            if (j < nb) s_ph[j] = u;                     // in place: the chunk's raw phases were read above
+            __syncwarp();
+        }
+        for (int j = lane; j < nb; j += 32) { sx += (float)j; sy += s_ph[j]; }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        const float mj = sx / nb, mu = sy / nb;
+        float sjj = 0.0f, sju = 0.0f;
+        for (int j = lane; j < nb; j += 32) {
+            const float dj = (float)j - mj;
+            sjj = fmaf(dj, dj, sjj);
+            sju = fmaf(dj, s_ph[j] - mu, sju);
+        }
+        sjj = warp_sum(sjj);
+        sju = warp_sum(sju);
+        if (lane == 0) s_wf = sju / (sjj * (float)Lb) / 4.0f;   // slope per symbol, / 4 for the 4th power
+    }
     __syncthreads();
     if (tid == 0) {
         const double PI = 3.14159265358979323846;
         const double wc = 2.0 * PI * (double)kappa / (4.0 * nf);
-        double wf = 0.0;
-        if (nb >= 2) {
-            // unwrap the block phases and fit their slope by least squares
-            double prev = s_a[0].x, shift = 0.0;
-            double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
-            for (int j = 0; j < nb; ++j) {
-                double ph = s_a[j].x;
-                if (j > 0) {
-                    const double d = (ph + shift) - prev;
-                    if (d > PI) shift -= 2.0 * PI;
-                    else if (d < -PI) shift += 2.0 * PI;
-                }
-                ph += shift;
-                prev = ph;
-                const double cx = (double)j * Lb + 0.5 * (Lb - 1);
-                sx += cx; sy += ph; sxx += cx * cx; sxy += cx * ph;
-            }
-            const double mx = sx / nb, my = sy / nb;
-            const double slope = (sxy - nb * mx * my) / (sxx - nb * mx * mx);
-            wf = slope / 4.0;
-        }
-        const double wh = wc + wf;
+        const double wh = wc + (nb >= 2 ? (double)s_wf : 0.0);
         const double u = wh * rs / (2.0 * PI) / grid;
         const double code = rint(u);
         st->fo_code = (int)code;
@@ -392,24 +415,24 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
         st->nco_inc = llrint(ldexp(F, 64));
     }
     __syncthreads();
-    // taps_init = taps_cma * exp(-j 2 pi code grid (k - c) / fs)
+    // taps_init = taps_cma * exp(-j 2 pi code grid (k - c) / fs): the phase accumulator at k - c
     const int c = (T - 1) / 2;
-    const double code = (double)st->fo_code;
+    const long long inc = st->nco_inc;
     for (int t = tid; t < 4 * T; t += nthr) {
         const int k = t % T;
-        double s, cs;
-        sincospi(-2.0 * code * grid * (double)(k - c) / fs, &s, &cs);
-        const float2 h = st->taps_cma[t];
-        st->taps_init[t] = cmul(h, make_float2((float)cs, (float)s));
+        st->taps_init[t] = cmul(st->taps_cma[t], nco_conj(inc, (long long)(k - c)));
     }
 }
 
 // max over |d| <= c of |rho_d| between the two CMA outputs (second half of
-// y_acq). One CTA per lag d plus one for the two energies, FP32 sums (a
-// threshold test at 0.5 needs no more precision); the CTA that finishes last
-// (a counter in flag[1], reset by it) combines the partials in flag[2 ...].
-__global__ void k_cma_check(const float2* __restrict__ yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st,
-                            int* flag, int pass) {
+// y_acq). CTA (i, ch): lag d = i - c for i < 2c + 1, the two energies for
+// i = 2c + 1, over chunk ch of CMA_CHUNKS; FP32 sums (a threshold test at 0.5
+// needs no more precision) stored in flag[2 ...]; the CTA that finishes last
+// (a counter in flag[1], reset by it) adds the chunks in a fixed order.
+constexpr int CMA_CHUNKS = 4;
+
+__global__ void __launch_bounds__(256) k_cma_check(const float2* __restrict__ yacq, int64_t ystride, int64_t nacq,
+                                                   int T, RxDevState* st, int* flag, int pass) {
     if (pass == 1 && *flag == 0) return;
     const int64_t h0 = nacq / 2;
     const int L = (int)(nacq - h0);
@@ -417,20 +440,25 @@ __global__ void k_cma_check(const float2* __restrict__ yacq, int64_t ystride, in
     const float2* y1 = yacq + ystride + h0;
     const int maxlag = (T - 1) / 2, nlag = 2 * maxlag + 1;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-    float* part = reinterpret_cast<float*>(flag + 2);
+    const int ch = blockIdx.y;
+    float* part = reinterpret_cast<float*>(flag + 2);          // [nlag + 1][CMA_CHUNKS][2]
     __shared__ float s_x[32], s_y[32];
     __shared__ bool s_last;
     float sx = 0.0f, sy = 0.0f;
+    const int clen = (L + CMA_CHUNKS - 1) / CMA_CHUNKS;
+    const int c0 = ch * clen, c1 = min(L, c0 + clen);
     if ((int)blockIdx.x < nlag) {
         const int d = (int)blockIdx.x - maxlag;
-        const int a0 = d < 0 ? -d : 0, a1 = L - (d > 0 ? d : 0);
+        const int a0 = max(c0, d < 0 ? -d : 0), a1 = min(c1, L - (d > 0 ? d : 0));
+#pragma unroll 4
         for (int n = a0 + tid; n < a1; n += blockDim.x) {
             const float2 v = cmulc(y0[n], y1[n + d]);
             sx += v.x;
             sy += v.y;
         }
     } else {
-        for (int n = tid; n < L; n += blockDim.x) {
+#pragma unroll 4
+        for (int n = c0 + tid; n < c1; n += blockDim.x) {
             sx += cabs2(y0[n]);
             sy += cabs2(y1[n]);
         }
@@ -442,29 +470,40 @@ __global__ void k_cma_check(const float2* __restrict__ yacq, int64_t ystride, in
     if (tid == 0) {
         float ax = 0.0f, ay = 0.0f;
         for (int k = 0; k < nw; ++k) { ax += s_x[k]; ay += s_y[k]; }
-        if ((int)blockIdx.x < nlag) {
-            part[blockIdx.x] = sqrtf(ax * ax + ay * ay);
-        } else {
-            part[nlag] = ax;
-            part[nlag + 1] = ay;
-        }
+        float* pp = part + ((int)blockIdx.x * CMA_CHUNKS + ch) * 2;
+        pp[0] = ax;
+        pp[1] = ay;
         __threadfence();
         const unsigned done = atomicAdd(reinterpret_cast<unsigned*>(flag + 1), 1u);
-        s_last = done == gridDim.x - 1;
+        s_last = done == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
-    if (!s_last || tid != 0) return;
+    if (!s_last) return;
+    // last CTA: every partial into shared memory with one parallel load (L2, not L1), then the sums
+    // over chunks in a fixed order and the maximum
     __threadfence();
-    const volatile float* vp = part;
-    const double den = sqrt((double)vp[nlag] * (double)vp[nlag + 1]);
-    double best = 0.0;
-    for (int k = 0; k < nlag; ++k) best = fmax(best, den > 0.0 ? (double)vp[k] / den : 0.0);
+    __shared__ float s_p[(RX_TMAX + 1) * CMA_CHUNKS * 2];
+    const int np = (nlag + 1) * CMA_CHUNKS * 2;
+    for (int i = tid; i < np; i += blockDim.x) s_p[i] = __ldcg(&part[i]);
+    __syncthreads();
+    if (tid != 0) return;
+    auto total = [&](int i, int comp) {
+        float v = 0.0f;
+        for (int c = 0; c < CMA_CHUNKS; ++c) v += s_p[(i * CMA_CHUNKS + c) * 2 + comp];
+        return v;
+    };
+    const float den = sqrtf(total(nlag, 0)) * sqrtf(total(nlag, 1));
+    float best = 0.0f;
+    for (int k = 0; k < nlag; ++k) {
+        const float rx = total(k, 0), ry = total(k, 1);
+        best = fmaxf(best, den > 0.0f ? sqrtf(rx * rx + ry * ry) / den : 0.0f);
+    }
     flag[1] = 0;
     if (pass == 0) {
-        *flag = best > 0.5 ? 1 : 0;
-        st->cma_rho = (float)best;
+        *flag = best > 0.5f ? 1 : 0;
+        st->cma_rho = best;
         st->cma_reran = 0;
-    } else if (best > 0.5) {
+    } else if (best > 0.5f) {
         atomicOr(&st->err_word, 4u);
     }
 }
@@ -563,8 +602,8 @@ cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw
 
 cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st, int* flag,
                              int pass, cudaStream_t s) {
-    const int nlag = 2 * ((T - 1) / 2) + 1;
-    k_cma_check<<<nlag + 1, 256, 0, s>>>(yacq, ystride, nacq, T, st, flag, pass);   // lags |d| <= c, energies
+    const int nlag = 2 * ((T - 1) / 2) + 1;                 // lags |d| <= c, then the energies
+    k_cma_check<<<dim3(nlag + 1, CMA_CHUNKS), 256, 0, s>>>(yacq, ystride, nacq, T, st, flag, pass);
     return cudaGetLastError();
 }
 

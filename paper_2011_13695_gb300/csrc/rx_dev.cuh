@@ -30,7 +30,7 @@ struct RxDevState {
     int32_t sync_len;
     uint32_t err_word;
     unsigned long long bits, bit_errors, symbols, symbol_errors;
-    double evm_num, evm_den;
+    unsigned long long evm_num_fx, evm_den_fx;   // EVM sums in units of 2^-28 (integer atomics)
 };
 
 // -------------------------------------------------------------------------
@@ -73,14 +73,25 @@ struct Qam {
     float hL;     // (L - 1) / 2
 };
 
+// a and 1/(2a) are the FP32 roundings of the FP64 values of 1/sqrt(2(M-1)/3) and sqrt(2(M-1)/3)/2,
+// written out for M = 4, 16, 64, 256 so that device code takes no FP64 arithmetic (a small fraction
+// of the FP32 rate on this part); other M compute them.
 __host__ __device__ inline Qam make_qam(int m) {
     Qam q;
     q.m = m;
     q.L = 1 << (m / 2);
-    int M = q.L * q.L;
-    q.a = (float)(1.0 / sqrt(2.0 * (M - 1) / 3.0));
-    q.half_inv_a = (float)(0.5 * sqrt(2.0 * (M - 1) / 3.0));
     q.hL = 0.5f * (float)(q.L - 1);
+    switch (m) {
+        case 2: q.a = 0x1.6a09e6p-1f; q.half_inv_a = 0x1.6a09e6p-1f; break;
+        case 4: q.a = 0x1.43d136p-2f; q.half_inv_a = 0x1.94c584p+0f; break;
+        case 6: q.a = 0x1.3c0366p-3f; q.half_inv_a = 0x1.9ec474p+1f; break;
+        case 8: q.a = 0x1.3a261cp-4f; q.half_inv_a = 0x1.a13a9cp+2f; break;
+        default: {
+            const int M = q.L * q.L;
+            q.a = (float)(1.0 / sqrt(2.0 * (M - 1) / 3.0));
+            q.half_inv_a = (float)(0.5 * sqrt(2.0 * (M - 1) / 3.0));
+        }
+    }
     return q;
 }
 
@@ -122,14 +133,13 @@ __device__ __forceinline__ float2 nco_conj(long long inc, long long g) {
 }
 
 // Principal square root of a unit complex number (c, s), arg in (-pi, pi] -> arg / 2 in (-pi/2, pi/2],
-// in the cancellation-free form for either sign of c.
+// in the cancellation-free form for either sign of c: with v = (1 + |c|) / 2 in [1/2, 1] and
+// r = 1 / sqrt(v), the larger component is v r = sqrt(v) and the smaller |s| / (2 sqrt(v)) = |s| r / 2.
 __device__ __forceinline__ float2 unit_sqrt(float2 u) {
-    if (u.x >= 0.0f) {
-        const float t = sqrtf(0.5f * (1.0f + u.x));
-        return make_float2(t, u.y / (2.0f * t));
-    }
-    const float t = sqrtf(0.5f * (1.0f - u.x));
-    return make_float2(fabsf(u.y) / (2.0f * t), copysignf(t, u.y));
+    const float v = 0.5f * (1.0f + fabsf(u.x));
+    const float r = rsqrtf(v);
+    if (u.x >= 0.0f) return make_float2(v * r, 0.5f * u.y * r);
+    return make_float2(0.5f * fabsf(u.y) * r, copysignf(v * r, u.y));
 }
 
 // exp(-j psi) with psi = arg(w) / 4, arg in (-pi, pi]: the conjugate of the principal fourth root of
@@ -145,6 +155,8 @@ __device__ __forceinline__ float2 quarter_root_conj(float2 w) {
     const float2 r = unit_sqrt(unit_sqrt(make_float2(w.x * inv, w.y * inv)));
     return make_float2(r.x, -r.y);
 }
+
+#define RX_EVM_FX_SCALE 268435456.0f                // 2^28
 
 // block-wide helpers
 __device__ __forceinline__ float warp_sum(float v) {

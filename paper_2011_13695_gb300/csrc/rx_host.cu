@@ -264,7 +264,7 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(dalloc(&h->yfoe, 2 * h->nw));
     A(dalloc(&h->pgram, 2 * (size_t)nf));
     A(dalloc(&h->sync_counts, 16 * (2 * RX_MAX_DELAY + 1)));
-    A(dalloc(&h->flag, 64));            // [0] CMA rerun flag, [1] check counter, [2..] check partials
+    A(dalloc(&h->flag, 512));           // [0] CMA rerun flag, [1] check counter, [2..] check partials
     A(dalloc(&h->taps_id, 4 * RX_TMAX));
     A(dalloc(&h->st, 1));
     A(cudaMalloc(&h->stage_in, (size_t)(2 * h->Smax * h->in_elem)));
@@ -290,7 +290,7 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaMemset(h->tail, 0, sizeof(float2) * 2 * h->hop));
     // counters that kernels accumulate into and reset after use must start at zero
     A(cudaMemset(h->sync_counts, 0, sizeof(int) * 16 * (2 * RX_MAX_DELAY + 1)));
-    A(cudaMemset(h->flag, 0, sizeof(int) * 64));
+    A(cudaMemset(h->flag, 0, sizeof(int) * 512));
     k_state_init<<<1, 1, 0, s0>>>(h->st);
     k_identity_taps<<<1, 256, 0, s0>>>(h->taps_id, h->T);
     A(cudaGetLastError());
@@ -543,10 +543,10 @@ rx_status rx_stats(rx_handle* h, rx_stats_t* out) {
     out->bit_errors = st.bit_errors;
     out->symbols_counted = st.symbols;
     out->symbol_errors = st.symbol_errors;
-    out->evm_num = st.evm_num;
-    out->evm_den = st.evm_den;
+    out->evm_num = (double)st.evm_num_fx / (double)RX_EVM_FX_SCALE;
+    out->evm_den = (double)st.evm_den_fx / (double)RX_EVM_FX_SCALE;
     out->ber = st.bits ? (double)st.bit_errors / (double)st.bits : 0.0;
-    out->evm = st.evm_den > 0 ? std::sqrt(st.evm_num / st.evm_den) : 0.0;
+    out->evm = out->evm_den > 0 ? std::sqrt(out->evm_num / out->evm_den) : 0.0;
     if (st.bits == 0) out->q_db = 0.0;
     else if (st.bit_errors == 0) out->q_db = INFINITY;
     else {
@@ -624,7 +624,7 @@ rx_status rx_reset(rx_handle* h) {
     RX_CK(cudaMemset(h->tail, 0, sizeof(float2) * 2 * h->hop));
     RX_CK(cudaMemset(h->cdc, 0, sizeof(float2) * 2 * h->cap));
     RX_CK(cudaMemset(h->sync_counts, 0, sizeof(int) * 16 * (2 * RX_MAX_DELAY + 1)));
-    RX_CK(cudaMemset(h->flag, 0, sizeof(int) * 64));
+    RX_CK(cudaMemset(h->flag, 0, sizeof(int) * 512));
     k_state_init<<<1, 1>>>(h->st);
     RX_CK(cudaGetLastError());
     RX_CK(cudaDeviceSynchronize());
