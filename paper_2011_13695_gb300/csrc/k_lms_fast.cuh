@@ -29,8 +29,12 @@ template <int NT, int T, int LB>
 struct LmsFastShape {
     static constexpr int C = (T - 1) / 2;
     static constexpr int XW = 2 * LB + T - 1;             // window samples per polarisation
-    static constexpr int XS = 2 * LB + T;                 // staging stride per polarisation
-    static constexpr int XE = (XW + 1) / 2;                // even-indexed samples first, odd ones at XE
+    static constexpr int XS = 2 * LB + T + 1;             // natural staging stride per polarisation (even)
+    static constexpr int XE = ((XW + 1) / 2 + 1) & ~1;     // split staging: even samples, odd ones at XE (even)
+    static constexpr int Q = 2 * NT / LB;                  // lanes per output pair (pair path: 2 or 4)
+    // the pair path for Q = 4 only: with Q = 2 (NT = LB) its registers cost segments CTAs per SM
+    static constexpr bool PAIR = Q == 4 && (2 * NT) % LB == 0;
+    static constexpr int RP = 2 * ((C + 2) / 2);           // split tap row: C + 1 even taps, padded to even
     static constexpr int P = NT / LB;                      // lanes per output
     static constexpr int PH = P >= 2 ? P / 2 : 1;          // lanes per polarisation (P >= 2)
     static constexpr int KC = 2 * ((T + 2 * PH - 1) / (2 * PH));   // taps per lane (even, P >= 2)
@@ -38,7 +42,7 @@ struct LmsFastShape {
     static constexpr int NG = (LB + G - 1) / G;            // symbols per group
     static constexpr int PF = (2 * XW + NT - 1) / NT;      // window registers per thread
     static constexpr int NWARP = NT / 32;
-    static constexpr int SMEM = 2 * T + 8 * XS + LB + G * 2 * T + NWARP + XW;   // float2 elements
+    static constexpr int SMEM = 4 * RP + 2 * T + 2 * (2 * XS + 4 * XE) + LB + G * 2 * T + NWARP + XW;   // float2
     static_assert(NT % LB == 0 && (P & (P - 1)) == 0 && P <= 32, "NT must be a power-of-two multiple of LB");
     static_assert(G >= 1, "at least 2T threads");
     static_assert(T % 2 == 1, "odd tap count: window index parity follows the tap index");
@@ -47,11 +51,14 @@ struct LmsFastShape {
 template <int NT, int T, int LB>
 __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     using S = LmsFastShape<NT, T, LB>;
-    extern __shared__ float2 smem[];
+    extern __shared__ float4 smem4[];                      // 16-byte aligned
+    float2* smem = reinterpret_cast<float2*>(smem4);
     if (a.run_if && *a.run_if == 0) return;
-    float2* taps = smem;                                   // [p][k]
-    float2* xsb = taps + 2 * T;                            // two windows of [2][XS] natural + [2][XS] split
-    float2* es = xsb + 8 * S::XS;                          // [LB]
+    float2* tps = smem;                                    // [p][parity][RP]: taps split by parity (16-B rows)
+    float2* taps = tps + 4 * S::RP;                        // [p][k]
+    constexpr int WBUF = 2 * S::XS + 4 * S::XE;            // one window: natural [2][XS], split [2][2 XE]
+    float2* xsb = taps + 2 * T;                            // two windows
+    float2* es = xsb + 2 * WBUF;                           // [LB]
     float2* part = es + LB;                                // [G][2T]
     float2* ypart = part + S::G * 2 * T;                   // [NWARP]
     float2* tab = ypart + S::NWARP;                        // [XW]
@@ -59,7 +66,17 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
     const long long inc = a.derotate ? a.st->nco_inc : 0;
-    for (int t = tid; t < 2 * T; t += NT) taps[t] = a.taps_in[q * 2 * T + t];
+    auto tps_at = [&](int t) -> float2* {                  // split position of tap t = (p, k)
+        const int p = t >= T ? 1 : 0, k = t - p * T;
+        return tps + (2 * p + (k & 1)) * S::RP + (k >> 1);
+    };
+    for (int t = tid; t < 4 * S::RP; t += NT) tps[t] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    for (int t = tid; t < 2 * T; t += NT) {
+        const float2 h = a.taps_in[q * 2 * T + t];
+        taps[t] = h;
+        *tps_at(t) = h;
+    }
     if (inc)
         for (int jj = tid; jj < S::XW; jj += NT) tab[jj] = nco_conj(inc, jj);
 
@@ -113,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                 float2 v = pf[r];
                 if (inc) v = cmul(v, cmul(base, tab[jj]));
                 xs[p * S::XS + jj] = v;
-                xs[(2 + p) * S::XS + ((jj & 1) ? S::XE + (jj >> 1) : (jj >> 1))] = v;
+                xs[2 * S::XS + p * 2 * S::XE + ((jj & 1) ? S::XE + (jj >> 1) : (jj >> 1))] = v;
             }
         }
     };
@@ -127,13 +144,23 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
 
     // Each window is staged twice: in natural order [p][jj] (the gradient's lanes run over taps, so
     // consecutive lanes read consecutive samples) and split by parity, sample jj at jj / 2 (even jj)
-    // or XE + jj / 2 (odd jj) of [2 + p] (the outputs' lanes run over n, so the samples x_p[2n + c - k]
-    // of consecutive outputs are consecutive); the parity of the window index 2n + T - 1 - k is k's.
-    // Output role: output n_out of the block, lane j of its P lanes; for P >= 2 the lane takes
-    // polarisation j / PH and taps k = h KC + i, h = j % PH (KC even, so k and i share parity).
-    const int n_out = tid / S::P, j = tid % S::P;
-    const int op = S::P >= 2 ? j / S::PH : 0, oh = S::P >= 2 ? j % S::PH : 0;
-    const int olim = T - oh * S::KC;                      // taps i < olim exist for this lane
+    // or XE + jj / 2 (odd jj) of the split plane of p (the outputs' lanes run over n, so the samples
+    // x_p[2n + c - k] of consecutive outputs are consecutive); the parity of the window index
+    // 2n + T - 1 - k is that of k.
+    //
+    // Output roles. Pair path (Q = 2 NT / LB lanes per pair of outputs 2m, 2m + 1, Q = 2 or 4): lane r
+    // of the pair takes polarisation r / (Q / 2) and, for Q = 4, the taps of parity r % 2 (both
+    // parities for Q = 2). With c = (T - 1) / 2, even taps k = 2i read E[2m + c - i] (output 2m) and
+    // E[2m + 1 + c - i] (output 2m + 1), odd taps k = 2i + 1 read O[2m + c - 1 - i] and O[2m + c - i],
+    // so the lane loads the runs E[2m .. 2m + c + 1] and O[2m .. 2m + c] with 16-byte loads and its
+    // taps with 16-byte loads from the parity-split tap rows. Other shapes: P = NT / LB lanes per
+    // output, the lane takes polarisation j / PH and taps k = h KC + i, h = j % PH (KC even).
+    const int n_out = S::PAIR ? 2 * (tid / S::Q) : tid / S::P;
+    const int j = S::PAIR ? tid % S::Q : tid % S::P;
+    const int op = S::PAIR ? j / (S::Q / 2) : (S::P >= 2 ? j / S::PH : 0);
+    const int opar = (S::PAIR && S::Q == 4) ? (j & 1) : 0;
+    const int oh = S::P >= 2 ? j % S::PH : 0;
+    const int olim = T - oh * S::KC;                      // taps i < olim exist for this lane (P path)
     // gradient role: tap t = (p, k), symbols n = g (mod G)
     const int gg = tid / (2 * T), gt = tid - gg * 2 * T;
     const bool grad_on = gg < S::G;
@@ -143,19 +170,87 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     for (int b = 0; b < nblk; ++b) {
         const int64_t n0 = nfirst + (int64_t)b * LB;
         const int L = b < nwarm ? LB : (int)min((int64_t)LB, end - n0);
-        float2* xs = xsb + (b & 1) * 4 * S::XS;
+        float2* xs = xsb + (b & 1) * WBUF;
+        float2* xsplit = xs + 2 * S::XS;
         if (b + 1 < nblk) prefetch(n0 + LB);
 
-        // outputs
-        const bool valid = n_out < L;
-        float2 y;
-        {
+        // outputs: y0 = y[n_out], y1 = y[n_out + 1] (pair path) or y0 = y[n_out]
+        float2 y0 = make_float2(0.0f, 0.0f), y1 = make_float2(0.0f, 0.0f);
+        if constexpr (S::PAIR) {
+            constexpr int C = S::C;
+            constexpr int NE = (C + 3) / 2;                 // float4 loads of the even run (C + 2 values)
+            constexpr int NO = (C + 2) / 2;                 // float4 loads of the odd run (C + 1 values)
+            const float4* E4 = reinterpret_cast<const float4*>(xsplit + op * 2 * S::XE + n_out);
+            const float4* O4 = reinterpret_cast<const float4*>(xsplit + op * 2 * S::XE + S::XE + n_out);
+            const float4* TE4 = reinterpret_cast<const float4*>(tps + (2 * op) * S::RP);
+            const float4* TO4 = reinterpret_cast<const float4*>(tps + (2 * op + 1) * S::RP);
+            float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, b0 = a0, b1 = a0;
+            if (S::Q == 2 || opar == 0) {
+                float2 xv[2 * NE], hv[2 * NE];
+#pragma unroll
+                for (int u = 0; u < NE; ++u) {
+                    const float4 v = E4[u];
+                    xv[2 * u] = make_float2(v.x, v.y);
+                    xv[2 * u + 1] = make_float2(v.z, v.w);
+                }
+#pragma unroll
+                for (int u = 0; u < S::RP / 2; ++u) {
+                    const float4 v = TE4[u];
+                    hv[2 * u] = make_float2(v.x, v.y);
+                    hv[2 * u + 1] = make_float2(v.z, v.w);
+                }
+#pragma unroll
+                for (int i = 0; i <= C; ++i) {
+                    if (i & 1) {
+                        b0 = cmac(b0, hv[i], xv[C - i]);
+                        b1 = cmac(b1, hv[i], xv[C + 1 - i]);
+                    } else {
+                        a0 = cmac(a0, hv[i], xv[C - i]);
+                        a1 = cmac(a1, hv[i], xv[C + 1 - i]);
+                    }
+                }
+            }
+            if (S::Q == 2 || opar == 1) {
+                float2 xv[2 * NO], hv[2 * NO];
+#pragma unroll
+                for (int u = 0; u < NO; ++u) {
+                    const float4 v = O4[u];
+                    xv[2 * u] = make_float2(v.x, v.y);
+                    xv[2 * u + 1] = make_float2(v.z, v.w);
+                }
+#pragma unroll
+                for (int u = 0; u < S::RP / 2; ++u) {
+                    const float4 v = TO4[u];
+                    hv[2 * u] = make_float2(v.x, v.y);
+                    hv[2 * u + 1] = make_float2(v.z, v.w);
+                }
+#pragma unroll
+                for (int i = 0; i < C; ++i) {
+                    if (i & 1) {
+                        b0 = cmac(b0, hv[i], xv[C - 1 - i]);
+                        b1 = cmac(b1, hv[i], xv[C - i]);
+                    } else {
+                        a0 = cmac(a0, hv[i], xv[C - 1 - i]);
+                        a1 = cmac(a1, hv[i], xv[C - i]);
+                    }
+                }
+            }
+            y0 = cadd(a0, b0);
+            y1 = cadd(a1, b1);
+#pragma unroll
+            for (int w = 1; w < S::Q; w <<= 1) {
+                y0.x += __shfl_xor_sync(0xffffffffu, y0.x, w);
+                y0.y += __shfl_xor_sync(0xffffffffu, y0.y, w);
+                y1.x += __shfl_xor_sync(0xffffffffu, y1.x, w);
+                y1.y += __shfl_xor_sync(0xffffffffu, y1.y, w);
+            }
+        } else {
             float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
             if constexpr (S::P == 1) {
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    const float2* be = xs + (2 + p) * S::XS + n_out + S::C;      // even taps: be[-k/2]
-                    const float2* bo = be + S::XE;                               // odd taps: bo[-(k+1)/2]
+                    const float2* be = xsplit + p * 2 * S::XE + n_out + S::C;   // even taps: be[-k/2]
+                    const float2* bo = be + S::XE;                             // odd taps: bo[-(k+1)/2]
 #pragma unroll
                     for (int k = 0; k < T; ++k) {
                         const float2 xv = (k & 1) ? bo[-((k + 1) >> 1)] : be[-(k >> 1)];
@@ -164,7 +259,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                     }
                 }
             } else {
-                const float2* be = xs + (2 + op) * S::XS + n_out + S::C - ((oh * S::KC) >> 1);
+                const float2* be = xsplit + op * 2 * S::XE + n_out + S::C - ((oh * S::KC) >> 1);
                 const float2* bo = be + S::XE;
                 const float2* hp = taps + op * T + oh * S::KC;
 #pragma unroll
@@ -176,22 +271,33 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                     }
                 }
             }
-            y = cadd(acc0, acc1);
+            y0 = cadd(acc0, acc1);
 #pragma unroll
             for (int w = 1; w < S::P; w <<= 1) {
-                y.x += __shfl_xor_sync(0xffffffffu, y.x, w);
-                y.y += __shfl_xor_sync(0xffffffffu, y.y, w);
+                y0.x += __shfl_xor_sync(0xffffffffu, y0.x, w);
+                y0.y += __shfl_xor_sync(0xffffffffu, y0.y, w);
             }
         }
-        const bool owner = valid && j == 0;
-        if (owner && b >= nwarm && a.y != nullptr) a.y[(int64_t)q * a.ystride + n0 + n_out] = y;
+        constexpr int NOUT = S::PAIR ? 2 : 1;
+        const bool lead = j == 0;
+        const bool v0 = lead && n_out < L, v1 = lead && NOUT == 2 && n_out + 1 < L;
+        if (b >= nwarm && a.y != nullptr) {
+            float2* yq = a.y + (int64_t)q * a.ystride + n0 + n_out;
+            if (v0) yq[0] = y0;
+            if (v1) yq[1] = y1;
+        }
         if (a.cma) {
-            if (owner) es[n_out] = cscale(y, a.R2 - cabs2(y));
+            if (v0) es[n_out] = cscale(y0, a.R2 - cabs2(y0));
+            if (v1) es[n_out + 1] = cscale(y1, a.R2 - cabs2(y1));
         } else {
             float2 c4 = make_float2(0.0f, 0.0f);
-            if (owner) {
-                const float2 y2 = cmul(y, y);
+            if (v0) {
+                const float2 y2 = cmul(y0, y0);
                 c4 = cmul(y2, y2);
+            }
+            if (v1) {
+                const float2 y2 = cmul(y1, y1);
+                c4 = cadd(c4, cmul(y2, y2));
             }
             c4.x = warp_sum(c4.x);
             c4.y = warp_sum(c4.y);
@@ -201,9 +307,13 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
 #pragma unroll
             for (int w = 1; w < S::NWARP; ++w) sum = cadd(sum, ypart[w]);
             const float2 r = quarter_root_conj(make_float2(-sum.x, -sum.y));
-            if (owner) {
-                const float2 d = qam_decide(cmul(y, r), qm);
-                es[n_out] = csub(cmulc(d, r), y);
+            if (v0) {
+                const float2 d = qam_decide(cmul(y0, r), qm);
+                es[n_out] = csub(cmulc(d, r), y0);
+            }
+            if (v1) {
+                const float2 d = qam_decide(cmul(y1, r), qm);
+                es[n_out + 1] = csub(cmulc(d, r), y1);
             }
         }
         __syncthreads();
@@ -229,9 +339,11 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
 #pragma unroll
             for (int k = 1; k < S::G; ++k) g = cadd(g, part[k * 2 * T + tid]);
             const float2 h = taps[tid];
-            taps[tid] = make_float2(fmaf(a.mu, g.x, h.x), fmaf(a.mu, g.y, h.y));
+            const float2 hn = make_float2(fmaf(a.mu, g.x, h.x), fmaf(a.mu, g.y, h.y));
+            taps[tid] = hn;
+            *tps_at(tid) = hn;
         }
-        if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * 4 * S::XS, n0 + LB);
+        if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * WBUF, n0 + LB);
         __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out)
