@@ -13,6 +13,8 @@
 // the N/2 valid samples out.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "rx_fft.cuh"
 #include "rx_kernels.h"
 
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16)
     constexpr int HOP = N / 2, LEAD = N / 4;
     extern __shared__ float2 sm[];
     const int p = blockIdx.y;
-    const int64_t j = blockIdx.x;
+    const int64_t j = a.j0 + blockIdx.x;
     const float sc = a.st->scale[p] * a.in_scale;
     const int64_t S = a.S;
     const void* in = a.in;
@@ -156,7 +158,10 @@ cudaError_t launch_cdc_t(const CdcArgs& a, cudaStream_t s) {
         attr = true;
     }
     const int64_t hop = N / 2;
-    dim3 grid((unsigned)((a.S + hop - 1) / hop), 2);
+    const int64_t total = (a.S + hop - 1) / hop;
+    const int64_t n = a.nblk < 0 ? total - a.j0 : std::min(a.nblk, total - a.j0);
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((unsigned)n, 2);
     k_cdc<K, FMT><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -24,10 +24,12 @@ constexpr double C_LIGHT = 299792458.0;
 
 enum Stage {
     ST_POWER, ST_CDC, ST_CMA, ST_FOE, ST_DDACQ, ST_LMS, ST_BPS, ST_UNWRAP, ST_SYNC, ST_COUNT, ST_STATE, ST_H2D,
-    ST_D2H, ST_N
+    ST_D2H, ST_CDC_REST, ST_N
 };
+// "cdc" is the part of the FD compensation the acquisition reads (all of it when there is no
+// acquisition); "cdc_rest" the remainder, which runs on the handle's side stream beside the acquisition
 const char* kStageNames[ST_N] = {"power", "cdc", "cma", "foe", "dd_acq", "lms", "bps",
-                                 "unwrap", "sync", "count", "stream_state", "h2d", "d2h"};
+                                 "unwrap", "sync", "count", "stream_state", "h2d", "d2h", "cdc_rest"};
 constexpr int kPool = 64;
 // CTA sizes of the block-LMS kernel: the acquisition is one CTA per output row
 // and issue-bound, so fewer threads (less per-thread overhead) finish sooner;
@@ -102,6 +104,8 @@ struct rx_handle {
     uint64_t frames = 0, sym_processed = 0;
     bool sync_done = false;
     cudaStream_t last = nullptr;
+    cudaStream_t side = nullptr;   // the rest of a frame's FD compensation, beside the acquisition
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t launches = 0;
     cudaError_t last_err = cudaSuccess;
     // timing
@@ -200,6 +204,9 @@ void free_all(rx_handle* h) {
         for (auto e : h->ev0[s]) cudaEventDestroy(e);
         for (auto e : h->ev1[s]) cudaEventDestroy(e);
     }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
 }
 
 }  // namespace
@@ -270,6 +277,9 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaMalloc(&h->stage_in, (size_t)(2 * h->Smax * h->in_elem)));
     A(dalloc(&h->stage_ref, 2 * words));
     A(dalloc(&h->stage_out, 2 * words));
+    A(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    A(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    A(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     for (int s = 0; s < ST_N && e == cudaSuccess; ++s) {
         h->ev0[s].resize(kPool);
         h->ev1[s].resize(kPool);
@@ -341,12 +351,34 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
         RX_CK(launch_power(d_in, c.input_format, c.input_scale, S, 2 * n_cma * Lb, st, s));
         ++nl;
     }
+    // A single frame with an acquisition: the FD compensation of the blocks the acquisition reads
+    // (symbols [0, max(n_cma, n_dd) Lb) and the filter's reach) comes first on the stream, the rest
+    // runs on the side stream meanwhile and joins before the segments.
+    const int hopc = c.fft_size / 2;
+    const int64_t nblk_cdc = (S + hopc - 1) / hopc;
+    const int64_t acq_sym = std::max(n_cma, n_dd) * Lb;
+    const int64_t nblk_a = std::min<int64_t>(nblk_cdc, (2 * acq_sym + T + 2 + hopc - 1) / hopc);
+    const bool split = !stream_mode && first && n_cma > 0 && nblk_a < nblk_cdc;
     {
         StageScope sc(h, ST_CDC, s);
         CdcArgs a{d_in, c.input_format, c.input_scale, S, c.fft_size, h->H, h->tw,
                   stream_mode ? h->tail : nullptr, h->cdc, h->cap, obase, st};
+        if (split) a.nblk = nblk_a;
         RX_CK(launch_cdc(a, s));
         ++nl;
+    }
+    if (split) {
+        RX_CK(cudaEventRecord(h->ev_fork, s));
+        RX_CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        {
+            StageScope sc(h, ST_CDC_REST, h->side);
+            CdcArgs a{d_in, c.input_format, c.input_scale, S, c.fft_size, h->H, h->tw, nullptr, h->cdc, h->cap,
+                      obase, st};
+            a.j0 = nblk_a;
+            RX_CK(launch_cdc(a, h->side));
+            ++nl;
+        }
+        RX_CK(cudaEventRecord(h->ev_join, h->side));
     }
     LmsArgs base{};
     base.x = h->cdc;
@@ -422,6 +454,7 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
     } else {
         RX_CK(cudaMemcpyAsync(st->taps_init, st->taps_last, sizeof(float2) * 4 * T, cudaMemcpyDeviceToDevice, s));
     }
+    if (split) RX_CK(cudaStreamWaitEvent(s, h->ev_join, 0));   // the whole frame is compensated
     {
         StageScope sc(h, ST_LMS, s);
         LmsArgs a = base;

@@ -18,6 +18,8 @@ struct CdcArgs {
     float2* out;           // buffer base; polarisation p writes out + p*ostride + obase
     int64_t ostride, obase;
     RxDevState* st;
+    int64_t j0 = 0;        // first overlap-save block of this launch
+    int64_t nblk = -1;     // blocks of this launch (-1: every block from j0 to the end of the frame)
 };
 
 struct LmsArgs {
