@@ -51,7 +51,9 @@ def parse():
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser")
     ap.add_argument("--launch-dbm", type=float, default=4.0, help="launch power of the learned workload")
-    ap.add_argument("--train-steps", type=int, default=4000, help="Adam steps of the learned workload")
+    ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
+    ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
+    ap.add_argument("--lr", type=float, default=7e-4, help="initial Adam learning rate of the learned workload")
     ap.add_argument("--fmt", default="i8", choices=["i8", "f16"], help="input format of the stream workload")
     return ap.parse_args()
 
@@ -524,12 +526,12 @@ def learned_arm(args) -> None:
     x, ref, sym = on_device(generate_nonlinear(link, fibre, w["test_seed"], device="cuda"))
     gen_s = time.perf_counter() - t0
 
-    window, steps = 4096, args.train_steps
+    window, steps = args.window, args.train_steps
     pe = PostEqualiser(N, he_init(seed=0))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    losses = pe.train(zs, ts, 1024, N - 1024, steps=steps, window=window, lr=1e-3, lr_final=1e-4, seed=0)
+    losses = pe.train(zs, ts, 1024, N - 1024, steps=steps, window=window, lr=args.lr, lr_final=args.lr / 10, seed=0)
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
@@ -581,7 +583,7 @@ def learned_arm(args) -> None:
         "dtype": "f32 chain, bf16 x bf16 -> f32 network", "data": "synthetic (split-step Manakov, seeded)",
         "config": {"workload": "dp-16qam-32gbd-ssfm", "symbols_per_pol": N, "launch_dbm": args.launch_dbm,
                    "spans": fibre.spans, "span_km": fibre.span_km, "train_frames": len(zs),
-                   "train_steps": steps, "window": window, "l2": "flushed between timed steps"},
+                   "train_steps": steps, "window": window, "lr": args.lr, "l2": "flushed between timed steps"},
         "plain": {"ber": plain["ber"], "evm": plain["evm"], "bit_errors": plain["bit_errors"],
                   "bits_counted": plain["bits_counted"]},
         "learned": {"ber": learned["ber"], "evm": learned["evm"], "bit_errors": learned["bit_errors"],
