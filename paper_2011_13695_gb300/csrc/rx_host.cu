@@ -105,7 +105,7 @@ struct rx_handle {
     bool sync_done = false;
     cudaStream_t last = nullptr;
     cudaStream_t side = nullptr;   // the rest of a frame's FD compensation, beside the acquisition
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_host = nullptr;
     uint64_t launches = 0;
     cudaError_t last_err = cudaSuccess;
     // timing
@@ -206,7 +206,24 @@ void free_all(rx_handle* h) {
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_host) cudaEventDestroy(h->ev_host);
     if (h->side) cudaStreamDestroy(h->side);
+}
+
+// Single frame with an acquisition: the number of overlap-save blocks whose FD compensation the
+// acquisition reads (symbols [0, max(n_cma, n_dd) Lb) plus the filter's reach); those come first,
+// the rest can run beside the acquisition. 0: no such split.
+int64_t acq_cdc_blocks(const rx_handle* h, int64_t N) {
+    const rx_config& c = h->cfg;
+    if (c.streaming) return 0;
+    const int64_t n_cma = std::min<int64_t>(c.cma_blocks, N / h->Lb);
+    if (n_cma <= 0) return 0;
+    const int64_t n_dd = std::min<int64_t>(c.dd_acq_blocks, N / h->Lb);
+    const int hopc = c.fft_size / 2;
+    const int64_t nblk = (2 * N + hopc - 1) / hopc;
+    const int64_t acq_sym = std::max(n_cma, n_dd) * h->Lb;
+    const int64_t na = std::min<int64_t>(nblk, (2 * acq_sym + h->T + 2 + hopc - 1) / hopc);
+    return na < nblk ? na : 0;
 }
 
 }  // namespace
@@ -280,6 +297,7 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     A(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     A(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    A(cudaEventCreateWithFlags(&h->ev_host, cudaEventDisableTiming));
     for (int s = 0; s < ST_N && e == cudaSuccess; ++s) {
         h->ev0[s].resize(kPool);
         h->ev1[s].resize(kPool);
@@ -354,11 +372,8 @@ rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32
     // A single frame with an acquisition: the FD compensation of the blocks the acquisition reads
     // (symbols [0, max(n_cma, n_dd) Lb) and the filter's reach) comes first on the stream, the rest
     // runs on the side stream meanwhile and joins before the segments.
-    const int hopc = c.fft_size / 2;
-    const int64_t nblk_cdc = (S + hopc - 1) / hopc;
-    const int64_t acq_sym = std::max(n_cma, n_dd) * Lb;
-    const int64_t nblk_a = std::min<int64_t>(nblk_cdc, (2 * acq_sym + T + 2 + hopc - 1) / hopc);
-    const bool split = !stream_mode && first && n_cma > 0 && nblk_a < nblk_cdc;
+    const int64_t nblk_a = acq_cdc_blocks(h, N);
+    const bool split = nblk_a > 0;
     {
         StageScope sc(h, ST_CDC, s);
         CdcArgs a{d_in, c.input_format, c.input_scale, S, c.fft_size, h->H, h->tw,
@@ -546,7 +561,32 @@ rx_status rx_process_host(rx_handle* h, const void* h_in, int64_t n_sym, const u
     cudaStream_t s = (cudaStream_t)stream_;
     const int64_t S = 2 * n_sym;
     const int64_t words = (n_sym * h->m + 31) / 32;
-    {
+    const int64_t na = acq_cdc_blocks(h, n_sym);
+    if (na > 0) {
+        // The acquisition needs only the head of each polarisation: that is copied on the caller's
+        // stream, the rest of the input and the reference bits on the side stream, where they overlap
+        // the acquisition and precede the rest of the FD compensation (and the join before the
+        // segments). The side stream first waits for the caller's stream, whose previous frame may
+        // still read the staging buffers.
+        const int64_t head = std::min<int64_t>(S, na * (h->cfg.fft_size / 2) + h->cfg.fft_size / 4);
+        const char* src = static_cast<const char*>(h_in);
+        char* dst = static_cast<char*>(h->stage_in);
+        const size_t eb = (size_t)h->in_elem;
+        RX_CK(cudaEventRecord(h->ev_host, s));
+        RX_CK(cudaStreamWaitEvent(h->side, h->ev_host, 0));
+        {
+            StageScope sc(h, ST_H2D, s);
+            for (int p = 0; p < 2; ++p)
+                RX_CK(cudaMemcpyAsync(dst + p * S * eb, src + p * S * eb, (size_t)head * eb, cudaMemcpyHostToDevice, s));
+        }
+        for (int p = 0; p < 2; ++p)
+            if (S > head)
+                RX_CK(cudaMemcpyAsync(dst + (p * S + head) * eb, src + (p * S + head) * eb, (size_t)(S - head) * eb,
+                                      cudaMemcpyHostToDevice, h->side));
+        if (h_ref)
+            RX_CK(cudaMemcpyAsync(h->stage_ref, h_ref, sizeof(uint32_t) * 2 * words, cudaMemcpyHostToDevice,
+                                  h->side));
+    } else {
         StageScope sc(h, ST_H2D, s);
         RX_CK(cudaMemcpyAsync(h->stage_in, h_in, (size_t)(2 * S * h->in_elem), cudaMemcpyHostToDevice, s));
         if (h_ref)
