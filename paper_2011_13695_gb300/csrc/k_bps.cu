@@ -192,20 +192,33 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* red, int* total)
     return before;
 }
 
+// the 4 b* of symbols k0 .. k0 + 3 (zero past N) and the b* before k0 (the carried one at k0 = 0);
+// one 32-bit load when the row is 4-byte aligned and the group is whole
+__device__ __forceinline__ void load_b4(const uint8_t* bq, int64_t k0, int64_t N, int bprev_carry, bool vec,
+                                        int bs[4], int& prev) {
+    if (vec && k0 + 3 < N) {
+        const uchar4 v = *reinterpret_cast<const uchar4*>(bq + k0);
+        bs[0] = v.x; bs[1] = v.y; bs[2] = v.z; bs[3] = v.w;
+    } else {
+        for (int u = 0; u < 4; ++u) bs[u] = k0 + u < N ? bq[k0 + u] : 0;
+    }
+    if (k0 > 0) prev = bq[k0 - 1];
+    else prev = bprev_carry >= 0 ? bprev_carry : bs[0];
+}
+
 __global__ void k_unwrap_sums(const uint8_t* __restrict__ bstar, int64_t bstride, int64_t N, int B,
-                              const RxDevState* st, int* tile_sums, int ntiles) {
+                              const RxDevState* st, int* tile_sums, int ntiles, int vec) {
     __shared__ int red[32];
     const int q = blockIdx.y;
     const uint8_t* bq = bstar + (int64_t)q * bstride;
     const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;
     int sum = 0;
-    for (int u = 0; u < 4; ++u) {
-        const int64_t k = k0 + u;
-        if (k < N) {
-            int prev;
-            if (k > 0) prev = bq[k - 1];
-            else prev = st->b_prev[q] >= 0 ? st->b_prev[q] : bq[0];
-            sum += jump(prev, bq[k], B);
+    if (k0 < N) {
+        int bs[4], prev;
+        load_b4(bq, k0, N, st->b_prev[q], vec != 0, bs, prev);
+        for (int u = 0; u < 4; ++u) {
+            if (k0 + u < N) sum += jump(prev, bs[u], B);
+            prev = bs[u];
         }
     }
     int total;
@@ -231,7 +244,8 @@ __global__ void k_unwrap_scan(int* tile_sums, int ntiles, const RxDevState* st) 
 
 __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, const uint8_t* __restrict__ bstar,
                                int64_t bstride, int64_t N, int B, const int* tile_base, int ntiles,
-                               const RxDevState* st, int* m_out, int64_t mstride, float2* z, int64_t zstride) {
+                               const RxDevState* st, int* m_out, int64_t mstride, float2* z, int64_t zstride,
+                               int vec) {
     __shared__ int red[32];
     __shared__ float2 rot[RX_BPS_MAXB];
     const int q = blockIdx.y;
@@ -242,37 +256,56 @@ __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, co
     }
     const uint8_t* bq = bstar + (int64_t)q * bstride;
     const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;
-    int J[4], bs[4];
+    int J[4] = {0, 0, 0, 0}, bs[4] = {0, 0, 0, 0};
     int sum = 0;
-    for (int u = 0; u < 4; ++u) {
-        const int64_t k = k0 + u;
-        J[u] = 0;
-        bs[u] = 0;
-        if (k < N) {
-            bs[u] = bq[k];
-            int prev;
-            if (k > 0) prev = bq[k - 1];
-            else prev = st->b_prev[q] >= 0 ? st->b_prev[q] : bs[u];
-            J[u] = jump(prev, bs[u], B);
+    if (k0 < N) {
+        int prev;
+        load_b4(bq, k0, N, st->b_prev[q], vec != 0, bs, prev);
+        for (int u = 0; u < 4; ++u) {
+            if (k0 + u < N) J[u] = jump(prev, bs[u], B);
+            prev = bs[u];
+            sum += J[u];
         }
-        sum += J[u];
     }
     int m = tile_base[q * ntiles + blockIdx.x] + block_exclusive_scan(sum, red, nullptr);
     __syncthreads();
+    if (k0 >= N) return;
+    const float2* yq = y + (int64_t)q * ystride + k0;
+    float2* zq = z + (int64_t)q * zstride + k0;
+    int* mq = m_out + (int64_t)q * mstride + k0;
+    const bool whole = vec && k0 + 3 < N;
+    float2 v[4];
+    if (whole) {
+        const float4 a = *reinterpret_cast<const float4*>(yq);
+        const float4 b = *reinterpret_cast<const float4*>(yq + 2);
+        v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+    } else {
+        for (int u = 0; u < 4; ++u) v[u] = k0 + u < N ? yq[u] : make_float2(0.0f, 0.0f);
+    }
+    int mm[4];
     for (int u = 0; u < 4; ++u) {
-        const int64_t k = k0 + u;
         m += J[u];
-        if (k < N) {
-            m_out[(int64_t)q * mstride + k] = m;
-            float2 v = cmul(y[(int64_t)q * ystride + k], rot[bs[u]]);
-            switch (m & 3) {                          // (-j)^(m mod 4)
-                case 1: v = make_float2(v.y, -v.x); break;
-                case 2: v = make_float2(-v.x, -v.y); break;
-                case 3: v = make_float2(-v.y, v.x); break;
-                default: break;
-            }
-            z[(int64_t)q * zstride + k] = v;
+        mm[u] = m;
+        float2 w = cmul(v[u], rot[bs[u]]);
+        switch (m & 3) {                              // (-j)^(m mod 4)
+            case 1: w = make_float2(w.y, -w.x); break;
+            case 2: w = make_float2(-w.x, -w.y); break;
+            case 3: w = make_float2(-w.y, w.x); break;
+            default: break;
         }
+        v[u] = w;
+    }
+    if (whole) {
+        *reinterpret_cast<int4*>(mq) = make_int4(mm[0], mm[1], mm[2], mm[3]);
+        *reinterpret_cast<float4*>(zq) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        *reinterpret_cast<float4*>(zq + 2) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else {
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u < N) {
+                mq[u] = mm[u];
+                zq[u] = v[u];
+            }
     }
 }
 
@@ -306,10 +339,16 @@ cudaError_t launch_unwrap(const float2* y, int64_t ystride, const uint8_t* bstar
                           cudaStream_t s, int* nlaunch) {
     if (N <= 0) return cudaSuccess;
     const int ntiles = (int)((N + UT - 1) / UT);
-    k_unwrap_sums<<<dim3(ntiles, 2), UTHR, 0, s>>>(bstar, bstride, N, B, st, tile_sums, ntiles);
+    // 4-symbol vector accesses when every row is aligned for them
+    auto al = [](const void* p, int64_t stride_bytes, int a) {
+        return ((uintptr_t)p % a) == 0 && (stride_bytes % a) == 0;
+    };
+    const int vec = al(bstar, bstride, 4) && al(y, ystride * 8, 16) && al(z, zstride * 8, 16) &&
+                    al(m_out, mstride * 4, 16);
+    k_unwrap_sums<<<dim3(ntiles, 2), UTHR, 0, s>>>(bstar, bstride, N, B, st, tile_sums, ntiles, vec);
     k_unwrap_scan<<<2, 1024, 0, s>>>(tile_sums, ntiles, st);
     k_unwrap_apply<<<dim3(ntiles, 2), UTHR, 0, s>>>(y, ystride, bstar, bstride, N, B, tile_sums, ntiles, st, m_out,
-                                                    mstride, z, zstride);
+                                                    mstride, z, zstride, vec);
     k_unwrap_commit<<<1, 32, 0, s>>>(bstar, bstride, m_out, mstride, N, st);
     if (nlaunch) *nlaunch += 4;
     return cudaGetLastError();
