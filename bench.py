@@ -572,7 +572,7 @@ def learned_arm(args) -> None:
     t = sum(step_ms) / len(step_ms)
     tc = sum(cnn_ms) / len(cnn_ms)
     pk = peaks()
-    fp32_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    bf16_peak = pk.get("bf16_tflops", 1900.0)
     fwd_tflops = 2 * N * CNN_FWD_FLOP / (tc * 1e-3) / 1e12
     train_tflops = steps * 2 * window * CNN_TRAIN_FLOP / (train_ms * 1e-3) / 1e12
     bits = 2 * m * N
@@ -591,9 +591,11 @@ def learned_arm(args) -> None:
         "evm_gain_db": 20 * np.log10(plain["evm"] / learned["evm"]),
         "train": {"ms": train_ms, "tflops": train_tflops, "loss_first": float(losses[:20].mean()),
                   "loss_last": float(losses[-20:].mean()), "train_plain_ber": [s_["ber"] for s_ in train_stats]},
-        "roofline": {"kernel": "cnn forward (4 conv launches)", "bound": "alu", "achieved": fwd_tflops,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": fwd_tflops / fp32_peak, "traffic": None,
-                     "note": "FP32 FMA pipes (CUDA cores), nominal unit count x max clock"},
+        "roofline": {"kernel": "cnn forward (k_conv64_mma x 2 on tensor cores, edge layers on CUDA cores)",
+                     "bound": "tensor", "achieved": fwd_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": fwd_tflops / bf16_peak, "traffic": None,
+                     "peak_source": "fallback" if pk.get("fallback") else "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                     "note": "whole forward's algorithmic flops over its time (4 conv launches + channel split)"},
         "cnn_ms": tc, "gpu_launches": int(launches), "generate_s": round(gen_s, 1), "clocks": clk.summary(),
     }
     print(json.dumps(line))

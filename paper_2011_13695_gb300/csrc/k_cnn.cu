@@ -246,11 +246,9 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* ou
     e = conv_t<__nv_bfloat16, 4, 64, 0>(B.act[0], Tp, T, W + B.off[0], W + B.off[1], B.act[1], nullptr, nullptr, nullptr,
                                         nullptr, s);
     if (e) return e;
-    e = conv_t<__nv_bfloat16, 64, 64, 0>(B.act[1], Tp, T, W + B.off[2], W + B.off[3], B.act[2], nullptr, nullptr,
-                                         nullptr, nullptr, s);
+    e = conv64_mma_fwd(B.act[1], Tp, T, W + B.off[2], W + B.off[3], B.act[2], s);
     if (e) return e;
-    e = conv_t<__nv_bfloat16, 64, 64, 0>(B.act[2], Tp, T, W + B.off[4], W + B.off[5], B.act[3], nullptr, nullptr,
-                                         nullptr, nullptr, s);
+    e = conv64_mma_fwd(B.act[2], Tp, T, W + B.off[4], W + B.off[5], B.act[3], s);
     if (e) return e;
     return conv_t<__nv_bfloat16, 64, 4, 1>(B.act[3], Tp, T, W + B.off[6], W + B.off[7], nullptr, nullptr, nullptr, z,
                                            out, s);

@@ -32,3 +32,6 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);
 cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s);
 cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s);
+// one 64 -> 64 forward convolution (bias, ReLU, BF16 out) on the tensor cores (k_cnn_mma.cu)
+cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const float* W, const float* b,
+                           __nv_bfloat16* act, cudaStream_t s);
