@@ -186,18 +186,22 @@ __global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__
 
 // W'[ci][co][k] = bf16(W[co][ci][K-1-k]) and the forward weights as BF16-rounded FP32
 __global__ void k_weights(const float* __restrict__ master, int64_t n, float* __restrict__ fwd, const int* offs,
-                          const int* cins, const int* couts, float* __restrict__ bwd) {
+                          const int* cins, const int* couts, float* __restrict__ bwd, __nv_bfloat16* __restrict__ wtc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float v = __bfloat162float(__float2bfloat16_rn(master[i]));
+    const __nv_bfloat16 vb = __float2bfloat16_rn(master[i]);
+    const float v = __bfloat162float(vb);
     fwd[i] = v;
-    // locate the layer and, for weights, the transposed position
+    // locate the layer and, for weights, the transposed position (and the tensor-core layout of the
+    // two hidden layers: [co][k * C + ci])
     for (int l = 0; l < 4; ++l) {
         const int64_t wo = offs[2 * l], nw = (int64_t)couts[l] * cins[l] * KW;
         if (i >= wo && i < wo + nw) {
             const int64_t r = i - wo;
             const int co = (int)(r / (cins[l] * KW)), ci = (int)((r / KW) % cins[l]), k = (int)(r % KW);
             bwd[wo + ((int64_t)ci * couts[l] + co) * KW + (KW - 1 - k)] = v;
+            if (l == 1 || l == 2)
+                wtc[(int64_t)(l - 1) * couts[l] * cins[l] * KW + ((int64_t)co * KW + k) * cins[l] + ci] = vb;
         }
     }
 }
@@ -246,9 +250,10 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* ou
     e = conv_t<__nv_bfloat16, 4, 64, 0>(B.act[0], Tp, T, W + B.off[0], W + B.off[1], B.act[1], nullptr, nullptr, nullptr,
                                         nullptr, s);
     if (e) return e;
-    e = conv64_mma_fwd(B.act[1], Tp, T, W + B.off[2], W + B.off[3], B.act[2], s);
+    const int64_t lw = (int64_t)C * C * KW;
+    e = conv64_mma_fwd(B.act[1], Tp, T, B.wtc, W + B.off[3], B.act[2], s);
     if (e) return e;
-    e = conv64_mma_fwd(B.act[2], Tp, T, W + B.off[4], W + B.off[5], B.act[3], s);
+    e = conv64_mma_fwd(B.act[2], Tp, T, B.wtc + lw, W + B.off[5], B.act[3], s);
     if (e) return e;
     return conv_t<__nv_bfloat16, 64, 4, 1>(B.act[3], Tp, T, W + B.off[6], W + B.off[7], nullptr, nullptr, nullptr, z,
                                            out, s);
@@ -302,7 +307,7 @@ cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s) {
 
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s) {
     k_weights<<<(unsigned)((B.nparam + 255) / 256), 256, 0, s>>>(B.master, B.nparam, B.wfwd, B.offs_dev, B.cin_dev,
-                                                                 B.cout_dev, B.wbwd);
+                                                                 B.cout_dev, B.wbwd, B.wtc);
     return cudaGetLastError();
 }
 

@@ -5,11 +5,13 @@
 // the order k * 64 + ci: A[co][k*64 + ci] = W[co][ci][k] and
 // B[k*64 + ci][t] = x[ci][t + k - 4]. A CTA computes all 64 output channels
 // of 128 positions per tile and loops over tiles (one resident wave of CTAs):
-// it converts the layer's weights to BF16 in shared memory once, in rows of
+// it keeps the layer's BF16 weights in shared memory, in rows of
 // (k, ci) padded to 584 entries so that the 8 rows an ldmatrix reads fall in
-// distinct banks; per tile it stages the input positions t0 - 4 .. t0 + 132
+// distinct banks (copied from a BF16 copy in that order that the weight
+// update writes); per tile it stages the input positions t0 - 4 .. t0 + 132
 // transposed to [position][channel] (rows of 72 entries), so that the B
-// fragment of tap k is an ldmatrix of rows shifted by k. Eight warps take
+// fragment of tap k is an ldmatrix of rows shifted by k, loading the next
+// tile into registers while the current one computes. Eight warps take
 // 32 x 32 output blocks (2 x 4 mma tiles, 36 K-steps of 16). The epilogue adds
 // the bias, applies the ReLU, rounds to BF16 and writes the activation plane.
 #include <cuda_bf16.h>
@@ -31,6 +33,8 @@ constexpr int KTOT = C * KW;       // 576
 constexpr int WS = KTOT + 8;       // weight row stride (bf16)
 constexpr int XR = TT + 2 * PAD;   // staged positions per tile
 constexpr int XS = C + 8;          // staged row stride (bf16)
+constexpr int OS = TT + 8;         // output tile row stride (bf16), over the staging rows
+static_assert(C * OS <= XR * XS, "the output tile fits over the staged input");
 constexpr size_t SMEM = sizeof(__nv_bfloat16) * ((size_t)C * WS + (size_t)XR * XS);
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -51,8 +55,12 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+constexpr int CH = XR / 8;                                 // 16-byte chunks per channel and tile
+constexpr int NCH = (C * CH + NTHR - 1) / NTHR;            // chunks per thread
+
 __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __restrict__ x, int64_t Tp, int64_t T,
-                                                        const float* __restrict__ W, const float* __restrict__ bias,
+                                                        const __nv_bfloat16* __restrict__ Wm,
+                                                        const float* __restrict__ bias,
                                                         __nv_bfloat16* __restrict__ act_out, int vec) {
     extern __shared__ float4 smem4[];
     __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem4);      // [C][WS]
@@ -61,10 +69,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
     const int wm = warp >> 2, wn = warp & 3;                          // 2 x 4 warps of 32 x 32
     const int g = lane >> 2, tq = lane & 3;
 
-    // weights, once: Ws[co][k * 64 + ci] = W[co][ci][k] (W holds BF16-rounded values)
-    for (int i = tid; i < C * KTOT; i += NTHR) {
-        const int co = i / KTOT, r = i - co * KTOT, ci = r / KW, k = r - ci * KW;
-        Ws[co * WS + k * C + ci] = __float2bfloat16_rn(W[i]);
+    // weights, once: rows of KTOT BF16 copied into rows of WS
+    for (int i = tid; i < C * (KTOT / 8); i += NTHR) {
+        const int co = i / (KTOT / 8), u = i - co * (KTOT / 8);
+        *reinterpret_cast<uint4*>(Ws + co * WS + 8 * u) = *reinterpret_cast<const uint4*>(Wm + co * KTOT + 8 * u);
     }
     float bco[2][2];
 #pragma unroll
@@ -78,36 +86,72 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
     const int bn = (lane >> 4) * 8 + (lane & 7), bk = ((lane >> 3) & 1) * 8;
     const uint32_t b_base = smem_addr(Xs + (wn * 32 + bn) * XS + bk);
 
+    // Staging: chunk i = u * C + ci holds x[ci][t0 + 8u .. t0 + 8u + 8) (padded index); consecutive
+    // threads take consecutive channels, so the transposed 2-byte stores Xs[8u + e][ci] of a warp are
+    // consecutive. The next tile's chunks are loaded into registers while the current tile computes.
+    uint4 pre[NCH];
+    auto fetch = [&](int64_t t0) {
+#pragma unroll
+        for (int r = 0; r < NCH; ++r) {
+            const int i = tid + r * NTHR;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (i < C * CH) {
+                const int u = i / C, ci = i - u * C;
+                const int64_t tp = t0 + 8 * u;
+                const __nv_bfloat16* src = x + (int64_t)ci * Tp + tp;
+                if (vec && tp + 7 < Tp) {
+                    v = __ldg(reinterpret_cast<const uint4*>(src));
+                } else {
+                    __nv_bfloat16 tmp[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? src[e] : __float2bfloat16_rn(0.0f);
+                    v = *reinterpret_cast<const uint4*>(tmp);
+                }
+            }
+            pre[r] = v;
+        }
+    };
+    // two neighbouring channels swap halves with one shuffle, so that each stores bf16 pairs
+    // (ci, ci + 1) of 4 positions as 32-bit words: the even lane positions 0..3, the odd lane 4..7
+    auto stage = [&]() {
+#pragma unroll
+        for (int r = 0; r < NCH; ++r) {
+            const int i = tid + r * NTHR;             // C is even: a pair never straddles the guard
+            const int u = i / C, ci = i - u * C;
+            const bool odd = ci & 1;
+            uint4 mine = pre[r];
+            // send the half the partner stores, receive the partner's half of the same positions
+            const uint32_t s0 = odd ? mine.x : mine.z, s1 = odd ? mine.y : mine.w;
+            const uint32_t r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+            if (i < C * CH) {
+                // my 4 positions (even lane: e = 0..3 from .x .y; odd lane: e = 4..7 from .z .w)
+                const uint32_t m0 = odd ? mine.z : mine.x, m1 = odd ? mine.w : mine.y;
+                const __nv_bfloat16* mv = reinterpret_cast<const __nv_bfloat16*>(&m0);
+                const __nv_bfloat16* mw = reinterpret_cast<const __nv_bfloat16*>(&m1);
+                const __nv_bfloat16* pv = reinterpret_cast<const __nv_bfloat16*>(&r0);
+                const __nv_bfloat16* pw = reinterpret_cast<const __nv_bfloat16*>(&r1);
+                const __nv_bfloat16 my4[4] = {mv[0], mv[1], mw[0], mw[1]};
+                const __nv_bfloat16 pa4[4] = {pv[0], pv[1], pw[0], pw[1]};
+                const int e0 = odd ? 4 : 0, c0 = ci & ~1;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    __nv_bfloat162 w;
+                    w.x = odd ? pa4[e] : my4[e];      // channel c0
+                    w.y = odd ? my4[e] : pa4[e];      // channel c0 + 1
+                    *reinterpret_cast<__nv_bfloat162*>(Xs + (8 * u + e0 + e) * XS + c0) = w;
+                }
+            }
+        }
+    };
+
     const int64_t ntiles = (T + TT - 1) / TT;
+    if ((int64_t)blockIdx.x < ntiles) fetch((int64_t)blockIdx.x * TT);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t t0 = tile * TT;                 // first output position; staged rows = padded t0 ..
         __syncthreads();                              // previous tile's reads of Xs are done
-        // stage x[ci][t0 + r] (padded index) transposed into Xs[r][ci], r < XR, zero past Tp
-        if (vec) {
-            constexpr int CH = XR / 8;                // 16-byte chunks per channel
-            for (int i = tid; i < C * CH; i += NTHR) {
-                const int ci = i / CH, u = i - ci * CH;
-                const int64_t tp = t0 + 8 * u;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (tp + 7 < Tp) v = *reinterpret_cast<const uint4*>(x + (int64_t)ci * Tp + tp);
-                else {
-                    __nv_bfloat16 tmp[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? x[(int64_t)ci * Tp + tp + e] : __float2bfloat16_rn(0.0f);
-                    v = *reinterpret_cast<const uint4*>(tmp);
-                }
-                const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) Xs[(8 * u + e) * XS + ci] = e8[e];
-            }
-        } else {
-            for (int i = tid; i < C * XR; i += NTHR) {
-                const int ci = i / XR, r = i - ci * XR;
-                const int64_t tp = t0 + r;
-                Xs[r * XS + ci] = tp < Tp ? x[(int64_t)ci * Tp + tp] : __float2bfloat16_rn(0.0f);
-            }
-        }
+        stage();
         __syncthreads();
+        if (tile + gridDim.x < ntiles) fetch((tile + gridDim.x) * TT);
 
         float acc[2][4][4];
 #pragma unroll
@@ -132,27 +176,42 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
 #pragma unroll
                 for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni][0], b[ni][1]);
         }
-        // epilogue: bias, ReLU, BF16 -> act_out[co][t + PAD]
+        // epilogue: bias, ReLU, BF16 into an output tile Os[co][t] (over Xs once every warp is done),
+        // then 8-byte row segments to act_out[co][t0 + PAD + ...]
+        __syncthreads();
+        __nv_bfloat16* Os = Xs;                       // [C][OS]
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
             for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int h = e >> 1;
+                for (int h = 0; h < 2; ++h) {
                     const int co = wm * 32 + mi * 16 + g + 8 * h;
-                    const int64_t t = t0 + wn * 32 + ni * 8 + 2 * tq + (e & 1);
-                    if (t < T) {
-                        const float v = fmaxf(acc[mi][ni][e] + bco[mi][h], 0.0f);
-                        act_out[(int64_t)co * Tp + t + PAD] = __float2bfloat16_rn(v);
-                    }
+                    const int n = wn * 32 + ni * 8 + 2 * tq;
+                    __nv_bfloat162 w;
+                    w.x = __float2bfloat16_rn(fmaxf(acc[mi][ni][2 * h] + bco[mi][h], 0.0f));
+                    w.y = __float2bfloat16_rn(fmaxf(acc[mi][ni][2 * h + 1] + bco[mi][h], 0.0f));
+                    *reinterpret_cast<__nv_bfloat162*>(Os + co * OS + n) = w;
                 }
+        __syncthreads();
+        for (int i = tid; i < C * (TT / 4); i += NTHR) {
+            const int co = i / (TT / 4), u = i - co * (TT / 4);
+            const int64_t t = t0 + 4 * u;
+            __nv_bfloat16* dst = act_out + (int64_t)co * Tp + t + PAD;
+            const __nv_bfloat16* src = Os + co * OS + 4 * u;
+            if (vec && t + 3 < T) {
+                *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
+            } else {
+                for (int e = 0; e < 4; ++e)
+                    if (t + e < T) dst[e] = src[e];
+            }
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const float* W, const float* b,
+cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const __nv_bfloat16* Wm, const float* b,
                            __nv_bfloat16* act, cudaStream_t s) {
     static int resident = 0;
     if (!resident) {
@@ -165,8 +224,8 @@ cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const 
     }
     const int64_t ntiles = (T + TT - 1) / TT;
     const int grid = (int)std::min<int64_t>(ntiles, resident);
-    // 16-byte staging loads need 16-byte aligned rows
-    const int vec = ((uintptr_t)x % 16 == 0) && (Tp % 8 == 0);
-    k_conv64_mma<<<grid, NTHR, SMEM, s>>>(x, Tp, T, W, b, act, vec);
+    // 16-byte staging loads need 16-byte aligned input rows, the 8-byte stores 8-byte aligned output rows
+    const int vec = ((uintptr_t)x % 16 == 0) && ((uintptr_t)act % 16 == 0) && (Tp % 8 == 0);
+    k_conv64_mma<<<grid, NTHR, SMEM, s>>>(x, Tp, T, Wm, b, act, vec);
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@ struct CnnBufs {
     float* grad = nullptr;          // FP32 gradients of the last backward
     float* wfwd = nullptr;          // BF16-rounded parameters as used by the forward
     float* wbwd = nullptr;          // transposed, flipped BF16-rounded weights for the data gradient
+    __nv_bfloat16* wtc = nullptr;  // BF16 weights of the two 64->64 layers as [co][k * 64 + ci] (tensor cores)
     int* offs_dev = nullptr;        // off[] on the device (int)
     int* cin_dev = nullptr;
     int* cout_dev = nullptr;
@@ -32,6 +33,7 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);
 cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s);
 cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s);
-// one 64 -> 64 forward convolution (bias, ReLU, BF16 out) on the tensor cores (k_cnn_mma.cu)
-cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const float* W, const float* b,
+// one 64 -> 64 forward convolution (bias, ReLU, BF16 out) on the tensor cores (k_cnn_mma.cu);
+// Wm: the layer's BF16 weights as [co][k * 64 + ci]
+cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const __nv_bfloat16* Wm, const float* b,
                            __nv_bfloat16* act, cudaStream_t s);
