@@ -106,6 +106,20 @@ struct rx_handle {
     cudaStream_t last = nullptr;
     cudaStream_t side = nullptr;   // the rest of a frame's FD compensation, beside the acquisition
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_host = nullptr;
+    // replay of a single frame's launches as one CUDA graph, per entry point (device / host buffers)
+    struct FrameGraph {
+        bool valid = false, timing = false;
+        const void* in = nullptr;
+        const void* ref = nullptr;
+        void* out = nullptr;
+        int64_t n = 0;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t nl = 0;                // kernels per replay
+        int events[ST_N] = {0};         // stage events recorded per replay
+    } graph[2];
+    cudaStream_t capstream = nullptr;  // graphs are captured here
+    bool graphs_ok = true;
+    bool capturing = false;
     uint64_t launches = 0;
     cudaError_t last_err = cudaSuccess;
     // timing
@@ -137,15 +151,17 @@ struct StageScope {
     int s;
     cudaStream_t st;
     bool on;
+    // while a frame is captured into a graph the events must be recorded by the graph itself
+    // (an external record), not taken as a capture dependency
     StageScope(rx_handle* h_, int s_, cudaStream_t st_) : h(h_), s(s_), st(st_), on(h_->timing) {
         if (on) {
             if (h->used[s] >= kPool) timing_flush(h);
-            cudaEventRecord(h->ev0[s][h->used[s]], st);
+            cudaEventRecordWithFlags(h->ev0[s][h->used[s]], st, h->capturing ? cudaEventRecordExternal : 0);
         }
     }
     ~StageScope() {
         if (on) {
-            cudaEventRecord(h->ev1[s][h->used[s]], st);
+            cudaEventRecordWithFlags(h->ev1[s][h->used[s]], st, h->capturing ? cudaEventRecordExternal : 0);
             h->used[s] += 1;
         }
     }
@@ -207,6 +223,9 @@ void free_all(rx_handle* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_host) cudaEventDestroy(h->ev_host);
+    for (auto& g : h->graph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (h->capstream) cudaStreamDestroy(h->capstream);
     if (h->side) cudaStreamDestroy(h->side);
 }
 
@@ -298,6 +317,7 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     A(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     A(cudaEventCreateWithFlags(&h->ev_host, cudaEventDisableTiming));
+    A(cudaStreamCreateWithFlags(&h->capstream, cudaStreamNonBlocking));
     for (int s = 0; s < ST_N && e == cudaSuccess; ++s) {
         h->ev0[s].resize(kPool);
         h->ev1[s].resize(kPool);
@@ -335,8 +355,8 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     return RX_OK;
 }
 
-rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32_t* d_ref, uint32_t* d_out,
-                     rx_stream_t stream_) {
+static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, const uint32_t* d_ref, uint32_t* d_out,
+                               rx_stream_t stream_) {
     if (!h || !d_in || n_sym < 1 || n_sym > h->Nmax) return RX_EINVAL;
     const rx_config& c = h->cfg;
     const bool stream_mode = c.streaming != 0;
@@ -555,8 +575,8 @@ rx_status rx_decide(rx_handle* h, const float* d_z, int64_t n_sym, const uint32_
     return RX_OK;
 }
 
-rx_status rx_process_host(rx_handle* h, const void* h_in, int64_t n_sym, const uint32_t* h_ref, uint32_t* h_out,
-                          rx_stream_t stream_) {
+static rx_status enqueue_host(rx_handle* h, const void* h_in, int64_t n_sym, const uint32_t* h_ref, uint32_t* h_out,
+                              rx_stream_t stream_) {
     if (!h || !h_in || n_sym < 1 || n_sym > h->Nmax) return RX_EINVAL;
     cudaStream_t s = (cudaStream_t)stream_;
     const int64_t S = 2 * n_sym;
@@ -592,14 +612,99 @@ rx_status rx_process_host(rx_handle* h, const void* h_in, int64_t n_sym, const u
         if (h_ref)
             RX_CK(cudaMemcpyAsync(h->stage_ref, h_ref, sizeof(uint32_t) * 2 * words, cudaMemcpyHostToDevice, s));
     }
-    rx_status r = rx_process(h, h->stage_in, n_sym, h_ref ? h->stage_ref : nullptr, h_out ? h->stage_out : nullptr,
-                             stream_);
+    rx_status r = enqueue_frame(h, h->stage_in, n_sym, h_ref ? h->stage_ref : nullptr,
+                                h_out ? h->stage_out : nullptr, stream_);
     if (r != RX_OK) return r;
     if (h_out) {
         StageScope sc(h, ST_D2H, s);
         RX_CK(cudaMemcpyAsync(h_out, h->stage_out, sizeof(uint32_t) * 2 * words, cudaMemcpyDeviceToHost, s));
     }
     return RX_OK;
+}
+
+// Single frames replay their launches as one CUDA graph, captured on the first call with a given set
+// of buffers and frame length (and timing on or off): the frame's launches carry no host-side state
+// that changes between frames. Streams of frames (each frame's launch arguments change), calls on a
+// stream that is itself being captured (the batch) and a handle whose capture failed once run the
+// launches directly. With stage timing on, the graph holds the stage events; their times are
+// collected before the next replay records them again.
+static rx_status run_graph(rx_handle* h, int which, const void* in, int64_t n_sym, const void* ref, void* out,
+                           cudaStream_t s, bool& done) {
+    done = false;
+    if (h->cfg.streaming || !h->graphs_ok) return RX_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return RX_OK;
+    rx_handle::FrameGraph& g = h->graph[which];
+    if (h->timing) timing_flush(h);                   // stage events of the previous frame, if any
+    const bool hit = g.valid && g.timing == h->timing && g.in == in && g.ref == ref && g.out == out && g.n == n_sym;
+    if (!hit) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = rx_handle::FrameGraph{};
+        const uint64_t l0 = h->launches, f0 = h->frames, s0 = h->sym_processed;
+        if (cudaStreamBeginCapture(h->capstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            h->graphs_ok = false;
+            return RX_OK;
+        }
+        h->capturing = true;
+        rx_status r = which == 0 ? enqueue_frame(h, in, n_sym, static_cast<const uint32_t*>(ref),
+                                                 static_cast<uint32_t*>(out), h->capstream)
+                                 : enqueue_host(h, in, n_sym, static_cast<const uint32_t*>(ref),
+                                                static_cast<uint32_t*>(out), h->capstream);
+        h->capturing = false;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->capstream, &graph);
+        const uint64_t nl_cap = h->launches - l0;     // what one replay adds
+        h->launches = l0;
+        h->frames = f0;
+        h->sym_processed = s0;
+        cudaGraphExec_t exec = nullptr;
+        const bool ok = r == RX_OK && ec == cudaSuccess && graph &&
+                        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            // e.g. pageable host buffers cannot be captured: run this handle's frames directly
+            cudaGetLastError();
+            for (int st = 0; st < ST_N; ++st) h->used[st] = 0;
+            h->graphs_ok = false;
+            return RX_OK;
+        }
+        g.valid = true;
+        g.timing = h->timing;
+        g.in = in;
+        g.ref = ref;
+        g.out = out;
+        g.n = n_sym;
+        g.exec = exec;
+        g.nl = nl_cap;
+        for (int st = 0; st < ST_N; ++st) g.events[st] = h->used[st];   // stage events each replay records
+    }
+    RX_CK(cudaGraphLaunch(g.exec, s));
+    h->last = s;
+    h->frames += 1;
+    h->sym_processed += 2 * (uint64_t)n_sym;
+    h->launches += g.nl;
+    for (int st = 0; st < ST_N; ++st) h->used[st] = g.events[st];
+    done = true;
+    return RX_OK;
+}
+
+rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32_t* d_ref, uint32_t* d_out,
+                     rx_stream_t stream_) {
+    if (!h || !d_in || n_sym < 1 || n_sym > h->Nmax) return RX_EINVAL;
+    bool done = false;
+    rx_status r = run_graph(h, 0, d_in, n_sym, d_ref, d_out, (cudaStream_t)stream_, done);
+    if (r != RX_OK || done) return r;
+    return enqueue_frame(h, d_in, n_sym, d_ref, d_out, stream_);
+}
+
+rx_status rx_process_host(rx_handle* h, const void* h_in, int64_t n_sym, const uint32_t* h_ref, uint32_t* h_out,
+                          rx_stream_t stream_) {
+    if (!h || !h_in || n_sym < 1 || n_sym > h->Nmax) return RX_EINVAL;
+    bool done = false;
+    rx_status r = run_graph(h, 1, h_in, n_sym, h_ref, h_out, (cudaStream_t)stream_, done);
+    if (r != RX_OK || done) return r;
+    return enqueue_host(h, h_in, n_sym, h_ref, h_out, stream_);
 }
 
 rx_status rx_stats(rx_handle* h, rx_stats_t* out) {
