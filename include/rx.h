@@ -154,6 +154,12 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out);
  * polarisation, quarter turn applied, in output order.
  * Asynchronous on `stream`; RX_EINVAL for n_sym < 1, n_sym > max_symbols or
  * (streaming) n_sym not a multiple of fft_size / 4.
+ * Single-frame handles record the frame's launches as a CUDA graph on the
+ * first call with a given (d_in, n_sym, d_ref_bits, d_out_bits) and replay it
+ * on later calls with the same pointers and length (the data may change);
+ * when the pointers change on three calls in a row, or a capture fails, the
+ * handle launches directly from then on. Calls on a stream that the caller is
+ * capturing always launch directly into that capture.
  */
 rx_status rx_process(rx_handle* h, const void* d_in, int64_t n_sym, const uint32_t* d_ref_bits,
                      uint32_t* d_out_bits, rx_stream_t stream);

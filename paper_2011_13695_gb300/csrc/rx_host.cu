@@ -120,6 +120,7 @@ struct rx_handle {
     cudaStream_t capstream = nullptr;  // graphs are captured here
     bool graphs_ok = true;
     bool capturing = false;
+    int graph_misses = 0;               // captures in a row without a replay
     uint64_t launches = 0;
     cudaError_t last_err = cudaSuccess;
     // timing
@@ -637,6 +638,12 @@ static rx_status run_graph(rx_handle* h, int which, const void* in, int64_t n_sy
     rx_handle::FrameGraph& g = h->graph[which];
     if (h->timing) timing_flush(h);                   // stage events of the previous frame, if any
     const bool hit = g.valid && g.timing == h->timing && g.in == in && g.ref == ref && g.out == out && g.n == n_sym;
+    if (hit) h->graph_misses = 0;
+    if (!hit && ++h->graph_misses > 2) {
+        // buffers or lengths change from call to call: capturing would cost more than it saves
+        h->graphs_ok = false;
+        return RX_OK;
+    }
     if (!hit) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g = rx_handle::FrameGraph{};
