@@ -606,11 +606,11 @@ def learned_arm(args) -> None:
         "evm_gain_db": 20 * np.log10(plain["evm"] / learned["evm"]),
         "train": {"ms": train_ms, "tflops": train_tflops, "loss_first": float(losses[:20].mean()),
                   "loss_last": float(losses[-20:].mean()), "train_plain_ber": [s_["ber"] for s_ in train_stats]},
-        "roofline": {"kernel": "cnn forward (k_conv64_mma x 2 on tensor cores, edge layers on CUDA cores)",
+        "roofline": {"kernel": "cnn forward (k_conv_tc: 4 tcgen05 launches, one per layer)",
                      "bound": "tensor", "achieved": fwd_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                      "frac": fwd_tflops / bf16_peak, "traffic": None,
                      "peak_source": "fallback" if pk.get("fallback") else "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
-                     "note": "whole forward's algorithmic flops over its time (4 conv launches + channel split)"},
+                     "note": "whole forward's algorithmic flops over its time (4 conv launches)"},
         "cnn_ms": tc, "gpu_launches": int(launches), "generate_s": round(gen_s, 1), "clocks": clk.summary(),
     }
     print(json.dumps(line))

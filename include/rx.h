@@ -64,6 +64,7 @@ typedef enum { RX_IN_C64 = 0, RX_IN_F16 = 1, RX_IN_I8 = 2 } rx_input;
 #define RX_ERR_NONFINITE 0x1u   /* a non-finite sample reached the equaliser */
 #define RX_ERR_SYNC_LOST 0x2u   /* best alignment matched < 90 % of the sync window */
 #define RX_ERR_SINGULAR 0x4u    /* CMA outputs still correlated after the rerun */
+#define RX_ERR_TIMEOUT 0x8u     /* a bounded wait inside a pipelined kernel ran out; outputs invalid */
 
 typedef struct rx_config {
     int32_t bits_per_sym;       /* m per polarisation: 2 (QPSK), 4 (16QAM), 6 (64QAM) */
@@ -273,7 +274,13 @@ int64_t rx_pe_param_count(int32_t channels, int32_t kernel);
 rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const float* h_params, rx_pe** out);
 /* current FP32 master parameters into h_params (synchronises) */
 rx_status rx_pe_params(rx_pe* p, float* h_params);
+/* inference: d_out = d_z + f(d_z). Runs on the tcgen05 tensor cores with the hidden activations in
+ * channel-chunk planes [C/8][T + 8][8]; training (rx_pe_gradients, rx_pe_train_step) keeps its own
+ * forward. */
 rx_status rx_pe_forward(rx_pe* p, const float* d_z, int64_t T, float* d_out, rx_stream_t stream);
+/* the post-equaliser's device error word (RX_ERR_TIMEOUT if a pipelined kernel gave up a wait;
+ * synchronises) */
+rx_status rx_pe_error_word(rx_pe* p, uint32_t* out);
 /* loss (mean squared error) and its gradient w.r.t. every parameter, without updating them */
 rx_status rx_pe_gradients(rx_pe* p, const float* d_z, const float* d_target, int64_t T, float* d_grads, float* d_loss,
                           rx_stream_t stream);

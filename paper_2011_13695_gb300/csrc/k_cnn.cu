@@ -192,16 +192,17 @@ __global__ void k_weights(const float* __restrict__ master, int64_t n, float* __
     const __nv_bfloat16 vb = __float2bfloat16_rn(master[i]);
     const float v = __bfloat162float(vb);
     fwd[i] = v;
-    // locate the layer and, for weights, the transposed position (and the tensor-core layout of the
-    // two hidden layers: [co][k * C + ci])
+    // locate the layer and, for weights, the transposed position and the tensor-core copy in (k, ci)
+    // order (rows of 9 * cin, the input layer's padded to 48)
     for (int l = 0; l < 4; ++l) {
         const int64_t wo = offs[2 * l], nw = (int64_t)couts[l] * cins[l] * KW;
         if (i >= wo && i < wo + nw) {
             const int64_t r = i - wo;
             const int co = (int)(r / (cins[l] * KW)), ci = (int)((r / KW) % cins[l]), k = (int)(r % KW);
             bwd[wo + ((int64_t)ci * couts[l] + co) * KW + (KW - 1 - k)] = v;
-            if (l == 1 || l == 2)
-                wtc[(int64_t)(l - 1) * couts[l] * cins[l] * KW + ((int64_t)co * KW + k) * cins[l] + ci] = vb;
+            const int C = cins[1];
+            const int row = l == 0 ? 48 : cins[l] * KW;
+            wtc[wtc_offset(C, l) + (int64_t)co * row + k * cins[l] + ci] = vb;
         }
     }
 }
@@ -250,10 +251,9 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* ou
     e = conv_t<__nv_bfloat16, 4, 64, 0>(B.act[0], Tp, T, W + B.off[0], W + B.off[1], B.act[1], nullptr, nullptr, nullptr,
                                         nullptr, s);
     if (e) return e;
-    const int64_t lw = (int64_t)C * C * KW;
-    e = conv64_mma_fwd(B.act[1], Tp, T, B.wtc, W + B.off[3], B.act[2], s);
+    e = conv64_mma_fwd(B.act[1], Tp, T, B.wtc + wtc_offset(C, 1), W + B.off[3], B.act[2], s);
     if (e) return e;
-    e = conv64_mma_fwd(B.act[2], Tp, T, B.wtc + lw, W + B.off[5], B.act[3], s);
+    e = conv64_mma_fwd(B.act[2], Tp, T, B.wtc + wtc_offset(C, 2), W + B.off[5], B.act[3], s);
     if (e) return e;
     return conv_t<__nv_bfloat16, 64, 4, 1>(B.act[3], Tp, T, W + B.off[6], W + B.off[7], nullptr, nullptr, nullptr, z,
                                            out, s);

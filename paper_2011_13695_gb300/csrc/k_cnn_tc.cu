@@ -1,0 +1,475 @@
+// Inference forward of the learned post-equaliser on the 5th-generation tensor
+// cores (tcgen05.mma, BF16 x BF16 -> FP32 accumulators in tensor memory).
+//
+// Each layer is a matrix product per tile of 128 output positions:
+//   D[t][co] = sum_K A[t][K] B[K][co],  K = (k, ci),
+//   A[t][(k, ci)] = x[ci][t + k - 4],   B[(k, ci)][co] = W[co][ci][k],
+// M = 128 positions (one TMEM lane each), N = the output channels (64, or 16
+// with 12 zero rows for the 4-channel output layer), K = 9 taps x the input
+// channels in steps of 16.
+//
+// Activation layout (HBM): the hidden layers' BF16 activations are stored in
+// eight channel-chunk planes [C/8][T + 8][8], padded position-major, so that
+// a chunk of 8 channels of one position is one 16-byte row. Staged to shared
+// memory unchanged (one bulk async copy per plane and tile), this is the
+// K-major no-swizzle operand layout of the MMA (core matrices of 8 rows x 16
+// bytes, rows 16 bytes apart, 8-row groups 128 bytes apart, K chunks one plane
+// apart), and the operand of tap k is the same planes read from row k: the
+// descriptor's start address moves by 16 k bytes, always 16-byte aligned.
+// The input layer (4 -> 64) builds its operand from the FP32 symbols:
+// K = (tap, channel) with 4 channels, padded to 48 with zero weights, six
+// planes whose row r holds the 8 values of taps 2j, 2j + 1 at position r.
+//
+// Roles (warp-specialised, one CTA per SM slot, tiles strided over the grid):
+//   warps 0-3  epilogue: TMEM lane quarter w holds positions 32 w .. 32 w + 31;
+//              bias, ReLU, BF16 and a 16-byte store per plane (coalesced), or
+//              for the output layer bias + residual into the symbols;
+//   producer   one thread issuing the bulk copies of a stage (hidden, output
+//              layers), or four warps building the input layer's planes;
+//   last warp  TMEM allocation, and one thread issuing the MMAs of a tile
+//              into one of two accumulator buffers and committing them to
+//              the stage-free and accumulator-full barriers.
+// Every wait is bounded (globaltimer); on a timeout the CTA sets the error
+// word, stops all roles, waits for its own copies and MMAs in flight (again
+// bounded) and frees its tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "../../include/rx.h"
+#include "rx_cnn.h"
+
+namespace {
+
+constexpr int KW = 9;
+constexpr int PAD = KW / 2;
+constexpr int TT = 128;                        // positions per tile (MMA M)
+constexpr int XR = TT + 2 * PAD;               // staged rows per tile (hidden/output layers)
+constexpr uint64_t kTimeoutNs = 500000000ull;  // 0.5 s per wait
+
+enum Mode { IN = 0, HID = 1, OUT = 2 };
+
+template <int MODE>
+struct TcShape {
+    static constexpr int NCO = MODE == OUT ? 16 : 64;                 // MMA N
+    static constexpr int COUT = MODE == OUT ? 4 : 64;
+    static constexpr int NKC = MODE == IN ? 6 : 72;                   // K chunks of 8 (K = 48 or 576)
+    static constexpr int NKS = NKC / 2;                               // MMAs of K = 16 per tile
+    static constexpr int ROWS = MODE == IN ? TT : XR;                 // rows of a staged plane
+    static constexpr int PLANE = ROWS * 16;                           // bytes
+    static constexpr int NPL = MODE == IN ? 6 : 8;                    // planes per stage
+    static constexpr int STAGE = NPL * PLANE;
+    static constexpr int S = MODE == IN ? 3 : 4;                      // pipeline stages
+    static constexpr int WB = NKC * NCO * 16;                         // weight bytes: planes [kc][co][8]
+    static constexpr int NPW = MODE == IN ? 4 : 1;                    // producer warps
+    static constexpr int NWARP = 4 + NPW + 1;
+    static constexpr int NTHR = 32 * NWARP;
+    static constexpr int TCOLS = MODE == OUT ? 32 : 128;              // TMEM columns (2 accumulators)
+    static constexpr int FROWS = TT + 12;                             // input layer: staged positions
+    // shared memory: weights, stages, (input layer) staged positions, then a slack region so that
+    // no operand read can leave the allocation, then barriers and small state
+    static constexpr int OFF_ST = WB;
+    static constexpr int OFF_F = OFF_ST + S * STAGE;
+    static constexpr int OFF_SLACK = OFF_F + (MODE == IN ? FROWS * 8 : 0);
+    static constexpr int SLACK = 40960;
+    static constexpr int OFF_BAR = (OFF_SLACK + SLACK + 15) & ~15;
+    static constexpr int NBAR = 2 * S + 4;
+    static constexpr int OFF_MISC = OFF_BAR + 8 * NBAR;               // tmem address, abort flag
+    static constexpr int OFF_BIAS = OFF_MISC + 16;
+    static constexpr int SMEM = OFF_BIAS + 4 * 64;
+    // instruction descriptor (kind::f16): F32 accumulator, BF16 A and B, both K-major, N >> 3, M >> 4
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCO >> 3) << 17) |
+                                      ((uint32_t)(TT >> 4) << 24);
+    static_assert(STAGE % 16 == 0 && WB % 16 == 0 && PLANE % 16 == 0, "16-byte aligned operands");
+    static_assert(NCO % 16 == 0 && NCO >= 16 && NCO <= 256, "M = 128 needs N a multiple of 16");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase of the given parity to complete; false on a timeout (which raises the CTA's
+// abort flag) or when another role has raised it
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!mbar_try(bar, parity)) {
+        if (*abort) return false;
+        if (gtimer() - t0 > kTimeoutNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// bounded wait used while shutting down (ignores the abort flag)
+__device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try(bar, parity))
+        if (gtimer() - t0 > kTimeoutNs) return;
+}
+
+// named barrier 1 over the 128 threads of the input layer's producer warps, OR of a predicate
+__device__ __forceinline__ bool bar_or_128(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory operand descriptor, K-major without swizzle: start, leading (K-direction core
+// matrix) byte offset, stride (8-row group) byte offset, fixed field 0b001 at bit 46
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive accumulator columns of this warp's 32 lanes, waited for in the same statement so
+// that no use of the registers can be scheduled before the load completes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+struct TcArgs {
+    const __nv_bfloat16* x;      // planar input activations [8][Tp][8] (hidden, output layers)
+    const float2* z;             // symbols [2][T] (input layer operand, output layer residual)
+    const __nv_bfloat16* Wm;     // BF16 weights [co][K] (K = k * CIN + ci; the input layer padded to 48)
+    const float* bias;           // [COUT]
+    __nv_bfloat16* act;          // planar output activations (input, hidden layers)
+    float2* sym;                 // output symbols [2][T] (output layer)
+    __nv_bfloat16* pads[3];      // input layer: planar buffers whose padding rows CTA 0 zeroes
+    int64_t T, Tp;
+    unsigned int* err;           // error word (RX_ERR_TIMEOUT on a stalled wait)
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
+    using S = TcShape<MODE>;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sbase = smem_u32(sm);
+    const uint32_t sW = sbase, sSt = sbase + S::OFF_ST;
+    const uint32_t bar0 = sbase + S::OFF_BAR;
+    auto in_full = [&](int s) { return bar0 + 8u * s; };
+    auto in_empty = [&](int s) { return bar0 + 8u * (S::S + s); };
+    auto acc_full = [&](int b) { return bar0 + 8u * (2 * S::S + b); };
+    auto acc_empty = [&](int b) { return bar0 + 8u * (2 * S::S + 2 + b); };
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S::OFF_MISC);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + S::OFF_MISC + 4);
+    float* bias_s = reinterpret_cast<float*>(sm + S::OFF_BIAS);
+    const int mma_warp = S::NWARP - 1;
+    const int64_t T = a.T, Tp = a.Tp;
+    const int64_t ntiles = (T + TT - 1) / TT;
+
+    // weights: 16-byte chunk (co, kc) of the row-major copy into plane kc, row co; rows COUT..NCO zero
+    for (int i = tid; i < S::NKC * S::NCO; i += S::NTHR) {
+        const int co = i / S::NKC, kc = i - co * S::NKC;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (co < S::COUT) v = __ldg(reinterpret_cast<const uint4*>(a.Wm + ((int64_t)co * S::NKC + kc) * 8));
+        *reinterpret_cast<uint4*>(sm + kc * S::NCO * 16 + co * 16) = v;
+    }
+    for (int i = tid; i < S::COUT; i += S::NTHR) bias_s[i] = a.bias[i];
+    if (tid == 0) {
+        *abort = 0;
+        for (int s = 0; s < S::S; ++s) {
+            mbar_init(in_full(s), MODE == IN ? 32 * S::NPW : 1);
+            mbar_init(in_empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full(b), 1);
+            mbar_init(acc_empty(b), 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == mma_warp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)S::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the input layer's CTA 0 zeroes the padding rows of the three planar activation buffers
+    if (MODE == IN && blockIdx.x == 0) {
+        for (int i = tid; i < 3 * 8 * 2 * PAD; i += S::NTHR) {
+            const int buf = i / (8 * 2 * PAD), r = i - buf * 8 * 2 * PAD, cc = r / (2 * PAD), u = r - cc * 2 * PAD;
+            const int64_t row = u < PAD ? u : T + u;           // [0, PAD) and [T + PAD, Tp)
+            __nv_bfloat16* pb = buf == 0 ? a.pads[0] : buf == 1 ? a.pads[1] : a.pads[2];
+            if (pb) *reinterpret_cast<uint4*>(pb + ((int64_t)cc * Tp + row) * 8) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    fence_async_smem();                                       // weights written by threads, read by the MMA
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ---- epilogue ----
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int ab = it & 1;
+            const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
+            if (!__all_sync(0xffffffffu, ok)) break;      // warp-uniform: the loads below are .sync.aligned
+            tc_after();
+            const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::NCO);
+            const int64_t t = tile * TT + 32 * warp + lane;   // this thread's output position
+            if constexpr (MODE == OUT) {
+                float v[4];
+                tmem_ld4(tl, v);
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty(ab));
+                if (t < T) {
+                    const float2 z0 = a.z[t], z1 = a.z[T + t];
+                    a.sym[t] = make_float2(z0.x + v[0] + bias_s[0], z0.y + v[1] + bias_s[1]);
+                    a.sym[T + t] = make_float2(z1.x + v[2] + bias_s[2], z1.y + v[3] + bias_s[3]);
+                }
+            } else {
+                float v[64];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tmem_ld16(tl + 16 * q, v + 16 * q);
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty(ab));
+                if (t < T) {
+                    __nv_bfloat16* dst = a.act + (t + PAD) * 8;
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        float w[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) w[e] = fmaxf(v[8 * cc + e] + bias_s[8 * cc + e], 0.0f);
+                        uint4 o;
+                        o.x = pack_bf16(w[0], w[1]);
+                        o.y = pack_bf16(w[2], w[3]);
+                        o.z = pack_bf16(w[4], w[5]);
+                        o.w = pack_bf16(w[6], w[7]);
+                        *reinterpret_cast<uint4*>(dst + (int64_t)cc * Tp * 8) = o;
+                    }
+                }
+            }
+        }
+    } else if (warp < 4 + S::NPW) {
+        // ---- producer ----
+        int it = 0, issued = 0;
+        if constexpr (MODE == IN) {
+            const int r = tid - 128;                          // 0 .. 127
+            unsigned char* F = sm + S::OFF_F;                 // [FROWS][4] BF16: position t0 - 4 + u
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int s = it % S::S;
+                bool ok = true;
+                if (r == 0) ok = mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort);
+                // one decision for the 128 producer threads; also orders the previous tile's reads of F
+                if (bar_or_128(!ok || *abort)) break;
+                const int64_t t0 = tile * TT;
+                for (int u = r; u < S::FROWS; u += 128) {
+                    const int64_t tt = t0 - PAD + u;
+                    float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
+                    if (tt >= 0 && tt < T) {
+                        z0 = a.z[tt];
+                        z1 = a.z[T + tt];
+                    }
+                    *reinterpret_cast<uint2*>(F + 8 * u) = make_uint2(pack_bf16(z0.x, z0.y), pack_bf16(z1.x, z1.y));
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                unsigned char* st = sm + S::OFF_ST + s * S::STAGE;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    const uint2 lo = *reinterpret_cast<const uint2*>(F + 8 * (r + 2 * j));
+                    const uint2 hi = *reinterpret_cast<const uint2*>(F + 8 * (r + 2 * j + 1));
+                    *reinterpret_cast<uint4*>(st + j * S::PLANE + 16 * r) = make_uint4(lo.x, lo.y, hi.x, hi.y);
+                }
+                fence_async_smem();
+                mbar_arrive(in_full(s));
+            }
+        } else {
+            if (lane == 0) {
+                for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                    const int s = it % S::S;
+                    if (!mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort)) break;
+                    const int64_t t0 = tile * TT;             // staged row u = padded position t0 + u
+                    const int rows = (int)min((int64_t)XR, Tp - t0);
+                    mbar_arrive_tx(in_full(s), (uint32_t)(8 * rows * 16));
+                    for (int cc = 0; cc < 8; ++cc)
+                        bulk_g2s(sSt + s * S::STAGE + cc * S::PLANE, a.x + ((int64_t)cc * Tp + t0) * 8,
+                                 (uint32_t)(rows * 16), in_full(s));
+                    issued = it + 1;
+                }
+                // copies still in flight after an abort land before the CTA exits
+                if (*abort)
+                    for (int i = max(0, issued - S::S); i < issued; ++i)
+                        mbar_drain(in_full(i % S::S), (uint32_t)((i / S::S) & 1));
+            }
+        }
+    } else if (lane == 0) {
+        // ---- MMA issue ----
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it % S::S, ab = it & 1;
+            if (!mbar_wait(in_full(s), (uint32_t)((it / S::S) & 1), abort)) break;
+            if (!mbar_wait(acc_empty(ab), (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
+            tc_after();
+            const uint32_t d = tmem + (uint32_t)(ab * S::NCO);
+            const uint32_t st = sSt + s * S::STAGE;
+#pragma unroll 4
+            for (int ks = 0; ks < S::NKS; ++ks) {
+                uint32_t aaddr, baddr;
+                if constexpr (MODE == IN) {
+                    aaddr = st + 2 * ks * S::PLANE;
+                    baddr = sW + 2 * ks * S::NCO * 16;
+                } else {
+                    const int k = ks >> 2, j = ks & 3;        // tap, 16-channel group
+                    aaddr = st + 2 * j * S::PLANE + 16 * k;
+                    baddr = sW + (8 * k + 2 * j) * S::NCO * 16;
+                }
+                mma_ss(d, sdesc(aaddr, S::PLANE, 128), sdesc(baddr, S::NCO * 16, 128), S::IDESC, ks > 0 ? 1u : 0u);
+            }
+            mma_commit(in_empty(s));
+            mma_commit(acc_full(ab));
+        }
+        // the last MMAs (and the stage-free arrivals they signal) complete before the CTA exits and
+        // its tensor memory is freed
+        for (int i = max(0, it - S::S); i < it; ++i) mbar_drain(in_empty(i % S::S), (uint32_t)((i / S::S) & 1));
+    }
+
+    tc_before();
+    __syncthreads();
+    if (*abort && tid == 0) atomicOr(a.err, RX_ERR_TIMEOUT);
+    if (warp == mma_warp) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TCOLS)
+                     : "memory");
+    }
+}
+
+template <int MODE>
+cudaError_t launch_tc(const TcArgs& a, cudaStream_t s) {
+    using S = TcShape<MODE>;
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, nsm = 152, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        if (e) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<MODE>, S::NTHR, S::SMEM);
+        resident = std::max(1, nsm * std::max(1, per));
+    }
+    const int64_t ntiles = (a.T + TT - 1) / TT;
+    if (ntiles <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(ntiles, resident);
+    k_conv_tc<MODE><<<grid, S::NTHR, S::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// the inference forward on the tensor cores: symbols -> act[1] -> act[2] -> act[3] (planar) -> out
+cudaError_t cnn_infer_tc(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s) {
+    if (B.C != 64) return cudaErrorInvalidValue;
+    const int64_t Tp = T + 2 * PAD;
+    const float* Wf = B.wfwd;
+    TcArgs a{};
+    a.T = T;
+    a.Tp = Tp;
+    a.z = z;
+    a.err = B.err;
+    // layer 0: 4 -> 64 from the symbols; also zeroes the padding rows of the three planar buffers
+    a.Wm = B.wtc + wtc_offset(B.C, 0);
+    a.bias = Wf + B.off[1];
+    a.act = B.act[1];
+    a.pads[0] = B.act[1];
+    a.pads[1] = B.act[2];
+    a.pads[2] = B.act[3];
+    cudaError_t e = launch_tc<IN>(a, s);
+    if (e) return e;
+    a.pads[0] = a.pads[1] = a.pads[2] = nullptr;
+    // layers 1, 2: 64 -> 64
+    a.x = B.act[1];
+    a.Wm = B.wtc + wtc_offset(B.C, 1);
+    a.bias = Wf + B.off[3];
+    a.act = B.act[2];
+    if ((e = launch_tc<HID>(a, s))) return e;
+    a.x = B.act[2];
+    a.Wm = B.wtc + wtc_offset(B.C, 2);
+    a.bias = Wf + B.off[5];
+    a.act = B.act[3];
+    if ((e = launch_tc<HID>(a, s))) return e;
+    // layer 3: 64 -> 4, bias and the residual into the output symbols
+    a.x = B.act[3];
+    a.Wm = B.wtc + wtc_offset(B.C, 3);
+    a.bias = Wf + B.off[7];
+    a.act = nullptr;
+    a.sym = out;
+    return launch_tc<OUT>(a, s);
+}

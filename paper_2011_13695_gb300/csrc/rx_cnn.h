@@ -17,7 +17,9 @@ struct CnnBufs {
     float* grad = nullptr;          // FP32 gradients of the last backward
     float* wfwd = nullptr;          // BF16-rounded parameters as used by the forward
     float* wbwd = nullptr;          // transposed, flipped BF16-rounded weights for the data gradient
-    __nv_bfloat16* wtc = nullptr;  // BF16 weights of the two 64->64 layers as [co][k * 64 + ci] (tensor cores)
+    // BF16 weights in (k, ci) order for the tensor cores: layers 1, 2 as [64][9 * 64], layer 3 as
+    // [4][9 * 64], then layer 0 as [64][48] (9 * 4 entries, the rest zero)
+    __nv_bfloat16* wtc = nullptr;
     int* offs_dev = nullptr;        // off[] on the device (int)
     int* cin_dev = nullptr;
     int* cout_dev = nullptr;
@@ -25,6 +27,7 @@ struct CnnBufs {
     float* d[4] = {nullptr, nullptr, nullptr, nullptr};             // [C][Tp] x 3, [4][Tp]
     float2* out = nullptr;          // [2][Tmax] forward output used by training
     float* loss = nullptr;          // [1]
+    unsigned int* err = nullptr;    // [1] error word (RX_ERR_* bits) of the tensor-core kernels
 };
 
 cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s);
@@ -33,6 +36,14 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);
 cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s);
 cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s);
+// the inference forward on the tcgen05 tensor cores (k_cnn_tc.cu); act[1..3] hold planar activations
+cudaError_t cnn_infer_tc(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s);
+// element offsets in wtc
+__host__ __device__ inline int64_t wtc_offset(int C, int layer) {
+    const int64_t lw = (int64_t)C * C * 9;
+    return layer == 1 ? 0 : layer == 2 ? lw : layer == 3 ? 2 * lw : 2 * lw + 4 * (int64_t)C * 9;
+}
+__host__ __device__ inline int64_t wtc_elems(int C) { return wtc_offset(C, 0) + (int64_t)C * 48; }
 // one 64 -> 64 forward convolution (bias, ReLU, BF16 out) on the tensor cores (k_cnn_mma.cu);
 // Wm: the layer's BF16 weights as [co][k * 64 + ci]
 cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const __nv_bfloat16* Wm, const float* b,

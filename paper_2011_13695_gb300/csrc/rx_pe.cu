@@ -34,7 +34,7 @@ int64_t count_params(int C, int64_t* off) {
 void pe_free(rx_pe* p) {
     CnnBufs& B = p->B;
     void* ptrs[] = {B.master, B.m, B.v, B.grad, B.wfwd, B.wbwd, B.wtc, B.offs_dev, B.cin_dev, B.cout_dev, B.out, B.loss,
-                    B.act[0], B.act[1], B.act[2], B.act[3], B.d[0], B.d[1], B.d[2], B.d[3]};
+                    B.act[0], B.act[1], B.act[2], B.act[3], B.d[0], B.d[1], B.d[2], B.d[3], B.err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -66,7 +66,8 @@ rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const 
     A(cudaMalloc(&B.grad, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.wfwd, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.wbwd, sizeof(float) * B.nparam));
-    A(cudaMalloc(&B.wtc, sizeof(__nv_bfloat16) * 2 * (size_t)channels * channels * KW));
+    A(cudaMalloc(&B.wtc, sizeof(__nv_bfloat16) * (size_t)wtc_elems(channels)));
+    A(cudaMalloc(&B.err, sizeof(unsigned int)));
     A(cudaMalloc(&B.offs_dev, sizeof(int) * 8));
     A(cudaMalloc(&B.cin_dev, sizeof(int) * 4));
     A(cudaMalloc(&B.cout_dev, sizeof(int) * 4));
@@ -92,6 +93,8 @@ rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const 
     else A(cudaMemset(B.master, 0, sizeof(float) * B.nparam));
     A(cudaMemset(B.m, 0, sizeof(float) * B.nparam));
     A(cudaMemset(B.v, 0, sizeof(float) * B.nparam));
+    A(cudaMemset(B.wtc, 0, sizeof(__nv_bfloat16) * (size_t)wtc_elems(channels)));   // the input layer's K padding
+    A(cudaMemset(B.err, 0, sizeof(unsigned int)));
     A(cnn_prepare_weights(B, 0));
     A(cudaDeviceSynchronize());
     if (e != cudaSuccess) {
@@ -115,8 +118,16 @@ rx_status rx_pe_forward(rx_pe* p, const float* d_z, int64_t T, float* d_out, rx_
     if (!p || !d_z || !d_out || T < 1 || T > p->B.Tmax) return RX_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     p->last = s;
-    if (cnn_zero_pads(p->B, T, s) != cudaSuccess) return RX_ECUDA;
-    if (cnn_forward(p->B, (const float2*)d_z, T, (float2*)d_out, s) != cudaSuccess) return RX_ECUDA;
+    if (cnn_infer_tc(p->B, (const float2*)d_z, T, (float2*)d_out, s) != cudaSuccess) return RX_ECUDA;
+    return RX_OK;
+}
+
+rx_status rx_pe_error_word(rx_pe* p, uint32_t* out) {
+    if (!p || !out) return RX_EINVAL;
+    if (p->last && cudaStreamSynchronize(p->last) != cudaSuccess) return RX_ECUDA;
+    unsigned int w = 0;
+    if (cudaMemcpy(&w, p->B.err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return RX_ECUDA;
+    *out = w;
     return RX_OK;
 }
 

@@ -76,6 +76,10 @@ class PostEqualiser:
         rx.rx_pe_forward(self.h, pz, T, self._seq(out)[0], s.cuda_stream)
         return out
 
+    def error_word(self) -> int:
+        """RX_ERR_* bits raised by the post-equaliser's kernels (synchronises)."""
+        return rx.rx_pe_error_word(self.h)
+
     def gradients(self, z: torch.Tensor, target: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
         pz, T = self._seq(z)
         grads = torch.empty(self.n_params, dtype=torch.float32, device=z.device)

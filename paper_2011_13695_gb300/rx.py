@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "librx.so")
 
 RX_OK, RX_EINVAL, RX_ENOMEM, RX_ECUDA, RX_ETIMEOUT, RX_ESTATE = 0, -1, -2, -3, -4, -5
 RX_IN_C64, RX_IN_F16, RX_IN_I8 = 0, 1, 2
-RX_ERR_NONFINITE, RX_ERR_SYNC_LOST, RX_ERR_SINGULAR = 0x1, 0x2, 0x4
+RX_ERR_NONFINITE, RX_ERR_SYNC_LOST, RX_ERR_SINGULAR, RX_ERR_TIMEOUT = 0x1, 0x2, 0x4, 0x8
 (RX_BUF_CDC, RX_BUF_Y, RX_BUF_Z, RX_BUF_BSTAR, RX_BUF_M, RX_BUF_TAPS_CMA, RX_BUF_TAPS_INIT, RX_BUF_TAPS_LAST,
  RX_BUF_Y_ACQ, RX_BUF_Y_FOE, RX_BUF_SCALE) = range(11)
 
@@ -27,8 +27,8 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_stage_name", "rx_stage_times", "rx_launch_count", "rx_destroy", "rx_strerror",
            "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
            "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
-           "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward", "rx_pe_gradients",
-           "rx_pe_train_step", "rx_pe_destroy")
+           "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
+           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy")
 RX_STATIC_MAX_SYMBOLS = 262144
 
 
@@ -107,6 +107,7 @@ def lib() -> C.CDLL:
             "rx_pe_create": (i32, [i32, i32, i64, vp, C.POINTER(vp)]),
             "rx_pe_params": (i32, [vp, vp]),
             "rx_pe_forward": (i32, [vp, vp, i64, vp, vp]),
+            "rx_pe_error_word": (i32, [vp, vp]),
             "rx_pe_gradients": (i32, [vp, vp, vp, i64, vp, vp, vp]),
             "rx_pe_train_step": (i32, [vp, vp, vp, i64, C.c_float, vp, vp]),
             "rx_pe_destroy": (None, [vp]),
@@ -289,6 +290,12 @@ def rx_pe_params(p: int, out) -> None:
 
 def rx_pe_forward(p: int, d_z: int, T: int, d_out: int, stream: int | None) -> None:
     _check(lib().rx_pe_forward(p, d_z, T, d_out, stream or None), "rx_pe_forward")
+
+
+def rx_pe_error_word(p: int) -> int:
+    w = C.c_uint32(0)
+    _check(lib().rx_pe_error_word(p, C.byref(w)), "rx_pe_error_word")
+    return int(w.value)
 
 
 def rx_pe_gradients(p: int, d_z: int, d_target: int, T: int, d_grads: int | None, d_loss: int | None,

@@ -73,13 +73,14 @@ def pe_params():
     return vec, cnn.unflatten(bf16(vec), C, K)
 
 
-@pytest.mark.parametrize("T", [1, 7, 300, 3001])
+@pytest.mark.parametrize("T", [1, 7, 300, 3001, 4096])
 def test_forward_matches_oracle(pe_params, T):
     from paper_2011_13695_gb300.learned import PostEqualiser
     vec, pb = pe_params
     zc = qam_like(T, seed=T)
     pe = PostEqualiser(4096, vec)
     out = pe.forward(to_dev(zc)).cpu().numpy().astype(np.complex128)
+    assert pe.error_word() == 0
     pe.close()
     zf = zc.astype(np.complex64).astype(np.complex128)
     f_gpu = channels(out - zf)
@@ -97,6 +98,7 @@ def test_forward_full_length_sampled(pe_params):
     zc = qam_like(T, seed=5)
     pe = PostEqualiser(T, vec)
     out = pe.forward(to_dev(zc)).cpu().numpy().astype(np.complex128)
+    assert pe.error_word() == 0
     pe.close()
     zf = zc.astype(np.complex64).astype(np.complex128)
     R, w = 16, 512
