@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
-    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch", "learned"],
+    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch", "learned", "cnn"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser")
@@ -583,7 +583,7 @@ def learned_arm(args) -> None:
             torch.cuda.synchronize()
             step_ms.append(a.elapsed_time(d))
             cnn_ms.append(b.elapsed_time(c))
-    launches = rx.rx_launch_count(rcv.h) - launches0 + args.steps * 5
+    launches = rx.rx_launch_count(rcv.h) - launches0 + args.steps * 4
     t = sum(step_ms) / len(step_ms)
     tc = sum(cnn_ms) / len(cnn_ms)
     pk = peaks()
@@ -617,6 +617,59 @@ def learned_arm(args) -> None:
     rcv.close()
 
 
+def cnn_arm(args) -> None:
+    """The post-equaliser's inference forward alone (4 tcgen05 launches) on He-initialised weights and
+    16QAM-like symbols of 2^20 symbols/pol (or --n-sym): a kernel measurement, not a bench line of the
+    chain. HBM algorithmic bytes per DP symbol: 16 in + 128 out (layer 0), 2 x (128 + 128) (hidden
+    layers), 128 + 16 + 16 (output layer)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300.learned import PostEqualiser, he_init
+
+    N = args.n_sym or (1 << 20)
+    rng = np.random.default_rng(7)
+    lv = np.array([-3.0, -1.0, 1.0, 3.0]) / np.sqrt(10.0)
+    zc = lv[rng.integers(0, 4, (2, N))] + 1j * lv[rng.integers(0, 4, (2, N))]
+    zc = zc + 0.05 * (rng.standard_normal((2, N)) + 1j * rng.standard_normal((2, N)))
+    z = torch.from_numpy(zc.astype(np.complex64)).cuda()
+    out = torch.empty_like(z)
+    pe = PostEqualiser(N, he_init(seed=0))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pe.forward(z, out)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pe.forward(z, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    err = pe.error_word()
+    pe.close()
+    t = sum(ms) / len(ms)
+    pk = peaks()
+    bf16_peak = pk.get("bf16_tflops", 1900.0)
+    tflops = 2 * N * CNN_FWD_FLOP / (t * 1e-3) / 1e12
+    hbm_bytes = N * ((16 + 128) + 2 * (128 + 128) + (128 + 16 + 16))
+    print(json.dumps({
+        "metric": "post-equaliser forward", "value": 2 * N / (t * 1e-3) / 1e9, "unit": "GSym/s (DP symbols x 2)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+        "dtype": "bf16 x bf16 -> f32", "data": "synthetic",
+        "config": {"workload": f"cnn-forward-{N}", "symbols_per_pol": N, "l2": "flushed between timed steps"},
+        "roofline": {"kernel": "k_conv_tc x 4 (whole forward)", "bound": "tensor", "achieved": tflops,
+                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": tflops / bf16_peak, "traffic": None,
+                     "hbm_gbs": hbm_bytes / (t * 1e-3) / 1e9, "hbm_frac": hbm_bytes / (t * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0)},
+        "error_word": err, "gpu_launches": 4 * args.steps, "clocks": clk.summary()}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -627,6 +680,8 @@ def main():
         batch_arm(args)
     elif args.workload == "learned":
         learned_arm(args)
+    elif args.workload == "cnn":
+        cnn_arm(args)
     else:
         our_arm(args)
 

@@ -58,11 +58,14 @@ struct TcShape {
     static constexpr int NKC = MODE == IN ? 6 : 72;                   // K chunks of 8 (K = 48 or 576)
     static constexpr int NKS = NKC / 2;                               // MMAs of K = 16 per tile
     static constexpr int ROWS = MODE == IN ? TT : XR;                 // rows of a staged plane
-    static constexpr int PLANE = ROWS * 16;                           // bytes
+    // plane strides are 64 bytes past a multiple of 128, so that the two 16-byte K chunks of a row
+    // that one MMA reads fall in different shared-memory banks
+    static constexpr int PLANE = (ROWS + 4) * 16;                     // bytes
+    static constexpr int WPL = (NCO + 4) * 16;                        // weight plane stride (bytes)
     static constexpr int NPL = MODE == IN ? 6 : 8;                    // planes per stage
     static constexpr int STAGE = NPL * PLANE;
     static constexpr int S = MODE == IN ? 3 : 4;                      // pipeline stages
-    static constexpr int WB = NKC * NCO * 16;                         // weight bytes: planes [kc][co][8]
+    static constexpr int WB = NKC * WPL;                              // weight bytes: planes [kc][co][8]
     static constexpr int NPW = MODE == IN ? 4 : 1;                    // producer warps
     static constexpr int NWARP = 4 + NPW + 1;
     static constexpr int NTHR = 32 * NWARP;
@@ -82,7 +85,7 @@ struct TcShape {
     // instruction descriptor (kind::f16): F32 accumulator, BF16 A and B, both K-major, N >> 3, M >> 4
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCO >> 3) << 17) |
                                       ((uint32_t)(TT >> 4) << 24);
-    static_assert(STAGE % 16 == 0 && WB % 16 == 0 && PLANE % 16 == 0, "16-byte aligned operands");
+    static_assert(STAGE % 16 == 0 && WB % 16 == 0 && PLANE % 128 == 64 && WPL % 128 == 64, "operand strides");
     static_assert(NCO % 16 == 0 && NCO >= 16 && NCO <= 256, "M = 128 needs N a multiple of 16");
 };
 
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         const int co = i / S::NKC, kc = i - co * S::NKC;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (co < S::COUT) v = __ldg(reinterpret_cast<const uint4*>(a.Wm + ((int64_t)co * S::NKC + kc) * 8));
-        *reinterpret_cast<uint4*>(sm + kc * S::NCO * 16 + co * 16) = v;
+        *reinterpret_cast<uint4*>(sm + kc * S::WPL + co * 16) = v;
     }
     for (int i = tid; i < S::COUT; i += S::NTHR) bias_s[i] = a.bias[i];
     if (tid == 0) {
@@ -279,11 +282,16 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         int it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int ab = it & 1;
+            const int64_t t = tile * TT + 32 * warp + lane;   // this thread's output position
+            float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
+            if (MODE == OUT && t < T) {                       // the residual, requested before the wait
+                z0 = a.z[t];
+                z1 = a.z[T + t];
+            }
             const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
             if (!__all_sync(0xffffffffu, ok)) break;      // warp-uniform: the loads below are .sync.aligned
             tc_after();
             const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::NCO);
-            const int64_t t = tile * TT + 32 * warp + lane;   // this thread's output position
             if constexpr (MODE == OUT) {
                 float v[4];
                 tmem_ld4(tl, v);
@@ -291,7 +299,6 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty(ab));
                 if (t < T) {
-                    const float2 z0 = a.z[t], z1 = a.z[T + t];
                     a.sym[t] = make_float2(z0.x + v[0] + bias_s[0], z0.y + v[1] + bias_s[1]);
                     a.sym[T + t] = make_float2(z1.x + v[2] + bias_s[2], z1.y + v[3] + bias_s[3]);
                 }
@@ -325,22 +332,32 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         if constexpr (MODE == IN) {
             const int r = tid - 128;                          // 0 .. 127
             unsigned char* F = sm + S::OFF_F;                 // [FROWS][4] BF16: position t0 - 4 + u
+            // this thread's staged positions u = r, r + 128 of a tile, loaded one tile ahead
+            uint2 zp[2];
+            auto zload = [&](int64_t tile) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int u = r + 128 * h;
+                    const int64_t tt = tile * TT - PAD + u;
+                    float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
+                    if (u < S::FROWS && tile < ntiles && tt >= 0 && tt < T) {
+                        z0 = a.z[tt];
+                        z1 = a.z[T + tt];
+                    }
+                    zp[h] = make_uint2(pack_bf16(z0.x, z0.y), pack_bf16(z1.x, z1.y));
+                }
+            };
+            zload(blockIdx.x);
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
                 const int s = it % S::S;
                 bool ok = true;
                 if (r == 0) ok = mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort);
                 // one decision for the 128 producer threads; also orders the previous tile's reads of F
                 if (bar_or_128(!ok || *abort)) break;
-                const int64_t t0 = tile * TT;
-                for (int u = r; u < S::FROWS; u += 128) {
-                    const int64_t tt = t0 - PAD + u;
-                    float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
-                    if (tt >= 0 && tt < T) {
-                        z0 = a.z[tt];
-                        z1 = a.z[T + tt];
-                    }
-                    *reinterpret_cast<uint2*>(F + 8 * u) = make_uint2(pack_bf16(z0.x, z0.y), pack_bf16(z1.x, z1.y));
-                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (r + 128 * h < S::FROWS) *reinterpret_cast<uint2*>(F + 8 * (r + 128 * h)) = zp[h];
+                zload(tile + gridDim.x);
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 unsigned char* st = sm + S::OFF_ST + s * S::STAGE;
 #pragma unroll
@@ -386,13 +403,13 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 uint32_t aaddr, baddr;
                 if constexpr (MODE == IN) {
                     aaddr = st + 2 * ks * S::PLANE;
-                    baddr = sW + 2 * ks * S::NCO * 16;
+                    baddr = sW + 2 * ks * S::WPL;
                 } else {
                     const int k = ks >> 2, j = ks & 3;        // tap, 16-channel group
                     aaddr = st + 2 * j * S::PLANE + 16 * k;
-                    baddr = sW + (8 * k + 2 * j) * S::NCO * 16;
+                    baddr = sW + (8 * k + 2 * j) * S::WPL;
                 }
-                mma_ss(d, sdesc(aaddr, S::PLANE, 128), sdesc(baddr, S::NCO * 16, 128), S::IDESC, ks > 0 ? 1u : 0u);
+                mma_ss(d, sdesc(aaddr, S::PLANE, 128), sdesc(baddr, S::WPL, 128), S::IDESC, ks > 0 ? 1u : 0u);
             }
             mma_commit(in_empty(s));
             mma_commit(acc_full(ab));

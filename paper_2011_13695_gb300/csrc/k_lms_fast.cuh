@@ -355,11 +355,11 @@ cudaError_t launch_lms_fast_t(const LmsArgs& a, cudaStream_t s) {
     using S = LmsFastShape<NT, T, LB>;
     const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
     if (nseg <= 0) return cudaSuccess;
-    const size_t smem = sizeof(float2) * S::SMEM;
-    static bool attr = false;
-    if (smem > 48 * 1024 && !attr) {
+    const size_t smem = lms_launch_smem(sizeof(float2) * S::SMEM, a.exclusive);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
         cudaFuncSetAttribute(k_lms_fast<NT, T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        attr = smem;
     }
     k_lms_fast<NT, T, LB><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
     return cudaGetLastError();

@@ -531,11 +531,23 @@ int64_t lms_smem_bytes(int T, int Lb, int threads) {
     return (int64_t)sizeof(float2) * (2 * T + 4 * XS + 2 * Lb + G * 2 * T + 1 + (2 * Lb + T - 1));
 }
 
+size_t lms_launch_smem(size_t need, int exclusive) {
+    if (!exclusive) return need;
+    static size_t optin = 0;
+    if (!optin) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        optin = v > 0 ? (size_t)v : need;
+    }
+    return need > optin ? need : optin;
+}
+
 template <int NT>
 static cudaError_t launch_lms_t(const LmsArgs& a, cudaStream_t s) {
     const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
     if (nseg <= 0) return cudaSuccess;
-    const size_t smem = (size_t)lms_smem_bytes(a.T, a.Lb, NT);
+    const size_t smem = lms_launch_smem((size_t)lms_smem_bytes(a.T, a.Lb, NT), a.exclusive);
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
         cudaFuncSetAttribute(k_lms<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -403,8 +403,13 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
         RX_CK(launch_cdc(a, s));
         ++nl;
     }
-    if (split) {
-        RX_CK(cudaEventRecord(h->ev_fork, s));
+    // the rest of the compensation forks here but is enqueued after the acquisition's first launch,
+    // whose CTAs, each holding a whole SM, are then placed before the side stream fills the GPU
+    if (split) RX_CK(cudaEventRecord(h->ev_fork, s));
+    bool rest_done = !split;
+    auto enqueue_rest = [&]() -> rx_status {
+        if (rest_done) return RX_OK;
+        rest_done = true;
         RX_CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         {
             StageScope sc(h, ST_CDC_REST, h->side);
@@ -415,7 +420,8 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
             ++nl;
         }
         RX_CK(cudaEventRecord(h->ev_join, h->side));
-    }
+        return RX_OK;
+    };
     LmsArgs base{};
     base.x = h->cdc;
     base.xstride = h->cap;
@@ -450,7 +456,9 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 a.taps_out = st->taps_cma;
                 a.y = h->yacq;
                 a.ystride = h->nacq;
+                a.exclusive = 1;
                 RX_CK(launch_lms(a, kAcqThreads, s));
+                if (rx_status r = enqueue_rest(); r != RX_OK) return r;
                 RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 0, s));
                 RX_CK(launch_cma_rebuild(st, T, h->flag, s));
                 LmsArgs a2 = a;
@@ -480,6 +488,7 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 a.taps_in = st->taps_init;
                 a.taps_out = st->taps_init;
                 a.y = nullptr;
+                a.exclusive = 1;
                 RX_CK(launch_lms(a, kAcqThreads, s));
                 ++nl;
             }
@@ -490,6 +499,7 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
     } else {
         RX_CK(cudaMemcpyAsync(st->taps_init, st->taps_last, sizeof(float2) * 4 * T, cudaMemcpyDeviceToDevice, s));
     }
+    if (rx_status r = enqueue_rest(); r != RX_OK) return r;
     if (split) RX_CK(cudaStreamWaitEvent(s, h->ev_join, 0));   // the whole frame is compensated
     {
         StageScope sc(h, ST_LMS, s);

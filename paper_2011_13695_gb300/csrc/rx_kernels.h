@@ -41,7 +41,12 @@ struct LmsArgs {
     int64_t ystride;
     const int* run_if;     // nullable: the kernel does nothing unless *run_if != 0
     RxDevState* st;
+    int exclusive;         // 1: each CTA asks for a whole SM's shared memory, so that no other kernel's
+                           // CTA shares its SM (the serial acquisition is latency-bound)
 };
+
+// shared memory a launch asks for: the kernel's need, or with `exclusive` the most a CTA may have
+size_t lms_launch_smem(size_t need, int exclusive);
 
 cudaError_t launch_power(const void* in, int fmt, float in_scale, int64_t S, int64_t n_win, RxDevState* st,
                          cudaStream_t s);
