@@ -7,7 +7,10 @@
 // Layout: one thread per test phase and strip of LEN consecutive symbols
 // (32 or 64 threads per strip), strips of one polarisation side by side in a
 // CTA. The strip's symbols (with a W/2 halo on each side) are staged in
-// shared memory and read as broadcasts. Each thread keeps the last W
+// shared memory as (x, y, y, -x) and read as 16-byte broadcasts, so that the
+// rotation, rounding and error of both dimensions are packed FP32x2
+// instructions (each component the same FMA or add as the scalar form, so
+// the results are bit-identical to it). Each thread keeps the last W
 // distances of its phase in registers (a ring indexed at compile time), slides
 // the window sum by one add and one subtract per symbol and re-forms it as a
 // direct sum of the ring every W symbols, which bounds the rounding drift to
@@ -29,17 +32,17 @@ namespace {
 
 constexpr int BPS_THREADS = 128;
 
-// distance of one symbol to the nearest point after rotation, in level units
-__device__ __forceinline__ float bps_dist(float2 v, float c, float s, float hL, float invLm1, float Lm1) {
-    const float MAGIC = 12582912.0f;                  // 1.5 * 2^23: x + MAGIC - MAGIC = rint(x)
-    const float vI = fmaf(v.x, c, fmaf(v.y, s, hL));
-    const float vQ = fmaf(v.y, c, fmaf(-v.x, s, hL));
-    const float wI = __saturatef(vI * invLm1);
-    const float wQ = __saturatef(vQ * invLm1);
-    const float tI = fmaf(wI, Lm1, MAGIC) - MAGIC;
-    const float tQ = fmaf(wQ, Lm1, MAGIC) - MAGIC;
-    const float eI = vI - tI, eQ = vQ - tQ;
-    return fmaf(eI, eI, eQ * eQ);
+// distance of one symbol to the nearest point after rotation, in level units. The symbol is staged
+// as (x, y, y, -x), so that the rotation of both components is two packed FMAs (per component the
+// same fmaf as the scalar form: vI = fma(x, c, fma(y, s, hL)), vQ = fma(y, c, fma(-x, s, hL))),
+// and the rounding and the error of both dimensions take one packed instruction each.
+__device__ __forceinline__ float bps_dist(float4 v, float2 cc, float2 ss, float2 hh, float invLm1, float2 ll) {
+    const float2 MAGIC = make_float2(12582912.0f, 12582912.0f);   // 1.5 * 2^23: x + MAGIC - MAGIC = rint(x)
+    const float2 r = __ffma2_rn(make_float2(v.x, v.y), cc, __ffma2_rn(make_float2(v.z, v.w), ss, hh));
+    const float2 w = make_float2(__saturatef(r.x * invLm1), __saturatef(r.y * invLm1));
+    const float2 t = __fadd2_rn(__ffma2_rn(w, ll, MAGIC), make_float2(-MAGIC.x, -MAGIC.y));
+    const float2 e = __ffma2_rn(t, make_float2(-1.0f, -1.0f), r);   // r - t, exactly rounded once
+    return fmaf(e.x, e.x, e.y * e.y);
 }
 
 // publish one window's warp minimum and the lanes holding it
@@ -51,14 +54,13 @@ __device__ __forceinline__ void bps_publish(float D, uint2* slot, int lane) {
 }
 
 template <int W, int GS>
-__global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ y, int64_t ystride, int64_t N, int B,
-                                                   float cI0, float hL, float invLm1, float Lm1, int LEN,
-                                                   uint8_t* __restrict__ bstar, int64_t bstride) {
+__global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict__ y, int64_t ystride, int64_t N,
+                                                      int B, float cI0, float hL, float invLm1, float Lm1, int LEN,
+                                                      uint8_t* __restrict__ bstar, int64_t bstride) {
     constexpr int NSTRIP = BPS_THREADS / GS;
     constexpr int NW = GS / 32;
-    extern __shared__ float smem_f[];
-    float* ring = smem_f;                             // [W][BPS_THREADS]: each thread's last W distances
-    float2* ys = reinterpret_cast<float2*>(smem_f + W * BPS_THREADS);   // [NSTRIP][LEN + W]
+    extern __shared__ float4 smem_v[];
+    float4* ys = smem_v;                              // [NSTRIP][LEN + W]: (x, y, y, -x)
     __shared__ uint2 slots[NSTRIP][NW][W];            // per output slot: (warp minimum bits, ballot of its lanes)
     const int tid = threadIdx.x;
     const int sl = tid / GS;                          // strip within the CTA
@@ -68,8 +70,7 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     const int64_t s0 = ((int64_t)blockIdx.x * NSTRIP + sl) * LEN;
     const int span = LEN + W;
     const float2* yq = y + (int64_t)q * ystride;
-    const float2* yl = ys + sl * span;
-    float* myring = ring + tid;
+    const float4* yl = ys + sl * span;
 
     // stage y[s0 - W/2, s0 + LEN + W/2); symbols outside [0, N) are NaN, whose
     // distance fmaxf(NaN, 0) turns into 0: they contribute nothing to any window
@@ -77,41 +78,45 @@ __global__ void __launch_bounds__(BPS_THREADS) k_bps(const float2* __restrict__ 
     for (int t = tid; t < NSTRIP * span; t += BPS_THREADS) {
         const int st = t / span, u = t - st * span;
         const int64_t i = ((int64_t)blockIdx.x * NSTRIP + st) * LEN - W / 2 + u;
-        ys[st * span + u] = (i >= 0 && i < N) ? yq[i] : make_float2(qnan, qnan);
+        const float2 v = (i >= 0 && i < N) ? yq[i] : make_float2(qnan, qnan);
+        ys[st * span + u] = make_float4(v.x, v.y, v.y, -v.x);
     }
     __syncthreads();
 
     // rotation by e^{-j theta_b} folded with 1/(2a); phases b >= B never win (penalty)
     float sn, cs;
     sincospif((float)(2 * b - B) / (float)(4 * B), &sn, &cs);   // theta_b / pi = (b/B - 1/2) / 2
-    const float c = cs * cI0, s = sn * cI0;
+    const float2 cc = make_float2(cs * cI0, cs * cI0), ss = make_float2(sn * cI0, sn * cI0);
+    const float2 hh = make_float2(hL, hL), ll = make_float2(Lm1, Lm1);
     const float pen = b < B ? 0.0f : 3.0e38f;
     const int nc = LEN / W;
     uint2* myslots = &slots[sl][wip][0];
 
+    // the last W distances of this thread's phase, in registers (indices fixed at compile time)
+    float ring[W];
     float D = pen;
-#pragma unroll 8
+#pragma unroll
     for (int u = 0; u < W; ++u) {
-        const float d = fmaxf(bps_dist(yl[u], c, s, hL, invLm1, Lm1), 0.0f);
-        myring[u * BPS_THREADS] = d;
+        const float d = fmaxf(bps_dist(yl[u], cc, ss, hh, invLm1, ll), 0.0f);
+        ring[u] = d;
         D += d;
     }
     bps_publish(D, &myslots[0], lane);                // window of local output 0
     for (int ch = 0; ch <= nc; ++ch) {
         if (ch > 0) {
-            const float2* yc = yl + ch * W;
-#pragma unroll 8
+            const float4* yc = yl + ch * W;
+#pragma unroll
             for (int u = 0; u < W; ++u) {
-                const float d = fmaxf(bps_dist(yc[u], c, s, hL, invLm1, Lm1), 0.0f);
-                const float old = myring[u * BPS_THREADS];
-                myring[u * BPS_THREADS] = d;
+                const float d = fmaxf(bps_dist(yc[u], cc, ss, hh, invLm1, ll), 0.0f);
+                const float old = ring[u];
+                ring[u] = d;
                 D = (D + d) - old;
                 // window of local output (ch - 1) W + u + 1 is complete; its slot is (u + 1) % W
                 bps_publish(fmaxf(D, 0.0f), &myslots[(u + 1) & (W - 1)], lane);
             }
             float t = pen;                            // re-form the sum directly from the ring
-#pragma unroll 8
-            for (int r = 0; r < W; ++r) t += myring[r * BPS_THREADS];
+#pragma unroll
+            for (int r = 0; r < W; ++r) t += ring[r];
             D = t;
         }
         __syncthreads();
@@ -139,7 +144,7 @@ cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uin
     constexpr int NSTRIP = BPS_THREADS / GS;
     const int64_t nstrip = (N + LEN - 1) / LEN;
     dim3 grid((unsigned)((nstrip + NSTRIP - 1) / NSTRIP), 2);
-    const size_t smem = sizeof(float) * W * BPS_THREADS + sizeof(float2) * NSTRIP * (LEN + W);
+    const size_t smem = sizeof(float4) * NSTRIP * (LEN + W);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_bps<W, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
