@@ -4,9 +4,11 @@
 // Each layer is a matrix product per tile of 128 output positions:
 //   D[t][co] = sum_K A[t][K] B[K][co],  K = (k, ci),
 //   A[t][(k, ci)] = x[ci][t + k - 4],   B[(k, ci)][co] = W[co][ci][k],
-// M = 128 positions (one TMEM lane each), N = the output channels (64, or 16
-// with 12 zero rows for the 4-channel output layer), K = 9 taps x the input
-// channels in steps of 16.
+// M = 128 positions (one TMEM lane each), N = the 64 output channels, K = 9
+// taps x the input channels in steps of 16 (input and hidden layers). The
+// 4-channel output layer swaps the roles: M = (tap, output channel) rows of
+// the weights, N = 256 positions, K = the 64 input channels, and the epilogue
+// adds each tap's row at its shift.
 //
 // Activation layout (HBM): the hidden layers' BF16 activations are stored in
 // eight channel-chunk planes [C/8][T + 8][8], padded position-major, so that
@@ -22,8 +24,9 @@
 //
 // Roles (warp-specialised, one CTA per SM slot, tiles strided over the grid):
 //   warps 0-3  epilogue: TMEM lane quarter w holds positions 32 w .. 32 w + 31;
-//              bias, ReLU, BF16 and a 16-byte store per plane (coalesced), or
-//              for the output layer bias + residual into the symbols;
+//              bias, ReLU, BF16 and a 16-byte store per plane (coalesced); the
+//              output layer's warps 0-1 copy the 36 used rows to shared memory
+//              and all four add the taps, the bias and the residual;
 //   producer   one thread issuing the bulk copies of a stage (hidden, output
 //              layers), or four warps building the input layer's planes;
 //   last warp  TMEM allocation, and one thread issuing the MMAs of a tile
@@ -45,48 +48,57 @@ namespace {
 
 constexpr int KW = 9;
 constexpr int PAD = KW / 2;
-constexpr int TT = 128;                        // positions per tile (MMA M)
-constexpr int XR = TT + 2 * PAD;               // staged rows per tile (hidden/output layers)
 constexpr uint64_t kTimeoutNs = 500000000ull;  // 0.5 s per wait
 
 enum Mode { IN = 0, HID = 1, OUT = 2 };
 
+// Input and hidden layers: A = activations (M = 128 positions), B = weights (N = 64 channels), one
+// MMA per (tap, 16 input channels), the tap as a row shift of A.
+// Output layer: A = weights with one row per (tap k, output channel co), row 4 k + co (36 of 128
+// rows used), B = activations (N = 256 staged positions, unshifted), one MMA per 16 input channels;
+// D[4 k + co][j] is tap k's term for the output at staged position j - k + 4, and the epilogue adds
+// the nine taps' rows at their shifts, so a tile of 256 staged positions yields 248 outputs.
 template <int MODE>
 struct TcShape {
-    static constexpr int NCO = MODE == OUT ? 16 : 64;                 // MMA N
+    static constexpr int TO = MODE == OUT ? 248 : 128;                // output positions per tile
+    static constexpr int MMA_N = MODE == OUT ? 256 : 64;
     static constexpr int COUT = MODE == OUT ? 4 : 64;
-    static constexpr int NKC = MODE == IN ? 6 : 72;                   // K chunks of 8 (K = 48 or 576)
+    static constexpr int NKC = MODE == IN ? 6 : MODE == HID ? 72 : 8;   // K chunks of 8 over all MMAs
     static constexpr int NKS = NKC / 2;                               // MMAs of K = 16 per tile
-    static constexpr int ROWS = MODE == IN ? TT : XR;                 // rows of a staged plane
-    // plane strides are 64 bytes past a multiple of 128, so that the two 16-byte K chunks of a row
-    // that one MMA reads fall in different shared-memory banks
-    static constexpr int PLANE = (ROWS + 4) * 16;                     // bytes
-    static constexpr int WPL = (NCO + 4) * 16;                        // weight plane stride (bytes)
-    static constexpr int NPL = MODE == IN ? 6 : 8;                    // planes per stage
-    static constexpr int STAGE = NPL * PLANE;
-    static constexpr int S = MODE == IN ? 3 : 4;                      // pipeline stages
-    static constexpr int WB = NKC * WPL;                              // weight bytes: planes [kc][co][8]
+    static constexpr int XROWS = MODE == IN ? 128 : MODE == HID ? 136 : 256;   // staged rows per plane
+    static constexpr int WROWS = MODE == OUT ? 128 : 64;              // weight rows per plane
+    // plane strides are 64 bytes past a multiple of 128 (the two 16-byte K chunks of a row that one
+    // MMA reads then fall in different shared-memory banks)
+    static constexpr int XPL = (XROWS + 4) * 16;                      // activation plane stride (bytes)
+    static constexpr int WPL = (WROWS + 4) * 16;                      // weight plane stride (bytes)
+    static constexpr int NPL = MODE == IN ? 6 : 8;                    // activation planes per stage
+    static constexpr int STAGE = NPL * XPL;
+    static constexpr int S = MODE == HID ? 4 : 3;                     // pipeline stages
+    static constexpr int WB = NKC * WPL;                              // weight bytes: planes [kc][row][8]
     static constexpr int NPW = MODE == IN ? 4 : 1;                    // producer warps
     static constexpr int NWARP = 4 + NPW + 1;
     static constexpr int NTHR = 32 * NWARP;
-    static constexpr int TCOLS = MODE == OUT ? 32 : 128;              // TMEM columns (2 accumulators)
-    static constexpr int FROWS = TT + 12;                             // input layer: staged positions
-    // shared memory: weights, stages, (input layer) staged positions, then a slack region so that
-    // no operand read can leave the allocation, then barriers and small state
+    static constexpr int TCOLS = MODE == OUT ? 512 : 128;             // TMEM columns (2 accumulators)
+    static constexpr int FROWS = 128 + 12;                            // input layer: staged positions
+    static constexpr int DROWS = 36, DSTR = 260;                      // output layer: D rows in smem (floats)
+    // shared memory: weights, stages, the input layer's staged positions or the output layer's D
+    // rows, a slack region (input and hidden layers) so that no operand read can leave the
+    // allocation, then barriers and small state
     static constexpr int OFF_ST = WB;
     static constexpr int OFF_F = OFF_ST + S * STAGE;
-    static constexpr int OFF_SLACK = OFF_F + (MODE == IN ? FROWS * 8 : 0);
-    static constexpr int SLACK = 40960;
+    static constexpr int OFF_SLACK = OFF_F + (MODE == IN ? FROWS * 8 : MODE == OUT ? DROWS * DSTR * 4 : 0);
+    static constexpr int SLACK = MODE == OUT ? 0 : 40960;
     static constexpr int OFF_BAR = (OFF_SLACK + SLACK + 15) & ~15;
     static constexpr int NBAR = 2 * S + 4;
     static constexpr int OFF_MISC = OFF_BAR + 8 * NBAR;               // tmem address, abort flag
     static constexpr int OFF_BIAS = OFF_MISC + 16;
     static constexpr int SMEM = OFF_BIAS + 4 * 64;
     // instruction descriptor (kind::f16): F32 accumulator, BF16 A and B, both K-major, N >> 3, M >> 4
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCO >> 3) << 17) |
-                                      ((uint32_t)(TT >> 4) << 24);
-    static_assert(STAGE % 16 == 0 && WB % 16 == 0 && PLANE % 128 == 64 && WPL % 128 == 64, "operand strides");
-    static_assert(NCO % 16 == 0 && NCO >= 16 && NCO <= 256, "M = 128 needs N a multiple of 16");
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
+                                      ((uint32_t)(128 >> 4) << 24);
+    static_assert(STAGE % 16 == 0 && WB % 16 == 0 && XPL % 128 == 64 && WPL % 128 == 64, "operand strides");
+    static_assert(MMA_N % 16 == 0 && MMA_N >= 16 && MMA_N <= 256, "M = 128 needs N a multiple of 16");
+    static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -138,13 +150,14 @@ __device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
         if (gtimer() - t0 > kTimeoutNs) return;
 }
 
-// named barrier 1 over the 128 threads of the input layer's producer warps, OR of a predicate
+// named barrier ID over 128 threads (four warps of one role), returning the OR of a predicate
+template <int ID>
 __device__ __forceinline__ bool bar_or_128(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(ID)
         : "memory");
     return r != 0;
 }
@@ -234,14 +247,21 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
     float* bias_s = reinterpret_cast<float*>(sm + S::OFF_BIAS);
     const int mma_warp = S::NWARP - 1;
     const int64_t T = a.T, Tp = a.Tp;
-    const int64_t ntiles = (T + TT - 1) / TT;
+    const int64_t ntiles = (T + S::TO - 1) / S::TO;
 
-    // weights: 16-byte chunk (co, kc) of the row-major copy into plane kc, row co; rows COUT..NCO zero
-    for (int i = tid; i < S::NKC * S::NCO; i += S::NTHR) {
-        const int co = i / S::NKC, kc = i - co * S::NKC;
+    // weights, as 16-byte chunks (row, kc) into plane kc. Input and hidden layers: row = output
+    // channel, chunk kc of its (k, ci) row. Output layer: row 4 k + co holds W[co][8 kc .. 8 kc + 8][k]
+    // (rows 36..127 zero).
+    for (int i = tid; i < S::NKC * S::WROWS; i += S::NTHR) {
+        const int r = i / S::NKC, kc = i - r * S::NKC;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (co < S::COUT) v = __ldg(reinterpret_cast<const uint4*>(a.Wm + ((int64_t)co * S::NKC + kc) * 8));
-        *reinterpret_cast<uint4*>(sm + kc * S::WPL + co * 16) = v;
+        if constexpr (MODE == OUT) {
+            if (r < S::DROWS)
+                v = __ldg(reinterpret_cast<const uint4*>(a.Wm + (int64_t)(r & 3) * 576 + (r >> 2) * 64 + kc * 8));
+        } else {
+            v = __ldg(reinterpret_cast<const uint4*>(a.Wm + ((int64_t)r * S::NKC + kc) * 8));
+        }
+        *reinterpret_cast<uint4*>(sm + kc * S::WPL + r * 16) = v;
     }
     for (int i = tid; i < S::COUT; i += S::NTHR) bias_s[i] = a.bias[i];
     if (tid == 0) {
@@ -282,27 +302,66 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         int it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int ab = it & 1;
-            const int64_t t = tile * TT + 32 * warp + lane;   // this thread's output position
-            float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
-            if (MODE == OUT && t < T) {                       // the residual, requested before the wait
-                z0 = a.z[t];
-                z1 = a.z[T + t];
-            }
-            const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
-            if (!__all_sync(0xffffffffu, ok)) break;      // warp-uniform: the loads below are .sync.aligned
-            tc_after();
-            const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::NCO);
+            const int64_t t0 = tile * S::TO;
             if constexpr (MODE == OUT) {
-                float v[4];
-                tmem_ld4(tl, v);
+                // this thread's outputs: tile positions p = tid and tid + 128 (p < 248); residual first
+                float2 zr[2][2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t t = t0 + tid + 128 * h;
+                    zr[h][0] = zr[h][1] = make_float2(0.0f, 0.0f);
+                    if (tid + 128 * h < S::TO && t < T) {
+                        zr[h][0] = a.z[t];
+                        zr[h][1] = a.z[T + t];
+                    }
+                }
+                const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
+                // one decision for the four epilogue warps (named barrier 2), which also orders the
+                // previous tile's reads of the D rows before this tile's writes
+                if (bar_or_128<2>(!ok || *abort)) break;
+                tc_after();
+                float* Ds = reinterpret_cast<float*>(sm + S::OFF_F);     // [36][DSTR]
+                if (warp < 2) {
+                    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::MMA_N);
+                    const int row = 32 * warp + lane;
+#pragma unroll 4
+                    for (int q = 0; q < S::MMA_N / 16; ++q) {
+                        float v[16];
+                        tmem_ld16(tl + 16 * q, v);
+                        if (row < S::DROWS) {
+                            float4* dst = reinterpret_cast<float4*>(Ds + row * S::DSTR + 16 * q);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                        }
+                    }
+                }
                 tc_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty(ab));
-                if (t < T) {
-                    a.sym[t] = make_float2(z0.x + v[0] + bias_s[0], z0.y + v[1] + bias_s[1]);
-                    a.sym[T + t] = make_float2(z1.x + v[2] + bias_s[2], z1.y + v[3] + bias_s[3]);
+                asm volatile("bar.sync 2, 128;" ::: "memory");     // D rows complete
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int p = tid + 128 * h;
+                    const int64_t t = t0 + p;
+                    if (p < S::TO && t < T) {
+                        float f[4];
+#pragma unroll
+                        for (int co = 0; co < 4; ++co) {
+                            float acc = 0.0f;
+#pragma unroll
+                            for (int k = 0; k < 9; ++k) acc += Ds[(4 * k + co) * S::DSTR + p + k];
+                            f[co] = acc;
+                        }
+                        a.sym[t] = make_float2(zr[h][0].x + f[0] + bias_s[0], zr[h][0].y + f[1] + bias_s[1]);
+                        a.sym[T + t] = make_float2(zr[h][1].x + f[2] + bias_s[2], zr[h][1].y + f[3] + bias_s[3]);
+                    }
                 }
             } else {
+                const int64_t t = t0 + 32 * warp + lane;      // this thread's output position
+                const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
+                if (!__all_sync(0xffffffffu, ok)) break;  // warp-uniform: the loads below are .sync.aligned
+                tc_after();
+                const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::MMA_N);
                 float v[64];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tmem_ld16(tl + 16 * q, v + 16 * q);
@@ -338,7 +397,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int u = r + 128 * h;
-                    const int64_t tt = tile * TT - PAD + u;
+                    const int64_t tt = tile * S::TO - PAD + u;
                     float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
                     if (u < S::FROWS && tile < ntiles && tt >= 0 && tt < T) {
                         z0 = a.z[tt];
@@ -353,7 +412,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 bool ok = true;
                 if (r == 0) ok = mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort);
                 // one decision for the 128 producer threads; also orders the previous tile's reads of F
-                if (bar_or_128(!ok || *abort)) break;
+                if (bar_or_128<1>(!ok || *abort)) break;
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     if (r + 128 * h < S::FROWS) *reinterpret_cast<uint2*>(F + 8 * (r + 128 * h)) = zp[h];
@@ -364,7 +423,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 for (int j = 0; j < 6; ++j) {
                     const uint2 lo = *reinterpret_cast<const uint2*>(F + 8 * (r + 2 * j));
                     const uint2 hi = *reinterpret_cast<const uint2*>(F + 8 * (r + 2 * j + 1));
-                    *reinterpret_cast<uint4*>(st + j * S::PLANE + 16 * r) = make_uint4(lo.x, lo.y, hi.x, hi.y);
+                    *reinterpret_cast<uint4*>(st + j * S::XPL + 16 * r) = make_uint4(lo.x, lo.y, hi.x, hi.y);
                 }
                 fence_async_smem();
                 mbar_arrive(in_full(s));
@@ -374,11 +433,11 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
                     const int s = it % S::S;
                     if (!mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort)) break;
-                    const int64_t t0 = tile * TT;             // staged row u = padded position t0 + u
-                    const int rows = (int)min((int64_t)XR, Tp - t0);
+                    const int64_t t0 = tile * S::TO;          // staged row u = padded position t0 + u
+                    const int rows = (int)min((int64_t)S::XROWS, Tp - t0);
                     mbar_arrive_tx(in_full(s), (uint32_t)(8 * rows * 16));
                     for (int cc = 0; cc < 8; ++cc)
-                        bulk_g2s(sSt + s * S::STAGE + cc * S::PLANE, a.x + ((int64_t)cc * Tp + t0) * 8,
+                        bulk_g2s(sSt + s * S::STAGE + cc * S::XPL, a.x + ((int64_t)cc * Tp + t0) * 8,
                                  (uint32_t)(rows * 16), in_full(s));
                     issued = it + 1;
                 }
@@ -396,20 +455,23 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
             if (!mbar_wait(in_full(s), (uint32_t)((it / S::S) & 1), abort)) break;
             if (!mbar_wait(acc_empty(ab), (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
             tc_after();
-            const uint32_t d = tmem + (uint32_t)(ab * S::NCO);
+            const uint32_t d = tmem + (uint32_t)(ab * S::MMA_N);
             const uint32_t st = sSt + s * S::STAGE;
 #pragma unroll 4
             for (int ks = 0; ks < S::NKS; ++ks) {
-                uint32_t aaddr, baddr;
+                uint64_t ad, bd;
                 if constexpr (MODE == IN) {
-                    aaddr = st + 2 * ks * S::PLANE;
-                    baddr = sW + 2 * ks * S::WPL;
-                } else {
+                    ad = sdesc(st + 2 * ks * S::XPL, S::XPL, 128);
+                    bd = sdesc(sW + 2 * ks * S::WPL, S::WPL, 128);
+                } else if constexpr (MODE == HID) {
                     const int k = ks >> 2, j = ks & 3;        // tap, 16-channel group
-                    aaddr = st + 2 * j * S::PLANE + 16 * k;
-                    baddr = sW + (8 * k + 2 * j) * S::WPL;
+                    ad = sdesc(st + 2 * j * S::XPL + 16 * k, S::XPL, 128);
+                    bd = sdesc(sW + (8 * k + 2 * j) * S::WPL, S::WPL, 128);
+                } else {                                      // weights as A, positions as B
+                    ad = sdesc(sW + 2 * ks * S::WPL, S::WPL, 128);
+                    bd = sdesc(st + 2 * ks * S::XPL, S::XPL, 128);
                 }
-                mma_ss(d, sdesc(aaddr, S::PLANE, 128), sdesc(baddr, S::WPL, 128), S::IDESC, ks > 0 ? 1u : 0u);
+                mma_ss(d, ad, bd, S::IDESC, ks > 0 ? 1u : 0u);
             }
             mma_commit(in_empty(s));
             mma_commit(acc_full(ab));
@@ -442,7 +504,7 @@ cudaError_t launch_tc(const TcArgs& a, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<MODE>, S::NTHR, S::SMEM);
         resident = std::max(1, nsm * std::max(1, per));
     }
-    const int64_t ntiles = (a.T + TT - 1) / TT;
+    const int64_t ntiles = (a.T + S::TO - 1) / S::TO;
     if (ntiles <= 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(ntiles, resident);
     k_conv_tc<MODE><<<grid, S::NTHR, S::SMEM, s>>>(a);
