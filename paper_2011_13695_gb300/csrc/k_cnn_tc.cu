@@ -52,42 +52,54 @@ constexpr uint64_t kTimeoutNs = 500000000ull;  // 0.5 s per wait
 
 enum Mode { IN = 0, HID = 1, OUT = 2 };
 
-// Input and hidden layers: A = activations (M = 128 positions), B = weights (N = 64 channels), one
-// MMA per (tap, 16 input channels), the tap as a row shift of A.
+// Input layer: A = operand planes built from the symbols (M = 128 positions), B = weights (N = 64
+// channels), K = (tap, channel) padded to 48.
+// Hidden layers: A = weights of a pair of taps (2m, 2m + 1) stacked as rows, B = activations
+// (N = 256 staged positions) shifted by 2m rows, one MMA per (pair, 16 input channels). Row r of A
+// sits in TMEM lane r: quarter w = r / 32 holds output channels 16 w .. 16 w + 15, lanes 0-15 of it
+// the even tap and lanes 16-31 the odd tap, so one warp holds both halves of its 16 channels.
+// D_even[co][j] is the even taps' sum for the output at tile position j, D_odd[co][j] the odd taps'
+// sum for position j - 1; the epilogue adds D_even[co][p] + D_odd[co][p + 1] (one shuffle), so a
+// tile of 256 columns yields 248 outputs. Tap 9 (the odd half of pair 4) has zero weights.
 // Output layer: A = weights with one row per (tap k, output channel co), row 4 k + co (36 of 128
 // rows used), B = activations (N = 256 staged positions, unshifted), one MMA per 16 input channels;
 // D[4 k + co][j] is tap k's term for the output at staged position j - k + 4, and the epilogue adds
 // the nine taps' rows at their shifts, so a tile of 256 staged positions yields 248 outputs.
 template <int MODE>
 struct TcShape {
-    static constexpr int TO = MODE == OUT ? 248 : 128;                // output positions per tile
-    static constexpr int MMA_N = MODE == OUT ? 256 : 64;
+    static constexpr int TO = MODE == IN ? 128 : 248;                 // output positions per tile
+    static constexpr int MMA_N = MODE == IN ? 64 : 256;
     static constexpr int COUT = MODE == OUT ? 4 : 64;
-    static constexpr int NKC = MODE == IN ? 6 : MODE == HID ? 72 : 8;   // K chunks of 8 over all MMAs
+    // weight planes of 8 K values: input layer 6 (K = 48); hidden layers 5 tap pairs x 8 channel
+    // chunks; output layer 8 channel chunks
+    static constexpr int NKC = MODE == IN ? 6 : MODE == HID ? 40 : 8;
     static constexpr int NKS = NKC / 2;                               // MMAs of K = 16 per tile
-    static constexpr int XROWS = MODE == IN ? 128 : MODE == HID ? 136 : 256;   // staged rows per plane
-    static constexpr int WROWS = MODE == OUT ? 128 : 64;              // weight rows per plane
+    static constexpr int XROWS = MODE == IN ? 128 : MODE == HID ? 264 : 256;   // staged rows per plane
+    static constexpr int WROWS = MODE == IN ? 64 : 128;               // weight rows per plane
     // plane strides are 64 bytes past a multiple of 128 (the two 16-byte K chunks of a row that one
     // MMA reads then fall in different shared-memory banks)
     static constexpr int XPL = (XROWS + 4) * 16;                      // activation plane stride (bytes)
     static constexpr int WPL = (WROWS + 4) * 16;                      // weight plane stride (bytes)
     static constexpr int NPL = MODE == IN ? 6 : 8;                    // activation planes per stage
     static constexpr int STAGE = NPL * XPL;
-    static constexpr int S = MODE == HID ? 4 : 3;                     // pipeline stages
+    static constexpr int S = 3;                                       // pipeline stages
     static constexpr int WB = NKC * WPL;                              // weight bytes: planes [kc][row][8]
     static constexpr int NPW = MODE == IN ? 4 : 1;                    // producer warps
-    static constexpr int NWARP = 4 + NPW + 1;
+    static constexpr int NEPI = MODE == HID ? 8 : 4;                  // epilogue warps
+    static constexpr int NWARP = NEPI + NPW + 1;
     static constexpr int NTHR = 32 * NWARP;
-    static constexpr int TCOLS = MODE == OUT ? 512 : 128;             // TMEM columns (2 accumulators)
+    static constexpr int TCOLS = MODE == IN ? 128 : 512;              // TMEM columns (2 accumulators)
     static constexpr int FROWS = 128 + 12;                            // input layer: staged positions
     static constexpr int DROWS = 36, DSTR = 260;                      // output layer: D rows in smem (floats)
-    // shared memory: weights, stages, the input layer's staged positions or the output layer's D
-    // rows, a slack region (input and hidden layers) so that no operand read can leave the
-    // allocation, then barriers and small state
+    static constexpr int OSTR = 72;                                   // hidden layers: output tile row (bf16)
+    // shared memory: weights, stages, then the input layer's staged positions, the hidden layers'
+    // BF16 output tile or the output layer's D rows, a slack region (input layer) so that no operand
+    // read can leave the allocation, then barriers and small state
     static constexpr int OFF_ST = WB;
     static constexpr int OFF_F = OFF_ST + S * STAGE;
-    static constexpr int OFF_SLACK = OFF_F + (MODE == IN ? FROWS * 8 : MODE == OUT ? DROWS * DSTR * 4 : 0);
-    static constexpr int SLACK = MODE == OUT ? 0 : 40960;
+    static constexpr int AUX = MODE == IN ? FROWS * 8 : MODE == HID ? TO * OSTR * 2 : DROWS * DSTR * 4;
+    static constexpr int OFF_SLACK = OFF_F + AUX;
+    static constexpr int SLACK = MODE == IN ? 40960 : 0;
     static constexpr int OFF_BAR = (OFF_SLACK + SLACK + 15) & ~15;
     static constexpr int NBAR = 2 * S + 4;
     static constexpr int OFF_MISC = OFF_BAR + 8 * NBAR;               // tmem address, abort flag
@@ -150,16 +162,20 @@ __device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
         if (gtimer() - t0 > kTimeoutNs) return;
 }
 
-// named barrier ID over 128 threads (four warps of one role), returning the OR of a predicate
-template <int ID>
-__device__ __forceinline__ bool bar_or_128(bool v) {
+// named barrier ID over the N threads of one role, returning the OR of a predicate
+template <int ID, int N>
+__device__ __forceinline__ bool bar_or(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(ID)
+        : "r"((uint32_t)v), "n"(ID), "n"(N)
         : "memory");
     return r != 0;
+}
+template <int ID, int N>
+__device__ __forceinline__ void bar_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -202,6 +218,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r)
+                 : "r"(taddr)
+                 : "memory");
+    return __uint_as_float(r);
 }
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
     uint32_t r[4];
@@ -249,20 +273,31 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
     const int64_t T = a.T, Tp = a.Tp;
     const int64_t ntiles = (T + S::TO - 1) / S::TO;
 
-    // weights, as 16-byte chunks (row, kc) into plane kc. Input and hidden layers: row = output
-    // channel, chunk kc of its (k, ci) row. Output layer: row 4 k + co holds W[co][8 kc .. 8 kc + 8][k]
-    // (rows 36..127 zero).
+    // weights, as 16-byte chunks (row, kc) into plane kc. Input layer: row = output channel, chunk kc
+    // of its (k, ci) row. Output layer: row 4 k + co holds W[co][8 kc .. 8 kc + 8][k] (rows 36..127
+    // zero). Hidden layers: below.
     for (int i = tid; i < S::NKC * S::WROWS; i += S::NTHR) {
         const int r = i / S::NKC, kc = i - r * S::NKC;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if constexpr (MODE == OUT) {
             if (r < S::DROWS)
                 v = __ldg(reinterpret_cast<const uint4*>(a.Wm + (int64_t)(r & 3) * 576 + (r >> 2) * 64 + kc * 8));
+        } else if constexpr (MODE == HID) {
+            // plane kc = 8 m + c: tap pair m, input channels 8 c .. 8 c + 7; row r: channel
+            // 16 (r / 32) + r % 16 of tap 2 m + (r / 16) % 2
+            const int m = kc >> 3, c = kc & 7;
+            const int co = 16 * (r >> 5) + (r & 15), tap = 2 * m + ((r >> 4) & 1);
+            if (tap < 9) v = __ldg(reinterpret_cast<const uint4*>(a.Wm + (int64_t)co * 576 + tap * 64 + c * 8));
         } else {
             v = __ldg(reinterpret_cast<const uint4*>(a.Wm + ((int64_t)r * S::NKC + kc) * 8));
         }
         *reinterpret_cast<uint4*>(sm + kc * S::WPL + r * 16) = v;
     }
+    // staged rows past a frame's end are read (by outputs past the end, and by the zero weights of
+    // tap 9): start every stage from finite values
+    if constexpr (MODE != IN)
+        for (int i = tid; i < S::S * S::STAGE / 16; i += S::NTHR)
+            *reinterpret_cast<uint4*>(sm + S::OFF_ST + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
     for (int i = tid; i < S::COUT; i += S::NTHR) bias_s[i] = a.bias[i];
     if (tid == 0) {
         *abort = 0;
@@ -272,7 +307,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
-            mbar_init(acc_empty(b), 4);
+            mbar_init(acc_empty(b), S::NEPI);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -297,7 +332,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
     tc_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 4) {
+    if (warp < S::NEPI) {
         // ---- epilogue ----
         int it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -318,7 +353,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
                 // one decision for the four epilogue warps (named barrier 2), which also orders the
                 // previous tile's reads of the D rows before this tile's writes
-                if (bar_or_128<2>(!ok || *abort)) break;
+                if (bar_or<2, 128>(!ok || *abort)) break;
                 tc_after();
                 float* Ds = reinterpret_cast<float*>(sm + S::OFF_F);     // [36][DSTR]
                 if (warp < 2) {
@@ -338,7 +373,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 tc_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty(ab));
-                asm volatile("bar.sync 2, 128;" ::: "memory");     // D rows complete
+                bar_sync<2, 128>();                           // D rows complete
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int p = tid + 128 * h;
@@ -355,6 +390,57 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                         a.sym[t] = make_float2(zr[h][0].x + f[0] + bias_s[0], zr[h][0].y + f[1] + bias_s[1]);
                         a.sym[T + t] = make_float2(zr[h][1].x + f[2] + bias_s[2], zr[h][1].y + f[3] + bias_s[3]);
                     }
+                }
+            } else if constexpr (MODE == HID) {
+                constexpr int NE = 32 * S::NEPI;
+                const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
+                // one decision for the eight epilogue warps, also ordering the previous tile's reads
+                // of the output tile before this tile's writes
+                if (bar_or<2, NE>(!ok || *abort)) break;
+                tc_after();
+                __nv_bfloat16* Os = reinterpret_cast<__nv_bfloat16*>(sm + S::OFF_F);   // [TO][OSTR]
+                // warp w reads lane quarter w % 4 (channels 16 (w % 4) ..) over columns of half w / 4
+                const int quarter = warp & 3, half = warp >> 2;
+                const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * S::MMA_N);
+                const bool even = lane < 16;
+                const int co = 16 * quarter + (lane & 15);
+                const float bco = bias_s[co];
+                // D_even of the column before this half (the even lanes' first output needs it)
+                float prev = half ? tmem_ld1(tl + 127) : 0.0f;
+#pragma unroll 2
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int q = 8 * half + qq;              // 16-column chunk
+                    float v[16];
+                    tmem_ld16(tl + 16 * q, v);
+                    // outputs p = 16 q - 1 + i (even lanes) and 16 q + 7 + i (odd lanes), i < 8, each
+                    // D_even[p] + D_odd[p + 1]; the partner lane (xor 16) supplies the other half
+                    float x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = __shfl_xor_sync(0xffffffffu, even ? v[7 + i] : v[i], 16);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float de = even ? (i == 0 ? prev : v[i - 1]) : x[i];
+                        const float dod = even ? x[i] : v[8 + i];
+                        const int pp = even ? 16 * q - 1 + i : 16 * q + 7 + i;
+                        if (pp >= 0 && pp < S::TO)
+                            Os[pp * S::OSTR + co] = __float2bfloat16_rn(fmaxf(de + dod + bco, 0.0f));
+                    }
+                    prev = v[15];
+                }
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty(ab));
+                bar_sync<2, NE>();                            // output tile complete
+                // 16-byte rows (8 channels of one position) to the planes; a warp covers two planes
+                // x 16 consecutive positions
+                const int cc = (tid >> 4) & 7, poff = 16 * (tid >> 7);
+#pragma unroll 4
+                for (int r = 0; r < (S::TO + 31) / 32; ++r) {
+                    const int pp = 32 * r + poff + (tid & 15);
+                    const int64_t t = t0 + pp;
+                    if (pp < S::TO && t < T)
+                        *reinterpret_cast<uint4*>(a.act + ((int64_t)cc * Tp + t + PAD) * 8) =
+                            *reinterpret_cast<const uint4*>(Os + pp * S::OSTR + 8 * cc);
                 }
             } else {
                 const int64_t t = t0 + 32 * warp + lane;      // this thread's output position
@@ -385,11 +471,11 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 }
             }
         }
-    } else if (warp < 4 + S::NPW) {
+    } else if (warp < S::NEPI + S::NPW) {
         // ---- producer ----
         int it = 0, issued = 0;
         if constexpr (MODE == IN) {
-            const int r = tid - 128;                          // 0 .. 127
+            const int r = tid - 32 * S::NEPI;                 // 0 .. 127
             unsigned char* F = sm + S::OFF_F;                 // [FROWS][4] BF16: position t0 - 4 + u
             // this thread's staged positions u = r, r + 128 of a tile, loaded one tile ahead
             uint2 zp[2];
@@ -412,7 +498,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 bool ok = true;
                 if (r == 0) ok = mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort);
                 // one decision for the 128 producer threads; also orders the previous tile's reads of F
-                if (bar_or_128<1>(!ok || *abort)) break;
+                if (bar_or<1, 128>(!ok || *abort)) break;
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     if (r + 128 * h < S::FROWS) *reinterpret_cast<uint2*>(F + 8 * (r + 128 * h)) = zp[h];
@@ -464,9 +550,9 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                     ad = sdesc(st + 2 * ks * S::XPL, S::XPL, 128);
                     bd = sdesc(sW + 2 * ks * S::WPL, S::WPL, 128);
                 } else if constexpr (MODE == HID) {
-                    const int k = ks >> 2, j = ks & 3;        // tap, 16-channel group
-                    ad = sdesc(st + 2 * j * S::XPL + 16 * k, S::XPL, 128);
-                    bd = sdesc(sW + (8 * k + 2 * j) * S::WPL, S::WPL, 128);
+                    const int m = ks >> 2, j = ks & 3;        // tap pair, 16-channel group
+                    ad = sdesc(sW + (8 * m + 2 * j) * S::WPL, S::WPL, 128);
+                    bd = sdesc(st + 2 * j * S::XPL + 32 * m, S::XPL, 128);   // rows shifted by 2 m
                 } else {                                      // weights as A, positions as B
                     ad = sdesc(sW + 2 * ks * S::WPL, S::WPL, 128);
                     bd = sdesc(st + 2 * ks * S::XPL, S::XPL, 128);

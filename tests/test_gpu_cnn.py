@@ -162,7 +162,10 @@ def test_adam_step_matches_oracle(pe_params):
 def test_training_reduces_loss():
     """A fixed linear inter-symbol interference (each symbol picks up 0.25 j times its predecessor) is
     learnable through the residual ReLU network: 400 Adam steps on 4096-symbol slices bring the MSE
-    to a small fraction of the identity's (an FP32 PyTorch run of the same recipe reaches 3 % of it)."""
+    to a small fraction of the identity's. The rate decays from 2e-3 to 2e-4 so that the weights
+    the inference forward is judged on are not taken at a spike of the last steps (at a constant
+    2e-3 the final weights scored between 5 % and 15 % of the identity's MSE from run to run, the
+    weight gradients' atomic sums making runs differ)."""
     import torch
     from paper_2011_13695_gb300.learned import PostEqualiser
     rng = np.random.default_rng(7)
@@ -173,7 +176,7 @@ def test_training_reduces_loss():
     params = cnn.init_params(C, K, seed=3)
     pe = PostEqualiser(4096, cnn.flatten(params).astype(np.float32))
     z, t = to_dev(zc), to_dev(s)
-    losses = pe.train(z, t, 0, T, steps=400, window=4096, lr=2e-3, seed=1)
+    losses = pe.train(z, t, 0, T, steps=400, window=4096, lr=2e-3, seed=1, lr_final=2e-4)
     out = pe.forward(z[:, :4096].contiguous())
     pe.close()
     l0 = float(np.mean(np.abs(zc[:, :4096] - s[:, :4096]) ** 2)) / 2
