@@ -85,10 +85,12 @@ struct TcShape {
     static constexpr int S = 3;                                       // pipeline stages
     static constexpr int WB = NKC * WPL;                              // weight bytes: planes [kc][row][8]
     static constexpr int NPW = MODE == IN ? 4 : 1;                    // producer warps
-    static constexpr int NEPI = MODE == HID ? 8 : 4;                  // epilogue warps
+    static constexpr int NPART = MODE == IN ? 2 : 4;                  // epilogue warps per TMEM lane quarter
+    static constexpr int NEPI = 4 * NPART;                            // epilogue warps
     static constexpr int NWARP = NEPI + NPW + 1;
     static constexpr int NTHR = 32 * NWARP;
-    static constexpr int TCOLS = MODE == IN ? 128 : 512;              // TMEM columns (2 accumulators)
+    static constexpr int NACC = MODE == IN ? 8 : 2;                   // accumulators in tensor memory
+    static constexpr int TCOLS = NACC * MMA_N;                        // TMEM columns (a power of 2)
     static constexpr int FROWS = 128 + 12;                            // input layer: staged positions
     static constexpr int DROWS = 36, DSTR = 260;                      // output layer: D rows in smem (floats)
     static constexpr int OSTR = 72;                                   // hidden layers: output tile row (bf16)
@@ -101,7 +103,7 @@ struct TcShape {
     static constexpr int OFF_SLACK = OFF_F + AUX;
     static constexpr int SLACK = MODE == IN ? 40960 : 0;
     static constexpr int OFF_BAR = (OFF_SLACK + SLACK + 15) & ~15;
-    static constexpr int NBAR = 2 * S + 4;
+    static constexpr int NBAR = 2 * S + 2 * NACC;
     static constexpr int OFF_MISC = OFF_BAR + 8 * NBAR;               // tmem address, abort flag
     static constexpr int OFF_BIAS = OFF_MISC + 16;
     static constexpr int SMEM = OFF_BIAS + 4 * 64;
@@ -227,16 +229,6 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
                  : "memory");
     return __uint_as_float(r);
 }
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\ttcgen05.wait::ld.sync.aligned;"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr)
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -265,7 +257,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
     auto in_full = [&](int s) { return bar0 + 8u * s; };
     auto in_empty = [&](int s) { return bar0 + 8u * (S::S + s); };
     auto acc_full = [&](int b) { return bar0 + 8u * (2 * S::S + b); };
-    auto acc_empty = [&](int b) { return bar0 + 8u * (2 * S::S + 2 + b); };
+    auto acc_empty = [&](int b) { return bar0 + 8u * (2 * S::S + S::NACC + b); };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S::OFF_MISC);
     volatile int* abort = reinterpret_cast<volatile int*>(sm + S::OFF_MISC + 4);
     float* bias_s = reinterpret_cast<float*>(sm + S::OFF_BIAS);
@@ -305,7 +297,7 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
             mbar_init(in_full(s), MODE == IN ? 32 * S::NPW : 1);
             mbar_init(in_empty(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < S::NACC; ++b) {
             mbar_init(acc_full(b), 1);
             mbar_init(acc_empty(b), S::NEPI);
         }
@@ -335,32 +327,42 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
     if (warp < S::NEPI) {
         // ---- epilogue ----
         int it = 0;
+        float2 zcur = make_float2(0.0f, 0.0f);            // output layer: residual of the current tile
+        if (MODE == OUT && (tid & 255) < S::TO) {
+            const int64_t t = (int64_t)blockIdx.x * S::TO + (tid & 255);
+            if (t < T) zcur = a.z[(int64_t)(tid >> 8) * T + t];
+        }
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int ab = it & 1;
+            const int ab = it % S::NACC;
+            const uint32_t aph = (uint32_t)((it / S::NACC) & 1);
             const int64_t t0 = tile * S::TO;
             if constexpr (MODE == OUT) {
-                // this thread's outputs: tile positions p = tid and tid + 128 (p < 248); residual first
-                float2 zr[2][2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t t = t0 + tid + 128 * h;
-                    zr[h][0] = zr[h][1] = make_float2(0.0f, 0.0f);
-                    if (tid + 128 * h < S::TO && t < T) {
-                        zr[h][0] = a.z[t];
-                        zr[h][1] = a.z[T + t];
-                    }
+                constexpr int NE = 32 * S::NEPI;
+                constexpr int QP = S::MMA_N / 16 / S::NPART;  // 16-column chunks per part
+                // this thread's output: tile position p = tid % 256, polarisation tid / 256 (co 2 pol,
+                // 2 pol + 1), so that a warp reads 32 consecutive columns of one D row
+                const int p = tid & 255, pol = tid >> 8;
+                const int64_t t = t0 + p;
+                const bool mine = p < S::TO && t < T;
+                // the residual of this tile (loaded during the previous one) and of the next
+                const float2 zr = zcur;
+                {
+                    const int64_t tn = t + (int64_t)gridDim.x * S::TO;
+                    zcur = (p < S::TO && tn < T) ? a.z[(int64_t)pol * T + tn] : make_float2(0.0f, 0.0f);
                 }
-                const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
-                // one decision for the four epilogue warps (named barrier 2), which also orders the
+                const bool ok = mbar_wait(acc_full(ab), aph, abort);
+                // one decision for the epilogue warps (named barrier 2), which also orders the
                 // previous tile's reads of the D rows before this tile's writes
-                if (bar_or<2, 128>(!ok || *abort)) break;
+                if (bar_or<2, NE>(!ok || *abort)) break;
                 tc_after();
                 float* Ds = reinterpret_cast<float*>(sm + S::OFF_F);     // [36][DSTR]
-                if (warp < 2) {
-                    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::MMA_N);
-                    const int row = 32 * warp + lane;
-#pragma unroll 4
-                    for (int q = 0; q < S::MMA_N / 16; ++q) {
+                const int quarter = warp & 3, part = warp >> 2;
+                if (quarter < 2) {                            // the 36 used rows are in quarters 0, 1
+                    const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * S::MMA_N);
+                    const int row = 32 * quarter + lane;
+#pragma unroll
+                    for (int qq = 0; qq < QP; ++qq) {
+                        const int q = QP * part + qq;
                         float v[16];
                         tmem_ld16(tl + 16 * q, v);
                         if (row < S::DROWS) {
@@ -373,43 +375,40 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 tc_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty(ab));
-                bar_sync<2, 128>();                           // D rows complete
+                bar_sync<2, NE>();                            // D rows complete
+                if (mine) {
+                    float f[2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int p = tid + 128 * h;
-                    const int64_t t = t0 + p;
-                    if (p < S::TO && t < T) {
-                        float f[4];
+                    for (int c = 0; c < 2; ++c) {
+                        const int co = 2 * pol + c;
+                        float acc = 0.0f;
 #pragma unroll
-                        for (int co = 0; co < 4; ++co) {
-                            float acc = 0.0f;
-#pragma unroll
-                            for (int k = 0; k < 9; ++k) acc += Ds[(4 * k + co) * S::DSTR + p + k];
-                            f[co] = acc;
-                        }
-                        a.sym[t] = make_float2(zr[h][0].x + f[0] + bias_s[0], zr[h][0].y + f[1] + bias_s[1]);
-                        a.sym[T + t] = make_float2(zr[h][1].x + f[2] + bias_s[2], zr[h][1].y + f[3] + bias_s[3]);
+                        for (int k = 0; k < 9; ++k) acc += Ds[(4 * k + co) * S::DSTR + p + k];
+                        f[c] = acc;
                     }
+                    a.sym[(int64_t)pol * T + t] =
+                        make_float2(zr.x + f[0] + bias_s[2 * pol], zr.y + f[1] + bias_s[2 * pol + 1]);
                 }
             } else if constexpr (MODE == HID) {
                 constexpr int NE = 32 * S::NEPI;
-                const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
-                // one decision for the eight epilogue warps, also ordering the previous tile's reads
+                const bool ok = mbar_wait(acc_full(ab), aph, abort);
+                // one decision for the epilogue warps, also ordering the previous tile's reads
                 // of the output tile before this tile's writes
                 if (bar_or<2, NE>(!ok || *abort)) break;
                 tc_after();
                 __nv_bfloat16* Os = reinterpret_cast<__nv_bfloat16*>(sm + S::OFF_F);   // [TO][OSTR]
-                // warp w reads lane quarter w % 4 (channels 16 (w % 4) ..) over columns of half w / 4
-                const int quarter = warp & 3, half = warp >> 2;
+                // warp w reads lane quarter w % 4 (channels 16 (w % 4) ..) over column part w / 4
+                constexpr int QP = S::MMA_N / 16 / S::NPART;  // 16-column chunks per part
+                const int quarter = warp & 3, part = warp >> 2;
                 const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * S::MMA_N);
                 const bool even = lane < 16;
                 const int co = 16 * quarter + (lane & 15);
                 const float bco = bias_s[co];
-                // D_even of the column before this half (the even lanes' first output needs it)
-                float prev = half ? tmem_ld1(tl + 127) : 0.0f;
+                // D_even of the column before this part (the even lanes' first output needs it)
+                float prev = part ? tmem_ld1(tl + 16 * QP * part - 1) : 0.0f;
 #pragma unroll 2
-                for (int qq = 0; qq < 8; ++qq) {
-                    const int q = 8 * half + qq;              // 16-column chunk
+                for (int qq = 0; qq < QP; ++qq) {
+                    const int q = QP * part + qq;             // 16-column chunk
                     float v[16];
                     tmem_ld16(tl + 16 * q, v);
                     // outputs p = 16 q - 1 + i (even lanes) and 16 q + 7 + i (odd lanes), i < 8, each
@@ -433,34 +432,40 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 bar_sync<2, NE>();                            // output tile complete
                 // 16-byte rows (8 channels of one position) to the planes; a warp covers two planes
                 // x 16 consecutive positions
+                constexpr int PSTEP = 16 * (NE / 128);        // positions per pass of all threads
                 const int cc = (tid >> 4) & 7, poff = 16 * (tid >> 7);
 #pragma unroll 4
-                for (int r = 0; r < (S::TO + 31) / 32; ++r) {
-                    const int pp = 32 * r + poff + (tid & 15);
+                for (int r = 0; r < (S::TO + PSTEP - 1) / PSTEP; ++r) {
+                    const int pp = PSTEP * r + poff + (tid & 15);
                     const int64_t t = t0 + pp;
                     if (pp < S::TO && t < T)
                         *reinterpret_cast<uint4*>(a.act + ((int64_t)cc * Tp + t + PAD) * 8) =
                             *reinterpret_cast<const uint4*>(Os + pp * S::OSTR + 8 * cc);
                 }
             } else {
-                const int64_t t = t0 + 32 * warp + lane;      // this thread's output position
-                const bool ok = mbar_wait(acc_full(ab), (uint32_t)((it >> 1) & 1), abort);
+                // warp w: positions of lane quarter w % 4, channels of part w / 4
+                constexpr int CP = S::MMA_N / S::NPART;       // channels per part
+                const int quarter = warp & 3, part = warp >> 2;
+                const int64_t t = t0 + 32 * quarter + lane;   // this thread's output position
+                const bool ok = mbar_wait(acc_full(ab), aph, abort);
                 if (!__all_sync(0xffffffffu, ok)) break;  // warp-uniform: the loads below are .sync.aligned
                 tc_after();
-                const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * S::MMA_N);
-                float v[64];
+                const uint32_t tl =
+                    tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * S::MMA_N + CP * part);
+                float v[CP];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tmem_ld16(tl + 16 * q, v + 16 * q);
+                for (int q = 0; q < CP / 16; ++q) tmem_ld16(tl + 16 * q, v + 16 * q);
                 tc_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty(ab));
                 if (t < T) {
                     __nv_bfloat16* dst = a.act + (t + PAD) * 8;
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) {
+                    for (int c8 = 0; c8 < CP / 8; ++c8) {
+                        const int cc = (CP / 8) * part + c8;
                         float w[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) w[e] = fmaxf(v[8 * cc + e] + bias_s[8 * cc + e], 0.0f);
+                        for (int e = 0; e < 8; ++e) w[e] = fmaxf(v[8 * c8 + e] + bias_s[8 * cc + e], 0.0f);
                         uint4 o;
                         o.x = pack_bf16(w[0], w[1]);
                         o.y = pack_bf16(w[2], w[3]);
@@ -477,32 +482,35 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         if constexpr (MODE == IN) {
             const int r = tid - 32 * S::NEPI;                 // 0 .. 127
             unsigned char* F = sm + S::OFF_F;                 // [FROWS][4] BF16: position t0 - 4 + u
-            // this thread's staged positions u = r, r + 128 of a tile, loaded one tile ahead
-            uint2 zp[2];
-            auto zload = [&](int64_t tile) {
+            // this thread's staged positions u = r, r + 128 of a tile, loaded two tiles ahead into one of
+            // two register sets used alternately and kept as loaded (converted only when written), so
+            // that each load has two tiles' time to arrive
+            float2 za[2][2], zb[2][2];
+            auto zload = [&](int64_t tile, float2 (&zz)[2][2]) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int u = r + 128 * h;
                     const int64_t tt = tile * S::TO - PAD + u;
-                    float2 z0 = make_float2(0.0f, 0.0f), z1 = z0;
+                    zz[h][0] = zz[h][1] = make_float2(0.0f, 0.0f);
                     if (u < S::FROWS && tile < ntiles && tt >= 0 && tt < T) {
-                        z0 = a.z[tt];
-                        z1 = a.z[T + tt];
+                        zz[h][0] = a.z[tt];
+                        zz[h][1] = a.z[T + tt];
                     }
-                    zp[h] = make_uint2(pack_bf16(z0.x, z0.y), pack_bf16(z1.x, z1.y));
                 }
             };
-            zload(blockIdx.x);
-            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            // one tile: planes from zz, then zz reloaded for the tile two steps later; false = stop
+            auto produce = [&](int64_t tile, float2 (&zz)[2][2]) -> bool {
                 const int s = it % S::S;
                 bool ok = true;
                 if (r == 0) ok = mbar_wait(in_empty(s), (uint32_t)(((it / S::S) & 1) ^ 1), abort);
                 // one decision for the 128 producer threads; also orders the previous tile's reads of F
-                if (bar_or<1, 128>(!ok || *abort)) break;
+                if (bar_or<1, 128>(!ok || *abort)) return false;
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
-                    if (r + 128 * h < S::FROWS) *reinterpret_cast<uint2*>(F + 8 * (r + 128 * h)) = zp[h];
-                zload(tile + gridDim.x);
+                    if (r + 128 * h < S::FROWS)
+                        *reinterpret_cast<uint2*>(F + 8 * (r + 128 * h)) =
+                            make_uint2(pack_bf16(zz[h][0].x, zz[h][0].y), pack_bf16(zz[h][1].x, zz[h][1].y));
+                zload(tile + 2 * (int64_t)gridDim.x, zz);
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 unsigned char* st = sm + S::OFF_ST + s * S::STAGE;
 #pragma unroll
@@ -513,6 +521,14 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 }
                 fence_async_smem();
                 mbar_arrive(in_full(s));
+                ++it;
+                return true;
+            };
+            zload(blockIdx.x, za);
+            zload(blockIdx.x + gridDim.x, zb);
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += 2 * (int64_t)gridDim.x) {
+                if (!produce(tile, za)) break;
+                if (tile + gridDim.x < ntiles && !produce(tile + gridDim.x, zb)) break;
             }
         } else {
             if (lane == 0) {
@@ -537,9 +553,9 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
         // ---- MMA issue ----
         int it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int s = it % S::S, ab = it & 1;
+            const int s = it % S::S, ab = it % S::NACC;
             if (!mbar_wait(in_full(s), (uint32_t)((it / S::S) & 1), abort)) break;
-            if (!mbar_wait(acc_empty(ab), (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
+            if (!mbar_wait(acc_empty(ab), (uint32_t)(((it / S::NACC) & 1) ^ 1), abort)) break;
             tc_after();
             const uint32_t d = tmem + (uint32_t)(ab * S::MMA_N);
             const uint32_t st = sSt + s * S::STAGE;
