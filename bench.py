@@ -233,9 +233,15 @@ def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz:
         name, flops = alu[stage]
         peak = 2 * lanes / 1e12
         a = flops / t / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                "traffic": _traffic(stage), "algorithmic_flops": flops,
-                "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+        r = {"kernel": name, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+             "traffic": _traffic(stage), "algorithmic_flops": flops,
+             "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+        if stage in ("cma", "dd_acq"):
+            # a serial chain of block steps, one CTA (holding a whole SM) per output row: the fraction of
+            # the two SMs it can occupy is the meaningful one
+            r["occupied_sms"] = 2
+            r["frac_of_occupied_sms"] = a / (peak * 2 / SM_COUNT_GB300)
+        return r
     if stage == "bps":
         ops = 2 * n_sym * rxs["bps_phases"] * 16          # lane-ops per (symbol, test phase)
         peak = lanes / 1e12
