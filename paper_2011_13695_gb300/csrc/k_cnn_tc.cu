@@ -1,14 +1,13 @@
 // Inference forward of the learned post-equaliser on the 5th-generation tensor
 // cores (tcgen05.mma, BF16 x BF16 -> FP32 accumulators in tensor memory).
 //
-// Each layer is a matrix product per tile of 128 output positions:
-//   D[t][co] = sum_K A[t][K] B[K][co],  K = (k, ci),
-//   A[t][(k, ci)] = x[ci][t + k - 4],   B[(k, ci)][co] = W[co][ci][k],
-// M = 128 positions (one TMEM lane each), N = the 64 output channels, K = 9
-// taps x the input channels in steps of 16 (input and hidden layers). The
-// 4-channel output layer swaps the roles: M = (tap, output channel) rows of
-// the weights, N = 256 positions, K = the 64 input channels, and the epilogue
-// adds each tap's row at its shift.
+// Each layer is a matrix product per tile of output positions, with
+//   out[co][t] = sum_{k, ci} W[co][ci][k] x[ci][t + k - 4]
+// and one of three operand mappings (details at TcShape below): the input
+// layer takes the positions as M (128 per tile) and the weights as N; the
+// hidden layers take the weights of two taps stacked as M and 256 positions
+// as N; the output layer takes (tap, output channel) weight rows as M and 256
+// positions as N.
 //
 // Activation layout (HBM): the hidden layers' BF16 activations are stored in
 // eight channel-chunk planes [C/8][T + 8][8], padded position-major, so that
@@ -16,22 +15,22 @@
 // memory unchanged (one bulk async copy per plane and tile), this is the
 // K-major no-swizzle operand layout of the MMA (core matrices of 8 rows x 16
 // bytes, rows 16 bytes apart, 8-row groups 128 bytes apart, K chunks one plane
-// apart), and the operand of tap k is the same planes read from row k: the
-// descriptor's start address moves by 16 k bytes, always 16-byte aligned.
+// apart), and shifting the operand by r positions moves the descriptor's
+// start address by 16 r bytes, always 16-byte aligned.
 // The input layer (4 -> 64) builds its operand from the FP32 symbols:
 // K = (tap, channel) with 4 channels, padded to 48 with zero weights, six
 // planes whose row r holds the 8 values of taps 2j, 2j + 1 at position r.
 //
-// Roles (warp-specialised, one CTA per SM slot, tiles strided over the grid):
-//   warps 0-3  epilogue: TMEM lane quarter w holds positions 32 w .. 32 w + 31;
-//              bias, ReLU, BF16 and a 16-byte store per plane (coalesced); the
-//              output layer's warps 0-1 copy the 36 used rows to shared memory
-//              and all four add the taps, the bias and the residual;
+// Roles (warp-specialised, one CTA per SM, tiles strided over the grid):
+//   epilogue   4 x NPART warps; warp w reads TMEM lane quarter w % 4 over
+//              part w / 4 of the accumulator's columns, then bias, ReLU, BF16
+//              and 16-byte stores per plane (coalesced), or for the output
+//              layer the taps' sum, bias and residual into the symbols;
 //   producer   one thread issuing the bulk copies of a stage (hidden, output
 //              layers), or four warps building the input layer's planes;
 //   last warp  TMEM allocation, and one thread issuing the MMAs of a tile
-//              into one of two accumulator buffers and committing them to
-//              the stage-free and accumulator-full barriers.
+//              into one of the accumulators and committing them to the
+//              stage-free and accumulator-full barriers.
 // Every wait is bounded (globaltimer); on a timeout the CTA sets the error
 // word, stops all roles, waits for its own copies and MMAs in flight (again
 // bounded) and frees its tensor memory.
