@@ -42,7 +42,8 @@ struct LmsFastShape {
     static constexpr int NG = (LB + G - 1) / G;            // symbols per group
     static constexpr int PF = (2 * XW + NT - 1) / NT;      // window registers per thread
     static constexpr int NWARP = NT / 32;
-    static constexpr int SMEM = 4 * RP + 2 * T + 2 * (2 * XS + 4 * XE) + LB + G * 2 * T + NWARP + XW;   // float2
+    static constexpr int NBT = 256;                        // derotation bases of the first NBT blocks
+    static constexpr int SMEM = 4 * RP + 2 * T + 2 * (2 * XS + 4 * XE) + LB + G * 2 * T + NWARP + XW + NBT;   // float2
     static_assert(NT % LB == 0 && (P & (P - 1)) == 0 && P <= 32, "NT must be a power-of-two multiple of LB");
     static_assert(G >= 1, "at least 2T threads");
     static_assert(T % 2 == 1, "odd tap count: window index parity follows the tap index");
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     float2* part = es + LB;                                // [G][2T]
     float2* ypart = part + S::G * 2 * T;                   // [NWARP]
     float2* tab = ypart + S::NWARP;                        // [XW]
+    float2* btab = tab + S::XW;                            // [NBT]: derotation base of block b's window
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
@@ -89,6 +91,11 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     const int64_t nfirst = start - (int64_t)nwarm * LB;    // block b starts at symbol nfirst + b LB
     const float2* const xp0 = a.x;
     const float2* const xp1 = a.x + a.xstride;
+    // the derotation of block b's window starts at input sample g0 + off + 2 (nfirst + b LB) - C; its
+    // phasor is taken once per block here instead of by every thread at every commit
+    const long long gfirst = a.g0 + a.off + 2 * nfirst - S::C;
+    if (inc)
+        for (int b = tid; b < nblk; b += NT) btab[b] = nco_conj(inc, gfirst + 2LL * LB * b);   // nblk <= NBT
 
     // every window the CTA will read, requested into L2 (128-byte lines)
     if (nblk > 0) {
@@ -119,9 +126,8 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
             pf[r] = v;
         }
     };
-    auto commit = [&](float2* xs, int64_t n0) {
-        const long long g0 = a.g0 + a.off + 2 * n0 - S::C;
-        const float2 base = inc ? nco_conj(inc, g0) : make_float2(1.0f, 0.0f);
+    auto commit = [&](float2* xs, int blk) {
+        const float2 base = inc ? btab[blk] : make_float2(1.0f, 0.0f);
 #pragma unroll
         for (int r = 0; r < S::PF; ++r) {
             const int t = tid + r * NT;
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
     __syncthreads();                                       // taps and table
     if (nblk > 0) {
         prefetch(nfirst);
-        commit(xsb, nfirst);
+        commit(xsb, 0);
     }
     __syncthreads();
 
@@ -281,14 +287,13 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
         constexpr int NOUT = S::PAIR ? 2 : 1;
         const bool lead = j == 0;
         const bool v0 = lead && n_out < L, v1 = lead && NOUT == 2 && n_out + 1 < L;
-        if (b >= nwarm && a.y != nullptr) {
-            float2* yq = a.y + (int64_t)q * a.ystride + n0 + n_out;
-            if (v0) yq[0] = y0;
-            if (v1) yq[1] = y1;
-        }
+        // every lane of a pair holds both sums: lane 0 takes the first output, lane 1 the second
+        const int jo = (NOUT == 2 && j < 2) ? j : 0;
+        const bool vo = (NOUT == 2 ? j < 2 : lead) && n_out + jo < L;
+        const float2 yo = jo ? y1 : y0;
+        if (b >= nwarm && a.y != nullptr && vo) a.y[(int64_t)q * a.ystride + n0 + n_out + jo] = yo;
         if (a.cma) {
-            if (v0) es[n_out] = cscale(y0, a.R2 - cabs2(y0));
-            if (v1) es[n_out + 1] = cscale(y1, a.R2 - cabs2(y1));
+            if (vo) es[n_out + jo] = cscale(yo, a.R2 - cabs2(yo));
         } else {
             float2 c4 = make_float2(0.0f, 0.0f);
             if (v0) {
@@ -307,13 +312,9 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
 #pragma unroll
             for (int w = 1; w < S::NWARP; ++w) sum = cadd(sum, ypart[w]);
             const float2 r = quarter_root_conj(make_float2(-sum.x, -sum.y));
-            if (v0) {
-                const float2 d = qam_decide(cmul(y0, r), qm);
-                es[n_out] = csub(cmulc(d, r), y0);
-            }
-            if (v1) {
-                const float2 d = qam_decide(cmul(y1, r), qm);
-                es[n_out + 1] = csub(cmulc(d, r), y1);
+            if (vo) {
+                const float2 d = qam_decide(cmul(yo, r), qm);
+                es[n_out + jo] = csub(cmulc(d, r), yo);
             }
         }
         __syncthreads();
@@ -343,11 +344,17 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
             taps[tid] = hn;
             *tps_at(tid) = hn;
         }
-        if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * WBUF, n0 + LB);
+        if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * WBUF, b + 1);
         __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out)
         for (int t = tid; t < 2 * T; t += NT) a.taps_out[q * 2 * T + t] = taps[t];
+}
+
+// the compile-time kernel keeps one derotation base per block of a CTA: at most NBT blocks
+template <int LB>
+inline bool lms_fast_fits(const LmsArgs& a) {
+    return (a.L_seg + LB - 1) / LB + a.n_wu <= 256;
 }
 
 template <int NT, int T, int LB>

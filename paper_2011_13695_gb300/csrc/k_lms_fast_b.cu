@@ -3,7 +3,7 @@
 
 template <int T, int LB>
 static bool pick(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err) {
-    if (a.T != T || a.Lb != LB) return false;
+    if (a.T != T || a.Lb != LB || !lms_fast_fits<LB>(a)) return false;
     if (threads == 128) { *err = launch_lms_fast_t<128, T, LB>(a, s); return true; }
     if (threads == 256) { *err = launch_lms_fast_t<256, T, LB>(a, s); return true; }
     if (threads == 512) { *err = launch_lms_fast_t<512, T, LB>(a, s); return true; }
