@@ -191,7 +191,7 @@ class ClockSampler:
 # DRAM traffic per launch from one ncu capture (profiles/), valid while the kernel's source file is
 # unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
 PROFILED_TRAFFIC = {
-    "dd_acq": ("k_lms_fast.cuh", "9f0dbfd647696cf096617912902fa5e32febde82", 559360),   # DRAM bytes read + written, one ncu capture of this launch
+    "dd_acq": ("k_lms_fast.cuh", "69f50b49384b4b79ea9d309a0e8eac02cc5bec2b", 561664),   # DRAM bytes read + written, one ncu capture of this launch
 }
 
 
