@@ -258,6 +258,27 @@ def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz:
 
 
 # --------------------------------------------------------------------------------------
+# replicas on several GPUs (host side; the data path has no collective)
+# --------------------------------------------------------------------------------------
+
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Each value replaced by its maximum over the ranks of the process group (the job's time is its
+    slowest replica's); without a process group the values are returned unchanged."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_line_rate(world: int, bits_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job line rate in Gb/s: every rank processes its own frame of bits_per_step bits per step,
+    and the job takes the slowest rank's time for the steps."""
+    return world * bits_per_step * steps / (total_ms * 1e-3) / 1e9
+
+
+# --------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------
 
@@ -329,10 +350,7 @@ def our_arm(args) -> None:
     barrier()
     stages = rx.rx_stage_times(rcv.h)
     rx.rx_set_timing(rcv.h, False)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks([total_ms], dist, "cuda")[0]
     st = rcv.stats()
 
     # end to end from pinned host memory
@@ -353,10 +371,7 @@ def our_arm(args) -> None:
             e_evs[i][1].record(stream)
         barrier()
         e2e_ms = sum(a.elapsed_time(b) for a, b in e_evs)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks([e2e_ms], dist, "cuda")[0]
 
     if rank != 0:
         if dist:
@@ -371,8 +386,8 @@ def our_arm(args) -> None:
     dom = max(single or per_stage, key=(single or per_stage).get)
     roof = stage_roofline(dom, per_stage[dom], w, N, pk, csum.get("sm_mhz"))
     roof["peak_source"] = "fallback" if pk.get("fallback") else "measured (MEASURED_PEAKS.json) / nominal unit count"
-    value = world * bits_per_step * args.steps / (total_ms * 1e-3) / 1e9
-    e2e = world * bits_per_step * args.steps / (e2e_ms * 1e-3) / 1e9 if e2e_ms == e2e_ms else None
+    value = replica_line_rate(world, bits_per_step, args.steps, total_ms)
+    e2e = replica_line_rate(world, bits_per_step, args.steps, e2e_ms) if e2e_ms == e2e_ms else None
     line = {
         "metric": "processed line rate", "value": value, "unit": "Gb/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
