@@ -98,7 +98,10 @@ struct TcShape {
     // read can leave the allocation, then barriers and small state
     static constexpr int OFF_ST = WB;
     static constexpr int OFF_F = OFF_ST + S * STAGE;
-    static constexpr int AUX = MODE == IN ? FROWS * 8 : MODE == HID ? TO * OSTR * 2 : DROWS * DSTR * 4;
+    // input layer: staged positions, then two output tiles [8 planes][128 positions][16 B] that bulk
+    // async stores write out
+    static constexpr int OB = 8 * 128 * 16;
+    static constexpr int AUX = MODE == IN ? FROWS * 8 + 2 * OB : MODE == HID ? TO * OSTR * 2 : DROWS * DSTR * 4;
     static constexpr int OFF_SLACK = OFF_F + AUX;
     static constexpr int SLACK = MODE == IN ? 40960 : 0;
     static constexpr int OFF_BAR = (OFF_SLACK + SLACK + 15) & ~15;
@@ -184,6 +187,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -442,12 +455,18 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                             *reinterpret_cast<const uint4*>(Os + pp * S::OSTR + 8 * cc);
                 }
             } else {
-                // warp w: positions of lane quarter w % 4, channels of part w / 4
+                // warp w: positions of lane quarter w % 4, channels of part w / 4; the tile goes through
+                // one of two shared-memory output tiles and leaves by bulk async stores (one per plane)
+                constexpr int NE = 32 * S::NEPI;
                 constexpr int CP = S::MMA_N / S::NPART;       // channels per part
                 const int quarter = warp & 3, part = warp >> 2;
-                const int64_t t = t0 + 32 * quarter + lane;   // this thread's output position
+                const int pl = 32 * quarter + lane;           // this thread's tile position
+                const int ob = it & 1;
+                const uint32_t obase = sbase + S::OFF_F + S::FROWS * 8 + ob * S::OB;
+                // the stores that read this output tile two tiles ago are done with it
+                if (tid == 0 && it >= 2) bulk_wait_read<1>();
                 const bool ok = mbar_wait(acc_full(ab), aph, abort);
-                if (!__all_sync(0xffffffffu, ok)) break;  // warp-uniform: the loads below are .sync.aligned
+                if (bar_or<2, NE>(!ok || *abort)) break;  // uniform; also orders the tile's reuse
                 tc_after();
                 const uint32_t tl =
                     tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ab * S::MMA_N + CP * part);
@@ -457,24 +476,31 @@ __global__ void __launch_bounds__(TcShape<MODE>::NTHR, 1) k_conv_tc(TcArgs a) {
                 tc_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty(ab));
-                if (t < T) {
-                    __nv_bfloat16* dst = a.act + (t + PAD) * 8;
+                unsigned char* otile = sm + S::OFF_F + S::FROWS * 8 + ob * S::OB;
 #pragma unroll
-                    for (int c8 = 0; c8 < CP / 8; ++c8) {
-                        const int cc = (CP / 8) * part + c8;
-                        float w[8];
+                for (int c8 = 0; c8 < CP / 8; ++c8) {
+                    const int cc = (CP / 8) * part + c8;
+                    float w[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) w[e] = fmaxf(v[8 * c8 + e] + bias_s[8 * cc + e], 0.0f);
-                        uint4 o;
-                        o.x = pack_bf16(w[0], w[1]);
-                        o.y = pack_bf16(w[2], w[3]);
-                        o.z = pack_bf16(w[4], w[5]);
-                        o.w = pack_bf16(w[6], w[7]);
-                        *reinterpret_cast<uint4*>(dst + (int64_t)cc * Tp * 8) = o;
-                    }
+                    for (int e = 0; e < 8; ++e) w[e] = fmaxf(v[8 * c8 + e] + bias_s[8 * cc + e], 0.0f);
+                    uint4 o;
+                    o.x = pack_bf16(w[0], w[1]);
+                    o.y = pack_bf16(w[2], w[3]);
+                    o.z = pack_bf16(w[4], w[5]);
+                    o.w = pack_bf16(w[6], w[7]);
+                    *reinterpret_cast<uint4*>(otile + (cc * 128 + pl) * 16) = o;
+                }
+                fence_async_smem();                           // written by threads, read by the copies
+                bar_sync<2, NE>();
+                if (tid == 0) {
+                    const int n = (int)min((int64_t)128, T - t0);   // positions of this tile in the frame
+                    for (int cc = 0; cc < 8; ++cc)
+                        bulk_s2g(a.act + ((int64_t)cc * Tp + t0 + PAD) * 8, obase + cc * 128 * 16, (uint32_t)(n * 16));
+                    bulk_commit();
                 }
             }
         }
+        if (MODE == IN && tid == 0) bulk_wait_all();          // the output tiles are written out
     } else if (warp < S::NEPI + S::NPW) {
         // ---- producer ----
         int it = 0, issued = 0;
