@@ -73,7 +73,9 @@ def pe_params():
     return vec, cnn.unflatten(bf16(vec), C, K)
 
 
-@pytest.mark.parametrize("T", [1, 7, 300, 3001, 4096])
+# 128 (input layer) and 248 (hidden and output layers) positions per tile: lengths at and around
+# the tile boundaries, and one that ends a tile one position into it
+@pytest.mark.parametrize("T", [1, 7, 127, 128, 129, 247, 248, 249, 300, 496, 497, 3001, 4096])
 def test_forward_matches_oracle(pe_params, T):
     from paper_2011_13695_gb300.learned import PostEqualiser
     vec, pb = pe_params
