@@ -189,6 +189,28 @@ def test_training_reduces_loss():
     assert last < 0.1 * first and l_end < 0.1 * l0, (first, last, l0, l_end)
 
 
+def test_inference_forward_equals_training_forward():
+    """The inference forward (tensor cores, channel-chunk planes) and the training forward (channel-major
+    activations) compute the same network: after some training, the loss of the inference output equals
+    the loss the gradient call computes from its own forward on the same window (both accumulate in FP32
+    over BF16 operands, in different orders)."""
+    import torch
+    from paper_2011_13695_gb300.learned import PostEqualiser
+    T = 3001
+    zc, tc = qam_like(T, seed=21), qam_like(T, seed=22)
+    params = cnn.init_params(C, K, seed=4)
+    pe = PostEqualiser(4096, cnn.flatten(params).astype(np.float32))
+    z, t = to_dev(zc), to_dev(tc)
+    pe.train(z, t, 0, T, steps=30, window=2048, lr=1e-3, seed=2)
+    out = pe.forward(z)
+    l_inf = float(torch.mean(torch.abs(out - t) ** 2).item()) / 2
+    _, loss = pe.gradients(z, t)
+    l_tr = float(loss.item())
+    assert pe.error_word() == 0
+    pe.close()
+    assert abs(l_inf - l_tr) <= 1e-4 * l_tr, (l_inf, l_tr)
+
+
 def test_invalid_arguments():
     import torch
     from paper_2011_13695_gb300 import rx
