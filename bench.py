@@ -272,6 +272,14 @@ def max_over_ranks(values, dist=None, device="cpu"):
     return [float(v) for v in t.tolist()]
 
 
+def hbm_step_roofline(bytes_per_step: int, ms_per_step: float, pk: dict) -> dict:
+    """A whole step's compulsory HBM bytes over its time, against the measured copy bandwidth."""
+    gbs = bytes_per_step / (ms_per_step * 1e-3) / 1e9
+    peak = pk.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "bytes_per_step": bytes_per_step, "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak}
+
+
 def replica_line_rate(world: int, bits_per_step: int, steps: int, total_ms: float) -> float:
     """Whole-job line rate in Gb/s: every rank processes its own frame of bits_per_step bits per step,
     and the job takes the slowest rank's time for the steps."""
@@ -400,6 +408,10 @@ def our_arm(args) -> None:
                 "d2h_bytes_per_step": int(oh.numel() * 4)},
         "gpu_launches": int(launches),
         "roofline": roof,
+        # the whole step against HBM: its compulsory bytes (the frame's samples and reference bits in,
+        # the decided bits out) over the step time; the chain is ALU- and latency-bound, so this is small
+        "hbm_roofline": hbm_step_roofline(int(x_host.nbytes + ref_host.nbytes + 2 * rcv.words(N) * 4),
+                                          total_ms / args.steps, pk),
         "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "ber": st["ber"], "evm": st["evm"], "fo_code": st["fo_code"],
         "clocks": csum,
