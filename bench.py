@@ -249,7 +249,11 @@ def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz:
         return {"kernel": "k_bps", "bound": "alu", "achieved": a, "peak": peak, "unit": "Tops/s",
                 "frac": a / peak, "traffic": _traffic(stage), "algorithmic_ops": ops,
                 "peak_note": "152 SMs x 128 lanes x max SM clock"}
-    byts = {"cdc": 2 * (2 * n_sym) * 8 * 2, "power": 2 * (2 * n_sym) * 8, "unwrap": 2 * n_sym * (8 + 1 + 8 + 4),
+    # FD compensation: the acquisition's blocks first ("cdc": its window plus one FFT of reach), the
+    # rest beside the acquisition ("cdc_rest"); the power estimate reads the CMA window only
+    acq_samples = min(2 * n_sym, 2 * max(rxs["cma_blocks"], rxs["dd_acq_blocks"]) * Lb + rxs["fft_size"])
+    byts = {"cdc": 2 * acq_samples * 8 * 2, "cdc_rest": 2 * (2 * n_sym - acq_samples) * 8 * 2,
+            "power": 2 * min(2 * n_sym, 2 * rxs["cma_blocks"] * Lb) * 8, "unwrap": 2 * n_sym * (8 + 1 + 8 + 4),
             "count": 2 * n_sym * 8 + 2 * 2 * n_sym * m / 8, "sync": 0, "foe": 0}.get(stage, 0)
     a = byts / t / 1e9 if t > 0 else 0.0
     peak = pk.get("hbm_gbs", 6800.0)
@@ -413,6 +417,11 @@ def our_arm(args) -> None:
         "hbm_roofline": hbm_step_roofline(int(x_host.nbytes + ref_host.nbytes + 2 * rcv.words(N) * 4),
                                           total_ms / args.steps, pk),
         "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        # every stage against its own bound (algorithmic work of the stage over its time)
+        "stage_roofline": {k: {"bound": r["bound"], "frac": round(r["frac"], 5), "unit": r["unit"],
+                               "achieved": round(r["achieved"], 3)}
+                           for k, r in ((k, stage_roofline(k, v, w, N, pk, csum.get("sm_mhz")))
+                                        for k, v in per_stage.items() if k not in ("sync", "foe"))},
         "ber": st["ber"], "evm": st["evm"], "fo_code": st["fo_code"],
         "clocks": csum,
     }
