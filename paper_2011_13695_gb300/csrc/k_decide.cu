@@ -152,7 +152,15 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
             v = quarter(z[(int64_t)q * zstride + n], r);
             sbits = msb_first_to_stream(qam_bits(qam_level(v.x, qm), qam_level(v.y, qm), qm), m);
         }
-        if (out) {
+        if (out && (m == 2 || m == 4)) {
+            // whole symbols per word: lanes g 32/m .. (g + 1) 32/m - 1 fill word g of the warp's m words;
+            // an OR over each lane group (shuffles within the group), then the group's first lane stores
+            const int per = 32 / m;                    // symbols per word
+            uint32_t word = (n < N) ? sbits << ((lane % per) * m) : 0u;
+            for (int o = 1; o < per; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
+            const int64_t wi = (n - lane) * m / 32 + lane / per;
+            if (lane % per == 0 && wi < nwords) out[(int64_t)q * outstride + wi] = word;
+        } else if (out) {
             // warp symbols n0..n0+31 fill words [n0*m/32, n0*m/32 + m)
             const int64_t n0 = n - lane;
             for (int w = 0; w < m; ++w) {
