@@ -597,19 +597,20 @@ static rx_status enqueue_host(rx_handle* h, const void* h_in, int64_t n_sym, con
         // The acquisition needs only the head of each polarisation: that is copied on the caller's
         // stream, the rest of the input and the reference bits on the side stream, where they overlap
         // the acquisition and precede the rest of the FD compensation (and the join before the
-        // segments). The side stream first waits for the caller's stream, whose previous frame may
-        // still read the staging buffers.
+        // segments). The side stream waits for the head's copy (and so for the caller's stream, whose
+        // previous frame may still read the staging buffers): copies issued together share the link,
+        // and the head would then arrive only with the whole frame.
         const int64_t head = std::min<int64_t>(S, na * (h->cfg.fft_size / 2) + h->cfg.fft_size / 4);
         const char* src = static_cast<const char*>(h_in);
         char* dst = static_cast<char*>(h->stage_in);
         const size_t eb = (size_t)h->in_elem;
-        RX_CK(cudaEventRecord(h->ev_host, s));
-        RX_CK(cudaStreamWaitEvent(h->side, h->ev_host, 0));
         {
             StageScope sc(h, ST_H2D, s);
             for (int p = 0; p < 2; ++p)
                 RX_CK(cudaMemcpyAsync(dst + p * S * eb, src + p * S * eb, (size_t)head * eb, cudaMemcpyHostToDevice, s));
         }
+        RX_CK(cudaEventRecord(h->ev_host, s));
+        RX_CK(cudaStreamWaitEvent(h->side, h->ev_host, 0));
         for (int p = 0; p < 2; ++p)
             if (S > head)
                 RX_CK(cudaMemcpyAsync(dst + (p * S + head) * eb, src + (p * S + head) * eb, (size_t)(S - head) * eb,
