@@ -93,18 +93,15 @@ struct TcShape {
     static constexpr int FROWS = 128 + 12;                            // input layer: staged positions
     static constexpr int DROWS = 36, DSTR = 260;                      // output layer: D rows in smem (floats)
     static constexpr int OSTR = 72;                                   // hidden layers: output tile row (bf16)
-    // shared memory: weights, stages, then the input layer's staged positions, the hidden layers'
-    // BF16 output tile or the output layer's D rows, a slack region (input layer) so that no operand
-    // read can leave the allocation, then barriers and small state
+    // shared memory: weights, stages, then the input layer's staged positions and output tiles, the
+    // hidden layers' BF16 output tile or the output layer's D rows, then barriers and small state
     static constexpr int OFF_ST = WB;
     static constexpr int OFF_F = OFF_ST + S * STAGE;
     // input layer: staged positions, then two output tiles [8 planes][128 positions][16 B] that bulk
     // async stores write out
     static constexpr int OB = 8 * 128 * 16;
     static constexpr int AUX = MODE == IN ? FROWS * 8 + 2 * OB : MODE == HID ? TO * OSTR * 2 : DROWS * DSTR * 4;
-    static constexpr int OFF_SLACK = OFF_F + AUX;
-    static constexpr int SLACK = MODE == IN ? 40960 : 0;
-    static constexpr int OFF_BAR = (OFF_SLACK + SLACK + 15) & ~15;
+    static constexpr int OFF_BAR = (OFF_F + AUX + 15) & ~15;
     static constexpr int NBAR = 2 * S + 2 * NACC;
     static constexpr int OFF_MISC = OFF_BAR + 8 * NBAR;               // tmem address, abort flag
     static constexpr int OFF_BIAS = OFF_MISC + 16;
@@ -627,6 +624,9 @@ cudaError_t launch_tc(const TcArgs& a, cudaStream_t s) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaError_t e = cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        if (e) return e;
+        // the whole unified L1 / shared memory as shared memory, so that the CTAs that fit are resident
+        e = cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e) return e;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<MODE>, S::NTHR, S::SMEM);
         resident = std::max(1, nsm * std::max(1, per));
