@@ -1,4 +1,5 @@
-"""A2 CMA acquisition, A3 frequency-offset estimate, A4 segmented DD-LMS, FP64.
+"""A2 CMA acquisition, A3 frequency-offset estimate, A4 segmented DD-LMS (linear
+and widely linear), FP64.
 
 TEST INFRASTRUCTURE (see the package docstring).
 
@@ -300,3 +301,40 @@ def dd_lms(xbuf, h_init, n_sym, L_b, seg_blocks, warmup_blocks, m, mu, off=0, di
     if diag is not None:
         diag["margin"] = margin
     return y, h_last
+
+
+# ----------------------------------------------------------------------------
+# Widely-linear segmented DD-LMS (Sec. IV-D: the paper's TD equaliser is
+# widely linear, after Silva et al., to undo transmitter IQ imbalance)
+# ----------------------------------------------------------------------------
+#
+# A widely-linear filter is a linear filter on the augmented input
+# [x_0, x_1, conj x_0, conj x_1]:
+#   y_q[n] = sum_p sum_k h_qp[k] x_p[2n + c - k] + g_qp[k] conj(x_p[2n + c - k]),
+# and its LMS update is the linear one on that input:
+#   h_qp[k] += mu   * sum_n e_q[n] conj(x_p[2n + c - k]),
+#   g_qp[k] += mu_c * sum_n e_q[n] x_p[2n + c - k].
+# Taps are [2 (q)][4][T]: [:, 0:2] multiply x_p, [:, 2:4] multiply conj(x_p).
+# Phase, decision, error and the segment schedule are the A4 ones above.
+
+def augment(xbuf: np.ndarray) -> np.ndarray:
+    """[x_0, x_1] -> [x_0, x_1, conj x_0, conj x_1]."""
+    return np.concatenate([xbuf, np.conj(xbuf)], axis=0)
+
+
+def wl_step(mu: float, mu_conj: float) -> np.ndarray:
+    """Step sizes of the four augmented inputs, shaped to broadcast over taps [..., q, 4, T]."""
+    return np.array([mu, mu, mu_conj, mu_conj], dtype=np.float64)[:, None]
+
+
+def wl_identity_taps(T: int) -> np.ndarray:
+    h = np.zeros((2, 4, T), dtype=np.complex128)
+    h[:, :2] = identity_taps(T)
+    return h
+
+
+def dd_lms_wl(xbuf, h_init, n_sym, L_b, seg_blocks, warmup_blocks, m, mu, mu_conj, off=0, diag=None):
+    """Widely-linear A4 on the segment schedule of ``dd_lms``. h_init: [2, 4, T].
+    Returns (y [2, n_sym], final taps [2, 4, T] of the last segment)."""
+    return dd_lms(augment(xbuf), h_init, n_sym, L_b, seg_blocks, warmup_blocks, m,
+                  wl_step(mu, mu_conj), off, diag)

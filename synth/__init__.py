@@ -16,6 +16,7 @@ from .channel import (  # noqa: F401
     quantise_int8,
     to_fp16,
     haar_unitary,
+    iq_coefficients,
     rrc_spectrum,
 )
 from .workloads import WORKLOADS, workload  # noqa: F401

@@ -8,6 +8,8 @@ symbols per polarisation, ``sps`` samples per symbol):
 2. root-raised-cosine pulse shaping, applied in the frequency domain over the
    whole frame (exact RRC spectrum, gain sqrt(sps) so that an RRC matched
    filter returns the symbols at the symbol instants);
+   optionally followed by a transmitter IQ imbalance x -> mu x + nu conj(x)
+   (``iq_imbalance``; see ``iq_coefficients``);
 3. chromatic dispersion of a fibre of length L, written with the group-velocity
    dispersion beta2 = -D * lambda^2 / (2 pi c):  H(w) = exp(j beta2/2 w^2 L);
 4. a Haar-random 2x2 unitary Jones matrix (QR of a complex Gaussian matrix with
@@ -51,6 +53,7 @@ class LinkParams:
     snr_db: float | None = 14.0      # Es/N0 per polarisation; None = noiseless
     jones: bool = True               # apply a Haar-random Jones matrix
     tx_rrc: bool = True              # RRC pulse shaping (False = rectangular spectrum)
+    iq_imbalance: tuple | None = None  # transmitter IQ imbalance (amplitude eps, phase skew rad), both pols
 
     @property
     def fs(self) -> float:
@@ -167,6 +170,14 @@ def haar_unitary(rng: np.random.Generator) -> np.ndarray:
     return q * (d / np.abs(d))[None, :]
 
 
+def iq_coefficients(eps: float, phi: float) -> tuple[complex, complex]:
+    """(mu, nu) of the transmitter IQ imbalance x -> mu x + nu conj(x) for I and Q branches
+    I' = (1 + eps)(I cos phi - Q sin phi), Q' = (1 - eps)(Q cos phi - I sin phi)."""
+    mu = np.cos(phi) + 1j * eps * np.sin(phi)
+    nu = eps * np.cos(phi) - 1j * np.sin(phi)
+    return complex(mu), complex(nu)
+
+
 def _streams(seed: int):
     ss = np.random.SeedSequence(seed)
     return [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(5)]
@@ -188,8 +199,17 @@ def generate(p: LinkParams, seed: int) -> Frame:
     f = np.fft.fftfreq(S, d=1.0 / p.fs)
     shape = np.sqrt(sps) * rrc_spectrum(f, p.symbol_rate, p.rolloff) if p.tx_rrc else \
         np.where(np.abs(f) <= p.symbol_rate / 2, np.sqrt(sps), 0.0)
-    X = np.fft.fft(x, axis=1) * (shape * fibre_dispersion(f, p))[None, :]
-    x = np.fft.ifft(X, axis=1)
+    extra = {}
+    if p.iq_imbalance is None:
+        X = np.fft.fft(x, axis=1) * (shape * fibre_dispersion(f, p))[None, :]
+        x = np.fft.ifft(X, axis=1)
+    else:
+        # the IQ modulator acts on the shaped drive signals, ahead of the fibre
+        x = np.fft.ifft(np.fft.fft(x, axis=1) * shape[None, :], axis=1)
+        mu, nu = iq_coefficients(*p.iq_imbalance)
+        x = mu * x + nu * np.conj(x)
+        x = np.fft.ifft(np.fft.fft(x, axis=1) * fibre_dispersion(f, p)[None, :], axis=1)
+        extra["iq"] = (mu, nu)
 
     J = haar_unitary(rng_jones) if p.jones else np.eye(2, dtype=np.complex128)
     x = J @ x
@@ -213,7 +233,7 @@ def generate(p: LinkParams, seed: int) -> Frame:
             x[pol] = x[pol] + np.sqrt(noise_var[pol] / 2.0) * n
 
     return Frame(params=p, seed=seed, samples=x, bits=bits, ref_words=pack_bits(bits),
-                 symbols=symbols, jones=J, phase=phase, noise_var=noise_var)
+                 symbols=symbols, jones=J, phase=phase, noise_var=noise_var, extra=extra)
 
 
 # ----------------------------------------------------------------------------

@@ -12,7 +12,7 @@ import oracle.bps as obps
 import oracle.cdc as ocdc
 import oracle.mimo as omimo
 import oracle.qam as oqam
-from tests import test_oracle_bps, test_oracle_cdc, test_oracle_mimo, test_oracle_qam
+from tests import test_oracle_bps, test_oracle_cdc, test_oracle_mimo, test_oracle_qam, test_oracle_wl
 
 
 def test_flipped_dispersion_sign_is_caught(monkeypatch):
@@ -67,3 +67,17 @@ def test_derotation_with_wrong_sign_is_caught(monkeypatch):
     monkeypatch.setattr(omimo, "derotate", lambda x, code, grid, fs, g0: real(x, -code, grid, fs, g0))
     with pytest.raises(AssertionError):
         test_oracle_mimo.test_large_offset_is_removed_on_noiseless_input()
+
+
+def test_widely_linear_without_the_conjugate_is_caught(monkeypatch):
+    monkeypatch.setattr(omimo, "augment", lambda x: np.concatenate([x, x], axis=0))
+    with pytest.raises(AssertionError):
+        test_oracle_wl.test_one_segment_by_explicit_loops(2)
+    with pytest.raises(AssertionError):
+        test_oracle_wl.test_converges_to_the_closed_form_inverse_of_a_tx_iq_imbalance()
+
+
+def test_widely_linear_step_on_the_wrong_taps_is_caught(monkeypatch):
+    monkeypatch.setattr(omimo, "wl_step", lambda mu, mu_c: np.array([mu_c, mu_c, mu, mu])[:, None])
+    with pytest.raises(AssertionError):
+        test_oracle_wl.test_one_segment_by_explicit_loops(4)
