@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
-    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch", "learned", "cnn"],
+    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch", "learned", "cnn", "wl"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
-                         "trained post-equaliser")
+                         "trained post-equaliser; cnn: the post-equaliser forward alone; wl: the "
+                         "widely-linear segmented DD-LMS alone on an IQ-imbalanced 16QAM frame")
     ap.add_argument("--launch-dbm", type=float, default=4.0, help="launch power of the learned workload")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
     ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
@@ -712,6 +713,75 @@ def cnn_arm(args) -> None:
         "error_word": err, "gpu_launches": 4 * args.steps, "clocks": clk.summary()}))
 
 
+def wl_arm(args) -> None:
+    """The widely-linear segmented DD-LMS alone (rx_dd_lms_wl: one launch, one CTA per segment and
+    output row) on a 16QAM 32 GBd frame of 2^20 symbols/pol (or --n-sym) with a transmitter IQ
+    imbalance (amplitude 0.10, phase skew 0.08 rad): 21 taps, blocks of 128 symbols, segments of
+    16 blocks with 4 warm-up blocks. A kernel measurement, not a bench line of the chain.
+    Algorithmic FP32 work per DP symbol: 2 rows x (4T complex MACs for the output + 4T for the
+    gradient) x 8 flops = 128 T, times 1 + warm-up/segment blocks."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300.receiver import dd_lms_wl
+    from synth import LinkParams, generate
+
+    N = args.n_sym or (1 << 20)
+    T, Lb, seg, wu, m, mu = 21, 128, 16, 4, 4, 1e-3
+    p = LinkParams(bits_per_sym=m, symbol_rate=32e9, n_sym=N, length=0.0, linewidth=0.0, freq_offset=0.0,
+                   snr_db=20.0, jones=False, tx_rrc=False, iq_imbalance=(0.10, 0.08))
+    fr = generate(p, SEED)
+    xs = fr.samples / np.sqrt(np.mean(np.abs(fr.samples[:, ::2]) ** 2, axis=1, keepdims=True))
+    x = torch.from_numpy(np.ascontiguousarray(xs.astype(np.complex64))).cuda()
+    h0 = torch.zeros((2, 4, T), dtype=torch.complex64, device="cuda")
+    h0[0, 0, T // 2] = 1.0
+    h0[1, 1, T // 2] = 1.0
+    y = torch.empty((2, N), dtype=torch.complex64, device="cuda")
+    ho = torch.empty_like(h0)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        dd_lms_wl(x, h0, N, Lb, seg, wu, m, mu, mu, y=y, taps_out=ho)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dd_lms_wl(x, h0, N, Lb, seg, wu, m, mu, mu, y=y, taps_out=ho)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    yc = y[:, 8192:].cpu().numpy()
+    psi = np.angle(-np.sum(yc ** 4, axis=-1, keepdims=True)) / 4
+    u = yc * np.exp(-1j * psi)
+    L = 1 << (m // 2)
+    a_l = 1.0 / np.sqrt(2.0 * (L * L - 1) / 3.0)
+    dec = lambda v: (np.clip(np.round((v / a_l + (L - 1)) / 2), 0, L - 1) * 2 - (L - 1)) * a_l
+    evm_db = 10 * np.log10(np.mean(np.abs(u - dec(u.real) - 1j * dec(u.imag)) ** 2))
+    pk = peaks()
+    lanes = SM_COUNT_GB300 * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    peak = 2 * lanes / 1e12
+    flops = N * (1 + wu / seg) * 128 * T
+    nseg = (N + seg * Lb - 1) // (seg * Lb)
+    achieved = flops / (t * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "widely-linear DD-LMS line rate", "value": 2 * m * N / (t * 1e-3) / 1e9, "unit": "Gb/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"wl-dd-lms-16qam-{N}", "symbols_per_pol": N, "taps": T, "block": Lb,
+                   "seg_blocks": seg, "warmup_blocks": wu, "l2": "flushed between timed steps (512 MiB write)"},
+        "roofline": {"kernel": "k_lms<256, widely linear>", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "algorithmic_flops": flops,
+                     "ctas": 2 * nseg,
+                     "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"},
+        "evm_db_after_8192_symbols": float(evm_db), "gpu_launches": args.steps, "clocks": clk.summary()}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -724,6 +794,8 @@ def main():
         learned_arm(args)
     elif args.workload == "cnn":
         cnn_arm(args)
+    elif args.workload == "wl":
+        wl_arm(args)
     else:
         our_arm(args)
 

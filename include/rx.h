@@ -315,6 +315,36 @@ void rx_pe_destroy(rx_pe* p);
 rx_status rx_carrier_recovery_static(const float* d_y, int64_t n_sym, int32_t bits_per_sym, int32_t bps_phases,
                                      int32_t bps_window, float* d_z, rx_stream_t stream);
 
+/*
+ * rx_dd_lms_wl: the widely-linear form of stage A4 alone. Sec. IV-D's TD
+ * equaliser is widely linear (it also undoes the transmitter's IQ
+ * imbalance): every output adds conjugate taps to the 2x2 butterfly,
+ *   y_q[n] = sum_p sum_k h_qp[k] x_p[2n + c - k] + g_qp[k] conj(x_p[2n + c - k]),
+ * c = (T-1)/2, x zero outside [0, x_len), and per block of block_len symbols
+ *   psi_q = arg(-sum_n y_q[n]^4) / 4,  d = dec(y e^{-j psi}),  e = d e^{j psi} - y,
+ *   h_qp[k] += mu * sum_n e_q[n] conj(x_p[2n + c - k]),
+ *   g_qp[k] += mu_conj * sum_n e_q[n] x_p[2n + c - k]
+ * (the linear update on the augmented input [x, conj x]; the outputs of a
+ * block use the taps it started with). Segment schedule as in rx_process:
+ * segments of seg_blocks blocks all start from d_taps_in; every segment but
+ * the first first runs warmup_blocks blocks on the symbols before it, whose
+ * outputs are discarded. mu_conj = 0 with zero conjugate taps is the linear
+ * DD-LMS.
+ *
+ * d_x: DEVICE float [2][x_len][2] (I, Q) input at 2 samples per symbol.
+ * d_taps_in: DEVICE float [2 (q)][4][T][2]: per output row h_q0, h_q1, g_q0,
+ * g_q1. d_y: DEVICE float [2][n_sym][2] outputs. d_taps_out: DEVICE, same
+ * layout as d_taps_in, receives the last segment's final taps (NULL: not
+ * written; must not overlap d_taps_in). All owned by the caller; nothing is
+ * allocated. n_taps odd 3..63, block_len 16..256, seg_blocks >= 1,
+ * warmup_blocks >= 0, bits_per_sym 2/4/6/8; RX_EINVAL otherwise, for
+ * n_sym < 1, x_len < 1 or more than 2^31 - 1 segments. Asynchronous on
+ * `stream`.
+ */
+rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const float* d_taps_in, int64_t n_sym,
+                       int32_t block_len, int32_t seg_blocks, int32_t warmup_blocks, int32_t bits_per_sym, float mu,
+                       float mu_conj, float* d_y, float* d_taps_out, rx_stream_t stream);
+
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);
 

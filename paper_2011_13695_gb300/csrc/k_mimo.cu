@@ -20,6 +20,12 @@
 // scheduling), the errors and the tap gradients (fixed-order partial sums),
 // then updates the row's taps in shared memory. All per-thread index
 // arithmetic is done once per kernel.
+//
+// The widely-linear form (WL = true; the paper's equaliser is widely linear,
+// Sec. IV-D) adds conjugate taps g_qp: y_q[n] += sum_p sum_k g_qp[k]
+// conj(x_p[2n + c - k]) and g_qp[k] += mu_c * sum_n e_q[n] x_p[2n + c - k].
+// A row's taps are then [h_q0, h_q1, g_q0, g_q1] (4T); the flattened term
+// index u = v 2T + p T + k (v = 1: conjugate) carries the same lane split.
 #include "rx_fft.cuh"
 #include "rx_kernels.h"
 
@@ -37,10 +43,11 @@ struct LmsCtx {
     float2* rot;     // e^{-j psi}
     float2* tab;     // NCO derotation of window offset jj: exp(-j 2 pi frac(inc jj)), jj < 2 Lb + T - 1
     int XS, G, logP, logR;
-    // output lanes: polarisation-0 taps [ka0, ka1), polarisation-1 taps [kb0, kb1)
-    int ka0, ka1, kb0, kb1;
-    // gradient thread: tap index (-1: idle), group, staging offset of its tap
-    int gt, gg, gx;
+    // output lanes: polarisation-0 taps [ka0, ka1), polarisation-1 taps [kb0, kb1); widely linear:
+    // conjugate taps of polarisation 0 [kc0, kc1) and of polarisation 1 [kd0, kd1)
+    int ka0, ka1, kb0, kb1, kc0, kc1, kd0, kd1;
+    // gradient thread: tap index (-1: idle), group, staging offset of its tap, conjugate tap
+    int gt, gg, gx, gconj;
     float2 pf[PF];
 };
 
@@ -85,11 +92,12 @@ __device__ __forceinline__ void lms_commit(const LmsArgs& a, LmsCtx<NT>& s, floa
 }
 
 // one block of row q: outputs, (DD) phase and errors, gradient, tap update
-template <int NT>
+template <int NT, bool WL>
 __device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const float2* __restrict__ xs,
                                           int64_t n0, int L, bool store, const Qam& qm, int q) {
     const int tid = threadIdx.x;
     const int T = a.T;
+    const int NTAP = (WL ? 4 : 2) * T;
     const int P = 1 << s.logP;
     {
         const int ostep = NT >> s.logP;
@@ -115,6 +123,23 @@ __device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const
                 acc1 = cmac(acc1, h1[k + 1], x1[-k - 1]);
             }
             if (k < b1) acc0 = cmac(acc0, h1[k], x1[-k]);
+            if constexpr (WL) {
+                const float2* g0 = s.taps + 2 * T;
+                const float2* g1 = s.taps + 3 * T;
+                const int c1 = valid ? s.kc1 : s.kc0, d1 = valid ? s.kd1 : s.kd0;
+                k = s.kc0;
+                for (; k + 1 < c1; k += 2) {
+                    acc0 = cmacc(acc0, g0[k], x0[-k]);
+                    acc1 = cmacc(acc1, g0[k + 1], x0[-k - 1]);
+                }
+                if (k < c1) acc0 = cmacc(acc0, g0[k], x0[-k]);
+                k = s.kd0;
+                for (; k + 1 < d1; k += 2) {
+                    acc0 = cmacc(acc0, g1[k], x1[-k]);
+                    acc1 = cmacc(acc1, g1[k + 1], x1[-k - 1]);
+                }
+                if (k < d1) acc0 = cmacc(acc0, g1[k], x1[-k]);
+            }
             float2 acc = cadd(acc0, acc1);
             for (int w = 1; w < P; w <<= 1) {
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, w);
@@ -154,12 +179,21 @@ __device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const
         float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
         const int G = s.G;
         int n = s.gg;
-        for (; n + G < L; n += 2 * G) {
-            acc0 = cmacc(acc0, s.es[n], xp[2 * n]);
-            acc1 = cmacc(acc1, s.es[n + G], xp[2 * (n + G)]);
+        if (WL && s.gconj) {
+            // conjugate tap: e x
+            for (; n + G < L; n += 2 * G) {
+                acc0 = cmac(acc0, s.es[n], xp[2 * n]);
+                acc1 = cmac(acc1, s.es[n + G], xp[2 * (n + G)]);
+            }
+            if (n < L) acc0 = cmac(acc0, s.es[n], xp[2 * n]);
+        } else {
+            for (; n + G < L; n += 2 * G) {
+                acc0 = cmacc(acc0, s.es[n], xp[2 * n]);
+                acc1 = cmacc(acc1, s.es[n + G], xp[2 * (n + G)]);
+            }
+            if (n < L) acc0 = cmacc(acc0, s.es[n], xp[2 * n]);
         }
-        if (n < L) acc0 = cmacc(acc0, s.es[n], xp[2 * n]);
-        s.part[s.gg * 2 * T + s.gt] = cadd(acc0, acc1);
+        s.part[s.gg * NTAP + s.gt] = cadd(acc0, acc1);
     }
     __syncthreads();
     {
@@ -167,63 +201,73 @@ __device__ __forceinline__ void lms_block(const LmsArgs& a, LmsCtx<NT>& s, const
         const int logR = s.logR, R = 1 << logR;
         const int t = tid >> logR, r = tid & (R - 1);
         float2 acc = make_float2(0.0f, 0.0f);
-        if (t < 2 * T) {
-            for (int g = r; g < s.G; g += R) acc = cadd(acc, s.part[g * 2 * T + t]);
+        if (t < NTAP) {
+            for (int g = r; g < s.G; g += R) acc = cadd(acc, s.part[g * NTAP + t]);
         }
         for (int w = 1; w < R; w <<= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, w);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, w);
         }
-        if (t < 2 * T && r == 0)
-            s.taps[t] = make_float2(fmaf(a.mu, acc.x, s.taps[t].x), fmaf(a.mu, acc.y, s.taps[t].y));
+        if (t < NTAP && r == 0) {
+            const float mu = (WL && t >= 2 * T) ? a.mu_c : a.mu;
+            s.taps[t] = make_float2(fmaf(mu, acc.x, s.taps[t].x), fmaf(mu, acc.y, s.taps[t].y));
+        }
     }
 }
 
-template <int NT>
+template <int NT, bool WL>
 __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
     extern __shared__ float2 smem[];
     if (a.run_if && *a.run_if == 0) return;
     const int T = a.T, Lb = a.Lb;
+    const int NTAP = (WL ? 4 : 2) * T;   // taps of one row
     const int q = blockIdx.y;
     const int tid = threadIdx.x;
     LmsCtx<NT> s;
     s.XS = 2 * Lb + T;
-    s.G = max(1, NT / (2 * T));
+    s.G = max(1, NT / NTAP);
     int logP = 0;
     while (logP < 4 && ((Lb << (logP + 1)) <= NT)) ++logP;
     s.logP = logP;
     int logR = 0;
-    while (logR < 3 && (1 << (logR + 1)) <= s.G && ((2 * T) << (logR + 1)) <= NT) ++logR;
+    while (logR < 3 && (1 << (logR + 1)) <= s.G && (NTAP << (logR + 1)) <= NT) ++logR;
     s.logR = logR;
     s.taps = smem;
-    s.xs0 = s.taps + 2 * T;
+    s.xs0 = s.taps + NTAP;
     s.xs1 = s.xs0 + 2 * s.XS;
     s.ys = s.xs1 + 2 * s.XS;
     s.es = s.ys + Lb;
     s.part = s.es + Lb;
-    s.rot = s.part + s.G * 2 * T;
+    s.rot = s.part + s.G * NTAP;
     s.tab = s.rot + 1;
     {
-        // output lane j of a group takes the flattened terms u in [j cs, (j + 1) cs), u = p T + k
+        // output lane j of a group takes the flattened terms u in [j cs, (j + 1) cs),
+        // u = v 2T + p T + k (v = 1: conjugate taps, widely linear only)
         const int P = 1 << logP, j = tid & (P - 1);
-        const int cs = (2 * T + P - 1) >> logP;
-        const int u0 = min(2 * T, j * cs), u1 = min(2 * T, u0 + cs);
+        const int cs = (NTAP + P - 1) >> logP;
+        const int u0 = min(NTAP, j * cs), u1 = min(NTAP, u0 + cs);
         s.ka0 = min(u0, T);
         s.ka1 = min(u1, T);
-        s.kb0 = max(u0, T) - T;
-        s.kb1 = max(u1, T) - T;
-        const int g = tid / (2 * T), t = tid - g * 2 * T;
+        s.kb0 = min(max(u0, T), 2 * T) - T;
+        s.kb1 = min(max(u1, T), 2 * T) - T;
+        s.kc0 = min(max(u0, 2 * T), 3 * T) - 2 * T;
+        s.kc1 = min(max(u1, 2 * T), 3 * T) - 2 * T;
+        s.kd0 = max(u0, 3 * T) - 3 * T;
+        s.kd1 = max(u1, 3 * T) - 3 * T;
+        const int g = tid / NTAP, t = tid - g * NTAP;
         s.gt = g < s.G ? t : -1;
         s.gg = g;
-        const int p = t >= T ? 1 : 0, k = t - p * T;
+        const int v = t >= 2 * T ? 1 : 0, t2 = t - v * 2 * T;
+        const int p = t2 >= T ? 1 : 0, k = t2 - p * T;
         s.gx = p * s.XS + T - 1 - k;
+        s.gconj = v;
     }
     const Qam qm = make_qam(a.m);
 
     const int64_t seg = blockIdx.x;
     const int64_t nseg = gridDim.x;
     const long long inc = a.derotate ? a.st->nco_inc : 0;
-    for (int t = tid; t < 2 * T; t += NT) s.taps[t] = a.taps_in[q * 2 * T + t];
+    for (int t = tid; t < NTAP; t += NT) s.taps[t] = a.taps_in[q * NTAP + t];
     if (inc)
         for (int jj = tid; jj < 2 * Lb + T - 1; jj += NT) s.tab[jj] = nco_conj(inc, jj);
     __syncthreads();
@@ -247,12 +291,12 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
         const int64_t n0 = blk_n0(b);
         const int L = blk_L(b);
         if (b + 1 < nblk) lms_prefetch(a, s, blk_n0(b + 1), blk_L(b + 1));
-        lms_block<NT>(a, s, (b & 1) ? s.xs1 : s.xs0, n0, L, b >= nwarm && a.y != nullptr, qm, q);
+        lms_block<NT, WL>(a, s, (b & 1) ? s.xs1 : s.xs0, n0, L, b >= nwarm && a.y != nullptr, qm, q);
         if (b + 1 < nblk) lms_commit(a, s, (b & 1) ? s.xs0 : s.xs1, blk_n0(b + 1), blk_L(b + 1), inc);
         __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out) {
-        for (int t = tid; t < 2 * T; t += NT) a.taps_out[q * 2 * T + t] = s.taps[t];
+        for (int t = tid; t < NTAP; t += NT) a.taps_out[q * NTAP + t] = s.taps[t];
     }
 }
 
@@ -525,10 +569,11 @@ __global__ void k_cma_rebuild(RxDevState* st, int T, const int* flag) {
 
 }  // namespace
 
-int64_t lms_smem_bytes(int T, int Lb, int threads) {
+int64_t lms_smem_bytes(int T, int Lb, int threads, bool wl) {
     const int XS = 2 * Lb + T;
-    const int G = threads / (2 * T) > 1 ? threads / (2 * T) : 1;
-    return (int64_t)sizeof(float2) * (2 * T + 4 * XS + 2 * Lb + G * 2 * T + 1 + (2 * Lb + T - 1));
+    const int NTAP = (wl ? 4 : 2) * T;
+    const int G = threads / NTAP > 1 ? threads / NTAP : 1;
+    return (int64_t)sizeof(float2) * (NTAP + 4 * XS + 2 * Lb + G * NTAP + 1 + (2 * Lb + T - 1));
 }
 
 size_t lms_launch_smem(size_t need, int exclusive) {
@@ -543,17 +588,17 @@ size_t lms_launch_smem(size_t need, int exclusive) {
     return need > optin ? need : optin;
 }
 
-template <int NT>
+template <int NT, bool WL = false>
 static cudaError_t launch_lms_t(const LmsArgs& a, cudaStream_t s) {
     const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
     if (nseg <= 0) return cudaSuccess;
-    const size_t smem = lms_launch_smem((size_t)lms_smem_bytes(a.T, a.Lb, NT), a.exclusive);
+    const size_t smem = lms_launch_smem((size_t)lms_smem_bytes(a.T, a.Lb, NT, WL), a.exclusive);
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
-        cudaFuncSetAttribute(k_lms<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_lms<NT, WL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_lms<NT><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
+    k_lms<NT, WL><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -571,6 +616,17 @@ cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
         case 512: return launch_lms_t<512>(a, s);
         case 1024: return launch_lms_t<1024>(a, s);
         default: return launch_lms_t<256>(a, s);
+    }
+}
+
+// widely-linear segmented DD-LMS: always this file's generic kernel (threads >= 4T)
+cudaError_t launch_lms_wl(const LmsArgs& a, int threads, cudaStream_t s) {
+    if (threads < 4 * a.T) return cudaErrorInvalidValue;
+    switch (threads) {
+        case 256: return launch_lms_t<256, true>(a, s);
+        case 512: return launch_lms_t<512, true>(a, s);
+        case 1024: return launch_lms_t<1024, true>(a, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

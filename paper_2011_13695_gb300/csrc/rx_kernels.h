@@ -43,6 +43,7 @@ struct LmsArgs {
     RxDevState* st;
     int exclusive;         // 1: each CTA asks for a whole SM's shared memory, so that no other kernel's
                            // CTA shares its SM (the serial acquisition is latency-bound)
+    float mu_c;            // widely-linear form only: step of the conjugate taps
 };
 
 // shared memory a launch asks for: the kernel's need, or with `exclusive` the most a CTA may have
@@ -59,7 +60,10 @@ cudaError_t launch_fill_filter(float2* H, int nfft, double fs, double dl_lambda2
                                cudaStream_t s);
 
 cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s);
-int64_t lms_smem_bytes(int T, int Lb, int threads);
+int64_t lms_smem_bytes(int T, int Lb, int threads, bool wl = false);
+// widely-linear form of the generic segmented kernel: taps_in/taps_out are [2][4][T] (h_q0, h_q1,
+// g_q0, g_q1 per row), mu_c the conjugate taps' step; threads 256/512/1024 and >= 4T
+cudaError_t launch_lms_wl(const LmsArgs& a, int threads, cudaStream_t s);
 
 cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
                               int64_t nw, const float2* taps, float2* yw, cudaStream_t s);

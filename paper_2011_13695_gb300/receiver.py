@@ -87,3 +87,27 @@ class Receiver:
         """Carrier-recovered symbols z of the last single frame, complex64 [2, n_sym]."""
         z = self.buffer(rx.RX_BUF_Z).view(2, -1)
         return z[:, :n_sym].contiguous()
+
+
+def dd_lms_wl(x: torch.Tensor, taps: torch.Tensor, n_sym: int, block_len: int, seg_blocks: int, warmup_blocks: int,
+              bits_per_sym: int, mu: float, mu_conj: float, y: torch.Tensor | None = None,
+              taps_out: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """Widely-linear segmented DD-LMS (rx_dd_lms_wl) on device tensors: x complex64 [2, x_len] at
+    2 samples/symbol, taps complex64 [2, 4, T] (h_q0, h_q1, g_q0, g_q1 per output row). Returns y
+    complex64 [2, n_sym]; ``taps_out`` (complex64 [2, 4, T]) receives the last segment's final taps."""
+    for t in (x, taps) + ((y,) if y is not None else ()) + ((taps_out,) if taps_out is not None else ()):
+        if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("dd_lms_wl takes contiguous complex64 CUDA tensors")
+    if x.dim() != 2 or x.shape[0] != 2 or taps.dim() != 3 or tuple(taps.shape[:2]) != (2, 4):
+        raise ValueError("x must be [2, x_len] and taps [2, 4, T]")
+    if y is None:
+        y = torch.empty((2, n_sym), dtype=torch.complex64, device=x.device)
+    elif tuple(y.shape) != (2, n_sym):
+        raise ValueError("y must be [2, n_sym]")
+    if taps_out is not None and taps_out.shape != taps.shape:
+        raise ValueError("taps_out must have the shape of taps")
+    s = stream or torch.cuda.current_stream()
+    rx.rx_dd_lms_wl(x.data_ptr(), x.shape[1], taps.shape[2], taps.data_ptr(), n_sym, block_len, seg_blocks,
+                    warmup_blocks, bits_per_sym, mu, mu_conj, y.data_ptr(),
+                    taps_out.data_ptr() if taps_out is not None else None, s.cuda_stream)
+    return y

@@ -28,7 +28,7 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
            "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
-           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy")
+           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl")
 RX_STATIC_MAX_SYMBOLS = 262144
 
 
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
             "rx_pe_gradients": (i32, [vp, vp, vp, i64, vp, vp, vp]),
             "rx_pe_train_step": (i32, [vp, vp, vp, i64, C.c_float, vp, vp]),
             "rx_pe_destroy": (None, [vp]),
+            "rx_dd_lms_wl": (i32, [vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -318,3 +319,11 @@ def rx_carrier_recovery_static(d_y: int, n_sym: int, bits_per_sym: int, bps_phas
     """Carrier recovery with the library's fixed device scratch (no allocation); see include/rx.h."""
     _check(lib().rx_carrier_recovery_static(d_y, n_sym, bits_per_sym, bps_phases, bps_window, d_z, stream or None),
            "rx_carrier_recovery_static")
+
+
+def rx_dd_lms_wl(d_x: int, x_len: int, n_taps: int, d_taps_in: int, n_sym: int, block_len: int, seg_blocks: int,
+                 warmup_blocks: int, bits_per_sym: int, mu: float, mu_conj: float, d_y: int, d_taps_out: int | None,
+                 stream: int | None) -> None:
+    """Widely-linear segmented DD-LMS on caller-owned device buffers; see include/rx.h."""
+    _check(lib().rx_dd_lms_wl(d_x, x_len, n_taps, d_taps_in, n_sym, block_len, seg_blocks, warmup_blocks,
+                              bits_per_sym, mu, mu_conj, d_y, d_taps_out or None, stream or None), "rx_dd_lms_wl")

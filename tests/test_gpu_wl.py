@@ -1,0 +1,162 @@
+"""GPU parity of the widely-linear segmented DD-LMS (rx_dd_lms_wl through the C ABI) against the
+FP64 oracle (``oracle.mimo.dd_lms_wl``) on the same seeded inputs.
+
+Inputs: dual-polarisation square QAM with a transmitter IQ imbalance (amplitude 0.10, phase
+skew 0.08 rad on both polarisations), Nyquist (sinc) pulses at 2 samples/symbol so that the
+symbol-instant samples carry no ISI, no fibre, identity Jones matrix, AWGN. The taps the
+segments start from are the oracle's, converged serially on the first part of the frame (an
+input to both sides).
+
+Tolerances, as for the linear A4 stage: outputs within 1e-4 relative RMS per (segment, row),
+final taps within 1e-4; a (segment, row) whose oracle decisions came within 1e-5 of a decision
+boundary may follow another valid trajectory (agreement to 1e-2 there; rare).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mimo, qam
+from synth import LinkParams, generate
+from tests.gpu_util import rel_rms
+
+pytestmark = pytest.mark.gpu
+
+NEAR_TIE = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2011_13695_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    build.build()
+
+
+class IqFrame:
+    def __init__(self, fr, samples):
+        self.frame, self.samples = fr, samples
+
+
+def iq_frame(m: int, n_sym: int, seed: int, snr_db: float) -> IqFrame:
+    """The frame, with each polarisation scaled to unit mean power at the symbol instants (the
+    sinc pulses at 2 samples/symbol carry the symbols at 1/sqrt(2) of their amplitude)."""
+    p = LinkParams(bits_per_sym=m, symbol_rate=32e9, n_sym=n_sym, length=0.0, linewidth=0.0, freq_offset=0.0,
+                   snr_db=snr_db, jones=False, tx_rrc=False, iq_imbalance=(0.10, 0.08))
+    fr = generate(p, seed)
+    x = fr.samples / np.sqrt(np.mean(np.abs(fr.samples[:, ::2]) ** 2, axis=1, keepdims=True))
+    return IqFrame(fr, x)
+
+
+def start_taps(x: np.ndarray, T: int, m: int, L_b: int, mu: float, n_train: int) -> np.ndarray:
+    """The oracle's serial widely-linear DD-LMS on the first n_train symbols, from identity taps."""
+    _, h = mimo.dd_lms_wl(x, mimo.wl_identity_taps(T), n_train, L_b, 10 ** 9, 0, m, mu, mu)
+    return h
+
+
+def run_gpu(x, h0, n_sym, L_b, seg, wu, m, mu, mu_c):
+    import torch
+    from paper_2011_13695_gb300.receiver import dd_lms_wl
+    xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    hd = torch.from_numpy(np.ascontiguousarray(h0.astype(np.complex64))).cuda()
+    ho = torch.empty_like(hd)
+    y = dd_lms_wl(xd, hd, n_sym, L_b, seg, wu, m, mu, mu_c, taps_out=ho)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.complex128), ho.cpu().numpy().astype(np.complex128)
+
+
+def compare(y_g, h_g, y_o, h_o, margin, L_seg):
+    N = y_o.shape[1]
+    diverged = []
+    for si, s0 in enumerate(range(0, N, L_seg)):
+        for q in range(2):
+            e = rel_rms(y_g[q, s0:s0 + L_seg], y_o[q, s0:s0 + L_seg])
+            if e >= 1e-4:
+                assert margin[si, q] < NEAR_TIE and e < 1e-2, (si, q, e, margin[si, q])
+                diverged.append((si, q))
+    n_pairs = 2 * math.ceil(N / L_seg)
+    assert len(diverged) <= max(1, 0.02 * n_pairs), diverged
+    last = math.ceil(N / L_seg) - 1
+    if not any(si == last for si, _ in diverged):
+        assert rel_rms(h_g, h_o) < 1e-4, rel_rms(h_g, h_o)
+    return diverged
+
+
+# (m, T, L_b, seg_blocks, warmup_blocks, n_sym): several segments with a ragged last one, frames
+# shorter than one block and one segment, the smallest and largest tap counts and block lengths
+CASES = [
+    (4, 21, 64, 16, 4, 16 * 64 * 6 + 37),
+    (4, 21, 128, 16, 4, 1),
+    (4, 21, 128, 16, 4, 100),
+    (2, 3, 16, 8, 2, 16 * 8 * 5 + 15),
+    (2, 63, 256, 4, 1, 256 * 4 * 3 + 255),
+    (6, 15, 32, 16, 0, 32 * 16 * 4),
+]
+
+
+@pytest.mark.parametrize("m,T,L_b,seg,wu,n_sym", CASES)
+def test_matches_oracle(m, T, L_b, seg, wu, n_sym):
+    snr = {2: 14.0, 4: 20.0, 6: 26.0}[m]
+    fr = iq_frame(m, max(n_sym, 4096) + 64, seed=100 + T + m, snr_db=snr)
+    x = fr.samples
+    mu = {2: 2e-3, 4: 1e-3, 6: 5e-4}[m]
+    h0 = start_taps(x, T, m, L_b, mu, 4096)
+    diag = {}
+    y_o, h_o = mimo.dd_lms_wl(x, h0, n_sym, L_b, seg, wu, m, mu, 0.7 * mu, diag=diag)
+    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, mu, 0.7 * mu)
+    compare(y_g, h_g, y_o, h_o, diag["margin"], seg * L_b)
+
+
+def test_frozen_conjugate_taps_give_the_linear_stage():
+    """mu_conj = 0 from zero conjugate taps: the kernel's outputs equal the oracle's linear A4 DD-LMS."""
+    m, T, L_b, seg, wu, n_sym = 4, 21, 64, 16, 4, 16 * 64 * 3 + 5
+    fr = iq_frame(m, n_sym + 64, seed=7, snr_db=20.0)
+    x = fr.samples
+    h_lin = mimo.identity_taps(T)
+    h0 = np.zeros((2, 4, T), dtype=np.complex128)
+    h0[:, :2] = h_lin
+    diag = {}
+    y_o, h_o = mimo.dd_lms(x, h_lin, n_sym, L_b, seg, wu, m, 1e-3, diag=diag)
+    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, 1e-3, 0.0)
+    assert not np.any(h_g[:, 2:])
+    compare(y_g, h_g[:, :2], y_o, h_o, diag["margin"], seg * L_b)
+
+
+def test_full_size_frame():
+    """The 16QAM 32 GBd frame size (2^20 symbols per polarisation, 21 taps, blocks of 128,
+    16-block segments with 4 warm-up blocks): every segment against the oracle."""
+    m, T, L_b, seg, wu, n_sym = 4, 21, 128, 16, 4, 1 << 20
+    fr = iq_frame(m, n_sym, seed=11, snr_db=20.0)
+    x = fr.samples
+    h0 = start_taps(x, T, m, L_b, 1e-3, 8192)
+    diag = {}
+    y_o, h_o = mimo.dd_lms_wl(x, h0, n_sym, L_b, seg, wu, m, 1e-3, 1e-3, diag=diag)
+    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, 1e-3, 1e-3)
+    compare(y_g, h_g, y_o, h_o, diag["margin"], seg * L_b)
+
+
+def test_conjugate_taps_remove_the_image():
+    """On the IQ-imbalanced 16QAM frame the widely-linear kernel's decisions beat the linear
+    kernel's (mu_conj = 0): the image term the linear filter leaves costs several dB of EVM."""
+    m, T, L_b, seg, wu, n_sym = 4, 21, 128, 16, 4, 1 << 17
+    fr = iq_frame(m, n_sym, seed=12, snr_db=24.0)
+    x = fr.samples
+
+    def evm_db(mu_c):
+        if mu_c:
+            h0 = start_taps(x, T, m, L_b, 1e-3, 8192)
+        else:
+            # the linear filter starts from the linear DD-LMS's own converged taps
+            h0 = np.zeros((2, 4, T), dtype=np.complex128)
+            _, h0[:, :2] = mimo.dd_lms(x, mimo.identity_taps(T), 8192, L_b, 10 ** 9, 0, m, 1e-3)
+        y, _ = run_gpu(x, h0, n_sym, L_b, seg, wu, m, 1e-3, mu_c)
+        y = y[:, 4096:]
+        psi = np.angle(-np.sum(y ** 4, axis=-1, keepdims=True)) / 4
+        u = y * np.exp(-1j * psi)
+        return 10 * np.log10(np.mean(np.abs(u - qam.decide(u, m)) ** 2))
+
+    wl, lin = evm_db(1e-3), evm_db(0.0)
+    print(f"EVM widely linear {wl:.2f} dB, linear {lin:.2f} dB")
+    assert wl < lin - 3.0, (wl, lin)
