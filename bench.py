@@ -148,6 +148,11 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # a timed region of a few milliseconds falls between two 100 ms samples: take the first
+            # sample before it starts and (on exit) one after it ends, so the record brackets it
+            t0 = time.time()
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 3.0:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
         return self
@@ -158,6 +163,9 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            n, t0 = len(self.lines), time.time()
+            while len(self.lines) == n and self.proc.poll() is None and time.time() - t0 < 0.5:
+                time.sleep(0.005)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -775,11 +783,49 @@ def wl_arm(args) -> None:
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"wl-dd-lms-16qam-{N}", "symbols_per_pol": N, "taps": T, "block": Lb,
                    "seg_blocks": seg, "warmup_blocks": wu, "l2": "flushed between timed steps (512 MiB write)"},
-        "roofline": {"kernel": "k_lms<256, widely linear>", "bound": "alu", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_lms_fast<128, 21, 128, widely linear>", "bound": "alu", "achieved": achieved,
+                     "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "algorithmic_flops": flops,
                      "ctas": 2 * nseg,
                      "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"},
-        "evm_db_after_8192_symbols": float(evm_db), "gpu_launches": args.steps, "clocks": clk.summary()}))
+        "evm_db_after_8192_symbols": float(evm_db), "gpu_launches": args.steps, "clocks": clk.summary(),
+        "cpu_baseline": None if args.no_cpu_baseline else wl_cpu_baseline()}))
+
+
+WL_CPU_SAMPLE = 1 << 20
+
+
+def wl_oracle_worker(n_sym: int, reps: int) -> dict:
+    """The oracle's widely-linear segmented DD-LMS on the first n_sym symbols of the wl frame."""
+    import numpy as np
+
+    from oracle import mimo
+    from synth import LinkParams, generate
+    p = LinkParams(bits_per_sym=4, symbol_rate=32e9, n_sym=n_sym, length=0.0, linewidth=0.0, freq_offset=0.0,
+                   snr_db=20.0, jones=False, tx_rrc=False, iq_imbalance=(0.10, 0.08))
+    fr = generate(p, SEED)
+    x = fr.samples / np.sqrt(np.mean(np.abs(fr.samples[:, ::2]) ** 2, axis=1, keepdims=True))
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        mimo.dd_lms_wl(x, mimo.wl_identity_taps(21), n_sym, 128, 16, 4, 4, 1e-3, 1e-3)
+        times.append(time.perf_counter() - t0)
+    return dict(times=times, bits=2 * 4 * n_sym)
+
+
+def wl_cpu_baseline(reps: int = 3) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.wl_oracle_worker(%d, %d)))" % (ROOT, WL_CPU_SAMPLE, reps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode:
+        raise RuntimeError(r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    t = statistics.median(res["times"])
+    return {"value": res["bits"] / t / 1e9, "unit": "Gb/s", "cores": 1, "kind": "oracle",
+            "sample": f"the wl frame, {WL_CPU_SAMPLE} symbols/pol, widely-linear segmented "
+                      f"DD-LMS in FP64 NumPy, single thread, median of {reps}"}
 
 
 def main():

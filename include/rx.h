@@ -336,14 +336,18 @@ rx_status rx_carrier_recovery_static(const float* d_y, int64_t n_sym, int32_t bi
  * g_q1. d_y: DEVICE float [2][n_sym][2] outputs. d_taps_out: DEVICE, same
  * layout as d_taps_in, receives the last segment's final taps (NULL: not
  * written; must not overlap d_taps_in). All owned by the caller; nothing is
- * allocated. n_taps odd 3..63, block_len 16..256, seg_blocks >= 1,
- * warmup_blocks >= 0, bits_per_sym 2/4/6/8; RX_EINVAL otherwise, for
- * n_sym < 1, x_len < 1 or more than 2^31 - 1 segments. Asynchronous on
- * `stream`.
+ * allocated. threads: CTA size. 0 lets the library choose (128 for the
+ * compiled shapes, n_taps 15/21/31 with block_len 128, at most 256 blocks
+ * per segment including warm-up; 256 otherwise); 128 or 256 run a compiled
+ * shape; any other shape runs the generic kernel with 256, 512 or 1024
+ * threads, at least 4 * n_taps. n_taps odd 3..63, block_len 16..256,
+ * seg_blocks >= 1, warmup_blocks >= 0, bits_per_sym 2/4/6/8; RX_EINVAL
+ * otherwise, for n_sym < 1, x_len < 1, a thread count the shape cannot use
+ * or more than 2^31 - 1 segments. Asynchronous on `stream`.
  */
 rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const float* d_taps_in, int64_t n_sym,
                        int32_t block_len, int32_t seg_blocks, int32_t warmup_blocks, int32_t bits_per_sym, float mu,
-                       float mu_conj, float* d_y, float* d_taps_out, rx_stream_t stream);
+                       float mu_conj, float* d_y, float* d_taps_out, int32_t threads, rx_stream_t stream);
 
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);

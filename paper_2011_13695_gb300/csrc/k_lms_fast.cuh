@@ -21,12 +21,18 @@
 //     is processed, and derotated with a per-kernel offset table as it is
 //     written to shared memory; the whole range a CTA reads is requested into
 //     L2 when it starts.
+// The widely-linear form (WL; Sec. IV-D) adds conjugate taps g_p: the output
+// gains sum_p sum_k g_p[k] conj(x_p[2n + c - k]) and g_p[k] += mu_c sum_n e[n]
+// x_p[2n + c - k]. Every sample a lane loads then feeds both its direct and
+// its conjugate product, and each gradient thread accumulates both sums of its
+// tap (p, k) from the same loads. Taps per row: [h_0, h_1, g_0, g_1].
 #pragma once
 
 #include "rx_kernels.h"
 
-template <int NT, int T, int LB>
+template <int NT, int T, int LB, bool WL = false>
 struct LmsFastShape {
+    static constexpr int NV = WL ? 2 : 1;                  // tap sets: direct (and conjugate)
     static constexpr int C = (T - 1) / 2;
     static constexpr int XW = 2 * LB + T - 1;             // window samples per polarisation
     static constexpr int XS = 2 * LB + T + 1;             // natural staging stride per polarisation (even)
@@ -43,39 +49,43 @@ struct LmsFastShape {
     static constexpr int PF = (2 * XW + NT - 1) / NT;      // window registers per thread
     static constexpr int NWARP = NT / 32;
     static constexpr int NBT = 256;                        // derotation bases of the first NBT blocks
-    static constexpr int SMEM = 4 * RP + 2 * T + 2 * (2 * XS + 4 * XE) + LB + G * 2 * T + NWARP + XW + NBT;   // float2
+    static constexpr int SMEM =
+        NV * (4 * RP + 2 * T) + 2 * (2 * XS + 4 * XE) + LB + G * NV * 2 * T + NWARP + XW + NBT;   // float2
     static_assert(NT % LB == 0 && (P & (P - 1)) == 0 && P <= 32, "NT must be a power-of-two multiple of LB");
     static_assert(G >= 1, "at least 2T threads");
     static_assert(T % 2 == 1, "odd tap count: window index parity follows the tap index");
 };
 
-template <int NT, int T, int LB>
+template <int NT, int T, int LB, bool WL = false>
 __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
-    using S = LmsFastShape<NT, T, LB>;
+    using S = LmsFastShape<NT, T, LB, WL>;
+    constexpr int NV = S::NV;
+    constexpr int NTAP = NV * 2 * T;                       // taps of one row
     extern __shared__ float4 smem4[];                      // 16-byte aligned
     float2* smem = reinterpret_cast<float2*>(smem4);
     if (a.run_if && *a.run_if == 0) return;
-    float2* tps = smem;                                    // [p][parity][RP]: taps split by parity (16-B rows)
-    float2* taps = tps + 4 * S::RP;                        // [p][k]
+    float2* tps = smem;                                    // [v][p][parity][RP]: taps split by parity (16-B rows)
+    float2* taps = tps + NV * 4 * S::RP;                   // [v][p][k]
     constexpr int WBUF = 2 * S::XS + 4 * S::XE;            // one window: natural [2][XS], split [2][2 XE]
-    float2* xsb = taps + 2 * T;                            // two windows
+    float2* xsb = taps + NTAP;                             // two windows
     float2* es = xsb + 2 * WBUF;                           // [LB]
-    float2* part = es + LB;                                // [G][2T]
-    float2* ypart = part + S::G * 2 * T;                   // [NWARP]
+    float2* part = es + LB;                                // [G][NTAP]
+    float2* ypart = part + S::G * NTAP;                    // [NWARP]
     float2* tab = ypart + S::NWARP;                        // [XW]
     float2* btab = tab + S::XW;                            // [NBT]: derotation base of block b's window
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
     const long long inc = a.derotate ? a.st->nco_inc : 0;
-    auto tps_at = [&](int t) -> float2* {                  // split position of tap t = (p, k)
-        const int p = t >= T ? 1 : 0, k = t - p * T;
-        return tps + (2 * p + (k & 1)) * S::RP + (k >> 1);
+    auto tps_at = [&](int t) -> float2* {                  // split position of tap t = (v, p, k)
+        const int v = t >= 2 * T ? 1 : 0, t2 = t - v * 2 * T;
+        const int p = t2 >= T ? 1 : 0, k = t2 - p * T;
+        return tps + v * 4 * S::RP + (2 * p + (k & 1)) * S::RP + (k >> 1);
     };
-    for (int t = tid; t < 4 * S::RP; t += NT) tps[t] = make_float2(0.0f, 0.0f);
+    for (int t = tid; t < NV * 4 * S::RP; t += NT) tps[t] = make_float2(0.0f, 0.0f);
     __syncthreads();
-    for (int t = tid; t < 2 * T; t += NT) {
-        const float2 h = a.taps_in[q * 2 * T + t];
+    for (int t = tid; t < NTAP; t += NT) {
+        const float2 h = a.taps_in[q * NTAP + t];
         taps[t] = h;
         *tps_at(t) = h;
     }
@@ -215,6 +225,25 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                         a1 = cmac(a1, hv[i], xv[C + 1 - i]);
                     }
                 }
+                if constexpr (WL) {
+                    const float4* GE4 = TE4 + 4 * S::RP / 2;    // conjugate taps: 4 RP float2 further
+#pragma unroll
+                    for (int u = 0; u < S::RP / 2; ++u) {
+                        const float4 v = GE4[u];
+                        hv[2 * u] = make_float2(v.x, v.y);
+                        hv[2 * u + 1] = make_float2(v.z, v.w);
+                    }
+#pragma unroll
+                    for (int i = 0; i <= C; ++i) {
+                        if (i & 1) {
+                            b0 = cmacc(b0, hv[i], xv[C - i]);
+                            b1 = cmacc(b1, hv[i], xv[C + 1 - i]);
+                        } else {
+                            a0 = cmacc(a0, hv[i], xv[C - i]);
+                            a1 = cmacc(a1, hv[i], xv[C + 1 - i]);
+                        }
+                    }
+                }
             }
             if (S::Q == 2 || opar == 1) {
                 float2 xv[2 * NO], hv[2 * NO];
@@ -240,6 +269,25 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                         a1 = cmac(a1, hv[i], xv[C - i]);
                     }
                 }
+                if constexpr (WL) {
+                    const float4* GO4 = TO4 + 4 * S::RP / 2;
+#pragma unroll
+                    for (int u = 0; u < S::RP / 2; ++u) {
+                        const float4 v = GO4[u];
+                        hv[2 * u] = make_float2(v.x, v.y);
+                        hv[2 * u + 1] = make_float2(v.z, v.w);
+                    }
+#pragma unroll
+                    for (int i = 0; i < C; ++i) {
+                        if (i & 1) {
+                            b0 = cmacc(b0, hv[i], xv[C - 1 - i]);
+                            b1 = cmacc(b1, hv[i], xv[C - i]);
+                        } else {
+                            a0 = cmacc(a0, hv[i], xv[C - 1 - i]);
+                            a1 = cmacc(a1, hv[i], xv[C - i]);
+                        }
+                    }
+                }
             }
             y0 = cadd(a0, b0);
             y1 = cadd(a1, b1);
@@ -262,6 +310,10 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                         const float2 xv = (k & 1) ? bo[-((k + 1) >> 1)] : be[-(k >> 1)];
                         if (k & 1) acc1 = cmac(acc1, taps[p * T + k], xv);
                         else acc0 = cmac(acc0, taps[p * T + k], xv);
+                        if constexpr (WL) {
+                            if (k & 1) acc1 = cmacc(acc1, taps[2 * T + p * T + k], xv);
+                            else acc0 = cmacc(acc0, taps[2 * T + p * T + k], xv);
+                        }
                     }
                 }
             } else {
@@ -274,6 +326,10 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                         const float2 xv = (i & 1) ? bo[-((i + 1) >> 1)] : be[-(i >> 1)];
                         if (i & 1) acc1 = cmac(acc1, hp[i], xv);
                         else acc0 = cmac(acc0, hp[i], xv);
+                        if constexpr (WL) {
+                            if (i & 1) acc1 = cmacc(acc1, hp[2 * T + i], xv);
+                            else acc0 = cmacc(acc0, hp[2 * T + i], xv);
+                        }
                     }
                 }
             }
@@ -323,6 +379,7 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
         if (grad_on) {
             const float2* xg = xs + goff;
             float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+            float2 cc0 = make_float2(0.0f, 0.0f), cc1 = make_float2(0.0f, 0.0f);   // conjugate taps: e x
 #pragma unroll
             for (int i = 0; i < S::NG; ++i) {
                 if (gg + S::G * i < L) {
@@ -330,25 +387,39 @@ __global__ void __launch_bounds__(NT) k_lms_fast(LmsArgs a) {
                     const float2 xv = xg[2 * S::G * i];
                     if (i & 1) acc1 = cmacc(acc1, e, xv);
                     else acc0 = cmacc(acc0, e, xv);
+                    if constexpr (WL) {
+                        if (i & 1) cc1 = cmac(cc1, e, xv);
+                        else cc0 = cmac(cc0, e, xv);
+                    }
                 }
             }
-            part[gg * 2 * T + gt] = cadd(acc0, acc1);
+            part[gg * NTAP + gt] = cadd(acc0, acc1);
+            if constexpr (WL) part[gg * NTAP + 2 * T + gt] = cadd(cc0, cc1);
         }
         __syncthreads();
         if (tid < 2 * T) {
             float2 g = part[tid];
 #pragma unroll
-            for (int k = 1; k < S::G; ++k) g = cadd(g, part[k * 2 * T + tid]);
+            for (int k = 1; k < S::G; ++k) g = cadd(g, part[k * NTAP + tid]);
             const float2 h = taps[tid];
             const float2 hn = make_float2(fmaf(a.mu, g.x, h.x), fmaf(a.mu, g.y, h.y));
             taps[tid] = hn;
             *tps_at(tid) = hn;
+            if constexpr (WL) {
+                float2 gc = part[2 * T + tid];
+#pragma unroll
+                for (int k = 1; k < S::G; ++k) gc = cadd(gc, part[k * NTAP + 2 * T + tid]);
+                const float2 hc = taps[2 * T + tid];
+                const float2 hcn = make_float2(fmaf(a.mu_c, gc.x, hc.x), fmaf(a.mu_c, gc.y, hc.y));
+                taps[2 * T + tid] = hcn;
+                *tps_at(2 * T + tid) = hcn;
+            }
         }
         if (b + 1 < nblk) commit(xsb + ((b + 1) & 1) * WBUF, b + 1);
         __syncthreads();
     }
     if (seg == nseg - 1 && a.taps_out)
-        for (int t = tid; t < 2 * T; t += NT) a.taps_out[q * 2 * T + t] = taps[t];
+        for (int t = tid; t < NTAP; t += NT) a.taps_out[q * NTAP + t] = taps[t];
 }
 
 // the compile-time kernel keeps one derotation base per block of a CTA: at most NBT blocks
@@ -357,17 +428,17 @@ inline bool lms_fast_fits(const LmsArgs& a) {
     return (a.L_seg + LB - 1) / LB + a.n_wu <= 256;
 }
 
-template <int NT, int T, int LB>
+template <int NT, int T, int LB, bool WL = false>
 cudaError_t launch_lms_fast_t(const LmsArgs& a, cudaStream_t s) {
-    using S = LmsFastShape<NT, T, LB>;
+    using S = LmsFastShape<NT, T, LB, WL>;
     const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
     if (nseg <= 0) return cudaSuccess;
     const size_t smem = lms_launch_smem(sizeof(float2) * S::SMEM, a.exclusive);
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
-        cudaFuncSetAttribute(k_lms_fast<NT, T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_lms_fast<NT, T, LB, WL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_lms_fast<NT, T, LB><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
+    k_lms_fast<NT, T, LB, WL><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
     return cudaGetLastError();
 }

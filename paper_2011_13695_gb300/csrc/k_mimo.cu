@@ -619,8 +619,14 @@ cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
     }
 }
 
-// widely-linear segmented DD-LMS: always this file's generic kernel (threads >= 4T)
+bool lms_fast_wl(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
+
+// widely-linear segmented DD-LMS: the compile-time shapes (k_lms_fast_wl.cu) first, this file's generic
+// kernel otherwise (threads >= 4T); threads 0 takes 128 for the compile-time shapes, else 256
 cudaError_t launch_lms_wl(const LmsArgs& a, int threads, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    if (lms_fast_wl(a, threads ? threads : 128, s, &err)) return err;
+    if (!threads) threads = 256;
     if (threads < 4 * a.T) return cudaErrorInvalidValue;
     switch (threads) {
         case 256: return launch_lms_t<256, true>(a, s);

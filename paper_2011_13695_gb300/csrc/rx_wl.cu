@@ -1,9 +1,10 @@
 // Widely-linear segmented DD-LMS (Sec. IV-D) as a stand-alone stage on caller-owned buffers.
 //
 // The paper's TD equaliser is widely linear so that it also compensates the
-// transmitter's IQ imbalance. The kernel is the generic segmented block LMS
-// of k_mimo.cu instantiated with conjugate taps: one CTA per (segment, output
-// row), the same fixed segment schedule and warm-up as the linear A4 stage,
+// transmitter's IQ imbalance. The kernels are the segmented block LMS ones
+// (compile-time shapes in k_lms_fast.cuh, the generic one in k_mimo.cu)
+// instantiated with conjugate taps: one CTA per (segment, output row), the
+// same fixed segment schedule and warm-up as the linear A4 stage,
 // the input read straight from the caller's buffer (no frequency-offset
 // derotation: the caller hands in the samples the equaliser sees).
 #include <cuda_runtime.h>
@@ -16,7 +17,8 @@
 extern "C" rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const float* d_taps_in,
                                   int64_t n_sym, int32_t block_len, int32_t seg_blocks, int32_t warmup_blocks,
                                   int32_t bits_per_sym, float mu, float mu_conj, float* d_y, float* d_taps_out,
-                                  rx_stream_t stream) {
+                                  int32_t threads, rx_stream_t stream) {
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512 && threads != 1024) return RX_EINVAL;
     if (!d_x || !d_taps_in || !d_y || n_sym < 1 || x_len < 1) return RX_EINVAL;
     if (n_taps < 3 || n_taps > 63 || !(n_taps & 1)) return RX_EINVAL;
     if (block_len < 16 || block_len > 256 || seg_blocks < 1 || warmup_blocks < 0) return RX_EINVAL;
@@ -53,6 +55,8 @@ extern "C" rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_tap
     a.run_if = nullptr;
     a.st = nullptr;
     a.exclusive = 0;
-    if (launch_lms_wl(a, 256, (cudaStream_t)stream) != cudaSuccess) return RX_ECUDA;
-    return RX_OK;
+    const cudaError_t e = launch_lms_wl(a, threads, (cudaStream_t)stream);
+    // invalid value: a thread count the shape cannot use, refused before any launch
+    if (e == cudaErrorInvalidValue) return RX_EINVAL;
+    return e == cudaSuccess ? RX_OK : RX_ECUDA;
 }

@@ -91,7 +91,8 @@ class Receiver:
 
 def dd_lms_wl(x: torch.Tensor, taps: torch.Tensor, n_sym: int, block_len: int, seg_blocks: int, warmup_blocks: int,
               bits_per_sym: int, mu: float, mu_conj: float, y: torch.Tensor | None = None,
-              taps_out: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+              taps_out: torch.Tensor | None = None, threads: int = 0,
+              stream: torch.cuda.Stream | None = None) -> torch.Tensor:
     """Widely-linear segmented DD-LMS (rx_dd_lms_wl) on device tensors: x complex64 [2, x_len] at
     2 samples/symbol, taps complex64 [2, 4, T] (h_q0, h_q1, g_q0, g_q1 per output row). Returns y
     complex64 [2, n_sym]; ``taps_out`` (complex64 [2, 4, T]) receives the last segment's final taps."""
@@ -109,5 +110,5 @@ def dd_lms_wl(x: torch.Tensor, taps: torch.Tensor, n_sym: int, block_len: int, s
     s = stream or torch.cuda.current_stream()
     rx.rx_dd_lms_wl(x.data_ptr(), x.shape[1], taps.shape[2], taps.data_ptr(), n_sym, block_len, seg_blocks,
                     warmup_blocks, bits_per_sym, mu, mu_conj, y.data_ptr(),
-                    taps_out.data_ptr() if taps_out is not None else None, s.cuda_stream)
+                    taps_out.data_ptr() if taps_out is not None else None, threads, s.cuda_stream)
     return y

@@ -111,7 +111,8 @@ def lib() -> C.CDLL:
             "rx_pe_gradients": (i32, [vp, vp, vp, i64, vp, vp, vp]),
             "rx_pe_train_step": (i32, [vp, vp, vp, i64, C.c_float, vp, vp]),
             "rx_pe_destroy": (None, [vp]),
-            "rx_dd_lms_wl": (i32, [vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, vp]),
+            "rx_dd_lms_wl": (i32, [vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, i32,
+                                   vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -323,7 +324,8 @@ def rx_carrier_recovery_static(d_y: int, n_sym: int, bits_per_sym: int, bps_phas
 
 def rx_dd_lms_wl(d_x: int, x_len: int, n_taps: int, d_taps_in: int, n_sym: int, block_len: int, seg_blocks: int,
                  warmup_blocks: int, bits_per_sym: int, mu: float, mu_conj: float, d_y: int, d_taps_out: int | None,
-                 stream: int | None) -> None:
+                 threads: int, stream: int | None) -> None:
     """Widely-linear segmented DD-LMS on caller-owned device buffers; see include/rx.h."""
     _check(lib().rx_dd_lms_wl(d_x, x_len, n_taps, d_taps_in, n_sym, block_len, seg_blocks, warmup_blocks,
-                              bits_per_sym, mu, mu_conj, d_y, d_taps_out or None, stream or None), "rx_dd_lms_wl")
+                              bits_per_sym, mu, mu_conj, d_y, d_taps_out or None, threads, stream or None),
+           "rx_dd_lms_wl")

@@ -69,12 +69,15 @@ def test_widely_linear_stage_rejects_bad_arguments_before_any_device_call(librx)
     from paper_2011_13695_gb300 import rx
     fake = 1 << 20          # never dereferenced: every case fails validation first
     base = dict(d_x=fake, x_len=4096, n_taps=21, d_taps_in=fake, n_sym=2048, block_len=64, seg_blocks=16,
-                warmup_blocks=4, bits_per_sym=4, mu=1e-3, mu_conj=1e-3, d_y=fake, d_taps_out=None, stream=None)
+                warmup_blocks=4, bits_per_sym=4, mu=1e-3, mu_conj=1e-3, d_y=fake, d_taps_out=None, threads=0,
+                stream=None)
     taps_bytes = 2 * 4 * 21 * 8
     bad = [dict(d_x=0), dict(d_y=0), dict(d_taps_in=0), dict(n_sym=0), dict(x_len=0), dict(n_taps=20),
            dict(n_taps=65), dict(n_taps=1), dict(block_len=8), dict(block_len=512), dict(seg_blocks=0),
            dict(warmup_blocks=-1), dict(bits_per_sym=3), dict(d_taps_out=fake + taps_bytes - 8),
-           dict(d_taps_out=fake - taps_bytes + 8), dict(n_sym=1 << 40, seg_blocks=1, block_len=16)]
+           dict(d_taps_out=fake - taps_bytes + 8), dict(n_sym=1 << 40, seg_blocks=1, block_len=16),
+           dict(threads=64), dict(threads=300), dict(threads=128, n_taps=23), dict(threads=256, n_taps=65),
+           dict(threads=128, seg_blocks=300)]
     for b in bad:
         with pytest.raises(rx.RxError) as e:
             rx.rx_dd_lms_wl(**dict(base, **b))

@@ -56,13 +56,13 @@ def start_taps(x: np.ndarray, T: int, m: int, L_b: int, mu: float, n_train: int)
     return h
 
 
-def run_gpu(x, h0, n_sym, L_b, seg, wu, m, mu, mu_c):
+def run_gpu(x, h0, n_sym, L_b, seg, wu, m, mu, mu_c, threads=0):
     import torch
     from paper_2011_13695_gb300.receiver import dd_lms_wl
     xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
     hd = torch.from_numpy(np.ascontiguousarray(h0.astype(np.complex64))).cuda()
     ho = torch.empty_like(hd)
-    y = dd_lms_wl(xd, hd, n_sym, L_b, seg, wu, m, mu, mu_c, taps_out=ho)
+    y = dd_lms_wl(xd, hd, n_sym, L_b, seg, wu, m, mu, mu_c, taps_out=ho, threads=threads)
     torch.cuda.synchronize()
     return y.cpu().numpy().astype(np.complex128), ho.cpu().numpy().astype(np.complex128)
 
@@ -84,20 +84,27 @@ def compare(y_g, h_g, y_o, h_o, margin, L_seg):
     return diverged
 
 
-# (m, T, L_b, seg_blocks, warmup_blocks, n_sym): several segments with a ragged last one, frames
-# shorter than one block and one segment, the smallest and largest tap counts and block lengths
+# (m, T, L_b, seg_blocks, warmup_blocks, n_sym, threads): several segments with a ragged last one,
+# frames shorter than one block and one segment, the smallest and largest tap counts and block
+# lengths; the compiled shapes (T 15/21/31, blocks of 128) with 128 threads (one lane per output)
+# and 256 (four lanes per output pair), and the generic kernel (other shapes, or 512 threads)
 CASES = [
-    (4, 21, 64, 16, 4, 16 * 64 * 6 + 37),
-    (4, 21, 128, 16, 4, 1),
-    (4, 21, 128, 16, 4, 100),
-    (2, 3, 16, 8, 2, 16 * 8 * 5 + 15),
-    (2, 63, 256, 4, 1, 256 * 4 * 3 + 255),
-    (6, 15, 32, 16, 0, 32 * 16 * 4),
+    (4, 21, 64, 16, 4, 16 * 64 * 6 + 37, 0),
+    (4, 21, 128, 16, 4, 1, 0),
+    (4, 21, 128, 16, 4, 100, 256),
+    (4, 21, 128, 16, 4, 16 * 128 * 5 + 77, 128),
+    (4, 21, 128, 16, 4, 16 * 128 * 5 + 77, 256),
+    (4, 21, 128, 16, 4, 16 * 128 * 5 + 77, 512),
+    (2, 15, 128, 8, 2, 8 * 128 * 4 + 5, 256),
+    (2, 31, 128, 4, 1, 4 * 128 * 6 + 127, 128),
+    (2, 3, 16, 8, 2, 16 * 8 * 5 + 15, 0),
+    (2, 63, 256, 4, 1, 256 * 4 * 3 + 255, 0),
+    (6, 15, 32, 16, 0, 32 * 16 * 4, 0),
 ]
 
 
-@pytest.mark.parametrize("m,T,L_b,seg,wu,n_sym", CASES)
-def test_matches_oracle(m, T, L_b, seg, wu, n_sym):
+@pytest.mark.parametrize("m,T,L_b,seg,wu,n_sym,threads", CASES)
+def test_matches_oracle(m, T, L_b, seg, wu, n_sym, threads):
     snr = {2: 14.0, 4: 20.0, 6: 26.0}[m]
     fr = iq_frame(m, max(n_sym, 4096) + 64, seed=100 + T + m, snr_db=snr)
     x = fr.samples
@@ -105,7 +112,7 @@ def test_matches_oracle(m, T, L_b, seg, wu, n_sym):
     h0 = start_taps(x, T, m, L_b, mu, 4096)
     diag = {}
     y_o, h_o = mimo.dd_lms_wl(x, h0, n_sym, L_b, seg, wu, m, mu, 0.7 * mu, diag=diag)
-    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, mu, 0.7 * mu)
+    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, mu, 0.7 * mu, threads)
     compare(y_g, h_g, y_o, h_o, diag["margin"], seg * L_b)
 
 
@@ -124,16 +131,18 @@ def test_frozen_conjugate_taps_give_the_linear_stage():
     compare(y_g, h_g[:, :2], y_o, h_o, diag["margin"], seg * L_b)
 
 
-def test_full_size_frame():
+@pytest.mark.parametrize("threads", [0, 256])
+def test_full_size_frame(threads):
     """The 16QAM 32 GBd frame size (2^20 symbols per polarisation, 21 taps, blocks of 128,
-    16-block segments with 4 warm-up blocks): every segment against the oracle."""
+    16-block segments with 4 warm-up blocks; the launch the bench times, and the four-lane form):
+    every segment against the oracle."""
     m, T, L_b, seg, wu, n_sym = 4, 21, 128, 16, 4, 1 << 20
     fr = iq_frame(m, n_sym, seed=11, snr_db=20.0)
     x = fr.samples
     h0 = start_taps(x, T, m, L_b, 1e-3, 8192)
     diag = {}
     y_o, h_o = mimo.dd_lms_wl(x, h0, n_sym, L_b, seg, wu, m, 1e-3, 1e-3, diag=diag)
-    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, 1e-3, 1e-3)
+    y_g, h_g = run_gpu(x, h0, n_sym, L_b, seg, wu, m, 1e-3, 1e-3, threads)
     compare(y_g, h_g, y_o, h_o, diag["margin"], seg * L_b)
 
 
