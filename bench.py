@@ -200,7 +200,8 @@ class ClockSampler:
 # DRAM traffic per launch from one ncu capture (profiles/), valid while the kernel's source file is
 # unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
 PROFILED_TRAFFIC = {
-    "dd_acq": ("k_lms_fast.cuh", "69f50b49384b4b79ea9d309a0e8eac02cc5bec2b", 561664),   # DRAM bytes read + written, one ncu capture of this launch
+    "dd_acq": ("k_lms_fast.cuh", "fca5f277b4ecd771cc2e0b0acdff6c7ea8cf98cc", 561664),   # DRAM bytes read + written, one ncu capture of this launch
+    "wl": ("k_lms_fast.cuh", "fca5f277b4ecd771cc2e0b0acdff6c7ea8cf98cc", 33638912),
 }
 
 
@@ -785,8 +786,8 @@ def wl_arm(args) -> None:
                    "seg_blocks": seg, "warmup_blocks": wu, "l2": "flushed between timed steps (512 MiB write)"},
         "roofline": {"kernel": "k_lms_fast<128, 21, 128, widely linear>", "bound": "alu", "achieved": achieved,
                      "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "algorithmic_flops": flops,
-                     "ctas": 2 * nseg,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic("wl") if N == 1 << 20 else None,
+                     "algorithmic_flops": flops, "ctas": 2 * nseg,
                      "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"},
         "evm_db_after_8192_symbols": float(evm_db), "gpu_launches": args.steps, "clocks": clk.summary(),
         "cpu_baseline": None if args.no_cpu_baseline else wl_cpu_baseline()}))
