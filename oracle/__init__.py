@@ -17,6 +17,12 @@ chain applies them, with no blocking, fusion or reordering:
   A5 ``bps.blind_phase_search``     BPS, integer unwrap, derotation
   A6 ``decide.resolve`` / ``count`` ambiguity resolution, Gray demap, BER/EVM
 
+Beyond the chain: ``mimo.dd_lms_wl`` (the widely-linear A4, conjugate taps
+for transmitter IQ imbalance) and ``kk.kk_receive`` (the Kramers-Kronig
+self-coherent front end: square root and log, overlap-save Hilbert
+transform, field reconstruction and downshift, matched filter and
+decimation to 2 samples/symbol).
+
 ``receiver.receive`` runs the chain end to end; ``theory`` holds closed forms
 (exact Gray square-QAM BER over AWGN, Q <-> BER).
 

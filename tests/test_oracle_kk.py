@@ -1,0 +1,139 @@
+"""Pins for the oracle's Kramers-Kronig front end (Sec. IV, Steps 1-8).
+
+* the front end's amplitude and log-amplitude, value by value;
+* the overlap-save Hilbert transform is exact on tones of the block grid (the
+  Hilbert transform of cos is sin) and approximates the full-length transform
+  (scipy.signal.hilbert) of a band-limited sequence, closer for longer blocks;
+* KK reconstruction is exact for a field exp(g) with g analytic (a
+  minimum-phase field whose log-amplitude and phase are a Hilbert pair on the
+  block grid), and on a synthetic QAM link it recovers the known field, more
+  closely as the carrier-to-signal power ratio rises;
+* the matched-filter decimation returns every other sample of on-grid tones
+  scaled by the filter's amplitude (2 RRC) at their frequencies;
+* end to end, the symbols of a noiseless 16QAM KK link come back error-free.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kk, qam
+from oracle.cdc import rrc_amplitude
+from synth.kk import KKLink, generate_kk
+
+
+def test_front_end_values():
+    codes = np.array([0, 1, 17, 2048, 4095], dtype=np.uint16)
+    scale, dc, i_min = 0.01, -0.1, 1e-6
+    a, l = kk.front_end(codes, scale, dc, i_min)
+    for c, av, lv in zip(codes, a, l):
+        I = max(scale * float(c) + dc, i_min)
+        assert abs(av - math.sqrt(I)) <= 1e-15 * math.sqrt(I)
+        assert abs(lv - 0.5 * math.log(I)) <= 1e-14
+
+
+def _interior(S, N):
+    """Samples kept by blocks whose input window lies inside the frame."""
+    hop, lead = N // 2, N // 4
+    lo = hop                                  # block 1 is the first with start >= 0
+    hi = ((S - (N - lead)) // hop) * hop + hop   # last block with start + N <= S keeps [j hop, j hop + hop)
+    return slice(lo, min(hi, S))
+
+
+def test_hilbert_is_exact_on_grid_tones():
+    N, S = 1024, 8 * 1024
+    rng = np.random.default_rng(1)
+    n = np.arange(S)
+    l = np.full(S, 0.7)
+    ref = np.zeros(S)
+    for k in rng.integers(1, N // 2, size=6):
+        c, th = rng.uniform(0.1, 1.0), rng.uniform(0, 2 * np.pi)
+        l += c * np.cos(2 * np.pi * k * n / N + th)
+        ref += c * np.sin(2 * np.pi * k * n / N + th)
+    phi = kk.hilbert_os(l, N)
+    sl = _interior(S, N)
+    # FP64 rounding of the tone phases (arguments up to 2.5e4 rad) is about 3e-12
+    assert np.max(np.abs(phi[sl] - ref[sl])) < 1e-10
+
+
+def test_hilbert_approximates_the_full_transform():
+    signal = pytest.importorskip("scipy.signal")
+    fr = generate_kk(KKLink(n_sym=1 << 14, cspr_db=12.0), 1)
+    _, l = kk.front_end(fr.intensity, 1.0, 0.0, 1e-12)
+    ref = np.imag(signal.hilbert(l))
+    errs = []
+    for N in (1024, 4096):
+        phi = kk.hilbert_os(l, N)
+        sl = slice(N, l.size - N)
+        errs.append(np.linalg.norm(phi[sl] - ref[sl]) / np.linalg.norm(ref[sl] - ref[sl].mean()))
+    assert errs[0] < 5e-3 and errs[1] < 0.5 * errs[0], errs
+
+
+@pytest.mark.parametrize("tone", [0.0, 0.13675])
+def test_kk_is_exact_for_an_analytic_log_field(tone):
+    """h = exp(g), g = sum c_i exp(j (2 pi k_i n / N + th_i)) with 0 < k_i < N/2: ln|h| = Re g and
+    arg h = Im g = H{Re g}, so |h|^2 alone gives h back (times the downshift)."""
+    N, S = 1024, 6 * 1024
+    rng = np.random.default_rng(2)
+    n = np.arange(S)
+    g = np.full(S, 0.3 + 0j)
+    for k in rng.integers(1, N // 2, size=5):
+        g += rng.uniform(0.05, 0.3) * np.exp(1j * (2 * np.pi * k * n / N + rng.uniform(0, 2 * np.pi)))
+    h = np.exp(g)
+    a, l = kk.front_end(np.abs(h) ** 2, 1.0, 0.0, 1e-300)
+    E = kk.reconstruct(a, kk.hilbert_os(l, N), tone)
+    sl = _interior(S, N)
+    ref = h * np.exp(-2j * np.pi * tone * n)
+    assert np.max(np.abs(E[sl] - ref[sl])) < 1e-10 * np.max(np.abs(h))
+
+
+def _field_error_db(cspr_db, N=1024):
+    p = KKLink(n_sym=1 << 13, cspr_db=cspr_db)
+    fr = generate_kk(p, 2)
+    E, _ = kk.kk_receive(fr.codes, fr.scale, fr.dc, 1e-9, p.tone_offset / p.fs, p.rolloff, N)
+    n = np.arange(E.size)
+    ref = fr.field * np.exp(-2j * np.pi * p.tone_offset / p.fs * n)
+    sl = slice(N, E.size - N)
+    return 10 * np.log10(np.sum(np.abs(E[sl] - ref[sl]) ** 2) / np.sum(np.abs(fr.signal[sl]) ** 2))
+
+
+def test_kk_recovers_the_field_better_at_higher_cspr():
+    errs = [_field_error_db(c) for c in (8.0, 11.0, 14.0, 18.0)]
+    assert errs[0] < -30.0, errs
+    assert all(b < a - 2.0 for a, b in zip(errs, errs[1:])), errs
+
+
+def test_matched_decimation_of_grid_tones():
+    """Tones on the block grid, inside and inside the roll-off of the matched filter, at positive and
+    negative frequencies: y[m] = sum_i c_i 2 RRC(f_i) exp(j 2 pi f_i 2m) (the filter's gain is
+    sqrt(4) = 2, so that with the transmitter's RRC of gain 2 the symbols come back at unit scale)."""
+    N, S, rolloff = 1024, 8 * 1024, 0.25
+    n = np.arange(S)
+    m = np.arange(S // 2)
+    rng = np.random.default_rng(3)
+    E = np.zeros(S, dtype=np.complex128)
+    ref = np.zeros(S // 2, dtype=np.complex128)
+    for k in (3, 40, 100, 140, 150, N - 7, N - 120, N - 145):
+        f = (k if k < N // 2 else k - N) / N
+        c = rng.normal() + 1j * rng.normal()
+        E += c * np.exp(2j * np.pi * f * n)
+        ref += c * 2.0 * rrc_amplitude(np.array([f]), 0.25, rolloff)[0] * np.exp(2j * np.pi * f * 2 * m)
+    y = kk.matched_decimate(E, N, rolloff)
+    sl = _interior(S, N)
+    sl2 = slice(sl.start // 2, sl.stop // 2)
+    assert np.max(np.abs(y[sl2] - ref[sl2])) < 1e-10
+    # a tone beyond fs/4 is removed
+    y2 = kk.matched_decimate(np.exp(2j * np.pi * 300 / N * n), N, rolloff)
+    assert np.max(np.abs(y2[sl2])) < 1e-10
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_noiseless_link_end_to_end(m):
+    p = KKLink(bits_per_sym=m, n_sym=1 << 13, cspr_db=6.0 if m == 2 else 11.0)
+    fr = generate_kk(p, 4)
+    _, y = kk.kk_receive(fr.codes, fr.scale, fr.dc, 1e-9, p.tone_offset / p.fs, p.rolloff, 1024)
+    ys, s = y[::2][256:-256], fr.symbols[256:-256]
+    evm_db = 10 * np.log10(np.mean(np.abs(ys - s) ** 2))
+    assert evm_db < -30.0, evm_db
+    assert np.array_equal(qam.decide(ys, m), qam.decide(s, m))

@@ -10,9 +10,10 @@ import pytest
 
 import oracle.bps as obps
 import oracle.cdc as ocdc
+import oracle.kk as okk
 import oracle.mimo as omimo
 import oracle.qam as oqam
-from tests import test_oracle_bps, test_oracle_cdc, test_oracle_mimo, test_oracle_qam, test_oracle_wl
+from tests import test_oracle_bps, test_oracle_cdc, test_oracle_kk, test_oracle_mimo, test_oracle_qam, test_oracle_wl
 
 
 def test_flipped_dispersion_sign_is_caught(monkeypatch):
@@ -81,3 +82,30 @@ def test_widely_linear_step_on_the_wrong_taps_is_caught(monkeypatch):
     monkeypatch.setattr(omimo, "wl_step", lambda mu, mu_c: np.array([mu_c, mu_c, mu, mu])[:, None])
     with pytest.raises(AssertionError):
         test_oracle_wl.test_one_segment_by_explicit_loops(4)
+
+
+def test_kk_hilbert_sign_flipped_is_caught(monkeypatch):
+    real = okk.hilbert_sign
+    monkeypatch.setattr(okk, "hilbert_sign", lambda N: -real(N))
+    with pytest.raises(AssertionError):
+        test_oracle_kk.test_kk_is_exact_for_an_analytic_log_field(0.0)
+
+
+def test_kk_log_of_intensity_instead_of_amplitude_is_caught(monkeypatch):
+    real = okk.front_end
+    monkeypatch.setattr(okk, "front_end", lambda *a: (real(*a)[0], 2.0 * real(*a)[1]))
+    with pytest.raises(AssertionError):
+        test_oracle_kk.test_kk_is_exact_for_an_analytic_log_field(0.0)
+
+
+def test_kk_missing_downshift_is_caught(monkeypatch):
+    real = okk.reconstruct
+    monkeypatch.setattr(okk, "reconstruct", lambda a, phi, tone: real(a, phi, 0.0))
+    with pytest.raises(AssertionError):
+        test_oracle_kk.test_kk_is_exact_for_an_analytic_log_field(0.13675)
+
+
+def test_kk_wrong_decimation_bins_are_caught(monkeypatch):
+    monkeypatch.setattr(okk, "decimation_bins", lambda N: np.arange(N // 2))
+    with pytest.raises(AssertionError):
+        test_oracle_kk.test_matched_decimation_of_grid_tones()
