@@ -46,16 +46,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
-    ap.add_argument("--workload", default="frame", choices=["frame", "stream", "batch", "learned", "cnn", "wl"],
+    ap.add_argument("--workload", default="frame",
+                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser; cnn: the post-equaliser forward alone; wl: the "
-                         "widely-linear segmented DD-LMS alone on an IQ-imbalanced 16QAM frame")
+                         "widely-linear segmented DD-LMS alone on an IQ-imbalanced 16QAM frame; kk: the "
+                         "Kramers-Kronig front end on a 2^22-sample 12-bit buffer")
     ap.add_argument("--launch-dbm", type=float, default=4.0, help="launch power of the learned workload")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
     ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
     ap.add_argument("--lr", type=float, default=7e-4, help="initial Adam learning rate of the learned workload")
     ap.add_argument("--fmt", default="i8", choices=["i8", "f16"], help="input format of the stream workload")
+    ap.add_argument("--wl-taps", type=int, default=21, help="tap count of the wl workload")
+    ap.add_argument("--wl-threads", type=int, default=0,
+                    help="CTA size of the wl workload (0: library choice; 512 runs the generic kernel)")
     return ap.parse_args()
 
 
@@ -738,7 +743,8 @@ def wl_arm(args) -> None:
     from synth import LinkParams, generate
 
     N = args.n_sym or (1 << 20)
-    T, Lb, seg, wu, m, mu = 21, 128, 16, 4, 4, 1e-3
+    T, Lb, seg, wu, m, mu = args.wl_taps, 128, 16, 4, 4, 1e-3
+    th = args.wl_threads
     p = LinkParams(bits_per_sym=m, symbol_rate=32e9, n_sym=N, length=0.0, linewidth=0.0, freq_offset=0.0,
                    snr_db=20.0, jones=False, tx_rrc=False, iq_imbalance=(0.10, 0.08))
     fr = generate(p, SEED)
@@ -751,7 +757,7 @@ def wl_arm(args) -> None:
     ho = torch.empty_like(h0)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        dd_lms_wl(x, h0, N, Lb, seg, wu, m, mu, mu, y=y, taps_out=ho)
+        dd_lms_wl(x, h0, N, Lb, seg, wu, m, mu, mu, y=y, taps_out=ho, threads=th)
     torch.cuda.synchronize()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ms = []
@@ -760,7 +766,7 @@ def wl_arm(args) -> None:
             flush.fill_(i & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dd_lms_wl(x, h0, N, Lb, seg, wu, m, mu, mu, y=y, taps_out=ho)
+            dd_lms_wl(x, h0, N, Lb, seg, wu, m, mu, mu, y=y, taps_out=ho, threads=th)
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
@@ -782,21 +788,27 @@ def wl_arm(args) -> None:
         "metric": "widely-linear DD-LMS line rate", "value": 2 * m * N / (t * 1e-3) / 1e9, "unit": "Gb/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"wl-dd-lms-16qam-{N}", "symbols_per_pol": N, "taps": T, "block": Lb,
+        "config": {"workload": f"wl-dd-lms-16qam-{N}", "symbols_per_pol": N, "taps": T, "block": Lb, "threads": th,
                    "seg_blocks": seg, "warmup_blocks": wu, "l2": "flushed between timed steps (512 MiB write)"},
-        "roofline": {"kernel": "k_lms_fast<128, 21, 128, widely linear>", "bound": "alu", "achieved": achieved,
-                     "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic("wl") if N == 1 << 20 else None,
+        "roofline": {"kernel": wl_kernel_name(T, Lb, th), "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic("wl") if (N, T, th) == (1 << 20, 21, 0) else None,
                      "algorithmic_flops": flops, "ctas": 2 * nseg,
                      "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"},
         "evm_db_after_8192_symbols": float(evm_db), "gpu_launches": args.steps, "clocks": clk.summary(),
-        "cpu_baseline": None if args.no_cpu_baseline else wl_cpu_baseline()}))
+        "cpu_baseline": None if args.no_cpu_baseline else wl_cpu_baseline(T)}))
+
+
+def wl_kernel_name(T: int, Lb: int, threads: int) -> str:
+    """The kernel rx_dd_lms_wl launches for this shape (compiled shapes: T 15/21/31, blocks of 128)."""
+    if T in (15, 21, 31) and Lb == 128 and threads in (0, 128, 256):
+        return f"k_lms_fast<{threads or 128}, {T}, {Lb}, widely linear>"
+    return f"k_lms<{threads or 256}, widely linear> (generic)"
 
 
 WL_CPU_SAMPLE = 1 << 20
 
 
-def wl_oracle_worker(n_sym: int, reps: int) -> dict:
+def wl_oracle_worker(n_sym: int, reps: int, T: int = 21) -> dict:
     """The oracle's widely-linear segmented DD-LMS on the first n_sym symbols of the wl frame."""
     import numpy as np
 
@@ -809,24 +821,123 @@ def wl_oracle_worker(n_sym: int, reps: int) -> dict:
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        mimo.dd_lms_wl(x, mimo.wl_identity_taps(21), n_sym, 128, 16, 4, 4, 1e-3, 1e-3)
+        mimo.dd_lms_wl(x, mimo.wl_identity_taps(T), n_sym, 128, 16, 4, 4, 1e-3, 1e-3)
         times.append(time.perf_counter() - t0)
     return dict(times=times, bits=2 * 4 * n_sym)
 
 
-def wl_cpu_baseline(reps: int = 3) -> dict:
+def wl_cpu_baseline(T: int = 21, reps: int = 3) -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.wl_oracle_worker(%d, %d)))" % (ROOT, WL_CPU_SAMPLE, reps))
+            "print(json.dumps(bench.wl_oracle_worker(%d, %d, %d)))" % (ROOT, WL_CPU_SAMPLE, reps, T))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode:
         raise RuntimeError(r.stderr[-2000:])
     res = json.loads(r.stdout.strip().splitlines()[-1])
     t = statistics.median(res["times"])
     return {"value": res["bits"] / t / 1e9, "unit": "Gb/s", "cores": 1, "kind": "oracle",
-            "sample": f"the wl frame, {WL_CPU_SAMPLE} symbols/pol, widely-linear segmented "
+            "sample": f"the wl frame, {WL_CPU_SAMPLE} symbols/pol, {T} taps, widely-linear segmented "
                       f"DD-LMS in FP64 NumPy, single thread, median of {reps}"}
+
+
+def kk_arm(args) -> None:
+    """The Kramers-Kronig front end alone (rx_kk_process: k_kk_phase + k_kk_mf, N = 1024) on the paper's
+    buffer of 2^22 12-bit samples (or --n-sym symbols x 4): 16QAM at 1 GBd, 4 samples/symbol, 1 %
+    roll-off, tone 0.547 GHz below the signal, 11 dB CSPR, 20 dB SNR. A kernel measurement, not a bench
+    line of the chain. Algorithmic HBM bytes per input sample: 2 (code) + 8 (field out) in the first
+    pass, 8 (field in) + 4 (half an output sample) in the second; FP32 FFT work 5 N log2 N per
+    N-point transform: 2 transforms of N per N/2 samples in the first pass, one of N and one of N/2 in
+    the second."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300.receiver import KKFrontEnd
+    from synth.kk import KKLink, generate_kk
+
+    n_sym = args.n_sym or (1 << 20)
+    N = 1024
+    p = KKLink(bits_per_sym=4, n_sym=n_sym, cspr_db=11.0, snr_db=20.0)
+    fr = generate_kk(p, SEED)
+    S = 4 * n_sym
+    fe = KKFrontEnd(N, p.tone_offset / p.fs, p.rolloff, fr.scale, fr.dc, 1e-6)
+    codes = torch.from_numpy(fr.codes.view(np.int16)).cuda()
+    field = torch.empty(S, dtype=torch.complex64, device="cuda")
+    out = torch.empty(S // 2, dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fe.process(codes, field, out)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fe.process(codes, field, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    fe.close()
+    t = sum(ms) / len(ms)
+    ys = out[::2].cpu().numpy()[256:-256]
+    s = fr.symbols[256:-256]
+    L = 4
+    a_l = 1.0 / np.sqrt(2.0 * (L * L - 1) / 3.0)
+    dec = lambda v: (np.clip(np.round((v / a_l + (L - 1)) / 2), 0, L - 1) * 2 - (L - 1)) * a_l
+    evm_db = 10 * np.log10(np.mean(np.abs(ys - s) ** 2))
+    ser = float(np.mean((dec(ys.real) != dec(s.real)) | (dec(ys.imag) != dec(s.imag))))
+    pk = peaks()
+    hbm_bytes = S * (2 + 8 + 8 + 4)
+    fft_flops = (S / (N / 2)) * (2 * 5 * N * 10 + 5 * N * 10 + 5 * (N // 2) * 9)
+    lanes = SM_COUNT_GB300 * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    hbm_gbs = hbm_bytes / (t * 1e-3) / 1e9
+    tflops = fft_flops / (t * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "KK front-end sample rate", "value": S / (t * 1e-3) / 1e9, "unit": "GSa/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "line_rate_gbps": 4 * n_sym / (t * 1e-3) / 1e9,
+        "paper_realtime_gsa_s": 4.0,
+        "config": {"workload": f"kk-16qam-1gbd-{S}", "samples": S, "fft": N, "sps_in": 4, "sps_out": 2,
+                   "cspr_db": 11.0, "l2": "flushed between timed steps (512 MiB write)"},
+        "roofline": {"kernel": "k_kk_phase + k_kk_mf (whole front end)", "bound": "hbm", "achieved": hbm_gbs,
+                     "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s", "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0),
+                     "traffic": None, "algorithmic_bytes": hbm_bytes, "fft_tflops": tflops,
+                     "fft_frac_of_fp32_peak": tflops / (2 * lanes / 1e12)},
+        "evm_db": float(evm_db), "symbol_error_rate": ser, "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(), "cpu_baseline": None if args.no_cpu_baseline else kk_cpu_baseline(n_sym)}))
+
+
+def kk_oracle_worker(n_sym: int, reps: int) -> dict:
+    """The oracle's KK front end on the kk workload's buffer."""
+    from oracle import kk
+    from synth.kk import KKLink, generate_kk
+    p = KKLink(bits_per_sym=4, n_sym=n_sym, cspr_db=11.0, snr_db=20.0)
+    fr = generate_kk(p, SEED)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        kk.kk_receive(fr.codes, fr.scale, fr.dc, 1e-6, p.tone_offset / p.fs, p.rolloff, 1024)
+        times.append(time.perf_counter() - t0)
+    return dict(times=times, samples=4 * n_sym)
+
+
+def kk_cpu_baseline(n_sym: int, reps: int = 3) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.kk_oracle_worker(%d, %d)))" % (ROOT, n_sym, reps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode:
+        raise RuntimeError(r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    t = statistics.median(res["times"])
+    return {"value": res["samples"] / t / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+            "sample": f"the kk buffer, {res['samples']} samples, Steps 1-8 in FP64 NumPy, single thread, "
+                      f"median of {reps}"}
 
 
 def main():
@@ -843,6 +954,8 @@ def main():
         cnn_arm(args)
     elif args.workload == "wl":
         wl_arm(args)
+    elif args.workload == "kk":
+        kk_arm(args)
     else:
         our_arm(args)
 

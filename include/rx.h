@@ -349,6 +349,39 @@ rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const fl
                        int32_t block_len, int32_t seg_blocks, int32_t warmup_blocks, int32_t bits_per_sym, float mu,
                        float mu_conj, float* d_y, float* d_taps_out, int32_t threads, rx_stream_t stream);
 
+/*
+ * Kramers-Kronig self-coherent front end (Sec. IV, Steps 1-8): one
+ * polarisation at 4 samples/symbol, from the ADC's 12-bit unsigned codes to
+ * the matched-filtered signal at 2 samples/symbol.
+ *   Step 1: I[n] = max(code_scale * code[n] + dc_offset, min_intensity)
+ *           (the static DC offset restores the term an AC-coupled digitiser
+ *           drops); amplitude sqrt(I), log-amplitude ln sqrt(I).
+ *   Steps 2-5: 100 % overlap-save blocks of N = fft_size samples (block j
+ *           starts at j N/2 - N/4, zero outside the frame, keeps its centre
+ *           N/2): FFT of the log-amplitude, times -j sgn(k) (0 at k = 0 and
+ *           N/2), IFFT -> phase phi; field E[n] = sqrt(I[n]) exp(j phi[n])
+ *           exp(-j 2 pi tone_over_fs n): the signal, which lies tone_over_fs
+ *           above the carrier tone, moved to DC.
+ *   Steps 6-8: second overlap-save pass on E: FFT, times 2 RRC(f_k)
+ *           (matched filter of roll-off rrc_rolloff, symbol rate fs/4), the
+ *           bins |f| < fs/4 into an N/2-point IFFT, i.e. 2 samples/symbol.
+ * rx_kk_create: fft_size 1024..8192 (power of two; the paper uses 1024),
+ * 0 < tone_over_fs < 0.5, 0 < rrc_rolloff <= 1, code_scale finite and
+ * nonzero, dc_offset finite, min_intensity > 0; RX_EINVAL otherwise. It
+ * allocates the twiddle table and the filter (RX_ENOMEM) and synchronises.
+ * rx_kk_process: d_codes DEVICE uint16 [n_samples] (12-bit codes); d_field
+ * DEVICE float [n_samples][2] receives E (4 samples/symbol); d_out DEVICE
+ * float [n_samples/2][2] the output (2 samples/symbol); all caller-owned.
+ * n_samples even, 2..2^36; RX_EINVAL otherwise. No allocation;
+ * asynchronous on `stream` (two kernel launches).
+ */
+typedef struct rx_kk rx_kk;
+rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff, float code_scale, float dc_offset,
+                       float min_intensity, rx_kk** out);
+rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, float* d_field, float* d_out,
+                        rx_stream_t stream);
+void rx_kk_destroy(rx_kk* k);
+
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);
 

@@ -112,3 +112,40 @@ def dd_lms_wl(x: torch.Tensor, taps: torch.Tensor, n_sym: int, block_len: int, s
                     warmup_blocks, bits_per_sym, mu, mu_conj, y.data_ptr(),
                     taps_out.data_ptr() if taps_out is not None else None, threads, s.cuda_stream)
     return y
+
+
+class KKFrontEnd:
+    """Kramers-Kronig self-coherent front end (rx_kk_*) on torch device tensors: 12-bit codes in 16-bit
+    words (any 2-byte dtype; the bits are read as uint16) at 4 samples/symbol in, the downshifted field
+    at 4 samples/symbol and the matched-filtered signal at 2 samples/symbol out (complex64)."""
+
+    def __init__(self, fft_size: int, tone_over_fs: float, rrc_rolloff: float, code_scale: float, dc_offset: float,
+                 min_intensity: float = 1e-6):
+        self.k = rx.rx_kk_create(fft_size, tone_over_fs, rrc_rolloff, code_scale, dc_offset, min_intensity)
+
+    def close(self):
+        if self.k:
+            rx.rx_kk_destroy(self.k)
+            self.k = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def process(self, codes: torch.Tensor, field: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                stream: torch.cuda.Stream | None = None):
+        if not codes.is_cuda or not codes.is_contiguous() or codes.element_size() != 2 or codes.dim() != 1:
+            raise ValueError("codes must be a contiguous 1-D CUDA tensor of 16-bit words")
+        S = codes.shape[0]
+        if field is None:
+            field = torch.empty(S, dtype=torch.complex64, device=codes.device)
+        if out is None:
+            out = torch.empty(S // 2, dtype=torch.complex64, device=codes.device)
+        for t, n in ((field, S), (out, S // 2)):
+            if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("field and out must be contiguous complex64 CUDA tensors of S and S/2 samples")
+        s = stream or torch.cuda.current_stream()
+        rx.rx_kk_process(self.k, codes.data_ptr(), S, field.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return field, out

@@ -28,7 +28,8 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
            "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
-           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl")
+           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl",
+           "rx_kk_create", "rx_kk_process", "rx_kk_destroy")
 RX_STATIC_MAX_SYMBOLS = 262144
 
 
@@ -113,6 +114,9 @@ def lib() -> C.CDLL:
             "rx_pe_destroy": (None, [vp]),
             "rx_dd_lms_wl": (i32, [vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, i32,
                                    vp]),
+            "rx_kk_create": (i32, [i32, C.c_double, C.c_double, C.c_float, C.c_float, C.c_float, C.POINTER(vp)]),
+            "rx_kk_process": (i32, [vp, vp, i64, vp, vp, vp]),
+            "rx_kk_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -329,3 +333,20 @@ def rx_dd_lms_wl(d_x: int, x_len: int, n_taps: int, d_taps_in: int, n_sym: int, 
     _check(lib().rx_dd_lms_wl(d_x, x_len, n_taps, d_taps_in, n_sym, block_len, seg_blocks, warmup_blocks,
                               bits_per_sym, mu, mu_conj, d_y, d_taps_out or None, threads, stream or None),
            "rx_dd_lms_wl")
+
+
+def rx_kk_create(fft_size: int, tone_over_fs: float, rrc_rolloff: float, code_scale: float, dc_offset: float,
+                 min_intensity: float) -> int:
+    """Kramers-Kronig front end handle; see include/rx.h."""
+    h = C.c_void_p()
+    _check(lib().rx_kk_create(fft_size, tone_over_fs, rrc_rolloff, code_scale, dc_offset, min_intensity,
+                              C.byref(h)), "rx_kk_create")
+    return h.value
+
+
+def rx_kk_process(k: int, d_codes: int, n_samples: int, d_field: int, d_out: int, stream: int | None) -> None:
+    _check(lib().rx_kk_process(k, d_codes, n_samples, d_field, d_out, stream or None), "rx_kk_process")
+
+
+def rx_kk_destroy(k: int) -> None:
+    lib().rx_kk_destroy(k)

