@@ -369,7 +369,8 @@ rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const fl
  * 0 < tone_over_fs < 0.5, 0 < rrc_rolloff <= 1, code_scale finite and
  * nonzero, dc_offset finite, min_intensity > 0; RX_EINVAL otherwise. It
  * allocates the twiddle table and the filter (RX_ENOMEM) and synchronises.
- * rx_kk_process: d_codes DEVICE uint16 [n_samples] (12-bit codes); d_field
+ * rx_kk_process: d_codes DEVICE uint16 [n_samples] (12-bit codes, 8-byte
+ * aligned: read four at a time); d_field
  * DEVICE float [n_samples][2] receives E (4 samples/symbol); d_out DEVICE
  * float [n_samples/2][2] the output (2 samples/symbol); all caller-owned.
  * n_samples even, 2..2^36; RX_EINVAL otherwise. No allocation;

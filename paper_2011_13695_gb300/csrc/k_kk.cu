@@ -4,9 +4,9 @@
 // samples starting N/4 before the N/2 they keep (zero outside the frame), one CTA
 // per block, the in-CTA Stockham FFT of rx_fft.cuh:
 //   k_kk_phase<K>  Steps 1-5: 12-bit code -> I = max(scale code + dc, i_min) ->
-//                  l = ln sqrt(I) (real block) -> FFT -> times -j sgn(k) -> IFFT ->
-//                  phi; for each kept sample E = sqrt(I) exp(j phi)
-//                  exp(-j 2 pi (f_t/fs) n) -> field buffer (8 B/sample);
+//                  l = ln sqrt(I) -> FFT -> times -j sgn(k) -> IFFT -> phi (two real
+//                  blocks per complex transform); for each kept sample
+//                  E = sqrt(I) exp(j phi) exp(-j 2 pi (f_t/fs) n) -> field buffer;
 //   k_kk_mf<K>     Steps 6-8: FFT of the field block -> times H[k] = 2 RRC(f_k) / N
 //                  on the bins |f| < fs/4, written straight into their places in
 //                  the N/2-point spectrum -> N/2-point IFFT -> the centre N/4
@@ -52,17 +52,45 @@ __device__ __forceinline__ float kk_intensity(const KkArgs& a, int64_t s) {
     return fmaxf(fmaf(a.scale, (float)a.codes[s], a.dc), a.i_min);
 }
 
+// One CTA takes the block pair (2b, 2b + 1): block 2b starts at 2b N/2 - N/4, block 2b + 1 N/2 later,
+// so the pair reads a window of 3N/2 samples. Their log-amplitudes are real, and -j sgn(k) maps the
+// spectrum of a real sequence to that of a real sequence, so one complex transform of
+// z = l_{2b} + j l_{2b+1} gives both phases: phi_{2b} = Re IFFT(-j sgn Z), phi_{2b+1} = Im.
+// Each sample's (log-amplitude, amplitude) is computed once into shared memory.
 template <int K>
 __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_kk_phase(KkArgs a) {
-    constexpr int N = 1 << K, HOP = N / 2, LEAD = N / 4;
+    constexpr int N = 1 << K, HOP = N / 2, LEAD = N / 4, W = N + HOP;
+    constexpr int NT = (N / 16 < 32) ? 32 : N / 16;
     extern __shared__ float2 sm[];
-    const int64_t start = (int64_t)blockIdx.x * HOP - LEAD;
-    auto load = [&](int idx) -> float2 {
-        const int64_t s = start + idx;
-        float l = 0.0f;
-        if (s >= 0 && s < a.S) l = 0.5f * logf(kk_intensity(a, s));
-        return make_float2(l, 0.0f);
-    };
+    float2* la = sm + fft_smem_elems(N);                    // [W]: (ln sqrt I, sqrt I), zero outside the frame
+    const int64_t start = (int64_t)blockIdx.x * N - LEAD;   // block 2b
+    for (int i = 4 * threadIdx.x; i < W; i += 4 * NT) {
+        const int64_t s0 = start + i;
+        uint16_t c[4] = {0, 0, 0, 0};
+        bool v[4];
+        if (s0 >= 0 && s0 + 3 < a.S) {                      // start and i are multiples of 4: 8-byte aligned
+            const ushort4 q = *reinterpret_cast<const ushort4*>(a.codes + s0);
+            c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+            v[0] = v[1] = v[2] = v[3] = true;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = s0 + u >= 0 && s0 + u < a.S;
+                if (v[u]) c[u] = a.codes[s0 + u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float2 r = make_float2(0.0f, 0.0f);
+            if (v[u]) {
+                const float I = fmaxf(fmaf(a.scale, (float)c[u], a.dc), a.i_min);
+                r = make_float2(0.5f * logf(I), sqrtf(I));
+            }
+            la[i + u] = r;
+        }
+    }
+    __syncthreads();
+    auto load = [&](int idx) -> float2 { return make_float2(la[idx].x, la[idx + HOP].x); };
     // -j sgn(k) and the inverse transform's 1/N
     auto store_h = [&](int k, float2 v) {
         constexpr float inv = 1.0f / (float)N;
@@ -76,12 +104,16 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_k
     float2* field = reinterpret_cast<float2*>(a.field);
     auto store_out = [&](int idx, float2 v) {
         if (idx >= LEAD && idx < LEAD + HOP) {
-            const int64_t n = start + idx;
-            if (n < a.S) {
-                const float amp = sqrtf(kk_intensity(a, n));
-                float sn, cs;
-                sincosf(v.x, &sn, &cs);
-                field[n] = cmul(make_float2(amp * cs, amp * sn), nco_conj(a.inc, n));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = idx + h * HOP;
+                const int64_t n = start + i;
+                if (n < a.S) {
+                    float sn, cs;
+                    sincosf(h ? v.y : v.x, &sn, &cs);
+                    const float amp = la[i].y;
+                    field[n] = cmul(make_float2(amp * cs, amp * sn), nco_conj(a.inc, n));
+                }
             }
         }
     };
@@ -90,7 +122,7 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_k
 }
 
 template <int K>
-__global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_kk_mf(KkArgs a) {
+__global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16, (K == 10) ? 16 : 1) k_kk_mf(KkArgs a) {
     constexpr int N = 1 << K, HOP = N / 2, LEAD = N / 4;
     extern __shared__ float2 sm[];
     const int64_t start = (int64_t)blockIdx.x * HOP - LEAD;
@@ -125,14 +157,15 @@ cudaError_t launch_kk_t(const KkArgs& a, cudaStream_t s) {
     constexpr int N = 1 << K;
     const int threads = N / 16 < 32 ? 32 : N / 16;
     const size_t smem = sizeof(float2) * fft_smem_elems(N);
+    const size_t smem_phase = smem + sizeof(float2) * (N + N / 2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_kk_phase<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_kk_phase<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phase);
         cudaFuncSetAttribute(k_kk_mf<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     const int64_t nblk = (a.S + N / 2 - 1) / (N / 2);
-    k_kk_phase<K><<<(unsigned)nblk, threads, smem, s>>>(a);
+    k_kk_phase<K><<<(unsigned)((nblk + 1) / 2), threads, smem_phase, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_kk_mf<K><<<(unsigned)nblk, threads, smem, s>>>(a);
@@ -203,6 +236,7 @@ rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff
 rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, float* d_field, float* d_out,
                         rx_stream_t stream) {
     if (!k || !d_codes || !d_field || !d_out) return RX_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_codes) & 7) return RX_EINVAL;   // the codes are read 4 at a time
     if (n_samples < 2 || (n_samples & 1) || n_samples > ((int64_t)1 << 36)) return RX_EINVAL;
     KkArgs a;
     a.codes = d_codes;

@@ -97,6 +97,7 @@ def test_kk_front_end_rejects_bad_arguments_before_any_device_call(librx):
         assert e.value.status == rx.RX_EINVAL, b
     fake = 1 << 20
     for args in [(0, fake, 1024, fake, fake), (fake, 0, 1024, fake, fake), (fake, fake, 1023, fake, fake),
+                 (fake, fake + 2, 1024, fake, fake),
                  (fake, fake, 0, fake, fake), (fake, fake, 1024, 0, fake), (fake, fake, 1024, fake, 0)]:
         with pytest.raises(rx.RxError) as e:
             rx.rx_kk_process(*args, None)
