@@ -47,12 +47,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
     ap.add_argument("--workload", default="frame",
-                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk"],
+                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk", "ingest"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser; cnn: the post-equaliser forward alone; wl: the "
                          "widely-linear segmented DD-LMS alone on an IQ-imbalanced 16QAM frame; kk: the "
-                         "Kramers-Kronig front end on a 2^22-sample 12-bit buffer")
+                         "Kramers-Kronig front end on a 2^22-sample 12-bit buffer; ingest: real-time ingest "
+                         "emulation of 2^22-sample buffers at 4 GSa/s through the KK front end")
     ap.add_argument("--launch-dbm", type=float, default=4.0, help="launch power of the learned workload")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
     ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
@@ -911,6 +912,42 @@ def kk_arm(args) -> None:
         "clocks": clk.summary(), "cpu_baseline": None if args.no_cpu_baseline else kk_cpu_baseline(n_sym)}))
 
 
+def ingest_arm(args) -> None:
+    """Real-time ingest emulation (rx_ingest_run): the digitiser delivers 2^22-sample 12-bit buffers at
+    4 GSa/s (one every 1.049 ms); each accepted buffer is copied in, joined to its predecessor, run
+    through the KK front end and its 2^21 output samples copied back to host memory. --steps buffers
+    (default 20 -> 500 buffers, 0.52 s) per run, for 1, 2 and 5 streams; a buffer that finds every
+    stream busy is dropped. The paper's condition: mean buffer time below 1.049 ms x streams."""
+    import numpy as np
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300.receiver import KKFrontEnd
+    from synth.kk import KKLink, generate_kk
+
+    S = 1 << 22
+    nbuf = max(1, args.steps) * 25
+    p = KKLink(bits_per_sym=4, n_sym=S // 4, cspr_db=11.0, snr_db=20.0)
+    fr = generate_kk(p, SEED)
+    fe = KKFrontEnd(1024, p.tone_offset / p.fs, p.rolloff, fr.scale, fr.dc, 1e-6)
+    fe.ingest(fr.codes, S, 4e9, 2, max(3, args.warmup))            # warm-up run
+    runs = {}
+    with ClockSampler(0) as clk:
+        for ns in (1, 2, 5):
+            st, _ = fe.ingest(fr.codes, S, 4e9, ns, nbuf)
+            runs[str(ns)] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
+    fe.close()
+    one = runs["1"]
+    print(json.dumps({
+        "metric": "ingest buffers dropped at 4 GSa/s (1 stream)", "value": one["dropped"], "unit": "buffers",
+        "n_gpus": 1, "steps": nbuf, "warmup": max(3, args.warmup), "higher_is_better": False,
+        "mean_latency_ms_1_stream": one["mean_latency_ms"], "buffer_period_ms": one["buffer_period_ms"],
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ingest-kk-16qam-4gsa", "buffer_samples": S, "sample_rate_gsa_s": 4.0,
+                   "buffers_per_run": nbuf, "streams": [1, 2, 5]},
+        "runs": runs, "gpu_launches": 2 * sum(r["processed"] for r in runs.values()), "clocks": clk.summary()}))
+
+
 def kk_oracle_worker(n_sym: int, reps: int) -> dict:
     """The oracle's KK front end on the kk workload's buffer."""
     from oracle import kk
@@ -956,6 +993,8 @@ def main():
         wl_arm(args)
     elif args.workload == "kk":
         kk_arm(args)
+    elif args.workload == "ingest":
+        ingest_arm(args)
     else:
         our_arm(args)
 

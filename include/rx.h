@@ -370,7 +370,9 @@ rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const fl
  * nonzero, dc_offset finite, min_intensity > 0; RX_EINVAL otherwise. It
  * allocates the twiddle table and the filter (RX_ENOMEM) and synchronises.
  * rx_kk_process: d_codes DEVICE uint16 [n_samples] (12-bit codes, 8-byte
- * aligned: read four at a time); d_field
+ * aligned: read four at a time); first_sample: the stream index of
+ * d_codes[0], which the downshift phase counts from (0 for a lone frame);
+ * d_field
  * DEVICE float [n_samples][2] receives E (4 samples/symbol); d_out DEVICE
  * float [n_samples/2][2] the output (2 samples/symbol); all caller-owned.
  * n_samples even, 2..2^36; RX_EINVAL otherwise. No allocation;
@@ -379,9 +381,49 @@ rx_status rx_dd_lms_wl(const float* d_x, int64_t x_len, int32_t n_taps, const fl
 typedef struct rx_kk rx_kk;
 rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff, float code_scale, float dc_offset,
                        float min_intensity, rx_kk** out);
-rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, float* d_field, float* d_out,
-                        rx_stream_t stream);
+rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, int64_t first_sample, float* d_field,
+                        float* d_out, rx_stream_t stream);
 void rx_kk_destroy(rx_kk* k);
+
+/*
+ * rx_ingest_run: real-time ingest emulation (Sec. II-C, II-D). A digitiser
+ * delivers n_buffers buffers of buffer_samples 12-bit codes at
+ * sample_rate_hz (buffer i is ready buffer_samples * i / sample_rate_hz after
+ * the start; its codes are h_source[(i * buffer_samples) mod
+ * source_samples ...]). Each ready buffer takes a free one of n_streams GPU
+ * slots (its own stream): copy in (the digitiser's DMA), the overlap step
+ * (the last 2N codes of the previous buffer go in front, in buffer order,
+ * through an event chain: each of the front end's two overlap-save passes
+ * needs N/4 samples of context on either side of what a block keeps), the
+ * KK front end of `kk` on the joined buffer, and the copy of its S/2 exact,
+ * continuing outputs to host memory. A buffer that finds every slot busy is
+ * dropped and the overlap chain restarts from zero codes: the first N/2
+ * outputs of the stream from a (re)starting buffer's first sample on are a
+ * start-up transient (the carry holds no data); every later output equals
+ * that of the front end on the whole stream as one frame.
+ * Output: buffer i's outputs are the 2-sample/symbol stream samples
+ * [i S/2 - N/2, (i + 1) S/2 - N/2) (an N/2-sample delay), written
+ * to h_out + i * S floats when h_out is not NULL (host, n_buffers * S/2
+ * complex; dropped buffers leave theirs untouched). h_source (and h_out) are
+ * page-locked for the run unless they already are. Blocking; it allocates
+ * its slots before the first buffer and frees them at the end. RX_EINVAL for
+ * buffer_samples not a multiple of N/2 or below 2N or above 2^30,
+ * source_samples not a multiple of buffer_samples, sample_rate_hz <= 0,
+ * n_streams outside 1..64 or n_buffers < 1.
+ */
+typedef struct rx_ingest_stats {
+    uint64_t buffers;           /* buffers the digitiser delivered */
+    uint64_t processed;         /* buffers that found a free slot */
+    uint64_t dropped;           /* buffers lost: every slot busy */
+    uint64_t pad0;
+    double buffer_period_ms;    /* buffer_samples / sample_rate_hz */
+    double mean_latency_ms;     /* ready -> outputs in host memory, processed buffers */
+    double max_latency_ms;
+    double wall_s;              /* the whole run */
+} rx_ingest_stats;
+rx_status rx_ingest_run(rx_kk* kk, const uint16_t* h_source, int64_t source_samples, int64_t buffer_samples,
+                        double sample_rate_hz, int32_t n_streams, int64_t n_buffers, float* h_out,
+                        rx_ingest_stats* stats);
 
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);

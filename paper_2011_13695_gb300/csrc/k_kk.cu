@@ -42,6 +42,7 @@ struct KkArgs {
     float* field;                // float2 [S]
     float* out;                  // float2 [S/2]
     int64_t S;
+    long long g0;                // stream index of sample 0 (downshift phase)
     float scale, dc, i_min;
     long long inc;
     const float2* tw;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_k
                     float sn, cs;
                     sincosf(h ? v.y : v.x, &sn, &cs);
                     const float amp = la[i].y;
-                    field[n] = cmul(make_float2(amp * cs, amp * sn), nco_conj(a.inc, n));
+                    field[n] = cmul(make_float2(amp * cs, amp * sn), nco_conj(a.inc, a.g0 + n));
                 }
             }
         }
@@ -233,8 +234,8 @@ rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff
     return RX_OK;
 }
 
-rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, float* d_field, float* d_out,
-                        rx_stream_t stream) {
+rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, int64_t first_sample, float* d_field,
+                        float* d_out, rx_stream_t stream) {
     if (!k || !d_codes || !d_field || !d_out) return RX_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_codes) & 7) return RX_EINVAL;   // the codes are read 4 at a time
     if (n_samples < 2 || (n_samples & 1) || n_samples > ((int64_t)1 << 36)) return RX_EINVAL;
@@ -243,6 +244,7 @@ rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, fl
     a.field = d_field;
     a.out = d_out;
     a.S = n_samples;
+    a.g0 = first_sample;
     a.scale = k->scale;
     a.dc = k->dc;
     a.i_min = k->i_min;
@@ -260,3 +262,5 @@ void rx_kk_destroy(rx_kk* k) {
 }
 
 }  // extern "C"
+
+int kk_fft_size(const rx_kk* k) { return 1 << k->K; }

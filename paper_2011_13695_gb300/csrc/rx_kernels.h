@@ -61,6 +61,9 @@ cudaError_t launch_fill_filter(float2* H, int nfft, double fs, double dl_lambda2
 
 cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s);
 int64_t lms_smem_bytes(int T, int Lb, int threads, bool wl = false);
+// FFT size of a Kramers-Kronig front-end handle (k_kk.cu)
+struct rx_kk;
+int kk_fft_size(const rx_kk* k);
 // widely-linear segmented DD-LMS: taps_in/taps_out are [2][4][T] (h_q0, h_q1, g_q0, g_q1 per row),
 // mu_c the conjugate taps' step; threads 0 (choose), 128/256 for the compile-time shapes, else
 // 256/512/1024 and >= 4T

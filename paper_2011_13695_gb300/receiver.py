@@ -135,7 +135,7 @@ class KKFrontEnd:
             pass
 
     def process(self, codes: torch.Tensor, field: torch.Tensor | None = None, out: torch.Tensor | None = None,
-                stream: torch.cuda.Stream | None = None):
+                stream: torch.cuda.Stream | None = None, first_sample: int = 0):
         if not codes.is_cuda or not codes.is_contiguous() or codes.element_size() != 2 or codes.dim() != 1:
             raise ValueError("codes must be a contiguous 1-D CUDA tensor of 16-bit words")
         S = codes.shape[0]
@@ -147,5 +147,15 @@ class KKFrontEnd:
             if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
                 raise ValueError("field and out must be contiguous complex64 CUDA tensors of S and S/2 samples")
         s = stream or torch.cuda.current_stream()
-        rx.rx_kk_process(self.k, codes.data_ptr(), S, field.data_ptr(), out.data_ptr(), s.cuda_stream)
+        rx.rx_kk_process(self.k, codes.data_ptr(), S, first_sample, field.data_ptr(), out.data_ptr(), s.cuda_stream)
         return field, out
+
+    def ingest(self, source, buffer_samples: int, sample_rate_hz: float, n_streams: int, n_buffers: int,
+               keep_outputs: bool = False):
+        """Real-time ingest emulation over host codes ``source`` (numpy uint16); returns (stats, outputs
+        complex64 [n_buffers * buffer_samples / 2] or None)."""
+        import numpy as np
+        src = np.ascontiguousarray(source, dtype=np.uint16)
+        out = np.zeros(n_buffers * buffer_samples // 2, dtype=np.complex64) if keep_outputs else None
+        stats = rx.rx_ingest_run(self.k, src, buffer_samples, sample_rate_hz, n_streams, n_buffers, out)
+        return stats, out

@@ -29,7 +29,7 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
            "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl",
-           "rx_kk_create", "rx_kk_process", "rx_kk_destroy")
+           "rx_kk_create", "rx_kk_process", "rx_kk_destroy", "rx_ingest_run")
 RX_STATIC_MAX_SYMBOLS = 262144
 
 
@@ -45,6 +45,12 @@ class rx_config(C.Structure):
         ("input_format", C.c_int32), ("input_scale", C.c_float), ("streaming", C.c_int32),
         ("max_symbols", C.c_int64), ("lms_threads", C.c_int32),
     ]
+
+
+class rx_ingest_stats(C.Structure):
+    _fields_ = [("buffers", C.c_uint64), ("processed", C.c_uint64), ("dropped", C.c_uint64), ("pad0", C.c_uint64),
+                ("buffer_period_ms", C.c_double), ("mean_latency_ms", C.c_double), ("max_latency_ms", C.c_double),
+                ("wall_s", C.c_double)]
 
 
 class rx_stats_t(C.Structure):
@@ -115,8 +121,9 @@ def lib() -> C.CDLL:
             "rx_dd_lms_wl": (i32, [vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, i32,
                                    vp]),
             "rx_kk_create": (i32, [i32, C.c_double, C.c_double, C.c_float, C.c_float, C.c_float, C.POINTER(vp)]),
-            "rx_kk_process": (i32, [vp, vp, i64, vp, vp, vp]),
+            "rx_kk_process": (i32, [vp, vp, i64, i64, vp, vp, vp]),
             "rx_kk_destroy": (None, [vp]),
+            "rx_ingest_run": (i32, [vp, vp, i64, i64, C.c_double, i32, i64, vp, C.POINTER(rx_ingest_stats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -344,8 +351,20 @@ def rx_kk_create(fft_size: int, tone_over_fs: float, rrc_rolloff: float, code_sc
     return h.value
 
 
-def rx_kk_process(k: int, d_codes: int, n_samples: int, d_field: int, d_out: int, stream: int | None) -> None:
-    _check(lib().rx_kk_process(k, d_codes, n_samples, d_field, d_out, stream or None), "rx_kk_process")
+def rx_kk_process(k: int, d_codes: int, n_samples: int, first_sample: int, d_field: int, d_out: int,
+                  stream: int | None) -> None:
+    _check(lib().rx_kk_process(k, d_codes, n_samples, first_sample, d_field, d_out, stream or None), "rx_kk_process")
+
+
+def rx_ingest_run(k: int, h_source, buffer_samples: int, sample_rate_hz: float, n_streams: int, n_buffers: int,
+                  h_out=None) -> dict:
+    """h_source: host uint16 array (contiguous); h_out: host complex64 array of n_buffers * buffer_samples / 2
+    values, or None. Returns the run's statistics."""
+    st = rx_ingest_stats()
+    _check(lib().rx_ingest_run(k, h_source.ctypes.data, h_source.size, buffer_samples, sample_rate_hz, n_streams,
+                               n_buffers, h_out.ctypes.data if h_out is not None else None, C.byref(st)),
+           "rx_ingest_run")
+    return {f: getattr(st, f) for f, _ in rx_ingest_stats._fields_ if f != "pad0"}
 
 
 def rx_kk_destroy(k: int) -> None:

@@ -96,22 +96,35 @@ def test_kk_front_end_rejects_bad_arguments_before_any_device_call(librx):
             rx.rx_kk_create(**dict(base, **b))
         assert e.value.status == rx.RX_EINVAL, b
     fake = 1 << 20
-    for args in [(0, fake, 1024, fake, fake), (fake, 0, 1024, fake, fake), (fake, fake, 1023, fake, fake),
-                 (fake, fake + 2, 1024, fake, fake),
-                 (fake, fake, 0, fake, fake), (fake, fake, 1024, 0, fake), (fake, fake, 1024, fake, 0)]:
+    for args in [(0, fake, 1024, 0, fake, fake), (fake, 0, 1024, 0, fake, fake), (fake, fake, 1023, 0, fake, fake),
+                 (fake, fake + 2, 1024, 0, fake, fake),
+                 (fake, fake, 0, 0, fake, fake), (fake, fake, 1024, 0, 0, fake), (fake, fake, 1024, 0, fake, 0)]:
         with pytest.raises(rx.RxError) as e:
             rx.rx_kk_process(*args, None)
         assert e.value.status == rx.RX_EINVAL, args
+
+
+def test_ingest_rejects_missing_arguments_before_any_device_call(librx):
+    import numpy as np
+    from paper_2011_13695_gb300 import rx
+    src = np.zeros(4096, dtype=np.uint16)
+    st = rx.rx_ingest_stats()
+    lib = rx.lib()
+    assert lib.rx_ingest_run(None, src.ctypes.data, 4096, 4096, 4e9, 2, 1, None, ctypes.byref(st)) == rx.RX_EINVAL
+    assert lib.rx_ingest_run(1 << 20, None, 4096, 4096, 4e9, 2, 1, None, ctypes.byref(st)) == rx.RX_EINVAL
+    assert lib.rx_ingest_run(1 << 20, src.ctypes.data, 4096, 4096, 4e9, 2, 1, None, None) == rx.RX_EINVAL
 
 
 def test_struct_layout_matches_the_c_compiler(librx):
     from paper_2011_13695_gb300 import rx
     fields = [n for n, _ in rx.rx_config._fields_]
     sfields = [n for n, _ in rx.rx_stats_t._fields_]
+    ifields = [n for n, _ in rx.rx_ingest_stats._fields_]
     prog = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){",
-            'printf("%zu %zu\\n", sizeof(rx_config), sizeof(rx_stats_t));']
+            'printf("%zu %zu %zu\\n", sizeof(rx_config), sizeof(rx_stats_t), sizeof(rx_ingest_stats));']
     prog += [f'printf("%zu\\n", offsetof(rx_config, {f}));' for f in fields]
     prog += [f'printf("%zu\\n", offsetof(rx_stats_t, {f}));' for f in sfields]
+    prog += [f'printf("%zu\\n", offsetof(rx_ingest_stats, {f}));' for f in ifields]
     prog += ["return 0;}"]
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
@@ -121,6 +134,9 @@ def test_struct_layout_matches_the_c_compiler(librx):
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     vals = list(map(int, out))
     assert vals[0] == ctypes.sizeof(rx.rx_config) and vals[1] == ctypes.sizeof(rx.rx_stats_t)
-    offs = vals[2:]
-    assert offs[:len(fields)] == [getattr(rx.rx_config, f).offset for f in fields]
-    assert offs[len(fields):] == [getattr(rx.rx_stats_t, f).offset for f in sfields]
+    assert vals[2] == ctypes.sizeof(rx.rx_ingest_stats)
+    offs = vals[3:]
+    n1, n2 = len(fields), len(fields) + len(sfields)
+    assert offs[:n1] == [getattr(rx.rx_config, f).offset for f in fields]
+    assert offs[n1:n2] == [getattr(rx.rx_stats_t, f).offset for f in sfields]
+    assert offs[n2:] == [getattr(rx.rx_ingest_stats, f).offset for f in ifields]
