@@ -21,7 +21,10 @@ Beyond the chain: ``mimo.dd_lms_wl`` (the widely-linear A4, conjugate taps
 for transmitter IQ imbalance) and ``kk.kk_receive`` (the Kramers-Kronig
 self-coherent front end: square root and log, overlap-save Hilbert
 transform, field reconstruction and downshift, matched filter and
-decimation to 2 samples/symbol).
+decimation to 2 samples/symbol) and ``pam.pam_receive`` (the IM/DD PAM-M chain:
+FD matched filter, block-wise FD clock-phase estimate, 105-block averaging,
+integer unwrap, FD clock correction, variable-rate symbol extraction,
+normalisation and Gray PAM decisions).
 
 ``receiver.receive`` runs the chain end to end; ``theory`` holds closed forms
 (exact Gray square-QAM BER over AWGN, Q <-> BER).

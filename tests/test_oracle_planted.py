@@ -12,8 +12,10 @@ import oracle.bps as obps
 import oracle.cdc as ocdc
 import oracle.kk as okk
 import oracle.mimo as omimo
+import oracle.pam as opam
 import oracle.qam as oqam
-from tests import test_oracle_bps, test_oracle_cdc, test_oracle_kk, test_oracle_mimo, test_oracle_qam, test_oracle_wl
+from tests import (test_oracle_bps, test_oracle_cdc, test_oracle_kk, test_oracle_mimo, test_oracle_pam, test_oracle_qam,
+                   test_oracle_wl)
 
 
 def test_flipped_dispersion_sign_is_caught(monkeypatch):
@@ -109,3 +111,24 @@ def test_kk_wrong_decimation_bins_are_caught(monkeypatch):
     monkeypatch.setattr(okk, "decimation_bins", lambda N: np.arange(N // 2))
     with pytest.raises(AssertionError):
         test_oracle_kk.test_matched_decimation_of_grid_tones()
+
+
+def test_pam_clock_product_conjugate_on_the_wrong_factor_is_caught(monkeypatch):
+    monkeypatch.setattr(opam, "clock_products",
+                        lambda X: np.sum(np.conj(X[:, :X.shape[1] // 2]) * X[:, X.shape[1] // 2:], axis=1))
+    with pytest.raises(AssertionError):
+        test_oracle_pam.test_clock_phase_returns_the_sampling_offset(0.2)
+
+
+def test_pam_winding_sign_reversed_is_caught(monkeypatch):
+    real = opam.winding
+    monkeypatch.setattr(opam, "winding", lambda phi: -real(phi))
+    with pytest.raises(AssertionError):
+        test_oracle_pam.test_variable_rate_extraction_is_continuous(25.0, 0.1)
+
+
+def test_pam_correction_ramp_sign_is_caught(monkeypatch):
+    real = opam.correct
+    monkeypatch.setattr(opam, "correct", lambda X, phi: real(X, -phi))
+    with pytest.raises(AssertionError):
+        test_oracle_pam.test_variable_rate_extraction_is_continuous(25.0, 0.1)
