@@ -47,13 +47,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
     ap.add_argument("--workload", default="frame",
-                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk", "ingest"],
+                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk", "ingest", "pam"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser; cnn: the post-equaliser forward alone; wl: the "
                          "widely-linear segmented DD-LMS alone on an IQ-imbalanced 16QAM frame; kk: the "
                          "Kramers-Kronig front end on a 2^22-sample 12-bit buffer; ingest: real-time ingest "
-                         "emulation of 2^22-sample buffers at 4 GSa/s through the KK front end")
+                         "emulation of 2^22-sample buffers at 4 GSa/s through the KK front end; pam: the IM/DD "
+                         "PAM-4 chain with FD clock recovery on a 2^22-sample buffer")
     ap.add_argument("--launch-dbm", type=float, default=4.0, help="launch power of the learned workload")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
     ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
@@ -948,6 +949,66 @@ def ingest_arm(args) -> None:
         "runs": runs, "gpu_launches": 2 * sum(r["processed"] for r in runs.values()), "clocks": clk.summary()}))
 
 
+def pam_arm(args) -> None:
+    """The IM/DD PAM-4 chain with FD clock recovery (rx_pam_process: clock products, 105-block average,
+    winding scan, offsets, correction + variable-rate extraction, two normalisation reductions, decision)
+    on the paper's buffer of 2^22 12-bit samples at 2 samples/symbol (2 GBd PAM-4, 50 % roll-off, a
+    25 ppm receiver clock offset, 20 dB SNR). Line rate: output symbols x 2 bits per buffer time.
+    Algorithmic HBM bytes per input sample: 2 (codes, read by two passes: 4) + 4 (y written, read
+    twice, 1 output per 2 samples: 6) + 0.5 (levels)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300.receiver import PAMReceiver
+    from synth.pam import PAMLink, generate_pam
+
+    S = args.n_sym * 2 if args.n_sym else (1 << 22)
+    p = PAMLink(levels=4, n_samp=S, clock_ppm=25.0, timing=0.2, snr_db=20.0)
+    fr = generate_pam(p, SEED)
+    pr = PAMReceiver(1024, 4, p.rolloff, fr.scale, fr.dc, S)
+    codes = torch.from_numpy(fr.codes.view(np.int16)).cuda()
+    cap = pr.capacity(S)
+    y = torch.empty(cap, dtype=torch.float32, device="cuda")
+    lev = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pr.process(codes, y, lev)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, _, n_out = pr.process(codes, y, lev)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    n = int(n_out.item())
+    got = lev[:n].cpu().numpy().astype(np.int64)
+    pr.close()
+    tx = (fr.symbols[fr.first:fr.first + n] + 3) // 2
+    E = 60 * 256
+    ser = float(np.mean(got[E:-E] != tx[E:-E]))
+    t = sum(ms) / len(ms)
+    pk = peaks()
+    hbm_bytes = S * (4 + 6 + 0.5)
+    print(json.dumps({
+        "metric": "PAM-4 chain line rate", "value": 2 * n / (t * 1e-3) / 1e9, "unit": "Gb/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "sample_rate_gsa_s": S / (t * 1e-3) / 1e9, "paper_realtime_gsa_s": 4.0,
+        "config": {"workload": f"pam4-2gbd-{S}", "samples": S, "fft": 1024, "clock_ppm": 25.0,
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "roofline": {"kernel": "rx_pam_process (10 launches)", "bound": "hbm",
+                     "achieved": hbm_bytes / (t * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                     "frac": hbm_bytes / (t * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0), "traffic": None},
+        "symbol_error_rate_interior": ser, "outputs": n, "gpu_launches": 10 * args.steps,
+        "clocks": clk.summary()}))
+
+
 def kk_oracle_worker(n_sym: int, reps: int) -> dict:
     """The oracle's KK front end on the kk workload's buffer."""
     from oracle import kk
@@ -995,6 +1056,8 @@ def main():
         kk_arm(args)
     elif args.workload == "ingest":
         ingest_arm(args)
+    elif args.workload == "pam":
+        pam_arm(args)
     else:
         our_arm(args)
 

@@ -425,6 +425,45 @@ rx_status rx_ingest_run(rx_kk* kk, const uint16_t* h_source, int64_t source_samp
                         double sample_rate_hz, int32_t n_streams, int64_t n_buffers, float* h_out,
                         rx_ingest_stats* stats);
 
+/*
+ * IM/DD PAM-M chain with frequency-domain clock recovery (Sec. III, Steps
+ * 1-9), one real signal at 2 samples/symbol:
+ *   Steps 1-2: v = code_scale * code + dc_offset; 100 % overlap-save blocks
+ *     of N = fft_size (block j from j N/2 - N/4, zero outside the frame);
+ *     FFT; the static FD equaliser as the RRC matched filter sqrt(2) RRC(f)
+ *     (roll-off rrc_rolloff, symbol rate fs/2).
+ *   Steps 3-4: clock product c_j = sum_{k < N/2} X_j[k] conj(X_j[k + N/2]);
+ *     average over the 105 blocks |i - j| <= 52 inside the frame, phase
+ *     phi_j = arg; winding numbers w_j from the unwrap steps (-1 when
+ *     phi_j - phi_{j-1} > pi, +1 when < -pi).
+ *   Steps 5-7: block spectrum times exp(-j phi_j f / Rs), IFFT; block j
+ *     outputs the real parts of its samples N/4 + 2 i, i < N/4 + w_{j+1} -
+ *     w_j (255, 256 or 257 symbols; the last block N/4, clipped to the
+ *     frame), at offset j N/4 + w_j - w_0.
+ *   Steps 8-9: u = (y - mean y) (M/2) / mean|y - mean y|; level index
+ *     clip(rint((u + M - 1) / 2), 0, M - 1) (thresholds at the level
+ *     midpoints; Gray word l ^ (l >> 1)).
+ * rx_pam_create: fft_size 1024/2048/4096, levels 2/4/8, 0 < rrc_rolloff <=
+ * 1, code_scale finite nonzero, dc_offset finite, max_samples 2..2^30;
+ * allocates (RX_ENOMEM) and synchronises.
+ * rx_pam_process: d_codes DEVICE uint16 [n_samples] (n_samples even, <=
+ * max_samples); d_y DEVICE float and d_levels DEVICE uint8, each with room
+ * for n_samples/2 + n_samples/(fft_size/2) + 1 outputs; d_n_out DEVICE
+ * int64 [1] receives the number of outputs. Asynchronous on `stream`, no
+ * allocation. rx_pam_get copies one of the chain's internal arrays of the
+ * last call (RX_PAM_*: float2 clock products, float phases, int32 winding
+ * numbers, int64 offsets [blocks + 1], double [2] mean and mean absolute
+ * deviation) into a DEVICE buffer; RX_EINVAL if bytes exceeds its size.
+ */
+typedef struct rx_pam rx_pam;
+enum { RX_PAM_CLOCK = 0, RX_PAM_PHASE = 1, RX_PAM_WINDING = 2, RX_PAM_OFFSETS = 3, RX_PAM_STATS = 4 };
+rx_status rx_pam_create(int32_t fft_size, int32_t levels, double rrc_rolloff, float code_scale, float dc_offset,
+                        int64_t max_samples, rx_pam** out);
+rx_status rx_pam_process(rx_pam* p, const uint16_t* d_codes, int64_t n_samples, float* d_y, uint8_t* d_levels,
+                         int64_t* d_n_out, rx_stream_t stream);
+rx_status rx_pam_get(rx_pam* p, int32_t which, void* d_dst, int64_t bytes, rx_stream_t stream);
+void rx_pam_destroy(rx_pam* p);
+
 void rx_destroy(rx_handle* h);
 const char* rx_strerror(rx_status s);
 

@@ -159,3 +159,54 @@ class KKFrontEnd:
         out = np.zeros(n_buffers * buffer_samples // 2, dtype=np.complex64) if keep_outputs else None
         stats = rx.rx_ingest_run(self.k, src, buffer_samples, sample_rate_hz, n_streams, n_buffers, out)
         return stats, out
+
+
+class PAMReceiver:
+    """IM/DD PAM-M chain with FD clock recovery (rx_pam_*) on torch device tensors: 12-bit codes in
+    16-bit words (any 2-byte dtype) at 2 samples/symbol in; extracted samples (float32), level
+    indices (uint8) and their count out."""
+
+    def __init__(self, fft_size: int, levels: int, rrc_rolloff: float, code_scale: float, dc_offset: float,
+                 max_samples: int):
+        self.max_samples = max_samples
+        self.fft_size = fft_size
+        self.p = rx.rx_pam_create(fft_size, levels, rrc_rolloff, code_scale, dc_offset, max_samples)
+        self.n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def close(self):
+        if self.p:
+            rx.rx_pam_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def capacity(self, n_samples: int) -> int:
+        return n_samples // 2 + n_samples // (self.fft_size // 2) + 1
+
+    def process(self, codes: torch.Tensor, y: torch.Tensor | None = None, levels: torch.Tensor | None = None,
+                stream: torch.cuda.Stream | None = None):
+        """Returns (y, levels, n_out device tensor); the first n_out entries are valid."""
+        if not codes.is_cuda or not codes.is_contiguous() or codes.element_size() != 2 or codes.dim() != 1:
+            raise ValueError("codes must be a contiguous 1-D CUDA tensor of 16-bit words")
+        S = codes.shape[0]
+        cap = self.capacity(S)
+        if y is None:
+            y = torch.empty(cap, dtype=torch.float32, device=codes.device)
+        if levels is None:
+            levels = torch.empty(cap, dtype=torch.uint8, device=codes.device)
+        if y.numel() < cap or levels.numel() < cap or y.dtype != torch.float32 or levels.dtype != torch.uint8:
+            raise ValueError("y (float32) and levels (uint8) need room for capacity(n_samples) outputs")
+        s = stream or torch.cuda.current_stream()
+        rx.rx_pam_process(self.p, codes.data_ptr(), S, y.data_ptr(), levels.data_ptr(), self.n_out.data_ptr(),
+                          s.cuda_stream)
+        return y, levels, self.n_out
+
+    def internal(self, which: int, count: int, dtype) -> torch.Tensor:
+        t = torch.empty(count, dtype=dtype, device="cuda")
+        rx.rx_pam_get(self.p, which, t.data_ptr(), t.numel() * t.element_size(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.current_stream().synchronize()
+        return t

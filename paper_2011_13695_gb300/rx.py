@@ -29,7 +29,9 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
            "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl",
-           "rx_kk_create", "rx_kk_process", "rx_kk_destroy", "rx_ingest_run")
+           "rx_kk_create", "rx_kk_process", "rx_kk_destroy", "rx_ingest_run", "rx_pam_create", "rx_pam_process",
+           "rx_pam_get", "rx_pam_destroy")
+RX_PAM_CLOCK, RX_PAM_PHASE, RX_PAM_WINDING, RX_PAM_OFFSETS, RX_PAM_STATS = range(5)
 RX_STATIC_MAX_SYMBOLS = 262144
 
 
@@ -124,6 +126,10 @@ def lib() -> C.CDLL:
             "rx_kk_process": (i32, [vp, vp, i64, i64, vp, vp, vp]),
             "rx_kk_destroy": (None, [vp]),
             "rx_ingest_run": (i32, [vp, vp, i64, i64, C.c_double, i32, i64, vp, C.POINTER(rx_ingest_stats)]),
+            "rx_pam_create": (i32, [i32, i32, C.c_double, C.c_float, C.c_float, i64, C.POINTER(vp)]),
+            "rx_pam_process": (i32, [vp, vp, i64, vp, vp, vp, vp]),
+            "rx_pam_get": (i32, [vp, i32, vp, i64, vp]),
+            "rx_pam_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -369,3 +375,25 @@ def rx_ingest_run(k: int, h_source, buffer_samples: int, sample_rate_hz: float, 
 
 def rx_kk_destroy(k: int) -> None:
     lib().rx_kk_destroy(k)
+
+
+def rx_pam_create(fft_size: int, levels: int, rrc_rolloff: float, code_scale: float, dc_offset: float,
+                  max_samples: int) -> int:
+    """IM/DD PAM chain handle; see include/rx.h."""
+    h = C.c_void_p()
+    _check(lib().rx_pam_create(fft_size, levels, rrc_rolloff, code_scale, dc_offset, max_samples, C.byref(h)),
+           "rx_pam_create")
+    return h.value
+
+
+def rx_pam_process(p: int, d_codes: int, n_samples: int, d_y: int, d_levels: int, d_n_out: int,
+                   stream: int | None) -> None:
+    _check(lib().rx_pam_process(p, d_codes, n_samples, d_y, d_levels, d_n_out, stream or None), "rx_pam_process")
+
+
+def rx_pam_get(p: int, which: int, d_dst: int, nbytes: int, stream: int | None) -> None:
+    _check(lib().rx_pam_get(p, which, d_dst, nbytes, stream or None), "rx_pam_get")
+
+
+def rx_pam_destroy(p: int) -> None:
+    lib().rx_pam_destroy(p)

@@ -104,6 +104,25 @@ def test_kk_front_end_rejects_bad_arguments_before_any_device_call(librx):
         assert e.value.status == rx.RX_EINVAL, args
 
 
+def test_pam_chain_rejects_bad_arguments_before_any_device_call(librx):
+    from paper_2011_13695_gb300 import rx
+    base = dict(fft_size=1024, levels=4, rrc_rolloff=0.5, code_scale=1e-3, dc_offset=0.5, max_samples=1 << 20)
+    bad = [dict(fft_size=512), dict(fft_size=8192), dict(fft_size=1000), dict(levels=3), dict(levels=16),
+           dict(rrc_rolloff=0.0), dict(rrc_rolloff=1.5), dict(code_scale=0.0), dict(dc_offset=float("nan")),
+           dict(max_samples=1), dict(max_samples=(1 << 30) + 2)]
+    for b in bad:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_pam_create(**dict(base, **b))
+        assert e.value.status == rx.RX_EINVAL, b
+    fake = 1 << 20
+    for args in [(0, fake, 1024, fake, fake, fake), (fake, 0, 1024, fake, fake, fake),
+                 (fake, fake, 1024, 0, fake, fake), (fake, fake, 1024, fake, 0, fake),
+                 (fake, fake, 1024, fake, fake, 0)]:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_pam_process(*args, None)
+        assert e.value.status == rx.RX_EINVAL, args
+
+
 def test_ingest_rejects_missing_arguments_before_any_device_call(librx):
     import numpy as np
     from paper_2011_13695_gb300 import rx
