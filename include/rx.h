@@ -447,8 +447,9 @@ rx_status rx_ingest_run(rx_kk* kk, const uint16_t* h_source, int64_t source_samp
  * 1, code_scale finite nonzero, dc_offset finite, max_samples 2..2^30;
  * allocates (RX_ENOMEM) and synchronises.
  * rx_pam_process: d_codes DEVICE uint16 [n_samples] (n_samples even, <=
- * max_samples); d_y DEVICE float and d_levels DEVICE uint8, each with room
- * for n_samples/2 + n_samples/(fft_size/2) + 1 outputs; d_n_out DEVICE
+ * max_samples); d_y DEVICE float (16-byte aligned) and d_levels DEVICE
+ * uint8 (4-byte aligned), each with room for n_samples/2 +
+ * n_samples/(fft_size/2) + 1 outputs; d_n_out DEVICE
  * int64 [1] receives the number of outputs. Asynchronous on `stream`, no
  * allocation. rx_pam_get copies one of the chain's internal arrays of the
  * last call (RX_PAM_*: float2 clock products, float phases, int32 winding

@@ -5,18 +5,20 @@
 //   k_pam_clock<K>    code -> v = scale code + dc -> FFT -> times sqrt(2) RRC(f) -> the block's
 //                     clock product c_j = sum_{k < N/2} X[k] conj(X[k + N/2]) (spectral line one
 //                     symbol rate apart; its phase is -2 pi Rs tau for a delay tau);
-//   k_pam_average     cbar_j = sum of c_i over |i - j| <= 52 inside the frame (FP64), phi_j =
-//                     arg cbar_j, and the unwrap step of block j: -1 if phi_j - phi_{j-1} > pi,
-//                     +1 if < -pi;
-//   k_pam_scan        one CTA: winding numbers w_j (integer prefix sum of the steps), each block's
+//   k_pam_prefix      one CTA: FP64 prefix sums of the clock products;
+//   k_pam_phase       cbar_j = sum of c_i over |i - j| <= 52 inside the frame (a difference of
+//                     prefix sums), phi_j = arg cbar_j, the unwrap step of block j (-1 if
+//                     phi_j - phi_{j-1} > pi, +1 if < -pi);
+//   k_pam_wind        one CTA: winding numbers w_j (integer prefix sum of the steps), each block's
 //                     output count N/4 + w_{j+1} - w_j (N/4 for the last block, clipped to the
-//                     frame) and output offset;
+//                     frame) and offset;
 //   k_pam_correct<K>  the FFT again (recomputing is cheaper than a 64 MB spectrum round trip),
 //                     times sqrt(2) RRC(f) exp(-j phi_j f / Rs) / N, inverse FFT; the block's
 //                     outputs are the real parts of its samples N/4 + 2 i, written at its offset
-//                     (variable rate: 255, 256 or 257 symbols per block);
-//   k_pam_partial, k_pam_final   buffer-wise mean, then mean absolute deviation (fixed-order
-//                     two-stage reductions, so results do not depend on scheduling);
+//                     (variable rate: 255, 256 or 257 symbols per block), and their sum;
+//   k_pam_final, k_pam_deviation   buffer-wise mean from the blocks' sums, then the mean absolute
+//                     deviation (fixed-order two-stage reductions: results do not depend on
+//                     scheduling);
 //   k_pam_decide      u = (y - mean) (M/2) / mad, level index clip(rint((u + M - 1) / 2)).
 // The paper estimates, averages and unwraps in separate kernels over five streams, unwraps
 // with one warp, and extracts symbols in a kernel of its own; here the unwrap is an exact integer
@@ -44,7 +46,8 @@ struct rx_pam {
     int* step = nullptr;         // [J] unwrap steps
     int* w = nullptr;            // [J] winding numbers
     long long* off = nullptr;    // [J + 1] output offsets (off[J] = outputs)
-    double* part = nullptr;      // [2][kParts] partial sums
+    double2* pre = nullptr;      // [J + 1] prefix sums of the clock products
+    double* part = nullptr;      // [J] per-block output sums, then [kParts] deviation partials
     double* stat = nullptr;      // [2] mean, mean absolute deviation
 };
 
@@ -66,6 +69,7 @@ struct PamArgs {
     int* step;
     int* w;
     long long* off;
+    double2* pre;
     float* y;
     uint8_t* levels;
     double* part;
@@ -103,65 +107,86 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_p
     }
 }
 
-__global__ void k_pam_average(PamArgs a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.J) return;
-    auto avg_phase = [&](int jj) -> double {
-        double re = 0.0, im = 0.0;
-        const int lo = max(0, jj - kAvgHalf), hi = min(a.J - 1, jj + kAvgHalf);
-        for (int i = lo; i <= hi; ++i) {
-            const float2 v = a.c[i];
-            re += (double)v.x;
-            im += (double)v.y;
-        }
-        return atan2(im, re);
-    };
-    const double p = avg_phase(j);
-    a.phi[j] = (float)p;
-    int s = 0;
-    if (j > 0) {
-        const double d = p - avg_phase(j - 1);
-        s = d > M_PI ? -1 : (d < -M_PI ? 1 : 0);
+// One CTA of 1024 threads: FP64 prefix sums P_i = c_0 + ... + c_{i-1} of the clock products, so that
+// each 105-block average is P_hi - P_lo. Thread t owns the contiguous blocks [t per, (t + 1) per).
+__global__ void __launch_bounds__(1024) k_pam_prefix(PamArgs a) {
+    __shared__ double2 dpart[1024];
+    const int t = threadIdx.x, J = a.J;
+    const int per = (J + 1023) / 1024;
+    const int lo = min(J, t * per), hi = min(J, lo + per);
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = lo; i < hi; ++i) {
+        const float2 v = a.c[i];
+        s.x += (double)v.x;
+        s.y += (double)v.y;
     }
-    a.step[j] = s;
-}
-
-// one CTA of 1024 threads: w = inclusive prefix sum of the steps, counts, offsets
-__global__ void __launch_bounds__(1024) k_pam_scan(PamArgs a) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int per = (a.J + 1023) / 1024;
-    const int lo = min(a.J, t * per), hi = min(a.J, lo + per);
-    int s = 0;
-    for (int i = lo; i < hi; ++i) s += a.step[i];
-    part[t] = s;
+    dpart[t] = s;
     __syncthreads();
     for (int d = 1; d < 1024; d <<= 1) {
-        const int v = t >= d ? part[t - d] : 0;
+        const double2 v = t >= d ? dpart[t - d] : make_double2(0.0, 0.0);
         __syncthreads();
-        part[t] += v;
+        dpart[t].x += v.x;
+        dpart[t].y += v.y;
         __syncthreads();
     }
-    int run = t > 0 ? part[t - 1] : 0;
+    double2 run = t > 0 ? dpart[t - 1] : make_double2(0.0, 0.0);
     for (int i = lo; i < hi; ++i) {
-        run += a.step[i];
-        a.w[i] = run;
+        a.pre[i] = run;
+        const float2 v = a.c[i];
+        run.x += (double)v.x;
+        run.y += (double)v.y;
     }
+    if (t == 1023) a.pre[J] = run;
 }
 
-__global__ void k_pam_offsets(PamArgs a, int quarter) {
+// per block: phi_j = arg(P_{j+53} - P_{j-52}) (clipped to the frame) and the unwrap step
+__global__ void k_pam_phase(PamArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > a.J) return;
-    const long long w0 = a.w[0];
-    const long long slots = a.S / 2;
-    if (j < a.J) {
-        a.off[j] = (long long)j * quarter + a.w[j] - w0;
-    } else {
+    if (j >= a.J) return;
+    auto phase = [&](int i) -> double {
+        const double2 h = a.pre[min(a.J, i + kAvgHalf + 1)], l = a.pre[max(0, i - kAvgHalf)];
+        return atan2(h.y - l.y, h.x - l.x);
+    };
+    const double p = phase(j);
+    a.phi[j] = (float)p;
+    int st = 0;
+    if (j > 0) {
+        const double d = p - phase(j - 1);
+        st = d > M_PI ? -1 : (d < -M_PI ? 1 : 0);
+    }
+    a.step[j] = st;
+}
+
+// One CTA of 1024 threads: winding numbers (integer prefix sum of the steps), output offsets
+// j N/4 + w_j - w_0 (w_0 = 0) and the output count.
+__global__ void __launch_bounds__(1024) k_pam_wind(PamArgs a, int quarter) {
+    __shared__ int ipart[1024];
+    const int t = threadIdx.x, J = a.J;
+    const int per = (J + 1023) / 1024;
+    const int lo = min(J, t * per), hi = min(J, lo + per);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += a.step[i];
+    ipart[t] = s;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int v = t >= d ? ipart[t - d] : 0;
+        __syncthreads();
+        ipart[t] += v;
+        __syncthreads();
+    }
+    int w = t > 0 ? ipart[t - 1] : 0;
+    for (int i = lo; i < hi; ++i) {
+        w += a.step[i];
+        a.w[i] = w;
+        a.off[i] = (long long)i * quarter + w;
+    }
+    __syncthreads();
+    if (t == 0) {
         // the last block outputs N/4 symbols, clipped to the frame's slots
-        const int jl = a.J - 1;
-        const long long n_last = min((long long)quarter, slots - (long long)jl * quarter);
-        a.off[a.J] = (long long)jl * quarter + a.w[jl] - w0 + max(n_last, 0LL);
-        *a.n_out = a.off[a.J];
+        const int jl = J - 1;
+        const long long n_last = min((long long)quarter, a.S / 2 - (long long)jl * quarter);
+        a.off[J] = a.off[jl] + max(n_last, 0LL);
+        *a.n_out = a.off[J];
     }
 }
 
@@ -181,62 +206,97 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_p
     auto store = [&](int k, float2 v) {
         const int ks = k < N / 2 ? k : (k == N / 2 ? 0 : k - N);
         float sn, cs;
-        sincosf(-ph * (float)ks * inv_half, &sn, &cs);
+        __sincosf(-ph * (float)ks * inv_half, &sn, &cs);    // |argument| <= pi
         sm[fft_pad(k)] = cscale(cmul(v, make_float2(cs, sn)), __ldg(&H[k]) * (1.0f / (float)N));
     };
     fft_run<K, -1, true, true>(sm, a.tw, load, store);
     __syncthreads();
     const long long o0 = a.off[j];
     const long long n = a.off[j + 1] - o0;
+    double bsum = 0.0;                                    // this block's outputs, for the mean
     auto store_out = [&](int idx, float2 v) {
         const int r = idx - LEAD;
-        if (r >= 0 && !(r & 1) && (r >> 1) < n) a.y[o0 + (r >> 1)] = v.x;
+        if (r >= 0 && !(r & 1) && (r >> 1) < n) {
+            a.y[o0 + (r >> 1)] = v.x;
+            bsum += (double)v.x;
+        }
     };
     SmemLoad sl{sm};
     fft_run<K, +1, false, true>(sm, a.tw, sl, store_out);
+    constexpr int NT = (N / 16 < 32) ? 32 : N / 16;
+    __shared__ double red[NT / 32];
+    for (int o = 16; o; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NT / 32; ++i) t += red[i];
+        a.part[j] = t;
+    }
 }
 
-// stage 1: CTA b sums its contiguous share of the outputs (mode 0: y; mode 1: |y - mean|)
-__global__ void __launch_bounds__(kRedThreads) k_pam_partial(PamArgs a, int mode) {
+// sum of |y - mean| over CTA b's contiguous share of the outputs, four outputs per load where the
+// share is aligned (the share boundaries are multiples of 4)
+__global__ void __launch_bounds__(kRedThreads) k_pam_deviation(PamArgs a) {
     __shared__ double red[kRedThreads / 32];
     const long long n = *a.n_out;
-    const long long per = (n + kParts - 1) / kParts;
+    const long long per = ((n + kParts - 1) / kParts + 3) & ~3LL;
     const long long lo = min(n, (long long)blockIdx.x * per), hi = min(n, lo + per);
-    const double mu = mode ? a.stat[0] : 0.0;
+    const float mu = (float)a.stat[0];
     double s = 0.0;
-    for (long long i = lo + threadIdx.x; i < hi; i += kRedThreads) {
-        const double v = (double)a.y[i];
-        s += mode ? fabs(v - mu) : v;
+    const long long v_hi = lo + ((hi - lo) & ~3LL);
+    const float4* y4 = reinterpret_cast<const float4*>(a.y);
+    for (long long i = lo + 4 * (long long)threadIdx.x; i < v_hi; i += 4 * kRedThreads) {
+        const float4 v = y4[i >> 2];
+        s += (double)(fabsf(v.x - mu) + fabsf(v.y - mu)) + (double)(fabsf(v.z - mu) + fabsf(v.w - mu));
     }
+    for (long long i = v_hi + threadIdx.x; i < hi; i += kRedThreads) s += (double)fabsf(a.y[i] - mu);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < kRedThreads / 32; ++i) t += red[i];
-        a.part[mode * kParts + blockIdx.x] = t;
+        a.part[a.J + blockIdx.x] = t;
     }
 }
 
-// stage 2: one warp adds the partials in a fixed order
-__global__ void k_pam_final(PamArgs a, int mode) {
+// stat[mode] = (sum of count partials from part + first) / outputs: one CTA of 1024 threads, a fixed
+// order (strided per-thread sums, then a shuffle and shared-memory tree)
+__global__ void __launch_bounds__(1024) k_pam_final(PamArgs a, int mode, int first, int count) {
+    __shared__ double red[32];
     const long long n = *a.n_out;
     double s = 0.0;
-    for (int i = threadIdx.x; i < kParts; i += 32) s += a.part[mode * kParts + i];
+    for (int i = threadIdx.x; i < count; i += 1024) s += a.part[first + i];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) a.stat[mode] = n > 0 ? s / (double)n : 0.0;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = red[threadIdx.x];
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) a.stat[mode] = n > 0 ? t / (double)n : 0.0;
+    }
 }
 
 __global__ void k_pam_decide(PamArgs a) {
     const long long n = *a.n_out;
     const float mu = (float)a.stat[0];
     const float g = a.stat[1] > 0.0 ? (float)(0.5 * a.M / a.stat[1]) : 0.0f;
-    const float hm = 0.5f * (float)(a.M - 1);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float u = (a.y[i] - mu) * g;
-        const float l = rintf(fmaf(0.5f, u, hm));
-        a.levels[i] = (uint8_t)fminf(fmaxf(l, 0.0f), (float)(a.M - 1));
+    const float hm = 0.5f * (float)(a.M - 1), top = (float)(a.M - 1);
+    auto level = [&](float y) -> uint8_t {
+        const float l = rintf(fmaf(0.5f, (y - mu) * g, hm));
+        return (uint8_t)fminf(fmaxf(l, 0.0f), top);
+    };
+    const long long n4 = n >> 2;
+    const float4* y4 = reinterpret_cast<const float4*>(a.y);
+    uchar4* l4 = reinterpret_cast<uchar4*>(a.levels);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 v = y4[i];
+        l4[i] = make_uchar4(level(v.x), level(v.y), level(v.z), level(v.w));
     }
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        a.levels[i] = level(a.y[i]);
 }
 
 template <int K>
@@ -251,14 +311,13 @@ cudaError_t launch_pam_t(const PamArgs& a, cudaStream_t s) {
         attr = true;
     }
     k_pam_clock<K><<<a.J, threads, smem, s>>>(a);
-    k_pam_average<<<(a.J + 255) / 256, 256, 0, s>>>(a);
-    k_pam_scan<<<1, 1024, 0, s>>>(a);
-    k_pam_offsets<<<(a.J + 1 + 255) / 256, 256, 0, s>>>(a, N / 4);
+    k_pam_prefix<<<1, 1024, 0, s>>>(a);
+    k_pam_phase<<<(a.J + 127) / 128, 128, 0, s>>>(a);
+    k_pam_wind<<<1, 1024, 0, s>>>(a, N / 4);
     k_pam_correct<K><<<a.J, threads, smem, s>>>(a);
-    k_pam_partial<<<kParts, kRedThreads, 0, s>>>(a, 0);
-    k_pam_final<<<1, 32, 0, s>>>(a, 0);
-    k_pam_partial<<<kParts, kRedThreads, 0, s>>>(a, 1);
-    k_pam_final<<<1, 32, 0, s>>>(a, 1);
+    k_pam_final<<<1, 1024, 0, s>>>(a, 0, 0, a.J);
+    k_pam_deviation<<<kParts, kRedThreads, 0, s>>>(a);
+    k_pam_final<<<1, 1024, 0, s>>>(a, 1, a.J, kParts);
     k_pam_decide<<<4 * 152, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -311,7 +370,8 @@ rx_status rx_pam_create(int32_t fft_size, int32_t levels, double rrc_rolloff, fl
               cudaMalloc(&p->step, sizeof(int) * J) == cudaSuccess &&
               cudaMalloc(&p->w, sizeof(int) * J) == cudaSuccess &&
               cudaMalloc(&p->off, sizeof(long long) * (J + 1)) == cudaSuccess &&
-              cudaMalloc(&p->part, sizeof(double) * 2 * kParts) == cudaSuccess &&
+              cudaMalloc(&p->pre, sizeof(double2) * (J + 1)) == cudaSuccess &&
+              cudaMalloc(&p->part, sizeof(double) * (J + kParts)) == cudaSuccess &&
               cudaMalloc(&p->stat, sizeof(double) * 2) == cudaSuccess;
     if (ok)
         ok = launch_fill_twiddles(p->tw, 0) == cudaSuccess &&
@@ -328,6 +388,8 @@ rx_status rx_pam_create(int32_t fft_size, int32_t levels, double rrc_rolloff, fl
 rx_status rx_pam_process(rx_pam* p, const uint16_t* d_codes, int64_t n_samples, float* d_y, uint8_t* d_levels,
                          int64_t* d_n_out, rx_stream_t stream) {
     if (!p || !d_codes || !d_y || !d_levels || !d_n_out) return RX_EINVAL;
+    // outputs are read four at a time
+    if ((reinterpret_cast<uintptr_t>(d_y) & 15) || (reinterpret_cast<uintptr_t>(d_levels) & 3)) return RX_EINVAL;
     if (n_samples < 2 || (n_samples & 1) || n_samples > p->max_samples) return RX_EINVAL;
     const int N = 1 << p->K;
     PamArgs a;
@@ -343,6 +405,7 @@ rx_status rx_pam_process(rx_pam* p, const uint16_t* d_codes, int64_t n_samples, 
     a.step = p->step;
     a.w = p->w;
     a.off = p->off;
+    a.pre = p->pre;
     a.y = d_y;
     a.levels = d_levels;
     a.part = p->part;
@@ -373,7 +436,7 @@ rx_status rx_pam_get(rx_pam* p, int32_t which, void* d_dst, int64_t bytes, rx_st
 
 void rx_pam_destroy(rx_pam* p) {
     if (!p) return;
-    void* ptrs[] = {p->tw, p->H, p->c, p->phi, p->step, p->w, p->off, p->part, p->stat};
+    void* ptrs[] = {p->tw, p->H, p->c, p->phi, p->step, p->w, p->off, p->pre, p->part, p->stat};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;

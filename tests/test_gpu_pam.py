@@ -4,7 +4,7 @@ the FP64 oracle (``oracle.pam.pam_receive``) on the same seeded 12-bit codes.
 Tolerances: the kernels compute the FFTs, the clock products and the corrected samples in FP32 and
 the 105-block averages and their phases in FP64. Clock products and extracted samples: 1e-5
 relative RMS; averaged phases: 1e-5 rad; winding numbers, output offsets and counts: equal; mean and
-mean absolute deviation: 1e-6 relative; levels: equal except where the oracle's normalised sample lies
+mean absolute deviation: within 1e-5 of the outputs' RMS (the outputs' own tolerance); levels: equal except where the oracle's normalised sample lies
 within 1e-4 of a decision threshold (every such symbol is checked, and they are at most 1e-5 of the
 symbols).
 """
@@ -65,7 +65,9 @@ def check(g, o, M):
     assert e <= 1e-5, e
     mu = np.mean(o["y"])
     mad = np.mean(np.abs(o["y"] - mu))
-    assert abs(g["stat"][0] - mu) <= 1e-6 * mad and abs(g["stat"][1] - mad) <= 1e-6 * mad
+    rms = np.sqrt(np.mean(o["y"] ** 2))
+    # the outputs carry the bias (the DC bin is the largest): their errors scale with their RMS
+    assert abs(g["stat"][0] - mu) <= 1e-5 * rms and abs(g["stat"][1] - mad) <= 1e-5 * rms
     diff = np.nonzero(g["levels"] != o["levels"])[0]
     if diff.size:
         t = (o["u"][diff] + (M - 1)) / 2.0
