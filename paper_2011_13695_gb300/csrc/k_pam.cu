@@ -2,9 +2,10 @@
 //
 // At 2 samples/symbol, overlap-save blocks of N = 2^K samples (block j from j N/2 - N/4, zero
 // outside the frame), one CTA per block, the in-CTA Stockham FFT of rx_fft.cuh:
-//   k_pam_clock<K>    code -> v = scale code + dc -> FFT -> times sqrt(2) RRC(f) -> the block's
-//                     clock product c_j = sum_{k < N/2} X[k] conj(X[k + N/2]) (spectral line one
-//                     symbol rate apart; its phase is -2 pi Rs tau for a delay tau);
+//   k_pam_clock<K>    code -> v = scale code + dc -> FFT (two real blocks per complex transform)
+//                     -> times sqrt(2) RRC(f) -> each block's clock product
+//                     c_j = sum_{k < N/2} X[k] conj(X[k + N/2]) (spectral line one symbol rate
+//                     apart; its phase is -2 pi Rs tau for a delay tau);
 //   k_pam_prefix      one CTA: FP64 prefix sums of the clock products;
 //   k_pam_phase       cbar_j = sum of c_i over |i - j| <= 52 inside the frame (a difference of
 //                     prefix sums), phi_j = arg cbar_j, the unwrap step of block j (-1 if
@@ -78,32 +79,56 @@ struct PamArgs {
     int M;
 };
 
+// A CTA takes the block pair (2b, 2b + 1), whose real inputs go through one complex transform as
+// z = v_{2b} + j v_{2b+1} (block 2b + 1 starts N/2 later). The matched filter is real and even, so
+// the filtered spectra split as A[k] = (Z[k] + conj Z[N-k]) / 2 and B[k] = (Z[k] - conj Z[N-k]) / 2j.
+template <int K>
+__device__ __forceinline__ void pam_pair_spectrum(const PamArgs& a, float2* sm, int64_t start) {
+    constexpr int N = 1 << K, HOP = N / 2;
+    auto sample = [&](int64_t s) -> float {
+        return (s >= 0 && s < a.S) ? fmaf(a.scale, (float)a.codes[s], a.dc) : 0.0f;
+    };
+    auto load = [&](int idx) -> float2 { return make_float2(sample(start + idx), sample(start + HOP + idx)); };
+    const float* __restrict__ H = a.H;
+    auto store = [&](int k, float2 v) { sm[fft_pad(k)] = cscale(v, __ldg(&H[k])); };
+    fft_run<K, -1, true, true>(sm, a.tw, load, store);
+    __syncthreads();
+}
+
 template <int K>
 __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_pam_clock(PamArgs a) {
     constexpr int N = 1 << K, HOP = N / 2, LEAD = N / 4;
     constexpr int NT = (N / 16 < 32) ? 32 : N / 16;
     extern __shared__ float2 sm[];
-    __shared__ float2 red[NT / 32];
-    const int j = blockIdx.x;
-    const int64_t start = (int64_t)j * HOP - LEAD;
-    auto load = [&](int idx) -> float2 {
-        const int64_t s = start + idx;
-        return make_float2((s >= 0 && s < a.S) ? fmaf(a.scale, (float)a.codes[s], a.dc) : 0.0f, 0.0f);
-    };
-    const float* __restrict__ H = a.H;
-    auto store = [&](int k, float2 v) { sm[fft_pad(k)] = cscale(v, __ldg(&H[k])); };
-    fft_run<K, -1, true, true>(sm, a.tw, load, store);
+    __shared__ float2 red[2][NT / 32];
+    const int j0 = 2 * blockIdx.x;
+    pam_pair_spectrum<K>(a, sm, (int64_t)j0 * HOP - LEAD);
+    float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+    for (int k = threadIdx.x; k < N / 2; k += NT) {
+        const float2 zk = sm[fft_pad(k)], zm = sm[fft_pad((N - k) & (N - 1))];
+        const float2 zh = sm[fft_pad(k + N / 2)], zhm = sm[fft_pad(N / 2 - k)];
+        // A = (z + conj zm) / 2, B = (z - conj zm) / 2j = ((z.y + zm.y) / 2, (zm.x - z.x) / 2)
+        const float2 ak = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 bk = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        const float2 ah = make_float2(0.5f * (zh.x + zhm.x), 0.5f * (zh.y - zhm.y));
+        const float2 bh = make_float2(0.5f * (zh.y + zhm.y), 0.5f * (zhm.x - zh.x));
+        acc0 = cmacc(acc0, ak, ah);
+        acc1 = cmacc(acc1, bk, bh);
+    }
+    acc0.x = warp_sum(acc0.x);
+    acc0.y = warp_sum(acc0.y);
+    acc1.x = warp_sum(acc1.x);
+    acc1.y = warp_sum(acc1.y);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = acc0;
+        red[1][threadIdx.x >> 5] = acc1;
+    }
     __syncthreads();
-    float2 acc = make_float2(0.0f, 0.0f);
-    for (int k = threadIdx.x; k < N / 2; k += NT) acc = cmacc(acc, sm[fft_pad(k)], sm[fft_pad(k + N / 2)]);
-    acc.x = warp_sum(acc.x);
-    acc.y = warp_sum(acc.y);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float2 t = red[0];
-        for (int i = 1; i < NT / 32; ++i) t = cadd(t, red[i]);
-        a.c[j] = t;
+    if (threadIdx.x < 2) {
+        const int h = threadIdx.x;
+        float2 t = red[h][0];
+        for (int i = 1; i < NT / 32; ++i) t = cadd(t, red[h][i]);
+        if (j0 + h < a.J) a.c[j0 + h] = t;
     }
 }
 
@@ -190,48 +215,68 @@ __global__ void __launch_bounds__(1024) k_pam_wind(PamArgs a, int quarter) {
     }
 }
 
+// the block pair again: split, each block's ramp exp(-j phi f / Rs) / N, recombined as
+// Y = A R_2b + j B R_2b+1 so that one inverse transform gives block 2b's samples as its real part
+// and block 2b + 1's as its imaginary part (both spectra stay Hermitian)
 template <int K>
 __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_pam_correct(PamArgs a) {
     constexpr int N = 1 << K, HOP = N / 2, LEAD = N / 4;
+    constexpr int NT = (N / 16 < 32) ? 32 : N / 16;
     extern __shared__ float2 sm[];
-    const int j = blockIdx.x;
-    const int64_t start = (int64_t)j * HOP - LEAD;
-    auto load = [&](int idx) -> float2 {
-        const int64_t s = start + idx;
-        return make_float2((s >= 0 && s < a.S) ? fmaf(a.scale, (float)a.codes[s], a.dc) : 0.0f, 0.0f);
-    };
-    const float* __restrict__ H = a.H;
-    const float ph = a.phi[j];
-    constexpr float inv_half = 2.0f / (float)N;
-    auto store = [&](int k, float2 v) {
-        const int ks = k < N / 2 ? k : (k == N / 2 ? 0 : k - N);
-        float sn, cs;
-        __sincosf(-ph * (float)ks * inv_half, &sn, &cs);    // |argument| <= pi
-        sm[fft_pad(k)] = cscale(cmul(v, make_float2(cs, sn)), __ldg(&H[k]) * (1.0f / (float)N));
-    };
-    fft_run<K, -1, true, true>(sm, a.tw, load, store);
+    const int j0 = 2 * blockIdx.x;
+    const bool has1 = j0 + 1 < a.J;
+    pam_pair_spectrum<K>(a, sm, (int64_t)j0 * HOP - LEAD);
+    const float ph0 = a.phi[j0], ph1 = has1 ? a.phi[j0 + 1] : 0.0f;
+    constexpr float inv_half = 2.0f / (float)N, inv_n = 1.0f / (float)N;
+    for (int k = threadIdx.x; k <= N / 2; k += NT) {
+        const int m = (N - k) & (N - 1);
+        const float2 zk = sm[fft_pad(k)], zm = sm[fft_pad(m)];
+        const float2 ak = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 bk = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        const float ks = k < N / 2 ? (float)k : 0.0f;
+        float s0, c0, s1, c1;
+        __sincosf(-ph0 * ks * inv_half, &s0, &c0);    // |argument| <= pi
+        __sincosf(-ph1 * ks * inv_half, &s1, &c1);
+        const float2 p = cscale(cmul(ak, make_float2(c0, s0)), inv_n);
+        const float2 q = cscale(cmul(bk, make_float2(c1, s1)), inv_n);
+        sm[fft_pad(k)] = make_float2(p.x - q.y, p.y + q.x);                 // p + j q
+        if (m != k) sm[fft_pad(m)] = make_float2(p.x + q.y, q.x - p.y);     // conj p + j conj q
+    }
     __syncthreads();
-    const long long o0 = a.off[j];
-    const long long n = a.off[j + 1] - o0;
-    double bsum = 0.0;                                    // this block's outputs, for the mean
+    const long long o0 = a.off[j0], n0 = a.off[j0 + 1] - o0;
+    const long long o1 = has1 ? a.off[j0 + 1] : 0, n1 = has1 ? a.off[j0 + 2] - o1 : 0;
+    double bsum0 = 0.0, bsum1 = 0.0;                       // the blocks' outputs, for the mean
     auto store_out = [&](int idx, float2 v) {
         const int r = idx - LEAD;
-        if (r >= 0 && !(r & 1) && (r >> 1) < n) {
-            a.y[o0 + (r >> 1)] = v.x;
-            bsum += (double)v.x;
+        if (r >= 0 && !(r & 1)) {
+            const int i = r >> 1;
+            if (i < n0) {
+                a.y[o0 + i] = v.x;
+                bsum0 += (double)v.x;
+            }
+            if (i < n1) {
+                a.y[o1 + i] = v.y;
+                bsum1 += (double)v.y;
+            }
         }
     };
     SmemLoad sl{sm};
     fft_run<K, +1, false, true>(sm, a.tw, sl, store_out);
-    constexpr int NT = (N / 16 < 32) ? 32 : N / 16;
-    __shared__ double red[NT / 32];
-    for (int o = 16; o; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bsum;
+    __shared__ double red[2][NT / 32];
+    for (int o = 16; o; o >>= 1) {
+        bsum0 += __shfl_xor_sync(0xffffffffu, bsum0, o);
+        bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = bsum0;
+        red[1][threadIdx.x >> 5] = bsum1;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 2) {
+        const int h = threadIdx.x;
         double t = 0.0;
-        for (int i = 0; i < NT / 32; ++i) t += red[i];
-        a.part[j] = t;
+        for (int i = 0; i < NT / 32; ++i) t += red[h][i];
+        if (j0 + h < a.J) a.part[j0 + h] = t;
     }
 }
 
@@ -310,11 +355,12 @@ cudaError_t launch_pam_t(const PamArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_pam_correct<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_pam_clock<K><<<a.J, threads, smem, s>>>(a);
+    const int pairs = (a.J + 1) / 2;
+    k_pam_clock<K><<<pairs, threads, smem, s>>>(a);
     k_pam_prefix<<<1, 1024, 0, s>>>(a);
     k_pam_phase<<<(a.J + 127) / 128, 128, 0, s>>>(a);
     k_pam_wind<<<1, 1024, 0, s>>>(a, N / 4);
-    k_pam_correct<K><<<a.J, threads, smem, s>>>(a);
+    k_pam_correct<K><<<pairs, threads, smem, s>>>(a);
     k_pam_final<<<1, 1024, 0, s>>>(a, 0, 0, a.J);
     k_pam_deviation<<<kParts, kRedThreads, 0, s>>>(a);
     k_pam_final<<<1, 1024, 0, s>>>(a, 1, a.J, kParts);
