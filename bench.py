@@ -950,9 +950,9 @@ def ingest_arm(args) -> None:
 
 
 def pam_arm(args) -> None:
-    """The IM/DD PAM-4 chain with FD clock recovery (rx_pam_process, 9 launches: clock products, prefix
-    sums, 105-block averages and phases, winding scan and offsets, correction + variable-rate
-    extraction, mean, deviation and its final sum, decision)
+    """The IM/DD PAM-4 chain with FD clock recovery (rx_pam_process, 8 launches: clock products,
+    105-block averages and phases, winding scan and offsets, correction + variable-rate extraction,
+    mean, deviation and its final sum, decision)
     on the paper's buffer of 2^22 12-bit samples at 2 samples/symbol (2 GBd PAM-4, 50 % roll-off, a
     25 ppm receiver clock offset, 20 dB SNR). Line rate: output symbols x 2 bits per buffer time.
     Algorithmic HBM bytes per input sample: 2 (codes, read by two passes: 4) + 4 (y written, read
@@ -1003,10 +1003,10 @@ def pam_arm(args) -> None:
         "data": "synthetic", "sample_rate_gsa_s": S / (t * 1e-3) / 1e9, "paper_realtime_gsa_s": 4.0,
         "config": {"workload": f"pam4-2gbd-{S}", "samples": S, "fft": 1024, "clock_ppm": 25.0,
                    "l2": "flushed between timed steps (512 MiB write)"},
-        "roofline": {"kernel": "rx_pam_process (9 launches)", "bound": "hbm",
+        "roofline": {"kernel": "rx_pam_process (8 launches)", "bound": "hbm",
                      "achieved": hbm_bytes / (t * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
                      "frac": hbm_bytes / (t * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0), "traffic": None},
-        "symbol_error_rate_interior": ser, "outputs": n, "gpu_launches": 9 * args.steps,
+        "symbol_error_rate_interior": ser, "outputs": n, "gpu_launches": 8 * args.steps,
         "clocks": clk.summary()}))
 
 

@@ -6,10 +6,9 @@
 //                     -> times sqrt(2) RRC(f) -> each block's clock product
 //                     c_j = sum_{k < N/2} X[k] conj(X[k + N/2]) (spectral line one symbol rate
 //                     apart; its phase is -2 pi Rs tau for a delay tau);
-//   k_pam_prefix      one CTA: FP64 prefix sums of the clock products;
-//   k_pam_phase       cbar_j = sum of c_i over |i - j| <= 52 inside the frame (a difference of
-//                     prefix sums), phi_j = arg cbar_j, the unwrap step of block j (-1 if
-//                     phi_j - phi_{j-1} > pi, +1 if < -pi);
+//   k_pam_window      cbar_j = sum of c_i over |i - j| <= 52 inside the frame (a difference of
+//                     FP64 prefix sums over each CTA's tile of products), phi_j = arg cbar_j, the
+//                     unwrap step of block j (-1 if phi_j - phi_{j-1} > pi, +1 if < -pi);
 //   k_pam_wind        one CTA: winding numbers w_j (integer prefix sum of the steps), each block's
 //                     output count N/4 + w_{j+1} - w_j (N/4 for the last block, clipped to the
 //                     frame) and offset;
@@ -47,7 +46,6 @@ struct rx_pam {
     int* step = nullptr;         // [J] unwrap steps
     int* w = nullptr;            // [J] winding numbers
     long long* off = nullptr;    // [J + 1] output offsets (off[J] = outputs)
-    double2* pre = nullptr;      // [J + 1] prefix sums of the clock products
     double* part = nullptr;      // [J] per-block output sums, then [kParts] deviation partials
     double* stat = nullptr;      // [2] mean, mean absolute deviation
 };
@@ -70,7 +68,6 @@ struct PamArgs {
     int* step;
     int* w;
     long long* off;
-    double2* pre;
     float* y;
     uint8_t* levels;
     double* part;
@@ -132,54 +129,65 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16) k_p
     }
 }
 
-// One CTA of 1024 threads: FP64 prefix sums P_i = c_0 + ... + c_{i-1} of the clock products, so that
-// each 105-block average is P_hi - P_lo. Thread t owns the contiguous blocks [t per, (t + 1) per).
-__global__ void __launch_bounds__(1024) k_pam_prefix(PamArgs a) {
-    __shared__ double2 dpart[1024];
-    const int t = threadIdx.x, J = a.J;
-    const int per = (J + 1023) / 1024;
-    const int lo = min(J, t * per), hi = min(J, lo + per);
-    double2 s = make_double2(0.0, 0.0);
-    for (int i = lo; i < hi; ++i) {
-        const float2 v = a.c[i];
-        s.x += (double)v.x;
-        s.y += (double)v.y;
+// 105-block averages, phases and unwrap steps, CTA b for blocks [128 b, 128 b + 128): one warp scans
+// the CTA's 233 clock products (the tile, the block before it and 52 on either side; zero outside
+// the frame, which clips the window at the frame edges) in FP64, so that each average is a
+// difference of two tile-local prefix sums; the steps compare each phase with the one before.
+constexpr int kWinTile = 128;
+__global__ void __launch_bounds__(kWinTile) k_pam_window(PamArgs a) {
+    constexpr int L = kWinTile + 1 + 2 * kAvgHalf;            // 233 products
+    constexpr int CH = (L + 31) / 32;                         // per lane
+    __shared__ double2 Q[L + 1];                              // Q[m] = sum of the first m products
+    __shared__ double ph[kWinTile + 1];
+    const int j0 = blockIdx.x * kWinTile;
+    const int base = j0 - 1 - kAvgHalf;                       // block of tile product 0
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, m0 = lane * CH;
+        double2 loc[CH];
+        double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int m = m0 + u, i = base + m;
+            const float2 v = (m < L && i >= 0 && i < a.J) ? a.c[i] : make_float2(0.0f, 0.0f);
+            s.x += (double)v.x;
+            s.y += (double)v.y;
+            loc[u] = s;
+        }
+        double2 inc = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double nx = __shfl_up_sync(0xffffffffu, inc.x, o), ny = __shfl_up_sync(0xffffffffu, inc.y, o);
+            if (lane >= o) {
+                inc.x += nx;
+                inc.y += ny;
+            }
+        }
+        const double2 ex = make_double2(inc.x - s.x, inc.y - s.y);
+        if (lane == 0) Q[0] = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (m0 + u < L) Q[m0 + u + 1] = make_double2(ex.x + loc[u].x, ex.y + loc[u].y);
     }
-    dpart[t] = s;
     __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        const double2 v = t >= d ? dpart[t - d] : make_double2(0.0, 0.0);
-        __syncthreads();
-        dpart[t].x += v.x;
-        dpart[t].y += v.y;
-        __syncthreads();
+    // ph[r] = phase of block j0 - 1 + r, whose window is tile products r .. r + 104
+    for (int r = threadIdx.x; r <= kWinTile; r += kWinTile) {
+        const int j = j0 - 1 + r;
+        if (j >= 0 && j < a.J) {
+            const double2 h = Q[r + 2 * kAvgHalf + 1], l = Q[r];
+            ph[r] = atan2(h.y - l.y, h.x - l.x);
+        }
     }
-    double2 run = t > 0 ? dpart[t - 1] : make_double2(0.0, 0.0);
-    for (int i = lo; i < hi; ++i) {
-        a.pre[i] = run;
-        const float2 v = a.c[i];
-        run.x += (double)v.x;
-        run.y += (double)v.y;
+    __syncthreads();
+    const int j = j0 + threadIdx.x;
+    if (j < a.J) {
+        const double p = ph[threadIdx.x + 1];
+        a.phi[j] = (float)p;
+        int st = 0;
+        if (j > 0) {
+            const double d = p - ph[threadIdx.x];
+            st = d > M_PI ? -1 : (d < -M_PI ? 1 : 0);
+        }
+        a.step[j] = st;
     }
-    if (t == 1023) a.pre[J] = run;
-}
-
-// per block: phi_j = arg(P_{j+53} - P_{j-52}) (clipped to the frame) and the unwrap step
-__global__ void k_pam_phase(PamArgs a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.J) return;
-    auto phase = [&](int i) -> double {
-        const double2 h = a.pre[min(a.J, i + kAvgHalf + 1)], l = a.pre[max(0, i - kAvgHalf)];
-        return atan2(h.y - l.y, h.x - l.x);
-    };
-    const double p = phase(j);
-    a.phi[j] = (float)p;
-    int st = 0;
-    if (j > 0) {
-        const double d = p - phase(j - 1);
-        st = d > M_PI ? -1 : (d < -M_PI ? 1 : 0);
-    }
-    a.step[j] = st;
 }
 
 // One CTA of 1024 threads: winding numbers (integer prefix sum of the steps), output offsets
@@ -357,8 +365,7 @@ cudaError_t launch_pam_t(const PamArgs& a, cudaStream_t s) {
     }
     const int pairs = (a.J + 1) / 2;
     k_pam_clock<K><<<pairs, threads, smem, s>>>(a);
-    k_pam_prefix<<<1, 1024, 0, s>>>(a);
-    k_pam_phase<<<(a.J + 127) / 128, 128, 0, s>>>(a);
+    k_pam_window<<<(a.J + kWinTile - 1) / kWinTile, kWinTile, 0, s>>>(a);
     k_pam_wind<<<1, 1024, 0, s>>>(a, N / 4);
     k_pam_correct<K><<<pairs, threads, smem, s>>>(a);
     k_pam_final<<<1, 1024, 0, s>>>(a, 0, 0, a.J);
@@ -416,7 +423,6 @@ rx_status rx_pam_create(int32_t fft_size, int32_t levels, double rrc_rolloff, fl
               cudaMalloc(&p->step, sizeof(int) * J) == cudaSuccess &&
               cudaMalloc(&p->w, sizeof(int) * J) == cudaSuccess &&
               cudaMalloc(&p->off, sizeof(long long) * (J + 1)) == cudaSuccess &&
-              cudaMalloc(&p->pre, sizeof(double2) * (J + 1)) == cudaSuccess &&
               cudaMalloc(&p->part, sizeof(double) * (J + kParts)) == cudaSuccess &&
               cudaMalloc(&p->stat, sizeof(double) * 2) == cudaSuccess;
     if (ok)
@@ -451,7 +457,6 @@ rx_status rx_pam_process(rx_pam* p, const uint16_t* d_codes, int64_t n_samples, 
     a.step = p->step;
     a.w = p->w;
     a.off = p->off;
-    a.pre = p->pre;
     a.y = d_y;
     a.levels = d_levels;
     a.part = p->part;
@@ -482,7 +487,7 @@ rx_status rx_pam_get(rx_pam* p, int32_t which, void* d_dst, int64_t bytes, rx_st
 
 void rx_pam_destroy(rx_pam* p) {
     if (!p) return;
-    void* ptrs[] = {p->tw, p->H, p->c, p->phi, p->step, p->w, p->off, p->pre, p->part, p->stat};
+    void* ptrs[] = {p->tw, p->H, p->c, p->phi, p->step, p->w, p->off, p->part, p->stat};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
