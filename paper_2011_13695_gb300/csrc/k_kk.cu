@@ -28,7 +28,6 @@
 
 struct rx_kk {
     int K = 10;
-    double tone_over_fs = 0.0;
     long long inc = 0;           // tone phase per sample, 2^-64 turns
     float scale = 1.0f, dc = 0.0f, i_min = 0.0f;
     float2* tw = nullptr;        // FFT twiddles
@@ -48,10 +47,6 @@ struct KkArgs {
     const float2* tw;
     const float* H;
 };
-
-__device__ __forceinline__ float kk_intensity(const KkArgs& a, int64_t s) {
-    return fmaxf(fmaf(a.scale, (float)a.codes[s], a.dc), a.i_min);
-}
 
 // One CTA takes the block pair (2b, 2b + 1): block 2b starts at 2b N/2 - N/4, block 2b + 1 N/2 later,
 // so the pair reads a window of 3N/2 samples. Their log-amplitudes are real, and -j sgn(k) maps the
@@ -201,7 +196,6 @@ rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff
     rx_kk* k = new (std::nothrow) rx_kk();
     if (!k) return RX_ENOMEM;
     k->K = K;
-    k->tone_over_fs = tone_over_fs;
     k->inc = std::llrint(std::ldexp(tone_over_fs, 64));
     k->scale = code_scale;
     k->dc = dc_offset;

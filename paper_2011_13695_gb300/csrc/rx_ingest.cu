@@ -29,7 +29,6 @@
 #include <chrono>
 #include <cstdint>
 #include <cstring>
-#include <new>
 #include <thread>
 #include <vector>
 
@@ -48,7 +47,6 @@ struct Slot {
     float* out = nullptr;           // [(2N + S) / 2] complex
     float* h_out = nullptr;         // pinned [S / 2] complex when the caller wants no outputs
     std::atomic<int64_t> finish_ns{0};
-    int64_t buffer = -1;
     Clock::time_point ready;
     bool busy = false;
 };
@@ -162,7 +160,6 @@ extern "C" rx_status rx_ingest_run(rx_kk* kk, const uint16_t* h_source, int64_t 
         }
         next_slot = pick + 1;
         Slot& s = slots[pick];
-        s.buffer = i;
         s.ready = ready;
         s.busy = true;
         s.finish_ns.store(0, std::memory_order_relaxed);
