@@ -1007,7 +1007,36 @@ def pam_arm(args) -> None:
                      "achieved": hbm_bytes / (t * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
                      "frac": hbm_bytes / (t * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0), "traffic": None},
         "symbol_error_rate_interior": ser, "outputs": n, "gpu_launches": 8 * args.steps,
-        "clocks": clk.summary()}))
+        "clocks": clk.summary(), "cpu_baseline": None if args.no_cpu_baseline else pam_cpu_baseline(S)}))
+
+
+def pam_oracle_worker(n_samp: int, reps: int) -> dict:
+    """The oracle's PAM chain on the pam workload's buffer."""
+    from oracle import pam
+    from synth.pam import PAMLink, generate_pam
+    p = PAMLink(levels=4, n_samp=n_samp, clock_ppm=25.0, timing=0.2, snr_db=20.0)
+    fr = generate_pam(p, SEED)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        pam.pam_receive(fr.codes, fr.scale, fr.dc, 4, p.rolloff, 1024)
+        times.append(time.perf_counter() - t0)
+    return dict(times=times, samples=n_samp)
+
+
+def pam_cpu_baseline(n_samp: int, reps: int = 3) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.pam_oracle_worker(%d, %d)))" % (ROOT, n_samp, reps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode:
+        raise RuntimeError(r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    t = statistics.median(res["times"])
+    return {"value": res["samples"] / t / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+            "sample": f"the pam buffer, {res['samples']} samples, Steps 1-9 in FP64 NumPy, single thread, "
+                      f"median of {reps}"}
 
 
 def kk_oracle_worker(n_sym: int, reps: int) -> dict:
