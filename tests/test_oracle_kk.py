@@ -138,3 +138,29 @@ def test_noiseless_link_end_to_end(m):
     evm_db = 10 * np.log10(np.mean(np.abs(ys - s) ** 2))
     assert evm_db < -25.0, evm_db
     assert np.array_equal(qam.decide(ys, m), qam.decide(s, m))
+
+
+def test_joined_buffers_reproduce_the_whole_stream():
+    """The ingest reading: buffers of S samples, each processed as a frame joined to the previous
+    buffer's last 2N codes (zero codes before the first) with the downshift counted from the stream
+    index, give outputs N/2 .. N/2 + S/2 of every joined frame that continue one another and equal the
+    front end on the whole stream as one frame; only the stream's first N/2 outputs (2 samples/symbol)
+    differ, where the first buffer's carry holds no data."""
+    N, S, nb = 1024, 8192, 4
+    fr = generate_kk(KKLink(bits_per_sym=4, n_sym=nb * S // 4, cspr_db=11.0, snr_db=25.0), seed=6)
+    p = fr.link
+    f = p.tone_offset / p.fs
+    _, y_ref = kk.kk_receive(fr.codes, fr.scale, fr.dc, 1e-6, f, p.rolloff, N)
+    carry = np.zeros(2 * N, dtype=np.uint16)
+    outs = []
+    for i in range(nb):
+        joined = np.concatenate([carry, fr.codes[i * S:(i + 1) * S]])
+        carry = joined[S:S + 2 * N].copy()
+        a, l = kk.front_end(joined, fr.scale, fr.dc, 1e-6)
+        n = np.arange(joined.size) + i * S - 2 * N
+        E = a * np.exp(1j * kk.hilbert_os(l, N)) * np.exp(-2j * np.pi * f * n)
+        outs.append(kk.matched_decimate(E, N, p.rolloff)[N // 2:N // 2 + S // 2])
+    got = np.concatenate(outs)[N // 2:]          # stream outputs from index 0
+    ref = y_ref[:got.size]
+    assert np.max(np.abs(got[N // 2:] - ref[N // 2:])) < 1e-9 * np.max(np.abs(ref))
+    assert np.max(np.abs(got[:N // 2] - ref[:N // 2])) > 1e-3 * np.max(np.abs(ref))

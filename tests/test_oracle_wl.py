@@ -144,3 +144,17 @@ def test_segment_schedule_matches_the_serial_run_when_converged():
     y_ser, _ = mimo.dd_lms_wl(x, h, 64 * 300, L_b, 10 ** 6, 0, 2, 0.004, 0.004)
     y_seg, _ = mimo.dd_lms_wl(x, h, 64 * 300, L_b, 16, 4, 2, 0.004, 0.004)
     assert np.max(np.abs(y_seg - y_ser)) < 1e-6
+
+
+def test_generator_iq_imbalance_is_the_branch_model():
+    """x -> mu x + nu conj(x) with (mu, nu) = iq_coefficients(eps, phi) is the I/Q branch model
+    I' = (1 + eps)(I cos phi - Q sin phi), Q' = (1 - eps)(Q cos phi - I sin phi)."""
+    rng = np.random.default_rng(4)
+    for eps, phi in ((0.1, 0.08), (-0.2, 0.3), (0.0, -0.5)):
+        mu, nu = iq_coefficients(eps, phi)
+        for _ in range(5):
+            I, Q = rng.normal(size=2)
+            x = complex(I, Q)
+            y = mu * x + nu * np.conj(x)
+            assert abs(y.real - (1 + eps) * (I * np.cos(phi) - Q * np.sin(phi))) < 1e-12
+            assert abs(y.imag - (1 - eps) * (Q * np.cos(phi) - I * np.sin(phi))) < 1e-12
