@@ -1,7 +1,8 @@
 // IM/DD PAM-M chain with frequency-domain clock recovery (Sec. III, Steps 1-9) and its C entry points.
 //
 // At 2 samples/symbol, overlap-save blocks of N = 2^K samples (block j from j N/2 - N/4, zero
-// outside the frame), one CTA per block, the in-CTA Stockham FFT of rx_fft.cuh:
+// outside the frame); the FFT passes take one CTA per block pair (the two real blocks go through
+// one complex transform) and use the in-CTA Stockham FFT of rx_fft.cuh:
 //   k_pam_clock<K>    code -> v = scale code + dc -> FFT (two real blocks per complex transform)
 //                     -> times sqrt(2) RRC(f) -> each block's clock product
 //                     c_j = sum_{k < N/2} X[k] conj(X[k + N/2]) (spectral line one symbol rate
@@ -13,7 +14,8 @@
 //                     output count N/4 + w_{j+1} - w_j (N/4 for the last block, clipped to the
 //                     frame) and offset;
 //   k_pam_correct<K>  the FFT again (recomputing is cheaper than a 64 MB spectrum round trip),
-//                     times sqrt(2) RRC(f) exp(-j phi_j f / Rs) / N, inverse FFT; the block's
+//                     split into the pair's spectra, each times sqrt(2) RRC(f) exp(-j phi_j f / Rs)
+//                     / N, recombined, one inverse FFT for both blocks; each block's
 //                     outputs are the real parts of its samples N/4 + 2 i, written at its offset
 //                     (variable rate: 255, 256 or 257 symbols per block), and their sum;
 //   k_pam_final, k_pam_deviation   buffer-wise mean from the blocks' sums, then the mean absolute
