@@ -12,7 +12,7 @@ chain applies them, with no blocking, fusion or reordering:
   A0 ``cdc.power_scale``            power normalisation of the ADC samples
   A1 ``cdc.overlap_save``           overlap-save FD chromatic-dispersion compensation
   A2 ``mimo.cma_acquire``           2x2 butterfly FIR, CMA block updates (acquisition)
-  A3 ``mimo.foe_code``              differential 4th-power frequency-offset estimate
+  A3 ``mimo.foe_code``              frequency offset: 4th-power periodogram peak + phase slope
   A4 ``mimo.dd_lms``                segmented block DD-LMS with in-loop 4th-power phase
   A5 ``bps.blind_phase_search``     BPS, integer unwrap, derotation
   A6 ``decide.resolve`` / ``count`` ambiguity resolution, Gray demap, BER/EVM

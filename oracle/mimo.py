@@ -123,22 +123,35 @@ def output_correlation(y: np.ndarray, max_lag: int) -> float:
     return best
 
 
-def cma_acquire(xbuf, T, L_b, n_blocks, mu, R2, off=0):
-    """Returns (taps, y_acq, rho, reran)."""
-    h, y = cma_pass(xbuf, identity_taps(T), L_b, n_blocks, mu, R2, off)
+def rebuild_second_row(h: np.ndarray) -> np.ndarray:
+    """Singularity recovery: keep the first row, replace the second by the
+    time-reversed conjugates h_yy[k] = conj h_xx[T-1-k], h_yx[k] = -conj h_xy[T-1-k].
+
+    About the centre tap the reversal conjugates the frequency response, so
+    the rebuilt 2x2 response is [[H_xx, H_xy], [-conj H_xy, conj H_xx]] at every
+    frequency: a scaled unitary whose second row extracts the polarisation the
+    first row rejects.
+    """
+    h2 = h.copy()
+    h2[1, 1, :] = np.conj(h[0, 0, ::-1])
+    h2[1, 0, :] = -np.conj(h[0, 1, ::-1])
+    return h2
+
+
+def cma_acquire(xbuf, T, L_b, n_blocks, mu, R2, off=0, h0=None):
+    """Returns (taps, y_acq, rho, reran). ``h0`` (default: identity taps) starts the first pass."""
+    h, y = cma_pass(xbuf, identity_taps(T) if h0 is None else h0, L_b, n_blocks, mu, R2, off)
     rho = output_correlation(y, (T - 1) // 2)
     reran = False
     if rho > 0.5:
-        h2 = h.copy()
-        h2[1, 1, :] = np.conj(h[0, 0, ::-1])
-        h2[1, 0, :] = -np.conj(h[0, 1, ::-1])
-        h, y = cma_pass(xbuf, h2, L_b, n_blocks, mu, R2, off)
+        h, y = cma_pass(xbuf, rebuild_second_row(h), L_b, n_blocks, mu, R2, off)
         reran = True
     return h, y, rho, reran
 
 
 # ----------------------------------------------------------------------------
-# A3: frequency offset (Leven et al. 2007, differential 4th power)
+# A3: frequency offset (4th-power periodogram peak, then the least-squares
+# slope of the per-block 4th-power phase)
 # ----------------------------------------------------------------------------
 
 def foe_window(xbuf, h, n_acq, T, off):

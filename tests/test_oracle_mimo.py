@@ -154,3 +154,104 @@ def test_decision_margin_by_brute_force():
         dist = lambda v: np.min(np.abs(v[..., None] - bounds), axis=-1)
         want = np.minimum(dist(u.real), dist(u.imag)).min(axis=-1)
         assert np.allclose(got, want, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# A2 singularity recovery (reading: outputs correlated beyond 0.5 at a lag up
+# to (T-1)/2 -> second row rebuilt from the first, acquisition rerun once)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [-7, -3, 0, 1, 5, 7])
+def test_output_correlation_of_a_delayed_copy_is_the_overlap_fraction(d):
+    """y1 = e^{j theta} y0 delayed by d on unit-modulus symbols: |rho_d| = (L - |d|) / L exactly.
+
+    Over the second half (L samples) the lag-d sum runs over the L - |d| aligned samples, each
+    |y0|^2 = 1, and both energies are L; the other lags are sums of random QPSK products, far lower.
+    """
+    rng = np.random.default_rng(11 + d)
+    L = 512
+    y0 = qam.alphabet(2)[rng.integers(0, 4, size=2 * L)]
+    y0 = y0 / np.abs(y0)
+    y1 = np.exp(1j * 0.7) * np.roll(y0, d)
+    got = mimo.output_correlation(np.stack([y0, y1]), 7)
+    assert got == pytest.approx((L - abs(d)) / L, abs=1e-12)
+
+
+def test_output_correlation_ignores_lags_beyond_the_window_and_independent_outputs():
+    rng = np.random.default_rng(12)
+    L = 2048
+    y0 = np.exp(1j * np.pi / 2 * rng.integers(0, 4, size=2 * L))
+    assert mimo.output_correlation(np.stack([y0, np.roll(y0, 9)]), 7) < 0.15
+    y1 = np.exp(1j * np.pi / 2 * rng.integers(0, 4, size=2 * L))
+    assert mimo.output_correlation(np.stack([y0, y1]), 7) < 0.15
+
+
+def _freq_response(h, w):
+    """H[..., q, p] at radian frequencies w [F], taps indexed about the centre tap."""
+    T = h.shape[-1]
+    c = (T - 1) // 2
+    E = np.exp(-1j * np.outer(w, np.arange(T) - c))          # [F, T]
+    return np.einsum("qpk,fk->fqp", h, E)
+
+
+@pytest.mark.parametrize("T", [3, 15, 21])
+def test_rebuilt_second_row_makes_a_scaled_unitary_at_every_frequency(T):
+    """[[H_xx, H_xy], [-conj H_xy, conj H_xx]]: W W^H = (|H_xx|^2 + |H_xy|^2) I for all w.
+
+    A dropped minus sign, a missing time reversal or a missing conjugate each leave an
+    off-diagonal term on frequency-selective taps.
+    """
+    rng = np.random.default_rng(T)
+    h = rng.normal(size=(2, 2, T)) + 1j * rng.normal(size=(2, 2, T))
+    h2 = mimo.rebuild_second_row(h)
+    assert np.array_equal(h2[0], h[0])
+    w = np.linspace(-np.pi, np.pi, 97)
+    W = _freq_response(h2, w)
+    G = W @ np.conj(np.swapaxes(W, -1, -2))
+    p = np.abs(W[:, 0, 0]) ** 2 + np.abs(W[:, 0, 1]) ** 2
+    assert np.max(np.abs(G - p[:, None, None] * np.eye(2))) < 1e-10 * np.max(p)
+
+
+def test_rebuilt_second_row_inverts_the_other_polarisation_of_a_jones_matrix():
+    """First row = first row of J^H for J = [[a, b], [-conj b, conj a]] (|a|^2 + |b|^2 = 1):
+    the rebuilt matrix is J^H itself, so W J = I."""
+    rng = np.random.default_rng(13)
+    for _ in range(5):
+        v = rng.normal(size=2) + 1j * rng.normal(size=2)
+        a, b = v / np.linalg.norm(v)
+        J = np.array([[a, b], [-np.conj(b), np.conj(a)]])
+        T = 9
+        h = np.zeros((2, 2, T), dtype=np.complex128)
+        h[0, :, (T - 1) // 2] = np.conj(J.T)[0]
+        W = mimo.rebuild_second_row(h).sum(axis=-1)
+        assert np.max(np.abs(W @ J - np.eye(2))) < 1e-13
+
+
+def test_cma_rerun_recovers_from_a_singular_start():
+    """Both rows started on the same polarisation lock onto one source (rho ~ 1); the rebuild
+    and rerun then demultiplex: -40 dB crosstalk through the channel's Jones matrix and
+    uncorrelated outputs, as from the identity start."""
+    p = _noiseless_link()
+    fr = generate(p, 2)
+    cfg = RxConfig(bits_per_sym=2, symbol_rate=p.symbol_rate, length=p.length, fft_size=1024,
+                   n_taps=15, lms_block=64, bps_phases=32, bps_window=64)
+    T, L_b, n_cma = cfg.n_taps, cfg.lms_block, cfg.cma_blocks
+    scale = cdc.power_scale(fr.samples, 2 * n_cma * L_b)
+    H = cdc.cdc_response(cfg.fft_size, cfg.fs, cfg.dispersion, cfg.length, cfg.wavelength,
+                         cfg.symbol_rate, cfg.rrc_rolloff, cfg.sps)
+    buf = cdc.overlap_save(fr.samples * scale[:, None], H)
+    h0 = np.zeros((2, 2, T), dtype=np.complex128)
+    h0[:, 0, (T - 1) // 2] = 1.0                                # both outputs read polarisation x
+    h1, y1 = mimo.cma_pass(buf, h0, L_b, n_cma, cfg.mu_cma, qam.cma_radius(2), 0)
+    assert mimo.output_correlation(y1, (T - 1) // 2) > 0.99       # the first pass is singular
+    h, y, rho, reran = mimo.cma_acquire(buf, T, L_b, n_cma, cfg.mu_cma, qam.cma_radius(2), 0, h0=h0)
+    assert reran and rho > 0.99
+    assert mimo.output_correlation(y, (T - 1) // 2) < 0.1
+    G = (h.sum(axis=-1) * scale[None, :]) @ fr.jones
+    if np.abs(G[0, 1]) > np.abs(G[0, 0]):
+        G = G[::-1]
+    D = G / np.abs(np.diag(G)).mean()
+    assert np.max(np.abs(D - np.diag(np.diag(D)))) < 1e-2       # crosstalk below -40 dB
+    # constant modulus reached on both outputs over the second half of the rerun
+    half = y[:, y.shape[1] // 2:]
+    assert np.mean(np.abs(np.abs(half) ** 2 - 1.0)) < 0.05

@@ -132,3 +132,29 @@ def test_pam_correction_ramp_sign_is_caught(monkeypatch):
     monkeypatch.setattr(opam, "correct", lambda X, phi: real(X, -phi))
     with pytest.raises(AssertionError):
         test_oracle_pam.test_variable_rate_extraction_is_continuous(25.0, 0.1)
+
+
+def _rebuild_variant(sign, reverse, conj):
+    def f(h):
+        h2 = h.copy()
+        r = (lambda v: v[::-1]) if reverse else (lambda v: v)
+        c = np.conj if conj else (lambda v: v)
+        h2[1, 1, :] = c(r(h[0, 0]))
+        h2[1, 0, :] = sign * c(r(h[0, 1]))
+        return h2
+    return f
+
+
+@pytest.mark.parametrize("variant", [(1.0, True, True), (-1.0, False, True), (-1.0, True, False)],
+                         ids=["no-minus", "no-reversal", "no-conjugate"])
+def test_wrong_singularity_rebuild_is_caught(monkeypatch, variant):
+    monkeypatch.setattr(omimo, "rebuild_second_row", _rebuild_variant(*variant))
+    with pytest.raises(AssertionError):
+        test_oracle_mimo.test_rebuilt_second_row_makes_a_scaled_unitary_at_every_frequency(15)
+
+
+def test_lag_zero_only_singularity_check_is_caught(monkeypatch):
+    real = omimo.output_correlation
+    monkeypatch.setattr(omimo, "output_correlation", lambda y, max_lag: real(y, 0))
+    with pytest.raises(AssertionError):
+        test_oracle_mimo.test_output_correlation_of_a_delayed_copy_is_the_overlap_fraction(5)
