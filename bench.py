@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "dp-16qam-32gbd"
 SEED = 1
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT_GB300 = 152
+SM_COUNT_GB300 = 152          # used only when no device is visible (CPU tests of the arithmetic)
 FP32_LANES_PER_SM = 128
 
 
@@ -225,18 +225,45 @@ def _traffic(stage: str):
     return rec[2] if sha == rec[1] else None
 
 
+def fp32_peak(pk: dict) -> tuple[float, float, int, str]:
+    """(FP32 flop/s peak, lane-op/s peak, SM count, note). The measured FMA rate when the bench
+    measured it (``measure_fp32_peak``), else the unit count: SMs x 128 lanes x 2 flops x max clock."""
+    sms = int(pk.get("sm_count", SM_COUNT_GB300))
+    if pk.get("fp32_flops"):
+        f = float(pk["fp32_flops"])
+        return f, f / 2, sms, (f"measured: FMA-chain microkernel on every SM ({pk.get('fp32_form', '')}), "
+                               f"{f / 1e12:.1f} TFLOP/s at SM clock {pk.get('fp32_sm_mhz')} MHz")
+    clock_mhz = pk.get("sm_max_mhz", 2070.0)
+    lanes = sms * FP32_LANES_PER_SM * clock_mhz * 1e6
+    return 2 * lanes, lanes, sms, f"nominal: {sms} SMs x 128 lanes x 2 flops x {clock_mhz:.0f} MHz"
+
+
+def measure_fp32_peak(rx, stream_handle, device_index: int = 0) -> dict:
+    """FP32 FMA throughput of this GPU through the library's microkernel (scalar and packed FP32x2
+    FMA chains on every SM), the SM clock sampled during it: the denominator of the ALU rooflines."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    best = {}
+    with ClockSampler(device_index) as clk:
+        for packed in (False, True):
+            rates = [rx.rx_fp32_fma_rate(packed, 1 << 16, stream_handle)[0] for _ in range(3)]
+            best["packed" if packed else "scalar"] = max(rates)
+    form = max(best, key=best.get)
+    return {"fp32_flops": best[form], "fp32_form": form, "fp32_scalar_flops": best["scalar"],
+            "fp32_packed_flops": best["packed"], "sm_count": sms, "fp32_sm_mhz": clk.summary().get("sm_mhz")}
+
+
 def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz: float | None) -> dict:
     """Roofline of one stage's dominant kernel: algorithmic work of one launch over its duration.
 
-    FP32 arithmetic is counted in flops (an FMA is 2) against the FMA pipes' peak (152 SMs x 128
-    lanes x 2 flops x max SM clock); BPS, whose work is compare/round/select as much as FMA, in
-    lane-operations against 152 x 128 x clock; HBM-bound stages in compulsory bytes against the
-    measured copy bandwidth."""
+    FP32 arithmetic is counted in flops (an FMA is 2) against the FMA pipes' peak (measured by the
+    FMA-chain microkernel when available, else SMs x 128 lanes x 2 flops x max SM clock); BPS, whose
+    work is compare/round/select as much as FMA, in lane-operations against half that flop rate;
+    HBM-bound stages in compulsory bytes against the measured copy bandwidth."""
     rxs = w["rx"]
     m = rxs["bits_per_sym"]
     T, Lb = rxs["n_taps"], rxs["lms_block"]
-    clock_mhz = pk.get("sm_max_mhz", 2070.0)
-    lanes = SM_COUNT_GB300 * FP32_LANES_PER_SM * clock_mhz * 1e6
+    flop_peak, lane_peak, sms, note = fp32_peak(pk)
     t = ms * 1e-3
     lms_flops_per_symbol = 2 * (16 * T + 16 * T)          # 2 rows x (outputs + gradient), 2T complex MACs each
     alu = {
@@ -248,24 +275,23 @@ def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz:
     }
     if stage in alu:
         name, flops = alu[stage]
-        peak = 2 * lanes / 1e12
+        peak = flop_peak / 1e12
         a = flops / t / 1e12
         r = {"kernel": name, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-             "traffic": _traffic(stage), "algorithmic_flops": flops,
-             "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+             "traffic": _traffic(stage), "algorithmic_flops": flops, "peak_note": "FP32 FMA pipes, " + note}
         if stage in ("cma", "dd_acq"):
             # a serial chain of block steps, one CTA (holding a whole SM) per output row: the fraction of
             # the two SMs it can occupy is the meaningful one
             r["occupied_sms"] = 2
-            r["frac_of_occupied_sms"] = a / (peak * 2 / SM_COUNT_GB300)
+            r["frac_of_occupied_sms"] = a / (peak * 2 / sms)
         return r
     if stage == "bps":
         ops = 2 * n_sym * rxs["bps_phases"] * 16          # lane-ops per (symbol, test phase)
-        peak = lanes / 1e12
+        peak = lane_peak / 1e12
         a = ops / t / 1e12
         return {"kernel": "k_bps", "bound": "alu", "achieved": a, "peak": peak, "unit": "Tops/s",
                 "frac": a / peak, "traffic": _traffic(stage), "algorithmic_ops": ops,
-                "peak_note": "152 SMs x 128 lanes x max SM clock"}
+                "peak_note": "lane-operations: half the FP32 flop peak, " + note}
     # FD compensation: the acquisition's blocks first ("cdc": its window plus one FFT of reach), the
     # rest beside the acquisition ("cdc_rest"); the power estimate reads the CMA window only
     acq_samples = min(2 * n_sym, 2 * max(rxs["cma_blocks"], rxs["dd_acq_blocks"]) * Lb + rxs["fft_size"])
@@ -299,6 +325,22 @@ def hbm_step_roofline(bytes_per_step: int, ms_per_step: float, pk: dict) -> dict
     peak = pk.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "bytes_per_step": bytes_per_step, "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": gbs / peak}
+
+
+def chain_flops_per_dp_symbol(rxs: dict) -> float:
+    """Algorithmic FP32 flops per DP symbol of the chain: the FD compensation's FFT pair and multiply
+    ((20 log2 N_fft + 12) x 4 per symbol: two polarisations, 2 samples/symbol, half of each block kept),
+    the butterfly's outputs and gradient (64 T) and BPS (36 B)."""
+    import math
+    return (20 * math.log2(rxs["fft_size"]) + 12) * 4 + 64 * rxs["n_taps"] + 36 * rxs["bps_phases"]
+
+
+def alu_step_roofline(w: dict, n_sym: int, ms_per_step: float, pk: dict) -> dict:
+    flops = n_sym * chain_flops_per_dp_symbol(w["rx"])
+    peak = fp32_peak(pk)[0]
+    a = flops / (ms_per_step * 1e-3)
+    return {"bound": "alu", "flops_per_step": flops, "achieved": a / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": a / peak}
 
 
 def replica_line_rate(world: int, bits_per_step: int, steps: int, total_ms: float) -> float:
@@ -406,7 +448,7 @@ def our_arm(args) -> None:
         if dist:
             dist.destroy_process_group()
         return
-    pk = peaks()
+    pk = dict(peaks(), **measure_fp32_peak(rx, stream.cuda_stream, local))
     csum = clk.summary()
     per_stage = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
     # the dominant kernel: the longest stage that is one kernel launch ("cma" also holds the
@@ -414,7 +456,8 @@ def our_arm(args) -> None:
     single = {k: v for k, v in per_stage.items() if k in ("dd_acq", "lms", "bps", "cdc", "cdc_rest", "count", "power")}
     dom = max(single or per_stage, key=(single or per_stage).get)
     roof = stage_roofline(dom, per_stage[dom], w, N, pk, csum.get("sm_mhz"))
-    roof["peak_source"] = "fallback" if pk.get("fallback") else "measured (MEASURED_PEAKS.json) / nominal unit count"
+    roof["peak_source"] = ("fallback" if pk.get("fallback") else
+                           "measured: HBM copy from MEASURED_PEAKS.json, FP32 FMA rate by the FMA-chain microkernel")
     value = replica_line_rate(world, bits_per_step, args.steps, total_ms)
     e2e = replica_line_rate(world, bits_per_step, args.steps, e2e_ms) if e2e_ms == e2e_ms else None
     line = {
@@ -433,6 +476,12 @@ def our_arm(args) -> None:
         # the decided bits out) over the step time; the chain is ALU- and latency-bound, so this is small
         "hbm_roofline": hbm_step_roofline(int(x_host.nbytes + ref_host.nbytes + 2 * rcv.words(N) * 4),
                                           total_ms / args.steps, pk),
+        # the whole step against the FP32 FMA peak: the chain's algorithmic flops per DP symbol (FFT pair
+        # of the FD compensation, butterfly outputs and gradient, BPS) over the step time
+        "alu_roofline": alu_step_roofline(w, N, total_ms / args.steps, pk),
+        "fp32_peak": {"tflops": pk["fp32_flops"] / 1e12, "form": pk["fp32_form"],
+                      "scalar_tflops": pk["fp32_scalar_flops"] / 1e12, "packed_tflops": pk["fp32_packed_flops"] / 1e12,
+                      "sm_count": pk["sm_count"], "sm_mhz": pk["fp32_sm_mhz"]},
         "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
         # every stage against its own bound (algorithmic work of the stage over its time)
         "stage_roofline": {k: {"bound": r["bound"], "frac": round(r["frac"], 5), "unit": r["unit"],
@@ -557,7 +606,9 @@ def batch_arm(args) -> None:
     rx.rx_batch_destroy(b)
 
 
-CNN_FWD_FLOP = 2 * 9 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 4)                 # per DP symbol
+# per position of the sequence: one position is one DP symbol (4 input channels I_x, Q_x, I_y, Q_y),
+# so a frame of N symbols per polarisation is N positions
+CNN_FWD_FLOP = 2 * 9 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 4)
 CNN_TRAIN_FLOP = 2 * CNN_FWD_FLOP + 2 * 9 * (64 * 64 + 64 * 64 + 64 * 4)         # + weight and data gradients
 
 
@@ -647,8 +698,8 @@ def learned_arm(args) -> None:
     tc = sum(cnn_ms) / len(cnn_ms)
     pk = peaks()
     bf16_peak = pk.get("bf16_tflops", 1900.0)
-    fwd_tflops = 2 * N * CNN_FWD_FLOP / (tc * 1e-3) / 1e12
-    train_tflops = steps * 2 * window * CNN_TRAIN_FLOP / (train_ms * 1e-3) / 1e12
+    fwd_tflops = N * CNN_FWD_FLOP / (tc * 1e-3) / 1e12
+    train_tflops = steps * window * CNN_TRAIN_FLOP / (train_ms * 1e-3) / 1e12
     bits = 2 * m * N
     pe.close()
     line = {
@@ -716,7 +767,7 @@ def cnn_arm(args) -> None:
     t = sum(ms) / len(ms)
     pk = peaks()
     bf16_peak = pk.get("bf16_tflops", 1900.0)
-    tflops = 2 * N * CNN_FWD_FLOP / (t * 1e-3) / 1e12
+    tflops = N * CNN_FWD_FLOP / (t * 1e-3) / 1e12
     hbm_bytes = N * ((16 + 128) + 2 * (128 + 128) + (128 + 16 + 16))
     print(json.dumps({
         "metric": "post-equaliser forward", "value": 2 * N / (t * 1e-3) / 1e9, "unit": "GSym/s (DP symbols x 2)",
@@ -780,9 +831,9 @@ def wl_arm(args) -> None:
     a_l = 1.0 / np.sqrt(2.0 * (L * L - 1) / 3.0)
     dec = lambda v: (np.clip(np.round((v / a_l + (L - 1)) / 2), 0, L - 1) * 2 - (L - 1)) * a_l
     evm_db = 10 * np.log10(np.mean(np.abs(u - dec(u.real) - 1j * dec(u.imag)) ** 2))
-    pk = peaks()
-    lanes = SM_COUNT_GB300 * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
-    peak = 2 * lanes / 1e12
+    pk = dict(peaks(), **measure_fp32_peak(rx, stream.cuda_stream))
+    flop_peak, _, _, peak_note = fp32_peak(pk)
+    peak = flop_peak / 1e12
     flops = N * (1 + wu / seg) * 128 * T
     nseg = (N + seg * Lb - 1) // (seg * Lb)
     achieved = flops / (t * 1e-3) / 1e12
@@ -794,8 +845,7 @@ def wl_arm(args) -> None:
                    "seg_blocks": seg, "warmup_blocks": wu, "l2": "flushed between timed steps (512 MiB write)"},
         "roofline": {"kernel": wl_kernel_name(T, Lb, th), "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic("wl") if (N, T, th) == (1 << 20, 21, 0) else None,
-                     "algorithmic_flops": flops, "ctas": 2 * nseg,
-                     "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock"},
+                     "algorithmic_flops": flops, "ctas": 2 * nseg, "peak_note": "FP32 FMA pipes, " + peak_note},
         "evm_db_after_8192_symbols": float(evm_db), "gpu_launches": args.steps, "clocks": clk.summary(),
         "cpu_baseline": None if args.no_cpu_baseline else wl_cpu_baseline(T)}))
 
@@ -895,7 +945,7 @@ def kk_arm(args) -> None:
     pk = peaks()
     hbm_bytes = S * (2 + 8 + 8 + 4)
     fft_flops = (S / (N / 2)) * (2 * 5 * N * 10 + 5 * N * 10 + 5 * (N // 2) * 9)
-    lanes = SM_COUNT_GB300 * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    flop_peak = fp32_peak(dict(pk, **measure_fp32_peak(rx, torch.cuda.current_stream().cuda_stream)))[0]
     hbm_gbs = hbm_bytes / (t * 1e-3) / 1e9
     tflops = fft_flops / (t * 1e-3) / 1e12
     print(json.dumps({
@@ -908,7 +958,7 @@ def kk_arm(args) -> None:
         "roofline": {"kernel": "k_kk_phase + k_kk_mf (whole front end)", "bound": "hbm", "achieved": hbm_gbs,
                      "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s", "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0),
                      "traffic": None, "algorithmic_bytes": hbm_bytes, "fft_tflops": tflops,
-                     "fft_frac_of_fp32_peak": tflops / (2 * lanes / 1e12)},
+                     "fft_frac_of_fp32_peak": tflops / (flop_peak / 1e12)},
         "evm_db": float(evm_db), "symbol_error_rate": ser, "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(), "cpu_baseline": None if args.no_cpu_baseline else kk_cpu_baseline(n_sym)}))
 

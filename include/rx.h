@@ -82,7 +82,7 @@ typedef struct rx_config {
     int32_t seg_blocks;         /* blocks per DD-LMS segment */
     int32_t warmup_blocks;      /* warm-up blocks ahead of every segment but the first */
     int32_t bps_phases;         /* B test phases, 2..64 */
-    int32_t bps_window;         /* W symbols, even, 2..64 */
+    int32_t bps_window;         /* W symbols, a power of two, 2..64 */
     int32_t edge_skip;          /* E: symbols left out of the counts at each frame edge */
     int32_t sync_len;           /* symbols of the alignment window, 1..32768 */
     int32_t max_delay;          /* alignment searches delays in [-max_delay, max_delay] */
@@ -290,6 +290,18 @@ rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, in
 void rx_pe_destroy(rx_pe* p);
 
 /*
+ * rx_fp32_fma_rate: measured FP32 FMA throughput of the current device (no
+ * paper counterpart; the roofline of the chain's FP32-bound stages uses it).
+ * One launch of every SM's worth of CTAs, each thread running eight
+ * independent FMA chains of `iters` steps (packed != 0: fma.rn.f32x2, two
+ * FMAs per instruction), timed with CUDA events after a warm-up launch.
+ * *flops_per_s receives 2 flops per FMA over the timed launch; *ms
+ * (nullable) its duration. Blocking (synchronises `stream`); allocates
+ * nothing. RX_EINVAL for iters < 1 or a NULL flops_per_s.
+ */
+rx_status rx_fp32_fma_rate(int32_t packed, int32_t iters, double* flops_per_s, double* ms, rx_stream_t stream);
+
+/*
  * rx_carrier_recovery_static: stage A5 alone (blind phase search, integer
  * unwrap, derotation) on one single frame of equalised symbols, for callers
  * that cannot allocate device memory when they process data (a real-time
@@ -304,9 +316,13 @@ void rx_pe_destroy(rx_pe* p);
  * The working memory is one file-scope device array of RX_STATIC_MAX_SYMBOLS
  * symbols per polarisation (about 2.6 MB) that every device loading the
  * library keeps until the process exits; the function allocates nothing.
- * Its first call on a device looks up that array's device address (make it
- * before any stream capture). Every call shares the array: calls that
- * overlap on the GPU (other streams, other threads) race with each other.
+ * Its first call on a device looks up that array's device address, and with
+ * lazy module loading (the CUDA default) it also loads the kernels it runs:
+ * make one warm-up call on each device before any stream capture. Every call
+ * shares the array (each call clears the carried unwrap state it uses):
+ * calls that overlap on the GPU (other streams, other threads) race with
+ * each other. `stream` must belong to the current device (RX_EINVAL
+ * otherwise: the array's address is looked up per device).
  * RX_EINVAL for n_sym < 1, n_sym > RX_STATIC_MAX_SYMBOLS or invalid BPS
  * parameters (bps_phases 2..64, bps_window a power of two 2..64).
  * Asynchronous on `stream`.
@@ -405,7 +421,11 @@ void rx_kk_destroy(rx_kk* k);
  * [i S/2 - N/2, (i + 1) S/2 - N/2) (an N/2-sample delay), written
  * to h_out + i * S floats when h_out is not NULL (host, n_buffers * S/2
  * complex; dropped buffers leave theirs untouched). h_source (and h_out) are
- * page-locked for the run unless they already are. Blocking; it allocates
+ * page-locked (cudaHostRegister) at the start of every call and unlocked at
+ * its end unless they already are page-locked: that costs host time before
+ * pacing starts (it is not in the latency statistics), and a caller that
+ * runs repeatedly passes memory it has already page-locked (cudaHostAlloc or
+ * its own cudaHostRegister) to skip it. Blocking; it allocates
  * its slots before the first buffer and frees them at the end. RX_EINVAL for
  * buffer_samples not a multiple of N/2 or below 2N or above 2^30,
  * source_samples not a multiple of buffer_samples, sample_rate_hz <= 0,

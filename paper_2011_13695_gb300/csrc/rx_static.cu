@@ -56,6 +56,10 @@ extern "C" rx_status rx_carrier_recovery_static(const float* d_y, int64_t n_sym,
     if (bps_window < 2 || bps_window > 64 || (bps_window & (bps_window - 1))) return RX_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RX_ECUDA;
+    // the scratch address is the current device's: a stream of another device would get the wrong one
+    int sdev = dev;
+    if (cudaStreamGetDevice((cudaStream_t)stream_, &sdev) != cudaSuccess) return RX_ECUDA;
+    if (sdev != dev) return RX_EINVAL;
     StaticScratch* sc = nullptr;
     {
         std::lock_guard<std::mutex> g(g_addr_mutex);

@@ -30,7 +30,7 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
            "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl",
            "rx_kk_create", "rx_kk_process", "rx_kk_destroy", "rx_ingest_run", "rx_pam_create", "rx_pam_process",
-           "rx_pam_get", "rx_pam_destroy")
+           "rx_pam_get", "rx_pam_destroy", "rx_fp32_fma_rate")
 RX_PAM_CLOCK, RX_PAM_PHASE, RX_PAM_WINDING, RX_PAM_OFFSETS, RX_PAM_STATS = range(5)
 RX_STATIC_MAX_SYMBOLS = 262144
 
@@ -130,6 +130,7 @@ def lib() -> C.CDLL:
             "rx_pam_process": (i32, [vp, vp, i64, vp, vp, vp, vp]),
             "rx_pam_get": (i32, [vp, i32, vp, i64, vp]),
             "rx_pam_destroy": (None, [vp]),
+            "rx_fp32_fma_rate": (i32, [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -330,6 +331,14 @@ def rx_pe_train_step(p: int, d_z: int, d_target: int, T: int, lr: float, d_loss:
 
 def rx_pe_destroy(p: int) -> None:
     lib().rx_pe_destroy(p)
+
+
+def rx_fp32_fma_rate(packed: bool, iters: int, stream: int | None) -> tuple[float, float]:
+    """Measured FP32 FMA throughput (flops/s, ms of the timed launch); see include/rx.h."""
+    f, t = C.c_double(), C.c_double()
+    _check(lib().rx_fp32_fma_rate(1 if packed else 0, iters, C.byref(f), C.byref(t), stream or None),
+           "rx_fp32_fma_rate")
+    return f.value, t.value
 
 
 def rx_carrier_recovery_static(d_y: int, n_sym: int, bits_per_sym: int, bps_phases: int, bps_window: int, d_z: int,

@@ -31,22 +31,80 @@ def device_input(samples: np.ndarray, fmt: int = 0):
     return torch.from_numpy(np.ascontiguousarray(codes)).cuda(), vals, step
 
 
-def run_gpu_frames(rx_settings: dict, frames: list, refs: list | None = None, fmt: int = 0, streaming=False,
-                   buffers=("y", "z", "bstar", "m", "cdc", "taps_cma", "taps_init", "taps_last", "y_foe", "scale")):
-    """Process frames (host complex128 [2, S] each) through librx; returns per-frame dicts."""
+def stream_inputs(samples: np.ndarray, fmt: int, n_frames: int):
+    """A stream's samples quantised once over the whole stream (one int8 step, as a digitiser has),
+    then cut into frames: [(device tensor, oracle values, input_scale)] per frame."""
+    import torch
+    from synth.channel import quantise_int8, to_fp16
+    S = samples.shape[1] // n_frames
+    if fmt == 0:
+        c = np.ascontiguousarray(samples.astype(np.complex64))
+        return [(torch.from_numpy(np.ascontiguousarray(c[:, f * S:(f + 1) * S]).view(np.float32)).cuda(),
+                 c[:, f * S:(f + 1) * S].astype(np.complex128), 1.0) for f in range(n_frames)]
+    if fmt == 1:
+        h = to_fp16(samples)
+        vals = h[..., 0].astype(np.float64) + 1j * h[..., 1].astype(np.float64)
+        return [(torch.from_numpy(np.ascontiguousarray(h[:, f * S:(f + 1) * S]).view(np.int16)).cuda(),
+                 vals[:, f * S:(f + 1) * S], 1.0) for f in range(n_frames)]
+    codes, delta = quantise_int8(samples)
+    step = float(delta[0])
+    vals = (codes[..., 0].astype(np.float64) + 1j * codes[..., 1].astype(np.float64)) * np.float64(np.float32(step))
+    return [(torch.from_numpy(np.ascontiguousarray(codes[:, f * S:(f + 1) * S])).cuda(), vals[:, f * S:(f + 1) * S],
+             step) for f in range(n_frames)]
+
+
+DEFAULT_BUFFERS = ("y", "z", "bstar", "m", "cdc", "taps_cma", "taps_init", "taps_last", "y_foe", "scale")
+
+
+def handle_buffers(h: int, N: int, T: int, streaming: bool = False, buffers=DEFAULT_BUFFERS) -> dict:
+    """The parity export of any librx handle (a single handle or a batch channel's) after a frame of N
+    symbols, as host arrays shaped the way the oracle's FrameResult holds them."""
     import torch
     from paper_2011_13695_gb300 import rx
-    from paper_2011_13695_gb300.receiver import Receiver
-    n_max = max(f.shape[1] // 2 for f in frames)
-    inputs = [device_input(f, fmt) for f in frames]
-    scale = inputs[0][2]
-    rcv = Receiver(rx_settings, n_max, input_format=fmt, input_scale=scale, streaming=streaming)
+    from paper_2011_13695_gb300.receiver import _BUF_LAYOUT
     names = {"y": rx.RX_BUF_Y, "z": rx.RX_BUF_Z, "bstar": rx.RX_BUF_BSTAR, "m": rx.RX_BUF_M, "cdc": rx.RX_BUF_CDC,
              "taps_cma": rx.RX_BUF_TAPS_CMA, "taps_init": rx.RX_BUF_TAPS_INIT, "taps_last": rx.RX_BUF_TAPS_LAST,
              "y_foe": rx.RX_BUF_Y_FOE, "scale": rx.RX_BUF_SCALE, "y_acq": rx.RX_BUF_Y_ACQ}
+    hist = (T - 1) // 2 + 2 * (((T - 1) // 2 + 1) // 2)
+    res = {}
+    for b in buffers:
+        which = names[b]
+        nbytes = rx.rx_buffer_bytes(h, which)
+        dt = _BUF_LAYOUT[which]
+        esz = torch.tensor([], dtype=dt).element_size()
+        buf = torch.empty(nbytes // esz, dtype=dt, device="cuda")
+        rx.rx_get_buffer(h, which, buf.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.current_stream().synchronize()
+        t = buf.cpu().numpy()
+        if b in ("y", "z", "bstar", "m"):
+            t = t.reshape(2, -1)[:, :N]
+        elif b == "cdc":
+            t = t.reshape(2, -1)
+            t = t[:, hist:hist + 2 * N] if streaming else t[:, :2 * N]
+        elif b.startswith("taps"):
+            t = t.reshape(2, 2, T)
+        elif b == "y_foe":
+            t = t.reshape(2, -1)
+        res[b] = t
+    return res
+
+
+COUNTERS = ("bits_counted", "bit_errors", "symbols_counted", "symbol_errors", "evm_num", "evm_den")
+
+
+def run_gpu_frames(rx_settings: dict, frames: list, refs: list | None = None, fmt: int = 0, streaming=False,
+                   buffers=DEFAULT_BUFFERS, inputs=None):
+    """Process frames (host complex128 [2, S] each) through librx; returns per-frame dicts.
+    ``inputs``: device inputs already made (``stream_inputs``) instead of quantising each frame alone."""
+    import torch
+    from paper_2011_13695_gb300.receiver import Receiver
+    n_max = max(f.shape[1] // 2 for f in frames)
+    if inputs is None:
+        inputs = [device_input(f, fmt) for f in frames]
+    scale = inputs[0][2]
+    rcv = Receiver(rx_settings, n_max, input_format=fmt, input_scale=scale, streaming=streaming)
     out = []
     T = rx_settings["n_taps"]
-    hist = (T - 1) // 2 + 2 * (((T - 1) // 2 + 1) // 2)
     for i, (x, vals, _) in enumerate(inputs):
         N = frames[i].shape[1] // 2
         ref = torch.from_numpy(refs[i].astype(np.int32).view(np.int32)).cuda() if refs is not None else None
@@ -56,23 +114,9 @@ def run_gpu_frames(rx_settings: dict, frames: list, refs: list | None = None, fm
         rcv.process(x, N, ref, bits)
         st = rcv.stats()
         res = dict(stats=st, oracle_input=vals, n=N)
-        res["delta"] = {k: st[k] - before[k] for k in ("bits_counted", "bit_errors", "symbols_counted",
-                                                      "symbol_errors", "evm_num", "evm_den")}
+        res["delta"] = {k: st[k] - before[k] for k in COUNTERS}
         res["bits"] = bits.cpu().numpy().view(np.uint32).reshape(2, words)
-        for b in buffers:
-            t = rcv.buffer(names[b]).cpu().numpy()
-            if b in ("y", "z"):
-                t = t.reshape(2, -1)[:, :N]
-            elif b in ("bstar", "m"):
-                t = t.reshape(2, -1)[:, :N]
-            elif b == "cdc":
-                t = t.reshape(2, -1)
-                t = t[:, hist:hist + 2 * N] if streaming else t[:, :2 * N]
-            elif b.startswith("taps"):
-                t = t.reshape(2, 2, T)
-            elif b == "y_foe":
-                t = t.reshape(2, -1)
-            res[b] = t
+        res.update(handle_buffers(rcv.h, N, T, streaming, buffers))
         out.append(res)
     rcv.close()
     return out

@@ -23,7 +23,7 @@ def librx():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(rx_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(rx_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():

@@ -1,8 +1,12 @@
 """GPU: batched channels in one graph launch (tuned FFT size and LMS CTA size).
 
 Every channel of the batch must give exactly what a single handle with the
-same (tuned) configuration gives on the same frame, and two channels are
-checked against the FP64 oracle with the tuned FFT size.
+same (tuned) configuration gives on the same frame, and every channel is held
+to the single-frame parity rules against the FP64 oracle with the tuned FFT
+size (y and z within 1e-4 relative RMS, FO code equal, b* near-ties only,
+decisions differing on at most 1e-5 of the symbols, exact bit-error counts).
+Frames take each channel's drawn length up to 2^18 symbols per polarisation
+(the oracle's time bound); the drawn lengths are 2^16 to 2^20.
 """
 
 import numpy as np
@@ -12,11 +16,11 @@ from oracle.receiver import Receiver as OracleRx
 from oracle.receiver import RxConfig
 from synth import generate
 from synth.workloads import batch_channels
-from tests.gpu_util import rel_rms
+from tests.gpu_util import COUNTERS, handle_buffers
 
 pytestmark = pytest.mark.gpu
 
-N_TEST = 1 << 14
+N_MAX = 1 << 18
 
 
 @pytest.fixture(scope="module")
@@ -28,7 +32,7 @@ def batch_setup():
     chans = batch_channels(42)
     frames, xs, refs, outs, cfgs = [], [], [], [], []
     for ch in chans:
-        link = ch["link"].with_(n_sym=min(ch["link"].n_sym, N_TEST))
+        link = ch["link"].with_(n_sym=min(ch["link"].n_sym, N_MAX))
         fr = generate(link, ch["seed"])
         frames.append(fr)
         x = np.ascontiguousarray(fr.samples.astype(np.complex64))
@@ -40,11 +44,17 @@ def batch_setup():
     b = rx.rx_batch_create(cfgs)
     n_sym = [fr.params.n_sym for fr in frames]
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):                                  # capture, then a replay
+    first = {}
+    for r in range(2):                                  # capture (and run), then a replay
         rx.rx_batch_process(b, [t.data_ptr() for t in xs], n_sym, [t.data_ptr() for t in refs],
                             [t.data_ptr() for t in outs], stream)
-    torch.cuda.synchronize()
-    yield dict(b=b, chans=chans, frames=frames, xs=xs, refs=refs, outs=outs, n_sym=n_sym)
+        torch.cuda.synchronize()
+        if r == 0:
+            # one frame's counters and every buffer of each channel after the first pass
+            for i, ch in enumerate(chans):
+                first[i] = dict(stats=rx.rx_batch_stats(b, i), bits=outs[i].cpu().numpy().view(np.uint32).copy(),
+                                **handle_buffers(rx.rx_batch_handle(b, i), n_sym[i], ch["rx"]["n_taps"]))
+    yield dict(b=b, chans=chans, frames=frames, xs=xs, refs=refs, outs=outs, n_sym=n_sym, first=first)
     rx.rx_batch_destroy(b)
 
 
@@ -81,28 +91,25 @@ def test_batch_equals_single_handles(batch_setup):
         rx.rx_destroy(h)
 
 
-@pytest.mark.parametrize("i", [0, 5])
-def test_batch_channels_against_the_oracle(batch_setup, i):
-    import torch
+@pytest.mark.parametrize("i", range(16))
+def test_batch_channel_against_the_oracle(batch_setup, i, record_property):
     from paper_2011_13695_gb300 import rx
-    from oracle import qam as oqam
+    from tests.test_gpu_parity import check_frame
     b = batch_setup["b"]
     cfg = rx.rx_batch_config(b, i)
     ch = batch_setup["chans"][i]
     fr = batch_setup["frames"][i]
     N = batch_setup["n_sym"][i]
     rxs = dict(ch["rx"], fft_size=cfg.fft_size)
-    h = rx.rx_batch_handle(b, i)
-    nbytes = rx.rx_buffer_bytes(h, rx.RX_BUF_Y)
-    yb = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
-    rx.rx_get_buffer(h, rx.RX_BUF_Y, yb.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
-    y = yb.cpu().numpy().view(np.complex64).reshape(2, -1)[:, :N]
-    x = fr.samples.astype(np.complex64).astype(np.complex128)
-    r = OracleRx(RxConfig.from_dict(rxs)).process(x, fr.ref_words)
-    if r.fo_margin < 0.01:
-        pytest.skip("oracle FO estimate within 1 % of a rounding boundary")
-    assert rel_rms(y, r.y) < 1e-4
-    bits = batch_setup["outs"][i].cpu().numpy().view(np.uint32).reshape(2, -1)
-    want = oqam.pack_words(__import__("oracle.decide", fromlist=["x"]).demap_output(r.z, r.sync, cfg.bits_per_sym))
-    assert np.mean(bits != want) < 1e-3
+    f = batch_setup["first"][i]
+    st = f["stats"]
+    g = dict(f, n=N, oracle_input=fr.samples.astype(np.complex64).astype(np.complex128),
+             delta={k: st[k] for k in COUNTERS}, bits=f["bits"].reshape(2, -1))
+    ocfg = RxConfig.from_dict(rxs)
+    r = OracleRx(ocfg).process(g["oracle_input"], fr.ref_words)
+    dev = check_frame(g, r, ocfg, fr.ref_words)
+    for k, v in dev.items():
+        record_property(k, v)
+    print(f"\nchannel {i} ({ch['link'].symbol_rate / 1e9:.0f} GBd, m {ch['link'].bits_per_sym}, N {N}, "
+          f"T {ch['rx']['n_taps']}, FFT {cfg.fft_size}): y {dev['y_rel_rms']:.2e}, z {dev['z_rel_rms']:.2e}, "
+          f"decisions differ {dev['decisions_differ']}")
