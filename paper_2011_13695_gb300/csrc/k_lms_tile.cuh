@@ -1,0 +1,362 @@
+// Block LMS (A2 CMA / DD acquisition, A4 segments) as a register-tiled kernel:
+// the same recursion and segment schedule as k_lms_fast.cuh and the generic
+// kernel in k_mimo.cu (Sec. IV-D's adaptive equaliser with block updates):
+//   y[n] = sum_p sum_k h_p[k] x_p[2n + c - k]                       (taps of the block's start)
+//   e[n] = y (R2 - |y|^2)  (CMA)   or   dec(y e^{-j psi}) e^{j psi} - y,  psi = arg(-sum y^4) / 4  (DD)
+//   h_p[k] += mu sum_n e[n] conj(x_p[2n + c - k])
+// for one output row q per CTA (blockIdx.y) and one segment per CTA (blockIdx.x).
+//
+// Why another mapping: the acquisition is a serial chain of block steps on one
+// CTA, so its speed is the latency of one step. Here every lane holds a tile
+// of OPL consecutive outputs x IM taps of one (polarisation, tap parity, tap
+// half) class, and the same OPL + IM - 1 samples in registers feed both the
+// tile's output products and its gradient products (one 16-byte shared-memory
+// load per two samples, no per-term loads). Per block step:
+//   1. outputs: each lane forms its tile's partial outputs with packed FP32x2
+//      FMAs (tap components staged as (hx, hx, hy, hy)); the eight classes of
+//      one output subset sit in lanes differing in bits 0-2, which a
+//      reduce-scatter by shuffles sums, leaving each output in one or two lanes;
+//   2. errors: CMA locally; DD takes the block phase from a warp sum of y^4,
+//      one barrier and the per-warp partials in a fixed order;
+//   3. the errors go through a warp-private shared-memory row (no barrier) to
+//      the lanes of their output subset, which form their tile's gradient
+//      partials from the samples still in registers; a reduce-scatter over the
+//      four output subsets (lane bits 3-4) leaves a quarter of the class's
+//      partials per lane, written per warp;
+//   4. barrier; one thread per tap component adds the warps' partials in a
+//      fixed order and updates its tap (held in a register) and the staged
+//      copy; barrier.
+// Windows are split by sample parity (tap k reads parity k % 2) and
+// double-buffered: a block's window is written at the start of the previous
+// step, derotated by the per-block and per-position phasor tables, and the
+// next one is requested from global memory at the same time.
+#pragma once
+
+#include "rx_kernels.h"
+
+template <int NT, int T, int LB>
+struct LmsTileShape {
+    static constexpr int NW = NT / 32;
+    static constexpr int OPL = LB / (NW * 4);              // outputs per lane
+    static constexpr int C = (T - 1) / 2;
+    static constexpr int NE = C + 1, NO = C;                // taps of even / odd index
+    static constexpr int up_even(int v) { return v + (v & 1); }
+    static constexpr int G0 = up_even((NE + 1) / 2);        // even taps of group 0 (group 1: the rest)
+    static constexpr int G1 = up_even((NO + 1) / 2);        // odd taps of group 0
+    static constexpr int IM = G0 > G1 ? G0 : G1;            // tap slots per lane (even)
+    static constexpr int R = OPL + IM;                      // sample registers (OPL + IM - 1 used; even)
+    static constexpr int PADL = 2 * IM + 2;                 // zero pad below logical index 0
+    // origin of the parity-r array: makes every lane's first sample 16-byte aligned
+    static constexpr int org(int r) { return PADL + ((PADL + C - r + 1) & 1); }
+    static constexpr int PS0 = org(0) + LB + C + 4;         // length of one parity array (float2)
+    static constexpr int PS = ((PS0 + 11) / 16) * 16 + 4;   // = 4 mod 16: the four arrays start in
+                                                            // different bank quarters
+    static constexpr int XW = 2 * LB + T - 1;               // window samples per polarisation
+    static constexpr int PF = (2 * XW + NT - 1) / NT;       // window registers per thread
+    static constexpr int TS = IM + 1;                       // staged tap row stride (float4, odd)
+    static constexpr int NBT = 256;                         // derotation bases of the first NBT blocks
+    static constexpr int NUPD = 8 * 2 * IM;                 // tap-component update threads
+    // shared memory in float4 units
+    static constexpr int WIN4 = 2 * 4 * PS / 2;             // two windows x 4 parity arrays
+    static constexpr int TAP4 = 8 * TS;
+    static constexpr int ES4 = LB;
+    static constexpr int PART4 = (NW * 8 * 2 * IM + 3) / 4;
+    static constexpr int YP4 = (NW + 1) / 2;
+    static constexpr int TAB4 = (XW + 1) / 2;
+    static constexpr int BT4 = NBT / 2;
+    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + TAB4 + BT4;
+    static_assert(NT % 32 == 0 && LB % (NW * 4) == 0, "LB must be a multiple of 4 x warps");
+    static_assert(OPL == 2 || OPL == 4 || OPL == 8, "2, 4 or 8 outputs per lane");
+    static_assert(T % 2 == 1 && T >= 3, "odd tap count");
+    static_assert(NUPD <= NT, "one thread per tap component");
+    static_assert(PS % 2 == 0, "16-byte aligned parity arrays");
+};
+
+// One halving level of a reduce-scatter: lanes with (lane & mask) keep the upper half of v[0, N),
+// the others the lower half; each adds its partner's copy of the half it keeps.
+template <int N, int M>
+__device__ __forceinline__ void rs_level(float (&v)[M], int mask, int lane) {
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const float send = up ? v[i] : v[i + N / 2];
+        const float keep = up ? v[i + N / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+}
+
+template <int NT, int T, int LB>
+__global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
+    using S = LmsTileShape<NT, T, LB>;
+    constexpr int NW = S::NW, OPL = S::OPL, IM = S::IM, R = S::R, PS = S::PS;
+    extern __shared__ float4 smem4[];
+    if (a.run_if && *a.run_if == 0) return;
+    float2* win = reinterpret_cast<float2*>(smem4);                 // [buf][p][parity][PS]
+    float4* tapx = smem4 + S::WIN4;                                 // [class][TS]: (hx, hx, hy, hy)
+    float4* es = tapx + S::TAP4;                                    // [LB]: (ex, ex, ey, ey)
+    float* part = reinterpret_cast<float*>(es + S::ES4);            // [warp][class][2 IM]
+    float2* ypart = reinterpret_cast<float2*>(es + S::ES4 + S::PART4);   // [NW]
+    float2* tab = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [XW]
+    float2* btab = tab + 2 * S::TAB4;                               // [NBT]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int q = blockIdx.y;
+    const Qam qm = make_qam(a.m);
+    const long long inc = a.derotate ? a.st->nco_inc : 0;
+
+    // lane class: b0 tap group, b1 tap parity, b2 polarisation; bits 3-4 the output subset
+    const int ig = lane & 1, r = (lane >> 1) & 1, p = (lane >> 2) & 1, cls = lane & 7, ns = lane >> 3;
+    const int Gr = r ? S::G1 : S::G0;
+    const int i0 = ig ? Gr : 0;
+
+    // zero both windows (pads stay zero), the staged taps and the derotation tables
+    for (int i = tid; i < S::WIN4; i += NT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < S::TAP4; i += NT) tapx[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+
+    // tap-component update role: thread u < NUPD owns component f of slot t of class c
+    const bool upd = tid < S::NUPD;
+    const int uc = tid / (2 * IM), uf = tid % (2 * IM), ut = uf >> 1;
+    const int ur = (uc >> 1) & 1, uig = uc & 1, up = (uc >> 2) & 1;
+    const int uG = ur ? S::G1 : S::G0, uN = ur ? S::NO : S::NE;
+    const int uI = uig ? max(uN - uG, 0) : min(uG, uN);
+    const bool ureal = upd && ut < uI;
+    const int uk = 2 * ((uig ? uG : 0) + ut) + ur;                  // tap index of the owned slot
+    float hreg = 0.0f;
+    if (ureal) {
+        const float2 h = a.taps_in[q * 2 * T + up * T + uk];
+        hreg = (uf & 1) ? h.y : h.x;
+        float* dst = reinterpret_cast<float*>(tapx + uc * S::TS + ut) + ((uf & 1) ? 2 : 0);
+        dst[0] = hreg;
+        dst[1] = hreg;
+    }
+    if (inc)
+        for (int jj = tid; jj < S::XW; jj += NT) tab[jj] = nco_conj(inc, jj);
+
+    const int64_t seg = blockIdx.x, nseg = gridDim.x;
+    const int64_t start = seg * a.L_seg;
+    const int64_t end = min(a.n_sym, start + a.L_seg);
+    const int nwarm = seg > 0 ? a.n_wu : 0;
+    const int nmain = (int)((end - start + LB - 1) / LB);
+    const int nblk = nwarm + nmain;
+    const int64_t nfirst = start - (int64_t)nwarm * LB;            // block b starts at symbol nfirst + b LB
+    const float2* const xp0 = a.x;
+    const float2* const xp1 = a.x + a.xstride;
+    const long long gfirst = a.g0 + a.off + 2 * nfirst - S::C;
+    if (inc)
+        for (int b = tid; b < nblk; b += NT) btab[b] = nco_conj(inc, gfirst + 2LL * LB * b);   // nblk <= NBT
+
+    // every window the CTA will read, requested into L2 (128-byte lines)
+    if (nblk > 0) {
+        const int64_t lo = max(a.off + 2 * nfirst - (int64_t)S::C, (int64_t)0);
+        const int64_t hi = min(a.off + 2 * (nfirst + (int64_t)nblk * LB) - (int64_t)S::C + T, a.xlen);
+        const int64_t l0 = (lo * 8) >> 7, l1 = (hi * 8 + 127) >> 7;
+        for (int64_t l = l0 + tid; l < l1; l += NT) {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const char* adr = reinterpret_cast<const char*>(pp ? xp1 : xp0) + (l << 7);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(adr));
+            }
+        }
+    }
+
+    float2 pf[S::PF];
+    auto prefetch = [&](int64_t n0) {
+        const int64_t i0g = a.off + 2 * n0 - S::C;
+#pragma unroll
+        for (int k = 0; k < S::PF; ++k) {
+            const int t = tid + k * NT;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (t < 2 * S::XW) {
+                const int pp = t >= S::XW ? 1 : 0, jj = t - pp * S::XW;
+                const int64_t i = i0g + jj;
+                if (i >= 0 && i < a.xlen) v = __ldg((pp ? xp1 : xp0) + i);
+            }
+            pf[k] = v;
+        }
+    };
+    auto commit = [&](int buf, int blk) {
+        const float2 base = inc ? btab[blk] : make_float2(1.0f, 0.0f);
+        float2* wb = win + buf * 4 * PS;
+#pragma unroll
+        for (int k = 0; k < S::PF; ++k) {
+            const int t = tid + k * NT;
+            if (t < 2 * S::XW) {
+                const int pp = t >= S::XW ? 1 : 0, jj = t - pp * S::XW;
+                float2 v = pf[k];
+                if (inc) v = cmul(v, cmul(base, tab[jj]));
+                const int par = jj & 1;
+                wb[(2 * pp + par) * PS + S::org(par) + (jj >> 1)] = v;
+            }
+        }
+    };
+
+    __syncthreads();                                                // tables and taps staged
+    if (nblk > 0) {
+        prefetch(nfirst);
+        commit(0, 0);
+        if (nblk > 1) prefetch(nfirst + LB);
+    }
+    __syncthreads();
+
+    // first output of the lane's tile within a block, and its first sample (logical parity index)
+    const int nl0 = w * (4 * OPL) + ns * OPL;
+    const int lbase = nl0 + S::C - r - i0 - IM + 1;
+    const int soff = (2 * p + r) * PS + S::org(r) + lbase;         // even: 16-byte aligned
+    // the output the lane holds after the reduce-scatter, and whether it is that output's owner
+    int jst, comp = 0;
+    bool owner;
+    if constexpr (OPL == 2) { jst = (lane >> 2) & 1; comp = (lane >> 1) & 1; owner = (lane & 3) == 0; }
+    else if constexpr (OPL == 4) { jst = 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1); comp = lane & 1; owner = comp == 0; }
+    else { jst = lane & 7; owner = true; }
+    const int nown = nl0 + jst;                                     // local index of the held output
+
+    for (int b = 0; b < nblk; ++b) {
+        const int64_t n0 = nfirst + (int64_t)b * LB;
+        const int L = b < nwarm ? LB : (int)min((int64_t)LB, end - n0);
+        if (b + 1 < nblk) {                                         // next window: stage it, request the one after
+            commit((b + 1) & 1, b + 1);
+            if (b + 2 < nblk) prefetch(n0 + 2 * LB);
+        }
+        const float2* xs = win + (b & 1) * 4 * PS + soff;
+
+        // 1. the tile's partial outputs
+        float2 xr[R];
+#pragma unroll
+        for (int u = 0; u < R / 2; ++u) {
+            const float4 v = reinterpret_cast<const float4*>(xs)[u];
+            xr[2 * u] = make_float2(v.x, v.y);
+            xr[2 * u + 1] = make_float2(v.z, v.w);
+        }
+        float2 accA[OPL], accB[OPL];
+#pragma unroll
+        for (int j = 0; j < OPL; ++j) accA[j] = accB[j] = make_float2(0.0f, 0.0f);
+        const float4* tp = tapx + cls * S::TS;
+#pragma unroll
+        for (int t = 0; t < IM; ++t) {
+            const float4 h = tp[t];
+            const float2 hx = make_float2(h.x, h.y), hy = make_float2(h.z, h.w);
+#pragma unroll
+            for (int j = 0; j < OPL; ++j) {
+                accA[j] = __ffma2_rn(hx, xr[j + IM - 1 - t], accA[j]);
+                accB[j] = __ffma2_rn(hy, xr[j + IM - 1 - t], accB[j]);
+            }
+        }
+        float v[2 * OPL];
+#pragma unroll
+        for (int j = 0; j < OPL; ++j) {
+            v[2 * j] = accA[j].x - accB[j].y;
+            v[2 * j + 1] = accA[j].y + accB[j].x;
+        }
+        // reduce-scatter over the eight classes (lane bits 2, 1, 0): outputs first, then components
+        float2 y;
+        if constexpr (OPL == 2) {
+            rs_level<4>(v, 4, lane);
+            rs_level<2>(v, 2, lane);
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            const float o = __shfl_xor_sync(0xffffffffu, v[0], 2);
+            y = comp ? make_float2(o, v[0]) : make_float2(v[0], o);
+        } else if constexpr (OPL == 4) {
+            rs_level<8>(v, 4, lane);
+            rs_level<4>(v, 2, lane);
+            rs_level<2>(v, 1, lane);
+            const float o = __shfl_xor_sync(0xffffffffu, v[0], 1);
+            y = comp ? make_float2(o, v[0]) : make_float2(v[0], o);
+        } else {
+            rs_level<16>(v, 4, lane);
+            rs_level<8>(v, 2, lane);
+            rs_level<4>(v, 1, lane);
+            y = make_float2(v[0], v[1]);
+        }
+        const bool valid = nown < L;
+        if (b >= nwarm && a.y != nullptr && owner && valid) a.y[(int64_t)q * a.ystride + n0 + nown] = y;
+
+        // 2. errors
+        float2 e = make_float2(0.0f, 0.0f);
+        if (a.cma) {
+            if (valid) e = cscale(y, a.R2 - cabs2(y));
+        } else {
+            float2 c4 = make_float2(0.0f, 0.0f);
+            if (owner && valid) {
+                const float2 y2 = cmul(y, y);
+                c4 = cmul(y2, y2);
+            }
+            c4.x = warp_sum(c4.x);
+            c4.y = warp_sum(c4.y);
+            if (lane == 0) ypart[w] = c4;
+            __syncthreads();
+            float2 sum = ypart[0];
+#pragma unroll
+            for (int k = 1; k < NW; ++k) sum = cadd(sum, ypart[k]);
+            const float2 rt = quarter_root_conj(make_float2(-sum.x, -sum.y));
+            if (valid) {
+                const float2 d = qam_decide(cmul(y, rt), qm);
+                e = csub(cmulc(d, rt), y);
+            }
+        }
+        // 3. the errors of the warp's outputs to the lanes of their subset, then the gradient partials
+        if (owner) es[nown] = make_float4(e.x, e.x, e.y, e.y);
+        __syncwarp();
+        float4 ev[OPL];
+#pragma unroll
+        for (int j = 0; j < OPL; ++j) ev[j] = es[nl0 + j];
+        float2 gA[IM], gB[IM];
+#pragma unroll
+        for (int t = 0; t < IM; ++t) {
+            gA[t] = gB[t] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < OPL; ++j) {
+                gA[t] = __ffma2_rn(make_float2(ev[j].x, ev[j].y), xr[j + IM - 1 - t], gA[t]);
+                gB[t] = __ffma2_rn(make_float2(ev[j].z, ev[j].w), xr[j + IM - 1 - t], gB[t]);
+            }
+        }
+        float g[2 * IM];
+#pragma unroll
+        for (int t = 0; t < IM; ++t) {
+            g[2 * t] = gA[t].x + gB[t].y;          // Re(e conj x)
+            g[2 * t + 1] = gB[t].x - gA[t].y;      // Im(e conj x)
+        }
+        rs_level<2 * IM>(g, 16, lane);
+        rs_level<IM>(g, 8, lane);
+        float* pw = part + (w * 8 + cls) * 2 * IM + ns * (IM / 2);
+#pragma unroll
+        for (int u = 0; u < IM / 2; ++u) pw[u] = g[u];
+        __syncthreads();
+
+        // 4. tap update: the warps' partials in a fixed order
+        if (ureal) {
+            float gs = part[uc * 2 * IM + uf];
+#pragma unroll
+            for (int k = 1; k < NW; ++k) gs += part[(k * 8 + uc) * 2 * IM + uf];
+            hreg = fmaf(a.mu, gs, hreg);
+            float* dst = reinterpret_cast<float*>(tapx + uc * S::TS + ut) + ((uf & 1) ? 2 : 0);
+            dst[0] = hreg;
+            dst[1] = hreg;
+        }
+        __syncthreads();
+    }
+    if (seg == nseg - 1 && a.taps_out && ureal) {
+        float* dst = reinterpret_cast<float*>(a.taps_out + q * 2 * T + up * T + uk) + (uf & 1);
+        *dst = hreg;
+    }
+}
+
+// the tiled kernel keeps one derotation base per block of a CTA: at most NBT blocks
+template <int LB>
+inline bool lms_tile_fits(const LmsArgs& a) {
+    return (a.L_seg + LB - 1) / LB + a.n_wu <= 256;
+}
+
+template <int NT, int T, int LB>
+cudaError_t launch_lms_tile_t(const LmsArgs& a, cudaStream_t s) {
+    using S = LmsTileShape<NT, T, LB>;
+    const int64_t nseg = (a.n_sym + a.L_seg - 1) / a.L_seg;
+    if (nseg <= 0) return cudaSuccess;
+    const size_t smem = lms_launch_smem(sizeof(float4) * S::SMEM4, a.exclusive);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        cudaFuncSetAttribute(k_lms_tile<NT, T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_lms_tile<NT, T, LB><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
