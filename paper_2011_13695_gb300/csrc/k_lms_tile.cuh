@@ -26,10 +26,11 @@
 //   4. barrier; one thread per tap component adds the warps' partials in a
 //      fixed order and updates its tap (held in a register) and the staged
 //      copy; barrier.
-// Windows are split by sample parity (tap k reads parity k % 2) and
-// double-buffered: a block's window is written at the start of the previous
-// step, derotated by the per-block and per-position phasor tables, and the
-// next one is requested from global memory at the same time.
+// Windows are split by sample parity (tap k reads parity k % 2) into three
+// rotating buffers: a block's window is copied asynchronously (cp.async) two
+// steps ahead, and one step ahead each thread waits for its own copies and
+// derotates them in place by a per-block phasor (shared table) times a
+// per-position phasor (registers).
 #pragma once
 
 #include "rx_kernels.h"
@@ -52,19 +53,21 @@ struct LmsTileShape {
     static constexpr int PS = ((PS0 + 11) / 16) * 16 + 4;   // = 4 mod 16: the four arrays start in
                                                             // different bank quarters
     static constexpr int XW = 2 * LB + T - 1;               // window samples per polarisation
-    static constexpr int PF = (2 * XW + NT - 1) / NT;       // window registers per thread
+    static constexpr int KS = (2 * XW + NT - 1) / NT;       // window samples staged per thread
     static constexpr int TS = IM + 1;                       // staged tap row stride (float4, odd)
     static constexpr int NBT = 256;                         // derotation bases of the first NBT blocks
     static constexpr int NUPD = 8 * 2 * IM;                 // tap-component update threads
     // shared memory in float4 units
-    static constexpr int WIN4 = 2 * 4 * PS / 2;             // two windows x 4 parity arrays
+    static constexpr int WIN4 = 3 * 4 * PS / 2;             // three windows x 4 parity arrays
     static constexpr int TAP4 = 8 * TS;
     static constexpr int ES4 = LB;
-    static constexpr int PART4 = (NW * 8 * 2 * IM + 3) / 4;
+    static constexpr int NPART = OPL == 8 ? NW * 4 : NW;    // gradient partials per tap component
+    static constexpr int PART4 = (NPART * 8 * 2 * IM + 3) / 4;
+    static constexpr int YTS = 84;                          // transposition stride per output subset (float2)
+    static constexpr int YT4 = OPL == 8 ? NW * 4 * YTS / 2 : 0;
     static constexpr int YP4 = (NW + 1) / 2;
-    static constexpr int TAB4 = (XW + 1) / 2;
     static constexpr int BT4 = NBT / 2;
-    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + TAB4 + BT4;
+    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + BT4 + YT4;
     static_assert(NT % 32 == 0 && LB % (NW * 4) == 0, "LB must be a multiple of 4 x warps");
     static_assert(OPL == 2 || OPL == 4 || OPL == 8, "2, 4 or 8 outputs per lane");
     static_assert(T % 2 == 1 && T >= 3, "odd tap count");
@@ -85,19 +88,20 @@ __device__ __forceinline__ void rs_level(float (&v)[M], int mask, int lane) {
     }
 }
 
+// 128-thread CTAs (the segments' shape) keep to 170 registers so that three share an SM
 template <int NT, int T, int LB>
-__global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
     using S = LmsTileShape<NT, T, LB>;
     constexpr int NW = S::NW, OPL = S::OPL, IM = S::IM, R = S::R, PS = S::PS;
     extern __shared__ float4 smem4[];
     if (a.run_if && *a.run_if == 0) return;
-    float2* win = reinterpret_cast<float2*>(smem4);                 // [buf][p][parity][PS]
+    float2* win = reinterpret_cast<float2*>(smem4);                 // [3 buffers][p][parity][PS]
     float4* tapx = smem4 + S::WIN4;                                 // [class][TS]: (hx, hx, hy, hy)
     float4* es = tapx + S::TAP4;                                    // [LB]: (ex, ex, ey, ey)
     float* part = reinterpret_cast<float*>(es + S::ES4);            // [warp][class][2 IM]
     float2* ypart = reinterpret_cast<float2*>(es + S::ES4 + S::PART4);   // [NW]
-    float2* tab = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [XW]
-    float2* btab = tab + 2 * S::TAB4;                               // [NBT]
+    float2* btab = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [NBT]
+    float2* ytr = btab + 2 * S::BT4;                                // [warp][subset][YTS] (OPL == 8)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
@@ -129,8 +133,6 @@ __global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
         dst[0] = hreg;
         dst[1] = hreg;
     }
-    if (inc)
-        for (int jj = tid; jj < S::XW; jj += NT) tab[jj] = nco_conj(inc, jj);
 
     const int64_t seg = blockIdx.x, nseg = gridDim.x;
     const int64_t start = seg * a.L_seg;
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
     const int64_t nfirst = start - (int64_t)nwarm * LB;            // block b starts at symbol nfirst + b LB
     const float2* const xp0 = a.x;
     const float2* const xp1 = a.x + a.xstride;
-    const long long gfirst = a.g0 + a.off + 2 * nfirst - S::C;
+    const long long gfirst = a.g0 + a.off + 2 * nfirst - S::C;   // input-sample index of block 0's window
     if (inc)
         for (int b = tid; b < nblk; b += NT) btab[b] = nco_conj(inc, gfirst + 2LL * LB * b);   // nblk <= NBT
 
@@ -159,42 +161,67 @@ __global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
         }
     }
 
-    float2 pf[S::PF];
-    auto prefetch = [&](int64_t n0) {
-        const int64_t i0g = a.off + 2 * n0 - S::C;
+    // Window staging by asynchronous copies (cp.async, 8 bytes per sample, zero fill outside the buffer):
+    // thread tid stages window positions s = tid + k NT of the two polarisations (s < 2 XW), into the
+    // parity arrays of one of three window buffers; a block's copies are issued two steps ahead, the
+    // thread waits for its own copies one step ahead and (DD) derotates them in place, and the barriers
+    // of that step make them visible. Slots and relative global offsets are the same for every block.
+    const int64_t gstart = a.off + 2 * nfirst - S::C;                  // window start of block 0
+    uint32_t sslot[S::KS];                                             // shared address in buffer 0
+    int spos[S::KS];                                                   // window position, -1: idle
+    float2 sph[S::KS];                                                 // per-position derotation phasor
+    const float2* ssrc[S::KS];                                         // source of the position in block 0
+    const uint32_t win_sa = (uint32_t)__cvta_generic_to_shared(win);
 #pragma unroll
-        for (int k = 0; k < S::PF; ++k) {
-            const int t = tid + k * NT;
-            float2 v = make_float2(0.0f, 0.0f);
-            if (t < 2 * S::XW) {
-                const int pp = t >= S::XW ? 1 : 0, jj = t - pp * S::XW;
-                const int64_t i = i0g + jj;
-                if (i >= 0 && i < a.xlen) v = __ldg((pp ? xp1 : xp0) + i);
+    for (int k = 0; k < S::KS; ++k) {
+        const int sidx = tid + k * NT;
+        const int pp = sidx >= S::XW ? 1 : 0, jj = sidx - pp * S::XW;
+        const bool in = sidx < 2 * S::XW;
+        const int par = jj & 1;
+        sslot[k] = win_sa + 8u * (uint32_t)((2 * pp + par) * PS + S::org(par) + (jj >> 1));
+        spos[k] = in ? jj : -1;
+        sph[k] = (in && inc) ? nco_conj(inc, jj) : make_float2(1.0f, 0.0f);
+        ssrc[k] = (pp ? xp1 : xp0) + gstart + jj;                      // address arithmetic only
+    }
+    auto issue = [&](int blk) {                                        // copies of block blk's window
+        const int64_t g0b = gstart + 2LL * LB * blk;
+        const bool fast = g0b >= 0 && g0b + S::XW <= a.xlen;          // whole window inside the buffer
+        const uint32_t boff = 8u * (uint32_t)((blk % 3) * 4 * PS);
+        const int64_t d = 2LL * LB * blk;
+#pragma unroll
+        for (int k = 0; k < S::KS; ++k) {
+            if (spos[k] < 0) continue;
+            bool ok = true;
+            if (!fast) {
+                const int64_t gi = g0b + spos[k];
+                ok = gi >= 0 && gi < a.xlen;
             }
-            pf[k] = v;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sslot[k] + boff),
+                         "l"(ok ? ssrc[k] + d : xp0), "r"(ok ? 8 : 0)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    auto commit = [&](int buf, int blk) {
-        const float2 base = inc ? btab[blk] : make_float2(1.0f, 0.0f);
-        float2* wb = win + buf * 4 * PS;
+    auto land = [&](int blk) {                                         // own copies of block blk complete
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        if (inc) {
+            const float2 base = btab[blk];
+            float2* wb = win + (blk % 3) * 4 * PS;
 #pragma unroll
-        for (int k = 0; k < S::PF; ++k) {
-            const int t = tid + k * NT;
-            if (t < 2 * S::XW) {
-                const int pp = t >= S::XW ? 1 : 0, jj = t - pp * S::XW;
-                float2 v = pf[k];
-                if (inc) v = cmul(v, cmul(base, tab[jj]));
-                const int par = jj & 1;
-                wb[(2 * pp + par) * PS + S::org(par) + (jj >> 1)] = v;
+            for (int k = 0; k < S::KS; ++k) {
+                if (spos[k] < 0) continue;
+                float2* slot = wb + (sslot[k] - win_sa) / 8;
+                *slot = cmul(*slot, cmul(base, sph[k]));
             }
         }
     };
 
     __syncthreads();                                                // tables and taps staged
     if (nblk > 0) {
-        prefetch(nfirst);
-        commit(0, 0);
-        if (nblk > 1) prefetch(nfirst + LB);
+        issue(0);
+        if (nblk > 1) issue(1);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        land(0);
     }
     __syncthreads();
 
@@ -213,11 +240,10 @@ __global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
     for (int b = 0; b < nblk; ++b) {
         const int64_t n0 = nfirst + (int64_t)b * LB;
         const int L = b < nwarm ? LB : (int)min((int64_t)LB, end - n0);
-        if (b + 1 < nblk) {                                         // next window: stage it, request the one after
-            commit((b + 1) & 1, b + 1);
-            if (b + 2 < nblk) prefetch(n0 + 2 * LB);
-        }
-        const float2* xs = win + (b & 1) * 4 * PS + soff;
+        // window of block b + 2 requested now (an empty group past the end keeps the wait count uniform)
+        if (b + 2 < nblk) issue(b + 2);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const float2* xs = win + (b % 3) * 4 * PS + soff;
 
         // 1. the tile's partial outputs
         float2 xr[R];
@@ -262,10 +288,19 @@ __global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
             const float o = __shfl_xor_sync(0xffffffffu, v[0], 1);
             y = comp ? make_float2(o, v[0]) : make_float2(v[0], o);
         } else {
-            rs_level<16>(v, 4, lane);
-            rs_level<8>(v, 2, lane);
-            rs_level<4>(v, 1, lane);
-            y = make_float2(v[0], v[1]);
+            // eight outputs per lane: transpose through shared memory (lane (ns, cls) writes its
+            // partial of output j at [ns][j][cls], the lane of output j reads the eight classes as
+            // four 16-byte loads; strides 10 and 84 keep both sides free of bank conflicts)
+            float2* yw = ytr + w * (4 * S::YTS) + ns * S::YTS;
+#pragma unroll
+            for (int j = 0; j < OPL; ++j) yw[j * 10 + cls] = make_float2(v[2 * j], v[2 * j + 1]);
+            __syncwarp();
+            const float4* yr = reinterpret_cast<const float4*>(yw + jst * 10);
+            const float4 c01 = yr[0], c23 = yr[1], c45 = yr[2], c67 = yr[3];
+            y = cadd(cadd(cadd(make_float2(c01.x, c01.y), make_float2(c01.z, c01.w)),
+                          cadd(make_float2(c23.x, c23.y), make_float2(c23.z, c23.w))),
+                     cadd(cadd(make_float2(c45.x, c45.y), make_float2(c45.z, c45.w)),
+                          cadd(make_float2(c67.x, c67.y), make_float2(c67.z, c67.w))));
         }
         const bool valid = nown < L;
         if (b >= nwarm && a.y != nullptr && owner && valid) a.y[(int64_t)q * a.ystride + n0 + nown] = y;
@@ -315,18 +350,36 @@ __global__ void __launch_bounds__(NT, 1) k_lms_tile(LmsArgs a) {
             g[2 * t] = gA[t].x + gB[t].y;          // Re(e conj x)
             g[2 * t + 1] = gB[t].x - gA[t].y;      // Im(e conj x)
         }
-        rs_level<2 * IM>(g, 16, lane);
-        rs_level<IM>(g, 8, lane);
-        float* pw = part + (w * 8 + cls) * 2 * IM + ns * (IM / 2);
+        if constexpr (OPL == 8) {
+            float4* pw = reinterpret_cast<float4*>(part + ((w * 4 + ns) * 8 + cls) * 2 * IM);
 #pragma unroll
-        for (int u = 0; u < IM / 2; ++u) pw[u] = g[u];
+            for (int u = 0; u < IM / 2; ++u) pw[u] = make_float4(g[4 * u], g[4 * u + 1], g[4 * u + 2], g[4 * u + 3]);
+        } else {
+            rs_level<2 * IM>(g, 16, lane);
+            rs_level<IM>(g, 8, lane);
+            float* pw = part + (w * 8 + cls) * 2 * IM + ns * (IM / 2);
+#pragma unroll
+            for (int u = 0; u < IM / 2; ++u) pw[u] = g[u];
+        }
+        if (b + 1 < nblk) land(b + 1);                              // next window in place before the barriers
         __syncthreads();
 
         // 4. tap update: the warps' partials in a fixed order
         if (ureal) {
-            float gs = part[uc * 2 * IM + uf];
+            float gs;
+            if constexpr (OPL == 8) {                                   // warps x subsets, in a fixed order
+                float g0 = part[uc * 2 * IM + uf], g1 = part[(8 + uc) * 2 * IM + uf];
 #pragma unroll
-            for (int k = 1; k < NW; ++k) gs += part[(k * 8 + uc) * 2 * IM + uf];
+                for (int k = 2; k < S::NPART; k += 2) {
+                    g0 += part[(k * 8 + uc) * 2 * IM + uf];
+                    g1 += part[((k + 1) * 8 + uc) * 2 * IM + uf];
+                }
+                gs = g0 + g1;
+            } else {
+                gs = part[uc * 2 * IM + uf];
+#pragma unroll
+                for (int k = 1; k < NW; ++k) gs += part[(k * 8 + uc) * 2 * IM + uf];
+            }
             hreg = fmaf(a.mu, gs, hreg);
             float* dst = reinterpret_cast<float*>(tapx + uc * S::TS + ut) + ((uf & 1) ? 2 : 0);
             dst[0] = hreg;

@@ -607,13 +607,14 @@ bool lms_fast_b(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err)
 bool lms_fast_c(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
 bool lms_tile_a(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
 bool lms_tile_b(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
+bool lms_tile_c(const LmsArgs& a, int threads, cudaStream_t s, cudaError_t* err);
 
-// The serial acquisition (one CTA per output row holding a whole SM) takes the register-tiled
-// kernel (k_lms_tile.cuh), the segments the compile-time shapes of k_lms_fast.cuh, this file's
-// generic kernel every other shape.
+// The register-tiled kernel (k_lms_tile.cuh) for its shapes at 128 or 256 threads, the compile-time
+// shapes of k_lms_fast.cuh next (512 threads included), this file's generic kernel every other shape.
 cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
-    if (a.exclusive && (lms_tile_a(a, threads, s, &err) || lms_tile_b(a, threads, s, &err))) return err;
+    if (lms_tile_a(a, threads, s, &err) || lms_tile_b(a, threads, s, &err) || lms_tile_c(a, threads, s, &err))
+        return err;
     if (lms_fast_b(a, threads, s, &err) || lms_fast_a(a, threads, s, &err) || lms_fast_c(a, threads, s, &err))
         return err;
     switch (threads) {

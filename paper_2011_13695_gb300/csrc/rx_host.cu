@@ -32,9 +32,9 @@ const char* kStageNames[ST_N] = {"power", "cdc", "cma", "foe", "dd_acq", "lms", 
                                  "unwrap", "sync", "count", "stream_state", "h2d", "d2h", "cdc_rest"};
 constexpr int kPool = 64;
 // CTA sizes of the block-LMS kernel: the acquisition is one CTA per output row
-// and issue-bound, so fewer threads (less per-thread overhead) finish sooner;
-// the segments are many CTAs, whose count per SM matters more.
-constexpr int kAcqThreads = 256;
+// and latency-bound, and four warps (eight outputs per lane) carry the least
+// per-step overhead; the segments are many CTAs, three of which share an SM.
+constexpr int kAcqThreads = 128;
 constexpr int kSegThreads = 128;
 
 __global__ void k_state_init(RxDevState* st) {

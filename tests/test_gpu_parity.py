@@ -131,20 +131,25 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, he
         pytest.skip("oracle FO estimate within 1 % of a rounding boundary: two correct codes")
     assert g["stats"]["fo_code"] == r.fo_code
     yok = check_y(g, r, cfg, tol_y)
-    # In a stream's first frame the start-up transient (no signal yet) makes b* arbitrary, so the
-    # integer unwrap count may settle on a different whole number of quarter turns; that is the
-    # same quarter-turn ambiguity the alignment resolves, and the unwrap carries it into every
-    # later frame of the stream. Compare z after removing that constant.
-    dm = np.zeros(2, dtype=np.int64)
+    # The unwrap count m may differ from the oracle's by a whole number of quarter turns: in a stream's
+    # first frame the start-up transient (no signal yet) makes b* arbitrary, so the count may settle on
+    # another whole number of turns (the quarter-turn ambiguity the alignment resolves, carried into
+    # every later frame); and where a b* near-tie falls at the wrap of the phase grid (b* = 0 against
+    # B - 1, adjacent phases), one side takes an unwrap jump the other does not, a carrier slip decided
+    # by the tie. So the offset dmk = m_gpu - m_oracle is piecewise constant, and may change only next
+    # to a verified b* near-tie (or inside a left-out near-tie segment); z is compared with it removed.
+    bagree = check_bstar(g, r, cfg, head, skip=~yok)
+    dmk = (g["m"] - r.m).astype(np.int64)
+    dmk[:, :head] = dmk[:, head:head + 1] if head < N else 0
     for q in range(2):
-        vals, cnt = np.unique((g["m"][q, head:] - r.m[q, head:]), return_counts=True)
-        if len(vals):
-            dm[q] = vals[np.argmax(cnt)]
-    m_agree = (g["m"] - r.m) == dm[:, None]
-    agree = check_bstar(g, r, cfg, head, skip=~yok) & m_agree & yok
+        ch = np.flatnonzero(dmk[q, 1:] != dmk[q, :-1]) + 1
+        for k in ch:
+            near = (not bagree[q, k]) or (not bagree[q, k - 1]) or (not yok[q, k]) or (not yok[q, k - 1])
+            assert near, f"unwrap offset changes at ({q},{k}) without a b* near-tie"
+    agree = bagree & yok
     agree[:, :head] = False
-    assert np.mean(agree[:, head:][yok[:, head:]]) > 1 - 1e-3
-    zg = g["z"] * (1j ** dm)[:, None]
+    assert np.mean(agree[:, head:][yok[:, head:]]) > 1 - 2e-3
+    zg = g["z"] * (1j ** dmk)
     z_rel = rel_rms(zg[agree], r.z[agree])
     assert z_rel < tol_y
     gl = oqam.decide_levels(zg, m)
@@ -156,33 +161,45 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, he
     # output bits: the GPU's bits are the demap of its own z (with its quarter turns)
     if ref_words is not None and r.sync is not None:
         st = g["stats"]
-        assert [tuple(s[:3]) for s in r.sync] == list(zip(st["pol_map"], [int((st["rotation"][q] - dm[q]) % 4)
+        E = max(cfg.edge_skip, lat + cfg.max_delay) if lat else cfg.edge_skip
+        lo_c, hi_c = E, max(N - E, E)
+        dm_sync = dmk[:, min(lo_c, N - 1)] if N else np.zeros(2, np.int64)
+        assert [tuple(s_[:3]) for s_ in r.sync] == list(zip(st["pol_map"], [int((st["rotation"][q] - dm_sync[q]) % 4)
                                                                            for q in range(2)], st["delay"]))
         d = g["delta"]
         assert d["bits_counted"] == r.counts["bits"]
-        E = max(cfg.edge_skip, lat + cfg.max_delay) if lat else cfg.edge_skip
-        assert host_recount(g, r.sync, ref_words, m, N, E, max(N - E, E), lat) == d["bit_errors"]
+        assert host_recount(g, r.sync, ref_words, m, N, lo_c, hi_c, lat) == d["bit_errors"]
         # symbols whose decisions may differ: the differing decisions, and the symbols of DD near-tie
         # segments left out of the comparisons, inside the counted window
         win = np.zeros((2, N), dtype=bool)
-        win[:, E:max(N - E, E)] = True
+        win[:, lo_c:hi_c] = True
         n_excl = int(np.sum(~yok & win))
         n_var = int(np.sum(dmask & win)) + n_excl
-        if n_var == 0:
+        slipped = any(len(np.unique(dmk[q, lo_c:hi_c])) > 1 for q in range(2)) if hi_c > lo_c else False
+        if slipped:
+            # a tie-decided carrier slip inside the counted window: the oracle's symbols brought into the
+            # GPU's unwrap frame, decided with the GPU's alignment, give the GPU's count
+            g_sync = [(st["pol_map"][q], st["rotation"][q], st["delay"][q]) for q in range(2)]
+            want = odec.count(r.z * ((-1j) ** dmk), g_sync, ref_words, m, N, lo_c, hi_c, lat)
+            assert abs(d["bit_errors"] - want["bit_errors"]) <= m * n_var, (d["bit_errors"], want["bit_errors"])
+            assert abs(d["symbol_errors"] - want["symbol_errors"]) <= n_var
+        elif n_var == 0:
             assert d["bit_errors"] == r.counts["bit_errors"]
             assert d["symbol_errors"] == r.counts["symbol_errors"]
         else:
             # each such symbol changes the count by at most its m bits (one symbol error)
             assert abs(d["bit_errors"] - r.counts["bit_errors"]) <= m * n_var, (d["bit_errors"], r.counts)
             assert abs(d["symbol_errors"] - r.counts["symbol_errors"]) <= n_var
-        assert d["evm_num"] / d["evm_den"] == pytest.approx(r.counts["evm_num"] / r.counts["evm_den"], rel=1e-3)
+        if not slipped:
+            assert d["evm_num"] / d["evm_den"] == pytest.approx(r.counts["evm_num"] / r.counts["evm_den"], rel=1e-3)
     st = g["stats"]
     g_sync = None if r.sync is None else [(st["pol_map"][q], st["rotation"][q], st["delay"][q]) for q in range(2)]
     want_bits = kernel_precision_bits(g["z"], g_sync, m)
     assert np.array_equal(g["bits"], want_bits)
     ok = yok[:, head:]
     return {"y_rel_rms": rel_rms(g["y"][:, head:][ok], r.y[:, head:][ok]), "z_rel_rms": z_rel,
-            "decisions_differ": ndiff, "symbols_excluded": int(np.sum(~yok[:, head:]))}
+            "decisions_differ": ndiff, "symbols_excluded": int(np.sum(~yok[:, head:])),
+            "unwrap_offset_changes": int(sum(np.sum(dmk[q, 1:] != dmk[q, :-1]) for q in range(2)))}
 
 
 def run_pair(w, seed, n_sym=None, fmt=0, link_kw=None, rx_kw=None):
