@@ -5,8 +5,10 @@ Tolerances (FP32 on the GPU, FP64 in the oracle):
   * FD-compensated samples: relative RMS <= 1e-5 (one FP32 FFT pair);
   * FO code: equal (unless the oracle's estimate lies within 1 % of a grid step
     of a rounding boundary, where both codes are correct);
-  * BPS phase index b* and hard decisions: differ on <= 1e-5 of the symbols
-    (rounded up to whole symbols);
+  * BPS phase index b*: may differ only at near-ties of the oracle's FP64 window
+    sums (each checked); hard decisions differ on <= 1e-5 of the symbols
+    (rounded up to whole symbols) where b* agrees, and may also differ where b*
+    took the other side of such a near-tie;
   * bit-error counts: exact; the GPU count equals the count recomputed on the
     host from the GPU's own output bits, and equals the oracle's count when
     the decisions agree.
@@ -156,8 +158,11 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, he
     ol = oqam.decide_levels(r.z, m)
     dmask = ((gl[0] != ol[0]) | (gl[1] != ol[1])) & yok
     dmask[:, :head] = False
-    ndiff = int(np.sum(dmask))
-    assert ndiff <= allowed(2 * N), f"decisions differ on {ndiff} symbols"
+    # a decision that follows a b* near-tie (the other, equally valid test phase: z turned by one grid
+    # step) is not held to the budget, which applies where both sides took the same b*
+    ndiff = int(np.sum(dmask & bagree))
+    ntie = int(np.sum(dmask & ~bagree))
+    assert ndiff <= allowed(2 * N), f"decisions differ on {ndiff} symbols (plus {ntie} after b* near-ties)"
     # output bits: the GPU's bits are the demap of its own z (with its quarter turns)
     if ref_words is not None and r.sync is not None:
         st = g["stats"]
@@ -198,7 +203,7 @@ def check_frame(g, r, cfg, ref_words=None, lat=0, tol_y=1e-4, check_cdc=True, he
     assert np.array_equal(g["bits"], want_bits)
     ok = yok[:, head:]
     return {"y_rel_rms": rel_rms(g["y"][:, head:][ok], r.y[:, head:][ok]), "z_rel_rms": z_rel,
-            "decisions_differ": ndiff, "symbols_excluded": int(np.sum(~yok[:, head:])),
+            "decisions_differ": ndiff, "decisions_after_bstar_ties": ntie, "symbols_excluded": int(np.sum(~yok[:, head:])),
             "unwrap_offset_changes": int(sum(np.sum(dmk[q, 1:] != dmk[q, :-1]) for q in range(2)))}
 
 
