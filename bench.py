@@ -45,9 +45,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="frame workload only: skip the precision, batched and learned forms (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
     ap.add_argument("--workload", default="frame",
-                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk", "ingest", "pam"],
+                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk", "ingest", "pam", "forms"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
                          "batch: 16 channels in one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser; cnn: the post-equaliser forward alone; wl: the "
@@ -59,7 +61,7 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
     ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
     ap.add_argument("--lr", type=float, default=7e-4, help="initial Adam learning rate of the learned workload")
-    ap.add_argument("--fmt", default="i8", choices=["i8", "f16"], help="input format of the stream workload")
+    ap.add_argument("--fmt", default="i8", choices=["i8", "f16", "c64"], help="input format of the stream workload")
     ap.add_argument("--wl-taps", type=int, default=21, help="tap count of the wl workload")
     ap.add_argument("--wl-threads", type=int, default=0,
                     help="CTA size of the wl workload (0: library choice; 512 runs the generic kernel)")
@@ -319,6 +321,27 @@ def max_over_ranks(values, dist=None, device="cpu"):
     return [float(v) for v in t.tolist()]
 
 
+def free_port() -> int:
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def _spawned_rank(rank: int, world: int, port: int, fn, fn_args: tuple) -> None:
+    os.environ.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(world), LOCAL_WORLD_SIZE=str(world),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    fn(*fn_args)
+
+
+def spawn_ranks(world: int, fn, *fn_args) -> None:
+    """Run fn(*fn_args) in `world` processes that see the rendezvous environment torchrun gives its
+    ranks (RANK = LOCAL_RANK, WORLD_SIZE, MASTER_ADDR 127.0.0.1, a free MASTER_PORT): one replica per
+    GPU of this host when bench.py is started without torchrun."""
+    import torch.multiprocessing as mp
+    mp.spawn(_spawned_rank, args=(world, free_port(), fn, fn_args), nprocs=world, join=True)
+
+
 def hbm_step_roofline(bytes_per_step: int, ms_per_step: float, pk: dict) -> dict:
     """A whole step's compulsory HBM bytes over its time, against the measured copy bandwidth."""
     gbs = bytes_per_step / (ms_per_step * 1e-3) / 1e9
@@ -496,13 +519,17 @@ def our_arm(args) -> None:
             line["cpu_baseline"] = cpu_baseline()
         except Exception as e:  # report, do not hide
             line["cpu_baseline"] = {"error": str(e)[:300]}
+    if not args.no_forms and world == 1 and not args.n_sym:
+        line["forms"] = other_forms(args)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
-def stream_arm(args) -> None:
-    """64QAM 48 GBd stream: 64 frames of 2^18 symbols/pol, int8 (or FP16) ADC input, carried state."""
+def stream_form(fmt: str, steps: int, warmup: int) -> dict:
+    """64QAM 48 GBd stream: 64 frames of 2^18 symbols/pol with carried state, from one seeded signal in
+    the input format fmt ("c64": the plain FP32 chain's complex64 input; "f16": FP16; "i8": 8-bit ADC,
+    4-sigma mid-tread). Each timed step is the whole 64-frame stream through a fresh handle."""
     import numpy as np
     import torch
 
@@ -517,19 +544,21 @@ def stream_arm(args) -> None:
     F, n = w["n_frames"], w["frame_sym"]
     fr = generate(w["link"], SEED)
     S = 2 * n
-    if args.fmt == "i8":
+    if fmt == "i8":
         codes, delta = quantise_int8(fr.samples)
-        data, fmt, scale, esz = codes, rx.RX_IN_I8, float(delta[0]), 2
+        data, rfmt, scale = codes, rx.RX_IN_I8, float(delta[0])
+    elif fmt == "f16":
+        data, rfmt, scale = to_fp16(fr.samples).view(np.int16), rx.RX_IN_F16, 1.0
     else:
-        data, fmt, scale, esz = to_fp16(fr.samples).view(np.int16), rx.RX_IN_F16, 1.0, 4
+        data, rfmt, scale = fr.samples.astype(np.complex64).view(np.float32).reshape(2, -1, 2), rx.RX_IN_C64, 1.0
     xs = [torch.from_numpy(np.ascontiguousarray(data[:, f * S:(f + 1) * S])).cuda() for f in range(F)]
     m = w["link"].bits_per_sym
     refs = [torch.from_numpy(pack_bits(fr.bits[:, f * n * m:(f + 1) * n * m]).astype(np.uint32).view(np.int32)).cuda()
             for f in range(F)]
     stream = torch.cuda.current_stream()
     times = []
-    for rep in range(args.warmup + args.steps):
-        rcv = Receiver(w["rx"], n, input_format=fmt, input_scale=scale, streaming=True)
+    for rep in range(warmup + steps):
+        rcv = Receiver(w["rx"], n, input_format=rfmt, input_scale=scale, streaming=True)
         out = torch.zeros(2 * rcv.words(n), dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -538,22 +567,59 @@ def stream_arm(args) -> None:
             rcv.process(xs[f], n, refs[f], out)
         e1.record(stream)
         torch.cuda.synchronize()
-        if rep >= args.warmup:
+        if rep >= warmup:
             times.append(e0.elapsed_time(e1))
         st = rcv.stats()
         rcv.close()
     t = sum(times) / len(times)
     bits = 2 * m * n * F
-    print(json.dumps({"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
-                      "higher_is_better": True, "dtype": f"{args.fmt} in, f32", "data": "synthetic",
-                      "config": {"workload": "dp-64qam-48gbd-stream", "frames": F, "symbols_per_frame": n,
-                                 "input": args.fmt},
-                      "ber": st["ber"], "evm": st["evm"], "q_db": st["q_db"], "error_word": st["error_word"]}))
+    in_bytes = int(sum(x.numel() * x.element_size() for x in xs))
+    return {"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": t, "higher_is_better": True,
+            "dtype": f"{fmt} in, f32", "data": "synthetic",
+            "config": {"workload": "dp-64qam-48gbd-stream", "frames": F, "symbols_per_frame": n, "input": fmt,
+                       "input_bytes": in_bytes, "l2": "inputs of the stream (64 frames) exceed L2 only for c64; "
+                                                      "every step is a fresh handle over the whole stream"},
+            "ber": st["ber"], "evm": st["evm"], "q_db": st["q_db"], "error_word": st["error_word"]}
 
 
-def batch_arm(args) -> None:
-    """16 seeded channels (16..64 GBd, QPSK/16QAM/64QAM, 2^16..2^20 symbols) in one graph launch."""
+def other_forms(args) -> dict:
+    """The chain's other forms on the same GPU, each beside its plain counterpart: the precision form
+    (64QAM 48 GBd stream of 64 x 2^18 symbols with complex64, FP16 and int8 input), the batched form (16
+    channels in one graph launch, and the same frames through single handles in turn) and the learned
+    form (split-step 16QAM link: chain + post-equaliser + decisions against the chain alone). A few
+    timed steps each, so that the whole run stays within minutes."""
+    import argparse
+    out = {}
+    try:
+        out["stream"] = {fmt: stream_form(fmt, 3, 3) for fmt in ("c64", "f16", "i8")}
+        base = out["stream"]["c64"]
+        for fmt in ("f16", "i8"):
+            f = out["stream"][fmt]
+            f["vs_c64"] = {"rate_ratio": f["value"] / base["value"], "ber_c64": base["ber"], "ber": f["ber"]}
+    except Exception as e:  # report, do not hide
+        out["stream"] = {"error": str(e)[:300]}
+    try:
+        out["batch"] = batch_form(5, 3)
+    except Exception as e:
+        out["batch"] = {"error": str(e)[:300]}
+    try:
+        la = argparse.Namespace(**vars(args))
+        la.steps, la.warmup, la.n_sym = 5, 3, 0
+        out["learned"] = learned_form(la)
+    except Exception as e:
+        out["learned"] = {"error": str(e)[:300]}
+    return out
+
+
+def stream_arm(args) -> None:
+    print(json.dumps(stream_form(args.fmt, args.steps, args.warmup)))
+
+
+def batch_form(steps: int, warmup: int) -> dict:
+    """16 seeded channels (16..64 GBd, QPSK/16QAM/64QAM, 2^16..2^20 symbols) in one graph launch,
+    beside the same frames through single handles of the same (tuned) configurations one after the
+    other on the same stream (the plain chain, channel by channel)."""
     import numpy as np
     import torch
 
@@ -581,29 +647,53 @@ def batch_arm(args) -> None:
     stream = torch.cuda.current_stream()
     args_ = ([t.data_ptr() for t in xs], n_sym, [t.data_ptr() for t in refs], [t.data_ptr() for t in outs],
              stream.cuda_stream)
-    for _ in range(args.warmup):
-        rx.rx_batch_process(b, *args_)
-    torch.cuda.synchronize()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    ms = []
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rx.rx_batch_process(b, *args_)
-        e1.record(stream)
+
+    def timed(run):
+        for _ in range(warmup):
+            run()
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    t = sum(ms) / len(ms)
+        ms = []
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms)
+
+    t = timed(lambda: rx.rx_batch_process(b, *args_))
     tuned = [(rx.rx_batch_config(b, i).fft_size, rx.rx_batch_config(b, i).lms_threads) for i in range(len(chans))]
-    print(json.dumps({"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
-                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "batch16-seed42", "channels": len(chans), "symbols": sum(n_sym),
-                                 "tuned_fft_and_lms_threads": tuned, "tune_s": round(tune_s, 2),
-                                 "l2": "flushed between timed steps"},
-                      "graph_launches_per_step": 1}))
+    errs = sum(rx.rx_batch_stats(b, i)["bit_errors"] for i in range(len(chans)))
+    counted = sum(rx.rx_batch_stats(b, i)["bits_counted"] for i in range(len(chans)))
+    # the plain chain: one handle per channel with the tuned configuration, frames one after another
+    hs = [rx.rx_create(rx.rx_batch_config(b, i)) for i in range(len(chans))]
+
+    def singles():
+        for i, h in enumerate(hs):
+            rx.rx_process(h, xs[i].data_ptr(), n_sym[i], refs[i].data_ptr(), outs[i].data_ptr(), stream.cuda_stream)
+    t1 = timed(singles)
+    s_errs = sum(rx.rx_stats(h)["bit_errors"] for h in hs)
+    s_counted = sum(rx.rx_stats(h)["bits_counted"] for h in hs)
+    for h in hs:
+        rx.rx_destroy(h)
     rx.rx_batch_destroy(b)
+    return {"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": t, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch16-seed42", "channels": len(chans), "symbols": sum(n_sym),
+                       "tuned_fft_and_lms_threads": tuned, "tune_s": round(tune_s, 2),
+                       "l2": "flushed between timed steps"},
+            "graph_launches_per_step": 1, "ber": errs / max(counted, 1),
+            "plain_sequential": {"value": bits / (t1 * 1e-3) / 1e9, "ms_per_step": t1,
+                                 "ber": s_errs / max(s_counted, 1),
+                                 "note": "same frames, one rx_process call per channel in turn"}}
+
+
+def batch_arm(args) -> None:
+    print(json.dumps(batch_form(args.steps, args.warmup)))
 
 
 # per position of the sequence: one position is one DP symbol (4 input channels I_x, Q_x, I_y, Q_y),
@@ -612,7 +702,7 @@ CNN_FWD_FLOP = 2 * 9 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 4)
 CNN_TRAIN_FLOP = 2 * CNN_FWD_FLOP + 2 * 9 * (64 * 64 + 64 * 64 + 64 * 4)         # + weight and data gradients
 
 
-def learned_arm(args) -> None:
+def learned_form(args) -> dict:
     """Learned post-equaliser on split-step DP-16QAM 32 GBd, 10 x 80 km: the plain chain on training
     frames, training by the library's kernels, then timed steps of chain + post-equaliser + decisions
     on a frame of another seed; BER/EVM of both forms reported."""
@@ -723,8 +813,12 @@ def learned_arm(args) -> None:
                      "note": "whole forward's algorithmic flops over its time (4 conv launches)"},
         "cnn_ms": tc, "gpu_launches": int(launches), "generate_s": round(gen_s, 1), "clocks": clk.summary(),
     }
-    print(json.dumps(line))
     rcv.close()
+    return line
+
+
+def learned_arm(args) -> None:
+    print(json.dumps(learned_form(args)))
 
 
 def cnn_arm(args) -> None:
@@ -1120,10 +1214,20 @@ def kk_cpu_baseline(n_sym: int, reps: int = 3) -> dict:
 
 def main():
     args = parse()
+    if args.impl == "ours" and args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # started without torchrun: one replica rank per GPU, as torchrun would start them
+        spawn_ranks(args.gpus, dispatch, args)
+        return
+    dispatch(args)
+
+
+def dispatch(args) -> None:
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "stream":
         stream_arm(args)
+    elif args.workload == "forms":
+        print(json.dumps(other_forms(args)))
     elif args.workload == "batch":
         batch_arm(args)
     elif args.workload == "learned":

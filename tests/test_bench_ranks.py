@@ -1,6 +1,7 @@
 """The multi-GPU path of bench.py on the CPU: every rank runs an independent replica of the chain (the
 path has no data-path collective), and the job's time is the slowest rank's. Two gloo ranks check the
-max-over-ranks reduction and the whole-job line rate computed from it."""
+max-over-ranks reduction and the whole-job line rate computed from it, and the self-launch that
+`bench.py --gpus N` uses without torchrun gives each rank the rendezvous environment torchrun would."""
 
 from __future__ import annotations
 
@@ -51,3 +52,32 @@ def test_single_process_is_unchanged():
     import bench
     assert bench.max_over_ranks([3.5, float("inf")]) == [3.5, float("inf")]
     assert abs(bench.replica_line_rate(1, 1 << 23, 20, 14.4) - (1 << 23) * 20 / 0.0144 / 1e9) < 1e-12
+
+
+def _env_rank(out_dir: str) -> None:
+    import json
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    dist.init_process_group("gloo")                       # env:// rendezvous from the spawned environment
+    t = torch.tensor([float(rank + 1)])
+    dist.all_reduce(t)
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"env{rank}.json"), "w") as f:
+        json.dump({"rank": rank, "world": world, "local": int(os.environ["LOCAL_RANK"]),
+                   "addr": os.environ["MASTER_ADDR"], "sum": float(t[0])}, f)
+
+
+def test_self_launch_gives_each_rank_the_torchrun_environment(tmp_path):
+    pytest.importorskip("torch.multiprocessing")
+    import json
+
+    import bench
+    world = 2
+    bench.spawn_ranks(world, _env_rank, str(tmp_path))
+    res = sorted((json.load(open(tmp_path / f"env{r}.json")) for r in range(world)), key=lambda d: d["rank"])
+    assert [d["rank"] for d in res] == [0, 1] and all(d["world"] == world for d in res)
+    assert [d["local"] for d in res] == [0, 1] and all(d["addr"] == "127.0.0.1" for d in res)
+    assert all(d["sum"] == 3.0 for d in res)
