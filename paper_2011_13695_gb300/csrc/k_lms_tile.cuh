@@ -29,8 +29,8 @@
 // Windows are split by sample parity (tap k reads parity k % 2) into three
 // rotating buffers: a block's window is copied asynchronously (cp.async) two
 // steps ahead, and one step ahead each thread waits for its own copies and
-// derotates them in place by a per-block phasor (shared table) times a
-// per-position phasor (registers).
+// derotates them in place by a per-block phasor times a per-position phasor
+// (both shared tables).
 #pragma once
 
 #include "rx_kernels.h"
@@ -47,11 +47,39 @@ struct LmsTileShape {
     static constexpr int IM = G0 > G1 ? G0 : G1;            // tap slots per lane (even)
     static constexpr int R = OPL + IM;                      // sample registers (OPL + IM - 1 used; even)
     static constexpr int PADL = 2 * IM + 2;                 // zero pad below logical index 0
-    // origin of the parity-r array: makes every lane's first sample 16-byte aligned
-    static constexpr int org(int r) { return PADL + ((PADL + C - r + 1) & 1); }
-    static constexpr int PS0 = org(0) + LB + C + 4;         // length of one parity array (float2)
-    static constexpr int PS = ((PS0 + 11) / 16) * 16 + 4;   // = 4 mod 16: the four arrays start in
-                                                            // different bank quarters
+    // origin of the parity-r array for an extra shift xo (even) of the odd-parity arrays: makes every
+    // lane's first sample 16-byte aligned
+    static constexpr int org2(int r, int xo) { return PADL + ((PADL + C - r + 1) & 1) + (r ? xo : 0); }
+    static constexpr int PS0 = PADL + 1 + 6 + LB + C + 4;   // least length of one parity array (float2)
+    // 16-byte bank group (of 8) of the first sample load of lane class (p, r, ig) for a parity-array
+    // stride ps: the eight classes of one output subset form one quarter-warp of a 16-byte load
+    static constexpr int group(int ps, int xo, int p, int r, int ig) {
+        const int i0 = ig ? (r ? G1 : G0) : 0;
+        return (((2 * p + r) * ps + org2(r, xo) + C - r - i0 - IM + 1) / 2 % 8 + 8) % 8;
+    }
+    // quarter-warp conflicts of the sample loads (the largest number of classes sharing a group)
+    static constexpr int conflicts(int ps, int xo) {
+        int worst = 0;
+        for (int g = 0; g < 8; ++g) {
+            int n = 0;
+            for (int c = 0; c < 8; ++c) n += group(ps, xo, c >> 2, (c >> 1) & 1, c & 1) == g ? 1 : 0;
+            worst = n > worst ? n : worst;
+        }
+        return worst;
+    }
+    static constexpr int pick(bool want_xo) {             // the least-conflict (stride, shift), smallest first
+        int bps = PS0 + (PS0 & 1), bxo = 0, bw = 99;
+        for (int xo = 0; xo <= 6; xo += 2)
+            for (int ps = PS0 + (PS0 & 1); ps < PS0 + 34; ps += 2) {
+                const int c = conflicts(ps, xo);
+                if (c < bw) { bw = c; bps = ps; bxo = xo; }
+            }
+        return want_xo ? bxo : bps;
+    }
+    static constexpr int PS = pick(false);                  // parity-array stride (float2, even)
+    static constexpr int XO = pick(true);                   // extra origin shift of the odd-parity arrays
+    static constexpr int org(int r) { return org2(r, XO); }
+    static constexpr int ESP = LB + LB / 8;                 // error row: one pad slot per eight outputs
     static constexpr int XW = 2 * LB + T - 1;               // window samples per polarisation
     static constexpr int KS = (2 * XW + NT - 1) / NT;       // window samples staged per thread
     static constexpr int TS = IM + 1;                       // staged tap row stride (float4, odd)
@@ -60,14 +88,16 @@ struct LmsTileShape {
     // shared memory in float4 units
     static constexpr int WIN4 = 3 * 4 * PS / 2;             // three windows x 4 parity arrays
     static constexpr int TAP4 = 8 * TS;
-    static constexpr int ES4 = LB;
+    static constexpr int ES4 = ESP;
     static constexpr int NPART = OPL == 8 ? NW * 4 : NW;    // gradient partials per tap component
     static constexpr int PART4 = (NPART * 8 * 2 * IM + 3) / 4;
-    static constexpr int YTS = 84;                          // transposition stride per output subset (float2)
+    static constexpr int YTS = 88;                          // transposition stride per output subset (float2):
+                                                            // = 8 mod 16, two subsets' 8-byte stores fill the 32 banks
     static constexpr int YT4 = OPL == 8 ? NW * 4 * YTS / 2 : 0;
     static constexpr int YP4 = (NW + 1) / 2;
     static constexpr int BT4 = NBT / 2;
-    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + BT4 + YT4;
+    static constexpr int TAB4 = (XW + 1) / 2;
+    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + BT4 + YT4 + TAB4;
     static_assert(NT % 32 == 0 && LB % (NW * 4) == 0, "LB must be a multiple of 4 x warps");
     static_assert(OPL == 2 || OPL == 4 || OPL == 8, "2, 4 or 8 outputs per lane");
     static_assert(T % 2 == 1 && T >= 3, "odd tap count");
@@ -88,20 +118,21 @@ __device__ __forceinline__ void rs_level(float (&v)[M], int mask, int lane) {
     }
 }
 
-// 128-thread CTAs (the segments' shape) keep to 170 registers so that three share an SM
+// 128-thread CTAs (the segments' shape) keep to 128 registers so that four share an SM
 template <int NT, int T, int LB>
-__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     using S = LmsTileShape<NT, T, LB>;
     constexpr int NW = S::NW, OPL = S::OPL, IM = S::IM, R = S::R, PS = S::PS;
     extern __shared__ float4 smem4[];
     if (a.run_if && *a.run_if == 0) return;
     float2* win = reinterpret_cast<float2*>(smem4);                 // [3 buffers][p][parity][PS]
     float4* tapx = smem4 + S::WIN4;                                 // [class][TS]: (hx, hx, hy, hy)
-    float4* es = tapx + S::TAP4;                                    // [LB]: (ex, ex, ey, ey)
+    float4* es = tapx + S::TAP4;                                    // [ESP]: (ex, ex, ey, ey), padded
     float* part = reinterpret_cast<float*>(es + S::ES4);            // [warp][class][2 IM]
     float2* ypart = reinterpret_cast<float2*>(es + S::ES4 + S::PART4);   // [NW]
     float2* btab = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [NBT]
     float2* ytr = btab + 2 * S::BT4;                                // [warp][subset][YTS] (OPL == 8)
+    float2* tab = ytr + 2 * S::YT4;                                 // [XW]: per-position derotation phasor
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
@@ -144,8 +175,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
     const float2* const xp0 = a.x;
     const float2* const xp1 = a.x + a.xstride;
     const long long gfirst = a.g0 + a.off + 2 * nfirst - S::C;   // input-sample index of block 0's window
-    if (inc)
+    if (inc) {
         for (int b = tid; b < nblk; b += NT) btab[b] = nco_conj(inc, gfirst + 2LL * LB * b);   // nblk <= NBT
+        for (int jj = tid; jj < S::XW; jj += NT) tab[jj] = nco_conj(inc, jj);
+    }
 
     // every window the CTA will read, requested into L2 (128-byte lines)
     if (nblk > 0) {
@@ -167,37 +200,31 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
     // thread waits for its own copies one step ahead and (DD) derotates them in place, and the barriers
     // of that step make them visible. Slots and relative global offsets are the same for every block.
     const int64_t gstart = a.off + 2 * nfirst - S::C;                  // window start of block 0
-    uint32_t sslot[S::KS];                                             // shared address in buffer 0
-    int spos[S::KS];                                                   // window position, -1: idle
-    float2 sph[S::KS];                                                 // per-position derotation phasor
-    const float2* ssrc[S::KS];                                         // source of the position in block 0
     const uint32_t win_sa = (uint32_t)__cvta_generic_to_shared(win);
-#pragma unroll
-    for (int k = 0; k < S::KS; ++k) {
+    // window position k of this thread: polarisation, position in the window, shared slot in buffer 0
+    auto spos = [&](int k, int& pp, int& jj) -> bool {
         const int sidx = tid + k * NT;
-        const int pp = sidx >= S::XW ? 1 : 0, jj = sidx - pp * S::XW;
-        const bool in = sidx < 2 * S::XW;
+        pp = sidx >= S::XW ? 1 : 0;
+        jj = sidx - pp * S::XW;
+        return sidx < 2 * S::XW;
+    };
+    auto sslot = [&](int pp, int jj) -> uint32_t {
         const int par = jj & 1;
-        sslot[k] = win_sa + 8u * (uint32_t)((2 * pp + par) * PS + S::org(par) + (jj >> 1));
-        spos[k] = in ? jj : -1;
-        sph[k] = (in && inc) ? nco_conj(inc, jj) : make_float2(1.0f, 0.0f);
-        ssrc[k] = (pp ? xp1 : xp0) + gstart + jj;                      // address arithmetic only
-    }
+        return win_sa + 8u * (uint32_t)((2 * pp + par) * PS + S::org(par) + (jj >> 1));
+    };
     auto issue = [&](int blk) {                                        // copies of block blk's window
         const int64_t g0b = gstart + 2LL * LB * blk;
         const bool fast = g0b >= 0 && g0b + S::XW <= a.xlen;          // whole window inside the buffer
         const uint32_t boff = 8u * (uint32_t)((blk % 3) * 4 * PS);
-        const int64_t d = 2LL * LB * blk;
+        const float2* src0 = xp0 + g0b;
+        const float2* src1 = xp1 + g0b;
 #pragma unroll
         for (int k = 0; k < S::KS; ++k) {
-            if (spos[k] < 0) continue;
-            bool ok = true;
-            if (!fast) {
-                const int64_t gi = g0b + spos[k];
-                ok = gi >= 0 && gi < a.xlen;
-            }
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sslot[k] + boff),
-                         "l"(ok ? ssrc[k] + d : xp0), "r"(ok ? 8 : 0)
+            int pp, jj;
+            if (!spos(k, pp, jj)) continue;
+            const bool ok = fast || (g0b + jj >= 0 && g0b + jj < a.xlen);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sslot(pp, jj) + boff),
+                         "l"(ok ? (pp ? src1 : src0) + jj : xp0), "r"(ok ? 8 : 0)
                          : "memory");
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -209,9 +236,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
             float2* wb = win + (blk % 3) * 4 * PS;
 #pragma unroll
             for (int k = 0; k < S::KS; ++k) {
-                if (spos[k] < 0) continue;
-                float2* slot = wb + (sslot[k] - win_sa) / 8;
-                *slot = cmul(*slot, cmul(base, sph[k]));
+                int pp, jj;
+                if (!spos(k, pp, jj)) continue;
+                float2* slot = wb + (sslot(pp, jj) - win_sa) / 8;
+                *slot = cmul(*slot, cmul(base, tab[jj]));
             }
         }
     };
@@ -290,7 +318,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
         } else {
             // eight outputs per lane: transpose through shared memory (lane (ns, cls) writes its
             // partial of output j at [ns][j][cls], the lane of output j reads the eight classes as
-            // four 16-byte loads; strides 10 and 84 keep both sides free of bank conflicts)
+            // four 16-byte loads; strides 10 and YTS keep both sides free of bank conflicts)
             float2* yw = ytr + w * (4 * S::YTS) + ns * S::YTS;
 #pragma unroll
             for (int j = 0; j < OPL; ++j) yw[j * 10 + cls] = make_float2(v[2 * j], v[2 * j + 1]);
@@ -329,19 +357,18 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) k_lms_tile(LmsArgs a) {
             }
         }
         // 3. the errors of the warp's outputs to the lanes of their subset, then the gradient partials
-        if (owner) es[nown] = make_float4(e.x, e.x, e.y, e.y);
+        if (owner) es[nown + nown / 8] = make_float4(e.x, e.x, e.y, e.y);
         __syncwarp();
-        float4 ev[OPL];
-#pragma unroll
-        for (int j = 0; j < OPL; ++j) ev[j] = es[nl0 + j];
         float2 gA[IM], gB[IM];
 #pragma unroll
-        for (int t = 0; t < IM; ++t) {
-            gA[t] = gB[t] = make_float2(0.0f, 0.0f);
+        for (int t = 0; t < IM; ++t) gA[t] = gB[t] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int j = 0; j < OPL; ++j) {
-                gA[t] = __ffma2_rn(make_float2(ev[j].x, ev[j].y), xr[j + IM - 1 - t], gA[t]);
-                gB[t] = __ffma2_rn(make_float2(ev[j].z, ev[j].w), xr[j + IM - 1 - t], gB[t]);
+        for (int j = 0; j < OPL; ++j) {                            // one error live at a time
+            const float4 ev = es[nl0 + j + (nl0 + j) / 8];
+#pragma unroll
+            for (int t = 0; t < IM; ++t) {
+                gA[t] = __ffma2_rn(make_float2(ev.x, ev.y), xr[j + IM - 1 - t], gA[t]);
+                gB[t] = __ffma2_rn(make_float2(ev.z, ev.w), xr[j + IM - 1 - t], gB[t]);
             }
         }
         float g[2 * IM];
