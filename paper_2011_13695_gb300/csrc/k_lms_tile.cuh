@@ -28,9 +28,13 @@
 //      copy; barrier.
 // Windows are split by sample parity (tap k reads parity k % 2) into three
 // rotating buffers: a block's window is copied asynchronously (cp.async) two
-// steps ahead, and one step ahead each thread waits for its own copies and
-// derotates them in place by a per-block phasor times a per-position phasor
-// (both shared tables).
+// steps ahead, and one step ahead each thread waits for its own copies.
+// The FO derotation of the input (phase 2 pi F g of input sample g, F turns
+// per sample) is linear in g, so it moves exactly onto the taps and outputs:
+// y[n] = e^{-j 2 pi F (g0 + 2n + c)} sum_k (h_k e^{+j 2 pi F k}) x[2n + c - k].
+// The kernel keeps the taps in that rotating frame, multiplies each output by
+// the NCO phasor of its centre sample and each error by the conjugate before
+// the gradient, and stages raw samples; the final taps are rotated back.
 #pragma once
 
 #include "rx_kernels.h"
@@ -83,7 +87,6 @@ struct LmsTileShape {
     static constexpr int XW = 2 * LB + T - 1;               // window samples per polarisation
     static constexpr int KS = (2 * XW + NT - 1) / NT;       // window samples staged per thread
     static constexpr int TS = IM + 1;                       // staged tap row stride (float4, odd)
-    static constexpr int NBT = 256;                         // derotation bases of the first NBT blocks
     static constexpr int NUPD = 8 * 2 * IM;                 // tap-component update threads
     // shared memory in float4 units
     static constexpr int WIN4 = 3 * 4 * PS / 2;             // three windows x 4 parity arrays
@@ -95,9 +98,7 @@ struct LmsTileShape {
                                                             // = 8 mod 16, two subsets' 8-byte stores fill the 32 banks
     static constexpr int YT4 = OPL == 8 ? NW * 4 * YTS / 2 : 0;
     static constexpr int YP4 = (NW + 1) / 2;
-    static constexpr int BT4 = NBT / 2;
-    static constexpr int TAB4 = (XW + 1) / 2;
-    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + BT4 + YT4 + TAB4;
+    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + YT4;
     static_assert(NT % 32 == 0 && LB % (NW * 4) == 0, "LB must be a multiple of 4 x warps");
     static_assert(OPL == 2 || OPL == 4 || OPL == 8, "2, 4 or 8 outputs per lane");
     static_assert(T % 2 == 1 && T >= 3, "odd tap count");
@@ -130,9 +131,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     float4* es = tapx + S::TAP4;                                    // [ESP]: (ex, ex, ey, ey), padded
     float* part = reinterpret_cast<float*>(es + S::ES4);            // [warp][class][2 IM]
     float2* ypart = reinterpret_cast<float2*>(es + S::ES4 + S::PART4);   // [NW]
-    float2* btab = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [NBT]
-    float2* ytr = btab + 2 * S::BT4;                                // [warp][subset][YTS] (OPL == 8)
-    float2* tab = ytr + 2 * S::YT4;                                 // [XW]: per-position derotation phasor
+    float2* ytr = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [warp][subset][YTS] (OPL == 8)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
@@ -158,7 +157,11 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     const int uk = 2 * ((uig ? uG : 0) + ut) + ur;                  // tap index of the owned slot
     float hreg = 0.0f;
     if (ureal) {
-        const float2 h = a.taps_in[q * 2 * T + up * T + uk];
+        float2 h = a.taps_in[q * 2 * T + up * T + uk];
+        if (inc) {                                                  // rotating frame: h'_k = h_k e^{+j 2 pi F k}
+            const float2 ph = nco_conj(inc, uk);
+            h = cmul(h, make_float2(ph.x, -ph.y));
+        }
         hreg = (uf & 1) ? h.y : h.x;
         float* dst = reinterpret_cast<float*>(tapx + uc * S::TS + ut) + ((uf & 1) ? 2 : 0);
         dst[0] = hreg;
@@ -174,11 +177,9 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     const int64_t nfirst = start - (int64_t)nwarm * LB;            // block b starts at symbol nfirst + b LB
     const float2* const xp0 = a.x;
     const float2* const xp1 = a.x + a.xstride;
-    const long long gfirst = a.g0 + a.off + 2 * nfirst - S::C;   // input-sample index of block 0's window
-    if (inc) {
-        for (int b = tid; b < nblk; b += NT) btab[b] = nco_conj(inc, gfirst + 2LL * LB * b);   // nblk <= NBT
-        for (int jj = tid; jj < S::XW; jj += NT) tab[jj] = nco_conj(inc, jj);
-    }
+    // input-sample index of the centre tap's sample of output n of block 0: the frame of its phasor
+    const long long gout0 = a.g0 + a.off + 2 * nfirst + S::C;
+
 
     // every window the CTA will read, requested into L2 (128-byte lines)
     if (nblk > 0) {
@@ -229,19 +230,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    auto land = [&](int blk) {                                         // own copies of block blk complete
+    auto land = [&]() {                                               // own copies of the next block complete
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        if (inc) {
-            const float2 base = btab[blk];
-            float2* wb = win + (blk % 3) * 4 * PS;
-#pragma unroll
-            for (int k = 0; k < S::KS; ++k) {
-                int pp, jj;
-                if (!spos(k, pp, jj)) continue;
-                float2* slot = wb + (sslot(pp, jj) - win_sa) / 8;
-                *slot = cmul(*slot, cmul(base, tab[jj]));
-            }
-        }
     };
 
     __syncthreads();                                                // tables and taps staged
@@ -249,7 +239,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         issue(0);
         if (nblk > 1) issue(1);
         else asm volatile("cp.async.commit_group;\n" ::: "memory");
-        land(0);
+        land();
     }
     __syncthreads();
 
@@ -330,6 +320,14 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
                      cadd(cadd(make_float2(c45.x, c45.y), make_float2(c45.z, c45.w)),
                           cadd(make_float2(c67.x, c67.y), make_float2(c67.z, c67.w))));
         }
+        // rotating frame: the taps are h_k e^{+j 2 pi F k} and the samples are not derotated, so the
+        // output takes the phasor of its centre sample, e^{-j 2 pi F (g0 + 2n + c)}, and the error the
+        // conjugate before it meets the samples in the gradient
+        float2 phi = make_float2(1.0f, 0.0f);
+        if (inc) {
+            phi = nco_conj(inc, gout0 + 2LL * ((int64_t)b * LB + nown));
+            y = cmul(y, phi);
+        }
         const bool valid = nown < L;
         if (b >= nwarm && a.y != nullptr && owner && valid) a.y[(int64_t)q * a.ystride + n0 + nown] = y;
 
@@ -357,6 +355,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
             }
         }
         // 3. the errors of the warp's outputs to the lanes of their subset, then the gradient partials
+        if (inc) e = cmulc(e, phi);
         if (owner) es[nown + nown / 8] = make_float4(e.x, e.x, e.y, e.y);
         __syncwarp();
         float2 gA[IM], gB[IM];
@@ -388,7 +387,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
 #pragma unroll
             for (int u = 0; u < IM / 2; ++u) pw[u] = g[u];
         }
-        if (b + 1 < nblk) land(b + 1);                              // next window in place before the barriers
+        if (b + 1 < nblk) land();                                   // next window in place before the barriers
         __syncthreads();
 
         // 4. tap update: the warps' partials in a fixed order
@@ -414,9 +413,14 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         }
         __syncthreads();
     }
-    if (seg == nseg - 1 && a.taps_out && ureal) {
-        float* dst = reinterpret_cast<float*>(a.taps_out + q * 2 * T + up * T + uk) + (uf & 1);
-        *dst = hreg;
+    // final taps of the last segment, back from the rotating frame (the staged copy holds both components)
+    if (seg == nseg - 1 && a.taps_out && tid < 2 * T) {
+        const int tp = tid / T, tk = tid - tp * T, tr = tk & 1, ti = tk >> 1;
+        const int tG = tr ? S::G1 : S::G0, tig = ti >= tG ? 1 : 0;
+        const float4 hv = tapx[(tp * 4 + tr * 2 + tig) * S::TS + ti - tig * tG];
+        float2 h = make_float2(hv.x, hv.z);
+        if (inc) h = cmul(h, nco_conj(inc, tk));
+        a.taps_out[q * 2 * T + tp * T + tk] = h;
     }
 }
 
