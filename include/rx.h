@@ -290,6 +290,28 @@ rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, in
 void rx_pe_destroy(rx_pe* p);
 
 /*
+ * rx_pe_targets: the post-equaliser's training labels on the device (no paper
+ * counterpart: the paper has no learned equaliser). The label of output q at
+ * index n is s_{p_q}[n + d_q] (-j)^{r_q}, the transmitted symbol that the
+ * alignment of stage A6 (pol_map, rotation, delay as rx_stats reports them)
+ * puts there, and 0 where n + d_q lies outside [0, n_ref). Each whole block of
+ * `block` symbols is then turned by the quarter turn u in {1, j, -1, -j} that
+ * minimises sum |z - label u|^2 over the block (the first minimum of FP32 sums
+ * taken in a fixed order), so that labels follow a carrier slip of the chain
+ * instead of teaching the network to undo it; a tail shorter than a block
+ * keeps its labels. d_z: DEVICE float [2][n_sym][2] (I, Q) the chain's
+ * carrier-recovered symbols; d_symbols: DEVICE float [2][n_ref][2] the
+ * transmitted symbols; h_pol_map, h_rotation, h_delay: HOST int32 [2];
+ * d_target: DEVICE float [2][n_sym][2] receives the labels (must not overlap
+ * the inputs). Caller-owned; nothing is allocated; asynchronous on `stream`.
+ * RX_EINVAL for NULL pointers, n_sym < 1, n_ref < 1, block < 1, a pol_map
+ * entry outside {0, 1} or a rotation outside 0..3.
+ */
+rx_status rx_pe_targets(const float* d_z, int64_t n_sym, const float* d_symbols, int64_t n_ref,
+                        const int32_t* h_pol_map, const int32_t* h_rotation, const int32_t* h_delay, int32_t block,
+                        float* d_target, rx_stream_t stream);
+
+/*
  * rx_fp32_fma_rate: measured FP32 FMA throughput of the current device (no
  * paper counterpart; the roofline of the chain's FP32-bound stages uses it).
  * One launch of every SM's worth of CTAs, each thread running eight
@@ -400,6 +422,35 @@ rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff
 rx_status rx_kk_process(rx_kk* k, const uint16_t* d_codes, int64_t n_samples, int64_t first_sample, float* d_field,
                         float* d_out, rx_stream_t stream);
 void rx_kk_destroy(rx_kk* k);
+/*
+ * rx_kk_equalise: Step 9 of the KK receiver (Sec. IV-D: a TD widely-linear
+ * DD-LMS that also undoes the transmitter's IQ imbalance, then the decision
+ * and demapping), on the front end's output at 2 samples/symbol:
+ *   y[n] = sum_k h[k] x[2n + c - k] + g[k] conj(x[2n + c - k]),
+ * c = (T-1)/2, x zero outside [0, x_len); per block of block_len symbols
+ *   psi = arg(-sum_n y[n]^4) / 4,  d = dec(y e^{-j psi}),  e = d e^{j psi} - y,
+ *   h[k] += mu sum_n e[n] conj(x[2n + c - k]),  g[k] += mu_conj sum_n e[n] x[2n + c - k];
+ * the segment schedule of rx_dd_lms_wl (segments of seg_blocks blocks from
+ * d_taps_in, warm-up blocks ahead of every segment but the first). The
+ * decisions are the nearest square-QAM points of y (the front end keeps the
+ * tone's phase, so no quarter-turn search), Gray-demapped.
+ * d_x: DEVICE float [x_len][2] (I, Q), e.g. rx_kk_process's d_out;
+ * d_taps_in: DEVICE float [2][T][2] (h, then g); d_y: DEVICE float
+ * [n_sym][2] equalised symbols; d_bits: DEVICE uint32 [ceil(n_sym m / 32)]
+ * decided bits in rx_process's layout for one polarisation (nullable);
+ * d_taps_out: DEVICE, layout of d_taps_in, the last segment's final taps
+ * (nullable). Caller-owned buffers; the taps pass through scratch the handle
+ * allocated at rx_kk_create; nothing is allocated here. Runs the generic
+ * widely-linear block-LMS kernel with one output row and one input
+ * polarisation. n_taps odd 3..63, block_len 16..256, seg_blocks >= 1,
+ * warmup_blocks >= 0, bits_per_sym 2/4/6/8; RX_EINVAL otherwise, for n_sym <
+ * 1, x_len < 1 or a NULL handle, input, taps or output. Asynchronous on
+ * `stream`; one handle's calls must not overlap (they share its scratch).
+ */
+rx_status rx_kk_equalise(rx_kk* k, const float* d_x, int64_t x_len, int32_t n_taps, const float* d_taps_in,
+                         int64_t n_sym, int32_t block_len, int32_t seg_blocks, int32_t warmup_blocks,
+                         int32_t bits_per_sym, float mu, float mu_conj, float* d_y, uint32_t* d_bits,
+                         float* d_taps_out, rx_stream_t stream);
 
 /*
  * rx_ingest_run: real-time ingest emulation (Sec. II-C, II-D). A digitiser

@@ -130,3 +130,46 @@ def unflatten(vec: np.ndarray, C: int = 64, K: int = 9):
         out.append([vec[o:o + nw].reshape(ws), vec[o + nw:o + nw + nb].reshape(bs)])
         o += nw + nb
     return out
+
+
+# ----------------------------------------------------------------------------
+# Training labels of the learned post-equaliser (reading taken, no paper
+# counterpart): the transmitted symbols put in the frame of the chain's
+# outputs by the alignment A6 found, then each block of `block` symbols
+# turned by the quarter turn that best matches the outputs, so that a
+# carrier slip of the chain is followed by the labels, not learned.
+# ----------------------------------------------------------------------------
+
+def aligned_targets(pol_map, rotation, delay, symbols: np.ndarray, n_sym: int) -> np.ndarray:
+    """Output q at index n carries s_{p_q}[n + d_q] turned by j^{r_q} (A6), so its label is
+    s_{p_q}[n + d_q] (-j)^{r_q}; indices without a transmitted symbol get 0."""
+    n_ref = symbols.shape[1]
+    out = np.zeros((2, n_sym), dtype=np.complex128)
+    for q in range(2):
+        p, r, d = pol_map[q], rotation[q], delay[q]
+        for n in range(n_sym):
+            if 0 <= n + d < n_ref:
+                out[q, n] = symbols[p, n + d] * (-1j) ** r
+    return out
+
+
+def quarter_turn_errors(z: np.ndarray, target: np.ndarray, block: int) -> np.ndarray:
+    """err[u, q, j] = sum over block j of |z_q - target_q j^u|^2, u = 0..3 (whole blocks only)."""
+    nb = z.shape[1] // block
+    err = np.zeros((4, 2, nb))
+    for u in range(4):
+        diff = z[:, :nb * block] - target[:, :nb * block] * (1j ** u)
+        err[u] = (np.abs(diff) ** 2).reshape(2, nb, block).sum(axis=-1)
+    return err
+
+
+def repair_quarter_turns(z: np.ndarray, target: np.ndarray, block: int = 1024) -> np.ndarray:
+    """Labels of each whole block turned by its best quarter turn (first minimum); a tail shorter
+    than a block keeps its labels."""
+    err = quarter_turn_errors(z, target, block)
+    best = np.argmin(err, axis=0)                       # [2, nb], ties to the smallest turn
+    out = np.array(target, dtype=np.complex128)
+    for q in range(2):
+        for j in range(best.shape[1]):
+            out[q, j * block:(j + 1) * block] *= 1j ** best[q, j]
+    return out

@@ -126,3 +126,32 @@ def kk_receive(codes: np.ndarray, scale: float, dc: float, i_min: float, tone_ov
     phi = hilbert_os(l, N)
     E = reconstruct(a, phi, tone_over_fs)
     return E, matched_decimate(E, N, rolloff)
+
+
+# ----------------------------------------------------------------------------
+# Step 9 (Sec. IV-D): the KK receiver's TD widely-linear DD-LMS, then the
+# decision and demapping, on the front end's output at 2 samples/symbol.
+# Reading: the single-polarisation equaliser is the widely-linear A4 with one
+# input and one output (y = h * x + g * conj(x) per output symbol, the A4
+# block phase, decisions, update and segment schedule); the front end keeps
+# the tone's phase, so the decisions need no quarter-turn search.
+# ----------------------------------------------------------------------------
+
+def kk_equalise(x: np.ndarray, h: np.ndarray, g: np.ndarray, n_sym: int, L_b: int, seg_blocks: int,
+                warmup_blocks: int, m: int, mu: float, mu_conj: float, diag=None):
+    """x: [S2] complex at 2 samples/symbol; h, g: [T] initial direct and conjugate taps.
+    Returns (y [n_sym], final h, final g, bits uint8 [n_sym m] of the Gray-demapped decisions).
+
+    Runs the dual-polarisation widely-linear segmented DD-LMS of ``mimo.dd_lms_wl`` with the second
+    input plane zero and row 0 holding (h, 0, g, 0): the second input's taps then receive e x_2 = 0
+    and stay zero, so row 0 is exactly the single-polarisation equaliser (row 1 is not used).
+    ``diag`` (a dict) receives the per-segment decision margins of ``mimo.dd_lms`` (row 0 in [:, 0])."""
+    from . import mimo, qam
+    T = h.shape[0]
+    xbuf = np.zeros((2, x.shape[0]), dtype=np.complex128)
+    xbuf[0] = x
+    taps = mimo.wl_identity_taps(T)
+    taps[0, 0], taps[0, 1], taps[0, 2], taps[0, 3] = h, 0.0, g, 0.0
+    y, hf = mimo.dd_lms_wl(xbuf, taps, n_sym, L_b, seg_blocks, warmup_blocks, m, mu, mu_conj, diag=diag)
+    li, lq = qam.decide_levels(y[0], m)
+    return y[0], hf[0, 0].copy(), hf[0, 2].copy(), qam.levels_to_bits(li, lq, m).reshape(-1)

@@ -32,9 +32,55 @@ struct rx_kk {
     float scale = 1.0f, dc = 0.0f, i_min = 0.0f;
     float2* tw = nullptr;        // FFT twiddles
     float* H = nullptr;          // [N] 2 RRC(f_k) / N
+    float2* eq = nullptr;        // Step 9 taps in the equaliser's row layout: in [4][RX_TMAX], out [4][RX_TMAX]
 };
 
 namespace {
+
+// Step 9 taps: caller layout [2][T] (h, then the conjugate taps g) -> row 0 of the equaliser's layout
+// [h_0, h_1, g_0, g_1] with the second input polarisation's taps zero, and back
+__global__ void k_kk_taps_in(const float2* in, int T, float2* out) {
+    const int t = threadIdx.x;
+    if (t < 4 * T) {
+        const int v = t / (2 * T), p = (t / T) & 1, k = t % T;
+        out[t] = p ? make_float2(0.0f, 0.0f) : in[v * T + k];
+    }
+}
+
+__global__ void k_kk_taps_out(const float2* eq, int T, float2* out) {
+    const int t = threadIdx.x;
+    if (t < 2 * T) {
+        const int v = t / T, k = t % T;
+        out[t] = eq[v * 2 * T + k];
+    }
+}
+
+// Step 9 decisions: Gray bits of the nearest square-QAM point, packed as rx_process packs one
+// polarisation (stream bit i in bit i % 32 of word i / 32; the first m/2 bits of a symbol are the
+// Gray word of its in-phase level, most significant first). One thread per output word.
+__global__ void k_kk_demap(const float2* __restrict__ y, int64_t n_sym, int m, uint32_t* __restrict__ bits,
+                           int64_t words) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= words) return;
+    const Qam qm = make_qam(m);
+    uint32_t word = 0;
+    int64_t cur = -1;
+    uint32_t sb = 0;
+    for (int i = 0; i < 32; ++i) {
+        const int64_t b = w * 32 + i;
+        const int64_t n = b / m;
+        if (n >= n_sym) break;
+        if (n != cur) {
+            cur = n;
+            const float2 v = y[n];
+            const int li = qam_level(v.x, qm), lq = qam_level(v.y, qm);
+            sb = qam_bits(li, lq, qm);                       // Gray I word in the top h bits, Q below
+        }
+        const int j = (int)(b - n * m);                      // bit j of the symbol, first transmitted = 0
+        word |= ((sb >> (m - 1 - j)) & 1u) << i;
+    }
+    bits[w] = word;
+}
 
 struct KkArgs {
     const uint16_t* codes;
@@ -210,9 +256,11 @@ rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff
         H[i] = (float)(2.0 * amp / (double)N);
     }
     if (cudaMalloc(&k->tw, sizeof(float2) * RX_FFT_TW_N) != cudaSuccess ||
-        cudaMalloc(&k->H, sizeof(float) * N) != cudaSuccess) {
+        cudaMalloc(&k->H, sizeof(float) * N) != cudaSuccess ||
+        cudaMalloc(&k->eq, sizeof(float2) * 8 * RX_TMAX) != cudaSuccess) {
         if (k->tw) cudaFree(k->tw);
         if (k->H) cudaFree(k->H);
+        if (k->eq) cudaFree(k->eq);
         delete k;
         return RX_ENOMEM;
     }
@@ -221,6 +269,7 @@ rx_status rx_kk_create(int32_t fft_size, double tone_over_fs, double rrc_rolloff
         cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(k->tw);
         cudaFree(k->H);
+        cudaFree(k->eq);
         delete k;
         return RX_ECUDA;
     }
@@ -252,7 +301,57 @@ void rx_kk_destroy(rx_kk* k) {
     if (!k) return;
     if (k->tw) cudaFree(k->tw);
     if (k->H) cudaFree(k->H);
+    if (k->eq) cudaFree(k->eq);
     delete k;
+}
+
+rx_status rx_kk_equalise(rx_kk* k, const float* d_x, int64_t x_len, int32_t n_taps, const float* d_taps_in,
+                         int64_t n_sym, int32_t block_len, int32_t seg_blocks, int32_t warmup_blocks,
+                         int32_t bits_per_sym, float mu, float mu_conj, float* d_y, uint32_t* d_bits,
+                         float* d_taps_out, rx_stream_t stream) {
+    if (!k || !d_x || !d_taps_in || !d_y || n_sym < 1 || x_len < 1) return RX_EINVAL;
+    if (n_taps < 3 || n_taps > 63 || !(n_taps & 1)) return RX_EINVAL;
+    if (block_len < 16 || block_len > 256 || seg_blocks < 1 || warmup_blocks < 0) return RX_EINVAL;
+    if (bits_per_sym != 2 && bits_per_sym != 4 && bits_per_sym != 6 && bits_per_sym != 8) return RX_EINVAL;
+    const int64_t L_seg = (int64_t)seg_blocks * block_len;
+    if ((n_sym + L_seg - 1) / L_seg > 0x7fffffffLL) return RX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    float2* eq_in = k->eq;
+    float2* eq_out = k->eq + 4 * RX_TMAX;
+    k_kk_taps_in<<<1, 256, 0, s>>>(reinterpret_cast<const float2*>(d_taps_in), n_taps, eq_in);
+    LmsArgs a{};
+    a.x = reinterpret_cast<const float2*>(d_x);
+    a.xstride = x_len;
+    a.xlen = x_len;
+    a.off = 0;
+    a.T = n_taps;
+    a.Lb = block_len;
+    a.n_sym = n_sym;
+    a.L_seg = L_seg;
+    a.n_wu = warmup_blocks;
+    a.cma = 0;
+    a.mu = mu;
+    a.mu_c = mu_conj;
+    a.R2 = 0.0f;
+    a.m = bits_per_sym;
+    a.derotate = 0;
+    a.g0 = 0;
+    a.taps_in = eq_in;
+    a.taps_out = eq_out;
+    a.y = reinterpret_cast<float2*>(d_y);
+    a.ystride = n_sym;
+    a.run_if = nullptr;
+    a.st = nullptr;
+    a.exclusive = 0;
+    a.npol = 1;
+    if (launch_lms_wl_generic(a, 256, s) != cudaSuccess) return RX_ECUDA;
+    if (d_taps_out) k_kk_taps_out<<<1, 128, 0, s>>>(eq_out, n_taps, reinterpret_cast<float2*>(d_taps_out));
+    if (d_bits) {
+        const int64_t words = (n_sym * bits_per_sym + 31) / 32;
+        k_kk_demap<<<(unsigned)((words + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float2*>(d_y), n_sym,
+                                                                    bits_per_sym, d_bits, words);
+    }
+    return cudaGetLastError() == cudaSuccess ? RX_OK : RX_ECUDA;
 }
 
 }  // extern "C"

@@ -65,7 +65,7 @@ __device__ __forceinline__ void lms_prefetch(const LmsArgs& a, LmsCtx<NT>& s, in
         if (t < 2 * XW) {
             const int p = t >= XW ? 1 : 0, jj = t - p * XW;
             const int64_t i = i0 + jj;
-            if (i >= 0 && i < a.xlen) v = a.x[(int64_t)p * a.xstride + i];
+            if (i >= 0 && i < a.xlen && p < a.npol) v = a.x[(int64_t)p * a.xstride + i];
         }
         s.pf[r] = v;
     }
@@ -598,7 +598,7 @@ static cudaError_t launch_lms_t(const LmsArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_lms<NT, WL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_lms<NT, WL><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
+    k_lms<NT, WL><<<dim3((unsigned)nseg, a.npol == 1 ? 1 : 2), NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -622,6 +622,16 @@ cudaError_t launch_lms(const LmsArgs& a, int threads, cudaStream_t s) {
         case 512: return launch_lms_t<512>(a, s);
         case 1024: return launch_lms_t<1024>(a, s);
         default: return launch_lms_t<256>(a, s);
+    }
+}
+
+cudaError_t launch_lms_wl_generic(const LmsArgs& a, int threads, cudaStream_t s) {
+    if (threads < 4 * a.T) return cudaErrorInvalidValue;
+    switch (threads) {
+        case 256: return launch_lms_t<256, true>(a, s);
+        case 512: return launch_lms_t<512, true>(a, s);
+        case 1024: return launch_lms_t<1024, true>(a, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -44,6 +44,8 @@ struct LmsArgs {
     int exclusive;         // 1: each CTA asks for a whole SM's shared memory, so that no other kernel's
                            // CTA shares its SM (the serial acquisition is latency-bound)
     float mu_c;            // widely-linear form only: step of the conjugate taps
+    int npol = 2;          // input polarisations; 1 (generic kernel only): the second input plane reads as
+                           // zero and only output row 0 runs, i.e. the single-polarisation equaliser
 };
 
 // shared memory a launch asks for: the kernel's need, or with `exclusive` the most a CTA may have
@@ -68,6 +70,8 @@ int kk_fft_size(const rx_kk* k);
 // mu_c the conjugate taps' step; threads 0 (choose), 128/256 for the compile-time shapes, else
 // 256/512/1024 and >= 4T
 cudaError_t launch_lms_wl(const LmsArgs& a, int threads, cudaStream_t s);
+// the generic widely-linear kernel alone (any npol), threads 256/512/1024 and >= 4T
+cudaError_t launch_lms_wl_generic(const LmsArgs& a, int threads, cudaStream_t s);
 
 cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
                               int64_t nw, const float2* taps, float2* yw, cudaStream_t s);

@@ -8,6 +8,7 @@
 
 #include "../../include/rx.h"
 #include "rx_cnn.h"
+#include "rx_dev.cuh"
 
 struct rx_pe {
     CnnBufs B;
@@ -39,9 +40,96 @@ void pe_free(rx_pe* p) {
         if (q) cudaFree(q);
 }
 
+// Training labels (rx_pe_targets): CTA (j, q) owns symbols [j block, (j + 1) block) of output q.
+__global__ void k_pe_targets(const float2* __restrict__ z, int64_t n_sym, const float2* __restrict__ s,
+                             int64_t n_ref, int p0, int p1, int r0, int r1, int64_t d0, int64_t d1, int block,
+                             float2* __restrict__ out) {
+    __shared__ float4 wsum[32];
+    __shared__ int best_s;
+    const int q = blockIdx.y;
+    const int p = q ? p1 : p0, r = q ? r1 : r0;
+    const int64_t d = q ? d1 : d0;
+    const int64_t lo = (int64_t)blockIdx.x * block, hi = min(n_sym, lo + block);
+    const bool whole = hi - lo == block;
+    const float2* sp = s + (int64_t)p * n_ref;
+    const float2* zq = z + (int64_t)q * n_sym;
+    auto label = [&](int64_t n) -> float2 {             // s_p[n + d] (-j)^r, 0 outside the reference
+        const int64_t i = n + d;
+        if (i < 0 || i >= n_ref) return make_float2(0.0f, 0.0f);
+        const float2 v = sp[i];
+        switch (r) {
+            case 1: return make_float2(v.y, -v.x);
+            case 2: return make_float2(-v.x, -v.y);
+            case 3: return make_float2(-v.y, v.x);
+            default: return v;
+        }
+    };
+    int best = 0;
+    if (whole) {
+        // sum |z - t u|^2 over the block for u = 1, j, -1, -j: per thread, then the warps in a fixed order
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+            const float2 t = label(n), zz = zq[n];
+            const float a0 = zz.x - t.x, b0 = zz.y - t.y;     // u = 1:  t
+            const float a1 = zz.x + t.y, b1 = zz.y - t.x;     // u = j:  (-t.y, t.x)
+            const float a2 = zz.x + t.x, b2 = zz.y + t.y;     // u = -1: -t
+            const float a3 = zz.x - t.y, b3 = zz.y + t.x;     // u = -j: (t.y, -t.x)
+            e.x += fmaf(a0, a0, b0 * b0);
+            e.y += fmaf(a1, a1, b1 * b1);
+            e.z += fmaf(a2, a2, b2 * b2);
+            e.w += fmaf(a3, a3, b3 * b3);
+        }
+        e.x = warp_sum(e.x);
+        e.y = warp_sum(e.y);
+        e.z = warp_sum(e.z);
+        e.w = warp_sum(e.w);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) wsum[w] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float4 t = wsum[0];
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                t.x += wsum[k].x; t.y += wsum[k].y; t.z += wsum[k].z; t.w += wsum[k].w;
+            }
+            const float v[4] = {t.x, t.y, t.z, t.w};
+            int b = 0;
+            for (int u = 1; u < 4; ++u)
+                if (v[u] < v[b]) b = u;                        // first minimum
+            best_s = b;
+        }
+        __syncthreads();
+        best = best_s;
+    }
+    for (int64_t n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+        float2 t = label(n);
+        switch (best) {                                        // t j^best
+            case 1: t = make_float2(-t.y, t.x); break;
+            case 2: t = make_float2(-t.x, -t.y); break;
+            case 3: t = make_float2(t.y, -t.x); break;
+            default: break;
+        }
+        out[(int64_t)q * n_sym + n] = t;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+rx_status rx_pe_targets(const float* d_z, int64_t n_sym, const float* d_symbols, int64_t n_ref,
+                        const int32_t* h_pol_map, const int32_t* h_rotation, const int32_t* h_delay, int32_t block,
+                        float* d_target, rx_stream_t stream) {
+    if (!d_z || !d_symbols || !d_target || !h_pol_map || !h_rotation || !h_delay) return RX_EINVAL;
+    if (n_sym < 1 || n_ref < 1 || block < 1) return RX_EINVAL;
+    for (int q = 0; q < 2; ++q)
+        if (h_pol_map[q] < 0 || h_pol_map[q] > 1 || h_rotation[q] < 0 || h_rotation[q] > 3) return RX_EINVAL;
+    const int64_t nb = (n_sym + block - 1) / block;
+    if (nb > 0x7fffffff) return RX_EINVAL;
+    k_pe_targets<<<dim3((unsigned)nb, 2), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float2*>(d_z), n_sym, reinterpret_cast<const float2*>(d_symbols), n_ref, h_pol_map[0],
+        h_pol_map[1], h_rotation[0], h_rotation[1], h_delay[0], h_delay[1], block, reinterpret_cast<float2*>(d_target));
+    return cudaGetLastError() == cudaSuccess ? RX_OK : RX_ECUDA;
+}
 
 int64_t rx_pe_param_count(int32_t channels, int32_t kernel) {
     if (channels != 64 || kernel != KW) return -1;

@@ -4,9 +4,10 @@ loop that drives it.
 The network (four 1-D convolutions 4->64->64->64->4, kernel 9, ReLU between,
 residual output z + f(z)) maps the carrier-recovered symbols z of both
 polarisations to corrected symbols. Its forward pass, MSE loss, backward pass
-and Adam update all run in librx's kernels (BF16 weights and activations,
-FP32 accumulation and master weights); this module only slices sequences,
-picks learning rates and counts steps. The paper has no learned equaliser.
+and Adam update, and the training labels, all run in librx's kernels (BF16
+weights and activations, FP32 accumulation and master weights); this module
+only slices sequences, picks learning rates and counts steps. The paper has no
+learned equaliser.
 """
 
 from __future__ import annotations
@@ -119,48 +120,21 @@ class PostEqualiser:
         return losses
 
 
-def aligned_targets(stats: dict, symbols: torch.Tensor, n_sym: int) -> torch.Tensor:
-    """Transmitted symbols [2, n_ref] put in the frame of the receiver's outputs z [2, n_sym] using the
-    alignment found by the decision stage: z_q[n] j^r_q carries s_p_q[n + d_q] (single frames), so the
-    target of z_q[n] is s_p_q[n + d_q] (-j)^r_q. Positions without a transmitted symbol get 0."""
-    out = torch.zeros((2, n_sym), dtype=torch.complex64, device=symbols.device)
-    n_ref = symbols.shape[1]
-    for q in range(2):
-        p, r, d = stats["pol_map"][q], stats["rotation"][q], stats["delay"][q]
-        a, b = max(0, -d), min(n_sym, n_ref - d)
-        if b > a:
-            out[q, a:b] = symbols[p, a + d:b + d] * ((-1j) ** r)
-    return out
-
-
-def repair_quarter_turns(z: torch.Tensor, target: torch.Tensor, block: int = 1024) -> torch.Tensor:
-    """Targets with each block of ``block`` symbols turned by the quarter turn that best matches z.
-    A carrier-phase cycle slip of the chain turns all later outputs by a multiple of pi/2 relative to
-    the alignment found at the start of the frame; training labels follow the slip so that the
-    network is not taught to undo it. (Decisions of the chain itself are not changed.)"""
-    n = (z.shape[1] // block) * block
-    if n == 0:
-        return target
-    zb = z[:, :n].reshape(2, -1, block)
-    tb = target[:, :n].reshape(2, -1, block)
-    turns = torch.tensor([1, 1j, -1, -1j], dtype=torch.complex64, device=z.device)
-    err = torch.stack([(zb - tb * u).abs().square().sum(-1) for u in turns])
-    best = turns[err.argmin(0)]
-    out = target.clone()
-    out[:, :n] = (tb * best[..., None]).reshape(2, n)
-    return out
-
-
-def chain_pairs(rcv, x: torch.Tensor, n_sym: int, ref: torch.Tensor, symbols: torch.Tensor):
+def chain_pairs(rcv, x: torch.Tensor, n_sym: int, ref: torch.Tensor, symbols: torch.Tensor, block: int = 1024):
     """Run the plain chain on one single frame and return (z, target, stats): the carrier-recovered
-    symbols, the transmitted symbols aligned to them (``aligned_targets``, then
-    ``repair_quarter_turns``) and the chain's statistics for this frame alone. ``rcv`` is a :class:`receiver.Receiver`; ``ref`` the packed transmitted bits
-    on the device; ``symbols`` the transmitted symbols (complex64 [2, n_ref]) on the device."""
+    symbols, their training labels (rx_pe_targets: the transmitted symbols put in z's frame by the
+    alignment the decision stage found, each block of ``block`` symbols turned by the quarter turn
+    that best matches z) and the chain's statistics for this frame alone. ``rcv`` is a
+    :class:`receiver.Receiver`; ``ref`` the packed transmitted bits on the device; ``symbols`` the
+    transmitted symbols (contiguous complex64 [2, n_ref]) on the device."""
     before = rcv.stats()
     rcv.process(x, n_sym, ref, None)
     st = rcv.stats()
     z = rcv.symbols(n_sym)
-    return z, repair_quarter_turns(z, aligned_targets(st, symbols, n_sym)), stats_delta(before, st)
+    target = torch.empty_like(z)
+    rx.rx_pe_targets(z.data_ptr(), n_sym, symbols.data_ptr(), symbols.shape[1], st["pol_map"], st["rotation"],
+                     st["delay"], block, target.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    return z, target, stats_delta(before, st)
 
 
 def stats_delta(before: dict, after: dict) -> dict:

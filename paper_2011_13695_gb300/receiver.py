@@ -161,6 +161,27 @@ class KKFrontEnd:
         return stats, out
 
 
+    def equalise(self, y: torch.Tensor, n_sym: int, taps: torch.Tensor, block_len: int, seg_blocks: int,
+                 warmup_blocks: int, bits_per_sym: int, mu: float, mu_conj: float,
+                 out: torch.Tensor | None = None, bits: torch.Tensor | None = None,
+                 taps_out: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None):
+        """Step 9 (rx_kk_equalise): widely-linear DD-LMS of the front end's output y (complex64, 2
+        samples/symbol), decisions and Gray demapping. taps: complex64 [2, T] (h, then g). Returns
+        (equalised symbols complex64 [n_sym], decided bits int32 [ceil(n_sym m / 32)])."""
+        if y.dtype != torch.complex64 or not y.is_cuda or not y.is_contiguous() or y.dim() != 1:
+            raise ValueError("y must be a contiguous 1-D complex64 CUDA tensor")
+        if taps.dtype != torch.complex64 or not taps.is_cuda or not taps.is_contiguous() or taps.dim() != 2 \
+                or taps.shape[0] != 2:
+            raise ValueError("taps must be a contiguous complex64 CUDA tensor [2, T]")
+        out = torch.empty(n_sym, dtype=torch.complex64, device=y.device) if out is None else out
+        words = (n_sym * bits_per_sym + 31) // 32
+        bits = torch.empty(words, dtype=torch.int32, device=y.device) if bits is None else bits
+        s = stream or torch.cuda.current_stream()
+        rx.rx_kk_equalise(self.k, y.data_ptr(), y.shape[0], taps.shape[1], taps.data_ptr(), n_sym, block_len,
+                          seg_blocks, warmup_blocks, bits_per_sym, mu, mu_conj, out.data_ptr(), bits.data_ptr(),
+                          taps_out.data_ptr() if taps_out is not None else None, s.cuda_stream)
+        return out, bits
+
 class PAMReceiver:
     """IM/DD PAM-M chain with FD clock recovery (rx_pam_*) on torch device tensors: 12-bit codes in
     16-bit words (any 2-byte dtype) at 2 samples/symbol in; extracted samples (float32), level

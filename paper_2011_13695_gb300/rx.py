@@ -30,7 +30,7 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
            "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl",
            "rx_kk_create", "rx_kk_process", "rx_kk_destroy", "rx_ingest_run", "rx_pam_create", "rx_pam_process",
-           "rx_pam_get", "rx_pam_destroy", "rx_fp32_fma_rate")
+           "rx_pam_get", "rx_pam_destroy", "rx_fp32_fma_rate", "rx_pe_targets", "rx_kk_equalise")
 RX_PAM_CLOCK, RX_PAM_PHASE, RX_PAM_WINDING, RX_PAM_OFFSETS, RX_PAM_STATS = range(5)
 RX_STATIC_MAX_SYMBOLS = 262144
 
@@ -131,6 +131,9 @@ def lib() -> C.CDLL:
             "rx_pam_get": (i32, [vp, i32, vp, i64, vp]),
             "rx_pam_destroy": (None, [vp]),
             "rx_fp32_fma_rate": (i32, [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
+            "rx_pe_targets": (i32, [vp, i64, vp, i64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), i32, vp, vp]),
+            "rx_kk_equalise": (i32, [vp, vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, vp,
+                                     vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -333,6 +336,14 @@ def rx_pe_destroy(p: int) -> None:
     lib().rx_pe_destroy(p)
 
 
+def rx_pe_targets(d_z: int, n_sym: int, d_symbols: int, n_ref: int, pol_map, rotation, delay, block: int,
+                  d_target: int, stream: int | None) -> None:
+    """Training labels of the post-equaliser on the device; see include/rx.h."""
+    arr = lambda v: (C.c_int32 * 2)(*[int(x) for x in v])
+    _check(lib().rx_pe_targets(d_z, n_sym, d_symbols, n_ref, arr(pol_map), arr(rotation), arr(delay), block, d_target,
+                               stream or None), "rx_pe_targets")
+
+
 def rx_fp32_fma_rate(packed: bool, iters: int, stream: int | None) -> tuple[float, float]:
     """Measured FP32 FMA throughput (flops/s, ms of the timed launch); see include/rx.h."""
     f, t = C.c_double(), C.c_double()
@@ -369,6 +380,15 @@ def rx_kk_create(fft_size: int, tone_over_fs: float, rrc_rolloff: float, code_sc
 def rx_kk_process(k: int, d_codes: int, n_samples: int, first_sample: int, d_field: int, d_out: int,
                   stream: int | None) -> None:
     _check(lib().rx_kk_process(k, d_codes, n_samples, first_sample, d_field, d_out, stream or None), "rx_kk_process")
+
+
+def rx_kk_equalise(k: int, d_x: int, x_len: int, n_taps: int, d_taps_in: int, n_sym: int, block_len: int,
+                   seg_blocks: int, warmup_blocks: int, bits_per_sym: int, mu: float, mu_conj: float, d_y: int,
+                   d_bits: int | None, d_taps_out: int | None, stream: int | None) -> None:
+    """Step 9 of the KK receiver: widely-linear DD-LMS, decisions and demapping; see include/rx.h."""
+    _check(lib().rx_kk_equalise(k, d_x, x_len, n_taps, d_taps_in, n_sym, block_len, seg_blocks, warmup_blocks,
+                                bits_per_sym, mu, mu_conj, d_y, d_bits or None, d_taps_out or None, stream or None),
+           "rx_kk_equalise")
 
 
 def rx_ingest_run(k: int, h_source, buffer_samples: int, sample_rate_hz: float, n_streams: int, n_buffers: int,

@@ -7,7 +7,9 @@ symbols, 4 samples per symbol):
    energy (``synth.channel.modulate``);
 2. root-raised-cosine pulse shaping in the frequency domain over the whole
    frame, gain 2 (= sqrt(4)) so that an RRC matched filter of gain 2 returns
-   the symbols at the symbol instants; the mean sample power P_s is measured
+   the symbols at the symbol instants, optionally followed by a transmitter
+   IQ imbalance s -> mu s + nu conj(s) (``iq_imbalance``, the model of
+   ``synth.channel.iq_coefficients``); the mean sample power P_s is measured
    (about 1/4: one symbol of unit energy per 4 samples);
 3. a carrier tone of amplitude A = sqrt(CSPR P_s) (CSPR = carrier-to-signal
    power ratio) ``tone_offset`` Hz below the signal centre. In the tone's frame the
@@ -32,7 +34,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .channel import modulate, rrc_spectrum
+from .channel import iq_coefficients, modulate, rrc_spectrum
 
 SPS = 4
 
@@ -47,6 +49,7 @@ class KKLink:
     cspr_db: float = 11.0
     snr_db: float | None = None      # None = noiseless
     adc_clip: float = 6.0            # ADC full scale in standard deviations of I
+    iq_imbalance: tuple | None = None  # transmitter IQ imbalance (amplitude eps, phase skew rad) of s(t)
 
     @property
     def fs(self) -> float:
@@ -79,6 +82,9 @@ def generate_kk(p: KKLink, seed: int) -> KKFrame:
     x[::SPS] = sym
     f = np.fft.fftfreq(S, d=1.0 / p.fs)
     s = np.fft.ifft(np.fft.fft(x) * np.sqrt(SPS) * rrc_spectrum(f, p.symbol_rate, p.rolloff))
+    if p.iq_imbalance is not None:
+        mu, nu = iq_coefficients(*p.iq_imbalance)
+        s = mu * s + nu * np.conj(s)
     P_s = float(np.mean(np.abs(s) ** 2))
     A = float(np.sqrt(10.0 ** (p.cspr_db / 10.0) * P_s))
     n = np.arange(S, dtype=np.float64)
