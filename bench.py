@@ -209,7 +209,7 @@ class ClockSampler:
 # DRAM traffic per launch from one ncu capture (profiles/), valid while the kernel's source file is
 # unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
 PROFILED_TRAFFIC = {
-    "dd_acq": ("k_lms_tile.cuh", "31339cadf54e641e7297e8d5854aef4a346bfbc8", 563968),   # DRAM bytes read + written, one ncu capture of this launch
+    "dd_acq": ("k_lms_tile.cuh", "4aa98ce249ce91924c62ffc72be7ff16c405b044", 558848),   # DRAM bytes read + written, one ncu capture of this launch
     "wl": ("k_lms_fast.cuh", "fca5f277b4ecd771cc2e0b0acdff6c7ea8cf98cc", 33638912),
 }
 

@@ -211,10 +211,17 @@ __device__ __forceinline__ void load_b4(const uint8_t* bq, int64_t k0, int64_t N
     else prev = bprev_carry >= 0 ? bprev_carry : bs[0];
 }
 
+// Pass 1: the jump sum of every tile; the first tile also copies the carried (b*, m) of its
+// polarisation after the sums (snap[q] = {b_prev, m_prev}), where pass 2 reads it while its last
+// tile writes the new carry.
 __global__ void k_unwrap_sums(const uint8_t* __restrict__ bstar, int64_t bstride, int64_t N, int B,
                               const RxDevState* st, int* tile_sums, int ntiles, int vec) {
     __shared__ int red[32];
     const int q = blockIdx.y;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        tile_sums[2 * ntiles + 2 * q] = st->b_prev[q];
+        tile_sums[2 * ntiles + 2 * q + 1] = st->m_prev[q];
+    }
     const uint8_t* bq = bstar + (int64_t)q * bstride;
     const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;
     int sum = 0;
@@ -231,27 +238,15 @@ __global__ void k_unwrap_sums(const uint8_t* __restrict__ bstar, int64_t bstride
     if (threadIdx.x == 0) tile_sums[q * ntiles + blockIdx.x] = total;
 }
 
-__global__ void k_unwrap_scan(int* tile_sums, int ntiles, const RxDevState* st) {
-    __shared__ int red[32];
-    const int q = blockIdx.x;
-    int carry = st->m_prev[q];
-    for (int base = 0; base < ntiles; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int v = i < ntiles ? tile_sums[q * ntiles + i] : 0;
-        int total;
-        const int ex = block_exclusive_scan(v, red, &total);
-        __syncthreads();
-        if (i < ntiles) tile_sums[q * ntiles + i] = carry + ex;     // becomes the tile's base
-        carry += total;
-        __syncthreads();
-    }
-}
-
+// Pass 2: the tile's base count (the carried m plus the sums of the tiles before it, integers in
+// any order), the scan within the tile, the derotation; the thread holding symbol N - 1 writes the
+// carry for the next frame.
 __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, const uint8_t* __restrict__ bstar,
-                               int64_t bstride, int64_t N, int B, const int* tile_base, int ntiles,
-                               const RxDevState* st, int* m_out, int64_t mstride, float2* z, int64_t zstride,
+                               int64_t bstride, int64_t N, int B, const int* tile_sums, int ntiles,
+                               RxDevState* st, int* m_out, int64_t mstride, float2* z, int64_t zstride,
                                int vec) {
     __shared__ int red[32];
+    __shared__ int s_base[UTHR / 32];
     __shared__ float2 rot[RX_BPS_MAXB];
     const int q = blockIdx.y;
     if (threadIdx.x < B) {
@@ -259,20 +254,28 @@ __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, co
         sincospif(-((float)threadIdx.x / (float)B - 0.5f) * 0.5f, &s, &c);   // e^{-j theta_b}
         rot[threadIdx.x] = make_float2(c, s);
     }
+    const int* snap = tile_sums + 2 * ntiles + 2 * q;
+    int before = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) before += tile_sums[q * ntiles + i];
+    before = __reduce_add_sync(0xffffffffu, before);
+    if ((threadIdx.x & 31) == 0) s_base[threadIdx.x >> 5] = before;
     const uint8_t* bq = bstar + (int64_t)q * bstride;
     const int64_t k0 = (int64_t)blockIdx.x * UT + threadIdx.x * 4;
     int J[4] = {0, 0, 0, 0}, bs[4] = {0, 0, 0, 0};
     int sum = 0;
     if (k0 < N) {
         int prev;
-        load_b4(bq, k0, N, st->b_prev[q], vec != 0, bs, prev);
+        load_b4(bq, k0, N, snap[0], vec != 0, bs, prev);
         for (int u = 0; u < 4; ++u) {
             if (k0 + u < N) J[u] = jump(prev, bs[u], B);
             prev = bs[u];
             sum += J[u];
         }
     }
-    int m = tile_base[q * ntiles + blockIdx.x] + block_exclusive_scan(sum, red, nullptr);
+    int m = block_exclusive_scan(sum, red, nullptr);  // its barriers also publish s_base
+    int base = snap[1];
+    for (int w = 0; w < UTHR / 32; ++w) base += s_base[w];
+    m += base;
     __syncthreads();
     if (k0 >= N) return;
     const float2* yq = y + (int64_t)q * ystride + k0;
@@ -301,6 +304,11 @@ __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, co
         }
         v[u] = w;
     }
+    if (N - 1 - k0 < 4) {                             // the frame's last symbol: the next frame's carry
+        const int u = (int)(N - 1 - k0);
+        st->b_prev[q] = bs[u];
+        st->m_prev[q] = mm[u];
+    }
     if (whole) {
         *reinterpret_cast<int4*>(mq) = make_int4(mm[0], mm[1], mm[2], mm[3]);
         *reinterpret_cast<float4*>(zq) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
@@ -311,15 +319,6 @@ __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, co
                 mq[u] = mm[u];
                 zq[u] = v[u];
             }
-    }
-}
-
-__global__ void k_unwrap_commit(const uint8_t* bstar, int64_t bstride, const int* m_out, int64_t mstride, int64_t N,
-                                RxDevState* st) {
-    const int q = threadIdx.x;
-    if (q < 2 && N > 0) {
-        st->b_prev[q] = bstar[(int64_t)q * bstride + N - 1];
-        st->m_prev[q] = m_out[(int64_t)q * mstride + N - 1];
     }
 }
 
@@ -351,10 +350,8 @@ cudaError_t launch_unwrap(const float2* y, int64_t ystride, const uint8_t* bstar
     const int vec = al(bstar, bstride, 4) && al(y, ystride * 8, 16) && al(z, zstride * 8, 16) &&
                     al(m_out, mstride * 4, 16);
     k_unwrap_sums<<<dim3(ntiles, 2), UTHR, 0, s>>>(bstar, bstride, N, B, st, tile_sums, ntiles, vec);
-    k_unwrap_scan<<<2, 1024, 0, s>>>(tile_sums, ntiles, st);
     k_unwrap_apply<<<dim3(ntiles, 2), UTHR, 0, s>>>(y, ystride, bstar, bstride, N, B, tile_sums, ntiles, st, m_out,
                                                     mstride, z, zstride, vec);
-    k_unwrap_commit<<<1, 32, 0, s>>>(bstar, bstride, m_out, mstride, N, st);
-    if (nlaunch) *nlaunch += 4;
+    if (nlaunch) *nlaunch += 2;
     return cudaGetLastError();
 }

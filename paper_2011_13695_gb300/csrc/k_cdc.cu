@@ -38,8 +38,20 @@ __device__ __forceinline__ float2 load_sample(const void* in, int64_t idx, float
 // A0: mean power of the first n_win samples of each polarisation: FP32 sums per thread (a few
 // dozen samples each), then pairwise across the warp and the CTA; scale = 1/sqrt(P).
 template <int FMT>
-__global__ void k_power(const void* in, float in_scale, int64_t S, int64_t n_win, RxDevState* st) {
+__global__ void k_power(const void* in, float in_scale, int64_t S, int64_t n_win, RxDevState* st, int single) {
     const int p = blockIdx.x;
+    if (p == 0 && threadIdx.x == 0) {                 // start of the frame (its first frame of a stream)
+        if (single) {
+            st->b_prev[0] = st->b_prev[1] = -1;
+            st->m_prev[0] = st->m_prev[1] = 0;
+            st->sync_valid = 0;
+        }
+        st->fo_code = 0;
+        st->nco_inc = 0;
+        st->fo_valid = 0;
+        st->cma_reran = 0;
+        st->cma_rho = 0.0f;
+    }
     float acc = 0.0f;
     for (int64_t i = threadIdx.x; i < n_win; i += blockDim.x) {
         float2 v = load_sample<FMT>(in, (int64_t)p * S + i, in_scale);
@@ -181,11 +193,11 @@ cudaError_t launch_cdc_f(const CdcArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_power(const void* in, int fmt, float in_scale, int64_t S, int64_t n_win, RxDevState* st,
-                         cudaStream_t s) {
+                         int single, cudaStream_t s) {
     if (n_win > S) n_win = S;
-    if (fmt == 0) k_power<0><<<2, 1024, 0, s>>>(in, in_scale, S, n_win, st);
-    else if (fmt == 1) k_power<1><<<2, 1024, 0, s>>>(in, in_scale, S, n_win, st);
-    else k_power<2><<<2, 1024, 0, s>>>(in, in_scale, S, n_win, st);
+    if (fmt == 0) k_power<0><<<2, 1024, 0, s>>>(in, in_scale, S, n_win, st, single);
+    else if (fmt == 1) k_power<1><<<2, 1024, 0, s>>>(in, in_scale, S, n_win, st, single);
+    else k_power<2><<<2, 1024, 0, s>>>(in, in_scale, S, n_win, st, single);
     return cudaGetLastError();
 }
 

@@ -6,11 +6,12 @@
 // transmitted polarisation, quarter turn and symbol delay each output
 // carries: 16 CTAs (output q, tx pol p, turn r) count decision matches for
 // every delay in [-D, D] over the sync window (a warp ballot + popcount per
-// delay), and one thread picks the best (p, r, d) with ties to the smallest
-// tuple. Counting then runs one thread per output symbol: the decided levels
-// become Gray bits, 32 symbols of a warp assemble m output words with
-// warp-wide ORs, errors are the popcount of the XOR with the reference bits,
-// integer counters accumulate with 64-bit atomics, EVM sums in FP64.
+// delay), and the last CTA to finish picks the best (p, r, d) with ties to
+// the smallest tuple. Counting then runs one thread per output symbol: the
+// decided levels become Gray bits, 32 symbols of a warp assemble m output
+// words with warp-wide ORs, errors are the popcount of the XOR with the
+// reference bits, integer counters accumulate with 64-bit atomics, EVM sums
+// as FP32 partials turned into fixed-point integer atomics.
 #include <algorithm>
 
 #include "rx_kernels.h"
@@ -49,61 +50,14 @@ __device__ __forceinline__ void bits_to_levels(uint32_t sbits, int m, int& li, i
     lq = gray_to_level(msb & ((1u << h) - 1u));
 }
 
-// blockIdx.x: (output q, tx pol p, turn r); blockIdx.y: slice of the sync window. Match counts of
-// the slice for every delay are added into counts (zeroed by k_sync_pick after it reads them).
-__global__ void k_sync(const float2* __restrict__ z, int64_t zstride, const uint32_t* __restrict__ ref,
-                       int64_t refstride, int64_t n_ref, int m, int64_t lo, int64_t hi, int D, int64_t lat,
-                       int64_t slice, int* counts) {
-    const int q = blockIdx.x >> 3, p = (blockIdx.x >> 2) & 1, r = blockIdx.x & 3;
-    const int64_t s0 = lo + (int64_t)blockIdx.y * slice;
-    const int64_t s1 = min(hi, s0 + slice);
-    extern __shared__ int16_t txl[];                  // tx levels for t in [s0 - lat - D, s1 - lat + D)
-    __shared__ int cnt[2 * RX_MAX_DELAY + 1];
-    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) cnt[i] = 0;
-    if (s0 >= s1) return;
-    const int64_t t0 = s0 - lat - D;
-    const int64_t nt = (s1 - s0) + 2 * D;
-    const uint32_t* rp = ref + (int64_t)p * refstride;
-    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) {
-        const int64_t t = t0 + i;
-        int16_t v = -1;
-        if (t >= 0 && t < n_ref) {
-            int li, lq;
-            bits_to_levels(ref_symbol_bits(rp, t, m), m, li, lq);
-            v = (int16_t)(li | (lq << 8));
-        }
-        txl[i] = v;
-    }
-    __syncthreads();
-    const Qam qm = make_qam(m);
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = s0 + (threadIdx.x & ~31); base < s1; base += blockDim.x) {
-        const int64_t n = base + lane;
-        int16_t mine = -2;
-        if (n < s1) {
-            const float2 v = quarter(z[(int64_t)q * zstride + n], r);
-            mine = (int16_t)(qam_level(v.x, qm) | (qam_level(v.y, qm) << 8));
-        }
-        for (int d = -D; d <= D; ++d) {
-            const bool hit = (n < s1) && (txl[n - s0 + D + d] == mine);
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (lane == 0 && bal) atomicAdd(&cnt[d + D], __popc(bal));
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x)
-        if (cnt[i]) atomicAdd(&counts[blockIdx.x * (2 * D + 1) + i], cnt[i]);
-}
-
-// One warp per output q: the (p, r, d) with most matches, ties to the smallest tuple (p, then r,
-// then d). The warp then zeroes the counts it read for the next sync.
-__global__ void k_sync_pick(int* counts, int D, int64_t len, RxDevState* st) {
-    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;     // launched with 64 threads
+// One warp per output q (warps 0 and 1 of the last CTA): the (p, r, d) with most matches, ties to
+// the smallest tuple (p, then r, then d). The warp then zeroes the counts it read for the next sync.
+__device__ void sync_pick(int* counts, int D, int64_t len, RxDevState* st, int q, int lane) {
     const int nd = 2 * D + 1, ntup = 8 * nd;
     int* cq = counts + (int64_t)q * ntup;             // tuple index t = (p * 4 + r) * nd + (d + D)
     int bv = -1, bt = 0;
     for (int t = lane; t < ntup; t += 32) {
-        const int v = cq[t];
+        const int v = __ldcg(&cq[t]);
         if (v > bv) { bv = v; bt = t; }               // t increases along the lane's scan
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -122,8 +76,72 @@ __global__ void k_sync_pick(int* counts, int D, int64_t len, RxDevState* st) {
         if (10LL * bv < 9LL * len) atomicOr(&st->err_word, 2u);
         if (q == 0) st->sync_len = (int)len;
     }
+}
+
+// blockIdx.x: (output q, tx pol p, turn r); blockIdx.y: slice of the sync window. Match counts of
+// the slice for every delay are added into counts; the last CTA to arrive (a ticket after the
+// counts, zero between launches) picks the alignment and zeroes the counts and the ticket.
+__global__ void __launch_bounds__(256) k_sync(const float2* __restrict__ z, int64_t zstride,
+                                              const uint32_t* __restrict__ ref, int64_t refstride, int64_t n_ref,
+                                              int m, int64_t lo, int64_t hi, int D, int64_t lat, int64_t slice,
+                                              int64_t len, int* counts, unsigned* ticket, RxDevState* st) {
+    const int q = blockIdx.x >> 3, p = (blockIdx.x >> 2) & 1, r = blockIdx.x & 3;
+    const int64_t s0 = lo + (int64_t)blockIdx.y * slice;
+    const int64_t s1 = min(hi, s0 + slice);
+    extern __shared__ int16_t txl[];                  // tx levels for t in [s0 - lat - D, s1 - lat + D)
+    __shared__ int cnt[2 * RX_MAX_DELAY + 1];
+    __shared__ bool s_last;
+    for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x) cnt[i] = 0;
+    if (s0 < s1) {
+        const int64_t t0 = s0 - lat - D;
+        const int64_t nt = (s1 - s0) + 2 * D;
+        const uint32_t* rp = ref + (int64_t)p * refstride;
+        for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int64_t t = t0 + i;
+            int16_t v = -1;
+            if (t >= 0 && t < n_ref) {
+                int li, lq;
+                bits_to_levels(ref_symbol_bits(rp, t, m), m, li, lq);
+                v = (int16_t)(li | (lq << 8));
+            }
+            txl[i] = v;
+        }
+        __syncthreads();
+        const Qam qm = make_qam(m);
+        const int lane = threadIdx.x & 31;
+        for (int64_t base = s0 + (threadIdx.x & ~31); base < s1; base += blockDim.x) {
+            const int64_t n = base + lane;
+            int16_t mine = -2;
+            if (n < s1) {
+                const float2 v = quarter(z[(int64_t)q * zstride + n], r);
+                mine = (int16_t)(qam_level(v.x, qm) | (qam_level(v.y, qm) << 8));
+            }
+            for (int d = -D; d <= D; ++d) {
+                const bool hit = (n < s1) && (txl[n - s0 + D + d] == mine);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (lane == 0 && bal) atomicAdd(&cnt[d + D], __popc(bal));
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x)
+            if (cnt[i]) atomicAdd(&counts[blockIdx.x * (2 * D + 1) + i], cnt[i]);
+    }
+    // arrival: this CTA's additions ordered before its ticket
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st->sync_valid = 1;
+    if (threadIdx.x == 0) {
+        const unsigned done = atomicAdd(ticket, 1u);
+        s_last = done == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < 64) sync_pick(counts, D, len, st, threadIdx.x >> 5, threadIdx.x & 31);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->sync_valid = 1;
+        *ticket = 0u;
+    }
 }
 
 // Grid-stride over the symbols of one output polarisation; counters stay in
@@ -250,10 +268,11 @@ cudaError_t launch_sync(const float2* z, int64_t zstride, const uint32_t* ref, i
         cudaFuncSetAttribute(k_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
+    // the arrival ticket sits after the largest count table
+    unsigned* ticket = reinterpret_cast<unsigned*>(counts + 16 * (2 * RX_MAX_DELAY + 1));
     k_sync<<<dim3(16, nsl), 256, smem, s>>>(z, zstride, ref, refstride, n_ref, m, lo, hi, max_delay, lat, slice,
-                                           counts);
-    k_sync_pick<<<1, 64, 0, s>>>(counts, max_delay, len, st);
-    if (nlaunch) *nlaunch += 2;
+                                           len, counts, ticket, st);
+    if (nlaunch) *nlaunch += 1;
     return cudaGetLastError();
 }
 

@@ -547,24 +547,22 @@ __global__ void __launch_bounds__(256) k_cma_check(const float2* __restrict__ ya
         *flag = best > 0.5f ? 1 : 0;
         st->cma_rho = best;
         st->cma_reran = 0;
+        if (best > 0.5f) {
+            // the rerun's start: the second row rebuilt from the first (h_yy[k] = conj h_xx[T-1-k],
+            // h_yx[k] = -conj h_xy[T-1-k]), the first row kept
+            for (int k = 0; k < T; ++k) {
+                const float2 hxx = st->taps_cma[0 * T + (T - 1 - k)];
+                const float2 hxy = st->taps_cma[1 * T + (T - 1 - k)];
+                st->taps_init[0 * T + k] = st->taps_cma[0 * T + k];
+                st->taps_init[1 * T + k] = st->taps_cma[1 * T + k];
+                st->taps_init[3 * T + k] = make_float2(hxx.x, -hxx.y);
+                st->taps_init[2 * T + k] = make_float2(-hxy.x, hxy.y);
+            }
+            st->cma_reran = 1;
+        }
     } else if (best > 0.5f) {
         atomicOr(&st->err_word, 4u);
     }
-}
-
-// second row from the first: h_yy[k] = conj h_xx[T-1-k], h_yx[k] = -conj h_xy[T-1-k]
-__global__ void k_cma_rebuild(RxDevState* st, int T, const int* flag) {
-    if (*flag == 0) return;
-    const int k = threadIdx.x;
-    if (k < T) {
-        const float2 hxx = st->taps_cma[0 * T + (T - 1 - k)];
-        const float2 hxy = st->taps_cma[1 * T + (T - 1 - k)];
-        st->taps_init[0 * T + k] = st->taps_cma[0 * T + k];
-        st->taps_init[1 * T + k] = st->taps_cma[1 * T + k];
-        st->taps_init[3 * T + k] = make_float2(hxx.x, -hxx.y);
-        st->taps_init[2 * T + k] = make_float2(-hxy.x, hxy.y);
-    }
-    if (k == 0) st->cma_reran = 1;
 }
 
 }  // namespace
@@ -697,7 +695,3 @@ cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_cma_rebuild(RxDevState* st, int T, const int* flag, cudaStream_t s) {
-    k_cma_rebuild<<<1, 64, 0, s>>>(st, T, flag);
-    return cudaGetLastError();
-}

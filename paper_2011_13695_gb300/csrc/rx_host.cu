@@ -42,20 +42,11 @@ __global__ void k_state_init(RxDevState* st) {
     st->scale[0] = st->scale[1] = 1.0f;
 }
 
-// start of a single frame: forget the carried unwrap state and alignment
-__global__ void k_frame_begin(RxDevState* st, int single, int first) {
-    if (single) {
-        st->b_prev[0] = st->b_prev[1] = -1;
-        st->m_prev[0] = st->m_prev[1] = 0;
-        st->sync_valid = 0;
-    }
-    if (first) {
-        st->fo_code = 0;
-        st->nco_inc = 0;
-        st->fo_valid = 0;
-        st->cma_reran = 0;
-        st->cma_rho = 0.0f;
-    }
+// start of a decision-only call: forget the carried unwrap state and alignment
+__global__ void k_decide_begin(RxDevState* st) {
+    st->b_prev[0] = st->b_prev[1] = -1;
+    st->m_prev[0] = st->m_prev[1] = 0;
+    st->sync_valid = 0;
 }
 
 __global__ void k_identity_taps(float2* taps, int T) {
@@ -303,11 +294,11 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(dalloc(&h->z, 2 * h->Nmax));
     A(dalloc(&h->bstar, 2 * h->Nmax));
     A(dalloc(&h->mq, 2 * h->Nmax));
-    A(dalloc(&h->tiles, 2 * ntiles));
+    A(dalloc(&h->tiles, 2 * ntiles + 4));          // per-tile jump sums, then the carry's snapshot
     A(dalloc(&h->yacq, 2 * h->nacq));
     A(dalloc(&h->yfoe, 2 * h->nw));
     A(dalloc(&h->pgram, 2 * (size_t)nf));
-    A(dalloc(&h->sync_counts, 16 * (2 * RX_MAX_DELAY + 1)));
+    A(dalloc(&h->sync_counts, 16 * (2 * RX_MAX_DELAY + 1) + 1));     // the counts, then an arrival ticket
     A(dalloc(&h->flag, 512));           // [0] CMA rerun flag, [1] check counter, [2..] check partials
     A(dalloc(&h->taps_id, 4 * RX_TMAX));
     A(dalloc(&h->st, 1));
@@ -338,7 +329,7 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaMemset(h->cdc, 0, sizeof(float2) * 2 * h->cap));
     A(cudaMemset(h->tail, 0, sizeof(float2) * 2 * h->hop));
     // counters that kernels accumulate into and reset after use must start at zero
-    A(cudaMemset(h->sync_counts, 0, sizeof(int) * 16 * (2 * RX_MAX_DELAY + 1)));
+    A(cudaMemset(h->sync_counts, 0, sizeof(int) * (16 * (2 * RX_MAX_DELAY + 1) + 1)));
     A(cudaMemset(h->flag, 0, sizeof(int) * 512));
     k_state_init<<<1, 1, 0, s0>>>(h->st);
     k_identity_taps<<<1, 256, 0, s0>>>(h->taps_id, h->T);
@@ -382,12 +373,11 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
     RxDevState* st = h->st;
     uint64_t nl = 0;
 
-    k_frame_begin<<<1, 1, 0, s>>>(st, stream_mode ? 0 : 1, first ? 1 : 0);
-    ++nl;
-    RX_CK(cudaGetLastError());
+    // a stream's later frames carry every piece of state; a first frame (every single frame) starts it
+    // in the power kernel
     if (first) {
         StageScope sc(h, ST_POWER, s);
-        RX_CK(launch_power(d_in, c.input_format, c.input_scale, S, 2 * n_cma * Lb, st, s));
+        RX_CK(launch_power(d_in, c.input_format, c.input_scale, S, 2 * n_cma * Lb, st, stream_mode ? 0 : 1, s));
         ++nl;
     }
     // A single frame with an acquisition: the FD compensation of the blocks the acquisition reads
@@ -460,13 +450,12 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 RX_CK(launch_lms(a, kAcqThreads, s));
                 if (rx_status r = enqueue_rest(); r != RX_OK) return r;
                 RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 0, s));
-                RX_CK(launch_cma_rebuild(st, T, h->flag, s));
                 LmsArgs a2 = a;
                 a2.taps_in = st->taps_init;
                 a2.run_if = h->flag;
                 RX_CK(launch_lms(a2, kAcqThreads, s));
                 RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 1, s));
-                nl += 5;
+                nl += 4;
             }
             {
                 StageScope sc(h, ST_FOE, s);
@@ -567,7 +556,7 @@ rx_status rx_decide(rx_handle* h, const float* d_z, int64_t n_sym, const uint32_
     h->last = s;
     const int64_t N = n_sym;
     const float2* z = reinterpret_cast<const float2*>(d_z);
-    k_frame_begin<<<1, 1, 0, s>>>(h->st, 1, 0);
+    k_decide_begin<<<1, 1, 0, s>>>(h->st);
     RX_CK(cudaGetLastError());
     const int64_t words = (N * h->m + 31) / 32;
     const int64_t lo = c.edge_skip, hi = std::max<int64_t>(N - c.edge_skip, lo);
@@ -819,7 +808,7 @@ rx_status rx_reset(rx_handle* h) {
     RX_CK(cudaMemset(h->st, 0, sizeof(RxDevState)));
     RX_CK(cudaMemset(h->tail, 0, sizeof(float2) * 2 * h->hop));
     RX_CK(cudaMemset(h->cdc, 0, sizeof(float2) * 2 * h->cap));
-    RX_CK(cudaMemset(h->sync_counts, 0, sizeof(int) * 16 * (2 * RX_MAX_DELAY + 1)));
+    RX_CK(cudaMemset(h->sync_counts, 0, sizeof(int) * (16 * (2 * RX_MAX_DELAY + 1) + 1)));
     RX_CK(cudaMemset(h->flag, 0, sizeof(int) * 512));
     k_state_init<<<1, 1>>>(h->st);
     RX_CK(cudaGetLastError());

@@ -51,8 +51,10 @@ struct LmsArgs {
 // shared memory a launch asks for: the kernel's need, or with `exclusive` the most a CTA may have
 size_t lms_launch_smem(size_t need, int exclusive);
 
+// A0 power of the first n_win samples; thread 0 of the first CTA also starts the frame's state (single:
+// forget the unwrap carry and the alignment; always: forget the FO code and the CMA rerun)
 cudaError_t launch_power(const void* in, int fmt, float in_scale, int64_t S, int64_t n_win, RxDevState* st,
-                         cudaStream_t s);
+                         int single, cudaStream_t s);
 cudaError_t launch_cdc(const CdcArgs& a, cudaStream_t s);
 cudaError_t launch_tail(const void* in, int fmt, float in_scale, int64_t S, int hop, float2* tail,
                         const RxDevState* st, cudaStream_t s);
@@ -78,16 +80,21 @@ cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, in
 cudaError_t launch_foe_pgram(const float2* yw, int64_t nw, int kf, const float2* tw, float* P, cudaStream_t s);
 cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw, int Lb, double rs, double fs,
                             double grid, int T, RxDevState* st, cudaStream_t s);
+// the singularity check of the CMA outputs; pass 0 also rebuilds the second row into taps_init when the
+// outputs correlate (the rerun's start)
 cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st,
                              int* flag_dev, int pass, cudaStream_t s);
-cudaError_t launch_cma_rebuild(RxDevState* st, int T, const int* flag_dev, cudaStream_t s);
 
 cudaError_t launch_bps(const float2* y, int64_t ystride, int64_t N, int B, int W, int m, uint8_t* bstar,
                        int64_t bstride, cudaStream_t s);
+// A5 unwrap and derotation in two passes; tile_sums holds 2 * ceil(N / 1024) + 4 ints (the per-tile
+// jump sums, then a snapshot of the carried (b*, m) of each polarisation)
 cudaError_t launch_unwrap(const float2* y, int64_t ystride, const uint8_t* bstar, int64_t bstride, int64_t N,
                           int B, int* tile_sums, int* m_out, int64_t mstride, float2* z, int64_t zstride,
                           RxDevState* st, cudaStream_t s, int* nlaunch);
 
+// A6 alignment search; counts holds 16 * (2 * RX_MAX_DELAY + 1) + 1 ints, zero on entry and on return
+// (the match counts, then the last-CTA arrival ticket)
 cudaError_t launch_sync(const float2* z, int64_t zstride, const uint32_t* ref, int64_t refstride, int64_t n_ref,
                         int m, int64_t lo, int64_t hi, int max_delay, int64_t lat, int* counts, RxDevState* st,
                         cudaStream_t s, int* nlaunch);

@@ -26,7 +26,7 @@ constexpr int64_t kTiles = (kStaticMaxSym + 1023) / 1024;
 
 struct StaticScratch {
     RxDevState st;                       // carried unwrap state (reset every call)
-    int tiles[2 * kTiles];               // per-tile jump sums, then tile bases
+    int tiles[2 * kTiles + 4];           // per-tile jump sums, then the carried (b*, m) snapshot
     int m[2 * kStaticMaxSym];            // unwrap count per symbol
     uint8_t bstar[2 * kStaticMaxSym];    // chosen test phase per symbol
 };
