@@ -52,11 +52,18 @@ __global__ void k_power(const void* in, float in_scale, int64_t S, int64_t n_win
         st->cma_reran = 0;
         st->cma_rho = 0.0f;
     }
+    // eight loads in flight per thread before their sums (same order of additions as one at a time)
     float acc = 0.0f;
-    for (int64_t i = threadIdx.x; i < n_win; i += blockDim.x) {
-        float2 v = load_sample<FMT>(in, (int64_t)p * S + i, in_scale);
-        acc += cabs2(v);
+    int64_t i = threadIdx.x;
+    const int64_t nt = blockDim.x;
+    for (; i + 7 * nt < n_win; i += 8 * nt) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = load_sample<FMT>(in, (int64_t)p * S + i + u * nt, in_scale);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += cabs2(v[u]);
     }
+    for (; i < n_win; i += nt) acc += cabs2(load_sample<FMT>(in, (int64_t)p * S + i, in_scale));
     __shared__ float red[32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

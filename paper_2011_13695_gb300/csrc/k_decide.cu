@@ -144,80 +144,113 @@ __global__ void __launch_bounds__(256) k_sync(const float2* __restrict__ z, int6
     }
 }
 
-// Grid-stride over the symbols of one output polarisation; counters stay in
-// registers until one block-wide reduction and one set of atomics per CTA.
-__global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int64_t zstride, int64_t N,
-                                               const uint32_t* __restrict__ ref, int64_t refstride, int64_t n_ref,
-                                               int m, int64_t lo, int64_t hi, int64_t lat,
-                                               uint32_t* __restrict__ out, int64_t outstride, RxDevState* st) {
+// Grid-stride over groups of four consecutive symbols of one output
+// polarisation (M bits per symbol); counters stay in registers until one
+// block-wide reduction and one set of atomics per CTA. Two tables in shared
+// memory, built per CTA with the same arithmetic as the direct forms: the
+// decision's stream bits by its levels (li + 16 lq), and the reference
+// symbol's ideal point and energy by its M stream bits. A thread's four
+// decisions form one 4M-bit chunk of the output stream; a warp's 32 chunks
+// are 4M whole words, each gathered by one lane with shuffles. The
+// reference bits of the four symbols are one funnel of two words, compared
+// with the chunk in one XOR. I is the index type: 32-bit when every index of
+// the launch fits, else 64-bit.
+template <int M, typename I>
+__global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, I zstride, I N,
+                                               const uint32_t* __restrict__ ref, I refstride, I n_ref,
+                                               I lo, I hi, I lat, uint32_t* __restrict__ out, I outstride,
+                                               RxDevState* st, int vec) {
+    constexpr int C = 4 * M;                          // chunk bits
+    constexpr uint32_t MASK = (1u << M) - 1u;
+    __shared__ float4 s_pt[1 << M];                   // reference bits -> (s.x, s.y, |s|^2, 0)
+    __shared__ uint32_t s_bits[256];                  // li + 16 lq -> decision stream bits
     const int q = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const bool have_sync = ref != nullptr && st->sync_valid;
     const int r = have_sync ? st->sync_r[q] : 0;
     const int p = have_sync ? st->sync_p[q] : 0, d = have_sync ? st->sync_d[q] : 0;
-    const Qam qm = make_qam(m);
-    const int64_t nwords = (N * m + 31) / 32;
-    const uint32_t* refp = have_sync ? ref + (int64_t)p * refstride : nullptr;
+    const Qam qm = make_qam(M);
+    {
+        const int i = threadIdx.x;                    // launched with 256 threads
+        const int li = i & 15, lq = i >> 4;
+        s_bits[i] = (li < qm.L && lq < qm.L) ? msb_first_to_stream(qam_bits(li, lq, qm), M) : 0u;
+        if (i < (1 << M)) {
+            int ti, tq;
+            bits_to_levels((uint32_t)i, M, ti, tq);
+            const float2 sp = make_float2(qam_value(ti, qm), qam_value(tq, qm));
+            s_pt[i] = make_float4(sp.x, sp.y, cabs2(sp), 0.0f);
+        }
+    }
+    __syncthreads();
+    const I nwords = (N * M + 31) / 32;
+    const I nrw = (n_ref * M + 31) / 32;
+    const uint32_t* refp = have_sync ? ref + (I)p * refstride : nullptr;
+    // counted symbols: n in [lo, hi) with reference index t = n + d - lat in [0, n_ref)
+    const I c0 = max(max(lo, lat - (I)d), (I)0);
+    const I c1 = min(min(hi, N), n_ref + lat - (I)d);
     uint32_t errs = 0, serr = 0, cnt = 0;
     // EVM sums: FP32 per thread (a handful of symbols each), per warp and per CTA, then fixed point
     // (FP64 arithmetic, atomics included, runs at a small fraction of the FP32 rate on this part)
     float en = 0.0f, ed = 0.0f;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n - lane < N; n += step) {
-        uint32_t sbits = 0;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (n < N) {
-            v = quarter(z[(int64_t)q * zstride + n], r);
-            sbits = msb_first_to_stream(qam_bits(qam_level(v.x, qm), qam_level(v.y, qm), qm), m);
+    const float2* zq = z + (I)q * zstride;
+    uint32_t* oq = out ? out + (I)q * outstride : nullptr;
+    const I G = (N + 3) / 4;
+    const I step = (I)gridDim.x * blockDim.x;
+    for (I g = (I)blockIdx.x * blockDim.x + threadIdx.x; g - lane < G; g += step) {
+        const I n0 = 4 * g;
+        float2 v[4];
+        if (vec && n0 + 3 < N) {
+            const float4 a = *reinterpret_cast<const float4*>(zq + n0);
+            const float4 b = *reinterpret_cast<const float4*>(zq + n0 + 2);
+            v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+            v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = n0 + k < N ? zq[n0 + k] : make_float2(0.0f, 0.0f);
         }
-        if (out && (m == 2 || m == 4)) {
-            // whole symbols per word: lanes g 32/m .. (g + 1) 32/m - 1 fill word g of the warp's m words;
-            // an OR over each lane group (shuffles within the group), then the group's first lane stores
-            const int per = 32 / m;                    // symbols per word
-            uint32_t word = (n < N) ? sbits << ((lane % per) * m) : 0u;
-            for (int o = 1; o < per; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
-            const int64_t wi = (n - lane) * m / 32 + lane / per;
-            if (lane % per == 0 && wi < nwords) out[(int64_t)q * outstride + wi] = word;
-        } else if (out) {
-            // warp symbols n0..n0+31 fill words [n0*m/32, n0*m/32 + m)
-            const int64_t n0 = n - lane;
-            for (int w = 0; w < m; ++w) {
-                const int sh = lane * m - 32 * w;      // position of this symbol's bit 0 in word w
-                uint32_t contrib = 0;
-                if (n < N) {
-                    if (sh >= 0 && sh < 32) contrib = sbits << sh;
-                    else if (sh < 0 && sh > -m) contrib = sbits >> (-sh);
-                }
-                const uint32_t word = __reduce_or_sync(0xffffffffu, contrib);
-                const int64_t wi = n0 * m / 32 + w;
-                if (lane == w && wi < nwords) out[(int64_t)q * outstride + wi] = word;
+        uint32_t chunk = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = quarter(v[k], r);
+            const uint32_t sb = s_bits[qam_level(v[k].x, qm) | (qam_level(v[k].y, qm) << 4)];
+            if (n0 + k < N) chunk |= sb << (k * M);
+        }
+        if (oq) {
+            // lane w < C assembles word w of the warp's C words: bits [32 w, 32 w + 32) of the 32 chunks
+            const int a = (lane * 32) / C, off = (lane * 32) % C;
+            uint32_t word = __shfl_sync(0xffffffffu, chunk, a < 32 ? a : 31) >> off;
+#pragma unroll
+            for (int k = 1; k <= (32 + C - 1) / C; ++k) {
+                const int src = a + k;
+                const uint32_t part = __shfl_sync(0xffffffffu, chunk, src < 32 ? src : 31);
+                const int sh = k * C - off;
+                if (src < 32 && sh < 32) word |= part << sh;
             }
+            const I wi = (g - lane) * (C / 4) / 8 + lane;   // (g - lane) 4M / 32 whole words before the warp
+            if (lane < C && wi < nwords) oq[wi] = word;
         }
-        if (have_sync) {
-            // the warp's 32 reference symbols t0 .. t0 + 31 are bits [t0 m, (t0 + 32) m) of the packed
-            // reference: lanes 0..m load the m + 1 words that hold them, every lane picks its bits with
-            // two shuffles
-            const int64_t t0 = (n - lane) + d - lat;
-            const int64_t bit0 = t0 * m;
-            const int64_t w0 = bit0 >> 5;                      // floor, also for t0 < 0
-            const int64_t nrw = (n_ref * m + 31) / 32;
-            uint32_t word = 0;
-            if (lane <= m && w0 + lane >= 0 && w0 + lane < nrw) word = __ldg(&refp[w0 + lane]);
-            const int b = lane * m + (int)(bit0 - w0 * 32);
-            const uint32_t lo_w = __shfl_sync(0xffffffffu, word, b >> 5);
-            const uint32_t hi_w = __shfl_sync(0xffffffffu, word, (b >> 5) + 1);
-            const uint32_t rb = (uint32_t)((((uint64_t)hi_w << 32) | lo_w) >> (b & 31)) & ((1u << m) - 1u);
-            const int64_t t = n + d - lat;
-            if (n < N && n >= lo && n < hi && t >= 0 && t < n_ref) {
-                const uint32_t e = __popc(rb ^ sbits);
-                errs += e;
-                serr += e ? 1u : 0u;
-                cnt += 1;
-                int ti, tq;
-                bits_to_levels(rb, m, ti, tq);
-                const float2 s = make_float2(qam_value(ti, qm), qam_value(tq, qm));
-                en += cabs2(csub(v, s));
-                ed += cabs2(s);
+        if (have_sync && n0 + 3 >= c0 && n0 < c1) {
+            const I bit0 = (n0 + (I)d - lat) * M;
+            const I w0 = bit0 >> 5;                   // floor, also below zero
+            const int off = (int)(bit0 & 31);
+            const uint32_t wl = (w0 >= 0 && w0 < nrw) ? __ldg(&refp[w0]) : 0u;
+            uint32_t rb4 = wl >> off;
+            if (off + C > 32) {
+                const uint32_t wh = (w0 + 1 >= 0 && w0 + 1 < nrw) ? __ldg(&refp[w0 + 1]) : 0u;
+                rb4 |= wh << (32 - off);
+            }
+            const uint32_t x = rb4 ^ chunk;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (n0 + k >= c0 && n0 + k < c1) {
+                    const uint32_t e = __popc((x >> (k * M)) & MASK);
+                    errs += e;
+                    serr += e ? 1u : 0u;
+                    cnt += 1;
+                    const float4 sp = s_pt[(rb4 >> (k * M)) & MASK];
+                    en += cabs2(csub(v[k], make_float2(sp.x, sp.y)));
+                    ed += sp.z;
+                }
             }
         }
     }
@@ -245,11 +278,30 @@ __global__ void __launch_bounds__(256) k_count(const float2* __restrict__ z, int
             atomicAdd(&st->bit_errors, a);
             atomicAdd(&st->symbol_errors, b);
             atomicAdd(&st->symbols, c);
-            atomicAdd(&st->bits, c * (unsigned long long)m);
+            atomicAdd(&st->bits, c * (unsigned long long)M);
             // EVM sums as fixed point: integer atomics, exact and in no particular order
             atomicAdd(&st->evm_num_fx, __float2ull_rn(x * RX_EVM_FX_SCALE));
             atomicAdd(&st->evm_den_fx, __float2ull_rn(y * RX_EVM_FX_SCALE));
         }
+    }
+}
+
+template <int M, typename I>
+cudaError_t count_m(dim3 grid, const float2* z, I zstride, I N, const uint32_t* ref, I refstride, I n_ref, I lo,
+                    I hi, I lat, uint32_t* out, I outstride, RxDevState* st, int vec, cudaStream_t s) {
+    k_count<M, I><<<grid, 256, 0, s>>>(z, zstride, N, ref, refstride, n_ref, lo, hi, lat, out, outstride, st, vec);
+    return cudaGetLastError();
+}
+
+template <typename I>
+cudaError_t count_i(int m, dim3 grid, const float2* z, I zstride, I N, const uint32_t* ref, I refstride, I n_ref,
+                    I lo, I hi, I lat, uint32_t* out, I outstride, RxDevState* st, int vec, cudaStream_t s) {
+    switch (m) {
+        case 2: return count_m<2, I>(grid, z, zstride, N, ref, refstride, n_ref, lo, hi, lat, out, outstride, st, vec, s);
+        case 4: return count_m<4, I>(grid, z, zstride, N, ref, refstride, n_ref, lo, hi, lat, out, outstride, st, vec, s);
+        case 6: return count_m<6, I>(grid, z, zstride, N, ref, refstride, n_ref, lo, hi, lat, out, outstride, st, vec, s);
+        case 8: return count_m<8, I>(grid, z, zstride, N, ref, refstride, n_ref, lo, hi, lat, out, outstride, st, vec, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -286,11 +338,20 @@ cudaError_t launch_count(const float2* z, int64_t zstride, int64_t N, const uint
         int dev = 0, nsm = 152, per = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_count, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_count<8, int64_t>, 256, 0);
         resident = std::max(1, nsm * per);
     }
-    const int64_t want = (N + 255) / 256;
+    const int64_t want = (N + 1023) / 1024;           // four symbols per thread
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(want, resident / 2)), 2);
-    k_count<<<grid, 256, 0, s>>>(z, zstride, N, ref, refstride, n_ref, m, lo, hi, lat, out, outstride, st);
-    return cudaGetLastError();
+    // 16-byte loads of four symbols when both rows are aligned for them
+    const int vec = ((uintptr_t)z % 16) == 0 && (zstride % 2) == 0;
+    // 32-bit indices when the largest of them (bit positions of both outputs and references, element
+    // offsets of the second rows, the grid-stride walk past N) stays below 2^31
+    const int64_t lim = (int64_t)1 << 30;
+    const bool narrow = N < lim / 16 && n_ref < lim / 16 && zstride < lim && refstride < lim && outstride < lim &&
+                        lat < lim && lo < lim && hi < lim;
+    if (narrow)
+        return count_i<int>(m, grid, z, (int)zstride, (int)N, ref, (int)refstride, (int)n_ref, (int)lo, (int)hi,
+                            (int)lat, out, (int)outstride, st, vec, s);
+    return count_i<int64_t>(m, grid, z, zstride, N, ref, refstride, n_ref, lo, hi, lat, out, outstride, st, vec, s);
 }
