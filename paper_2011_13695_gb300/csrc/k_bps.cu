@@ -45,12 +45,67 @@ __device__ __forceinline__ float bps_dist(float4 v, float2 cc, float2 ss, float2
     return fmaf(e.x, e.x, e.y * e.y);
 }
 
-// publish one window's warp minimum and the lanes holding it
+// publish one window's warp minimum and the lanes holding it: the minimum of the sums' bit patterns as
+// signed integers (the order of the sums, which are not negative)
 __device__ __forceinline__ void bps_publish(float D, uint2* slot, int lane) {
-    const unsigned int bits = __float_as_uint(D);
-    const unsigned int mn = __reduce_min_sync(0xffffffffu, bits);
+    const int bits = __float_as_int(D);
+    const int mn = __reduce_min_sync(0xffffffffu, bits);
     const unsigned int bal = __ballot_sync(0xffffffffu, bits == mn);
-    if (lane == 0) *slot = make_uint2(mn, bal);
+    if (lane == 0) *slot = make_uint2((unsigned int)mn, bal);
+}
+
+// the windows of one strip for one test phase: the ring of distances, the sliding sum, the published
+// minima and the picks (EDGE: the strip's span holds symbols outside the frame, NaN, guarded to 0)
+template <int W, int GS, bool EDGE>
+__device__ __forceinline__ void bps_strip(const float4* __restrict__ yl, float2 cc, float2 ss, float2 hh, float invLm1,
+                                          float2 ll, float pen, int nc, int LEN, int64_t s0, int64_t N,
+                                          uint2 (*slots)[W], uint2* myslots, int b, int lane, int q,
+                                          uint8_t* __restrict__ bstar, int64_t bstride) {
+    constexpr int NW = GS / 32;
+    // the last W distances of this thread's phase, in registers (indices fixed at compile time)
+    float ring[W];
+    float D = pen;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        float d = bps_dist(yl[u], cc, ss, hh, invLm1, ll);
+        if (EDGE) d = fmaxf(d, 0.0f);
+        ring[u] = d;
+        D += d;
+    }
+    bps_publish(D, &myslots[0], lane);                // window of local output 0
+    for (int ch = 0; ch <= nc; ++ch) {
+        if (ch > 0) {
+            const float4* yc = yl + ch * W;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                float d = bps_dist(yc[u], cc, ss, hh, invLm1, ll);
+                if (EDGE) d = fmaxf(d, 0.0f);
+                const float old = ring[u];
+                ring[u] = d;
+                D = (D + d) - old;
+                // window of local output (ch - 1) W + u + 1 is complete; its slot is (u + 1) % W
+                bps_publish(EDGE ? fmaxf(D, 0.0f) : D, &myslots[(u + 1) & (W - 1)], lane);
+            }
+            float t = pen;                            // re-form the sum directly from the ring
+#pragma unroll
+            for (int r = 0; r < W; ++r) t += ring[r];
+            D = t;
+        }
+        __syncthreads();
+        for (int slot = b; slot < W; slot += GS) {
+            const int kl = slot == 0 ? ch * W : (ch - 1) * W + slot;
+            if (kl >= 0 && kl < LEN && s0 + kl < N) {
+                const uint2 w0 = slots[0][slot];
+                int r = __ffs(w0.y) - 1;
+                if (NW == 2) {
+                    const uint2 w1 = slots[NW - 1][slot];
+                    if ((int)w1.x < (int)w0.x) r = 32 + __ffs(w1.y) - 1;
+                }
+                bstar[(int64_t)q * bstride + s0 + kl] = (uint8_t)r;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 template <int W, int GS>
@@ -82,6 +137,10 @@ __global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict
         ys[st * span + u] = make_float4(v.x, v.y, v.y, -v.x);
     }
     __syncthreads();
+    // a CTA whose staged spans hold no symbol outside the frame needs no NaN guard: its distances are
+    // sums of squares, and the guard is left out of its loop
+    const bool edge = (int64_t)blockIdx.x * NSTRIP * LEN < W / 2 ||
+                      ((int64_t)blockIdx.x + 1) * NSTRIP * LEN + W / 2 > N;
 
     // rotation by e^{-j theta_b} folded with 1/(2a); phases b >= B never win (penalty)
     float sn, cs;
@@ -92,48 +151,12 @@ __global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict
     const int nc = LEN / W;
     uint2* myslots = &slots[sl][wip][0];
 
-    // the last W distances of this thread's phase, in registers (indices fixed at compile time)
-    float ring[W];
-    float D = pen;
-#pragma unroll
-    for (int u = 0; u < W; ++u) {
-        const float d = fmaxf(bps_dist(yl[u], cc, ss, hh, invLm1, ll), 0.0f);
-        ring[u] = d;
-        D += d;
-    }
-    bps_publish(D, &myslots[0], lane);                // window of local output 0
-    for (int ch = 0; ch <= nc; ++ch) {
-        if (ch > 0) {
-            const float4* yc = yl + ch * W;
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                const float d = fmaxf(bps_dist(yc[u], cc, ss, hh, invLm1, ll), 0.0f);
-                const float old = ring[u];
-                ring[u] = d;
-                D = (D + d) - old;
-                // window of local output (ch - 1) W + u + 1 is complete; its slot is (u + 1) % W
-                bps_publish(fmaxf(D, 0.0f), &myslots[(u + 1) & (W - 1)], lane);
-            }
-            float t = pen;                            // re-form the sum directly from the ring
-#pragma unroll
-            for (int r = 0; r < W; ++r) t += ring[r];
-            D = t;
-        }
-        __syncthreads();
-        for (int slot = b; slot < W; slot += GS) {
-            const int kl = slot == 0 ? ch * W : (ch - 1) * W + slot;
-            if (kl >= 0 && kl < LEN && s0 + kl < N) {
-                const uint2 w0 = slots[sl][0][slot];
-                int r = __ffs(w0.y) - 1;
-                if (NW == 2) {
-                    const uint2 w1 = slots[sl][NW - 1][slot];
-                    if (w1.x < w0.x) r = 32 + __ffs(w1.y) - 1;
-                }
-                bstar[(int64_t)q * bstride + s0 + kl] = (uint8_t)r;
-            }
-        }
-        __syncthreads();
-    }
+    if (edge)
+        bps_strip<W, GS, true>(yl, cc, ss, hh, invLm1, ll, pen, nc, LEN, s0, N, slots[sl], myslots, b, lane, q, bstar,
+                               bstride);
+    else
+        bps_strip<W, GS, false>(yl, cc, ss, hh, invLm1, ll, pen, nc, LEN, s0, N, slots[sl], myslots, b, lane, q, bstar,
+                                bstride);
 }
 
 template <int W, int GS>

@@ -98,7 +98,9 @@ struct LmsTileShape {
                                                             // = 8 mod 16, two subsets' 8-byte stores fill the 32 banks
     static constexpr int YT4 = OPL == 8 ? NW * 4 * YTS / 2 : 0;
     static constexpr int YP4 = (NW + 1) / 2;
-    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + YT4;
+    static constexpr int NBT = 256;                         // blocks of one CTA with a phasor slot
+    static constexpr int PH4 = NBT / 2;                     // block phasors (float2)
+    static constexpr int SMEM4 = WIN4 + TAP4 + ES4 + PART4 + YP4 + YT4 + PH4;
     static_assert(NT % 32 == 0 && LB % (NW * 4) == 0, "LB must be a multiple of 4 x warps");
     static_assert(OPL == 2 || OPL == 4 || OPL == 8, "2, 4 or 8 outputs per lane");
     static_assert(T % 2 == 1 && T >= 3, "odd tap count");
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     float* part = reinterpret_cast<float*>(es + S::ES4);            // [warp][class][2 IM]
     float2* ypart = reinterpret_cast<float2*>(es + S::ES4 + S::PART4);   // [NW]
     float2* ytr = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [warp][subset][YTS] (OPL == 8)
+    float2* bph = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4 + S::YT4);   // [NBT]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
@@ -179,6 +182,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     const float2* const xp1 = a.x + a.xstride;
     // input-sample index of the centre tap's sample of output n of block 0: the frame of its phasor
     const long long gout0 = a.g0 + a.off + 2 * nfirst + S::C;
+    // the phasor of output n of block b is e^{-j 2 pi F (gout0 + 2 n)} e^{-j 2 pi F 2 LB b}: the first
+    // factor per lane in registers, the second per block in a table (nblk <= NBT)
+    if (inc)
+        for (int i = tid; i < nblk; i += NT) bph[i] = nco_conj(inc, 2LL * LB * i);
 
 
     // every window the CTA will read, requested into L2 (128-byte lines)
@@ -213,20 +220,40 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         const int par = jj & 1;
         return win_sa + 8u * (uint32_t)((2 * pp + par) * PS + S::org(par) + (jj >> 1));
     };
+    // per window position k of this thread: its shared slot in buffer 0 and its sample offset from
+    // xp0 (the polarisation's row plus the position; the launch keeps it below 2^31)
+    uint32_t kslot[S::KS];
+    int ksrc[S::KS];
+#pragma unroll
+    for (int k = 0; k < S::KS; ++k) {
+        int pp, jj;
+        const bool in = spos(k, pp, jj);
+        kslot[k] = in ? sslot(pp, jj) : 0u;
+        ksrc[k] = in ? (int)(pp * a.xstride) + jj : -1;
+    }
     auto issue = [&](int blk) {                                        // copies of block blk's window
         const int64_t g0b = gstart + 2LL * LB * blk;
         const bool fast = g0b >= 0 && g0b + S::XW <= a.xlen;          // whole window inside the buffer
         const uint32_t boff = 8u * (uint32_t)((blk % 3) * 4 * PS);
-        const float2* src0 = xp0 + g0b;
-        const float2* src1 = xp1 + g0b;
+        const float2* src = xp0 + g0b;
+        if (fast) {
 #pragma unroll
-        for (int k = 0; k < S::KS; ++k) {
-            int pp, jj;
-            if (!spos(k, pp, jj)) continue;
-            const bool ok = fast || (g0b + jj >= 0 && g0b + jj < a.xlen);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sslot(pp, jj) + boff),
-                         "l"(ok ? (pp ? src1 : src0) + jj : xp0), "r"(ok ? 8 : 0)
-                         : "memory");
+            for (int k = 0; k < S::KS; ++k) {
+                if (ksrc[k] < 0) continue;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(kslot[k] + boff),
+                             "l"(src + ksrc[k])
+                             : "memory");
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < S::KS; ++k) {
+                int pp, jj;
+                if (!spos(k, pp, jj)) continue;
+                const bool ok = g0b + jj >= 0 && g0b + jj < a.xlen;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(kslot[k] + boff),
+                             "l"(ok ? src + ksrc[k] : xp0), "r"(ok ? 8 : 0)
+                             : "memory");
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -254,6 +281,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     else if constexpr (OPL == 4) { jst = 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1); comp = lane & 1; owner = comp == 0; }
     else { jst = lane & 7; owner = true; }
     const int nown = nl0 + jst;                                     // local index of the held output
+    const float2 pown = inc ? nco_conj(inc, gout0 + 2LL * nown) : make_float2(1.0f, 0.0f);
 
     for (int b = 0; b < nblk; ++b) {
         const int64_t n0 = nfirst + (int64_t)b * LB;
@@ -325,7 +353,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         // conjugate before it meets the samples in the gradient
         float2 phi = make_float2(1.0f, 0.0f);
         if (inc) {
-            phi = nco_conj(inc, gout0 + 2LL * ((int64_t)b * LB + nown));
+            phi = cmul(pown, bph[b]);
             y = cmul(y, phi);
         }
         const bool valid = nown < L;
@@ -424,10 +452,11 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     }
 }
 
-// the tiled kernel keeps one derotation base per block of a CTA: at most NBT blocks
+// the tiled kernel keeps one output phasor per block of a CTA (at most 256 blocks) and the sample
+// offsets of its window copies as 32-bit integers
 template <int LB>
 inline bool lms_tile_fits(const LmsArgs& a) {
-    return (a.L_seg + LB - 1) / LB + a.n_wu <= 256;
+    return (a.L_seg + LB - 1) / LB + a.n_wu <= 256 && a.xstride < ((int64_t)1 << 30);
 }
 
 template <int NT, int T, int LB>
