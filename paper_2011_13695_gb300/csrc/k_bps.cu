@@ -163,15 +163,17 @@ template <int W, int GS>
 cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
                   cudaStream_t s) {
     const Qam qm = make_qam(m);
-    const int LEN = 512;
+    // symbols per strip (a multiple of W): 768 for 64-symbol windows on frames of a few waves of strips
+    // (less halo per strip), else 512
+    const int LEN = (W == 64 && N >= (int64_t)1 << 18) ? 768 : 512;
     constexpr int NSTRIP = BPS_THREADS / GS;
     const int64_t nstrip = (N + LEN - 1) / LEN;
     dim3 grid((unsigned)((nstrip + NSTRIP - 1) / NSTRIP), 2);
     const size_t smem = sizeof(float4) * NSTRIP * (LEN + W);
-    static bool attr = false;
-    if (!attr) {
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
         cudaFuncSetAttribute(k_bps<W, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        attr = smem;
     }
     const float Lm1 = (float)(qm.L - 1);
     k_bps<W, GS><<<grid, BPS_THREADS, smem, s>>>(y, ystride, N, B, qm.half_inv_a, qm.hL, 1.0f / Lm1, Lm1, LEN, bstar,

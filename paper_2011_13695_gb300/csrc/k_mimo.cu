@@ -523,45 +523,52 @@ __global__ void __launch_bounds__(256) k_cma_check(const float2* __restrict__ ya
     }
     __syncthreads();
     if (!s_last) return;
-    // last CTA: every partial into shared memory with one parallel load (L2, not L1), then the sums
-    // over chunks in a fixed order and the maximum
+    // last CTA: every partial into shared memory with one parallel load (L2, not L1), then per lag (one
+    // lane each of warp 0) the sums over chunks in a fixed order, and the maximum over lags
     __threadfence();
     __shared__ float s_p[(RX_TMAX + 1) * CMA_CHUNKS * 2];
+    __shared__ float s_best;
     const int np = (nlag + 1) * CMA_CHUNKS * 2;
     for (int i = tid; i < np; i += blockDim.x) s_p[i] = __ldcg(&part[i]);
     __syncthreads();
-    if (tid != 0) return;
-    auto total = [&](int i, int comp) {
-        float v = 0.0f;
-        for (int c = 0; c < CMA_CHUNKS; ++c) v += s_p[(i * CMA_CHUNKS + c) * 2 + comp];
-        return v;
-    };
-    const float den = sqrtf(total(nlag, 0)) * sqrtf(total(nlag, 1));
-    float best = 0.0f;
-    for (int k = 0; k < nlag; ++k) {
-        const float rx = total(k, 0), ry = total(k, 1);
-        best = fmaxf(best, den > 0.0f ? sqrtf(rx * rx + ry * ry) / den : 0.0f);
-    }
-    flag[1] = 0;
-    if (pass == 0) {
-        *flag = best > 0.5f ? 1 : 0;
-        st->cma_rho = best;
-        st->cma_reran = 0;
-        if (best > 0.5f) {
-            // the rerun's start: the second row rebuilt from the first (h_yy[k] = conj h_xx[T-1-k],
-            // h_yx[k] = -conj h_xy[T-1-k]), the first row kept
-            for (int k = 0; k < T; ++k) {
-                const float2 hxx = st->taps_cma[0 * T + (T - 1 - k)];
-                const float2 hxy = st->taps_cma[1 * T + (T - 1 - k)];
-                st->taps_init[0 * T + k] = st->taps_cma[0 * T + k];
-                st->taps_init[1 * T + k] = st->taps_cma[1 * T + k];
-                st->taps_init[3 * T + k] = make_float2(hxx.x, -hxx.y);
-                st->taps_init[2 * T + k] = make_float2(-hxy.x, hxy.y);
-            }
-            st->cma_reran = 1;
+    if (w == 0) {
+        auto total = [&](int i, int comp) {
+            float v = 0.0f;
+            for (int c = 0; c < CMA_CHUNKS; ++c) v += s_p[(i * CMA_CHUNKS + c) * 2 + comp];
+            return v;
+        };
+        const float den = sqrtf(total(nlag, 0)) * sqrtf(total(nlag, 1));
+        float best = 0.0f;
+        for (int k = lane; k < nlag; k += 32) {
+            const float rx = total(k, 0), ry = total(k, 1);
+            best = fmaxf(best, den > 0.0f ? sqrtf(rx * rx + ry * ry) / den : 0.0f);
         }
-    } else if (best > 0.5f) {
-        atomicOr(&st->err_word, 4u);
+        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) s_best = best;
+    }
+    __syncthreads();
+    const float best = s_best;
+    const bool corr = best > 0.5f;
+    if (tid == 0) {
+        flag[1] = 0;
+        if (pass == 0) {
+            *flag = corr ? 1 : 0;
+            st->cma_rho = best;
+            st->cma_reran = corr ? 1 : 0;
+        } else if (corr) {
+            atomicOr(&st->err_word, 4u);
+        }
+    }
+    // the rerun's start: the second row rebuilt from the first (h_yy[k] = conj h_xx[T-1-k],
+    // h_yx[k] = -conj h_xy[T-1-k]), the first row kept; one thread per tap
+    if (pass == 0 && corr && tid < T) {
+        const int k = tid;
+        const float2 hxx = st->taps_cma[0 * T + (T - 1 - k)];
+        const float2 hxy = st->taps_cma[1 * T + (T - 1 - k)];
+        st->taps_init[0 * T + k] = st->taps_cma[0 * T + k];
+        st->taps_init[1 * T + k] = st->taps_cma[1 * T + k];
+        st->taps_init[3 * T + k] = make_float2(hxx.x, -hxx.y);
+        st->taps_init[2 * T + k] = make_float2(-hxy.x, hxy.y);
     }
 }
 
