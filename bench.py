@@ -49,9 +49,11 @@ def parse():
                     help="frame workload only: skip the precision, batched and learned forms (profiling runs)")
     ap.add_argument("--n-sym", type=int, default=0, help="smaller frame for profiling captures (not a bench line)")
     ap.add_argument("--workload", default="frame",
-                    choices=["frame", "stream", "batch", "learned", "cnn", "wl", "kk", "ingest", "pam", "forms"],
+                    choices=["frame", "stream", "batch", "inflight", "learned", "cnn", "wl", "kk", "ingest", "pam",
+                             "forms"],
                     help="frame: the 16QAM frame (the bench line); stream: 64QAM int8/FP16 stream of 64 frames; "
-                         "batch: 16 channels in one graph launch; learned: split-step link, chain + "
+                         "batch: 16 channels in one graph launch; inflight: --frames independent 16QAM frames in "
+                         "one graph launch; learned: split-step link, chain + "
                          "trained post-equaliser; cnn: the post-equaliser forward alone; wl: the "
                          "widely-linear segmented DD-LMS alone on an IQ-imbalanced 16QAM frame; kk: the "
                          "Kramers-Kronig front end on a 2^22-sample 12-bit buffer; ingest: real-time ingest "
@@ -61,6 +63,7 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned workload")
     ap.add_argument("--window", type=int, default=16384, help="symbols per training step of the learned workload")
     ap.add_argument("--lr", type=float, default=7e-4, help="initial Adam learning rate of the learned workload")
+    ap.add_argument("--frames", type=int, default=4, help="frames in flight of the inflight workload")
     ap.add_argument("--fmt", default="i8", choices=["i8", "f16", "c64"], help="input format of the stream workload")
     ap.add_argument("--wl-taps", type=int, default=21, help="tap count of the wl workload")
     ap.add_argument("--wl-threads", type=int, default=0,
@@ -604,6 +607,10 @@ def other_forms(args) -> dict:
     except Exception as e:
         out["batch"] = {"error": str(e)[:300]}
     try:
+        out["inflight"] = inflight_form(4, 5, 3)
+    except Exception as e:
+        out["inflight"] = {"error": str(e)[:300]}
+    try:
         la = argparse.Namespace(**vars(args))
         la.steps, la.warmup, la.n_sym = 5, 3, 0
         out["learned"] = learned_form(la)
@@ -690,6 +697,77 @@ def batch_form(steps: int, warmup: int) -> dict:
             "plain_sequential": {"value": bits / (t1 * 1e-3) / 1e9, "ms_per_step": t1,
                                  "ber": s_errs / max(s_counted, 1),
                                  "note": "same frames, one rx_process call per channel in turn"}}
+
+
+def inflight_form(frames: int, steps: int, warmup: int) -> dict:
+    """Independent DP-16QAM 32 GBd frames of 2^20 symbols/pol (the headline frame, one seed each), F of
+    them in one graph launch (one handle and forked stream per frame, the configuration unchanged:
+    FFT 4096, 128-thread LMS CTAs, no tuning): while one frame's serial acquisition holds two SMs,
+    the others' throughput stages use the rest. Beside it, the same frames one rx_process call after
+    another on one stream."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.receiver import config_from
+    from synth import generate, workload
+
+    w = workload("dp-16qam-32gbd")
+    N, m = w["link"].n_sym, w["link"].bits_per_sym
+    xs, refs, outs, bits = [], [], [], 0
+    for f in range(frames):
+        fr = generate(w["link"], SEED + f)
+        xs.append(torch.from_numpy(np.ascontiguousarray(fr.samples.astype(np.complex64)).view(np.float32)).cuda())
+        refs.append(torch.from_numpy(fr.ref_words.astype(np.uint32).view(np.int32)).cuda())
+        outs.append(torch.zeros(2 * ((N * m + 31) // 32), dtype=torch.int32, device="cuda"))
+        bits += 2 * m * N
+    cfg = config_from(w["rx"], N)
+    cfg.lms_threads = 128
+    b = rx.rx_batch_create([cfg] * frames)
+    stream = torch.cuda.current_stream()
+    n_sym = [N] * frames
+    args_ = ([t.data_ptr() for t in xs], n_sym, [t.data_ptr() for t in refs], [t.data_ptr() for t in outs],
+             stream.cuda_stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(run):
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms)
+
+    t = timed(lambda: rx.rx_batch_process(b, *args_))
+    errs = sum(rx.rx_batch_stats(b, i)["bit_errors"] for i in range(frames))
+    counted = sum(rx.rx_batch_stats(b, i)["bits_counted"] for i in range(frames))
+    h = rx.rx_create(cfg)
+
+    def singles():
+        for i in range(frames):
+            rx.rx_process(h, xs[i].data_ptr(), N, refs[i].data_ptr(), outs[i].data_ptr(), stream.cuda_stream)
+    t1 = timed(singles)
+    s_errs, s_counted = rx.rx_stats(h)["bit_errors"], rx.rx_stats(h)["bits_counted"]
+    rx.rx_destroy(h)
+    rx.rx_batch_destroy(b)
+    return {"metric": "processed line rate", "value": bits / (t * 1e-3) / 1e9, "unit": "Gb/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": t, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dp-16qam-32gbd frames in flight", "frames": frames, "symbols_per_pol": N,
+                       "l2": "flushed between timed steps"},
+            "graph_launches_per_step": 1, "ber": errs / max(counted, 1),
+            "plain_sequential": {"value": bits / (t1 * 1e-3) / 1e9, "ms_per_step": t1,
+                                 "ber": s_errs / max(s_counted, 1),
+                                 "note": "same frames, one rx_process call per frame in turn"}}
 
 
 def batch_arm(args) -> None:
@@ -1230,6 +1308,8 @@ def dispatch(args) -> None:
         print(json.dumps(other_forms(args)))
     elif args.workload == "batch":
         batch_arm(args)
+    elif args.workload == "inflight":
+        print(json.dumps(inflight_form(args.frames, args.steps, args.warmup)))
     elif args.workload == "learned":
         learned_arm(args)
     elif args.workload == "cnn":
