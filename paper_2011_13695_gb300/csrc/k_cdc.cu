@@ -109,7 +109,16 @@ __global__ void __launch_bounds__(((1 << K) / 16 < 32) ? 32 : (1 << K) / 16)
     };
     const float2* __restrict__ H = a.H;
     auto store_h = [&](int idx, float2 v) { sm[fft_pad(idx)] = cmul(v, __ldg(&H[idx])); };
-    fft_run<K, -1, true, true>(sm, a.tw, load, store_h);
+    // a block wholly inside the frame (the common case) loads without bounds checks
+    auto load_in = [&](int idx) -> float2 {
+        const float2 v = load_sample<FMT>(in, pbase + start + idx, sc);
+        bad |= !isfinite(v.x + v.y);
+        return v;
+    };
+    if (start >= 0 && start + N <= S)
+        fft_run<K, -1, true, true>(sm, a.tw, load_in, store_h);
+    else
+        fft_run<K, -1, true, true>(sm, a.tw, load, store_h);
     __syncthreads();
     float2* out = a.out + (int64_t)p * a.ostride + a.obase;
     const int64_t o0 = j * HOP - LEAD;

@@ -109,6 +109,9 @@ __global__ void __launch_bounds__(256) k_sync(const float2* __restrict__ z, int6
         __syncthreads();
         const Qam qm = make_qam(m);
         const int lane = threadIdx.x & 31;
+        const int nd = 2 * D + 1;
+        // lane j of a warp keeps the warp's matches of delays 32 k + j - D (k < 5) in registers
+        int creg[(2 * RX_MAX_DELAY + 32) / 32] = {0};
         for (int64_t base = s0 + (threadIdx.x & ~31); base < s1; base += blockDim.x) {
             const int64_t n = base + lane;
             int16_t mine = -2;
@@ -116,12 +119,25 @@ __global__ void __launch_bounds__(256) k_sync(const float2* __restrict__ z, int6
                 const float2 v = quarter(z[(int64_t)q * zstride + n], r);
                 mine = (int16_t)(qam_level(v.x, qm) | (qam_level(v.y, qm) << 8));
             }
-            for (int d = -D; d <= D; ++d) {
-                const bool hit = (n < s1) && (txl[n - s0 + D + d] == mine);
-                const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                if (lane == 0 && bal) atomicAdd(&cnt[d + D], __popc(bal));
+            const int16_t* tx = txl + (n - s0);
+#pragma unroll
+            for (int k = 0; k < (2 * RX_MAX_DELAY + 32) / 32; ++k) {
+                if (32 * k >= nd) break;
+                int c = 0;
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) {
+                    const int di = 32 * k + j;
+                    if (di >= nd) break;
+                    const bool hit = (n < s1) && (tx[di] == mine);
+                    const int pc = __popc(__ballot_sync(0xffffffffu, hit));
+                    c = lane == j ? pc : c;
+                }
+                creg[k] += c;
             }
         }
+#pragma unroll
+        for (int k = 0; k < (2 * RX_MAX_DELAY + 32) / 32; ++k)
+            if (32 * k + lane < nd && creg[k]) atomicAdd(&cnt[32 * k + lane], creg[k]);
         __syncthreads();
         for (int i = threadIdx.x; i < 2 * D + 1; i += blockDim.x)
             if (cnt[i]) atomicAdd(&counts[blockIdx.x * (2 * D + 1) + i], cnt[i]);
