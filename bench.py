@@ -212,7 +212,11 @@ class ClockSampler:
 # DRAM traffic per launch from one ncu capture (profiles/), valid while the kernel's source file is
 # unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
 PROFILED_TRAFFIC = {
-    "dd_acq": ("k_lms_tile.cuh", "4aa98ce249ce91924c62ffc72be7ff16c405b044", 558848),   # DRAM bytes read + written, one ncu capture of this launch
+    # DRAM bytes read + written, one ncu capture of this launch
+    "dd_acq": ("k_lms_tile.cuh", "867bea91c38ec87ab3f9267cb8cc92be49321113", 563200),
+    # captured on the 2^18-symbol frame (4,277,248 B: the equalised symbols read once, under ncu's
+    # cache flush) and scaled by the symbols of the 2^20-symbol launch (traffic in proportion)
+    "bps": ("k_bps.cu", "9dfb588f3d52777eede3d91485f63858569bdbc5", 17108992),
     "wl": ("k_lms_fast.cuh", "fca5f277b4ecd771cc2e0b0acdff6c7ea8cf98cc", 33638912),
 }
 

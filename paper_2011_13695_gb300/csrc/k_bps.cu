@@ -26,6 +26,8 @@
 // in order; here the unwrap is exact integer arithmetic on b*, so it becomes
 // a three-step scan: per-tile jump sums, a scan of the tile sums with the
 // carried count, then per-tile prefixes that also write z.
+#include <algorithm>
+
 #include "rx_kernels.h"
 
 namespace {
@@ -163,10 +165,25 @@ template <int W, int GS>
 cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
                   cudaStream_t s) {
     const Qam qm = make_qam(m);
-    // symbols per strip (a multiple of W): 768 for 64-symbol windows on frames of a few waves of strips
-    // (less halo per strip), else 512
-    const int LEN = (W == 64 && N >= (int64_t)1 << 18) ? 768 : 512;
     constexpr int NSTRIP = BPS_THREADS / GS;
+    // symbols per strip, a multiple of W: the least of (waves of CTAs) x (LEN + W), the time model of a
+    // launch whose CTAs each take LEN + W symbols' work, over 4 W .. 16 W (ties to the shorter strip)
+    static int slots = 0;
+    if (!slots) {
+        int dev = 0, nsm = 152, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bps<W, GS>, BPS_THREADS,
+                                                      sizeof(float4) * NSTRIP * (8 * W + W));
+        slots = std::max(1, nsm * std::max(1, per));
+    }
+    int LEN = 8 * W;
+    int64_t best = -1;
+    for (int len = 4 * W; len <= 16 * W && len <= 1024; len += W) {
+        const int64_t ctas = 2 * (((N + len - 1) / len + NSTRIP - 1) / NSTRIP);
+        const int64_t cost = ((ctas + slots - 1) / slots) * (len + W);
+        if (best < 0 || cost < best) { best = cost; LEN = len; }
+    }
     const int64_t nstrip = (N + LEN - 1) / LEN;
     dim3 grid((unsigned)((nstrip + NSTRIP - 1) / NSTRIP), 2);
     const size_t smem = sizeof(float4) * NSTRIP * (LEN + W);
