@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "rx_cnn.h"
@@ -110,49 +111,75 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
     }
 }
 
-// dW[co][ci][k] += sum_t dY[co][t] x[ci][t + k - 4], db[co] += sum_t dY[co][t] over a chunk of positions
+// Weight gradients dW[co][ci][k] = sum_t dY[co][t] x[ci][t + k - 4], db[co] = sum_t dY[co][t]: CTA
+// (x, y, z) sums the 256-position chunks x, x + gridDim.x, ... of its (co, ci) tile in registers and writes
+// its partial to row x of part ([row][co][ci][k], then [row][COUT][co] for the biases); k_wgrad_sum adds
+// the rows in order. No atomics: every run gives the same sums.
 template <typename Tin, int CIN, int COUT>
 __global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, const float* __restrict__ dy,
-                                                   int64_t Tp, int64_t T, float* __restrict__ dW, float* __restrict__ db) {
+                                                   int64_t Tp, int64_t T, float* __restrict__ part) {
     constexpr int TC = 256;                           // positions per chunk (static smem < 48 KB)
     constexpr int CO_TILE = COUT < 16 ? COUT : 16;
     constexpr int CI_TILE = CIN < 16 ? CIN : 16;
+    constexpr int64_t ROW = (int64_t)COUT * CIN * KW + COUT;
     __shared__ float dys[CO_TILE][TC];
     __shared__ float xs[CI_TILE][TC + 2 * PAD];
     const int co0 = blockIdx.y * CO_TILE, ci0 = blockIdx.z * CI_TILE;
-    const int64_t t0 = (int64_t)blockIdx.x * TC;      // unpadded
     const int tid = threadIdx.x;
-    for (int i = tid; i < CO_TILE * TC; i += CT) {
-        const int c = i / TC, u = i - c * TC;
-        const int64_t t = t0 + u;
-        dys[c][u] = (t < T) ? dy[(int64_t)(co0 + c) * Tp + t + PAD] : 0.0f;
-    }
-    for (int i = tid; i < CI_TILE * (TC + 2 * PAD); i += CT) {
-        const int c = i / (TC + 2 * PAD), u = i - c * (TC + 2 * PAD);
-        const int64_t tp = t0 + u;                    // padded index of position t0 + u - 4
-        xs[c][u] = (tp < Tp) ? ld(x + (int64_t)(ci0 + c) * Tp + tp) : 0.0f;
-    }
-    __syncthreads();
     const int co = tid / 16, ci = tid % 16;
-    if (co < CO_TILE && ci < CI_TILE) {
-        float acc[KW];
-        float win[KW];
+    const bool mine = co < CO_TILE && ci < CI_TILE;
+    float acc[KW];
 #pragma unroll
-        for (int k = 0; k < KW; ++k) { acc[k] = 0.0f; win[k] = xs[ci][k]; }
-        float dbs = 0.0f;
-        for (int u = 0; u < TC; ++u) {
-            const float d = dys[co][u];
-#pragma unroll
-            for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, win[k], acc[k]);
-            dbs += d;
-#pragma unroll
-            for (int k = 0; k < KW - 1; ++k) win[k] = win[k + 1];
-            if (u + 1 < TC) win[KW - 1] = xs[ci][u + KW];   // window of position u + 1 (xs has TC + 8 columns)
+    for (int k = 0; k < KW; ++k) acc[k] = 0.0f;
+    float dbs = 0.0f;
+    const int64_t nchunk = (T + TC - 1) / TC;
+    for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        const int64_t t0 = ch * TC;                   // unpadded
+        __syncthreads();                              // the previous chunk's reads are done
+        for (int i = tid; i < CO_TILE * TC; i += CT) {
+            const int c = i / TC, u = i - c * TC;
+            const int64_t t = t0 + u;
+            dys[c][u] = (t < T) ? dy[(int64_t)(co0 + c) * Tp + t + PAD] : 0.0f;
         }
+        for (int i = tid; i < CI_TILE * (TC + 2 * PAD); i += CT) {
+            const int c = i / (TC + 2 * PAD), u = i - c * (TC + 2 * PAD);
+            const int64_t tp = t0 + u;                // padded index of position t0 + u - 4
+            xs[c][u] = (tp < Tp) ? ld(x + (int64_t)(ci0 + c) * Tp + tp) : 0.0f;
+        }
+        __syncthreads();
+        if (mine) {
+            float win[KW];
 #pragma unroll
-        for (int k = 0; k < KW; ++k) atomicAdd(&dW[((int64_t)(co0 + co) * CIN + ci0 + ci) * KW + k], acc[k]);
-        if (ci == 0 && blockIdx.z == 0) atomicAdd(&db[co0 + co], dbs);
+            for (int k = 0; k < KW; ++k) win[k] = xs[ci][k];
+            for (int u = 0; u < TC; ++u) {
+                const float d = dys[co][u];
+#pragma unroll
+                for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, win[k], acc[k]);
+                dbs += d;
+#pragma unroll
+                for (int k = 0; k < KW - 1; ++k) win[k] = win[k + 1];
+                if (u + 1 < TC) win[KW - 1] = xs[ci][u + KW];   // window of position u + 1 (xs has TC + 8 columns)
+            }
+        }
     }
+    if (mine) {
+        float* row = part + (int64_t)blockIdx.x * ROW;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) row[((int64_t)(co0 + co) * CIN + ci0 + ci) * KW + k] = acc[k];
+        if (ci == 0 && blockIdx.z == 0) row[(int64_t)COUT * CIN * KW + co0 + co] = dbs;
+    }
+}
+
+// dW = the sum of the nrow partial rows in order, then db likewise
+__global__ void k_wgrad_sum(const float* __restrict__ part, int64_t nw, int64_t nb, int nrow, float* __restrict__ dW,
+                            float* __restrict__ db) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nw + nb) return;
+    const int64_t row = nw + nb;
+    float s = 0.0f;
+    for (int r = 0; r < nrow; ++r) s += part[(int64_t)r * row + i];
+    if (i < nw) dW[i] = s;
+    else db[i - nw] = s;
 }
 
 __global__ void k_to_channels(const float2* __restrict__ z, int64_t T, int64_t Tp, __nv_bfloat16* __restrict__ x0) {
@@ -229,11 +256,18 @@ cudaError_t conv_t(const Tin* x, int64_t Tp, int64_t T, const float* W, const fl
 }
 
 template <typename Tin, int CIN, int COUT>
-cudaError_t wgrad_t(const Tin* x, const float* dy, int64_t Tp, int64_t T, float* dW, float* db, cudaStream_t s) {
+cudaError_t wgrad_t(const Tin* x, const float* dy, int64_t Tp, int64_t T, float* part, float* dW, float* db,
+                    cudaStream_t s) {
     constexpr int CO_TILE = COUT < 16 ? COUT : 16;
     constexpr int CI_TILE = CIN < 16 ? CIN : 16;
-    dim3 grid((unsigned)((T + 255) / 256), COUT / CO_TILE, CIN / CI_TILE);
-    k_conv_wgrad<Tin, CIN, COUT><<<grid, CT, 0, s>>>(x, dy, Tp, T, dW, db);
+    const int64_t nchunk = (T + 255) / 256;
+    const int nrow = (int)std::min<int64_t>(std::max<int64_t>(nchunk, 1), CNN_WG_SPLIT);
+    dim3 grid((unsigned)nrow, COUT / CO_TILE, CIN / CI_TILE);
+    k_conv_wgrad<Tin, CIN, COUT><<<grid, CT, 0, s>>>(x, dy, Tp, T, part);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    const int64_t nw = (int64_t)COUT * CIN * KW, nb = COUT;
+    k_wgrad_sum<<<(unsigned)((nw + nb + 255) / 256), 256, 0, s>>>(part, nw, nb, nrow, dW, db);
     return cudaGetLastError();
 }
 
@@ -259,30 +293,29 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* ou
                                            out, s);
 }
 
-// loss gradient and all parameter gradients (B.grad zeroed here) for the last forward
+// loss gradient and all parameter gradients (every entry of B.grad written) for the last forward
 cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t T, float* loss,
                          cudaStream_t s) {
     const int64_t Tp = T + 2 * PAD;
-    cudaError_t e = cudaMemsetAsync(B.grad, 0, sizeof(float) * B.nparam, s);
-    if (e) return e;
+    cudaError_t e = cudaSuccess;
     k_mse<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(out, tgt, T, Tp, B.d[3], loss);
     if ((e = cudaGetLastError())) return e;
     float* G = B.grad;
     const float* Wb = B.wbwd;
     // layer 3: weights, then data (masked by act[3] > 0) -> d[2]
-    if ((e = wgrad_t<__nv_bfloat16, 64, 4>(B.act[3], B.d[3], Tp, T, G + B.off[6], G + B.off[7], s))) return e;
+    if ((e = wgrad_t<__nv_bfloat16, 64, 4>(B.act[3], B.d[3], Tp, T, B.wpart, G + B.off[6], G + B.off[7], s))) return e;
     if ((e = conv_t<float, 4, 64, 2>(B.d[3], Tp, T, Wb + B.off[6], nullptr, nullptr, B.act[3], B.d[2], nullptr,
                                      nullptr, s)))
         return e;
-    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[2], B.d[2], Tp, T, G + B.off[4], G + B.off[5], s))) return e;
+    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[2], B.d[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
     if ((e = conv_t<float, 64, 64, 2>(B.d[2], Tp, T, Wb + B.off[4], nullptr, nullptr, B.act[2], B.d[1], nullptr,
                                       nullptr, s)))
         return e;
-    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[1], B.d[1], Tp, T, G + B.off[2], G + B.off[3], s))) return e;
+    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[1], B.d[1], Tp, T, B.wpart, G + B.off[2], G + B.off[3], s))) return e;
     if ((e = conv_t<float, 64, 64, 2>(B.d[1], Tp, T, Wb + B.off[2], nullptr, nullptr, B.act[1], B.d[0], nullptr,
                                       nullptr, s)))
         return e;
-    return wgrad_t<__nv_bfloat16, 4, 64>(B.act[0], B.d[0], Tp, T, G + B.off[0], G + B.off[1], s);
+    return wgrad_t<__nv_bfloat16, 4, 64>(B.act[0], B.d[0], Tp, T, B.wpart, G + B.off[0], G + B.off[1], s);
 }
 
 // the padding columns of every activation/gradient plane for a sequence of length T

@@ -6,6 +6,10 @@
 
 #include <cstdint>
 
+// the weight gradients sum their positions in CNN_WG_SPLIT interleaved shares (one CTA each), then the
+// shares in a fixed order: the same sums on every run
+#define CNN_WG_SPLIT 32
+
 struct CnnBufs {
     int C = 64;                     // hidden channels
     int64_t nparam = 0;
@@ -15,6 +19,7 @@ struct CnnBufs {
     float* m = nullptr;             // Adam moments
     float* v = nullptr;
     float* grad = nullptr;          // FP32 gradients of the last backward
+    float* wpart = nullptr;         // [CNN_WG_SPLIT][C * C * 9 + C] per-CTA weight-gradient partials
     float* wfwd = nullptr;          // BF16-rounded parameters as used by the forward
     float* wbwd = nullptr;          // transposed, flipped BF16-rounded weights for the data gradient
     // BF16 weights in (k, ci) order for the tensor cores: layers 1, 2 as [64][9 * 64], layer 3 as

@@ -34,7 +34,7 @@ int64_t count_params(int C, int64_t* off) {
 
 void pe_free(rx_pe* p) {
     CnnBufs& B = p->B;
-    void* ptrs[] = {B.master, B.m, B.v, B.grad, B.wfwd, B.wbwd, B.wtc, B.offs_dev, B.cin_dev, B.cout_dev, B.out, B.loss,
+    void* ptrs[] = {B.master, B.m, B.v, B.grad, B.wpart, B.wfwd, B.wbwd, B.wtc, B.offs_dev, B.cin_dev, B.cout_dev, B.out, B.loss,
                     B.act[0], B.act[1], B.act[2], B.act[3], B.d[0], B.d[1], B.d[2], B.d[3], B.err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -152,6 +152,7 @@ rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const 
     A(cudaMalloc(&B.m, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.v, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.grad, sizeof(float) * B.nparam));
+    A(cudaMalloc(&B.wpart, sizeof(float) * CNN_WG_SPLIT * ((size_t)channels * channels * 9 + channels)));
     A(cudaMalloc(&B.wfwd, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.wbwd, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.wtc, sizeof(__nv_bfloat16) * (size_t)wtc_elems(channels)));
