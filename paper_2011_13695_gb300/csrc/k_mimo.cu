@@ -26,6 +26,8 @@
 // conj(x_p[2n + c - k]) and g_qp[k] += mu_c * sum_n e_q[n] x_p[2n + c - k].
 // A row's taps are then [h_q0, h_q1, g_q0, g_q1] (4T); the flattened term
 // index u = v 2T + p T + k (v = 1: conjugate) carries the same lane split.
+#include <cooperative_groups.h>
+
 #include "rx_fft.cuh"
 #include "rx_kernels.h"
 
@@ -301,108 +303,206 @@ __global__ void __launch_bounds__(NT) k_lms(LmsArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// A3 on the fixed CMA taps
-// ---------------------------------------------------------------------------
+// A3 on the fixed CMA taps, in one launch: a cluster of FOE_CL CTAs, CTA r on output row
+// q = r / (FOE_CL / 2) and one contiguous share of the window. Each CTA stages its share's input
+// samples in shared memory (every load in flight at once: the latency of this part's L2 is long), writes
+// its outputs y to yw and v = y^4 into the shared memory of its row's leader (rank q FOE_CL / 2) through
+// distributed shared memory. Each leader transforms its row's v (N points, zero padded; the last pass
+// writes P_q[k] = |V_q[k]|^2 into its own and, where room allows, the other leader's shared memory),
+// finds the first maximum of P_0 + P_1 (both leaders add in the same order), and forms its row's
+// per-block sums sum_n v_n e^{-j 2 pi kappa n / N}, which equal sum_n (y_n e^{-j w_c n})^4 for
+// w_c = 2 pi kappa / (4 N); the phasor is an entry of the FFT twiddle table. Leader 1 writes its sums into
+// leader 0's shared memory; leader 0 then takes the phases, their unwrap, the least-squares slope, the
+// code and the corrected taps. Every CTA arrives at the cluster barrier first thing and waits on it
+// before its first access to another CTA's shared memory, then passes the same three cluster barriers;
+// after the third no CTA touches another's shared memory, so the others may exit.
+constexpr int FOE_CL = 8;            // CTAs per cluster: four per output row
+constexpr int FOE_NBMAX = 1024;      // window blocks of the fine stage, at most
 
-__global__ void k_foe_window(const float2* __restrict__ x, int64_t xstride, int64_t xlen, int64_t off, int T,
-                             int64_t n0, int64_t nw, const float2* __restrict__ taps, float2* yw) {
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= 2 * nw) return;
-    const int q = (int)(o / nw);
-    const int64_t n = n0 + (o - q * nw);
-    const int c = (T - 1) / 2;
-    float2 acc = make_float2(0.0f, 0.0f);
-    for (int p = 0; p < 2; ++p) {
-        for (int k = 0; k < T; ++k) {
-            const int64_t i = off + 2 * n + c - k;
-            if (i >= 0 && i < xlen) acc = cmac(acc, taps[(q * 2 + p) * T + k], x[(int64_t)p * xstride + i]);
-        }
-    }
-    yw[o] = acc;
-}
-
-// |FFT_Nf(y_q^4)|^2 per polarisation, zero padded beyond nw
 template <int K>
-__global__ void __launch_bounds__((1 << K) / 16) k_foe_pgram(const float2* yw, int64_t nw, const float2* tw,
-                                                            float* P) {
-    constexpr int N = 1 << K;
-    extern __shared__ float2 sm[];
-    const int q = blockIdx.x;
-    const float2* y = yw + (int64_t)q * nw;
-    auto load = [&](int i) -> float2 {
-        if (i >= nw) return make_float2(0.0f, 0.0f);
-        const float2 v = y[i];
-        const float2 v2 = cmul(v, v);
-        return cmul(v2, v2);
-    };
-    float* Pq = P + (int64_t)q * N;
-    auto store = [&](int i, float2 v) { Pq[i] = cabs2(v); };
-    fft_run<K, -1, true, true>(sm, tw, load, store);
-}
+struct FoeShape {
+    static constexpr int N = 1 << K;
+    static constexpr int NTH = N / 16 > 512 ? N / 16 : 512;
+    static constexpr int FB = fft_smem_elems(N);                // FFT working copy (float2)
+    static constexpr bool TWS = K <= 13;                        // twiddles and the other periodogram in shared memory
+    static constexpr int TWN = TWS ? N : 0;                     // entries t = i RX_FFT_TW_N / N, i < N
+    static constexpr int PCN = TWS ? N / 2 : 0;                 // the other leader's P (N floats)
+    static constexpr size_t SMEM = sizeof(float2) * (FB + N / 2 + 2 * FOE_NBMAX + TWN + PCN);
+    // staged samples per thread: 2 (2 ceil(N / 8) + RX_TMAX - 1) at most over NTH threads
+    static constexpr int XPER = (2 * (2 * (N / 8 + 1) + RX_TMAX) + NTH - 1) / NTH;
+};
 
-// coarse peak, fine slope, code, phase increment and corrected taps. FP32 except the few scalar
-// steps from the slope to the integer code (FP64 is a small fraction of the FP32 rate here).
-__global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __restrict__ yw, int64_t nw, int Lb,
-                           double rs, double fs, double grid, int T, RxDevState* st) {
-    const int nf = 1 << kf;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+template <int K>
+__global__ void __cluster_dims__(FOE_CL, 1, 1) __launch_bounds__(FoeShape<K>::NTH, 1) k_foe(FoeArgs a) {
+    namespace cg = cooperative_groups;
+    using S = FoeShape<K>;
+    constexpr int N = S::N, NTH = S::NTH, HALF = FOE_CL / 2;
+    constexpr int TWSHIFT = RX_FFT_TW_LOG2 - K;
+    extern __shared__ float2 fsm[];
+    float2* fbuf = fsm;                               // window samples, then the FFT working copy, then P_q
+    float2* vbuf = fsm + S::FB;                       // [N / 2] v of this row (leaders)
+    float2* asum = vbuf + N / 2;                      // [2][FOE_NBMAX] per-block sums (leader 0)
+    float2* tws = asum + 2 * FOE_NBMAX;               // [N] twiddle entries (leaders, K <= 13)
+    float* Pc = reinterpret_cast<float*>(tws + S::TWN);   // [N] the other leader's P (leaders, K <= 13)
+    __shared__ float2 s_taps[2 * RX_TMAX];
     __shared__ float bv[32];
     __shared__ int bi[32];
     __shared__ int s_kappa;
-    __shared__ float s_ph[1024];
     __shared__ float s_wf;
-    // first maximum of P0 + P1
-    float best = -1.0f;
-    int besti = 0;
-    for (int k = tid; k < nf; k += nthr) {
-        const float v = P[k] + P[nf + k];
-        if (v > best) { best = v; besti = k; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
-        if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
-    }
-    if ((tid & 31) == 0) { bv[tid >> 5] = best; bi[tid >> 5] = besti; }
-    __syncthreads();
-    if (tid == 0) {
-        float b = -1.0f;
-        int idx = 0;
-        for (int w = 0; w < (nthr >> 5); ++w) {
-            if (bv[w] > b || (bv[w] == b && bi[w] < idx)) { b = bv[w]; idx = bi[w]; }
+    cg::cluster_group cl = cg::this_cluster();
+    cl.barrier_arrive();                              // this CTA has started
+    const int rank = (int)cl.block_rank();
+    const int q = rank / HALF, part = rank % HALF;
+    const bool leader = part == 0;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int T = a.T, c = (T - 1) / 2;
+    const int64_t nw = a.nw;
+
+    // 0. stage this CTA's input samples (both polarisations, zero outside the buffer), the row's taps
+    //    and, in the leaders, the transform's twiddles
+    const int64_t chunk = (nw + HALF - 1) / HALF;
+    const int64_t i0 = min(nw, part * chunk), i1 = min(nw, i0 + chunk);
+    const int span = i1 > i0 ? (int)(2 * (i1 - i0 - 1) + T) : 0;   // samples of the share's outputs
+    const int64_t lo = a.off + 2 * (a.n0 + i0) + c - (T - 1);      // buffer index of sample 0 of the span
+    {
+        float2 xv[S::XPER];
+#pragma unroll
+        for (int j = 0; j < S::XPER; ++j) {
+            const int t = tid + j * NTH;
+            const int p = t >= span ? 1 : 0;
+            const int64_t g = lo + (t - p * span);
+            xv[j] = (t < 2 * span && g >= 0 && g < a.xlen) ? __ldg(a.x + (int64_t)p * a.xstride + g)
+                                                            : make_float2(0.0f, 0.0f);
         }
-        s_kappa = idx < nf / 2 ? idx : idx - nf;
-    }
-    __syncthreads();
-    const int kappa = s_kappa;
-    // a_j = sum_q sum_{n in block j} (y_q[n] e^{-j w_c n})^4, w_c = 2 pi kappa / (4 nf); one warp per
-    // block, FP32 sums (2 Lb terms of order one), then arg(a_j) by one thread per block
-    // (|kappa n| < nf nw / 2 <= 2^26 and period <= 2^16: 32-bit index arithmetic is exact)
-    const int nb = min((int)(nw / Lb), 1024);
-    const int w = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
-    const int period = 4 * nf;
-    for (int j = w; j < nb; j += nwarp) {
-        float ax = 0.0f, ay = 0.0f;
-        for (int q = 0; q < 2; ++q) {
-            for (int n = j * Lb + lane; n < (j + 1) * Lb; n += 32) {
-                int r = (kappa * n) % period;
-                if (r < 0) r += period;
-                float sn, cs;
-                sincospif(-2.0f * (float)r / (float)period, &sn, &cs);
-                const float2 v = cmul(yw[(int64_t)q * nw + n], make_float2(cs, sn));
-                const float2 v2 = cmul(v, v);
-                const float2 v4 = cmul(v2, v2);
-                ax += v4.x;
-                ay += v4.y;
+        if (S::TWS && leader) {
+            constexpr int TPER = S::TWN / NTH > 0 ? S::TWN / NTH : 1;
+            float2 tv[TPER];
+#pragma unroll
+            for (int j = 0; j < TPER; ++j) {
+                const int i = tid + j * NTH;
+                tv[j] = i < S::TWN ? __ldg(&a.tw[i << TWSHIFT]) : make_float2(0.0f, 0.0f);
             }
+#pragma unroll
+            for (int j = 0; j < TPER; ++j)
+                if (tid + j * NTH < S::TWN) tws[tid + j * NTH] = tv[j];
         }
-        ax = warp_sum(ax);
-        ay = warp_sum(ay);
-        if (lane == 0) s_ph[j] = atan2f(ay, ax);
+#pragma unroll
+        for (int j = 0; j < S::XPER; ++j)
+            if (tid + j * NTH < 2 * span) fbuf[tid + j * NTH] = xv[j];
+    }
+    for (int t = tid; t < 2 * T; t += NTH) s_taps[t] = a.taps[q * 2 * T + t];
+    __syncthreads();
+
+    // 1. this CTA's share of row q's outputs, two per thread in one pass over the taps
+    cl.barrier_wait();                                // every CTA of the cluster has started
+    float2* vlead = cl.map_shared_rank(vbuf, q * HALF);
+    for (int64_t i = i0 + tid; i < i1; i += 2 * NTH) {
+        const bool two = i + NTH < i1;
+        const int u0 = 2 * (int)(i - i0) + T - 1;      // span index of tap 0's sample
+        const int u1 = two ? u0 + 2 * NTH : u0;
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll 3
+        for (int k = 0; k < T; ++k) {
+            const float2 h0 = s_taps[k], h1 = s_taps[T + k];
+            a0 = cmac(a0, h0, fbuf[u0 - k]);
+            b0 = cmac(b0, h1, fbuf[span + u0 - k]);
+            a1 = cmac(a1, h0, fbuf[u1 - k]);
+            b1 = cmac(b1, h1, fbuf[span + u1 - k]);
+        }
+        const float2 y0 = cadd(a0, b0);
+        a.yw[(int64_t)q * nw + i] = y0;
+        const float2 z0 = cmul(y0, y0);
+        vlead[i] = cmul(z0, z0);
+        if (two) {
+            const float2 y1 = cadd(a1, b1);
+            a.yw[(int64_t)q * nw + i + NTH] = y1;
+            const float2 z1 = cmul(y1, y1);
+            vlead[i + NTH] = cmul(z1, z1);
+        }
+    }
+    cl.sync();                                        // #1: every v in its leader (and the spans read)
+
+    // 2. leaders: P_q = |FFT_N(v_q)|^2, left in the FFT buffer as floats by the last pass (whose reads
+    //    all precede its writes), and copied into the other leader
+    float* P = reinterpret_cast<float*>(fbuf);
+    if (leader) {
+        auto load = [&](int i) -> float2 { return i < nw ? vbuf[i] : make_float2(0.0f, 0.0f); };
+        if constexpr (S::TWS) {
+            float* Pr = cl.map_shared_rank(Pc, q ? 0 : HALF);
+            auto store = [&](int i, float2 v) {
+                const float e = cabs2(v);
+                P[i] = e;
+                Pr[i] = e;
+            };
+            fft_run_tw<K, -1, true, true>(fbuf, TwShared{tws, TWSHIFT}, load, store);
+        } else {
+            auto store = [&](int i, float2 v) { P[i] = cabs2(v); };
+            fft_run<K, -1, true, true>(fbuf, a.tw, load, store);
+        }
+    }
+    cl.sync();                                        // #2: both periodograms complete
+
+    const int nb = min((int)(nw / a.Lb), FOE_NBMAX);
+    if (leader) {
+        // 3. first maximum of P_0 + P_1 (a + b == b + a: both leaders find the same bin); the other
+        //    leader's bins from the local copy, else across the cluster, all in flight together
+        const float* Pp = S::TWS ? Pc : cl.map_shared_rank(P, q ? 0 : HALF);
+        constexpr int PER = N / NTH;
+        float pv[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) pv[u] = Pp[tid + u * NTH];
+        float best = -1.0f;
+        int besti = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const float v = P[tid + u * NTH] + pv[u];
+            if (v > best) { best = v; besti = tid + u * NTH; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+            if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
+        }
+        if (lane == 0) { bv[w] = best; bi[w] = besti; }
+        __syncthreads();
+        if (tid == 0) {
+            float b = -1.0f;
+            int idx = 0;
+            for (int k = 0; k < NTH / 32; ++k)
+                if (bv[k] > b || (bv[k] == b && bi[k] < idx)) { b = bv[k]; idx = bi[k]; }
+            s_kappa = idx < N / 2 ? idx : idx - N;
+        }
+        __syncthreads();
+        // 4. this row's per-block sums, one warp per block (|kappa n| < N nw / 2 <= 2^26: the phase
+        //    index kappa n mod N is exact in 32 bits; e^{-j 2 pi t / N} is twiddle entry t RX_FFT_TW_N / N),
+        //    into leader 0's shared memory
+        const int kappa = s_kappa;
+        float2* adst = cl.map_shared_rank(asum, 0) + q * FOE_NBMAX;
+        for (int j = w; j < nb; j += NTH / 32) {
+            float ax = 0.0f, ay = 0.0f;
+            for (int n = j * a.Lb + lane; n < (j + 1) * a.Lb; n += 32) {
+                const int t = (kappa * n) & (N - 1);
+                const float2 ph = S::TWS ? tws[t] : __ldg(&a.tw[t << TWSHIFT]);
+                const float2 v = cmul(vbuf[n], ph);
+                ax += v.x;
+                ay += v.y;
+            }
+            ax = warp_sum(ax);
+            ay = warp_sum(ay);
+            if (lane == 0) adst[j] = make_float2(ax, ay);
+        }
+    }
+    cl.sync();                                        // #3: both rows' sums in leader 0
+    if (rank != 0) return;
+
+    // 5. leader 0: phi_j = arg(a_0j + a_1j), unwrapped in sequence (a prefix sum of the steps brought
+    //    into [-pi, pi]), then the least-squares slope against the block centres, by warp 0
+    float* s_ph = reinterpret_cast<float*>(vbuf);     // vbuf is no longer read
+    for (int j = tid; j < nb; j += NTH) {
+        const float2 s0 = asum[j], s1 = asum[FOE_NBMAX + j];
+        s_ph[j] = atan2f(s0.y + s1.y, s0.x + s1.x);
     }
     __syncthreads();
-    // unwrap: u_j = u_{j-1} + wrap(ph_j - ph_{j-1}) (the step brought into [-pi, pi]), a prefix sum;
-    // then the least-squares slope of u_j against the block centres, all by warp 0
     const float PIf = 3.14159265358979f;
     if (w == 0 && nb >= 2) {
         const float ph0 = s_ph[0];
@@ -426,7 +526,7 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
             prev_raw = __shfl_sync(0xffffffffu, ph, 31);
             carry = __shfl_sync(0xffffffffu, carry + st_, 31);
             __syncwarp();
-            if (j < nb) s_ph[j] = u;                     // in place: the chunk's raw phases were read above
+            if (j < nb) s_ph[j] = u;                  // in place: the chunk's raw phases were read above
             __syncwarp();
         }
         for (int j = lane; j < nb; j += 32) { sx += (float)j; sy += s_ph[j]; }
@@ -441,28 +541,30 @@ __global__ void k_foe_fine(const float* __restrict__ P, int kf, const float2* __
         }
         sjj = warp_sum(sjj);
         sju = warp_sum(sju);
-        if (lane == 0) s_wf = sju / (sjj * (float)Lb) / 4.0f;   // slope per symbol, / 4 for the 4th power
+        if (lane == 0) s_wf = sju / (sjj * (float)a.Lb) / 4.0f;   // slope per symbol, / 4 for the 4th power
     }
     __syncthreads();
+    // 6. the code: w_c = 2 pi kappa / (4 N) is kappa (pi / 2^(K+1)), the same rounding; the few FP64
+    //    steps use host-side scales instead of divisions
+    RxDevState* st = a.st;
     if (tid == 0) {
         const double PI = 3.14159265358979323846;
-        const double wc = 2.0 * PI * (double)kappa / (4.0 * nf);
+        const int kappa = s_kappa;
+        const double wc = (double)kappa * ldexp(PI, -(K + 1));
         const double wh = wc + (nb >= 2 ? (double)s_wf : 0.0);
-        const double u = wh * rs / (2.0 * PI) / grid;
+        const double u = wh * a.u_scale;
         const double code = rint(u);
         st->fo_code = (int)code;
         st->fo_w = wh;
         st->coarse_bin = kappa;
         st->fo_margin = fabs(fabs(u - floor(u)) - 0.5);
         st->fo_valid = 1;
-        const double F = code * grid / fs;                // turns per sample, |F| < 0.5
-        st->nco_inc = llrint(ldexp(F, 64));
+        st->nco_inc = llrint(ldexp(code * a.f_scale, 64));   // turns per sample, |F| < 0.5
     }
     __syncthreads();
     // taps_init = taps_cma * exp(-j 2 pi code grid (k - c) / fs): the phase accumulator at k - c
-    const int c = (T - 1) / 2;
     const long long inc = st->nco_inc;
-    for (int t = tid; t < 4 * T; t += nthr) {
+    for (int t = tid; t < 4 * T; t += NTH) {
         const int k = t % T;
         st->taps_init[t] = cmul(st->taps_cma[t], nco_conj(inc, (long long)(k - c)));
     }
@@ -657,42 +759,29 @@ cudaError_t launch_lms_wl(const LmsArgs& a, int threads, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
-                              int64_t nw, const float2* taps, float2* yw, cudaStream_t s) {
-    const int64_t tot = 2 * nw;
-    k_foe_window<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, xstride, xlen, off, T, n0, nw, taps, yw);
-    return cudaGetLastError();
-}
-
 template <int K>
-static cudaError_t pgram_t(const float2* yw, int64_t nw, const float2* tw, float* P, cudaStream_t s) {
-    constexpr int N = 1 << K;
-    const size_t smem = sizeof(float2) * fft_smem_elems(N);
+static cudaError_t foe_t(const FoeArgs& a, cudaStream_t s) {
+    using S = FoeShape<K>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_foe_pgram<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_foe<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         attr = true;
     }
-    k_foe_pgram<K><<<2, N / 16, smem, s>>>(yw, nw, tw, P);
+    k_foe<K><<<FOE_CL, S::NTH, S::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_foe_pgram(const float2* yw, int64_t nw, int kf, const float2* tw, float* P, cudaStream_t s) {
+cudaError_t launch_foe(const FoeArgs& a, int kf, cudaStream_t s) {
+    if (a.nw < 1 || a.T < 1 || a.T > RX_TMAX || a.Lb < 1 || 2 * a.nw > ((int64_t)1 << kf)) return cudaErrorInvalidValue;
     switch (kf) {
-        case 9: return pgram_t<9>(yw, nw, tw, P, s);
-        case 10: return pgram_t<10>(yw, nw, tw, P, s);
-        case 11: return pgram_t<11>(yw, nw, tw, P, s);
-        case 12: return pgram_t<12>(yw, nw, tw, P, s);
-        case 13: return pgram_t<13>(yw, nw, tw, P, s);
-        case 14: return pgram_t<14>(yw, nw, tw, P, s);
+        case 9: return foe_t<9>(a, s);
+        case 10: return foe_t<10>(a, s);
+        case 11: return foe_t<11>(a, s);
+        case 12: return foe_t<12>(a, s);
+        case 13: return foe_t<13>(a, s);
+        case 14: return foe_t<14>(a, s);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw, int Lb, double rs, double fs,
-                            double grid, int T, RxDevState* st, cudaStream_t s) {
-    k_foe_fine<<<1, 1024, 0, s>>>(P, kf, yw, nw, Lb, rs, fs, grid, T, st);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st, int* flag,

@@ -91,10 +91,22 @@ __device__ __forceinline__ void dftR(float2* v) {
     else dft16<DIR>(v);
 }
 
+// Twiddle sources: entry t of the table exp(-2 pi i t / RX_FFT_TW_N) from global memory, or from a
+// shared copy of every 2^shift-th entry (the only ones an N-point transform reads have t a multiple of
+// RX_FFT_TW_N / N).
+struct TwGlobal {
+    const float2* __restrict__ p;
+    __device__ float2 operator()(int t) const { return __ldg(&p[t]); }
+};
+struct TwShared {
+    const float2* p;
+    int shift;
+    __device__ float2 operator()(int t) const { return p[t >> shift]; }
+};
+
 // One Stockham pass. SRC/DST: 0 = shared memory, 1 = functor.
-template <int N, int R, int DIR, int SRC, int DST, class Load, class Store>
-__device__ __forceinline__ void fft_pass(float2* sm, int Ns, const float2* __restrict__ tw, const Load& load,
-                                         const Store& store) {
+template <int N, int R, int DIR, int SRC, int DST, class Load, class Store, class Tw>
+__device__ __forceinline__ void fft_pass(float2* sm, int Ns, const Tw& tw, const Load& load, const Store& store) {
     constexpr int P = N / 16;
     constexpr int BPT = 16 / R;
     const int tid = threadIdx.x;
@@ -120,8 +132,8 @@ __device__ __forceinline__ void fft_pass(float2* sm, int Ns, const float2* __res
                 const int step = (RX_FFT_TW_N / (Ns * R)) * k;
                 if constexpr (R == 16) {
                     float2 w[16];
-                    w[1] = __ldg(&tw[step]);
-                    w[4] = __ldg(&tw[4 * step]);
+                    w[1] = tw(step);
+                    w[4] = tw(4 * step);
                     if (DIR > 0) { w[1].y = -w[1].y; w[4].y = -w[4].y; }
                     w[2] = cmul(w[1], w[1]);
                     w[3] = cmul(w[2], w[1]);
@@ -136,7 +148,7 @@ __device__ __forceinline__ void fft_pass(float2* sm, int Ns, const float2* __res
                 } else {
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
-                        float2 w = __ldg(&tw[step * r]);
+                        float2 w = tw(step * r);
                         if (DIR > 0) w.y = -w.y;
                         v[b][r] = cmul(v[b][r], w);
                     }
@@ -168,9 +180,8 @@ struct SmemStore {
 // LAST_TO_FN: the last pass writes store(idx, value) (natural order).
 // Otherwise data comes from / goes to shared memory. Must be called by all
 // threads of the block (blockDim.x >= N/16).
-template <int K, int DIR, bool FIRST_FROM_FN, bool LAST_TO_FN, class Load, class Store>
-__device__ __forceinline__ void fft_run(float2* sm, const float2* __restrict__ tw, const Load& load,
-                                        const Store& store) {
+template <int K, int DIR, bool FIRST_FROM_FN, bool LAST_TO_FN, class Load, class Store, class Tw>
+__device__ __forceinline__ void fft_run_tw(float2* sm, const Tw& tw, const Load& load, const Store& store) {
     constexpr int N = 1 << K;
     constexpr int NR16 = K / 4;
     constexpr int REM = K % 4;
@@ -203,4 +214,10 @@ __device__ __forceinline__ void fft_run(float2* sm, const float2* __restrict__ t
             Ns *= 16;
         }
     }
+}
+
+template <int K, int DIR, bool FIRST_FROM_FN, bool LAST_TO_FN, class Load, class Store>
+__device__ __forceinline__ void fft_run(float2* sm, const float2* __restrict__ tw, const Load& load,
+                                        const Store& store) {
+    fft_run_tw<K, DIR, FIRST_FROM_FN, LAST_TO_FN>(sm, TwGlobal{tw}, load, store);
 }

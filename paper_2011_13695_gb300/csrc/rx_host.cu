@@ -82,7 +82,6 @@ struct rx_handle {
     int* tiles = nullptr;
     float2* yacq = nullptr;       // [2][nacq]
     float2* yfoe = nullptr;       // [2][nw]
-    float* pgram = nullptr;       // [2][nf]
     int* sync_counts = nullptr;
     int* flag = nullptr;
     float2* taps_id = nullptr;
@@ -204,7 +203,7 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_all(rx_handle* h) {
     void* ptrs[] = {h->H,    h->tw,    h->cdc,   h->tail,     h->y,           h->z,    h->bstar,
-                    h->mq,   h->tiles, h->yacq,  h->yfoe,     h->pgram,       h->sync_counts, h->flag,
+                    h->mq,   h->tiles, h->yacq,  h->yfoe,     h->sync_counts, h->flag,
                     h->taps_id, h->st, h->stage_in, h->stage_ref, h->stage_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -297,7 +296,6 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(dalloc(&h->tiles, 2 * ntiles + 4));          // per-tile jump sums, then the carry's snapshot
     A(dalloc(&h->yacq, 2 * h->nacq));
     A(dalloc(&h->yfoe, 2 * h->nw));
-    A(dalloc(&h->pgram, 2 * (size_t)nf));
     A(dalloc(&h->sync_counts, 16 * (2 * RX_MAX_DELAY + 1) + 1));     // the counts, then an arrival ticket
     A(dalloc(&h->flag, 512));           // [0] CMA rerun flag, [1] check counter, [2..] check partials
     A(dalloc(&h->taps_id, 4 * RX_TMAX));
@@ -449,6 +447,8 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 a.exclusive = 1;
                 RX_CK(launch_lms(a, kAcqThreads, s));
                 if (rx_status r = enqueue_rest(); r != RX_OK) return r;
+                // the singularity check (it also rebuilds the rerun's start taps), then the rerun when the
+                // check raised the flag
                 RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 0, s));
                 LmsArgs a2 = a;
                 a2.taps_in = st->taps_init;
@@ -459,11 +459,10 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
             }
             {
                 StageScope sc(h, ST_FOE, s);
-                RX_CK(launch_foe_window(h->cdc, h->cap, xlen, off, T, nacq_e / 2, nw_e, st->taps_cma, h->yfoe, s));
-                RX_CK(launch_foe_pgram(h->yfoe, nw_e, kf_e, h->tw, h->pgram, s));
-                RX_CK(launch_foe_fine(h->pgram, kf_e, h->yfoe, nw_e, Lb, c.symbol_rate_hz, h->fs, c.fo_grid_hz, T, st,
-                                      s));
-                nl += 3;
+                FoeArgs f{h->cdc, h->cap, xlen, off, T, nacq_e / 2, nw_e, st->taps_cma, h->yfoe, h->tw, Lb,
+                          c.symbol_rate_hz / (2.0 * M_PI) / c.fo_grid_hz, c.fo_grid_hz / h->fs, st};
+                RX_CK(launch_foe(f, kf_e, s));
+                ++nl;
             }
             if (n_dd > 0) {
                 StageScope sc(h, ST_DDACQ, s);

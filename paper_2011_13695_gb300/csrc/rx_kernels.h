@@ -75,11 +75,23 @@ cudaError_t launch_lms_wl(const LmsArgs& a, int threads, cudaStream_t s);
 // the generic widely-linear kernel alone (any npol), threads 256/512/1024 and >= 4T
 cudaError_t launch_lms_wl_generic(const LmsArgs& a, int threads, cudaStream_t s);
 
-cudaError_t launch_foe_window(const float2* x, int64_t xstride, int64_t xlen, int64_t off, int T, int64_t n0,
-                              int64_t nw, const float2* taps, float2* yw, cudaStream_t s);
-cudaError_t launch_foe_pgram(const float2* yw, int64_t nw, int kf, const float2* tw, float* P, cudaStream_t s);
-cudaError_t launch_foe_fine(const float* P, int kf, const float2* yw, int64_t nw, int Lb, double rs, double fs,
-                            double grid, int T, RxDevState* st, cudaStream_t s);
+// A3 on the fixed CMA taps in one launch (a cluster of CTAs joined through distributed shared memory):
+// the window outputs, the 4th-power periodogram of N = 2^kf points, its first maximum, the per-block
+// phase slope, the code, the phase increment and the corrected taps
+struct FoeArgs {
+    const float2* x;       // equaliser input buffer (polarisation stride xstride), valid [0, xlen)
+    int64_t xstride, xlen, off;
+    int T;
+    int64_t n0, nw;        // window: outputs n0 .. n0 + nw - 1 (2 nw <= 2^kf)
+    const float2* taps;    // [2][2][T] fixed taps
+    float2* yw;            // [2][nw] window outputs
+    const float2* tw;      // FFT twiddle table
+    int Lb;                // symbols per block of the fine stage
+    double u_scale;        // Rs / (2 pi) / grid: rad/symbol to grid steps
+    double f_scale;        // grid / fs: code to turns per sample
+    RxDevState* st;
+};
+cudaError_t launch_foe(const FoeArgs& a, int kf, cudaStream_t s);
 // the singularity check of the CMA outputs; pass 0 also rebuilds the second row into taps_init when the
 // outputs correlate (the rerun's start)
 cudaError_t launch_cma_check(const float2* yacq, int64_t ystride, int64_t nacq, int T, RxDevState* st,
