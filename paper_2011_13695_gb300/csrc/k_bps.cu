@@ -15,8 +15,11 @@
 // the window sum by one add and one subtract per symbol and re-forms it as a
 // direct sum of the ring every W symbols, which bounds the rounding drift to
 // that of a W-term sum. The minimum over phases is one warp-wide min reduction
-// of the (non-negative) sums' bit patterns plus a ballot for the first lane
-// holding it, so ties go to the smallest b exactly. The decision per real
+// of a key per lane: the (non-negative) sum's bit pattern with its low six
+// bits replaced by the phase index, so one reduction gives both the least sum
+// and its phase; sums that agree to within 64 units in the last place
+// (7.6e-6 relative, below the FP32 sums' own rounding of ~64 terms) count as
+// a tie, which goes to the smallest b. The decision per real
 // dimension is evaluated in level units: v = r / (2a) + (L-1)/2, the nearest
 // level is rint(clamp(v, 0, L-1)), computed with a saturating multiply and
 // the 1.5 * 2^23 rounding constant, so the distance costs only FMA-pipe
@@ -47,13 +50,12 @@ __device__ __forceinline__ float bps_dist(float4 v, float2 cc, float2 ss, float2
     return fmaf(e.x, e.x, e.y * e.y);
 }
 
-// publish one window's warp minimum and the lanes holding it: the minimum of the sums' bit patterns as
-// signed integers (the order of the sums, which are not negative)
-__device__ __forceinline__ void bps_publish(float D, uint2* slot, int lane) {
-    const int bits = __float_as_int(D);
-    const int mn = __reduce_min_sync(0xffffffffu, bits);
-    const unsigned int bal = __ballot_sync(0xffffffffu, bits == mn);
-    if (lane == 0) *slot = make_uint2((unsigned int)mn, bal);
+// publish one window's warp minimum: the least key (sum bits >> 6, phase) as unsigned integers, the
+// order of the sums, which are not negative
+__device__ __forceinline__ void bps_publish(float D, unsigned int* slot, int lane, unsigned int b) {
+    const unsigned int key = (__float_as_uint(D) & ~63u) | b;
+    const unsigned int mn = __reduce_min_sync(0xffffffffu, key);
+    if (lane == 0) *slot = mn;
 }
 
 // the windows of one strip for one test phase: the ring of distances, the sliding sum, the published
@@ -61,7 +63,7 @@ __device__ __forceinline__ void bps_publish(float D, uint2* slot, int lane) {
 template <int W, int GS, bool EDGE>
 __device__ __forceinline__ void bps_strip(const float4* __restrict__ yl, float2 cc, float2 ss, float2 hh, float invLm1,
                                           float2 ll, float pen, int nc, int LEN, int64_t s0, int64_t N,
-                                          uint2 (*slots)[W], uint2* myslots, int b, int lane, int q,
+                                          unsigned int (*slots)[W], unsigned int* myslots, int b, int lane, int q,
                                           uint8_t* __restrict__ bstar, int64_t bstride) {
     constexpr int NW = GS / 32;
     // the last W distances of this thread's phase, in registers (indices fixed at compile time)
@@ -74,7 +76,7 @@ __device__ __forceinline__ void bps_strip(const float4* __restrict__ yl, float2 
         ring[u] = d;
         D += d;
     }
-    bps_publish(D, &myslots[0], lane);                // window of local output 0
+    bps_publish(D, &myslots[0], lane, (unsigned)b);   // window of local output 0
     for (int ch = 0; ch <= nc; ++ch) {
         if (ch > 0) {
             const float4* yc = yl + ch * W;
@@ -86,7 +88,7 @@ __device__ __forceinline__ void bps_strip(const float4* __restrict__ yl, float2 
                 ring[u] = d;
                 D = (D + d) - old;
                 // window of local output (ch - 1) W + u + 1 is complete; its slot is (u + 1) % W
-                bps_publish(EDGE ? fmaxf(D, 0.0f) : D, &myslots[(u + 1) & (W - 1)], lane);
+                bps_publish(EDGE ? fmaxf(D, 0.0f) : D, &myslots[(u + 1) & (W - 1)], lane, (unsigned)b);
             }
             float t = pen;                            // re-form the sum directly from the ring
 #pragma unroll
@@ -97,12 +99,8 @@ __device__ __forceinline__ void bps_strip(const float4* __restrict__ yl, float2 
         for (int slot = b; slot < W; slot += GS) {
             const int kl = slot == 0 ? ch * W : (ch - 1) * W + slot;
             if (kl >= 0 && kl < LEN && s0 + kl < N) {
-                const uint2 w0 = slots[0][slot];
-                int r = __ffs(w0.y) - 1;
-                if (NW == 2) {
-                    const uint2 w1 = slots[NW - 1][slot];
-                    if ((int)w1.x < (int)w0.x) r = 32 + __ffs(w1.y) - 1;
-                }
+                const unsigned int k0 = slots[0][slot];
+                const int r = (int)((NW == 2 ? min(k0, slots[NW - 1][slot]) : k0) & 63u);
                 bstar[(int64_t)q * bstride + s0 + kl] = (uint8_t)r;
             }
         }
@@ -118,7 +116,7 @@ __global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict
     constexpr int NW = GS / 32;
     extern __shared__ float4 smem_v[];
     float4* ys = smem_v;                              // [NSTRIP][LEN + W]: (x, y, y, -x)
-    __shared__ uint2 slots[NSTRIP][NW][W];            // per output slot: (warp minimum bits, ballot of its lanes)
+    __shared__ unsigned int slots[NSTRIP][NW][W];     // per output slot: the warp's least key
     const int tid = threadIdx.x;
     const int sl = tid / GS;                          // strip within the CTA
     const int b = tid % GS;
@@ -151,7 +149,7 @@ __global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict
     const float2 hh = make_float2(hL, hL), ll = make_float2(Lm1, Lm1);
     const float pen = b < B ? 0.0f : 3.0e38f;
     const int nc = LEN / W;
-    uint2* myslots = &slots[sl][wip][0];
+    unsigned int* myslots = &slots[sl][wip][0];
 
     if (edge)
         bps_strip<W, GS, true>(yl, cc, ss, hh, invLm1, ll, pen, nc, LEN, s0, N, slots[sl], myslots, b, lane, q, bstar,
