@@ -105,8 +105,13 @@ struct LmsTileShape {
     static_assert(OPL == 2 || OPL == 4 || OPL == 8, "2, 4 or 8 outputs per lane");
     static_assert(T % 2 == 1 && T >= 3, "odd tap count");
     static_assert(NUPD <= NT, "one thread per tap component");
+    static_assert(NT <= 256, "the DD block phase's fixed-point sum holds NT <= 256 terms");
     static_assert(PS % 2 == 0, "16-byte aligned parity arrays");
 };
+
+// fixed-point scale of the DD block phase's sum of y^4, and the bound of one term (|y^4| < 64)
+constexpr float kPhaseFx = 65536.0f;
+constexpr float kPhaseLim = 4194304.0f;
 
 // One halving level of a reduce-scatter: lanes with (lane & mask) keep the upper half of v[0, N),
 // the others the lower half; each adds its partner's copy of the half it keeps.
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     float4* tapx = smem4 + S::WIN4;                                 // [class][TS]: (hx, hx, hy, hy)
     float4* es = tapx + S::TAP4;                                    // [ESP]: (ex, ex, ey, ey), padded
     float* part = reinterpret_cast<float*>(es + S::ES4);            // [warp][class][2 IM]
-    float2* ypart = reinterpret_cast<float2*>(es + S::ES4 + S::PART4);   // [NW]
+    int2* ypart = reinterpret_cast<int2*>(es + S::ES4 + S::PART4);       // [NW] block phase partials
     float2* ytr = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4);   // [warp][subset][YTS] (OPL == 8)
     float2* bph = reinterpret_cast<float2*>(es + S::ES4 + S::PART4 + S::YP4 + S::YT4);   // [NBT]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -364,18 +369,24 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         if (a.cma) {
             if (valid) e = cscale(y, a.R2 - cabs2(y));
         } else {
-            float2 c4 = make_float2(0.0f, 0.0f);
+            // the block sum of y^4 in 2^-16 fixed point: one integer warp reduction per component (exact and
+            // in no particular order) instead of five dependent shuffle levels; each term is held to
+            // |y^4| < 64 so that no sum of NT <= 256 terms can overflow, far beyond any equalised symbol
+            int2 c4 = make_int2(0, 0);
             if (owner && valid) {
                 const float2 y2 = cmul(y, y);
-                c4 = cmul(y2, y2);
+                const float2 y4 = cmul(y2, y2);
+                c4.x = __float2int_rn(fminf(fmaxf(y4.x * kPhaseFx, -kPhaseLim), kPhaseLim));
+                c4.y = __float2int_rn(fminf(fmaxf(y4.y * kPhaseFx, -kPhaseLim), kPhaseLim));
             }
-            c4.x = warp_sum(c4.x);
-            c4.y = warp_sum(c4.y);
+            c4.x = __reduce_add_sync(0xffffffffu, c4.x);
+            c4.y = __reduce_add_sync(0xffffffffu, c4.y);
             if (lane == 0) ypart[w] = c4;
             __syncthreads();
-            float2 sum = ypart[0];
+            int2 isum = ypart[0];
 #pragma unroll
-            for (int k = 1; k < NW; ++k) sum = cadd(sum, ypart[k]);
+            for (int k = 1; k < NW; ++k) { isum.x += ypart[k].x; isum.y += ypart[k].y; }
+            const float2 sum = make_float2((float)isum.x * (1.0f / kPhaseFx), (float)isum.y * (1.0f / kPhaseFx));
             const float2 rt = quarter_root_conj(make_float2(-sum.x, -sum.y));
             if (valid) {
                 const float2 d = qam_decide(cmul(y, rt), qm);
