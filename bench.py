@@ -213,10 +213,10 @@ class ClockSampler:
 # unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
 PROFILED_TRAFFIC = {
     # DRAM bytes read + written, one ncu capture of this launch
-    "dd_acq": ("k_lms_tile.cuh", "867bea91c38ec87ab3f9267cb8cc92be49321113", 563200),
-    # captured on the 2^18-symbol frame (4,277,248 B: the equalised symbols read once, under ncu's
+    "dd_acq": ("k_lms_tile.cuh", "fc6c10aaebce0d8bd21f8070b26bf8cceea39364", 562688),
+    # captured on the 2^18-symbol frame (4,283,648 B: the equalised symbols read once, under ncu's
     # cache flush) and scaled by the symbols of the 2^20-symbol launch (traffic in proportion)
-    "bps": ("k_bps.cu", "9dfb588f3d52777eede3d91485f63858569bdbc5", 17108992),
+    "bps": ("k_bps.cu", "5a40944c37ba1dc03b9f6c576ad10c97677a554d", 17134592),
     "wl": ("k_lms_fast.cuh", "fca5f277b4ecd771cc2e0b0acdff6c7ea8cf98cc", 33638912),
 }
 
