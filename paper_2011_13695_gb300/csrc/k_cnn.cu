@@ -192,6 +192,15 @@ __global__ void k_to_channels(const float2* __restrict__ z, int64_t T, int64_t T
     x0[3 * Tp + t + PAD] = __float2bfloat16_rn(b.y);
 }
 
+// BF16 copy of the interior of C gradient planes (the tensor-core data gradient's operand)
+__global__ void k_planes_bf16(const float* __restrict__ src, int64_t T, int64_t Tp, int C,
+                              __nv_bfloat16* __restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)C * T) return;
+    const int64_t c = i / T, t = i - c * T;
+    dst[c * Tp + t + PAD] = __float2bfloat16_rn(src[c * Tp + t + PAD]);
+}
+
 // d3[c][t] = 2 (out - target) / (4 T); loss += sum (out - target)^2 / (4 T)
 __global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__ tgt, int64_t T, int64_t Tp,
                       float* __restrict__ d3, float* __restrict__ loss) {
@@ -213,7 +222,8 @@ __global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__
 
 // W'[ci][co][k] = bf16(W[co][ci][K-1-k]) and the forward weights as BF16-rounded FP32
 __global__ void k_weights(const float* __restrict__ master, int64_t n, float* __restrict__ fwd, const int* offs,
-                          const int* cins, const int* couts, float* __restrict__ bwd, __nv_bfloat16* __restrict__ wtc) {
+                          const int* cins, const int* couts, float* __restrict__ bwd, __nv_bfloat16* __restrict__ wtc,
+                          __nv_bfloat16* __restrict__ wtd) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const __nv_bfloat16 vb = __float2bfloat16_rn(master[i]);
@@ -230,6 +240,8 @@ __global__ void k_weights(const float* __restrict__ master, int64_t n, float* __
             const int C = cins[1];
             const int row = l == 0 ? 48 : cins[l] * KW;
             wtc[wtc_offset(C, l) + (int64_t)co * row + k * cins[l] + ci] = vb;
+            if (l == 1 || l == 2)                     // the data gradient's flipped transpose, (k, co) order
+                wtd[(int64_t)(l - 1) * C * C * KW + (int64_t)ci * (KW * C) + (KW - 1 - k) * C + co] = vb;
         }
     }
 }
@@ -307,14 +319,14 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
     if ((e = conv_t<float, 4, 64, 2>(B.d[3], Tp, T, Wb + B.off[6], nullptr, nullptr, B.act[3], B.d[2], nullptr,
                                      nullptr, s)))
         return e;
+    // the hidden layers' data gradients on the tensor cores, from BF16 copies of the gradient planes
+    k_planes_bf16<<<(unsigned)((64 * T + 255) / 256), 256, 0, s>>>(B.d[2], T, Tp, 64, B.d16[2]);
+    if ((e = cudaGetLastError())) return e;
     if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[2], B.d[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
-    if ((e = conv_t<float, 64, 64, 2>(B.d[2], Tp, T, Wb + B.off[4], nullptr, nullptr, B.act[2], B.d[1], nullptr,
-                                      nullptr, s)))
-        return e;
+    const int64_t lw = (int64_t)64 * 64 * KW;
+    if ((e = conv64_mma_dgrad(B.d16[2], Tp, T, B.wtd + lw, B.act[2], B.d[1], B.d16[1], s))) return e;
     if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[1], B.d[1], Tp, T, B.wpart, G + B.off[2], G + B.off[3], s))) return e;
-    if ((e = conv_t<float, 64, 64, 2>(B.d[1], Tp, T, Wb + B.off[2], nullptr, nullptr, B.act[1], B.d[0], nullptr,
-                                      nullptr, s)))
-        return e;
+    if ((e = conv64_mma_dgrad(B.d16[1], Tp, T, B.wtd, B.act[1], B.d[0], nullptr, s))) return e;
     return wgrad_t<__nv_bfloat16, 4, 64>(B.act[0], B.d[0], Tp, T, B.wpart, G + B.off[0], G + B.off[1], s);
 }
 
@@ -330,6 +342,7 @@ __global__ void k_zero_pads(CnnBufs B, int64_t T) {
         if (c < nch) B.act[buf][(int64_t)c * Tp + col] = __float2bfloat16_rn(0.0f);
         const int ndch = buf == 3 ? 4 : B.C;
         if (c < ndch) B.d[buf][(int64_t)c * Tp + col] = 0.0f;
+        if ((buf == 1 || buf == 2) && c < B.C) B.d16[buf][(int64_t)c * Tp + col] = __float2bfloat16_rn(0.0f);
     }
 }
 
@@ -340,7 +353,7 @@ cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s) {
 
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s) {
     k_weights<<<(unsigned)((B.nparam + 255) / 256), 256, 0, s>>>(B.master, B.nparam, B.wfwd, B.offs_dev, B.cin_dev,
-                                                                 B.cout_dev, B.wbwd, B.wtc);
+                                                                 B.cout_dev, B.wbwd, B.wtc, B.wtd);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,13 @@
 // tile into registers while the current one computes. Eight warps take
 // 32 x 32 output blocks (2 x 4 mma tiles, 36 K-steps of 16). The epilogue adds
 // the bias, applies the ReLU, rounds to BF16 and writes the activation plane.
+//
+// The same product gives the layer's data gradient in the backward pass:
+// din[ci][t] = sum_{k', co} W[co][ci][8 - k'] dout[co][t + k' - 4], i.e. the
+// weights' flipped transpose as A (rows ci, K = (k', co)) and the BF16 copy of
+// the gradient planes as B; that epilogue multiplies by the forward ReLU's
+// derivative (the layer's input activation > 0) and writes FP32 gradient planes
+// (and a BF16 copy for the next layer's data gradient).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -58,10 +65,13 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 constexpr int CH = XR / 8;                                 // 16-byte chunks per channel and tile
 constexpr int NCH = (C * CH + NTHR - 1) / NTHR;            // chunks per thread
 
+template <int EPI>                             // 0: forward (bias, ReLU, BF16); 1: data gradient (mask, FP32)
 __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __restrict__ x, int64_t Tp, int64_t T,
                                                         const __nv_bfloat16* __restrict__ Wm,
                                                         const float* __restrict__ bias,
-                                                        __nv_bfloat16* __restrict__ act_out, int vec) {
+                                                        __nv_bfloat16* __restrict__ act_out, int vec,
+                                                        const __nv_bfloat16* __restrict__ mask,
+                                                        float* __restrict__ gout, __nv_bfloat16* __restrict__ gout16) {
     extern __shared__ float4 smem4[];
     __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem4);      // [C][WS]
     __nv_bfloat16* Xs = Ws + C * WS;                                  // [XR][XS]
@@ -74,11 +84,13 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
         const int co = i / (KTOT / 8), u = i - co * (KTOT / 8);
         *reinterpret_cast<uint4*>(Ws + co * WS + 8 * u) = *reinterpret_cast<const uint4*>(Wm + co * KTOT + 8 * u);
     }
-    float bco[2][2];
+    float bco[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    if constexpr (EPI == 0) {
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+        for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) bco[mi][h] = bias[wm * 32 + mi * 16 + g + 8 * h];
+            for (int h = 0; h < 2; ++h) bco[mi][h] = bias[wm * 32 + mi * 16 + g + 8 * h];
+    }
 
     // ldmatrix row addresses: A rows co0 + (lane % 16), column block (lane / 16) * 8;
     // B^T rows n = (lane / 16) * 8 + lane % 8 of an n-tile pair, column block ((lane / 8) % 2) * 8
@@ -176,6 +188,36 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
 #pragma unroll
                 for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni][0], b[ni][1]);
         }
+        if constexpr (EPI == 1) {
+            // data gradient: times the forward ReLU's derivative, FP32 pairs (and BF16 pairs) straight
+            // from the fragments
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int ci = wm * 32 + mi * 16 + g + 8 * h;
+                        const int64_t t = t0 + wn * 32 + ni * 8 + 2 * tq;
+                        const int64_t o = (int64_t)ci * Tp + t + PAD;
+                        if (vec && t + 1 < T) {
+                            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + o);
+                            const float2 v = make_float2(__bfloat162float(mk.x) > 0.0f ? acc[mi][ni][2 * h] : 0.0f,
+                                                         __bfloat162float(mk.y) > 0.0f ? acc[mi][ni][2 * h + 1] : 0.0f);
+                            *reinterpret_cast<float2*>(gout + o) = v;
+                            if (gout16) *reinterpret_cast<__nv_bfloat162*>(gout16 + o) = __floats2bfloat162_rn(v.x, v.y);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e)
+                                if (t + e < T) {
+                                    const float v = __bfloat162float(mask[o + e]) > 0.0f ? acc[mi][ni][2 * h + e] : 0.0f;
+                                    gout[o + e] = v;
+                                    if (gout16) gout16[o + e] = __float2bfloat16_rn(v);
+                                }
+                        }
+                    }
+            continue;
+        }
         // epilogue: bias, ReLU, BF16 into an output tile Os[co][t] (over Xs once every warp is done),
         // then 8-byte row segments to act_out[co][t0 + PAD + ...]
         __syncthreads();
@@ -211,21 +253,34 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
 
 }  // namespace
 
-cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const __nv_bfloat16* Wm, const float* b,
-                           __nv_bfloat16* act, cudaStream_t s) {
+template <int EPI>
+int conv64_grid(int64_t T) {
     static int resident = 0;
     if (!resident) {
         int dev = 0, nsm = 152, per = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_conv64_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv64_mma, NTHR, SMEM);
+        cudaFuncSetAttribute(k_conv64_mma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv64_mma<EPI>, NTHR, SMEM);
         resident = std::max(1, nsm * per);
     }
     const int64_t ntiles = (T + TT - 1) / TT;
-    const int grid = (int)std::min<int64_t>(ntiles, resident);
+    return (int)std::min<int64_t>(ntiles, resident);
+}
+
+cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const __nv_bfloat16* Wm, const float* b,
+                           __nv_bfloat16* act, cudaStream_t s) {
     // 16-byte staging loads need 16-byte aligned input rows, the 8-byte stores 8-byte aligned output rows
     const int vec = ((uintptr_t)x % 16 == 0) && ((uintptr_t)act % 16 == 0) && (Tp % 8 == 0);
-    k_conv64_mma<<<grid, NTHR, SMEM, s>>>(x, Tp, T, Wm, b, act, vec);
+    k_conv64_mma<0><<<conv64_grid<0>(T), NTHR, SMEM, s>>>(x, Tp, T, Wm, b, act, vec, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t conv64_mma_dgrad(const __nv_bfloat16* dout, int64_t Tp, int64_t T, const __nv_bfloat16* Wd,
+                             const __nv_bfloat16* mask, float* din, __nv_bfloat16* din16, cudaStream_t s) {
+    // 16-byte staging loads; the epilogue's pairs need even element offsets (8- and 4-byte aligned)
+    const int vec = ((uintptr_t)dout % 16 == 0) && ((uintptr_t)din % 16 == 0) && ((uintptr_t)mask % 16 == 0) &&
+                    (!din16 || (uintptr_t)din16 % 16 == 0) && (Tp % 8 == 0);
+    k_conv64_mma<1><<<conv64_grid<1>(T), NTHR, SMEM, s>>>(dout, Tp, T, Wd, nullptr, nullptr, vec, mask, din, din16);
     return cudaGetLastError();
 }

@@ -25,6 +25,10 @@ struct CnnBufs {
     // BF16 weights in (k, ci) order for the tensor cores: layers 1, 2 as [64][9 * 64], layer 3 as
     // [4][9 * 64], then layer 0 as [64][48] (9 * 4 entries, the rest zero)
     __nv_bfloat16* wtc = nullptr;
+    // BF16 weights of the hidden layers' data gradient in (k, co) order: layer l (1, 2) at (l - 1) 64 x 576,
+    // row ci, entry k x 64 + co = W_l[co][ci][8 - k] (the flipped transpose)
+    __nv_bfloat16* wtd = nullptr;
+    __nv_bfloat16* d16[3] = {nullptr, nullptr, nullptr};            // BF16 copies of d[1], d[2] ([C][Tp])
     int* offs_dev = nullptr;        // off[] on the device (int)
     int* cin_dev = nullptr;
     int* cout_dev = nullptr;
@@ -53,3 +57,7 @@ __host__ __device__ inline int64_t wtc_elems(int C) { return wtc_offset(C, 0) + 
 // Wm: the layer's BF16 weights as [co][k * 64 + ci]
 cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const __nv_bfloat16* Wm, const float* b,
                            __nv_bfloat16* act, cudaStream_t s);
+// the data gradient of a 64 -> 64 layer on the tensor cores: din[ci][t] = (sum_{k, co} Wd[ci][k * 64 + co]
+// dout[co][t + k - 4]) x (mask[ci][t] > 0), FP32 into din and (nullable) BF16 into din16; dout BF16 planes
+cudaError_t conv64_mma_dgrad(const __nv_bfloat16* dout, int64_t Tp, int64_t T, const __nv_bfloat16* Wd,
+                             const __nv_bfloat16* mask, float* din, __nv_bfloat16* din16, cudaStream_t s);

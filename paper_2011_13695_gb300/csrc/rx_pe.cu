@@ -35,7 +35,8 @@ int64_t count_params(int C, int64_t* off) {
 void pe_free(rx_pe* p) {
     CnnBufs& B = p->B;
     void* ptrs[] = {B.master, B.m, B.v, B.grad, B.wpart, B.wfwd, B.wbwd, B.wtc, B.offs_dev, B.cin_dev, B.cout_dev, B.out, B.loss,
-                    B.act[0], B.act[1], B.act[2], B.act[3], B.d[0], B.d[1], B.d[2], B.d[3], B.err};
+                    B.act[0], B.act[1], B.act[2], B.act[3], B.d[0], B.d[1], B.d[2], B.d[3], B.err, B.wtd,
+                    B.d16[1], B.d16[2]};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -156,6 +157,7 @@ rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const 
     A(cudaMalloc(&B.wfwd, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.wbwd, sizeof(float) * B.nparam));
     A(cudaMalloc(&B.wtc, sizeof(__nv_bfloat16) * (size_t)wtc_elems(channels)));
+    A(cudaMalloc(&B.wtd, sizeof(__nv_bfloat16) * 2 * (size_t)channels * channels * 9));
     A(cudaMalloc(&B.err, sizeof(unsigned int)));
     A(cudaMalloc(&B.offs_dev, sizeof(int) * 8));
     A(cudaMalloc(&B.cin_dev, sizeof(int) * 4));
@@ -166,6 +168,7 @@ rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const 
         const int ach = l == 0 ? 4 : channels, dch = l == 3 ? 4 : channels;
         A(cudaMalloc(&B.act[l], sizeof(__nv_bfloat16) * ach * Tp));
         A(cudaMalloc(&B.d[l], sizeof(float) * dch * Tp));
+        if (l == 1 || l == 2) A(cudaMalloc(&B.d16[l], sizeof(__nv_bfloat16) * channels * Tp));
     }
     if (e != cudaSuccess) {
         pe_free(p);
