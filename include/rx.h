@@ -275,7 +275,7 @@ rx_status rx_pe_create(int32_t channels, int32_t kernel, int64_t max_len, const 
 /* current FP32 master parameters into h_params (synchronises) */
 rx_status rx_pe_params(rx_pe* p, float* h_params);
 /* inference: d_out = d_z + f(d_z). Runs on the tcgen05 tensor cores with the hidden activations in
- * channel-chunk planes [C/8][T + 8][8]; training (rx_pe_gradients, rx_pe_train_step) keeps its own
+ * channel-chunk planes [C/8][T + 8][8]; training (rx_pe_gradients, rx_pe_train_step(s)) keeps its own
  * forward. */
 rx_status rx_pe_forward(rx_pe* p, const float* d_z, int64_t T, float* d_out, rx_stream_t stream);
 /* the post-equaliser's device error word (RX_ERR_TIMEOUT if a pipelined kernel gave up a wait;
@@ -287,6 +287,16 @@ rx_status rx_pe_gradients(rx_pe* p, const float* d_z, const float* d_target, int
 /* one Adam step on the sequence: forward, backward, update (d_loss nullable) */
 rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, int64_t T, float lr, float* d_loss,
                            rx_stream_t stream);
+/* `steps` Adam steps in one call, step i on the window [offs[i], offs[i] + window) of the sequence pair
+ * which[i]: d_z[k] and d_target[k] are device pointers to complex sequences [2][len[k]] (polarisation 1
+ * at len[k] samples), read in place; host arrays which, offs, lrs (the step's learning rate) of `steps`
+ * entries, d_losses (nullable) a device array of `steps` losses. The same steps as `steps` calls of
+ * rx_pe_train_step on contiguous copies of the windows, bit for bit, without a host round trip or a
+ * copy per step. RX_EINVAL for a window outside its sequence, a pair index outside [0, npairs) or
+ * window > max_len. */
+rx_status rx_pe_train_steps(rx_pe* p, const float* const* d_z, const float* const* d_target, const int64_t* len,
+                            int32_t npairs, int64_t window, int32_t steps, const int32_t* which, const int64_t* offs,
+                            const float* lrs, float* d_losses, rx_stream_t stream);
 void rx_pe_destroy(rx_pe* p);
 
 /*

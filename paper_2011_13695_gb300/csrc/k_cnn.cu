@@ -41,11 +41,12 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
                                              const float* __restrict__ W, const float* __restrict__ bias,
                                              __nv_bfloat16* __restrict__ act_out, const __nv_bfloat16* __restrict__ mask,
                                              float* __restrict__ grad_out, const float2* __restrict__ zres,
-                                             float2* __restrict__ sym_out) {
+                                             float2* __restrict__ sym_out, int64_t zs) {
     constexpr int CO_T = COUT >= 8 ? 8 : COUT;       // output channels per thread
     constexpr int NG = COUT / CO_T;                   // output-channel groups
     constexpr int TPG = CT / NG;                      // threads per group
-    constexpr int TT = TPG * 4;                       // positions per CTA
+    constexpr int PPT = COUT <= 4 ? 1 : 4;            // positions per thread (the 4-channel layer: more CTAs)
+    constexpr int TT = TPG * PPT;                     // positions per CTA
     constexpr int XW = TT + 2 * PAD;
     constexpr int CCH = CIN < (TT >= 1024 ? CC / 2 : CC) ? CIN : (TT >= 1024 ? CC / 2 : CC);   // static smem < 48 KB
     __shared__ float xs[CCH][XW];
@@ -53,17 +54,28 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
     const int tid = threadIdx.x;
     const int g = tid / TPG, lt = tid - g * TPG;
     const int64_t t0 = (int64_t)blockIdx.x * TT;      // first output position (unpadded index)
-    float acc[CO_T][4];
+    float acc[CO_T][PPT];
 #pragma unroll
     for (int c = 0; c < CO_T; ++c)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[c][j] = 0.0f;
+        for (int j = 0; j < PPT; ++j) acc[c][j] = 0.0f;
     for (int c0 = 0; c0 < CIN; c0 += CCH) {
-        // stage x[c0 .. c0+CCH)[t0 - 4 .. t0 + TT + 4) (padded index t0 .. t0 + XW)
-        for (int i = tid; i < CCH * XW; i += CT) {
-            const int ci = i / XW, u = i - ci * XW;
-            const int64_t tp = t0 + u;
-            xs[ci][u] = (tp < Tp) ? ld(x + (int64_t)(c0 + ci) * Tp + tp) : 0.0f;
+        // stage x[c0 .. c0+CCH)[t0 - 4 .. t0 + TT + 4) (padded index t0 .. t0 + XW), eight loads per thread
+        // in flight at a time (the latency of this part's L2 is long)
+        for (int i0 = 0; i0 < CCH * XW; i0 += 8 * CT) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + e * CT + tid;
+                const int ci = i / XW, u = i - ci * XW;
+                const int64_t tp = t0 + u;
+                v[e] = (i < CCH * XW && tp < Tp) ? ld(x + (int64_t)(c0 + ci) * Tp + tp) : 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + e * CT + tid;
+                if (i < CCH * XW) xs[i / XW][i - (i / XW) * XW] = v[e];
+            }
         }
         for (int i = tid; i < CCH * KW * COUT; i += CT) {
             const int co = i / (CCH * KW), r = i - co * CCH * KW, ci = r / KW, k = r - ci * KW;
@@ -78,8 +90,8 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
 #pragma unroll
                 for (int c = 0; c < CO_T; ++c) w[c] = ws[ci][k][g * CO_T + c];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float xv = xs[ci][lt + j * (TT / 4) + k];
+                for (int j = 0; j < PPT; ++j) {
+                    const float xv = xs[ci][lt + j * (TT / PPT) + k];
 #pragma unroll
                     for (int c = 0; c < CO_T; ++c) acc[c][j] = fmaf(w[c], xv, acc[c][j]);
                 }
@@ -88,8 +100,8 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
         __syncthreads();
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int64_t t = t0 + lt + j * (TT / 4);     // unpadded output position
+    for (int j = 0; j < PPT; ++j) {
+        const int64_t t = t0 + lt + j * (TT / PPT);   // unpadded output position
         if (t >= T) continue;
 #pragma unroll
         for (int c = 0; c < CO_T; ++c) {
@@ -104,7 +116,7 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
         }
         if (EPI == 1) {
             // channels (I_x, Q_x, I_y, Q_y) -> symbols of pol 0 and 1
-            const float2 z0 = zres[t], z1 = zres[T + t];
+            const float2 z0 = zres[t], z1 = zres[zs + t];     // the residual's polarisations zs apart
             sym_out[t] = make_float2(z0.x + acc[0][j] + bias[0], z0.y + acc[1][j] + bias[1]);
             sym_out[T + t] = make_float2(z1.x + acc[2][j] + bias[2], z1.y + acc[3][j] + bias[3]);
         }
@@ -136,15 +148,37 @@ __global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, co
     for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
         const int64_t t0 = ch * TC;                   // unpadded
         __syncthreads();                              // the previous chunk's reads are done
-        for (int i = tid; i < CO_TILE * TC; i += CT) {
-            const int c = i / TC, u = i - c * TC;
-            const int64_t t = t0 + u;
-            dys[c][u] = (t < T) ? dy[(int64_t)(co0 + c) * Tp + t + PAD] : 0.0f;
+        // staging with eight loads per thread in flight at a time
+        for (int i0 = 0; i0 < CO_TILE * TC; i0 += 8 * CT) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + e * CT + tid;
+                const int c = i / TC, u = i - c * TC;
+                const int64_t t = t0 + u;
+                v[e] = (i < CO_TILE * TC && t < T) ? dy[(int64_t)(co0 + c) * Tp + t + PAD] : 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + e * CT + tid;
+                if (i < CO_TILE * TC) dys[i / TC][i - (i / TC) * TC] = v[e];
+            }
         }
-        for (int i = tid; i < CI_TILE * (TC + 2 * PAD); i += CT) {
-            const int c = i / (TC + 2 * PAD), u = i - c * (TC + 2 * PAD);
-            const int64_t tp = t0 + u;                // padded index of position t0 + u - 4
-            xs[c][u] = (tp < Tp) ? ld(x + (int64_t)(ci0 + c) * Tp + tp) : 0.0f;
+        constexpr int XWC = TC + 2 * PAD;
+        for (int i0 = 0; i0 < CI_TILE * XWC; i0 += 8 * CT) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + e * CT + tid;
+                const int c = i / XWC, u = i - c * XWC;
+                const int64_t tp = t0 + u;            // padded index of position t0 + u - 4
+                v[e] = (i < CI_TILE * XWC && tp < Tp) ? ld(x + (int64_t)(ci0 + c) * Tp + tp) : 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + e * CT + tid;
+                if (i < CI_TILE * XWC) xs[i / XWC][i - (i / XWC) * XWC] = v[e];
+            }
         }
         __syncthreads();
         if (mine) {
@@ -182,10 +216,11 @@ __global__ void k_wgrad_sum(const float* __restrict__ part, int64_t nw, int64_t 
     else db[i - nw] = s;
 }
 
-__global__ void k_to_channels(const float2* __restrict__ z, int64_t T, int64_t Tp, __nv_bfloat16* __restrict__ x0) {
+__global__ void k_to_channels(const float2* __restrict__ z, int64_t zs, int64_t T, int64_t Tp,
+                              __nv_bfloat16* __restrict__ x0) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
-    const float2 a = z[t], b = z[T + t];
+    const float2 a = z[t], b = z[zs + t];
     x0[0 * Tp + t + PAD] = __float2bfloat16_rn(a.x);
     x0[1 * Tp + t + PAD] = __float2bfloat16_rn(a.y);
     x0[2 * Tp + t + PAD] = __float2bfloat16_rn(b.x);
@@ -202,13 +237,13 @@ __global__ void k_planes_bf16(const float* __restrict__ src, int64_t T, int64_t 
 }
 
 // d3[c][t] = 2 (out - target) / (4 T); loss += sum (out - target)^2 / (4 T)
-__global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__ tgt, int64_t T, int64_t Tp,
+__global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__ tgt, int64_t ts, int64_t T, int64_t Tp,
                       float* __restrict__ d3, float* __restrict__ loss) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.0f;
     if (t < T) {
         const float inv = 1.0f / (4.0f * (float)T);
-        const float2 a = out[t], b = out[T + t], ta = tgt[t], tb = tgt[T + t];
+        const float2 a = out[t], b = out[T + t], ta = tgt[t], tb = tgt[ts + t];
         const float e[4] = {a.x - ta.x, a.y - ta.y, b.x - tb.x, b.y - tb.y};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -260,10 +295,10 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 
 template <typename Tin, int CIN, int COUT, int EPI>
 cudaError_t conv_t(const Tin* x, int64_t Tp, int64_t T, const float* W, const float* b, __nv_bfloat16* act,
-                   const __nv_bfloat16* mask, float* grad, const float2* zres, float2* sym, cudaStream_t s) {
+                   const __nv_bfloat16* mask, float* grad, const float2* zres, float2* sym, cudaStream_t s, int64_t zs = 0) {
     constexpr int CO_T = COUT >= 8 ? 8 : COUT;
-    constexpr int TT = (CT / (COUT / CO_T)) * 4;
-    k_conv<Tin, CIN, COUT, EPI><<<(unsigned)((T + TT - 1) / TT), CT, 0, s>>>(x, Tp, T, W, b, act, mask, grad, zres, sym);
+    constexpr int TT = (CT / (COUT / CO_T)) * (COUT <= 4 ? 1 : 4);   // k_conv's positions per CTA
+    k_conv<Tin, CIN, COUT, EPI><<<(unsigned)((T + TT - 1) / TT), CT, 0, s>>>(x, Tp, T, W, b, act, mask, grad, zres, sym, zs);
     return cudaGetLastError();
 }
 
@@ -283,14 +318,25 @@ cudaError_t wgrad_t(const Tin* x, const float* dy, int64_t Tp, int64_t T, float*
     return cudaGetLastError();
 }
 
+// the hidden layers' weight gradients: partial rows on the tensor cores, then the rows in order
+cudaError_t wgrad64_t(const __nv_bfloat16* x, const __nv_bfloat16* dy16, const float* dy, int64_t Tp, int64_t T,
+                      float* part, float* dW, float* db, cudaStream_t s) {
+    int nrow = 0;
+    cudaError_t e = conv64_mma_wgrad_parts(x, dy16, dy, Tp, T, part, CNN_WG_SPLIT, &nrow, s);
+    if (e) return e;
+    const int64_t nw = (int64_t)64 * 64 * KW, nb = 64;
+    k_wgrad_sum<<<(unsigned)((nw + nb + 255) / 256), 256, 0, s>>>(part, nw, nb, nrow, dW, db);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // forward of the 4 layers; act[0] holds the input channels, act[1..3] the hidden activations
-cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s) {
+cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T, float2* out, cudaStream_t s) {
     const int64_t Tp = T + 2 * PAD;
     const int C = B.C;
     if (C != 64) return cudaErrorInvalidValue;
-    k_to_channels<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(z, T, Tp, B.act[0]);
+    k_to_channels<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(z, zs, T, Tp, B.act[0]);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
     const float* W = B.wfwd;
@@ -302,15 +348,15 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* ou
     e = conv64_mma_fwd(B.act[2], Tp, T, B.wtc + wtc_offset(C, 2), W + B.off[5], B.act[3], s);
     if (e) return e;
     return conv_t<__nv_bfloat16, 64, 4, 1>(B.act[3], Tp, T, W + B.off[6], W + B.off[7], nullptr, nullptr, nullptr, z,
-                                           out, s);
+                                           out, s, zs);
 }
 
 // loss gradient and all parameter gradients (every entry of B.grad written) for the last forward
-cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t T, float* loss,
+cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t ts, int64_t T, float* loss,
                          cudaStream_t s) {
     const int64_t Tp = T + 2 * PAD;
     cudaError_t e = cudaSuccess;
-    k_mse<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(out, tgt, T, Tp, B.d[3], loss);
+    k_mse<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(out, tgt, ts, T, Tp, B.d[3], loss);
     if ((e = cudaGetLastError())) return e;
     float* G = B.grad;
     const float* Wb = B.wbwd;
@@ -322,10 +368,10 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
     // the hidden layers' data gradients on the tensor cores, from BF16 copies of the gradient planes
     k_planes_bf16<<<(unsigned)((64 * T + 255) / 256), 256, 0, s>>>(B.d[2], T, Tp, 64, B.d16[2]);
     if ((e = cudaGetLastError())) return e;
-    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[2], B.d[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
+    if ((e = wgrad64_t(B.act[2], B.d16[2], B.d[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
     const int64_t lw = (int64_t)64 * 64 * KW;
     if ((e = conv64_mma_dgrad(B.d16[2], Tp, T, B.wtd + lw, B.act[2], B.d[1], B.d16[1], s))) return e;
-    if ((e = wgrad_t<__nv_bfloat16, 64, 64>(B.act[1], B.d[1], Tp, T, B.wpart, G + B.off[2], G + B.off[3], s))) return e;
+    if ((e = wgrad64_t(B.act[1], B.d16[1], B.d[1], Tp, T, B.wpart, G + B.off[2], G + B.off[3], s))) return e;
     if ((e = conv64_mma_dgrad(B.d16[1], Tp, T, B.wtd, B.act[1], B.d[0], nullptr, s))) return e;
     return wgrad_t<__nv_bfloat16, 4, 64>(B.act[0], B.d[0], Tp, T, B.wpart, G + B.off[0], G + B.off[1], s);
 }

@@ -54,6 +54,12 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                  : "r"(addr));
 }
 
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
@@ -251,6 +257,145 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
     }
 }
 
+
+// Weight gradients of a 64 -> 64 layer on the tensor cores. For tap k, dW[co][ci][k] = sum_t dY[co][t]
+// x[ci][t + k - 4] is the product D_k = A B_k with A[co][t] = dY (the BF16 copy of the gradient planes,
+// M = 64, K = positions) and B_k[t][ci] = x[ci][t + k - 4] (the layer's input activation, N = 64). A chunk
+// of WT positions stages A as rows [co][t] (ldmatrix) and x transposed to [position][channel] like the
+// forward, so that tap k's B fragment is an ldmatrix.trans of the rows shifted by k. CTA (r, j) takes taps
+// 3 j .. 3 j + 2 and the chunks r, r + gridDim.x, ...; eight warps hold 32 x 16 output blocks of the three
+// taps in FP32 fragments and write them to partial row r ([co][ci][k], then the bias gradient, summed from
+// the FP32 planes by tap group 0); k_wgrad_sum adds the rows in a fixed order.
+constexpr int WT = 128;                                    // positions per chunk
+constexpr int WXR = WT + 2 * PAD;                          // staged input positions per chunk
+constexpr int WAS = WT + 8;                                // A row stride (bf16)
+constexpr size_t WSMEM = sizeof(__nv_bfloat16) * ((size_t)C * WAS + (size_t)WXR * XS);
+
+__global__ void __launch_bounds__(NTHR) k_wgrad64_mma(const __nv_bfloat16* __restrict__ x,
+                                                      const __nv_bfloat16* __restrict__ dy16,
+                                                      const float* __restrict__ dy, int64_t Tp, int64_t T,
+                                                      float* __restrict__ part, int vec) {
+    extern __shared__ float4 smem4[];
+    __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem4);      // [C][WAS]: dY of positions t0 + j
+    __nv_bfloat16* Xs = As + C * WAS;                                 // [WXR][XS]: x of padded index t0 + r
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 2, wn = warp & 3;                          // 2 x 4 warps of 32 co x 16 ci
+    const int g = lane >> 2, tq = lane & 3;
+    const int kt0 = blockIdx.y * 3;                                   // taps of this CTA
+    constexpr int64_t ROW = (int64_t)C * C * KW + C;
+    float* prow = part + (int64_t)blockIdx.x * ROW;
+
+    // A rows co0 + (lane % 16), column block (lane / 16) * 8 (as the forward's weights)
+    const uint32_t a_base = smem_addr(As + (wm * 32 + (lane & 15)) * WAS + (lane >> 4) * 8);
+    // B (x4.trans): matrix i = lane / 8 covers positions (i & 1) * 8 + lane % 8 of the k-step and channels
+    // (i >> 1) * 8 of the warp's 16
+    const uint32_t b_base = smem_addr(Xs + (((lane >> 3) & 1) * 8 + (lane & 7)) * XS + wn * 16 + (lane >> 4) * 8);
+
+    float acc[3][2][2][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[k][mi][ni][e] = 0.0f;
+    float dbs = 0.0f;                                                 // bias: thread co = tid / 4, quarter tid % 4
+
+    const int64_t nchunk = (T + WT - 1) / WT;
+    for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        const int64_t t0 = ch * WT;                                   // first position; padded window t0 ..
+        __syncthreads();                                              // the previous chunk's reads are done
+        // A: dY of positions t0 .. t0 + WT (padded t0 + 4 ..), loaded as aligned 16-byte chunks of the padded
+        // row from t0 and stored as two 8-byte halves at their column (out of range and past Tp: zero)
+#pragma unroll
+        for (int i = tid; i < C * (WT / 8 + 1); i += NTHR) {
+            const int co = i / (WT / 8 + 1), u = i - co * (WT / 8 + 1);
+            const int64_t tp = t0 + 8 * u;                            // padded index of the chunk
+            const __nv_bfloat16* src = dy16 + (int64_t)co * Tp + tp;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (vec && tp + 7 < Tp) {
+                v = __ldg(reinterpret_cast<const uint4*>(src));
+            } else {
+                __nv_bfloat16 tmp[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? src[e] : __float2bfloat16_rn(0.0f);
+                v = *reinterpret_cast<const uint4*>(tmp);
+            }
+            const int c0 = 8 * u - PAD;                               // column of the chunk's first element
+            if (c0 >= 0) *reinterpret_cast<uint2*>(As + co * WAS + c0) = make_uint2(v.x, v.y);
+            if (c0 + 4 < WT) *reinterpret_cast<uint2*>(As + co * WAS + c0 + 4) = make_uint2(v.z, v.w);
+        }
+        // x transposed: Xs[r][ci] = x[ci][padded t0 + r], r < WXR
+#pragma unroll
+        for (int i = tid; i < C * (WXR / 8); i += NTHR) {
+            const int u = i / C, ci = i - u * C;
+            const int64_t tp = t0 + 8 * u;
+            const __nv_bfloat16* src = x + (int64_t)ci * Tp + tp;
+            __nv_bfloat16 tmp[8];
+            if (vec && tp + 7 < Tp) {
+                *reinterpret_cast<uint4*>(tmp) = __ldg(reinterpret_cast<const uint4*>(src));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? src[e] : __float2bfloat16_rn(0.0f);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) Xs[(8 * u + e) * XS + ci] = tmp[e];
+        }
+        // the bias gradient from the FP32 planes: four threads per channel, 32 positions each, all loads in
+        // flight together
+        if (blockIdx.y == 0) {
+            const int co = tid >> 2, qq = tid & 3;
+            float v[WT / 4];
+#pragma unroll
+            for (int j = 0; j < WT / 4; ++j) {
+                const int64_t t = t0 + qq * (WT / 4) + j;
+                v[j] = t < T ? dy[(int64_t)co * Tp + t + PAD] : 0.0f;
+            }
+            float sb = 0.0f;
+#pragma unroll
+            for (int j = 0; j < WT / 4; ++j) sb += v[j];
+            sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+            sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+            dbs += sb;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int ks = 0; ks < WT / 16; ++ks) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldsm_x4(a_base + (uint32_t)((mi * 16 * WAS + ks * 16) * 2), a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                // tap kt0 + k: positions t0 + 16 ks + (0..15) read x at padded t0 + 16 ks + kt0 + k + (0..15)
+                uint32_t b[4];
+                ldsm_x4_t(b_base + (uint32_t)(((ks * 16 + kt0 + k) * XS) * 2), b[0], b[1], b[2], b[3]);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    mma_bf16(acc[k][mi][0], a[mi], b[0], b[1]);
+                    mma_bf16(acc[k][mi][1], a[mi], b[2], b[3]);
+                }
+            }
+        }
+    }
+    // the CTA's partial row: D_k fragment (row co, column ci) -> dW[co][ci][k]
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int co = wm * 32 + mi * 16 + g + 8 * h, ci = wn * 16 + ni * 8 + 2 * tq + e;
+                        prow[((int64_t)co * C + ci) * KW + kt0 + k] = acc[k][mi][ni][2 * h + e];
+                    }
+    if (blockIdx.y == 0 && (tid & 3) == 0) prow[(int64_t)C * C * KW + (tid >> 2)] = dbs;
+}
+
 }  // namespace
 
 template <int EPI>
@@ -282,5 +427,20 @@ cudaError_t conv64_mma_dgrad(const __nv_bfloat16* dout, int64_t Tp, int64_t T, c
     const int vec = ((uintptr_t)dout % 16 == 0) && ((uintptr_t)din % 16 == 0) && ((uintptr_t)mask % 16 == 0) &&
                     (!din16 || (uintptr_t)din16 % 16 == 0) && (Tp % 8 == 0);
     k_conv64_mma<1><<<conv64_grid<1>(T), NTHR, SMEM, s>>>(dout, Tp, T, Wd, nullptr, nullptr, vec, mask, din, din16);
+    return cudaGetLastError();
+}
+
+cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* dy16, const float* dy, int64_t Tp,
+                                   int64_t T, float* part, int max_rows, int* nrow, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_wgrad64_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WSMEM);
+        attr = true;
+    }
+    const int64_t nchunk = (T + WT - 1) / WT;
+    const int rows = (int)std::min<int64_t>(std::max<int64_t>(nchunk, 1), max_rows);
+    const int vec = ((uintptr_t)x % 16 == 0) && ((uintptr_t)dy16 % 16 == 0) && (Tp % 8 == 0);
+    k_wgrad64_mma<<<dim3((unsigned)rows, KW / 3), NTHR, WSMEM, s>>>(x, dy16, dy, Tp, T, part, vec);
+    *nrow = rows;
     return cudaGetLastError();
 }

@@ -39,8 +39,9 @@ struct CnnBufs {
     unsigned int* err = nullptr;    // [1] error word (RX_ERR_* bits) of the tensor-core kernels
 };
 
-cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s);
-cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t T, float* loss,
+// z, tgt: the two polarisations zs / ts complex samples apart (T for contiguous sequences)
+cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T, float2* out, cudaStream_t s);
+cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t ts, int64_t T, float* loss,
                          cudaStream_t s);
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);
 cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s);
@@ -59,5 +60,10 @@ cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const 
                            __nv_bfloat16* act, cudaStream_t s);
 // the data gradient of a 64 -> 64 layer on the tensor cores: din[ci][t] = (sum_{k, co} Wd[ci][k * 64 + co]
 // dout[co][t + k - 4]) x (mask[ci][t] > 0), FP32 into din and (nullable) BF16 into din16; dout BF16 planes
+// the partial rows of a 64 -> 64 layer's weight and bias gradients on the tensor cores (at most max_rows
+// rows of C * C * 9 + C floats in part; *nrow = rows written); x: the layer's input activation planes,
+// dy16 / dy: the BF16 copy and the FP32 gradient planes
+cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* dy16, const float* dy, int64_t Tp,
+                                   int64_t T, float* part, int max_rows, int* nrow, cudaStream_t s);
 cudaError_t conv64_mma_dgrad(const __nv_bfloat16* dout, int64_t Tp, int64_t T, const __nv_bfloat16* Wd,
                              const __nv_bfloat16* mask, float* din, __nv_bfloat16* din16, cudaStream_t s);

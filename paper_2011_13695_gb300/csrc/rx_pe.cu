@@ -230,9 +230,9 @@ rx_status rx_pe_gradients(rx_pe* p, const float* d_z, const float* d_target, int
     p->last = s;
     CnnBufs& B = p->B;
     if (cnn_zero_pads(B, T, s) != cudaSuccess) return RX_ECUDA;
-    if (cnn_forward(B, (const float2*)d_z, T, B.out, s) != cudaSuccess) return RX_ECUDA;
+    if (cnn_forward(B, (const float2*)d_z, T, T, B.out, s) != cudaSuccess) return RX_ECUDA;
     if (cudaMemsetAsync(B.loss, 0, sizeof(float), s) != cudaSuccess) return RX_ECUDA;
-    if (cnn_backward(B, B.out, (const float2*)d_target, T, B.loss, s) != cudaSuccess) return RX_ECUDA;
+    if (cnn_backward(B, B.out, (const float2*)d_target, T, T, B.loss, s) != cudaSuccess) return RX_ECUDA;
     if (d_grads && cudaMemcpyAsync(d_grads, B.grad, sizeof(float) * B.nparam, cudaMemcpyDeviceToDevice, s))
         return RX_ECUDA;
     if (d_loss && cudaMemcpyAsync(d_loss, B.loss, sizeof(float), cudaMemcpyDeviceToDevice, s)) return RX_ECUDA;
@@ -247,6 +247,37 @@ rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, in
     p->step += 1;
     if (cnn_adam(p->B, lr, p->step, s) != cudaSuccess) return RX_ECUDA;
     if (cnn_prepare_weights(p->B, s) != cudaSuccess) return RX_ECUDA;
+    return RX_OK;
+}
+
+rx_status rx_pe_train_steps(rx_pe* p, const float* const* d_z, const float* const* d_target, const int64_t* len,
+                            int32_t npairs, int64_t window, int32_t steps, const int32_t* which, const int64_t* offs,
+                            const float* lrs, float* d_losses, rx_stream_t stream) {
+    if (!p || !d_z || !d_target || !len || npairs < 1 || window < 1 || window > p->B.Tmax || steps < 0 ||
+        (steps > 0 && (!which || !offs || !lrs)))
+        return RX_EINVAL;
+    for (int32_t i = 0; i < steps; ++i) {
+        const int32_t k = which[i];
+        if (k < 0 || k >= npairs || !d_z[k] || !d_target[k] || offs[i] < 0 || offs[i] + window > len[k])
+            return RX_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last = s;
+    CnnBufs& B = p->B;
+    if (cnn_zero_pads(B, window, s) != cudaSuccess) return RX_ECUDA;   // the pad columns of this length
+    for (int32_t i = 0; i < steps; ++i) {
+        const int32_t k = which[i];
+        const float2* z = reinterpret_cast<const float2*>(d_z[k]) + offs[i];
+        const float2* t = reinterpret_cast<const float2*>(d_target[k]) + offs[i];
+        if (cnn_forward(B, z, len[k], window, B.out, s) != cudaSuccess) return RX_ECUDA;
+        if (cudaMemsetAsync(B.loss, 0, sizeof(float), s) != cudaSuccess) return RX_ECUDA;
+        if (cnn_backward(B, B.out, t, len[k], window, B.loss, s) != cudaSuccess) return RX_ECUDA;
+        if (d_losses && cudaMemcpyAsync(d_losses + i, B.loss, sizeof(float), cudaMemcpyDeviceToDevice, s))
+            return RX_ECUDA;
+        p->step += 1;
+        if (cnn_adam(B, lrs[i], p->step, s) != cudaSuccess) return RX_ECUDA;
+        if (cnn_prepare_weights(B, s) != cudaSuccess) return RX_ECUDA;
+    }
     return RX_OK;
 }
 

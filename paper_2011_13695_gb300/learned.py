@@ -112,11 +112,19 @@ class PostEqualiser:
         offs = rng.integers(lo, hi - window + 1, size=steps)
         losses = torch.zeros(steps, dtype=torch.float32, device=zs_all[0].device)
         ratio = 1.0 if lr_final is None else (lr_final / lr) ** (1.0 / max(steps - 1, 1))
-        for i in range(steps):
-            k, o = int(which[i]), int(offs[i])
-            zs = zs_all[k][:, o:o + window].contiguous()
-            ts = ts_all[k][:, o:o + window].contiguous()
-            self.train_step(zs, ts, lr * ratio ** i, losses.data_ptr() + 4 * i)
+        lrs = [lr * ratio ** i for i in range(steps)]
+        # one library call for the whole schedule: the windows are read in place (each pair contiguous
+        # [2][n], polarisation 1 n samples on)
+        zc = [a.contiguous() for a in zs_all]
+        tc = [a.contiguous() for a in ts_all]
+        for a in zc + tc:
+            if a.dtype != torch.complex64 or a.dim() != 2 or a.shape[0] != 2:
+                raise ValueError("z and target must be complex64 [2, n] tensors")
+        if any(a.shape[1] != b.shape[1] for a, b in zip(zc, tc)):
+            raise ValueError("each target must be as long as its z")
+        rx.rx_pe_train_steps(self.h, [a.data_ptr() for a in zc], [a.data_ptr() for a in tc],
+                             [a.shape[1] for a in zc], window, which, offs, lrs, losses.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
         return losses
 
 

@@ -28,7 +28,7 @@ EXPORTS = ("rx_create", "rx_process", "rx_process_host", "rx_stats", "rx_buffer_
            "rx_batch_create", "rx_batch_config", "rx_batch_handle", "rx_batch_process", "rx_batch_stats",
            "rx_batch_launch_count", "rx_batch_destroy", "rx_carrier_recovery_static",
            "rx_decide", "rx_pe_param_count", "rx_pe_create", "rx_pe_params", "rx_pe_forward",
-           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_destroy", "rx_dd_lms_wl",
+           "rx_pe_error_word", "rx_pe_gradients", "rx_pe_train_step", "rx_pe_train_steps", "rx_pe_destroy", "rx_dd_lms_wl",
            "rx_kk_create", "rx_kk_process", "rx_kk_destroy", "rx_ingest_run", "rx_pam_create", "rx_pam_process",
            "rx_pam_get", "rx_pam_destroy", "rx_fp32_fma_rate", "rx_pe_targets", "rx_kk_equalise")
 RX_PAM_CLOCK, RX_PAM_PHASE, RX_PAM_WINDING, RX_PAM_OFFSETS, RX_PAM_STATS = range(5)
@@ -119,6 +119,7 @@ def lib() -> C.CDLL:
             "rx_pe_error_word": (i32, [vp, vp]),
             "rx_pe_gradients": (i32, [vp, vp, vp, i64, vp, vp, vp]),
             "rx_pe_train_step": (i32, [vp, vp, vp, i64, C.c_float, vp, vp]),
+            "rx_pe_train_steps": (i32, [vp, vp, vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]),
             "rx_pe_destroy": (None, [vp]),
             "rx_dd_lms_wl": (i32, [vp, i64, i32, vp, i64, i32, i32, i32, i32, C.c_float, C.c_float, vp, vp, i32,
                                    vp]),
@@ -330,6 +331,23 @@ def rx_pe_gradients(p: int, d_z: int, d_target: int, T: int, d_grads: int | None
 def rx_pe_train_step(p: int, d_z: int, d_target: int, T: int, lr: float, d_loss: int | None,
                      stream: int | None) -> None:
     _check(lib().rx_pe_train_step(p, d_z, d_target, T, lr, d_loss or None, stream or None), "rx_pe_train_step")
+
+
+def rx_pe_train_steps(p: int, d_z: list[int], d_target: list[int], lens: list[int], window: int, which, offs, lrs,
+                      d_losses: int | None, stream: int | None) -> None:
+    """len(which) Adam steps in one call; see include/rx.h."""
+    n = len(d_z)
+    steps = len(which)
+    if len(d_target) != n or len(lens) != n or len(offs) != steps or len(lrs) != steps:
+        raise ValueError("mismatched argument lengths")
+    zp = (C.c_void_p * n)(*d_z)
+    tp = (C.c_void_p * n)(*d_target)
+    ln = (C.c_int64 * n)(*[int(v) for v in lens])
+    wh = (C.c_int32 * max(steps, 1))(*[int(v) for v in which])
+    of = (C.c_int64 * max(steps, 1))(*[int(v) for v in offs])
+    lr = (C.c_float * max(steps, 1))(*[float(v) for v in lrs])
+    _check(lib().rx_pe_train_steps(p, zp, tp, ln, n, window, steps, wh, of, lr, d_losses or None, stream or None),
+           "rx_pe_train_steps")
 
 
 def rx_pe_destroy(p: int) -> None:

@@ -189,6 +189,45 @@ def test_training_reduces_loss():
     assert last < 0.1 * first and l_end < 0.1 * l0, (first, last, l0, l_end)
 
 
+def test_train_steps_equal_single_steps():
+    """rx_pe_train_steps (the whole schedule in one call, windows read in place from two sequences of
+    different lengths) leaves the same parameters, bit for bit, as one rx_pe_train_step per step on
+    contiguous copies of the same windows with the same rates (the update's kernels are deterministic),
+    and the same losses to rounding."""
+    import torch
+    from paper_2011_13695_gb300 import rx
+    from paper_2011_13695_gb300.learned import PostEqualiser
+    n = [5000, 3100]
+    zs = [to_dev(qam_like(v, seed=31 + i)) for i, v in enumerate(n)]
+    ts = [to_dev(qam_like(v, seed=41 + i)) for i, v in enumerate(n)]
+    params = cnn.flatten(cnn.init_params(C, K, seed=5)).astype(np.float32)
+    rng = np.random.default_rng(9)
+    W, steps = 1024, 12
+    which = rng.integers(0, 2, size=steps)
+    offs = [int(rng.integers(0, n[k] - W + 1)) for k in which]
+    lrs = [1e-3 * 0.9 ** i for i in range(steps)]
+    a = PostEqualiser(4096, params)
+    la = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    rx.rx_pe_train_steps(a.h, [v.data_ptr() for v in zs], [v.data_ptr() for v in ts], n, W, which, offs, lrs,
+                         la.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    b = PostEqualiser(4096, params)
+    lb = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    for i, k in enumerate(which):
+        zw = zs[k][:, offs[i]:offs[i] + W].contiguous()
+        tw = ts[k][:, offs[i]:offs[i] + W].contiguous()
+        b.train_step(zw, tw, lrs[i], lb.data_ptr() + 4 * i)
+    pa, pb = a.params(), b.params()
+    assert a.error_word() == 0 and b.error_word() == 0
+    with pytest.raises(rx.RxError):                  # a window past the end of its sequence
+        rx.rx_pe_train_steps(a.h, [zs[0].data_ptr()], [ts[0].data_ptr()], [n[0]], W, [0], [n[0] - W + 1], [1e-3],
+                             None, None)
+    a.close()
+    b.close()
+    assert np.array_equal(pa, pb), float(np.max(np.abs(pa - pb)))
+    # the reported loss is summed with float atomics across warps (it feeds no update): equal to rounding
+    assert torch.allclose(la, lb, rtol=1e-5, atol=0.0), (la, lb)
+
+
 def test_inference_forward_equals_training_forward():
     """The inference forward (tensor cores, channel-chunk planes) and the training forward (channel-major
     activations) compute the same network: after some training, the loss of the inference output equals
