@@ -319,10 +319,10 @@ cudaError_t wgrad_t(const Tin* x, const float* dy, int64_t Tp, int64_t T, float*
 }
 
 // the hidden layers' weight gradients: partial rows on the tensor cores, then the rows in order
-cudaError_t wgrad64_t(const __nv_bfloat16* x, const __nv_bfloat16* dy16, const float* dy, int64_t Tp, int64_t T,
-                      float* part, float* dW, float* db, cudaStream_t s) {
+cudaError_t wgrad64_t(const __nv_bfloat16* x, const __nv_bfloat16* dy16, int64_t Tp, int64_t T, float* part, float* dW,
+                      float* db, cudaStream_t s) {
     int nrow = 0;
-    cudaError_t e = conv64_mma_wgrad_parts(x, dy16, dy, Tp, T, part, CNN_WG_SPLIT, &nrow, s);
+    cudaError_t e = conv64_mma_wgrad_parts(x, dy16, Tp, T, part, CNN_WG_SPLIT, &nrow, s);
     if (e) return e;
     const int64_t nw = (int64_t)64 * 64 * KW, nb = 64;
     k_wgrad_sum<<<(unsigned)((nw + nb + 255) / 256), 256, 0, s>>>(part, nw, nb, nrow, dW, db);
@@ -368,10 +368,10 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
     // the hidden layers' data gradients on the tensor cores, from BF16 copies of the gradient planes
     k_planes_bf16<<<(unsigned)((64 * T + 255) / 256), 256, 0, s>>>(B.d[2], T, Tp, 64, B.d16[2]);
     if ((e = cudaGetLastError())) return e;
-    if ((e = wgrad64_t(B.act[2], B.d16[2], B.d[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
+    if ((e = wgrad64_t(B.act[2], B.d16[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
     const int64_t lw = (int64_t)64 * 64 * KW;
     if ((e = conv64_mma_dgrad(B.d16[2], Tp, T, B.wtd + lw, B.act[2], B.d[1], B.d16[1], s))) return e;
-    if ((e = wgrad64_t(B.act[1], B.d16[1], B.d[1], Tp, T, B.wpart, G + B.off[2], G + B.off[3], s))) return e;
+    if ((e = wgrad64_t(B.act[1], B.d16[1], Tp, T, B.wpart, G + B.off[2], G + B.off[3], s))) return e;
     if ((e = conv64_mma_dgrad(B.d16[1], Tp, T, B.wtd, B.act[1], B.d[0], nullptr, s))) return e;
     return wgrad_t<__nv_bfloat16, 4, 64>(B.act[0], B.d[0], Tp, T, B.wpart, G + B.off[0], G + B.off[1], s);
 }

@@ -264,17 +264,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv64_mma(const __nv_bfloat16* __r
 // of WT positions stages A as rows [co][t] (ldmatrix) and x transposed to [position][channel] like the
 // forward, so that tap k's B fragment is an ldmatrix.trans of the rows shifted by k. CTA (r, j) takes taps
 // 3 j .. 3 j + 2 and the chunks r, r + gridDim.x, ...; eight warps hold 32 x 16 output blocks of the three
-// taps in FP32 fragments and write them to partial row r ([co][ci][k], then the bias gradient, summed from
-// the FP32 planes by tap group 0); k_wgrad_sum adds the rows in a fixed order.
+// taps in FP32 fragments and write them to partial row r ([co][ci][k], then the bias gradient, summed by
+// tap group 0 from the staged BF16 dY); k_wgrad_sum adds the rows in a fixed order. The next chunk's
+// global loads are in flight while the current chunk computes.
 constexpr int WT = 128;                                    // positions per chunk
 constexpr int WXR = WT + 2 * PAD;                          // staged input positions per chunk
 constexpr int WAS = WT + 8;                                // A row stride (bf16)
 constexpr size_t WSMEM = sizeof(__nv_bfloat16) * ((size_t)C * WAS + (size_t)WXR * XS);
 
 __global__ void __launch_bounds__(NTHR) k_wgrad64_mma(const __nv_bfloat16* __restrict__ x,
-                                                      const __nv_bfloat16* __restrict__ dy16,
-                                                      const float* __restrict__ dy, int64_t Tp, int64_t T,
-                                                      float* __restrict__ part, int vec) {
+                                                      const __nv_bfloat16* __restrict__ dy16, int64_t Tp,
+                                                      int64_t T, float* __restrict__ part, int vec) {
     extern __shared__ float4 smem4[];
     __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem4);      // [C][WAS]: dY of positions t0 + j
     __nv_bfloat16* Xs = As + C * WAS;                                 // [WXR][XS]: x of padded index t0 + r
@@ -303,63 +303,88 @@ __global__ void __launch_bounds__(NTHR) k_wgrad64_mma(const __nv_bfloat16* __res
     float dbs = 0.0f;                                                 // bias: thread co = tid / 4, quarter tid % 4
 
     const int64_t nchunk = (T + WT - 1) / WT;
+    // Staging, software-pipelined: the next chunk's global loads go to registers while the current chunk
+    // computes. Thread item i < C (WT / 8 + 1) of A: row co, 16-byte chunk u of the padded row from t0;
+    // item i < C (WXR / 8) of x: 16-byte chunk u of channel ci.
+    constexpr int NA = (C * (WT / 8 + 1) + NTHR - 1) / NTHR, NX = (C * (WXR / 8) + NTHR - 1) / NTHR;
+    uint4 pa[NA], px[NX];
+    auto load16 = [&](const __nv_bfloat16* src, int64_t tp) -> uint4 {
+        if (vec && tp + 7 < Tp) return __ldg(reinterpret_cast<const uint4*>(src));
+        __nv_bfloat16 tmp[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? src[e] : __float2bfloat16_rn(0.0f);
+        return *reinterpret_cast<const uint4*>(tmp);
+    };
+    auto fetch = [&](int64_t t0) {
+#pragma unroll
+        for (int r = 0; r < NA; ++r) {
+            const int i = tid + r * NTHR;
+            pa[r] = make_uint4(0u, 0u, 0u, 0u);
+            if (i < C * (WT / 8 + 1)) {
+                const int co = i / (WT / 8 + 1), u = i - co * (WT / 8 + 1);
+                pa[r] = load16(dy16 + (int64_t)co * Tp + t0 + 8 * u, t0 + 8 * u);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+            const int i = tid + r * NTHR;
+            px[r] = make_uint4(0u, 0u, 0u, 0u);
+            if (i < C * (WXR / 8)) {
+                const int u = i / C, ci = i - u * C;
+                px[r] = load16(x + (int64_t)ci * Tp + t0 + 8 * u, t0 + 8 * u);
+            }
+        }
+    };
+    // A: dY of positions t0 .. t0 + WT (padded t0 + 4 ..): the padded row's 16-byte chunks from t0 stored as
+    // two 8-byte halves at their column; x transposed: Xs[r][ci] = x[ci][padded t0 + r]
+    auto stage = [&]() {
+#pragma unroll
+        for (int r = 0; r < NA; ++r) {
+            const int i = tid + r * NTHR;
+            if (i < C * (WT / 8 + 1)) {
+                const int co = i / (WT / 8 + 1), u = i - co * (WT / 8 + 1);
+                const int c0 = 8 * u - PAD;                       // column of the chunk's first element
+                if (c0 >= 0) *reinterpret_cast<uint2*>(As + co * WAS + c0) = make_uint2(pa[r].x, pa[r].y);
+                if (c0 + 4 < WT) *reinterpret_cast<uint2*>(As + co * WAS + c0 + 4) = make_uint2(pa[r].z, pa[r].w);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+            const int i = tid + r * NTHR;
+            if (i < C * (WXR / 8)) {
+                const int u = i / C, ci = i - u * C;
+                const __nv_bfloat16* v = reinterpret_cast<const __nv_bfloat16*>(&px[r]);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) Xs[(8 * u + e) * XS + ci] = v[e];
+            }
+        }
+    };
+    if ((int64_t)blockIdx.x < nchunk) fetch((int64_t)blockIdx.x * WT);
     for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-        const int64_t t0 = ch * WT;                                   // first position; padded window t0 ..
         __syncthreads();                                              // the previous chunk's reads are done
-        // A: dY of positions t0 .. t0 + WT (padded t0 + 4 ..), loaded as aligned 16-byte chunks of the padded
-        // row from t0 and stored as two 8-byte halves at their column (out of range and past Tp: zero)
-#pragma unroll
-        for (int i = tid; i < C * (WT / 8 + 1); i += NTHR) {
-            const int co = i / (WT / 8 + 1), u = i - co * (WT / 8 + 1);
-            const int64_t tp = t0 + 8 * u;                            // padded index of the chunk
-            const __nv_bfloat16* src = dy16 + (int64_t)co * Tp + tp;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (vec && tp + 7 < Tp) {
-                v = __ldg(reinterpret_cast<const uint4*>(src));
-            } else {
-                __nv_bfloat16 tmp[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? src[e] : __float2bfloat16_rn(0.0f);
-                v = *reinterpret_cast<const uint4*>(tmp);
-            }
-            const int c0 = 8 * u - PAD;                               // column of the chunk's first element
-            if (c0 >= 0) *reinterpret_cast<uint2*>(As + co * WAS + c0) = make_uint2(v.x, v.y);
-            if (c0 + 4 < WT) *reinterpret_cast<uint2*>(As + co * WAS + c0 + 4) = make_uint2(v.z, v.w);
-        }
-        // x transposed: Xs[r][ci] = x[ci][padded t0 + r], r < WXR
-#pragma unroll
-        for (int i = tid; i < C * (WXR / 8); i += NTHR) {
-            const int u = i / C, ci = i - u * C;
-            const int64_t tp = t0 + 8 * u;
-            const __nv_bfloat16* src = x + (int64_t)ci * Tp + tp;
-            __nv_bfloat16 tmp[8];
-            if (vec && tp + 7 < Tp) {
-                *reinterpret_cast<uint4*>(tmp) = __ldg(reinterpret_cast<const uint4*>(src));
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) tmp[e] = tp + e < Tp ? src[e] : __float2bfloat16_rn(0.0f);
-            }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) Xs[(8 * u + e) * XS + ci] = tmp[e];
-        }
-        // the bias gradient from the FP32 planes: four threads per channel, 32 positions each, all loads in
-        // flight together
+        stage();
+        __syncthreads();
+        if (ch + gridDim.x < nchunk) fetch((ch + gridDim.x) * WT);
+        // the bias gradient from the staged dY: four threads per channel, 32 positions each, pairs of
+        // the quarter's 8-element groups in order
         if (blockIdx.y == 0) {
             const int co = tid >> 2, qq = tid & 3;
-            float v[WT / 4];
-#pragma unroll
-            for (int j = 0; j < WT / 4; ++j) {
-                const int64_t t = t0 + qq * (WT / 4) + j;
-                v[j] = t < T ? dy[(int64_t)co * Tp + t + PAD] : 0.0f;
-            }
+            const uint4* ar = reinterpret_cast<const uint4*>(As + co * WAS + qq * (WT / 4));
             float sb = 0.0f;
 #pragma unroll
-            for (int j = 0; j < WT / 4; ++j) sb += v[j];
+            for (int j = 0; j < WT / 32; ++j) {
+                const uint4 w4 = ar[j];
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w4);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 f = __bfloat1622float2(h[e]);
+                    sb += f.x + f.y;
+                }
+            }
             sb += __shfl_xor_sync(0xffffffffu, sb, 1);
             sb += __shfl_xor_sync(0xffffffffu, sb, 2);
             dbs += sb;
         }
-        __syncthreads();
 #pragma unroll 2
         for (int ks = 0; ks < WT / 16; ++ks) {
             uint32_t a[2][4];
@@ -430,8 +455,8 @@ cudaError_t conv64_mma_dgrad(const __nv_bfloat16* dout, int64_t Tp, int64_t T, c
     return cudaGetLastError();
 }
 
-cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* dy16, const float* dy, int64_t Tp,
-                                   int64_t T, float* part, int max_rows, int* nrow, cudaStream_t s) {
+cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* dy16, int64_t Tp, int64_t T,
+                                   float* part, int max_rows, int* nrow, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_wgrad64_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WSMEM);
@@ -440,7 +465,7 @@ cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* 
     const int64_t nchunk = (T + WT - 1) / WT;
     const int rows = (int)std::min<int64_t>(std::max<int64_t>(nchunk, 1), max_rows);
     const int vec = ((uintptr_t)x % 16 == 0) && ((uintptr_t)dy16 % 16 == 0) && (Tp % 8 == 0);
-    k_wgrad64_mma<<<dim3((unsigned)rows, KW / 3), NTHR, WSMEM, s>>>(x, dy16, dy, Tp, T, part, vec);
+    k_wgrad64_mma<<<dim3((unsigned)rows, KW / 3), NTHR, WSMEM, s>>>(x, dy16, Tp, T, part, vec);
     *nrow = rows;
     return cudaGetLastError();
 }

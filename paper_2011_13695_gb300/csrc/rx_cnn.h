@@ -62,8 +62,8 @@ cudaError_t conv64_mma_fwd(const __nv_bfloat16* x, int64_t Tp, int64_t T, const 
 // dout[co][t + k - 4]) x (mask[ci][t] > 0), FP32 into din and (nullable) BF16 into din16; dout BF16 planes
 // the partial rows of a 64 -> 64 layer's weight and bias gradients on the tensor cores (at most max_rows
 // rows of C * C * 9 + C floats in part; *nrow = rows written); x: the layer's input activation planes,
-// dy16 / dy: the BF16 copy and the FP32 gradient planes
-cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* dy16, const float* dy, int64_t Tp,
-                                   int64_t T, float* part, int max_rows, int* nrow, cudaStream_t s);
+// dy16: the BF16 copy of the gradient planes
+cudaError_t conv64_mma_wgrad_parts(const __nv_bfloat16* x, const __nv_bfloat16* dy16, int64_t Tp, int64_t T,
+                                   float* part, int max_rows, int* nrow, cudaStream_t s);
 cudaError_t conv64_mma_dgrad(const __nv_bfloat16* dout, int64_t Tp, int64_t T, const __nv_bfloat16* Wd,
                              const __nv_bfloat16* mask, float* din, __nv_bfloat16* din16, cudaStream_t s);
