@@ -96,6 +96,7 @@ struct rx_handle {
     cudaStream_t last = nullptr;
     cudaStream_t side = nullptr;   // the rest of a frame's FD compensation, beside the acquisition
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_host = nullptr;
+    cudaEvent_t ev_chk = nullptr, ev_chk_done = nullptr;   // the rerun's check beside the segments
     // replay of a single frame's launches as one CUDA graph, per entry point (device / host buffers)
     struct FrameGraph {
         bool valid = false, timing = false;
@@ -213,6 +214,8 @@ void free_all(rx_handle* h) {
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_chk) cudaEventDestroy(h->ev_chk);
+    if (h->ev_chk_done) cudaEventDestroy(h->ev_chk_done);
     if (h->ev_host) cudaEventDestroy(h->ev_host);
     for (auto& g : h->graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -306,6 +309,8 @@ rx_status rx_create(const rx_config* cfg, rx_handle** out) {
     A(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     A(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     A(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    A(cudaEventCreateWithFlags(&h->ev_chk, cudaEventDisableTiming));
+    A(cudaEventCreateWithFlags(&h->ev_chk_done, cudaEventDisableTiming));
     A(cudaEventCreateWithFlags(&h->ev_host, cudaEventDisableTiming));
     A(cudaStreamCreateWithFlags(&h->capstream, cudaStreamNonBlocking));
     for (int s = 0; s < ST_N && e == cudaSuccess; ++s) {
@@ -420,6 +425,7 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
     base.m = h->m;
     base.g0 = g0;
     base.st = st;
+    bool late_check = false;                      // the rerun's check on the side stream (joined before the count)
     if (first) {
         if (n_cma > 0) {
             {
@@ -454,7 +460,10 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 a2.taps_in = st->taps_init;
                 a2.run_if = h->flag;
                 RX_CK(launch_lms(a2, kAcqThreads, s));
-                RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 1, s));
+                // the rerun's own check only raises an error bit: with a side stream it runs there after
+                // the DD acquisition's launch, beside the segments, and joins before the count
+                if (!split) RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 1, s));
+                late_check = split;
                 nl += 4;
             }
             {
@@ -479,6 +488,12 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 a.exclusive = 1;
                 RX_CK(launch_lms(a, kAcqThreads, s));
                 ++nl;
+            }
+            if (late_check) {
+                RX_CK(cudaEventRecord(h->ev_chk, s));
+                RX_CK(cudaStreamWaitEvent(h->side, h->ev_chk, 0));
+                RX_CK(launch_cma_check(h->yacq, h->nacq, nacq_e, T, st, h->flag, 1, h->side));
+                RX_CK(cudaEventRecord(h->ev_chk_done, h->side));
             }
         } else {
             RX_CK(cudaMemcpyAsync(st->taps_init, h->taps_id, sizeof(float2) * 4 * T, cudaMemcpyDeviceToDevice, s));
@@ -530,6 +545,7 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
             h->sync_done = true;
         }
     }
+    if (late_check) RX_CK(cudaStreamWaitEvent(s, h->ev_chk_done, 0));
     if (d_ref || d_out) {
         StageScope sc(h, ST_COUNT, s);
         RX_CK(launch_count(h->z, h->Nmax, N, d_ref, words, N, h->m, lo, hi, lat, d_out, words, st, s));
