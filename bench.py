@@ -214,9 +214,9 @@ class ClockSampler:
 PROFILED_TRAFFIC = {
     # DRAM bytes read + written, one ncu capture of this launch
     "dd_acq": ("k_lms_tile.cuh", "fc6c10aaebce0d8bd21f8070b26bf8cceea39364", 562688),
-    # captured on the 2^18-symbol frame (4,283,648 B: the equalised symbols read once, under ncu's
+    # captured on the 2^18-symbol frame (4,312,576 B: the equalised symbols read once, under ncu's
     # cache flush) and scaled by the symbols of the 2^20-symbol launch (traffic in proportion)
-    "bps": ("k_bps.cu", "5a40944c37ba1dc03b9f6c576ad10c97677a554d", 17134592),
+    "bps": ("k_bps.cu", "bb4e2868647e8ca446b00df3180daf7090885807", 17250304),
     "wl": ("k_lms_fast.cuh", "fca5f277b4ecd771cc2e0b0acdff6c7ea8cf98cc", 33638912),
 }
 
@@ -298,7 +298,7 @@ def stage_roofline(stage: str, ms: float, w: dict, n_sym: int, pk: dict, sm_mhz:
         ops = 2 * n_sym * rxs["bps_phases"] * 16          # lane-ops per (symbol, test phase)
         peak = lane_peak / 1e12
         a = ops / t / 1e12
-        return {"kernel": "k_bps", "bound": "alu", "achieved": a, "peak": peak, "unit": "Tops/s",
+        return {"kernel": "k_bps2", "bound": "alu", "achieved": a, "peak": peak, "unit": "Tops/s",
                 "frac": a / peak, "traffic": _traffic(stage), "algorithmic_ops": ops,
                 "peak_note": "lane-operations: half the FP32 flop peak, " + note}
     # FD compensation: the acquisition's blocks first ("cdc": its window plus one FFT of reach), the

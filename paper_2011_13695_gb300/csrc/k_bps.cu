@@ -4,9 +4,9 @@
 // dist = |y_k e^{-j theta_b} - dec(.)|^2 and D[k, b] is its sum over the window
 // [k - W/2, k + W/2) clipped to the frame; b*_k = argmin_b D (first minimum).
 //
-// Layout: one thread per test phase and strip of LEN consecutive symbols
-// (32 or 64 threads per strip), strips of one polarisation side by side in a
-// CTA. The strip's symbols (with a W/2 halo on each side) are staged in
+// Layout, B <= 32: one thread per test phase and strip of LEN consecutive
+// symbols (32 threads per strip), strips of one polarisation side by side in
+// a CTA. The strip's symbols (with a W/2 halo on each side) are staged in
 // shared memory as (x, y, y, -x) and read as 16-byte broadcasts, so that the
 // rotation, rounding and error of both dimensions are packed FP32x2
 // instructions (each component the same FMA or add as the scalar form, so
@@ -14,7 +14,10 @@
 // distances of its phase in registers (a ring indexed at compile time), slides
 // the window sum by one add and one subtract per symbol and re-forms it as a
 // direct sum of the ring every W symbols, which bounds the rounding drift to
-// that of a W-term sum. The minimum over phases is one warp-wide min reduction
+// that of a W-term sum. B > 32 (k_bps2): one warp per strip, each lane holding
+// phases l and l + 32, the packed instructions running over the phase pair
+// (symbols staged as (x, x, y, y)); the same operations per component, so the
+// two layouts give the same bits. The minimum over phases is one warp-wide min reduction
 // of a key per lane: the (non-negative) sum's bit pattern with its low six
 // bits replaced by the phase index, so one reduction gives both the least sum
 // and its phase; sums that agree to within 64 units in the last place
@@ -159,6 +162,174 @@ __global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict
                                 bstride);
 }
 
+// ---------------------------------------------------------------------------
+// Phase pairs: one warp per strip, lane l holding test phases l and l + 32 (B > 32). The rotation,
+// rounding and error of a dimension are packed over the two phases, as are the distance and the
+// window sums, so that every component is the same FMA or add as the scalar form above and the
+// results are bit-identical to it; the minimum over the 64 keys is one in-lane min and one warp
+// reduction, and the strip needs no block barrier.
+// ---------------------------------------------------------------------------
+// W = 64: half of the ring (32 pairs) in registers and half in shared memory, so that 166 registers
+// give six CTAs of two warps per SM (12 warps). On a 2^20-symbol frame in the chain this takes 0.133 ms
+// against 0.138 ms for the one-phase-per-thread form; the whole ring in registers (8 warps per SM), the
+// first window folded into the chunk loop, and a rolled loop over a ring wholly in shared memory were
+// each slower.
+constexpr int BPS2_STRIPS = 2;                        // strips (warps) per CTA
+constexpr int BPS2_MINB = 6;                          // CTAs per SM the registers are sized for
+constexpr int BPS2_WR64 = 32;                         // W = 64: ring entries in registers
+
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+struct Bps2Phase {
+    float2 c, s, ns;                                  // cos, sin, -sin of the two phases, times 1/(2a)
+    float2 hh, ll;                                    // (L-1)/2, L-1
+    float invLm1;
+    float2 pen;                                       // 0, or a penalty for phases >= B
+};
+
+// distances of one symbol, staged as (x, x, y, y), to the nearest point after the two rotations:
+// per phase vI = fma(x, c, fma(y, s, hL)), vQ = fma(y, c, fma(x, -s, hL)) and
+// d = fma(eI, eI, eQ * eQ), the operations of bps_dist
+__device__ __forceinline__ float2 bps_dist2(float4 v, const Bps2Phase& p) {
+    const float2 MAGIC = make_float2(12582912.0f, 12582912.0f);
+    const float2 NMAGIC = make_float2(-12582912.0f, -12582912.0f);
+    const float2 NONE = make_float2(-1.0f, -1.0f);
+    const float2 xx = make_float2(v.x, v.y), yy = make_float2(v.z, v.w);
+    const float2 rI = __ffma2_rn(xx, p.c, __ffma2_rn(yy, p.s, p.hh));
+    const float2 rQ = __ffma2_rn(yy, p.c, __ffma2_rn(xx, p.ns, p.hh));
+    const float2 wI = make_float2(__saturatef(rI.x * p.invLm1), __saturatef(rI.y * p.invLm1));
+    const float2 wQ = make_float2(__saturatef(rQ.x * p.invLm1), __saturatef(rQ.y * p.invLm1));
+    const float2 tI = __fadd2_rn(__ffma2_rn(wI, p.ll, MAGIC), NMAGIC);
+    const float2 tQ = __fadd2_rn(__ffma2_rn(wQ, p.ll, MAGIC), NMAGIC);
+    const float2 eI = __ffma2_rn(tI, NONE, rI), eQ = __ffma2_rn(tQ, NONE, rQ);
+    return __ffma2_rn(eI, eI, __fmul2_rn(eQ, eQ));
+}
+
+// the least key of the warp's 64 (phase l: D.x, phase l + 32: D.y), as bps_publish
+__device__ __forceinline__ void bps_publish2(float2 D, unsigned int* slot, int lane) {
+    const unsigned int klo = (__float_as_uint(D.x) & ~63u) | (unsigned)lane;
+    const unsigned int khi = (__float_as_uint(D.y) & ~63u) | (unsigned)(lane + 32);
+    const unsigned int mn = __reduce_min_sync(0xffffffffu, min(klo, khi));
+    if (lane == 0) *slot = mn;
+}
+
+// the NaN guard of the CTAs whose spans reach past the frame (as in bps_strip)
+template <bool EDGE>
+__device__ __forceinline__ float2 guard2(float2 d) {
+    return EDGE ? make_float2(fmaxf(d.x, 0.0f), fmaxf(d.y, 0.0f)) : d;
+}
+
+// the windows of one strip: the ring of W distance pairs (the first WR in registers, indices fixed
+// at compile time, the rest in this lane's column of rs), the sliding sums, and the sum of the
+// current chunk, which equals the re-formed window sum of bps_strip (the same terms in the same
+// order) at the chunk's end
+template <int W, int WR, bool EDGE>
+__device__ __forceinline__ void bps2_strip(const float4* __restrict__ yl, const Bps2Phase& p, int nc, int LEN,
+                                           int64_t s0, int64_t N, unsigned int* slots, float2* rs, int lane,
+                                           uint8_t* __restrict__ bq) {
+    float2 ring[WR > 0 ? WR : 1];
+    float2* rl = rs + lane;                           // entry u >= WR at rl[(u - WR) * 32]
+    float2 D = p.pen;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        const float2 d = guard2<EDGE>(bps_dist2(yl[u], p));
+        if (u < WR) ring[u < WR ? u : 0] = d;
+        else rl[(u - WR) * 32] = d;
+        D = __fadd2_rn(D, d);
+    }
+    bps_publish2(D, &slots[0], lane);
+    for (int ch = 0; ch <= nc; ++ch) {
+        if (ch > 0) {
+            const float4* yc = yl + ch * W;
+            float2 C = p.pen;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                const float2 d = guard2<EDGE>(bps_dist2(yc[u], p));
+                const float2 old = u < WR ? ring[u < WR ? u : 0] : rl[(u - WR) * 32];
+                D = sub2_rn(__fadd2_rn(D, d), old);
+                if (u < WR) ring[u < WR ? u : 0] = d;
+                else rl[(u - WR) * 32] = d;
+                C = __fadd2_rn(C, d);
+                bps_publish2(guard2<EDGE>(D), &slots[(u + 1) & (W - 1)], lane);
+            }
+            D = C;
+        }
+        __syncwarp();
+        for (int slot = lane; slot < W; slot += 32) {
+            const int kl = slot == 0 ? ch * W : (ch - 1) * W + slot;
+            if (kl >= 0 && kl < LEN && s0 + kl < N) bq[s0 + kl] = (uint8_t)(slots[slot] & 63u);
+        }
+        __syncwarp();
+    }
+}
+
+// distance pairs of the ring kept in registers (the rest in shared memory)
+template <int W>
+__host__ __device__ constexpr int bps2_wr() {
+    return W <= 32 ? W : BPS2_WR64;
+}
+
+template <int W>
+__global__ void __launch_bounds__(32 * BPS2_STRIPS, BPS2_MINB) k_bps2(const float2* __restrict__ y, int64_t ystride,
+                                                                      int64_t N, int B, float cI0, float hL,
+                                                                      float invLm1, float Lm1, int LEN,
+                                                                      uint8_t* __restrict__ bstar, int64_t bstride) {
+    constexpr int WR = bps2_wr<W>();
+    extern __shared__ float4 smem_v[];
+    const int span = LEN + W;
+    float4* ys = smem_v;                              // [BPS2_STRIPS][LEN + W]: (x, x, y, y)
+    float2* rs = reinterpret_cast<float2*>(ys + BPS2_STRIPS * span);   // [BPS2_STRIPS][W - WR][32]
+    __shared__ unsigned int slots[BPS2_STRIPS][W];
+    const int tid = threadIdx.x, sl = tid >> 5, lane = tid & 31;
+    const int q = blockIdx.y;
+    const int64_t s0 = ((int64_t)blockIdx.x * BPS2_STRIPS + sl) * LEN;
+    const float2* yq = y + (int64_t)q * ystride;
+
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int t = tid; t < BPS2_STRIPS * span; t += 32 * BPS2_STRIPS) {
+        const int st = t / span, u = t - st * span;
+        const int64_t i = ((int64_t)blockIdx.x * BPS2_STRIPS + st) * LEN - W / 2 + u;
+        const float2 v = (i >= 0 && i < N) ? yq[i] : make_float2(qnan, qnan);
+        ys[st * span + u] = make_float4(v.x, v.x, v.y, v.y);
+    }
+    __syncthreads();
+    const bool edge = (int64_t)blockIdx.x * BPS2_STRIPS * LEN < W / 2 ||
+                      ((int64_t)blockIdx.x + 1) * BPS2_STRIPS * LEN + W / 2 > N;
+
+    Bps2Phase p;
+    float s1, c1, s2, c2;
+    sincospif((float)(2 * lane - B) / (float)(4 * B), &s1, &c1);
+    sincospif((float)(2 * (lane + 32) - B) / (float)(4 * B), &s2, &c2);
+    p.c = make_float2(c1 * cI0, c2 * cI0);
+    p.s = make_float2(s1 * cI0, s2 * cI0);
+    p.ns = make_float2(-p.s.x, -p.s.y);
+    p.hh = make_float2(hL, hL);
+    p.ll = make_float2(Lm1, Lm1);
+    p.invLm1 = invLm1;
+    p.pen = make_float2(lane < B ? 0.0f : 3.0e38f, lane + 32 < B ? 0.0f : 3.0e38f);
+    const int nc = LEN / W;
+    const float4* yl = ys + sl * span;
+    float2* rsw = rs + sl * (W - WR) * 32;
+    uint8_t* bq = bstar + (int64_t)q * bstride;
+    if (edge)
+        bps2_strip<W, WR, true>(yl, p, nc, LEN, s0, N, slots[sl], rsw, lane, bq);
+    else
+        bps2_strip<W, WR, false>(yl, p, nc, LEN, s0, N, slots[sl], rsw, lane, bq);
+}
+
+// dynamic shared memory of k_bps2<W> for strips of LEN symbols
+template <int W>
+size_t bps2_smem(int LEN) {
+    return sizeof(float4) * BPS2_STRIPS * (LEN + W) + sizeof(float2) * BPS2_STRIPS * (W - bps2_wr<W>()) * 32;
+}
+
 template <int W, int GS>
 cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
                   cudaStream_t s) {
@@ -185,10 +356,13 @@ cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uin
     const int64_t nstrip = (N + LEN - 1) / LEN;
     dim3 grid((unsigned)((nstrip + NSTRIP - 1) / NSTRIP), 2);
     const size_t smem = sizeof(float4) * NSTRIP * (LEN + W);
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        cudaFuncSetAttribute(k_bps<W, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
+    // opt in once for the largest strip (1024 symbols): the static slots come on top of the dynamic
+    // part, so no size near the 48 KB default is left to chance
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bps<W, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float4) * NSTRIP * (1024 + W)));
+        attr = true;
     }
     const float Lm1 = (float)(qm.L - 1);
     k_bps<W, GS><<<grid, BPS_THREADS, smem, s>>>(y, ystride, N, B, qm.half_inv_a, qm.hL, 1.0f / Lm1, Lm1, LEN, bstar,
@@ -197,10 +371,44 @@ cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uin
 }
 
 template <int W>
+cudaError_t bps2_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
+                   cudaStream_t s) {
+    const Qam qm = make_qam(m);
+    // strip length: the wave model of bps_t
+    static int slots = 0;
+    if (!slots) {
+        int dev = 0, nsm = 152, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bps2<W>, 32 * BPS2_STRIPS, bps2_smem<W>(8 * W));
+        slots = std::max(1, nsm * std::max(1, per));
+    }
+    int LEN = 8 * W;
+    int64_t best = -1;
+    for (int len = 4 * W; len <= 16 * W && len <= 1024; len += W) {
+        const int64_t ctas = 2 * (((N + len - 1) / len + BPS2_STRIPS - 1) / BPS2_STRIPS);
+        const int64_t cost = ((ctas + slots - 1) / slots) * (len + W);
+        if (best < 0 || cost < best) { best = cost; LEN = len; }
+    }
+    const int64_t nstrip = (N + LEN - 1) / LEN;
+    dim3 grid((unsigned)((nstrip + BPS2_STRIPS - 1) / BPS2_STRIPS), 2);
+    const size_t smem = bps2_smem<W>(LEN);
+    static bool attr = false;                         // as in bps_t
+    if (!attr) {
+        cudaFuncSetAttribute(k_bps2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bps2_smem<W>(1024));
+        attr = true;
+    }
+    const float Lm1 = (float)(qm.L - 1);
+    k_bps2<W><<<grid, 32 * BPS2_STRIPS, smem, s>>>(y, ystride, N, B, qm.half_inv_a, qm.hL, 1.0f / Lm1, Lm1, LEN,
+                                                   bstar, bstride);
+    return cudaGetLastError();
+}
+
+template <int W>
 cudaError_t bps_w(const float2* y, int64_t ystride, int64_t N, int B, int m, uint8_t* bstar, int64_t bstride,
                   cudaStream_t s) {
     if (B <= 32) return bps_t<W, 32>(y, ystride, N, B, m, bstar, bstride, s);
-    return bps_t<W, 64>(y, ystride, N, B, m, bstar, bstride, s);
+    return bps2_t<W>(y, ystride, N, B, m, bstar, bstride, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -242,6 +242,16 @@ def test_16qam_32gbd_full_frame():
     check_frame(g, r, cfg, fr.ref_words)
 
 
+@pytest.mark.parametrize("phases,window", [(48, 32), (33, 64), (64, 16), (40, 8)])
+def test_bps_phase_pairs_other_shapes(phases, window):
+    """Test-phase counts above 32 run with two phases per lane (the upper ones beyond B penalised);
+    other window lengths keep the whole ring in registers. A ragged 16QAM frame whose strips reach
+    both frame edges."""
+    w = workload("dp-16qam-32gbd", n_sym=(1 << 15) + 77)
+    g, r, cfg, fr = run_pair(w, 5, rx_kw={"bps_phases": phases, "bps_window": window})
+    check_frame(g, r, cfg, fr.ref_words)
+
+
 @pytest.mark.parametrize("n_sym", [5003, 777, 100, 40])
 def test_ragged_and_tiny_frames(n_sym):
     """Frames that are not a whole number of blocks/segments/tiles, shorter than the
