@@ -35,7 +35,7 @@ __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162
 __device__ __forceinline__ float ld(const float* p) { return *p; }
 
 // EPI 0: bias + ReLU -> BF16 activations; 1: bias + residual -> float2 symbols (COUT = 4);
-// EPI 2: ReLU mask of `mask` -> FP32 gradient (no bias)
+// EPI 2: ReLU mask of `mask` -> FP32 gradient (no bias) and, when act_out is given, its BF16 copy
 template <typename Tin, int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t Tp, int64_t T,
                                              const float* __restrict__ W, const float* __restrict__ bias,
@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
     constexpr int CO_T = COUT >= 8 ? 8 : COUT;       // output channels per thread
     constexpr int NG = COUT / CO_T;                   // output-channel groups
     constexpr int TPG = CT / NG;                      // threads per group
-    constexpr int PPT = COUT <= 4 ? 1 : 4;            // positions per thread (the 4-channel layer: more CTAs)
+    // positions per thread: fewer for the 4-channel layers, so that a 16384-position window gives 256 CTAs
+    constexpr int PPT = COUT <= 4 ? 1 : CIN <= 4 ? 2 : 4;
     constexpr int TT = TPG * PPT;                     // positions per CTA
     constexpr int XW = TT + 2 * PAD;
     constexpr int CCH = CIN < (TT >= 1024 ? CC / 2 : CC) ? CIN : (TT >= 1024 ? CC / 2 : CC);   // static smem < 48 KB
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
             } else if (EPI == 2) {
                 const bool on = __bfloat162float(mask[(int64_t)co * Tp + t + PAD]) > 0.0f;
                 grad_out[(int64_t)co * Tp + t + PAD] = on ? acc[c][j] : 0.0f;
+                if (act_out) act_out[(int64_t)co * Tp + t + PAD] = __float2bfloat16_rn(on ? acc[c][j] : 0.0f);
             }
         }
         if (EPI == 1) {
@@ -123,23 +125,98 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
     }
 }
 
+// The C -> 4 layer (bias + residual into the symbols): four output channels leave too few products per
+// position to fill CTAs with positions alone, so each position's input channels are split over four
+// lanes (lane bits 3-4: channels s, s + 4, s + 8, ..., whose rows fall in distinct shared-memory banks)
+// and two shuffles add the four partial sums; 64 positions per CTA, all input channels staged at once.
+template <int CIN>
+__global__ void __launch_bounds__(CT) k_conv_out4(const __nv_bfloat16* __restrict__ x, int64_t Tp, int64_t T,
+                                                  const float* __restrict__ W, const float* __restrict__ bias,
+                                                  const float2* __restrict__ zres, float2* __restrict__ sym_out,
+                                                  int64_t zs) {
+    constexpr int CS = 4;                             // lanes per position
+    constexpr int TT = CT / CS;                       // positions per CTA
+    constexpr int XW = TT + 2 * PAD;                  // 72: rows s and s + 1 are 8 banks apart
+    static_assert(CIN % CS == 0 && (CS * XW) % 32 == 0, "channel split");
+    __shared__ float xs[CIN][XW];
+    __shared__ __align__(16) float ws[CIN][KW][4];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int sp = lane >> 3;                         // channel split
+    const int p = 8 * (tid >> 5) + (lane & 7);        // tile position
+    const int64_t t0 = (int64_t)blockIdx.x * TT;
+    for (int i0 = 0; i0 < CIN * XW; i0 += 8 * CT) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = i0 + e * CT + tid;
+            const int ci = i / XW, u = i - ci * XW;
+            const int64_t tp = t0 + u;
+            v[e] = (i < CIN * XW && tp < Tp) ? __bfloat162float(x[(int64_t)ci * Tp + tp]) : 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = i0 + e * CT + tid;
+            if (i < CIN * XW) xs[i / XW][i - (i / XW) * XW] = v[e];
+        }
+    }
+    for (int i = tid; i < CIN * KW * 4; i += CT) {
+        const int co = i / (CIN * KW), r = i - co * CIN * KW, ci = r / KW, k = r - ci * KW;
+        ws[ci][k][co] = W[((int64_t)co * CIN + ci) * KW + k];
+    }
+    __syncthreads();
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+    for (int j = 0; j < CIN / CS; ++j) {
+        const int ci = sp + CS * j;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            const float4 w = *reinterpret_cast<const float4*>(&ws[ci][k][0]);
+            const float xv = xs[ci][p + k];
+            acc[0] = fmaf(w.x, xv, acc[0]);
+            acc[1] = fmaf(w.y, xv, acc[1]);
+            acc[2] = fmaf(w.z, xv, acc[2]);
+            acc[3] = fmaf(w.w, xv, acc[3]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 8);
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+    }
+    const int64_t t = t0 + p;
+    if (sp == 0 && t < T) {
+        // channels (I_x, Q_x, I_y, Q_y) -> symbols of pol 0 and 1
+        const float2 z0 = zres[t], z1 = zres[zs + t];
+        sym_out[t] = make_float2(z0.x + acc[0] + bias[0], z0.y + acc[1] + bias[1]);
+        sym_out[T + t] = make_float2(z1.x + acc[2] + bias[2], z1.y + acc[3] + bias[3]);
+    }
+}
+
 // Weight gradients dW[co][ci][k] = sum_t dY[co][t] x[ci][t + k - 4], db[co] = sum_t dY[co][t]: CTA
-// (x, y, z) sums the 256-position chunks x, x + gridDim.x, ... of its (co, ci) tile in registers and writes
-// its partial to row x of part ([row][co][ci][k], then [row][COUT][co] for the biases); k_wgrad_sum adds
-// the rows in order. No atomics: every run gives the same sums.
+// (x, y, z) sums the 256-position chunks x, x + gridDim.x, ... of its (co, ci) tile and writes its partial
+// to row x of part ([row][co][ci][k], then [row][COUT][co] for the biases); k_wgrad_sum adds the rows in
+// order. A tile of fewer than 256 (co, ci) pairs splits each chunk's positions over PS threads per pair,
+// whose sums are added in split order at the end. No atomics: every run gives the same sums.
 template <typename Tin, int CIN, int COUT>
 __global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, const float* __restrict__ dy,
                                                    int64_t Tp, int64_t T, float* __restrict__ part) {
     constexpr int TC = 256;                           // positions per chunk (static smem < 48 KB)
     constexpr int CO_TILE = COUT < 16 ? COUT : 16;
     constexpr int CI_TILE = CIN < 16 ? CIN : 16;
+    constexpr int NP = CO_TILE * CI_TILE;             // (co, ci) pairs of the tile
+    constexpr int PS = CT / NP;                       // threads per pair
+    constexpr int TS = TC / PS;                       // positions per thread and chunk
     constexpr int64_t ROW = (int64_t)COUT * CIN * KW + COUT;
-    __shared__ float dys[CO_TILE][TC];
-    __shared__ float xs[CI_TILE][TC + 2 * PAD];
+    constexpr int DYS = TC + 1, XWC = TC + 2 * PAD, XSS = XWC + 1;   // row strides: rows in distinct banks
+    static_assert(CT % NP == 0 && TC % PS == 0, "pairs x splits = threads");
+    __shared__ float dys[CO_TILE][DYS];
+    __shared__ float xs[CI_TILE][XSS];
+    __shared__ float red[PS > 1 ? PS - 1 : 1][NP][KW + 1];
     const int co0 = blockIdx.y * CO_TILE, ci0 = blockIdx.z * CI_TILE;
     const int tid = threadIdx.x;
-    const int co = tid / 16, ci = tid % 16;
-    const bool mine = co < CO_TILE && ci < CI_TILE;
+    const int pi = tid % NP, sp = tid / NP;
+    const int co = pi / CI_TILE, ci = pi % CI_TILE;
+    const int u0 = sp * TS;
     float acc[KW];
 #pragma unroll
     for (int k = 0; k < KW; ++k) acc[k] = 0.0f;
@@ -164,7 +241,6 @@ __global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, co
                 if (i < CO_TILE * TC) dys[i / TC][i - (i / TC) * TC] = v[e];
             }
         }
-        constexpr int XWC = TC + 2 * PAD;
         for (int i0 = 0; i0 < CI_TILE * XWC; i0 += 8 * CT) {
             float v[8];
 #pragma unroll
@@ -181,22 +257,34 @@ __global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, co
             }
         }
         __syncthreads();
-        if (mine) {
-            float win[KW];
+        float win[KW];
 #pragma unroll
-            for (int k = 0; k < KW; ++k) win[k] = xs[ci][k];
-            for (int u = 0; u < TC; ++u) {
-                const float d = dys[co][u];
+        for (int k = 0; k < KW; ++k) win[k] = xs[ci][u0 + k];
+        for (int u = u0; u < u0 + TS; ++u) {
+            const float d = dys[co][u];
 #pragma unroll
-                for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, win[k], acc[k]);
-                dbs += d;
+            for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, win[k], acc[k]);
+            dbs += d;
 #pragma unroll
-                for (int k = 0; k < KW - 1; ++k) win[k] = win[k + 1];
-                if (u + 1 < TC) win[KW - 1] = xs[ci][u + KW];   // window of position u + 1 (xs has TC + 8 columns)
-            }
+            for (int k = 0; k < KW - 1; ++k) win[k] = win[k + 1];
+            if (u + 1 < u0 + TS) win[KW - 1] = xs[ci][u + KW];   // window of position u + 1
         }
     }
-    if (mine) {
+    if (PS > 1) {
+        if (sp > 0) {
+#pragma unroll
+            for (int k = 0; k < KW; ++k) red[sp - 1][pi][k] = acc[k];
+            red[sp - 1][pi][KW] = dbs;
+        }
+        __syncthreads();
+        if (sp == 0)
+            for (int r = 0; r < PS - 1; ++r) {
+#pragma unroll
+                for (int k = 0; k < KW; ++k) acc[k] += red[r][pi][k];
+                dbs += red[r][pi][KW];
+            }
+    }
+    if (sp == 0) {
         float* row = part + (int64_t)blockIdx.x * ROW;
 #pragma unroll
         for (int k = 0; k < KW; ++k) row[((int64_t)(co0 + co) * CIN + ci0 + ci) * KW + k] = acc[k];
@@ -204,14 +292,20 @@ __global__ void __launch_bounds__(CT) k_conv_wgrad(const Tin* __restrict__ x, co
     }
 }
 
-// dW = the sum of the nrow partial rows in order, then db likewise
+// dW = the sum of the nrow partial rows in order, then db likewise; every row's load is issued before
+// the first add (one memory latency per thread instead of nrow)
 __global__ void k_wgrad_sum(const float* __restrict__ part, int64_t nw, int64_t nb, int nrow, float* __restrict__ dW,
                             float* __restrict__ db) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nw + nb) return;
     const int64_t row = nw + nb;
+    float v[CNN_WG_SPLIT];
+#pragma unroll
+    for (int r = 0; r < CNN_WG_SPLIT; ++r) v[r] = r < nrow ? part[(int64_t)r * row + i] : 0.0f;
     float s = 0.0f;
-    for (int r = 0; r < nrow; ++r) s += part[(int64_t)r * row + i];
+#pragma unroll
+    for (int r = 0; r < CNN_WG_SPLIT; ++r)
+        if (r < nrow) s += v[r];
     if (i < nw) dW[i] = s;
     else db[i - nw] = s;
 }
@@ -225,15 +319,6 @@ __global__ void k_to_channels(const float2* __restrict__ z, int64_t zs, int64_t 
     x0[1 * Tp + t + PAD] = __float2bfloat16_rn(a.y);
     x0[2 * Tp + t + PAD] = __float2bfloat16_rn(b.x);
     x0[3 * Tp + t + PAD] = __float2bfloat16_rn(b.y);
-}
-
-// BF16 copy of the interior of C gradient planes (the tensor-core data gradient's operand)
-__global__ void k_planes_bf16(const float* __restrict__ src, int64_t T, int64_t Tp, int C,
-                              __nv_bfloat16* __restrict__ dst) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)C * T) return;
-    const int64_t c = i / T, t = i - c * T;
-    dst[c * Tp + t + PAD] = __float2bfloat16_rn(src[c * Tp + t + PAD]);
 }
 
 // d3[c][t] = 2 (out - target) / (4 T); loss += sum (out - target)^2 / (4 T)
@@ -297,7 +382,7 @@ template <typename Tin, int CIN, int COUT, int EPI>
 cudaError_t conv_t(const Tin* x, int64_t Tp, int64_t T, const float* W, const float* b, __nv_bfloat16* act,
                    const __nv_bfloat16* mask, float* grad, const float2* zres, float2* sym, cudaStream_t s, int64_t zs = 0) {
     constexpr int CO_T = COUT >= 8 ? 8 : COUT;
-    constexpr int TT = (CT / (COUT / CO_T)) * (COUT <= 4 ? 1 : 4);   // k_conv's positions per CTA
+    constexpr int TT = (CT / (COUT / CO_T)) * (COUT <= 4 ? 1 : CIN <= 4 ? 2 : 4);   // k_conv's positions per CTA
     k_conv<Tin, CIN, COUT, EPI><<<(unsigned)((T + TT - 1) / TT), CT, 0, s>>>(x, Tp, T, W, b, act, mask, grad, zres, sym, zs);
     return cudaGetLastError();
 }
@@ -347,8 +432,9 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T
     if (e) return e;
     e = conv64_mma_fwd(B.act[2], Tp, T, B.wtc + wtc_offset(C, 2), W + B.off[5], B.act[3], s);
     if (e) return e;
-    return conv_t<__nv_bfloat16, 64, 4, 1>(B.act[3], Tp, T, W + B.off[6], W + B.off[7], nullptr, nullptr, nullptr, z,
-                                           out, s, zs);
+    k_conv_out4<64><<<(unsigned)((T + CT / 4 - 1) / (CT / 4)), CT, 0, s>>>(B.act[3], Tp, T, W + B.off[6], W + B.off[7],
+                                                                            z, out, zs);
+    return cudaGetLastError();
 }
 
 // loss gradient and all parameter gradients (every entry of B.grad written) for the last forward
@@ -362,12 +448,10 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
     const float* Wb = B.wbwd;
     // layer 3: weights, then data (masked by act[3] > 0) -> d[2]
     if ((e = wgrad_t<__nv_bfloat16, 64, 4>(B.act[3], B.d[3], Tp, T, B.wpart, G + B.off[6], G + B.off[7], s))) return e;
-    if ((e = conv_t<float, 4, 64, 2>(B.d[3], Tp, T, Wb + B.off[6], nullptr, nullptr, B.act[3], B.d[2], nullptr,
+    // (and the BF16 copy of d[2]: the hidden layers' data gradients on the tensor cores read it)
+    if ((e = conv_t<float, 4, 64, 2>(B.d[3], Tp, T, Wb + B.off[6], nullptr, B.d16[2], B.act[3], B.d[2], nullptr,
                                      nullptr, s)))
         return e;
-    // the hidden layers' data gradients on the tensor cores, from BF16 copies of the gradient planes
-    k_planes_bf16<<<(unsigned)((64 * T + 255) / 256), 256, 0, s>>>(B.d[2], T, Tp, 64, B.d16[2]);
-    if ((e = cudaGetLastError())) return e;
     if ((e = wgrad64_t(B.act[2], B.d16[2], Tp, T, B.wpart, G + B.off[4], G + B.off[5], s))) return e;
     const int64_t lw = (int64_t)64 * 64 * KW;
     if ((e = conv64_mma_dgrad(B.d16[2], Tp, T, B.wtd + lw, B.act[2], B.d[1], B.d16[1], s))) return e;
