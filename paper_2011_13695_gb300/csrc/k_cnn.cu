@@ -340,13 +340,12 @@ __global__ void k_mse(const float2* __restrict__ out, const float2* __restrict__
     if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
 }
 
-// W'[ci][co][k] = bf16(W[co][ci][K-1-k]) and the forward weights as BF16-rounded FP32
-__global__ void k_weights(const float* __restrict__ master, int64_t n, float* __restrict__ fwd, const int* offs,
-                          const int* cins, const int* couts, float* __restrict__ bwd, __nv_bfloat16* __restrict__ wtc,
-                          __nv_bfloat16* __restrict__ wtd) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const __nv_bfloat16 vb = __float2bfloat16_rn(master[i]);
+// W'[ci][co][k] = bf16(W[co][ci][K-1-k]) and the forward weights as BF16-rounded FP32, for parameter i
+// of value w
+__device__ __forceinline__ void weight_copies(int64_t i, float w, float* __restrict__ fwd, const int* offs,
+                                              const int* cins, const int* couts, float* __restrict__ bwd,
+                                              __nv_bfloat16* __restrict__ wtc, __nv_bfloat16* __restrict__ wtd) {
+    const __nv_bfloat16 vb = __float2bfloat16_rn(w);
     const float v = __bfloat162float(vb);
     fwd[i] = v;
     // locate the layer and, for weights, the transposed position and the tensor-core copy in (k, ci)
@@ -366,8 +365,19 @@ __global__ void k_weights(const float* __restrict__ master, int64_t n, float* __
     }
 }
 
+__global__ void k_weights(const float* __restrict__ master, int64_t n, float* __restrict__ fwd, const int* offs,
+                          const int* cins, const int* couts, float* __restrict__ bwd, __nv_bfloat16* __restrict__ wtc,
+                          __nv_bfloat16* __restrict__ wtd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    weight_copies(i, master[i], fwd, offs, cins, couts, bwd, wtc, wtd);
+}
+
+// one Adam step of parameter i, then (with B's copies given) the weight copies of the new value
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, float* __restrict__ fwd,
+                       const int* offs, const int* cins, const int* couts, float* __restrict__ bwd,
+                       __nv_bfloat16* __restrict__ wtc, __nv_bfloat16* __restrict__ wtd) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -375,7 +385,9 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float pn = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pn;
+    if (fwd) weight_copies(i, pn, fwd, offs, cins, couts, bwd, wtc, wtd);
 }
 
 template <typename Tin, int CIN, int COUT, int EPI>
@@ -487,10 +499,11 @@ cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s) {
+cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s, bool copies) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
     k_adam<<<(unsigned)((B.nparam + 255) / 256), 256, 0, s>>>(B.master, B.grad, B.m, B.v, B.nparam, lr, b1, b2, eps,
-                                                              c1, c2);
+                                                              c1, c2, copies ? B.wfwd : nullptr, B.offs_dev, B.cin_dev,
+                                                              B.cout_dev, B.wbwd, B.wtc, B.wtd);
     return cudaGetLastError();
 }

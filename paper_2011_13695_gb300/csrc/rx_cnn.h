@@ -8,7 +8,7 @@
 
 // the weight gradients sum their positions in CNN_WG_SPLIT interleaved shares (one CTA each), then the
 // shares in a fixed order: the same sums on every run
-#define CNN_WG_SPLIT 32
+#define CNN_WG_SPLIT 48
 
 struct CnnBufs {
     int C = 64;                     // hidden channels
@@ -44,7 +44,8 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T
 cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t ts, int64_t T, float* loss,
                          cudaStream_t s);
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);
-cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s);
+// one Adam step; with copies, also the weight copies of cnn_prepare_weights for the new values
+cudaError_t cnn_adam(const CnnBufs& B, float lr, int step, cudaStream_t s, bool copies = false);
 cudaError_t cnn_zero_pads(const CnnBufs& B, int64_t T, cudaStream_t s);
 // the inference forward on the tcgen05 tensor cores (k_cnn_tc.cu); act[1..3] hold planar activations
 cudaError_t cnn_infer_tc(const CnnBufs& B, const float2* z, int64_t T, float2* out, cudaStream_t s);

@@ -245,8 +245,7 @@ rx_status rx_pe_train_step(rx_pe* p, const float* d_z, const float* d_target, in
     if (r != RX_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
     p->step += 1;
-    if (cnn_adam(p->B, lr, p->step, s) != cudaSuccess) return RX_ECUDA;
-    if (cnn_prepare_weights(p->B, s) != cudaSuccess) return RX_ECUDA;
+    if (cnn_adam(p->B, lr, p->step, s, true) != cudaSuccess) return RX_ECUDA;
     return RX_OK;
 }
 
@@ -265,18 +264,20 @@ rx_status rx_pe_train_steps(rx_pe* p, const float* const* d_z, const float* cons
     p->last = s;
     CnnBufs& B = p->B;
     if (cnn_zero_pads(B, window, s) != cudaSuccess) return RX_ECUDA;   // the pad columns of this length
+    if (d_losses && steps > 0 && cudaMemsetAsync(d_losses, 0, sizeof(float) * (size_t)steps, s) != cudaSuccess)
+        return RX_ECUDA;
     for (int32_t i = 0; i < steps; ++i) {
         const int32_t k = which[i];
         const float2* z = reinterpret_cast<const float2*>(d_z[k]) + offs[i];
         const float2* t = reinterpret_cast<const float2*>(d_target[k]) + offs[i];
         if (cnn_forward(B, z, len[k], window, B.out, s) != cudaSuccess) return RX_ECUDA;
-        if (cudaMemsetAsync(B.loss, 0, sizeof(float), s) != cudaSuccess) return RX_ECUDA;
-        if (cnn_backward(B, B.out, t, len[k], window, B.loss, s) != cudaSuccess) return RX_ECUDA;
-        if (d_losses && cudaMemcpyAsync(d_losses + i, B.loss, sizeof(float), cudaMemcpyDeviceToDevice, s))
-            return RX_ECUDA;
+        // the loss accumulates straight into its slot of d_losses (zeroed above), else into B.loss
+        float* loss = d_losses ? d_losses + i : B.loss;
+        if (!d_losses && cudaMemsetAsync(B.loss, 0, sizeof(float), s) != cudaSuccess) return RX_ECUDA;
+        if (cnn_backward(B, B.out, t, len[k], window, loss, s) != cudaSuccess) return RX_ECUDA;
         p->step += 1;
-        if (cnn_adam(B, lrs[i], p->step, s) != cudaSuccess) return RX_ECUDA;
-        if (cnn_prepare_weights(B, s) != cudaSuccess) return RX_ECUDA;
+        // the Adam step and the weight copies of the new values in one launch
+        if (cnn_adam(B, lrs[i], p->step, s, true) != cudaSuccess) return RX_ECUDA;
     }
     return RX_OK;
 }
