@@ -351,6 +351,8 @@ __global__ void __cluster_dims__(FOE_CL, 1, 1) __launch_bounds__(FoeShape<K>::NT
     __shared__ float s_wf;
     cg::cluster_group cl = cg::this_cluster();
     cl.barrier_arrive();                              // this CTA has started
+    // the DD acquisition, launched programmatically after this kernel, may become resident now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int rank = (int)cl.block_rank();
     const int q = rank / HALF, part = rank % HALF;
     const bool leader = part == 0;
@@ -390,6 +392,10 @@ __global__ void __cluster_dims__(FOE_CL, 1, 1) __launch_bounds__(FoeShape<K>::NT
         for (int j = 0; j < S::XPER; ++j)
             if (tid + j * NTH < 2 * span) fbuf[tid + j * NTH] = xv[j];
     }
+    // the samples and twiddles above were complete before the stream's previous kernel (the CMA rerun)
+    // started; its taps, and everything else it writes or reads, only after its completion: this launch
+    // is programmatic, so its staging overlaps the rerun
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int t = tid; t < 2 * T; t += NTH) s_taps[t] = a.taps[q * 2 * T + t];
     __syncthreads();
 
@@ -767,8 +773,18 @@ static cudaError_t foe_t(const FoeArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_foe<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         attr = true;
     }
-    k_foe<K><<<FOE_CL, S::NTH, S::SMEM, s>>>(a);
-    return cudaGetLastError();
+    // a programmatic dependent of the stream's previous kernel (the kernel waits before reading its outputs)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(FOE_CL);
+    cfg.blockDim = dim3(S::NTH);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_foe<K>, a);
 }
 
 cudaError_t launch_foe(const FoeArgs& a, int kf, cudaStream_t s) {

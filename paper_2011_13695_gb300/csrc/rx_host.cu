@@ -486,6 +486,7 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 a.taps_out = st->taps_init;
                 a.y = nullptr;
                 a.exclusive = 1;
+                a.pdl = 1;                                // resident while the FO estimate runs
                 RX_CK(launch_lms(a, kAcqThreads, s));
                 ++nl;
             }

@@ -46,6 +46,9 @@ struct LmsArgs {
     float mu_c;            // widely-linear form only: step of the conjugate taps
     int npol = 2;          // input polarisations; 1 (generic kernel only): the second input plane reads as
                            // zero and only output row 0 runs, i.e. the single-polarisation equaliser
+    int pdl = 0;           // tiled kernel only: launched as a programmatic dependent of the stream's previous
+                           // kernel (its CTAs become resident early and wait for that kernel's completion
+                           // before their first read)
 };
 
 // shared memory a launch asks for: the kernel's need, or with `exclusive` the most a CTA may have
