@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(BPS_THREADS, 5) k_bps(const float2* __restrict
                                                       uint8_t* __restrict__ bstar, int64_t bstride) {
     constexpr int NSTRIP = BPS_THREADS / GS;
     constexpr int NW = GS / 32;
+    pdl_trigger();                                    // the unwrap may become resident now
+    pdl_wait();                                       // launched programmatically: y is complete after this
     extern __shared__ float4 smem_v[];
     float4* ys = smem_v;                              // [NSTRIP][LEN + W]: (x, y, y, -x)
     __shared__ unsigned int slots[NSTRIP][NW][W];     // per output slot: the warp's least key
@@ -282,6 +284,8 @@ __global__ void __launch_bounds__(32 * BPS2_STRIPS, BPS2_MINB) k_bps2(const floa
                                                                       float invLm1, float Lm1, int LEN,
                                                                       uint8_t* __restrict__ bstar, int64_t bstride) {
     constexpr int WR = bps2_wr<W>();
+    pdl_trigger();                                    // the unwrap may become resident now
+    pdl_wait();                                       // launched programmatically: y is complete after this
     extern __shared__ float4 smem_v[];
     const int span = LEN + W;
     float4* ys = smem_v;                              // [BPS2_STRIPS][LEN + W]: (x, x, y, y)
@@ -365,9 +369,8 @@ cudaError_t bps_t(const float2* y, int64_t ystride, int64_t N, int B, int m, uin
         attr = true;
     }
     const float Lm1 = (float)(qm.L - 1);
-    k_bps<W, GS><<<grid, BPS_THREADS, smem, s>>>(y, ystride, N, B, qm.half_inv_a, qm.hL, 1.0f / Lm1, Lm1, LEN, bstar,
-                                                bstride);
-    return cudaGetLastError();
+    return launch_pdl(k_bps<W, GS>, grid, dim3(BPS_THREADS), smem, s, y, ystride, N, B, qm.half_inv_a, qm.hL,
+                      1.0f / Lm1, Lm1, LEN, bstar, bstride);
 }
 
 template <int W>
@@ -399,9 +402,8 @@ cudaError_t bps2_t(const float2* y, int64_t ystride, int64_t N, int B, int m, ui
         attr = true;
     }
     const float Lm1 = (float)(qm.L - 1);
-    k_bps2<W><<<grid, 32 * BPS2_STRIPS, smem, s>>>(y, ystride, N, B, qm.half_inv_a, qm.hL, 1.0f / Lm1, Lm1, LEN,
-                                                   bstar, bstride);
-    return cudaGetLastError();
+    return launch_pdl(k_bps2<W>, grid, dim3(32 * BPS2_STRIPS), smem, s, y, ystride, N, B, qm.half_inv_a, qm.hL,
+                      1.0f / Lm1, Lm1, LEN, bstar, bstride);
 }
 
 template <int W>
@@ -464,6 +466,8 @@ __device__ __forceinline__ void load_b4(const uint8_t* bq, int64_t k0, int64_t N
 // tile writes the new carry.
 __global__ void k_unwrap_sums(const uint8_t* __restrict__ bstar, int64_t bstride, int64_t N, int B,
                               const RxDevState* st, int* tile_sums, int ntiles, int vec) {
+    pdl_trigger();
+    pdl_wait();                                       // launched programmatically: b* is complete after this
     __shared__ int red[32];
     const int q = blockIdx.y;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -493,6 +497,8 @@ __global__ void k_unwrap_apply(const float2* __restrict__ y, int64_t ystride, co
                                int64_t bstride, int64_t N, int B, const int* tile_sums, int ntiles,
                                RxDevState* st, int* m_out, int64_t mstride, float2* z, int64_t zstride,
                                int vec) {
+    pdl_trigger();
+    pdl_wait();                                       // launched programmatically: the tile sums are complete
     __shared__ int red[32];
     __shared__ int s_base[UTHR / 32];
     __shared__ float2 rot[RX_BPS_MAXB];
@@ -597,9 +603,11 @@ cudaError_t launch_unwrap(const float2* y, int64_t ystride, const uint8_t* bstar
     };
     const int vec = al(bstar, bstride, 4) && al(y, ystride * 8, 16) && al(z, zstride * 8, 16) &&
                     al(m_out, mstride * 4, 16);
-    k_unwrap_sums<<<dim3(ntiles, 2), UTHR, 0, s>>>(bstar, bstride, N, B, st, tile_sums, ntiles, vec);
-    k_unwrap_apply<<<dim3(ntiles, 2), UTHR, 0, s>>>(y, ystride, bstar, bstride, N, B, tile_sums, ntiles, st, m_out,
-                                                    mstride, z, zstride, vec);
+    cudaError_t e = launch_pdl(k_unwrap_sums, dim3(ntiles, 2), dim3(UTHR), 0, s, bstar, bstride, N, B,
+                               (const RxDevState*)st, tile_sums, ntiles, vec);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_unwrap_apply, dim3(ntiles, 2), dim3(UTHR), 0, s, y, ystride, bstar, bstride, N, B,
+                   (const int*)tile_sums, ntiles, st, m_out, mstride, z, zstride, vec);
     if (nlaunch) *nlaunch += 2;
-    return cudaGetLastError();
+    return e;
 }

@@ -132,11 +132,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     using S = LmsTileShape<NT, T, LB>;
     constexpr int NW = S::NW, OPL = S::OPL, IM = S::IM, R = S::R, PS = S::PS;
     extern __shared__ float4 smem4[];
-    // a programmatically launched successor may become resident now (it waits for this grid's completion
-    // before reading anything); when this launch is itself programmatic, everything the stream's previous
-    // kernel wrote is complete and visible after the wait (both are no-ops otherwise)
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_trigger();                                                  // the next kernel may become resident
+    pdl_wait();                                                     // (programmatic launches) inputs ready
     if (a.run_if && *a.run_if == 0) return;
     float2* win = reinterpret_cast<float2*>(smem4);                 // [3 buffers][p][parity][PS]
     float4* tapx = smem4 + S::WIN4;                                 // [class][TS]: (hx, hx, hy, hy)
@@ -486,19 +483,7 @@ cudaError_t launch_lms_tile_t(const LmsArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_lms_tile<NT, T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    if (!a.pdl) {
-        k_lms_tile<NT, T, LB><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)nseg, 2);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_lms_tile<NT, T, LB>, a);
+    if (a.pdl) return launch_pdl(k_lms_tile<NT, T, LB>, dim3((unsigned)nseg, 2), dim3(NT), smem, s, a);
+    k_lms_tile<NT, T, LB><<<dim3((unsigned)nseg, 2), NT, smem, s>>>(a);
+    return cudaGetLastError();
 }

@@ -351,8 +351,7 @@ __global__ void __cluster_dims__(FOE_CL, 1, 1) __launch_bounds__(FoeShape<K>::NT
     __shared__ float s_wf;
     cg::cluster_group cl = cg::this_cluster();
     cl.barrier_arrive();                              // this CTA has started
-    // the DD acquisition, launched programmatically after this kernel, may become resident now
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_trigger();                                    // the DD acquisition may become resident now
     const int rank = (int)cl.block_rank();
     const int q = rank / HALF, part = rank % HALF;
     const bool leader = part == 0;
@@ -395,7 +394,7 @@ __global__ void __cluster_dims__(FOE_CL, 1, 1) __launch_bounds__(FoeShape<K>::NT
     // the samples and twiddles above were complete before the stream's previous kernel (the CMA rerun)
     // started; its taps, and everything else it writes or reads, only after its completion: this launch
     // is programmatic, so its staging overlaps the rerun
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_wait();
     for (int t = tid; t < 2 * T; t += NTH) s_taps[t] = a.taps[q * 2 * T + t];
     __syncthreads();
 
@@ -585,6 +584,7 @@ constexpr int CMA_CHUNKS = 4;
 
 __global__ void __launch_bounds__(256) k_cma_check(const float2* __restrict__ yacq, int64_t ystride, int64_t nacq,
                                                    int T, RxDevState* st, int* flag, int pass) {
+    pdl_trigger();                                    // the rerun (pass 0) may become resident now
     if (pass == 1 && *flag == 0) return;
     const int64_t h0 = nacq / 2;
     const int L = (int)(nacq - h0);
@@ -774,17 +774,7 @@ static cudaError_t foe_t(const FoeArgs& a, cudaStream_t s) {
         attr = true;
     }
     // a programmatic dependent of the stream's previous kernel (the kernel waits before reading its outputs)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(FOE_CL);
-    cfg.blockDim = dim3(S::NTH);
-    cfg.dynamicSmemBytes = S::SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_foe<K>, a);
+    return launch_pdl(k_foe<K>, dim3(FOE_CL), dim3(S::NTH), S::SMEM, s, a);
 }
 
 cudaError_t launch_foe(const FoeArgs& a, int kf, cudaStream_t s) {

@@ -36,6 +36,13 @@ struct RxDevState {
 // -------------------------------------------------------------------------
 // complex helpers (float2 = I, Q)
 // -------------------------------------------------------------------------
+// Programmatic dependent launch. A kernel that lets the stream's next kernel (launched with launch_pdl)
+// become resident while it runs calls pdl_trigger; a kernel launched with launch_pdl calls pdl_wait before
+// its first access to anything the stream's previous kernel writes or reads: after it, that kernel has
+// completed and its writes are visible. Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }

@@ -459,6 +459,7 @@ static rx_status enqueue_frame(rx_handle* h, const void* d_in, int64_t n_sym, co
                 LmsArgs a2 = a;
                 a2.taps_in = st->taps_init;
                 a2.run_if = h->flag;
+                a2.pdl = 1;                               // resident while the check runs
                 RX_CK(launch_lms(a2, kAcqThreads, s));
                 // the rerun's own check only raises an error bit: with a side stream it runs there after
                 // the DD acquisition's launch, beside the segments, and joins before the count
