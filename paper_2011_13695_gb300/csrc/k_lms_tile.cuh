@@ -133,8 +133,6 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     constexpr int NW = S::NW, OPL = S::OPL, IM = S::IM, R = S::R, PS = S::PS;
     extern __shared__ float4 smem4[];
     pdl_trigger();                                                  // the next kernel may become resident
-    pdl_wait();                                                     // (programmatic launches) inputs ready
-    if (a.run_if && *a.run_if == 0) return;
     float2* win = reinterpret_cast<float2*>(smem4);                 // [3 buffers][p][parity][PS]
     float4* tapx = smem4 + S::WIN4;                                 // [class][TS]: (hx, hx, hy, hy)
     float4* es = tapx + S::TAP4;                                    // [ESP]: (ex, ex, ey, ey), padded
@@ -145,8 +143,6 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q = blockIdx.y;
     const Qam qm = make_qam(a.m);
-    const long long inc = a.derotate ? a.st->nco_inc : 0;
-
     // lane class: b0 tap group, b1 tap parity, b2 polarisation; bits 3-4 the output subset
     const int ig = lane & 1, r = (lane >> 1) & 1, p = (lane >> 2) & 1, cls = lane & 7, ns = lane >> 3;
     const int Gr = r ? S::G1 : S::G0;
@@ -156,27 +152,6 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     for (int i = tid; i < S::WIN4; i += NT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < S::TAP4; i += NT) tapx[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-
-    // tap-component update role: thread u < NUPD owns component f of slot t of class c
-    const bool upd = tid < S::NUPD;
-    const int uc = tid / (2 * IM), uf = tid % (2 * IM), ut = uf >> 1;
-    const int ur = (uc >> 1) & 1, uig = uc & 1, up = (uc >> 2) & 1;
-    const int uG = ur ? S::G1 : S::G0, uN = ur ? S::NO : S::NE;
-    const int uI = uig ? max(uN - uG, 0) : min(uG, uN);
-    const bool ureal = upd && ut < uI;
-    const int uk = 2 * ((uig ? uG : 0) + ut) + ur;                  // tap index of the owned slot
-    float hreg = 0.0f;
-    if (ureal) {
-        float2 h = a.taps_in[q * 2 * T + up * T + uk];
-        if (inc) {                                                  // rotating frame: h'_k = h_k e^{+j 2 pi F k}
-            const float2 ph = nco_conj(inc, uk);
-            h = cmul(h, make_float2(ph.x, -ph.y));
-        }
-        hreg = (uf & 1) ? h.y : h.x;
-        float* dst = reinterpret_cast<float*>(tapx + uc * S::TS + ut) + ((uf & 1) ? 2 : 0);
-        dst[0] = hreg;
-        dst[1] = hreg;
-    }
 
     const int64_t seg = blockIdx.x, nseg = gridDim.x;
     const int64_t start = seg * a.L_seg;
@@ -189,12 +164,6 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     const float2* const xp1 = a.x + a.xstride;
     // input-sample index of the centre tap's sample of output n of block 0: the frame of its phasor
     const long long gout0 = a.g0 + a.off + 2 * nfirst + S::C;
-    // the phasor of output n of block b is e^{-j 2 pi F (gout0 + 2 n)} e^{-j 2 pi F 2 LB b}: the first
-    // factor per lane in registers, the second per block in a table (nblk <= NBT)
-    if (inc)
-        for (int i = tid; i < nblk; i += NT) bph[i] = nco_conj(inc, 2LL * LB * i);
-
-
     // every window the CTA will read, requested into L2 (128-byte lines)
     if (nblk > 0) {
         const int64_t lo = max(a.off + 2 * nfirst - (int64_t)S::C, (int64_t)0);
@@ -212,8 +181,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
     // Window staging by asynchronous copies (cp.async, 8 bytes per sample, zero fill outside the buffer):
     // thread tid stages window positions s = tid + k NT of the two polarisations (s < 2 XW), into the
     // parity arrays of one of three window buffers; a block's copies are issued two steps ahead, the
-    // thread waits for its own copies one step ahead and (DD) derotates them in place, and the barriers
-    // of that step make them visible. Slots and relative global offsets are the same for every block.
+    // thread waits for its own copies one step ahead, and the barriers of that step make them visible.
+    // Slots and relative global offsets are the same for every block.
     const int64_t gstart = a.off + 2 * nfirst - S::C;                  // window start of block 0
     const uint32_t win_sa = (uint32_t)__cvta_generic_to_shared(win);
     // window position k of this thread: polarisation, position in the window, shared slot in buffer 0
@@ -268,13 +237,48 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1) k_lms_tile(LmsArgs a) {
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     };
 
-    __syncthreads();                                                // tables and taps staged
+    // the first two windows' copies are issued before the wait: the samples were complete before the
+    // stream's previous kernel started (a programmatic launch follows a kernel that does not write them)
     if (nblk > 0) {
         issue(0);
         if (nblk > 1) issue(1);
         else asm volatile("cp.async.commit_group;\n" ::: "memory");
-        land();
     }
+    pdl_wait();                                                     // (programmatic launches) inputs ready
+    if (a.run_if && *a.run_if == 0) {
+        asm volatile("cp.async.wait_all;\n" ::: "memory");         // no copy outlives the CTA
+        return;
+    }
+    const long long inc = a.derotate ? a.st->nco_inc : 0;
+
+    // tap-component update role: thread u < NUPD owns component f of slot t of class c
+    const bool upd = tid < S::NUPD;
+    const int uc = tid / (2 * IM), uf = tid % (2 * IM), ut = uf >> 1;
+    const int ur = (uc >> 1) & 1, uig = uc & 1, up = (uc >> 2) & 1;
+    const int uG = ur ? S::G1 : S::G0, uN = ur ? S::NO : S::NE;
+    const int uI = uig ? max(uN - uG, 0) : min(uG, uN);
+    const bool ureal = upd && ut < uI;
+    const int uk = 2 * ((uig ? uG : 0) + ut) + ur;                  // tap index of the owned slot
+    float hreg = 0.0f;
+    if (ureal) {
+        float2 h = a.taps_in[q * 2 * T + up * T + uk];
+        if (inc) {                                                  // rotating frame: h'_k = h_k e^{+j 2 pi F k}
+            const float2 ph = nco_conj(inc, uk);
+            h = cmul(h, make_float2(ph.x, -ph.y));
+        }
+        hreg = (uf & 1) ? h.y : h.x;
+        float* dst = reinterpret_cast<float*>(tapx + uc * S::TS + ut) + ((uf & 1) ? 2 : 0);
+        dst[0] = hreg;
+        dst[1] = hreg;
+    }
+
+    // the phasor of output n of block b is e^{-j 2 pi F (gout0 + 2 n)} e^{-j 2 pi F 2 LB b}: the first
+    // factor per lane in registers, the second per block in a table (nblk <= NBT)
+    if (inc)
+        for (int i = tid; i < nblk; i += NT) bph[i] = nco_conj(inc, 2LL * LB * i);
+
+    __syncthreads();                                                // tables and taps staged
+    if (nblk > 0) land();
     __syncthreads();
 
     // first output of the lane's tile within a block, and its first sample (logical parity index)

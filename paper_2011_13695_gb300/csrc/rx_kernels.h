@@ -63,8 +63,9 @@ struct LmsArgs {
     int npol = 2;          // input polarisations; 1 (generic kernel only): the second input plane reads as
                            // zero and only output row 0 runs, i.e. the single-polarisation equaliser
     int pdl = 0;           // tiled kernel only: launched as a programmatic dependent of the stream's previous
-                           // kernel (its CTAs become resident early and wait for that kernel's completion
-                           // before their first read)
+                           // kernel (its CTAs become resident early, issue their first window copies, and wait
+                           // for that kernel's completion before reading anything else); x must not be
+                           // written by that kernel
 };
 
 // shared memory a launch asks for: the kernel's need, or with `exclusive` the most a CTA may have
