@@ -6,15 +6,16 @@
 //
 // Layout: activations [C][T + 8] with the 4 zero columns of the padding on
 // each side stored, so a convolution reads x[c][t + k] with no bounds checks.
-// One CTA computes 128 positions (or 1024 for 4 outputs) of all output
-// channels: 8 output channels x 4 positions per thread (positions strided by
-// 32 so a warp's loads hit distinct banks), input channels staged in chunks of
-// 16 (FP32 in shared memory), weights staged as [ci][k][co] so 8 output
-// channels come from two 128-bit broadcast loads. The backward pass on the
-// data reuses the same kernel with transposed, flipped weights
-// W'[ci][co][k] = W[co][ci][K-1-k] and the ReLU mask fused into its store;
-// the weight gradient sums dY[co][t] x[ci][t + k - 4] over a chunk of
-// positions per CTA with a 9-register sliding window and adds the chunk's
+// One CTA computes 128 positions (64 in the 4-input-channel layers) of all
+// output channels: 8 output channels x 4 (2) positions per thread (positions
+// strided by 32 so a warp's loads hit distinct banks), input channels staged
+// in chunks of 16 (FP32 in shared memory), weights staged as [ci][k][co] so 8
+// output channels come from two 128-bit broadcast loads; the 4-output layer
+// (k_conv_out4) splits each position's input channels over four lanes. The
+// backward pass on the data reuses the same kernel with transposed, flipped
+// weights W'[ci][co][k] = W[co][ci][K-1-k] and the ReLU mask fused into its
+// store; the weight gradient sums dY[co][t] x[ci][t + k - 4] over a chunk of
+// positions per thread with a 9-register sliding window and adds the chunk's
 // result to FP32 accumulators.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
