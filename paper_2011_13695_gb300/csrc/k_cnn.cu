@@ -130,11 +130,14 @@ __global__ void __launch_bounds__(CT) k_conv(const Tin* __restrict__ x, int64_t 
 // position to fill CTAs with positions alone, so each position's input channels are split over four
 // lanes (lane bits 3-4: channels s, s + 4, s + 8, ..., whose rows fall in distinct shared-memory banks)
 // and two shuffles add the four partial sums; 64 positions per CTA, all input channels staged at once.
+// With a target (training), the epilogue also forms the loss gradient d3 and adds the loss, as k_mse
+// does from the stored output.
 template <int CIN>
 __global__ void __launch_bounds__(CT) k_conv_out4(const __nv_bfloat16* __restrict__ x, int64_t Tp, int64_t T,
                                                   const float* __restrict__ W, const float* __restrict__ bias,
                                                   const float2* __restrict__ zres, float2* __restrict__ sym_out,
-                                                  int64_t zs) {
+                                                  int64_t zs, const float2* __restrict__ tgt, int64_t ts,
+                                                  float* __restrict__ d3, float* __restrict__ loss) {
     constexpr int CS = 4;                             // lanes per position
     constexpr int TT = CT / CS;                       // positions per CTA
     constexpr int XW = TT + 2 * PAD;                  // 72: rows s and s + 1 are 8 banks apart
@@ -185,11 +188,28 @@ __global__ void __launch_bounds__(CT) k_conv_out4(const __nv_bfloat16* __restric
         acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
     }
     const int64_t t = t0 + p;
+    float l = 0.0f;
     if (sp == 0 && t < T) {
         // channels (I_x, Q_x, I_y, Q_y) -> symbols of pol 0 and 1
         const float2 z0 = zres[t], z1 = zres[zs + t];
-        sym_out[t] = make_float2(z0.x + acc[0] + bias[0], z0.y + acc[1] + bias[1]);
-        sym_out[T + t] = make_float2(z1.x + acc[2] + bias[2], z1.y + acc[3] + bias[3]);
+        const float2 a = make_float2(z0.x + acc[0] + bias[0], z0.y + acc[1] + bias[1]);
+        const float2 b = make_float2(z1.x + acc[2] + bias[2], z1.y + acc[3] + bias[3]);
+        sym_out[t] = a;
+        sym_out[T + t] = b;
+        if (tgt) {
+            const float inv = 1.0f / (4.0f * (float)T);
+            const float2 ta = tgt[t], tb = tgt[ts + t];
+            const float e[4] = {a.x - ta.x, a.y - ta.y, b.x - tb.x, b.y - tb.y};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                d3[(int64_t)c * Tp + t + PAD] = 2.0f * e[c] * inv;
+                l += e[c] * e[c] * inv;
+            }
+        }
+    }
+    if (tgt) {                                        // uniform over the grid
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0 && loss) atomicAdd(loss, l);
     }
 }
 
@@ -430,7 +450,8 @@ cudaError_t wgrad64_t(const __nv_bfloat16* x, const __nv_bfloat16* dy16, int64_t
 }  // namespace
 
 // forward of the 4 layers; act[0] holds the input channels, act[1..3] the hidden activations
-cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T, float2* out, cudaStream_t s) {
+cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T, float2* out, cudaStream_t s,
+                        const float2* tgt, int64_t ts, float* loss) {
     const int64_t Tp = T + 2 * PAD;
     const int C = B.C;
     if (C != 64) return cudaErrorInvalidValue;
@@ -446,7 +467,7 @@ cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T
     e = conv64_mma_fwd(B.act[2], Tp, T, B.wtc + wtc_offset(C, 2), W + B.off[5], B.act[3], s);
     if (e) return e;
     k_conv_out4<64><<<(unsigned)((T + CT / 4 - 1) / (CT / 4)), CT, 0, s>>>(B.act[3], Tp, T, W + B.off[6], W + B.off[7],
-                                                                            z, out, zs);
+                                                                            z, out, zs, tgt, ts, B.d[3], loss);
     return cudaGetLastError();
 }
 
@@ -455,8 +476,10 @@ cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt,
                          cudaStream_t s) {
     const int64_t Tp = T + 2 * PAD;
     cudaError_t e = cudaSuccess;
-    k_mse<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(out, tgt, ts, T, Tp, B.d[3], loss);
-    if ((e = cudaGetLastError())) return e;
+    if (tgt) {                                        // else the forward formed d[3] and the loss
+        k_mse<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(out, tgt, ts, T, Tp, B.d[3], loss);
+        if ((e = cudaGetLastError())) return e;
+    }
     float* G = B.grad;
     const float* Wb = B.wbwd;
     // layer 3: weights, then data (masked by act[3] > 0) -> d[2]

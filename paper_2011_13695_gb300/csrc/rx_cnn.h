@@ -39,8 +39,10 @@ struct CnnBufs {
     unsigned int* err = nullptr;    // [1] error word (RX_ERR_* bits) of the tensor-core kernels
 };
 
-// z, tgt: the two polarisations zs / ts complex samples apart (T for contiguous sequences)
-cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T, float2* out, cudaStream_t s);
+// z, tgt: the two polarisations zs / ts complex samples apart (T for contiguous sequences). With a target,
+// the forward also forms the loss gradient and adds the loss, and the backward is then called without one.
+cudaError_t cnn_forward(const CnnBufs& B, const float2* z, int64_t zs, int64_t T, float2* out, cudaStream_t s,
+                        const float2* tgt = nullptr, int64_t ts = 0, float* loss = nullptr);
 cudaError_t cnn_backward(const CnnBufs& B, const float2* out, const float2* tgt, int64_t ts, int64_t T, float* loss,
                          cudaStream_t s);
 cudaError_t cnn_prepare_weights(const CnnBufs& B, cudaStream_t s);

@@ -270,11 +270,12 @@ rx_status rx_pe_train_steps(rx_pe* p, const float* const* d_z, const float* cons
         const int32_t k = which[i];
         const float2* z = reinterpret_cast<const float2*>(d_z[k]) + offs[i];
         const float2* t = reinterpret_cast<const float2*>(d_target[k]) + offs[i];
-        if (cnn_forward(B, z, len[k], window, B.out, s) != cudaSuccess) return RX_ECUDA;
-        // the loss accumulates straight into its slot of d_losses (zeroed above), else into B.loss
+        // the loss accumulates straight into its slot of d_losses (zeroed above), else into B.loss; the
+        // forward's output layer forms the loss gradient
         float* loss = d_losses ? d_losses + i : B.loss;
         if (!d_losses && cudaMemsetAsync(B.loss, 0, sizeof(float), s) != cudaSuccess) return RX_ECUDA;
-        if (cnn_backward(B, B.out, t, len[k], window, loss, s) != cudaSuccess) return RX_ECUDA;
+        if (cnn_forward(B, z, len[k], window, B.out, s, t, len[k], loss) != cudaSuccess) return RX_ECUDA;
+        if (cnn_backward(B, B.out, nullptr, 0, window, nullptr, s) != cudaSuccess) return RX_ECUDA;
         p->step += 1;
         // the Adam step and the weight copies of the new values in one launch
         if (cnn_adam(B, lrs[i], p->step, s, true) != cudaSuccess) return RX_ECUDA;
