@@ -213,7 +213,7 @@ class ClockSampler:
 # unchanged since the capture: stage -> (source file, sha1 of it at capture, bytes read + written).
 PROFILED_TRAFFIC = {
     # DRAM bytes read + written, one ncu capture of this launch
-    "dd_acq": ("k_lms_tile.cuh", "fc6c10aaebce0d8bd21f8070b26bf8cceea39364", 562688),
+    "dd_acq": ("k_lms_tile.cuh", "b23aec6f6da92bcbfffa6aceeb6794cf68d1c9cd", 563456),
     # captured on the 2^18-symbol frame (4,316,416 B: the equalised symbols read once, under ncu's
     # cache flush) and scaled by the symbols of the 2^20-symbol launch (traffic in proportion)
     "bps": ("k_bps.cu", "a6a86046abed1084d0a65f4aa2c6ebe9be2e1228", 17265664),
